@@ -1,0 +1,210 @@
+"""Pins for the oracle's solver layer: V-cycle (Algorithm 3.1 step 1), SCF on small spaces,
+one correction step (Algorithm 3.1) and the full multigrid scheme (Algorithm 3.2).
+
+The references are: the exact linear solve (spsolve), continuum eigenvalues 2 pi^2 / 3 pi^2
+with their O(h^2) rate (Assumption B1), brute-force minimisation of the Gross-Pitaevskii
+energy with an independent quadrature for int u^4, fixed points implied by Theorem 3.1, and
+symmetries of the model problem."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+from scipy.optimize import minimize
+
+from oracle import fmg_oracle as O
+from tests.quadrature import p1_eval, simplex_points
+
+
+def quartic_by_quadrature(mesh, u):
+    full = mesh.to_full(u)
+    tot = 0.0
+    for el in mesh.elems:
+        x, w = simplex_points(mesh.coords[el], mesh.dim)
+        tot += np.sum(w * p1_eval(mesh.coords[el], full[el], x) ** 4)
+    return tot
+
+
+@pytest.mark.parametrize("dim,ns,limit", [(2, (8, 16, 32), 2 * np.pi ** 2), (3, (4, 8, 16), 3 * np.pi ** 2)])
+def test_laplace_eigenvalue_converges_at_h_squared(dim, ns, limit):
+    """W = 0, zeta = 0: lambda_h -> d pi^2 from above with error ratio ~4 per halving."""
+    errs = []
+    for n in ns:
+        mesh = O.Mesh(dim, n, 1.0)
+        lam = spla.eigsh(O.stiffness(mesh).tocsc(), k=1, M=O.mass(mesh).tocsc(), sigma=0.0, which="LM")[0][0]
+        assert lam > limit
+        errs.append(lam - limit)
+    r = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.6 < x < 4.4 for x in r), r
+
+
+def test_level_solve_minimises_gp_energy():
+    """The SCF ground state equals the brute-force minimiser of
+    E(u) = 1/2 u^T (A + W) u + zeta/4 int u^4 on u^T M u = 1 (int u^4 by independent quadrature)."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=1, w_quad=(1.0, 2.0, 0.0), zeta=5.0)
+    lev = O.build_hierarchy(prob)[0]
+    lam, u, res = O.discrete_ground_state(prob, lev)
+    assert res.converged
+    k = (lev.A + lev.Wm).toarray()
+    mm = lev.M.toarray()
+
+    def energy(v):
+        v = v / np.sqrt(v @ mm @ v)
+        return 0.5 * v @ k @ v + prob.zeta / 4 * quartic_by_quadrature(lev.mesh, v)
+
+    best = minimize(energy, np.ones(lev.mesh.n_interior), method="BFGS", options={"gtol": 1e-11})
+    v = best.x / np.sqrt(best.x @ mm @ best.x)
+    v = v if v.sum() > 0 else -v
+    assert np.abs(v - u).max() < 1e-5
+    lam_bf = v @ k @ v + prob.zeta * quartic_by_quadrature(lev.mesh, v)
+    assert abs(lam_bf - lam) < 1e-8 * lam
+
+
+def test_lambda_identity_and_symmetry():
+    """lambda = a^(u,u) + (W u,u) + zeta int u^4 with b(u,u) = 1 (Example 4.1 tested against u
+    itself), and u(x,y) = u(y,x) when W is symmetric (the (1,1)-diagonal mesh is too)."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=3, zeta=3.0)
+    lv = O.build_hierarchy(prob)
+    r = O.fmg_solve(prob, lv)
+    fine = lv[-1]
+    au, q4, bu = O.gp_energy_parts(prob, fine, r.u)
+    assert abs(bu - 1) < 1e-13
+    q4_ind = quartic_by_quadrature(fine.mesh, r.u)
+    assert abs(au + prob.zeta * q4_ind - r.lam) < 1e-11 * r.lam
+    m = fine.mesh.n - 1
+    grid = r.u.reshape(m, m)
+    assert np.abs(grid - grid.T).max() < 1e-11
+    assert np.all(r.u > 0)
+
+
+def test_lambda_increases_with_zeta():
+    lams = []
+    for z in (0.0, 1.0, 10.0, 50.0):
+        prob = O.Problem(dim=2, coarse_cells=4, levels=2, zeta=z)
+        lams.append(O.fmg_solve(prob).lam)
+    assert all(a < b for a, b in zip(lams, lams[1:]))
+
+
+@pytest.mark.parametrize("dim,nc,levels", [(2, 4, 4), (3, 2, 3)])
+def test_vcycle_converges_to_exact_solve(dim, nc, levels):
+    prob = O.Problem(dim=dim, coarse_cells=nc, levels=levels, w_quad=(1.0, 1.0, 1.0))
+    lv = O.build_hierarchy(prob)
+    fine = lv[-1]
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=fine.mesh.n_interior)
+    exact = spla.spsolve(fine.L.tocsc(), f)
+    x = np.zeros_like(f)
+    errs = []
+    for _ in range(16):
+        x = O.vcycle(lv, levels, f, x, prob)
+        errs.append(np.linalg.norm(x - exact))
+    rate = (errs[10] / errs[2]) ** (1 / 8)
+    assert rate < 0.35, rate
+    assert errs[-1] < 1e-6 * np.linalg.norm(exact)
+
+
+def test_two_level_cycle_with_exact_coarse_grid():
+    """With levels = 2 the V-cycle is a two-grid cycle: zero smoothing leaves exactly the
+    Galerkin coarse-grid correction, whose residual is orthogonal to range(P)."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=2, nu_pre=0, nu_post=0)
+    lv = O.build_hierarchy(prob)
+    fine = lv[-1]
+    rng = np.random.default_rng(2)
+    f = rng.normal(size=fine.mesh.n_interior)
+    x = O.vcycle(lv, 2, f, np.zeros_like(f), prob)
+    r = f - fine.L @ x
+    assert np.abs(fine.P.T @ r).max() < 1e-12
+
+
+@pytest.mark.parametrize("form", [O.W_LEFT, O.PAPER_LITERAL])
+def test_correction_fixed_point(form):
+    """Theorem 3.1 with u^(l) = the discrete solution: the auxiliary solution equals it, so it
+    lies in V_{H,h_k} and EigenMG returns it unchanged."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=2, zeta=4.0, operator_form=form, vcycles=3)
+    lv = O.build_hierarchy(prob)
+    lam, u, res = O.discrete_ground_state(prob, lv[-1])
+    info = O.eigen_mg(prob, lv, 2, lam, u)
+    assert abs(info.lam - lam) < 1e-11 * lam
+    assert np.abs(info.u - u).max() < 1e-9
+    assert np.abs(info.u_tilde - u).max() < 1e-9
+
+
+def test_correction_contracts_error():
+    """Repeated corrections converge geometrically to the discrete solution (gamma < 1)."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=3, zeta=2.0, vcycles=1)
+    lv = O.build_hierarchy(prob)
+    lam_h, u_h, _ = O.discrete_ground_state(prob, lv[-1])
+    a = (lv[-1].A).tocsr()
+    r = O.fmg_solve(O.Problem(dim=2, coarse_cells=4, levels=2, zeta=2.0, vcycles=1))
+    lam, u = r.lam, lv[-1].P @ r.u
+    errs = []
+    for _ in range(6):
+        e = u - u_h
+        errs.append(np.sqrt(e @ (a @ e)))
+        info = O.eigen_mg(prob, lv, 3, lam, u)
+        lam, u = info.lam, info.u
+    ratios = [errs[i + 1] / errs[i] for i in range(len(errs) - 1)]
+    assert max(ratios) < 0.5, ratios
+
+
+def test_augmented_solution_minimises_energy_on_augmented_space():
+    """Step 2 of Algorithm 3.1 gives the GP ground state on V_H + span{u~}: it matches a
+    brute-force energy minimisation over that space and lies between the energy bounds."""
+    prob = O.Problem(dim=2, coarse_cells=2, levels=3, zeta=6.0, w_quad=(1.0, 3.0, 0.0))
+    lv = O.build_hierarchy(prob)
+    r2 = O.fmg_solve(O.Problem(dim=2, coarse_cells=2, levels=2, zeta=6.0, w_quad=(1.0, 3.0, 0.0)))
+    lam0, u0 = r2.lam, lv[-1].P @ r2.u
+    info = O.eigen_mg(prob, lv, 3, lam0, u0)
+    psi, k0, mm = O.augmented_blocks(lv, 3, info.u_tilde)
+    fine = lv[-1]
+
+    def energy_c(c):
+        c = c / np.sqrt(c @ mm @ c)
+        v = psi @ c
+        return 0.5 * c @ k0 @ c + prob.zeta / 4 * quartic_by_quadrature(fine.mesh, v)
+
+    c0 = np.zeros(psi.shape[1])
+    c0[-1] = 1.0
+    best = minimize(energy_c, c0, method="BFGS", options={"gtol": 1e-12})
+    c = best.x / np.sqrt(best.x @ mm @ best.x)
+    c = c if c[-1] > 0 else -c
+    assert np.abs(psi @ c - info.u).max() < 1e-5
+
+    def energy(v):
+        k = lv[-1].A + lv[-1].Wm
+        return 0.5 * v @ (k @ v) + prob.zeta / 4 * O.quartic(fine.mesh, v)
+
+    ut = info.u_tilde / np.sqrt(info.u_tilde @ (fine.M @ info.u_tilde))
+    _, u_h, _ = O.discrete_ground_state(prob, fine)
+    assert energy(u_h) - 1e-12 <= energy(info.u) <= energy(ut) + 1e-12
+
+
+def test_fmg_converges_to_discrete_solution_with_many_corrections():
+    prob = O.Problem(dim=2, coarse_cells=4, levels=3, zeta=8.0, corrections=12)
+    lv = O.build_hierarchy(prob)
+    lam_h, u_h, _ = O.discrete_ground_state(prob, lv[-1])
+    r = O.fmg_solve(prob, lv)
+    assert abs(r.lam - lam_h) < 1e-11 * lam_h
+    assert np.abs(r.u - u_h).max() < 1e-8
+
+
+def test_fmg_error_far_below_discretisation_error():
+    """Theorem 3.2: with p = 1 the FMG eigenvalue is much closer to the discrete one than the
+    discrete one is to the next coarser level's (the O(h^2) discretisation error)."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=4, zeta=1.0)
+    lv = O.build_hierarchy(prob)
+    r = O.fmg_solve(prob, lv)
+    lam_h, _, _ = O.discrete_ground_state(prob, lv[-1])
+    lam_2h, _, _ = O.discrete_ground_state(prob, lv[-2])
+    assert abs(r.lam - lam_h) < 0.05 * abs(lam_2h - lam_h)
+
+
+def test_fmg_3d_kuhn_small():
+    prob = O.Problem(dim=3, coarse_cells=2, levels=3, zeta=2.0, w_quad=(1.0, 1.0, 4.0))
+    lv = O.build_hierarchy(prob)
+    r = O.fmg_solve(prob, lv)
+    assert r.converged
+    au, q4, bu = O.gp_energy_parts(prob, lv[-1], r.u)
+    assert abs(bu - 1) < 1e-13 and abs(au + prob.zeta * q4 - r.lam) < 1e-11 * r.lam
+    lam_h, _, _ = O.discrete_ground_state(prob, lv[-1])
+    lam_2h, _, _ = O.discrete_ground_state(prob, lv[-2])
+    assert abs(r.lam - lam_h) < 0.1 * abs(lam_2h - lam_h)
