@@ -1,0 +1,188 @@
+/*
+ * fmg_eig.h - C ABI of the GB300 full-multigrid solver for the Gross-Pitaevskii ground state.
+ *
+ * Method: Jia, Xie, Xie, Xu, "A Full Multigrid Method for Nonlinear Eigenvalue Problems"
+ * (arXiv:1502.04657).  The problem is Example 4.1 (Section 4):
+ *
+ *     -Lap u + W u + zeta u^3 = lambda u  in [0, L]^d,  u = 0 on the boundary,  int u^2 = 1,
+ *
+ * with W(x) = w_const + sum_d w_quad[d] x_d^2, discretised by P1 finite elements (Section 2)
+ * on nested, regularly refined structured meshes (Section 3: beta = 2): 2D squares split by
+ * their (1,1) diagonal, 3D cubes split into 6 Kuhn tetrahedra.  fmg_eig_solve runs the full
+ * multigrid scheme (Algorithm 3.2): a direct nonlinear solve on the coarsest level, then on
+ * every finer level p correction steps (Algorithm 3.1), each = m multigrid V-cycles on the
+ * auxiliary linear problem followed by the nonlinear eigenproblem on V_H + span{u~}.
+ *
+ * Conventions (every entry point):
+ *   - Return 0 (FMG_OK) or a negative FMG_E* code; nothing is thrown across the ABI.
+ *   - Vectors u on level k are FP64, interior nodes only, lexicographic with x fastest:
+ *     (n_k - 1)^d entries, n_k = coarse_cells << (k - 1) cells per side.  Dirichlet values
+ *     are zero and are not stored.
+ *   - The library owns every device buffer it allocates; the caller owns the buffers it
+ *     passes.  "_dev" pointers are device memory on the handle's device, other pointers are
+ *     host memory (pinned or pageable).
+ *   - A handle is not thread-safe: use one handle per host thread.  All work of a handle is
+ *     ordered on the stream passed to the call (NULL = the handle's own stream).
+ *   - Every device-side loop (SCF/Newton iterations) is bounded; a bound that is hit is
+ *     reported as FMG_ENOCONV with the partial result still written.
+ */
+#ifndef FMG_EIG_H
+#define FMG_EIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMG_OK 0
+#define FMG_EINVAL (-1)   /* invalid argument or size */
+#define FMG_ENOMEM (-2)   /* device allocation failed */
+#define FMG_ENOCONV (-3)  /* a nonlinear solve hit its iteration cap */
+#define FMG_ECUDA (-4)    /* a CUDA runtime call failed */
+#define FMG_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define FMG_ENOTSUP (-6)  /* combination of options not built */
+
+#define FMG_SMOOTH_JACOBI 0
+#define FMG_FP64 0
+#define FMG_MIXED_FP32 1
+#define FMG_W_LEFT 0        /* (A + W) u^ = lambda M u - N(u)              */
+#define FMG_PAPER_LITERAL 1 /*  A u^      = lambda M u - W u - N(u)        */
+
+/* Problem and method parameters.  Example 4.1 fixes the PDE; Algorithm 3.1 fixes m (vcycles)
+ * and Algorithm 3.2 fixes p (corrections) and the level count n.                            */
+typedef struct fmg_eig_problem {
+  int32_t dim;          /* 2 or 3                                                          */
+  int32_t coarse_cells; /* cells per side of T_H = T_{h_1}; >= 2                           */
+  int32_t levels;       /* n >= 1; finest cells per side = coarse_cells << (levels - 1)    */
+  int32_t nu_pre;       /* damped-Jacobi pre-smoothing sweeps per V-cycle level (>= 0)     */
+  int32_t nu_post;      /* post-smoothing sweeps (>= 0)                                    */
+  int32_t vcycles;      /* m of Algorithm 3.1 (>= 1)                                       */
+  int32_t corrections;  /* p of Algorithm 3.2 (>= 1)                                       */
+  int32_t smoother;     /* FMG_SMOOTH_JACOBI                                               */
+  int32_t precision;    /* FMG_FP64 | FMG_MIXED_FP32                                       */
+  int32_t operator_form;/* FMG_W_LEFT | FMG_PAPER_LITERAL                                  */
+  int32_t scf_max_iter; /* cap on nonlinear iterations per small solve (e.g. 100)          */
+  int32_t reserved;
+  double box_len;       /* L > 0                                                           */
+  double w_const;       /* W(x) = w_const + sum_d w_quad[d] x_d^2                          */
+  double w_quad[3];
+  double zeta;          /* >= 0                                                            */
+  double omega;         /* Jacobi damping, 0 < omega <= 1 (2/3)                            */
+  double scf_tol;       /* relative residual tolerance of the small nonlinear solves       */
+} fmg_eig_problem;
+
+#define FMG_MAX_LEVELS 16
+
+typedef struct fmg_eig_stats {
+  double lambda;                        /* final eigenvalue                                */
+  double solve_ms;                      /* device time of the solve (CUDA events)          */
+  double norm_defect;                   /* b(u,u) - 1 on the finest level                  */
+  double identity_defect;               /* lambda - a(u,u) - (Wu,u) - zeta int u^4         */
+  double lambda_levels[FMG_MAX_LEVELS]; /* lambda_{h_k} after level k                      */
+  int32_t scf_iters[FMG_MAX_LEVELS];    /* nonlinear iterations of the last small solve    */
+  int32_t levels;
+  int32_t status;                       /* FMG_OK or FMG_ENOCONV                           */
+} fmg_eig_stats;
+
+typedef struct fmg_eig_handle fmg_eig_handle;
+
+/* Validate *prob, allocate the level hierarchy on the current CUDA device and record the
+ * solve as a CUDA graph.  Returns FMG_EINVAL for a bad parameter, FMG_ENOMEM if device
+ * memory runs out (nothing stays allocated then), FMG_ECUDA for other CUDA failures.      */
+int fmg_eig_create(const fmg_eig_problem* prob, fmg_eig_handle** out);
+
+/* Number of interior unknowns of level k (1-based) of this handle, 0 for a bad k.          */
+size_t fmg_eig_level_size(const fmg_eig_handle* h, int32_t level);
+
+/* Algorithm 3.2 end to end with host buffers: writes lambda_{h_n} to *lambda and, when
+ * u_host is not NULL, u_{h_n} (u_len must equal fmg_eig_level_size(h, levels)).  stats may
+ * be NULL.  Synchronous.                                                                    */
+int fmg_eig_solve(fmg_eig_handle* h, double* lambda, double* u_host, size_t u_len,
+                  fmg_eig_stats* stats);
+
+/* Same solve with device outputs and no host synchronisation: lambda_dev (1 double) and
+ * u_dev (nullable, u_len doubles) are written in stream order on `stream` (a cudaStream_t,
+ * NULL for the handle's stream).                                                            */
+int fmg_eig_solve_dev(fmg_eig_handle* h, double* lambda_dev, double* u_dev, size_t u_len,
+                      void* stream);
+
+/* Release every device buffer, graph and stream of the handle.  NULL is ignored.           */
+void fmg_eig_destroy(fmg_eig_handle* h);
+
+/* Change the potential (w_const, w_quad), zeta and omega of an existing handle: the PDE of
+ * Example 4.1 with new coefficients on the same mesh hierarchy.  Every other field of *prob
+ * must equal the handle's (FMG_EINVAL otherwise).  Synchronises the handle's stream; the
+ * next solve uses the new values (they are uploaded from pinned host memory per solve).   */
+int fmg_eig_set_params(fmg_eig_handle* h, const fmg_eig_problem* prob);
+
+/* Instrumentation (no counterpart in the paper).  fmg_eig_kernel_count: kernel launches
+ * per solve (nodes of the solve's CUDA graph).  fmg_eig_profile: device time in ms of the
+ * finest-level launch of each step in the most recent solve, in the order
+ * [Jacobi sweep, residual, restriction, prolongation, auxiliary RHS, moments, augmented
+ * nonlinear solve, one whole V-cycle]; writes min(count, 8) entries and returns that number
+ * (FMG_EINVAL for bad arguments).  Synchronises the handle's stream.                       */
+int fmg_eig_kernel_count(const fmg_eig_handle* h);
+int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count);
+
+/* Static description of a return code.                                                    */
+const char* fmg_eig_strerror(int code);
+
+/* ------------------------------------------------------------------------------------------
+ * Component entry points: the steps of the hot path, one call each, on device vectors in the
+ * interior layout above.  Each call is asynchronous on `stream` (NULL = handle's stream) and
+ * uses the handle's level buffers as scratch, so calls on one handle must not overlap.
+ * ---------------------------------------------------------------------------------------- */
+
+/* y = L_k x with L = A + W (FMG_W_LEFT) or A (FMG_PAPER_LITERAL): the operator of the
+ * auxiliary problem of Algorithm 3.1 step 1 (Section 2, the forms a^ and (W u, v)).          */
+int fmg_eig_apply_operator(fmg_eig_handle* h, int32_t level, const double* x_dev,
+                           double* y_dev, void* stream);
+
+/* y = M_k x, the mass matrix of b(u, v) = int u v (Section 2).                             */
+int fmg_eig_apply_mass(fmg_eig_handle* h, int32_t level, const double* x_dev, double* y_dev,
+                       void* stream);
+
+/* One damped Jacobi sweep x_out = x_in + omega D^{-1} (f - L_k x_in) (the smoother of the
+ * multigrid iteration of Algorithm 3.1 step 1).                                             */
+int fmg_eig_jacobi(fmg_eig_handle* h, int32_t level, const double* f_dev,
+                   const double* x_in_dev, double* x_out_dev, void* stream);
+
+/* r_c = P_k^T (f - L_k x): fine residual restricted to level k-1 (k >= 2).                 */
+int fmg_eig_residual_restrict(fmg_eig_handle* h, int32_t level, const double* f_dev,
+                              const double* x_dev, double* rc_dev, void* stream);
+
+/* x += P_k e_c: coarse correction of level k-1 prolonged to level k (k >= 2); the nested
+ * space embedding of Section 3.                                                             */
+int fmg_eig_prolong_add(fmg_eig_handle* h, int32_t level, const double* ec_dev, double* x_dev,
+                        void* stream);
+
+/* n_i = int u^3 phi_i on level k (the cubic part of f(x, u) of Example 4.1, without zeta). */
+int fmg_eig_nonlinear_load(fmg_eig_handle* h, int32_t level, const double* u_dev,
+                           double* n_dev, void* stream);
+
+/* f = lambda M_k u - zeta N(u) [- W_k u for FMG_PAPER_LITERAL]: the right-hand side of the
+ * auxiliary problem (Algorithm 3.1 step 1).  lambda is read from host memory.               */
+int fmg_eig_aux_rhs(fmg_eig_handle* h, int32_t level, double lambda, const double* u_dev,
+                    double* f_dev, void* stream);
+
+/* x <- MG(V_{h_k}, f, x, m): m V-cycles in place (Algorithm 3.1 step 1).                    */
+int fmg_eig_multigrid(fmg_eig_handle* h, int32_t level, const double* f_dev, double* x_dev,
+                      void* stream);
+
+/* One correction step EigenMG(V_H, lambda, u, V_{h_k}, m) (Algorithm 3.1) on level k >= 2:
+ * reads (lambda_in, u_in), writes the new pair and, if u_tilde_dev is not NULL, the
+ * auxiliary iterate u~.  *iters receives the nonlinear iteration count.  Synchronous.       */
+int fmg_eig_correction(fmg_eig_handle* h, int32_t level, double lambda_in,
+                       const double* u_in_dev, double* lambda_out, double* u_out_dev,
+                       double* u_tilde_dev, int32_t* iters);
+
+/* Algorithm 3.2 step 1: the nonlinear eigenproblem directly on V_{h_1}.  Synchronous.       */
+int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev,
+                         int32_t* iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMG_EIG_H */

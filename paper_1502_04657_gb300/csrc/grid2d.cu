@@ -1,0 +1,286 @@
+// 2D level kernels: matrix-free P1 stencils on the structured right-triangle mesh.
+//
+// Mesh (Section 3, regular refinement with beta = 2): squares of side h split by their (1,1)
+// diagonal, so node (i,j) couples to E, W, N, S, NE and SW.  With x = i h, y = j h and
+// W = w0 + wx x^2 + wy y^2, exact integration of a^(phi_p, phi_q) + (W phi_p, phi_q)
+// (Section 2) gives, per node, the stencil
+//   C : 4  + h^2 w0/2  + h^4 [wx (9i^2+1)/18          + wy (9j^2+1)/18]
+//   E : -1 + h^2 w0/12 + h^4 [wx (10i^2+10i+3)/120    + wy (15j^2+1)/180]
+//   N : -1 + h^2 w0/12 + h^4 [wx (15i^2+1)/180        + wy (10j^2+10j+3)/120]
+//   NE:      h^2 w0/12 + h^4 [wx (10i^2+10i+3)/120    + wy (10j^2+10j+3)/120]
+// with W = E(i-1,j), S = N(i,j-1), SW = NE(i-1,j-1) by symmetry; the mass stencil is
+// h^2/12 (6 at C, 1 at the six neighbours).  (Derived once by symbolic integration over the
+// six triangles of a node's star.)
+//
+// FP64 on this part issues at ~1/64 of the FP32 rate, so the kernels trade bandwidth for
+// FP64 instructions: the four coupling arrays and omega/D are materialised once per solve
+// (40 B/node extra traffic) and every sweep then costs 9 FP64 instructions per node.
+#include "fmg_internal.h"
+
+namespace fmg {
+namespace {
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+
+__device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j * pitch + i; }
+
+__global__ void k_coef2d(int n, int pitch, double h, const PotentialParams* __restrict__ pp,
+                         Coef2D c) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (i > n || j > n) return;
+  const PotentialParams p = *pp;
+  const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
+  const double h2 = h * h, h4 = h2 * h2;
+  const double di = i, dj = j;
+  const double m = h2 * p.w0;
+  const double xe = (10.0 * di * di + 10.0 * di + 3.0) / 120.0;
+  const double yn = (10.0 * dj * dj + 10.0 * dj + 3.0) / 120.0;
+  const size_t k = at(i, j, pitch);
+  const double cc = 4.0 + wl * (m / 2.0 + h4 * (p.wx * (9.0 * di * di + 1.0) / 18.0 +
+                                                p.wy * (9.0 * dj * dj + 1.0) / 18.0));
+  c.cC[k] = cc;
+  c.cE[k] = -1.0 + wl * (m / 12.0 + h4 * (p.wx * xe + p.wy * (15.0 * dj * dj + 1.0) / 180.0));
+  c.cN[k] = -1.0 + wl * (m / 12.0 + h4 * (p.wx * (15.0 * di * di + 1.0) / 180.0 + p.wy * yn));
+  c.cNE[k] = wl * (m / 12.0 + h4 * (p.wx * xe + p.wy * yn));
+  c.dinv[k] = p.omega / cc;
+}
+
+// (L x)_k: 1 DMUL + 6 DFMA
+__device__ __forceinline__ double lop(const Coef2D& c, const double* __restrict__ x, size_t k,
+                                      int pitch) {
+  double v = c.cC[k] * x[k];
+  v = fma(c.cE[k], x[k + 1], v);
+  v = fma(c.cE[k - 1], x[k - 1], v);
+  v = fma(c.cN[k], x[k + pitch], v);
+  v = fma(c.cN[k - pitch], x[k - pitch], v);
+  v = fma(c.cNE[k], x[k + pitch + 1], v);
+  v = fma(c.cNE[k - pitch - 1], x[k - pitch - 1], v);
+  return v;
+}
+
+#define INTERIOR_2D                                 \
+  const int i = 1 + blockIdx.x * BX + threadIdx.x;  \
+  const int j = 1 + blockIdx.y * BY + threadIdx.y;  \
+  if (i >= n || j >= n) return;                     \
+  const size_t k = at(i, j, pitch);
+
+__global__ void k_apply2d(int n, int pitch, Coef2D c, const double* __restrict__ x,
+                          double* __restrict__ y) {
+  INTERIOR_2D
+  y[k] = lop(c, x, k, pitch);
+}
+
+__global__ void k_mass2d(int n, int pitch, double h2_12, const double* __restrict__ x,
+                         double* __restrict__ y) {
+  INTERIOR_2D
+  const double s = ((x[k + 1] + x[k - 1]) + (x[k + pitch] + x[k - pitch])) +
+                   (x[k + pitch + 1] + x[k - pitch - 1]);
+  y[k] = h2_12 * fma(6.0, x[k], s);
+}
+
+__global__ void k_jacobi2d(int n, int pitch, Coef2D c, const double* __restrict__ f,
+                           const double* __restrict__ x, double* __restrict__ xo) {
+  INTERIOR_2D
+  xo[k] = fma(c.dinv[k], f[k] - lop(c, x, k, pitch), x[k]);
+}
+
+__global__ void k_jacobi2d_zero(int n, int pitch, Coef2D c, const double* __restrict__ f,
+                                double* __restrict__ xo) {
+  INTERIOR_2D
+  xo[k] = c.dinv[k] * f[k];
+}
+
+__global__ void k_residual2d(int n, int pitch, Coef2D c, const double* __restrict__ f,
+                             const double* __restrict__ x, double* __restrict__ r) {
+  INTERIOR_2D
+  r[k] = f[k] - lop(c, x, k, pitch);
+}
+
+// r_c = P^T r_f: a coarse node takes its own fine value plus half of the six fine nodes on
+// the coarse edges through it (the (1,1)-diagonal edges included).
+__global__ void k_restrict2d(int nc, int pc, int pf, const double* __restrict__ rf,
+                             double* __restrict__ rc) {
+  const int I = 1 + blockIdx.x * BX + threadIdx.x;
+  const int J = 1 + blockIdx.y * BY + threadIdx.y;
+  if (I >= nc || J >= nc) return;
+  const size_t kf = at(2 * I, 2 * J, pf);
+  const double s = ((rf[kf + 1] + rf[kf - 1]) + (rf[kf + pf] + rf[kf - pf])) +
+                   (rf[kf + pf + 1] + rf[kf - pf - 1]);
+  rc[at(I, J, pc)] = fma(0.5, s, rf[kf]);
+}
+
+// x_f (+)= P e_c (+ scale * extra): fine node (2I+a, 2J+b) is the midpoint of coarse nodes
+// (I,J) and (I+a, J+b), a, b in {0,1}.
+__global__ void k_prolong2d(int nf, int pf, int pc, const double* __restrict__ ec,
+                            double* __restrict__ xf, int add, const double* __restrict__ extra,
+                            const double* __restrict__ scale) {
+  const int n = nf, pitch = pf;
+  INTERIOR_2D
+  const int a = i & 1, b = j & 1;
+  const size_t kc = at(i >> 1, j >> 1, pc);
+  double e = ec[kc];
+  if (a | b) e = 0.5 * (e + ec[kc + a + (size_t)b * pc]);
+  if (add) e += xf[k];
+  if (extra) e = fma(scale[0], extra[k], e);
+  xf[k] = e;
+}
+
+// int u^3 phi_p over the six triangles of the star of p, exactly.  With the hexagon of
+// neighbours n_0..n_5 = E, NE, N, W, SW, S taken cyclically (each consecutive pair closes one
+// triangle with p), summing int_K u^3 lambda_p = |K|/60 sum_{|b|=3} u^b (b_p + 1) gives
+//   |K|/60 [24u^3 + 6u^2 S1 + 2u(2 S2 + P) + 2 S3 + Q],
+// S_q = sum n_k^q, P = sum n_k n_{k+1}, Q = sum n_k n_{k+1} (n_k + n_{k+1}), |K| = h^2/2.
+__device__ __forceinline__ double nload_at(const double* __restrict__ u, size_t k, int pitch) {
+  const double up = u[k];
+  const double n0 = u[k + 1], n1 = u[k + pitch + 1], n2 = u[k + pitch];
+  const double n3 = u[k - 1], n4 = u[k - pitch - 1], n5 = u[k - pitch];
+  const double s1 = ((n0 + n1) + (n2 + n3)) + (n4 + n5);
+  const double q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = n3 * n3, q4 = n4 * n4,
+               q5 = n5 * n5;
+  const double s2 = ((q0 + q1) + (q2 + q3)) + (q4 + q5);
+  double s3 = q0 * n0;
+  s3 = fma(q1, n1, s3);
+  s3 = fma(q2, n2, s3);
+  s3 = fma(q3, n3, s3);
+  s3 = fma(q4, n4, s3);
+  s3 = fma(q5, n5, s3);
+  const double p0 = n0 * n1, p1 = n1 * n2, p2 = n2 * n3, p3 = n3 * n4, p4 = n4 * n5,
+               p5 = n5 * n0;
+  const double pp = ((p0 + p1) + (p2 + p3)) + (p4 + p5);
+  double qq = p0 * (n0 + n1);
+  qq = fma(p1, n1 + n2, qq);
+  qq = fma(p2, n2 + n3, qq);
+  qq = fma(p3, n3 + n4, qq);
+  qq = fma(p4, n4 + n5, qq);
+  qq = fma(p5, n5 + n0, qq);
+  const double u2 = up * up;
+  double v = 24.0 * u2 * up;
+  v = fma(6.0 * u2, s1, v);
+  v = fma(2.0 * up, fma(2.0, s2, pp), v);
+  v = fma(2.0, s3, v);
+  return v + qq;
+}
+
+__global__ void k_nload2d(int n, int pitch, double scale, const double* __restrict__ u,
+                          double* __restrict__ out) {
+  INTERIOR_2D
+  out[k] = scale * nload_at(u, k, pitch);
+}
+
+__global__ void k_rhs2d(int n, int pitch, double h2_12, double h2_120,
+                        const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                        const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_2D
+  const double nscale = pp->zeta * h2_120;
+  const double s = ((u[k + 1] + u[k - 1]) + (u[k + pitch] + u[k - pitch])) +
+                   (u[k + pitch + 1] + u[k - pitch - 1]);
+  const double mu = h2_12 * fma(6.0, u[k], s);
+  f[k] = fma(lam[0], mu, -nscale * nload_at(u, k, pitch));
+}
+
+__global__ void k_dense_level1_2d(int n, int pitch, double h2_12, Coef2D c, double* L,
+                                  double* M) {
+  const int m = n - 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m * m) return;
+  const int i = 1 + p % m, j = 1 + p / m;
+  double* lr = L + (size_t)p * m * m;
+  double* mr = M + (size_t)p * m * m;
+  for (int q = 0; q < m * m; ++q) {
+    lr[q] = 0.0;
+    mr[q] = 0.0;
+  }
+  const size_t k = at(i, j, pitch);
+  lr[p] = c.cC[k];
+  mr[p] = 6.0 * h2_12;
+  auto put = [&](int di, int dj, double v) {
+    const int ii = i + di, jj = j + dj;
+    if (ii < 1 || jj < 1 || ii >= n || jj >= n) return;
+    const int q = (ii - 1) + (jj - 1) * m;
+    lr[q] = v;
+    mr[q] = h2_12;
+  };
+  put(1, 0, c.cE[k]);
+  put(-1, 0, c.cE[k - 1]);
+  put(0, 1, c.cN[k]);
+  put(0, -1, c.cN[k - pitch]);
+  put(1, 1, c.cNE[k]);
+  put(-1, -1, c.cNE[k - pitch - 1]);
+}
+
+__global__ void k_start2d(int n, double* c) {
+  const int m = n - 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m * m) return;
+  const int i = 1 + p % m, j = 1 + p / m;
+  c[p] = sinpi((double)i / n) * sinpi((double)j / n);
+}
+
+dim3 grid_of(int count_x, int count_y) {
+  return dim3((count_x + BX - 1) / BX, (count_y + BY - 1) / BY);
+}
+
+}  // namespace
+
+void coef2d_setup(const Grid& g, const PotentialParams* p, const Coef2D& c, cudaStream_t s) {
+  k_coef2d<<<grid_of(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, g.h, p, c);
+}
+
+void apply2d(const Grid& g, const Coef2D& c, const double* x, double* y, cudaStream_t s) {
+  k_apply2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, x, y);
+}
+
+void mass2d(const Grid& g, const double* x, double* y, cudaStream_t s) {
+  k_mass2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, g.h * g.h / 12.0,
+                                                              x, y);
+}
+
+void jacobi2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* xo,
+              bool x_is_zero, cudaStream_t s) {
+  if (x_is_zero)
+    k_jacobi2d_zero<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, xo);
+  else
+    k_jacobi2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x, xo);
+}
+
+void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* r,
+                cudaStream_t s) {
+  k_residual2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x, r);
+}
+
+void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
+                cudaStream_t s) {
+  k_restrict2d<<<grid_of(coarse.n - 1, coarse.n - 1), dim3(BX, BY), 0, s>>>(
+      coarse.n, coarse.pitch, fine.pitch, rf, rc);
+}
+
+void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
+               const double* extra, const double* scale, cudaStream_t s) {
+  k_prolong2d<<<grid_of(fine.n - 1, fine.n - 1), dim3(BX, BY), 0, s>>>(
+      fine.n, fine.pitch, coarse.pitch, ec, xf, add ? 1 : 0, extra, scale);
+}
+
+void nload2d(const Grid& g, const double* u, double* out, cudaStream_t s) {
+  k_nload2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch,
+                                                               g.h * g.h / 120.0, u, out);
+}
+
+void rhs2d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
+           double* f, cudaStream_t s) {
+  k_rhs2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(
+      g.n, g.pitch, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
+}
+
+void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s) {
+  const int m = g.n - 1;
+  k_dense_level1_2d<<<(m * m + 63) / 64, 64, 0, s>>>(g.n, g.pitch, g.h * g.h / 12.0, c, L, M);
+}
+
+void start_vector(const Grid& g, double /*box_len*/, double* c, cudaStream_t s) {
+  const int m = g.n - 1;
+  k_start2d<<<(m * m + 63) / 64, 64, 0, s>>>(g.n, c);
+}
+
+}  // namespace fmg

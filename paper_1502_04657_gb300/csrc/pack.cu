@@ -1,0 +1,46 @@
+// Conversion between the ABI layout (interior nodes, x fastest) and the padded device layout.
+#include "fmg_internal.h"
+
+namespace fmg {
+namespace {
+
+__device__ __forceinline__ size_t padded_index(int dim, int n, int pitch, size_t p) {
+  const size_t m = (size_t)(n - 1);
+  const size_t i = 1 + p % m;
+  if (dim == 2) return (1 + p / m) * pitch + i;
+  const size_t j = 1 + (p / m) % m;
+  const size_t l = 1 + p / (m * m);
+  return (l * (size_t)(n + 1) + j) * pitch + i;
+}
+
+__global__ void k_pack(int dim, int n, int pitch, size_t count, const double* __restrict__ in,
+                       double* __restrict__ out) {
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p < count) out[padded_index(dim, n, pitch, p)] = in[p];
+}
+
+__global__ void k_unpack(int dim, int n, int pitch, size_t count, const double* __restrict__ in,
+                         double* __restrict__ out) {
+  const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p < count) out[p] = in[padded_index(dim, n, pitch, p)];
+}
+
+}  // namespace
+
+void pack_interior(const Grid& g, const double* interior, double* padded, cudaStream_t s) {
+  const size_t count = g.interior();
+  k_pack<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(g.dim, g.n, g.pitch, count, interior,
+                                                         padded);
+}
+
+void unpack_interior(const Grid& g, const double* padded, double* interior, cudaStream_t s) {
+  const size_t count = g.interior();
+  k_unpack<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(g.dim, g.n, g.pitch, count, padded,
+                                                           interior);
+}
+
+void scatter_level1(const Grid& g, const double* c, double* padded, cudaStream_t s) {
+  pack_interior(g, c, padded, s);
+}
+
+}  // namespace fmg

@@ -1,0 +1,51 @@
+// Deterministic FP64 dot products: fixed block count and fixed-order trees, so the result
+// does not depend on scheduling (no atomics).
+#include "fmg_internal.h"
+
+namespace fmg {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+__global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
+                              size_t n, size_t chunk, double* __restrict__ partials) {
+  __shared__ double sh[kThreads];
+  const size_t beg = blockIdx.x * chunk;
+  const size_t end = beg + chunk < n ? beg + chunk : n;
+  double s = 0.0;
+  for (size_t i = beg + threadIdx.x; i < end; i += kThreads) s = fma(a[i], b[i], s);
+  const double t = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void k_sum_final(const double* __restrict__ partials, int m, double* out) {
+  __shared__ double sh[kThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += kThreads) s += partials[i];
+  const double t = block_sum(s, sh);
+  if (threadIdx.x == 0) out[0] = t;
+}
+
+}  // namespace
+
+void dot(const double* a, const double* b, size_t n, double* partials, double* out,
+         cudaStream_t s) {
+  size_t blocks = (n + 4 * kThreads - 1) / (4 * kThreads);
+  if (blocks > (size_t)kReduceBlocks) blocks = kReduceBlocks;
+  if (blocks < 1) blocks = 1;
+  const size_t chunk = (n + blocks - 1) / blocks;
+  k_dot_partial<<<(unsigned)blocks, kThreads, 0, s>>>(a, b, n, chunk, partials);
+  k_sum_final<<<1, kThreads, 0, s>>>(partials, (int)blocks, out);
+}
+
+}  // namespace fmg

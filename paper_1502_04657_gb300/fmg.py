@@ -1,0 +1,251 @@
+"""ctypes binding of libfmg_eig (include/fmg_eig.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels.  Importing this module never
+falls back to anything else: if the shared library is missing the first call raises."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfmg_eig.so")
+
+FMG_OK, FMG_EINVAL, FMG_ENOMEM, FMG_ENOCONV, FMG_ECUDA, FMG_ETIMEOUT, FMG_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+FMG_FP64, FMG_MIXED_FP32 = 0, 1
+FMG_W_LEFT, FMG_PAPER_LITERAL = 0, 1
+FMG_MAX_LEVELS = 16
+
+
+class fmg_eig_problem(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32), ("coarse_cells", C.c_int32), ("levels", C.c_int32),
+        ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("vcycles", C.c_int32),
+        ("corrections", C.c_int32), ("smoother", C.c_int32), ("precision", C.c_int32),
+        ("operator_form", C.c_int32), ("scf_max_iter", C.c_int32), ("reserved", C.c_int32),
+        ("box_len", C.c_double), ("w_const", C.c_double), ("w_quad", C.c_double * 3),
+        ("zeta", C.c_double), ("omega", C.c_double), ("scf_tol", C.c_double),
+    ]
+
+
+class fmg_eig_stats(C.Structure):
+    _fields_ = [
+        ("lambda_", C.c_double), ("solve_ms", C.c_double), ("norm_defect", C.c_double),
+        ("identity_defect", C.c_double), ("lambda_levels", C.c_double * FMG_MAX_LEVELS),
+        ("scf_iters", C.c_int32 * FMG_MAX_LEVELS), ("levels", C.c_int32), ("status", C.c_int32),
+    ]
+
+
+class FmgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.c_int32
+
+_SIGS = {
+    "fmg_eig_create": (C.c_int, [C.POINTER(fmg_eig_problem), C.POINTER(_P)]),
+    "fmg_eig_level_size": (C.c_size_t, [_P, _I32]),
+    "fmg_eig_solve": (C.c_int, [_P, _D, _P, C.c_size_t, C.POINTER(fmg_eig_stats)]),
+    "fmg_eig_solve_dev": (C.c_int, [_P, _P, _P, C.c_size_t, _P]),
+    "fmg_eig_destroy": (None, [_P]),
+    "fmg_eig_strerror": (C.c_char_p, [C.c_int]),
+    "fmg_eig_set_params": (C.c_int, [_P, C.POINTER(fmg_eig_problem)]),
+    "fmg_eig_kernel_count": (C.c_int, [_P]),
+    "fmg_eig_profile": (C.c_int, [_P, _D, _I32]),
+    "fmg_eig_apply_operator": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "fmg_eig_apply_mass": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "fmg_eig_jacobi": (C.c_int, [_P, _I32, _P, _P, _P, _P]),
+    "fmg_eig_residual_restrict": (C.c_int, [_P, _I32, _P, _P, _P, _P]),
+    "fmg_eig_prolong_add": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "fmg_eig_nonlinear_load": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "fmg_eig_aux_rhs": (C.c_int, [_P, _I32, C.c_double, _P, _P, _P]),
+    "fmg_eig_multigrid": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "fmg_eig_correction": (C.c_int, [_P, _I32, C.c_double, _P, _D, _P, _P, C.POINTER(_I32)]),
+    "fmg_eig_coarse_solve": (C.c_int, [_P, _D, _P, C.POINTER(_I32)]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfmg_eig.so and declare every exported entry point; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FmgError(FMG_ECUDA, f"libfmg_eig.so not built at {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load_library().fmg_eig_strerror(code).decode()
+    except Exception:  # library missing: still give a readable message
+        return str(code)
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+@dataclass
+class Problem:
+    """Mirror of fmg_eig_problem with the defaults of the 2D benchmark configurations."""
+
+    dim: int = 2
+    coarse_cells: int = 8
+    levels: int = 6
+    nu_pre: int = 2
+    nu_post: int = 2
+    vcycles: int = 2
+    corrections: int = 1
+    precision: int = FMG_FP64
+    operator_form: int = FMG_W_LEFT
+    scf_max_iter: int = 100
+    box_len: float = 1.0
+    w_const: float = 0.0
+    w_quad: tuple = (1.0, 1.0, 1.0)
+    zeta: float = 1.0
+    omega: float = 2.0 / 3.0
+    scf_tol: float = 1e-13
+
+    def to_c(self) -> fmg_eig_problem:
+        p = fmg_eig_problem()
+        for f in ("dim", "coarse_cells", "levels", "nu_pre", "nu_post", "vcycles", "corrections",
+                  "precision", "operator_form", "scf_max_iter", "box_len", "w_const", "zeta",
+                  "omega", "scf_tol"):
+            setattr(p, f, getattr(self, f))
+        p.smoother = 0
+        p.w_quad[:] = [float(x) for x in self.w_quad]
+        return p
+
+    def cells(self, k: int) -> int:
+        return self.coarse_cells << (k - 1)
+
+    def size(self, k: int) -> int:
+        return (self.cells(k) - 1) ** self.dim
+
+
+def _ptr(t) -> int | None:
+    """Device or host address of a torch tensor / numpy array (None passes NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+class Solver:
+    """One handle of libfmg_eig; methods map 1:1 to the C entry points."""
+
+    def __init__(self, problem: Problem):
+        self.lib = load_library()
+        self.problem = problem
+        self._cp = problem.to_c()
+        h = _P()
+        rc = self.lib.fmg_eig_create(C.byref(self._cp), C.byref(h))
+        if rc != FMG_OK:
+            raise FmgError(rc, "fmg_eig_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fmg_eig_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def level_size(self, k: int) -> int:
+        return self.lib.fmg_eig_level_size(self.h, k)
+
+    PROFILE_KEYS = ("jacobi", "residual", "restrict", "prolong", "rhs", "moments", "dense", "vcycle")
+
+    def set_params(self, problem: Problem):
+        cp = problem.to_c()
+        self._check(self.lib.fmg_eig_set_params(self.h, C.byref(cp)), "set_params")
+        self.problem, self._cp = problem, cp
+
+    def kernel_count(self) -> int:
+        return self.lib.fmg_eig_kernel_count(self.h)
+
+    def profile(self) -> dict:
+        buf = (C.c_double * 8)()
+        n = self.lib.fmg_eig_profile(self.h, buf, 8)
+        if n < 0:
+            raise FmgError(n, "profile")
+        return {k: buf[i] for i, k in enumerate(self.PROFILE_KEYS[:n])}
+
+    def _check(self, rc, what, allow=()):
+        if rc != FMG_OK and rc not in allow:
+            raise FmgError(rc, what)
+        return rc
+
+    # -- whole solve ---------------------------------------------------------------------
+    def solve(self, u_host=None, stats: bool = False):
+        lam = C.c_double()
+        st = fmg_eig_stats() if stats else None
+        n = 0 if u_host is None else int(u_host.size if hasattr(u_host, "size") and not callable(u_host.size) else u_host.numel())
+        rc = self.lib.fmg_eig_solve(self.h, C.byref(lam), _ptr(u_host), n,
+                                    C.byref(st) if st is not None else None)
+        self._check(rc, "fmg_eig_solve", allow=(FMG_ENOCONV,))
+        return lam.value, st, rc
+
+    def solve_dev(self, lam_dev, u_dev=None, stream=None):
+        n = 0 if u_dev is None else u_dev.numel()
+        rc = self.lib.fmg_eig_solve_dev(self.h, _ptr(lam_dev), _ptr(u_dev), n, stream)
+        return self._check(rc, "fmg_eig_solve_dev")
+
+    # -- components ----------------------------------------------------------------------
+    def apply_operator(self, k, x, y, stream=None):
+        return self._check(self.lib.fmg_eig_apply_operator(self.h, k, _ptr(x), _ptr(y), stream), "apply_operator")
+
+    def apply_mass(self, k, x, y, stream=None):
+        return self._check(self.lib.fmg_eig_apply_mass(self.h, k, _ptr(x), _ptr(y), stream), "apply_mass")
+
+    def jacobi(self, k, f, x_in, x_out, stream=None):
+        return self._check(self.lib.fmg_eig_jacobi(self.h, k, _ptr(f), _ptr(x_in), _ptr(x_out), stream), "jacobi")
+
+    def residual_restrict(self, k, f, x, rc, stream=None):
+        return self._check(self.lib.fmg_eig_residual_restrict(self.h, k, _ptr(f), _ptr(x), _ptr(rc), stream), "residual_restrict")
+
+    def prolong_add(self, k, ec, x, stream=None):
+        return self._check(self.lib.fmg_eig_prolong_add(self.h, k, _ptr(ec), _ptr(x), stream), "prolong_add")
+
+    def nonlinear_load(self, k, u, out, stream=None):
+        return self._check(self.lib.fmg_eig_nonlinear_load(self.h, k, _ptr(u), _ptr(out), stream), "nonlinear_load")
+
+    def aux_rhs(self, k, lam, u, f, stream=None):
+        return self._check(self.lib.fmg_eig_aux_rhs(self.h, k, float(lam), _ptr(u), _ptr(f), stream), "aux_rhs")
+
+    def multigrid(self, k, f, x, stream=None):
+        return self._check(self.lib.fmg_eig_multigrid(self.h, k, _ptr(f), _ptr(x), stream), "multigrid")
+
+    def correction(self, k, lam, u_in, u_out, u_tilde=None):
+        lo = C.c_double()
+        it = C.c_int32()
+        rc = self.lib.fmg_eig_correction(self.h, k, float(lam), _ptr(u_in), C.byref(lo), _ptr(u_out),
+                                         _ptr(u_tilde), C.byref(it))
+        self._check(rc, "correction", allow=(FMG_ENOCONV,))
+        return lo.value, it.value, rc
+
+    def coarse_solve(self, u_out):
+        lo = C.c_double()
+        it = C.c_int32()
+        rc = self.lib.fmg_eig_coarse_solve(self.h, C.byref(lo), _ptr(u_out), C.byref(it))
+        self._check(rc, "coarse_solve", allow=(FMG_ENOCONV,))
+        return lo.value, it.value, rc
