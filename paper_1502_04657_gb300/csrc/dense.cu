@@ -462,12 +462,15 @@ void dense_scf(const DenseProblem& p, cudaStream_t s) {
   k_dense_scf<<<1, kThreads, dense_smem_bytes(n, p.ntri, p.nvert), s>>>(p);
 }
 
-cudaError_t dense_prepare(size_t max_smem) {
+// The attribute is per function, shared by every handle in the process, so it is always set
+// to the ceiling every caller is validated against (never to one caller's smaller need).
+cudaError_t dense_prepare(size_t need) {
+  if (need > kDenseSmemLimit) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_dense_scf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)max_smem);
+                                       (int)kDenseSmemLimit);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spd_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)max_smem);
+                              (int)kDenseSmemLimit);
 }
 
 void dense_spd_inverse(const double* L, double* Linv, int n, cudaStream_t s) {

@@ -486,7 +486,7 @@ int fmg_eig_create(const fmg_eig_problem* prob, fmg_eig_handle** out) {
         return FMG_ECUDA;
       }
   cudaMemcpy(h->dparams, h->hparams, sizeof(PotentialParams), cudaMemcpyHostToDevice);
-  if (h->dense_smem > 200 * 1024) {  // the small dense solve keeps everything in shared memory
+  if (h->dense_smem > kDenseSmemLimit) {  // the small dense solve keeps everything in shared memory
     delete h;
     return FMG_ENOTSUP;
   }

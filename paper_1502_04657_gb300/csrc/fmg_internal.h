@@ -120,6 +120,7 @@ struct DenseProblem {
   int* iters_out;        // 1
   int* status_out;       // 1 (0 converged, 1 cap hit)
 };
+constexpr size_t kDenseSmemLimit = 200 * 1024;  // dynamic shared memory of the dense solve
 size_t dense_smem_bytes(int n, int ntri, int nvert);
 cudaError_t dense_prepare(size_t max_smem);  // opt in to large dynamic shared memory
 void dense_scf(const DenseProblem& p, cudaStream_t s);
