@@ -182,6 +182,25 @@ int fmg_eig_correction(fmg_eig_handle* h, int32_t level, double lambda_in,
 int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev,
                          int32_t* iters);
 
+/* The same coarsest-level solve as fmg_eig_coarse_solve, for callers that must not allocate
+ * device memory (the paper has no counterpart: this is a library service).  Examples are code
+ * running under a stream capture that forbids allocation, frameworks that own every byte of
+ * the GPU through their own pool, and services that may not allocate once they serve.  No
+ * handle is needed and nothing is allocated: the caller passes the problem (only dim,
+ * coarse_cells, box_len, w_const, w_quad, zeta, omega, scf_tol and scf_max_iter are read)
+ * and u_dev, a device buffer of (coarse_cells - 1)^2 doubles that receives u_{h_1} in the
+ * interior layout.  *lambda_out (host) receives lambda_{h_1}; iters (host, nullable) the
+ * nonlinear iteration count.  All intermediates live in one fixed 256 KiB device array inside
+ * the library, which every GPU that loads the library keeps until the process exits.
+ * Limits: dim = 2, FMG_FP64, FMG_W_LEFT (else FMG_ENOTSUP); 2 <= coarse_cells <= 10 (else
+ * FMG_EINVAL, the array's capacity).  The first call on a device looks up the array's device
+ * address and should come before any stream capture on that device.  Calls share the array
+ * and run synchronously on `stream` (NULL = legacy default stream); calls that overlap on
+ * the GPU, from several host threads or streams, race and must be serialised by the caller.
+ * Returns FMG_OK, FMG_ENOCONV (cap hit, partial result written) or an error code.          */
+int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double* lambda_out, double* u_dev,
+                                 int32_t* iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

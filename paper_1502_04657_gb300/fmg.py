@@ -67,7 +67,21 @@ _SIGS = {
     "fmg_eig_multigrid": (C.c_int, [_P, _I32, _P, _P, _P]),
     "fmg_eig_correction": (C.c_int, [_P, _I32, C.c_double, _P, _D, _P, _P, C.POINTER(_I32)]),
     "fmg_eig_coarse_solve": (C.c_int, [_P, _D, _P, C.POINTER(_I32)]),
+    "fmg_eig_coarse_solve_noalloc": (C.c_int, [C.POINTER(fmg_eig_problem), _D, _P, C.POINTER(_I32), _P]),
 }
+
+
+def coarse_solve_noalloc(problem: "Problem", u_dev, stream=None):
+    """fmg_eig_coarse_solve_noalloc: the coarsest-level solve without a handle and without any
+    device allocation (for callers that may not allocate).  u_dev receives u_{h_1}."""
+    lib = load_library()
+    cp = problem.to_c()
+    lo = C.c_double()
+    it = C.c_int32()
+    rc = lib.fmg_eig_coarse_solve_noalloc(C.byref(cp), C.byref(lo), _ptr(u_dev), C.byref(it), stream)
+    if rc not in (FMG_OK, FMG_ENOCONV):
+        raise FmgError(rc, "fmg_eig_coarse_solve_noalloc")
+    return lo.value, it.value, rc
 
 
 def load_library(path: str = LIB_PATH):
