@@ -367,18 +367,21 @@ class ScfResult:
 
 
 def scf(k0: np.ndarray, mm: np.ndarray, gfun, zeta: float, c0: np.ndarray, sign_fn,
-        tol: float, max_iter: int) -> ScfResult:
+        tol: float, max_iter: int, history: int = 6, beta: float = 0.5) -> ScfResult:
     """Lowest solution of (K0 + zeta G(c)) c = lambda M c, c^T M c = 1.
 
-    Each step solves the linear eigenproblem with the mixed density matrix G_mix and takes
-    its lowest eigenpair (aufbau); G_mix <- G_mix + alpha (G(c) - G_mix).  alpha starts at 1
-    and is halved (down to 1/64) whenever the nonlinear residual grows.  lambda is reported
-    as c^T (K0 + zeta G(c)) c, the nonlinear Rayleigh quotient."""
-    g_mix = gfun(c0)
-    alpha, prev = 1.0, np.inf
+    Self-consistent field iteration: each step solves the linear eigenproblem
+    (K0 + zeta X) c = mu M c for the lowest eigenpair (aufbau) and forms the density matrix
+    G(c).  The input matrix X is updated by Anderson (Pulay) mixing of the residuals
+    F = G(c(X)) - X over the last `history` steps with damping beta (plain damped SCF for the
+    first step); the fixed point X = G(c) is the SCF solution.  lambda is reported as
+    c^T (K0 + zeta G(c)) c, the nonlinear Rayleigh quotient, and the iteration stops when the
+    relative residual of the nonlinear equation is below tol."""
+    x = gfun(c0)
+    xs, fs = [], []
     c, lam, res = c0, np.nan, np.inf
     for it in range(1, max_iter + 1):
-        _, vecs = sla.eigh(k0 + zeta * g_mix, mm)
+        _, vecs = sla.eigh(k0 + zeta * x, mm)
         c = vecs[:, 0] / np.sqrt(vecs[:, 0] @ mm @ vecs[:, 0])
         if sign_fn(c) < 0:
             c = -c
@@ -389,10 +392,18 @@ def scf(k0: np.ndarray, mm: np.ndarray, gfun, zeta: float, c0: np.ndarray, sign_
         res = float(np.linalg.norm(r) / (abs(lam) * np.linalg.norm(mm @ c)))
         if res <= tol:
             return ScfResult(lam, c, it, res, True)
-        if res > prev:
-            alpha = max(alpha / 2, 1.0 / 64)
-        prev = res
-        g_mix = g_mix + alpha * (g_new - g_mix)
+        f = (g_new - x).ravel()
+        xs.append(x.ravel().copy())
+        fs.append(f)
+        xs, fs = xs[-(history + 1):], fs[-(history + 1):]
+        step = beta * f
+        if len(fs) > 1:
+            d_f = np.stack([fs[i + 1] - fs[i] for i in range(len(fs) - 1)], axis=1)
+            d_x = np.stack([xs[i + 1] - xs[i] for i in range(len(xs) - 1)], axis=1)
+            gamma = np.linalg.lstsq(d_f, f, rcond=None)[0]
+            step = step - (d_x + beta * d_f) @ gamma
+        x = x + step.reshape(x.shape)
+        x = 0.5 * (x + x.T)
     return ScfResult(lam, c, max_iter, res, False)
 
 
