@@ -178,6 +178,17 @@ int fmg_eig_correction(fmg_eig_handle* h, int32_t level, double lambda_in,
                        const double* u_in_dev, double* lambda_out, double* u_out_dev,
                        double* u_tilde_dev, int32_t* iters);
 
+/* The small system of Algorithm 3.1 step 2 on level k >= 2 for a given u~ (u_tilde_dev, level
+ * k interior layout): with the basis psi = (phi^H_1..phi^H_N, u~), N = interior nodes of
+ * level 1, writes the n x n row-major host matrices (n = N + 1)
+ *   K[i][j] = a^(psi_i, psi_j) + (W psi_i, psi_j),  M[i][j] = b(psi_i, psi_j),
+ *   G[i][j] = int w^2 psi_i psi_j  with w = sum_j c_host[j] psi_j,
+ * as the small nonlinear solve assembles them from one fine pass.  FMG_EINVAL if n != N + 1.
+ * Synchronous.                                                                              */
+int fmg_eig_augmented_system(fmg_eig_handle* h, int32_t level, const double* u_tilde_dev,
+                             const double* c_host, int32_t n, double* K_host, double* M_host,
+                             double* G_host);
+
 /* Algorithm 3.2 step 1: the nonlinear eigenproblem directly on V_{h_1}.  Synchronous.       */
 int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev,
                          int32_t* iters);
@@ -192,7 +203,7 @@ int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev,
  * interior layout.  *lambda_out (host) receives lambda_{h_1}; iters (host, nullable) the
  * nonlinear iteration count.  All intermediates live in one fixed 256 KiB device array inside
  * the library, which every GPU that loads the library keeps until the process exits.
- * Limits: dim = 2, FMG_FP64, FMG_W_LEFT (else FMG_ENOTSUP); 2 <= coarse_cells <= 10 (else
+ * Limits: dim = 2, FMG_FP64, FMG_W_LEFT (else FMG_ENOTSUP); 2 <= coarse_cells <= 9 (else
  * FMG_EINVAL, the array's capacity).  The first call on a device looks up the array's device
  * address and should come before any stream capture on that device.  Calls share the array
  * and run synchronously on `stream` (NULL = legacy default stream); calls that overlap on

@@ -1,0 +1,351 @@
+// Fine-grid pass of the augmented nonlinear problem on the 3D Kuhn mesh: the per-coarse-
+// tetrahedron integrals T3^T_abc = int_T u~ mu_a mu_b mu_c (the other moments, T0, T1 and
+// the density stencil B(u~), come from grid3d.cu exactly as in 2D, see augment2d.cu).
+//
+// Coarse cell (I,J,L) holds 6 Kuhn tetrahedra T_s = {x_s0 >= x_s1 >= x_s2}; in the chain
+// coordinates (a, b, c) = (x_s0, x_s1, x_s2) / r of a fine node (r fine cells per coarse
+// cell) the barycentrics are mu = (1 - a, a - b, b - c, c) for every s, and the Kuhn mesh is
+// symmetric under axis permutations, so one description serves all six.  T3 is linear in u~:
+//   T3^T = sum_v u~_v int_T phi_v q,   q = mu_a mu_b mu_c (a cubic),
+// and a Taylor expansion of q about node v is exact: int_T phi_v q = sum_{|b|<=3} D^b q(v)/b!
+// m_b, m_b the moments of phi_v over the star tetrahedra of v inside T.  Those depend only
+// on v's class - interior of T, one of 4 faces, 6 edges or 4 vertices - so T3 is a fixed
+// linear map of the 15 x 20 class monomial sums S^class_g = sum u~ (a,b,c)^g, |g| <= 3.
+#include <math.h>
+
+#include <map>
+#include <vector>
+
+#include "fmg_internal.h"
+
+namespace fmg {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMono = 20;       // monomials of degree <= 3 in 3 variables
+constexpr int kClasses = 15;    // interior, F0..F3, E01 E02 E03 E12 E13 E23, V0..V3
+constexpr int kNodesPerThread = 8;
+constexpr int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+__constant__ int kPermDev[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// monomial order: degree 0; a b c; a^2 ab ac b^2 bc c^2; a^3 a^2b a^2c ab^2 abc ac^2 b^3 b^2c bc^2 c^3
+__device__ __forceinline__ void monomials(double a, double b, double c, double* m) {
+  m[0] = 1.0;
+  m[1] = a; m[2] = b; m[3] = c;
+  m[4] = a * a; m[5] = a * b; m[6] = a * c; m[7] = b * b; m[8] = b * c; m[9] = c * c;
+  m[10] = m[4] * a; m[11] = m[4] * b; m[12] = m[4] * c; m[13] = a * m[7]; m[14] = m[5] * c;
+  m[15] = a * m[9]; m[16] = m[7] * b; m[17] = m[7] * c; m[18] = b * m[9]; m[19] = m[9] * c;
+}
+
+__device__ void block_reduce(double* acc, int count, double* sh, double* out) {
+  for (int m = 0; m < count; ++m) {
+    sh[threadIdx.x] = acc[m];
+    __syncthreads();
+    for (int st = kThreads / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[m] = sh[0];
+    __syncthreads();
+  }
+}
+
+// Interior class: block (chunk, tet); nodes of the coarse cell in flat order.
+__global__ void __launch_bounds__(kThreads)
+    k_t3_interior3d(int pf, long planef, int n1, int r, const double* __restrict__ u,
+                    double* __restrict__ partials) {
+  __shared__ double sh[kThreads];
+  const int tet = blockIdx.y;
+  const int cell = tet / 6, s = tet % 6;
+  const int I = cell % n1, J = (cell / n1) % n1, L = cell / (n1 * n1);
+  const int r1 = r + 1;
+  const size_t cnt = (size_t)r1 * r1 * r1;
+  const double inv_r = 1.0 / r;
+  double acc[kMono];
+#pragma unroll
+  for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
+  const size_t beg = (size_t)blockIdx.x * kThreads * kNodesPerThread;
+  for (int it = 0; it < kNodesPerThread; ++it) {
+    const size_t idx = beg + (size_t)it * kThreads + threadIdx.x;
+    if (idx >= cnt) break;
+    const int x0 = (int)(idx % r1), x1 = (int)((idx / r1) % r1), x2 = (int)(idx / ((size_t)r1 * r1));
+    const int co[3] = {x0, x1, x2};
+    const int a = co[kPermDev[s][0]], b = co[kPermDev[s][1]], c = co[kPermDev[s][2]];
+    if (!(r > a && a > b && b > c && c > 0)) continue;
+    const double val = u[(size_t)(L * r + x2) * planef + (size_t)(J * r + x1) * pf + (I * r + x0)];
+    double m[kMono];
+    monomials(a * inv_r, b * inv_r, c * inv_r, m);
+#pragma unroll
+    for (int q = 0; q < kMono; ++q) acc[q] = fma(val, m[q], acc[q]);
+  }
+  block_reduce(acc, kMono, sh, partials + ((size_t)tet * gridDim.x + blockIdx.x) * kMono);
+}
+
+// Boundary classes: block (class - 1, tet); each class is a 0-, 1- or 2-parameter set of
+// chain coordinates.
+__device__ __forceinline__ bool class_node(int cls, int r, int p, int q, int* abc) {
+  switch (cls) {
+    case 1: abc[0] = r; abc[1] = p; abc[2] = q; return r > p && p > q && q > 0;  // F0
+    case 2: abc[0] = p; abc[1] = p; abc[2] = q; return r > p && p > q && q > 0;  // F1
+    case 3: abc[0] = p; abc[1] = q; abc[2] = q; return r > p && p > q && q > 0;  // F2
+    case 4: abc[0] = p; abc[1] = q; abc[2] = 0; return r > p && p > q && q > 0;  // F3
+    case 5: abc[0] = r; abc[1] = r; abc[2] = p; return q == 1 && r > p && p > 0; // E01
+    case 6: abc[0] = r; abc[1] = p; abc[2] = p; return q == 1 && r > p && p > 0; // E02
+    case 7: abc[0] = r; abc[1] = p; abc[2] = 0; return q == 1 && r > p && p > 0; // E03
+    case 8: abc[0] = p; abc[1] = p; abc[2] = p; return q == 1 && r > p && p > 0; // E12
+    case 9: abc[0] = p; abc[1] = p; abc[2] = 0; return q == 1 && r > p && p > 0; // E13
+    case 10: abc[0] = p; abc[1] = 0; abc[2] = 0; return q == 1 && r > p && p > 0; // E23
+    case 11: abc[0] = 0; abc[1] = 0; abc[2] = 0; return p == 1 && q == 1;         // V0
+    case 12: abc[0] = r; abc[1] = 0; abc[2] = 0; return p == 1 && q == 1;         // V1
+    case 13: abc[0] = r; abc[1] = r; abc[2] = 0; return p == 1 && q == 1;         // V2
+    default: abc[0] = r; abc[1] = r; abc[2] = r; return p == 1 && q == 1;         // V3
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_t3_boundary3d(int pf, long planef, int n1, int r, const double* __restrict__ u,
+                    double* __restrict__ partials) {
+  __shared__ double sh[kThreads];
+  const int cls = 1 + blockIdx.x;
+  const int tet = blockIdx.y;
+  const int cell = tet / 6, s = tet % 6;
+  const int I = cell % n1, J = (cell / n1) % n1, L = cell / (n1 * n1);
+  const double inv_r = 1.0 / r;
+  double acc[kMono];
+#pragma unroll
+  for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
+  const int span = r + 1;
+  for (size_t idx = threadIdx.x; idx < (size_t)span * span; idx += kThreads) {
+    const int p = (int)(idx % span), q = (int)(idx / span);
+    int abc[3];
+    if (!class_node(cls, r, p, q, abc)) continue;
+    int co[3];
+    co[kPermDev[s][0]] = abc[0];
+    co[kPermDev[s][1]] = abc[1];
+    co[kPermDev[s][2]] = abc[2];
+    const double val =
+        u[(size_t)(L * r + co[2]) * planef + (size_t)(J * r + co[1]) * pf + (I * r + co[0])];
+    double m[kMono];
+    monomials(abc[0] * inv_r, abc[1] * inv_r, abc[2] * inv_r, m);
+#pragma unroll
+    for (int k = 0; k < kMono; ++k) acc[k] = fma(val, m[k], acc[k]);
+  }
+  block_reduce(acc, kMono, sh,
+               partials + ((size_t)tet * (kClasses - 1) + blockIdx.x) * kMono);
+}
+
+// T3_e = h^3 sum_{class, g} map[e][class][g] S^class_g
+__global__ void k_t3_finalize3d(int chunks, double h3, const double* __restrict__ pin,
+                                const double* __restrict__ pbd, const double* __restrict__ map,
+                                double* __restrict__ t3) {
+  const int tet = blockIdx.x;
+  __shared__ double S[kClasses * kMono];
+  for (int m = threadIdx.x; m < kMono; m += blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < chunks; ++c) acc += pin[((size_t)tet * chunks + c) * kMono + m];
+    S[m] = acc;
+  }
+  for (int e = threadIdx.x; e < (kClasses - 1) * kMono; e += blockDim.x)
+    S[kMono + e] = pbd[(size_t)tet * (kClasses - 1) * kMono + e];
+  __syncthreads();
+  const int e = threadIdx.x;
+  if (e >= 20) return;
+  const double* row = map + (size_t)e * kClasses * kMono;
+  double acc = 0.0;
+  for (int q = 0; q < kClasses * kMono; ++q) acc = fma(row[q], S[q], acc);
+  t3[(size_t)tet * 20 + e] = h3 * acc;
+}
+
+int interior_chunks(int r) {
+  const size_t cnt = (size_t)(r + 1) * (r + 1) * (r + 1);
+  return (int)((cnt + kThreads * kNodesPerThread - 1) / (kThreads * kNodesPerThread));
+}
+
+// ---- host: class moments and the linear map ---------------------------------------------
+// Polynomials in the 4 barycentrics of a tetrahedron, exponents packed in a key.
+using Poly = std::map<int, double>;
+int key(const int* e) { return e[0] | e[1] << 4 | e[2] << 8 | e[3] << 12; }
+double fact(int k) {
+  double r = 1.0;
+  for (int i = 2; i <= k; ++i) r *= i;
+  return r;
+}
+Poly mul(const Poly& x, const Poly& y) {
+  Poly z;
+  for (auto& a : x)
+    for (auto& b : y) {
+      int e[4];
+      for (int i = 0; i < 4; ++i) e[i] = ((a.first >> (4 * i)) & 15) + ((b.first >> (4 * i)) & 15);
+      z[key(e)] += a.second * b.second;
+    }
+  return z;
+}
+// int_K lambda^alpha for a tetrahedron of volume 1/6 (fine units): 6 |K| alpha! / (|alpha|+3)!
+double integrate(const Poly& x) {
+  double s = 0.0;
+  for (auto& a : x) {
+    int tot = 0;
+    double num = 1.0;
+    for (int i = 0; i < 4; ++i) {
+      const int ei = (a.first >> (4 * i)) & 15;
+      tot += ei;
+      num *= fact(ei);
+    }
+    s += a.second * num / fact(tot + 3);
+  }
+  return s;
+}
+
+const int kMonoExp[20][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                             {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2},
+                             {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1},
+                             {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}};
+
+int mono_index(int a, int b, int c) {
+  for (int q = 0; q < 20; ++q)
+    if (kMonoExp[q][0] == a && kMonoExp[q][1] == b && kMonoExp[q][2] == c) return q;
+  return -1;
+}
+
+// Moments m[class][g] = sum over the star tetrahedra of a class-representative node that lie
+// in T = {R >= x0 >= x1 >= x2 >= 0} of int_K lambda_v (x - x_v)^g (fine units).
+void class_moments3d(double mom[kClasses][kMono]) {
+  const int R = 12;
+  const int rep[kClasses][3] = {{9, 6, 3},   {12, 8, 4}, {8, 8, 4},  {8, 4, 4},   {8, 4, 0},
+                                {12, 12, 6}, {12, 6, 6}, {12, 6, 0}, {6, 6, 6},   {6, 6, 0},
+                                {6, 0, 0},   {0, 0, 0},  {12, 0, 0}, {12, 12, 0}, {12, 12, 12}};
+  for (int cls = 0; cls < kClasses; ++cls) {
+    for (int g = 0; g < kMono; ++g) mom[cls][g] = 0.0;
+    const int* v = rep[cls];
+    // the 8 cells around v and their Kuhn tetrahedra
+    for (int o = 0; o < 8; ++o) {
+      const int c0[3] = {v[0] - (o & 1), v[1] - ((o >> 1) & 1), v[2] - ((o >> 2) & 1)};
+      for (int s = 0; s < 6; ++s) {
+        int vt[4][3];
+        for (int a = 0; a < 3; ++a) vt[0][a] = c0[a];
+        for (int a = 0; a < 3; ++a) vt[1][a] = vt[0][a] + (a == kPerm[s][0]);
+        for (int a = 0; a < 3; ++a) vt[2][a] = vt[1][a] + (a == kPerm[s][1]);
+        for (int a = 0; a < 3; ++a) vt[3][a] = c0[a] + 1;
+        int iv = -1;
+        for (int w = 0; w < 4; ++w)
+          if (vt[w][0] == v[0] && vt[w][1] == v[1] && vt[w][2] == v[2]) iv = w;
+        if (iv < 0) continue;
+        double cen[3] = {0, 0, 0};
+        for (int w = 0; w < 4; ++w)
+          for (int a = 0; a < 3; ++a) cen[a] += vt[w][a] / 4.0;
+        if (!(R > cen[0] && cen[0] > cen[1] && cen[1] > cen[2] && cen[2] > 0)) continue;
+        // x - x_v = sum_w lambda_w (x_w - x_v)
+        Poly lin[3];
+        for (int a = 0; a < 3; ++a)
+          for (int w = 0; w < 4; ++w) {
+            const double d = vt[w][a] - v[a];
+            if (d == 0.0) continue;
+            int e[4] = {0, 0, 0, 0};
+            e[w] = 1;
+            lin[a][key(e)] += d;
+          }
+        int ev[4] = {0, 0, 0, 0};
+        ev[iv] = 1;
+        for (int g = 0; g < kMono; ++g) {
+          Poly p;
+          p[key(ev)] = 1.0;
+          for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < kMonoExp[g][a]; ++k) p = mul(p, lin[a]);
+          mom[cls][g] += integrate(p);
+        }
+      }
+    }
+  }
+}
+
+// Every class sum is taken with the node's actual chain coordinates, so S^class_g is simply
+// slot class * 20 + g.
+void class_sum_terms(int cls, int ga, int gb, int gc, std::vector<std::pair<int, double>>& out) {
+  out.clear();
+  const int q = mono_index(ga, gb, gc);
+  if (q >= 0) out.push_back({cls * kMono + q, 1.0});
+}
+
+}  // namespace
+
+size_t t3_partials3d(const Grid& fine, int n1) {
+  const int r = fine.n / n1;
+  const size_t tets = (size_t)6 * n1 * n1 * n1;
+  return tets * kMono * ((size_t)interior_chunks(r) + (kClasses - 1));
+}
+
+void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
+                  double* partials, double* t3, cudaStream_t s) {
+  const int r = fine.n / n1;
+  const int tets = 6 * n1 * n1 * n1;
+  const int chunks = interior_chunks(r);
+  const long planef = (long)(fine.n + 1) * fine.pitch;
+  double* pin = partials;
+  double* pbd = partials + (size_t)tets * chunks * kMono;
+  k_t3_interior3d<<<dim3(chunks, tets), kThreads, 0, s>>>(fine.pitch, planef, n1, r, u, pin);
+  k_t3_boundary3d<<<dim3(kClasses - 1, tets), kThreads, 0, s>>>(fine.pitch, planef, n1, r, u, pbd);
+  k_t3_finalize3d<<<tets, 32, 0, s>>>(chunks, fine.h * fine.h * fine.h, pin, pbd, map, t3);
+}
+
+// Host: map[e][class][g] for T3_e = h^3 sum map S^class_g (r fine cells per coarse cell),
+//   T3_e = sum_class sum_{|b|<=3} m^class_b r^-|b| / b! sum_{|g|<=3} c^e_g (g)_b S^class_{g-b},
+// c^e the monomial coefficients of q_e = mu_a mu_b mu_c in chain coordinates and (g)_b the
+// falling factorials.
+void t3_map3d(int r, double* out) {
+  double mom[kClasses][kMono];
+  class_moments3d(mom);
+  for (int i = 0; i < 20 * kClasses * kMono; ++i) out[i] = 0.0;
+  // barycentrics (const, a, b, c) coefficients
+  const double mu[4][4] = {{1, -1, 0, 0}, {0, 1, -1, 0}, {0, 0, 1, -1}, {0, 0, 0, 1}};
+  auto ff = [](int g, int b) {  // falling factorial (g)_b
+    double r = 1.0;
+    for (int i = 0; i < b; ++i) r *= (g - i);
+    return r;
+  };
+  std::vector<std::pair<int, double>> terms;
+  int e = 0;
+  for (int x = 0; x < 4; ++x)
+    for (int y = x; y < 4; ++y)
+      for (int z = y; z < 4; ++z, ++e) {
+        double cq[4][4][4] = {};
+        cq[0][0][0] = 1.0;
+        const int f3[3] = {x, y, z};
+        for (int f = 0; f < 3; ++f) {
+          double nq[4][4][4] = {};
+          const double* m = mu[f3[f]];
+          for (int a = 0; a < 4; ++a)
+            for (int b = 0; a + b < 4; ++b)
+              for (int c = 0; a + b + c < 4; ++c) {
+                if (cq[a][b][c] == 0.0) continue;
+                nq[a][b][c] += cq[a][b][c] * m[0];
+                if (a + b + c + 1 < 4) {
+                  nq[a + 1][b][c] += cq[a][b][c] * m[1];
+                  nq[a][b + 1][c] += cq[a][b][c] * m[2];
+                  nq[a][b][c + 1] += cq[a][b][c] * m[3];
+                }
+              }
+          for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+              for (int c = 0; c < 4; ++c) cq[a][b][c] = nq[a][b][c];
+        }
+        double* row = out + (size_t)e * kClasses * kMono;
+        for (int cls = 0; cls < kClasses; ++cls)
+          for (int bq = 0; bq < kMono; ++bq) {
+            const double mb = mom[cls][bq];
+            if (mb == 0.0) continue;
+            const int b0 = kMonoExp[bq][0], b1 = kMonoExp[bq][1], b2 = kMonoExp[bq][2];
+            const double w = mb * pow((double)r, -(b0 + b1 + b2)) / (fact(b0) * fact(b1) * fact(b2));
+            for (int g0 = b0; g0 < 4; ++g0)
+              for (int g1 = b1; g0 + g1 < 4; ++g1)
+                for (int g2 = b2; g0 + g1 + g2 < 4; ++g2) {
+                  const double cg = cq[g0][g1][g2];
+                  if (cg == 0.0) continue;
+                  const double coef = w * cg * ff(g0, b0) * ff(g1, b1) * ff(g2, b2);
+                  class_sum_terms(cls, g0 - b0, g1 - b1, g2 - b2, terms);
+                  for (auto& t : terms) row[t.first] += coef * t.second;
+                }
+          }
+      }
+}
+
+}  // namespace fmg

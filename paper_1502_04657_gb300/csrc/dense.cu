@@ -8,21 +8,27 @@
 // or Newton-type iterations; both converge to the same ground state, which is what the
 // result is.  This kernel takes inverse-power steps c <- (K0 + zeta G(c))^{-1} M c while the
 // relative residual is large (they pull any positive start into the ground state's basin),
-// then Newton steps on the bordered system
-//     [K0 + 3 zeta G(c) - lambda M   -M c] [dc]   [-F]
-//     [-(M c)^T                        0 ] [dl] = [ 0]
-// (d/dc of G(c) c is 3 G(c) for the cubic term), which converge quadratically.  lambda is
-// reported as c^T (K0 + zeta G(c)) c at the final c.
+// then Newton steps, which converge quadratically.  A Newton step solves the bordered system
+//     [A    -M c] [dc]   [-r]        A = K0 + 3 zeta G(c) - lambda M,  r = F(c, lambda)
+//     [-c^T M  0] [dl] = [ 0]        (d/dc of G(c) c is 3 G(c) for the cubic term)
+// by block elimination with A' = A + lambda (M c)(M c)^T: the constraint (M c)^T dc = 0 makes
+// A' dc = A dc, and A' is positive definite near the ground state (A is semidefinite there,
+// singular only along c), so an LDL^T factorisation without pivoting applies:
+//     y1 = A'^{-1} r,  y2 = A'^{-1} M c,  dl = (Mc.y1)/(Mc.y2),  dc = -y1 + dl y2.
+// lambda is reported as c^T (K0 + zeta G(c)) c at the final c.
 //
-// G(c) is assembled per coarse simplex T from the moments of u~ (see moments2d.cu) and the
-// exact quartic table q4 of the coarse barycentrics:
-//   int_T w^2 mu_a mu_b  = |T| sum w_c w_d q4_abcd + 2 c_u sum w_c T3_abc + c_u^2 T2_ab
-//   int_T w^2 mu_a u~    = sum w_c w_d T3_acd + 2 c_u sum w_c T2_ac + c_u^2 T1_a
-//   int_T w^2 u~^2       = sum w_c w_d T2_cd  + 2 c_u sum w_c T1_c  + c_u^2 T0
-// with w_c the coarse coefficients at T's vertices (0 on the boundary), c_u that of u~.
+// G(c) is assembled per coarse simplex T from the exact quartic table q4 of the coarse
+// barycentrics and, on the augmented space (w = w_H + c_u u~), from the fine-pass integrals
+// (augment2d.cu): T3^T (per simplex), B1 = int u~^2 phi phi, t1 = int u~^3 phi, T0 = int u~^4:
+//   G_ab = sum_T [|T| sum w_c w_d q4_abcd + 2 c_u sum w_c T3_abc] + c_u^2 B1_ab
+//   G_au = sum_T sum w_c w_d T3_acd + 2 c_u (B1 c_H)_a + c_u^2 t1_a
+//   G_uu = c_H^T B1 c_H + 2 c_u t1.c_H + c_u^2 T0
+// with w_c the coarse coefficients at T's vertices (0 on the boundary).
 //
-// One CTA of 256 threads per problem, everything in shared memory, fixed-order reductions.
-// The iteration count is bounded by max_iter; hitting it sets status 1.
+// One CTA of 512 threads per problem (enough warps to hide shared-memory and FP64 latency),
+// everything in shared memory, fixed-order reductions, one barrier per elimination step and
+// warp-synchronous triangular solves.  The iteration count is bounded by max_iter; hitting it
+// sets status 1.
 #include <math.h>
 
 #include "fmg_internal.h"
@@ -30,35 +36,43 @@
 namespace fmg {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
 constexpr int kMaxVert = 4;
 constexpr double kSwitch = 1e-2;  // relative residual below which Newton takes over
 
 struct Smem {
-  double *K0, *MM, *G, *J, *c, *Mc, *Hc, *x, *loc, *red;
-  int n, nh, n1p, L;
+  double *K0, *MM, *G, *A, *B1, *loc, *q4;
+  double *c, *Mc, *Hc, *Gc, *r, *y1, *y2, *dinv, *red;
+  int* sym3;  // nv^3 table of sorted-triple indices
+  int *tri, *adj;  // shared copies of the simplex and adjacency tables
+  double *t3, *t1;  // shared copies of the fine-pass integrals (augmented problem)
+  int n, nh, L;
 };
 
-__device__ double block_sum(double v, double* red) {
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = kThreads / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// y = A c for an n x n row-major matrix
-__device__ void matvec(const double* A, const double* c, double* y, int n) {
-  for (int a = threadIdx.x; a < n; a += kThreads) {
-    double s = 0.0;
-    const double* row = A + (size_t)a * n;
-    for (int b = 0; b < n; ++b) s = fma(row[b], c[b], s);
-    y[a] = s;
-  }
+// Block-wide sum in a fixed order: butterfly within each warp, then warp 0 adds the warp
+// totals in the same butterfly order (two barriers).  Every thread gets the result.
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = (threadIdx.x & 31) < kWarps ? red[threadIdx.x & 31] : 0.0;
+  t = warp_sum(t);
+  __syncthreads();  // red may be reused right away
+  return t;
+}
+
+// 1 / d by Newton's iteration from a single-precision seed (two steps reach FP64 rounding).
+__device__ __forceinline__ double recip(double d) {
+  double y = (double)__frcp_rn((float)d);
+  y = fma(y, fma(-d, y, 1.0), y);
+  y = fma(y, fma(-d, y, 1.0), y);
+  return y;
 }
 
 __device__ double dotv(const double* a, const double* b, int n, double* red) {
@@ -67,258 +81,232 @@ __device__ double dotv(const double* a, const double* b, int n, double* red) {
   return block_sum(s, red);
 }
 
-__device__ __forceinline__ int sym2(int a, int b, int nv) {
-  if (a > b) {
-    const int t = a;
-    a = b;
-    b = t;
+// rows of (K0 c, G c, M c), one warp per row
+__device__ void apply_all(Smem& s) {
+  const int n = s.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int a = warp; a < n; a += kWarps) {
+    const double* kr = s.K0 + (size_t)a * n;
+    const double* gr = s.G + (size_t)a * n;
+    const double* mr = s.MM + (size_t)a * n;
+    double hk = 0.0, hg = 0.0, mc = 0.0;
+    for (int b = lane; b < n; b += 32) {
+      const double cb = s.c[b];
+      hk = fma(kr[b], cb, hk);
+      hg = fma(gr[b], cb, hg);
+      mc = fma(mr[b], cb, mc);
+    }
+    hk = warp_sum(hk);
+    hg = warp_sum(hg);
+    mc = warp_sum(mc);
+    if (lane == 0) {
+      s.Hc[a] = hk;
+      s.Gc[a] = hg;
+      s.Mc[a] = mc;
+    }
   }
-  return a * nv - a * (a - 1) / 2 + (b - a);
-}
-
-__device__ __forceinline__ int sym3(int a, int b, int c, int nv) {
-  // sort a <= b <= c, then count lexicographically smaller sorted triples
-  if (a > b) { const int t = a; a = b; b = t; }
-  if (b > c) { const int t = b; b = c; c = t; }
-  if (a > b) { const int t = a; a = b; b = t; }
-  int idx = 0;
-  for (int x = 0; x < a; ++x) idx += (nv - x) * (nv - x + 1) / 2;
-  for (int y = a; y < b; ++y) idx += nv - y;
-  return idx + (c - b);
+  __syncthreads();
 }
 
 __device__ void build_G(const DenseProblem& p, Smem& s) {
   const int nv = p.nvert, L = s.L, nh = s.nh, n = s.n;
-  const int nmom = 1 + nv + nv * (nv + 1) / 2 + nv * (nv + 1) * (nv + 2) / 6;
-  const int o2 = 1 + nv, o3 = o2 + nv * (nv + 1) / 2;
-  for (int t = threadIdx.x; t < p.ntri; t += kThreads) {
-    double w[kMaxVert];
+  const double cu = p.aug ? s.c[nh] : 0.0;
+  const int npair = nv * (nv + 1) / 2;
+  const int items = npair + (p.aug ? nv : 0);
+  // local contributions: one work item = (simplex, entry)
+  for (int w = threadIdx.x; w < p.ntri * items; w += kThreads) {
+    const int t = w / items, e = w - t * items;
+    double wv[kMaxVert];
     for (int v = 0; v < nv; ++v) {
-      const int id = p.tri[t * nv + v];
-      w[v] = id >= 0 ? s.c[id] : 0.0;
+      const int id = s.tri[t * nv + v];
+      wv[v] = id >= 0 ? s.c[id] : 0.0;
     }
-    const double cu = p.aug ? s.c[nh] : 0.0;
-    const double* mom = p.aug ? p.mom + (size_t)t * nmom : nullptr;
+    const double* t3 = p.aug ? s.t3 + (size_t)t * p.nt3 : nullptr;
     double* lt = s.loc + (size_t)t * L * L;
-    for (int a = 0; a < nv; ++a) {
-      for (int b = a; b < nv; ++b) {
-        double q = 0.0;
-        for (int c = 0; c < nv; ++c)
-          for (int d = 0; d < nv; ++d)
-            q = fma(w[c] * w[d], p.q4[((a * nv + b) * nv + c) * nv + d], q);
-        double v = p.tri_vol * q;
-        if (p.aug) {
-          double t3 = 0.0;
-          for (int c = 0; c < nv; ++c) t3 = fma(w[c], mom[o3 + sym3(a, b, c, nv)], t3);
-          v = fma(2.0 * cu, t3, v);
-          v = fma(cu * cu, mom[o2 + sym2(a, b, nv)], v);
-        }
-        lt[a * L + b] = v;
-        lt[b * L + a] = v;
+    if (e < npair) {
+      int a = 0, b = e;  // e-th pair (a <= b)
+      while (b >= nv - a) {
+        b -= nv - a;
+        ++a;
       }
-    }
-    if (p.aug) {
-      for (int a = 0; a < nv; ++a) {
-        double t3 = 0.0, t2 = 0.0;
-        for (int c = 0; c < nv; ++c) {
-          t2 = fma(w[c], mom[o2 + sym2(a, c, nv)], t2);
-          for (int d = 0; d < nv; ++d) t3 = fma(w[c] * w[d], mom[o3 + sym3(a, c, d, nv)], t3);
-        }
-        const double v = fma(cu * cu, mom[1 + a], fma(2.0 * cu, t2, t3));
-        lt[a * L + nv] = v;
-        lt[nv * L + a] = v;
-      }
-      double t2 = 0.0, t1 = 0.0;
+      b += a;
+      double q = 0.0;
+      const double* q4 = s.q4 + (size_t)(a * nv + b) * nv * nv;
       for (int c = 0; c < nv; ++c) {
-        t1 = fma(w[c], mom[1 + c], t1);
-        for (int d = 0; d < nv; ++d) t2 = fma(w[c] * w[d], mom[o2 + sym2(c, d, nv)], t2);
+        double qc = 0.0;
+        for (int d = 0; d < nv; ++d) qc = fma(wv[d], q4[c * nv + d], qc);
+        q = fma(wv[c], qc, q);
       }
-      lt[nv * L + nv] = fma(cu * cu, mom[0], fma(2.0 * cu, t1, t2));
+      double v = p.tri_vol * q;
+      if (p.aug) {
+        double x3 = 0.0;
+        for (int c = 0; c < nv; ++c) x3 = fma(wv[c], t3[s.sym3[(a * nv + b) * nv + c]], x3);
+        v = fma(2.0 * cu, x3, v);
+      }
+      lt[a * L + b] = v;
+      lt[b * L + a] = v;
+    } else {
+      const int a = e - npair;
+      double x3 = 0.0;
+      for (int c = 0; c < nv; ++c) {
+        double xc = 0.0;
+        for (int d = 0; d < nv; ++d) xc = fma(wv[d], t3[s.sym3[(a * nv + c) * nv + d]], xc);
+        x3 = fma(wv[c], xc, x3);
+      }
+      lt[a * L + nv] = x3;
     }
   }
-  for (int e = threadIdx.x; e < n * n; e += kThreads) s.G[e] = 0.0;
-  __syncthreads();
-  // rows of coarse nodes: each thread owns one row, sums its incident simplices in order
-  for (int a = threadIdx.x; a < nh; a += kThreads) {
-    double* row = s.G + (size_t)a * n;
-    double au = 0.0;
-    for (int e = 0; e < p.maxadj; ++e) {
-      const int code = p.adj[a * p.maxadj + e];
-      if (code < 0) break;
-      const int t = code >> 3, la = code & 7;
-      const double* lt = s.loc + (size_t)t * L * L;
-      for (int lb = 0; lb < nv; ++lb) {
-        const int vb = p.tri[t * nv + lb];
-        if (vb >= 0) row[vb] += lt[la * L + lb];
-      }
-      if (p.aug) au += lt[la * L + nv];
+  if (p.aug) {  // Hc <- B1 c_H (scratch; recomputed by apply_all afterwards)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int a = warp; a < nh; a += kWarps) {
+      const double* row = s.B1 + (size_t)a * nh;
+      double acc = 0.0;
+      for (int b = lane; b < nh; b += 32) acc = fma(row[b], s.c[b], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) s.Hc[a] = acc;
     }
-    if (p.aug) row[nh] = au;
-  }
-  if (p.aug && threadIdx.x == kThreads - 1) {
-    double uu = 0.0;
-    for (int t = 0; t < p.ntri; ++t) uu += s.loc[(size_t)t * L * L + nv * L + nv];
-    s.G[(size_t)nh * n + nh] = uu;
   }
   __syncthreads();
-  if (p.aug)
+  // coarse rows: a warp per row; lanes fill the global part, lane 0 adds the simplices
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double cu2 = cu * cu;
+    for (int a = warp; a < nh; a += kWarps) {
+      double* row = s.G + (size_t)a * n;
+      const double* brow = p.aug ? s.B1 + (size_t)a * nh : nullptr;
+      for (int b = lane; b < nh; b += 32) row[b] = p.aug ? cu2 * brow[b] : 0.0;
+      __syncwarp();
+      if (lane == 0) {
+        double au = 0.0;
+        for (int e = 0; e < p.maxadj; ++e) {
+          const int code = s.adj[a * p.maxadj + e];
+          if (code < 0) break;
+          const int t = code >> 3, la = code & 7;
+          const double* lt = s.loc + (size_t)t * L * L;
+          for (int lb = 0; lb < nv; ++lb) {
+            const int vb = s.tri[t * nv + lb];
+            if (vb >= 0) row[vb] += lt[la * L + lb];
+          }
+          if (p.aug) au += lt[la * L + nv];
+        }
+        if (p.aug) row[nh] = fma(cu2, s.t1[a], fma(2.0 * cu, s.Hc[a], au));
+      }
+      __syncwarp();
+    }
+  }
+  if (p.aug) {
+    double part = 0.0;
+    for (int a = threadIdx.x; a < nh; a += kThreads)
+      part = fma(s.c[a], fma(2.0 * cu, s.t1[a], s.Hc[a]), part);
+    const double tot = block_sum(part, s.red);  // also orders the row writes above
+    if (threadIdx.x == 0) s.G[(size_t)nh * n + nh] = fma(cu * cu, p.t0[0], tot);
     for (int a = threadIdx.x; a < nh; a += kThreads) s.G[(size_t)nh * n + a] = s.G[(size_t)a * n + nh];
+  }
   __syncthreads();
 }
 
-// In-place Cholesky of the n x n matrix A (lower triangle).  Returns false if not SPD.
-__device__ bool cholesky(double* A, int n, double* red) {
-  __shared__ int fail;
-  if (threadIdx.x == 0) fail = 0;
-  __syncthreads();
+// In-place symmetric elimination A = L D L^T (no pivoting; the full trailing block is kept,
+// so it stays symmetric and rows are read contiguously).  One barrier per step.  Returns
+// false at a non-positive pivot (every thread sees the same pivot, so all return together).
+__device__ bool ldlt(double* A, int n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = A[k * n + k];
-      if (!(d > 0.0)) fail = 1;
-      else A[k * n + k] = sqrt(d);
-    }
-    __syncthreads();
-    if (fail) return false;
-    const double dk = A[k * n + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += kThreads) A[i * n + k] /= dk;
-    __syncthreads();
-    const int m = n - k - 1;
-    for (int e = threadIdx.x; e < m * m; e += kThreads) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) A[i * n + j] = fma(-A[i * n + k], A[j * n + k], A[i * n + j]);
+    const double d = A[k * n + k];
+    if (!(d > 0.0)) return false;
+    const double inv = recip(d);
+    const double* rk = A + (size_t)k * n;
+    for (int i = k + 1 + warp; i < n; i += kWarps) {
+      const double l = A[i * n + k] * inv;
+      double* ri = A + (size_t)i * n;
+      for (int j = k + 1 + lane; j < n; j += 32) ri[j] = fma(-l, rk[j], ri[j]);
     }
     __syncthreads();
   }
   return true;
 }
 
-// Solve (L L^T) x = b in place (x holds b on entry); warp 0 works, others wait.
-__device__ void chol_solve(const double* A, int n, double* x) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int j = lane; j < i; j += 32) s = fma(A[i * n + j], x[j], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = (x[i] - s) / A[i * n + i];
-      __syncwarp();
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int j = i + 1 + lane; j < n; j += 32) s = fma(A[j * n + i], x[j], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = (x[i] - s) / A[i * n + i];
-      __syncwarp();
-    }
+// Solve (L D L^T) x = b for x held in `x` (b on entry), by one warp, column by column: once
+// an entry is final, the lanes update the remaining ones (only warp-level synchronisation).
+// The factor is stored as A_ik = L_ik D_k (symmetric); dinv holds 1 / D.
+__device__ void ldlt_solve_warp(const double* A, const double* dinv, int n, double* x) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < n; ++k) {  // forward: w_k = z_k / D_k, z_i -= A_ik w_k (i > k)
+    const double wk = x[k] * dinv[k];
+    __syncwarp();
+    if (lane == 0) x[k] = wk;
+    for (int i = k + 1 + lane; i < n; i += 32) x[i] = fma(-A[i * n + k], wk, x[i]);
+    __syncwarp();
   }
-  __syncthreads();
+  for (int k = n - 1; k >= 0; --k) {  // backward: x_i -= (A_ik / D_i) x_k (i < k)
+    const double xk = x[k];
+    for (int i = lane; i < k; i += 32) x[i] = fma(-A[i * n + k] * dinv[i], xk, x[i]);
+    __syncwarp();
+  }
 }
 
-// Gaussian elimination with partial pivoting on the m x m matrix A, right-hand side x.
-__device__ bool lu_solve(double* A, int m, double* x) {
-  __shared__ int piv;
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int k = 0; k < m; ++k) {
-    if (threadIdx.x < 32) {
-      double best = -1.0;
-      int bi = k;
-      for (int i = k + threadIdx.x; i < m; i += 32) {
-        const double v = fabs(A[i * m + k]);
-        if (v > best) { best = v; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (threadIdx.x == 0) {
-        piv = bi;
-        if (!(best > 0.0)) bad = 1;
-      }
-    }
-    __syncthreads();
-    if (bad) return false;
-    const int pk = piv;
-    if (pk != k) {
-      for (int j = threadIdx.x; j < m; j += kThreads) {
-        const double t = A[k * m + j];
-        A[k * m + j] = A[pk * m + j];
-        A[pk * m + j] = t;
-      }
-      if (threadIdx.x == 0) {
-        const double t = x[k];
-        x[k] = x[pk];
-        x[pk] = t;
-      }
-    }
-    __syncthreads();
-    const double d = A[k * m + k];
-    for (int i = k + 1 + threadIdx.x; i < m; i += kThreads) A[i * m + k] /= d;
-    __syncthreads();
-    const int r = m - k - 1;
-    for (int e = threadIdx.x; e < r * r; e += kThreads) {
-      const int i = k + 1 + e / r, j = k + 1 + e % r;
-      A[i * m + j] = fma(-A[i * m + k], A[k * m + j], A[i * m + j]);
-    }
-    for (int i = k + 1 + threadIdx.x; i < m; i += kThreads) x[i] = fma(-A[i * m + k], x[k], x[i]);
-    __syncthreads();
-  }
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int i = m - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int j = i + 1 + lane; j < m; j += 32) s = fma(A[i * m + j], x[j], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = (x[i] - s) / A[i * m + i];
-      __syncwarp();
-    }
-  }
+__device__ void invert_pivots(const double* A, int n, double* dinv) {
+  for (int k = threadIdx.x; k < n; k += kThreads) dinv[k] = recip(A[k * n + k]);
   __syncthreads();
-  return true;
 }
 
 __device__ void normalise_and_sign(const DenseProblem& p, Smem& s) {
-  matvec(s.MM, s.c, s.Mc, s.n);
+  const int n = s.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int a = warp; a < n; a += kWarps) {
+    const double* mr = s.MM + (size_t)a * n;
+    double mc = 0.0;
+    for (int b = lane; b < n; b += 32) mc = fma(mr[b], s.c[b], mc);
+    mc = warp_sum(mc);
+    if (lane == 0) s.Mc[a] = mc;
+  }
   __syncthreads();
-  const double cmc = dotv(s.c, s.Mc, s.n, s.red);
+  const double cmc = dotv(s.c, s.Mc, n, s.red);
   double sg;
   if (p.aug) {
     sg = s.c[s.nh];
   } else {
     double t = 0.0;
-    for (int i = threadIdx.x; i < s.n; i += kThreads) t += s.c[i];
+    for (int i = threadIdx.x; i < n; i += kThreads) t += s.c[i];
     sg = block_sum(t, s.red);
   }
   __syncthreads();  // every thread has read c before any thread rescales it
   const double f = (sg < 0.0 ? -1.0 : 1.0) / sqrt(cmc);
-  for (int i = threadIdx.x; i < s.n; i += kThreads) s.c[i] *= f;
+  for (int i = threadIdx.x; i < n; i += kThreads) s.c[i] *= f;
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   extern __shared__ double sm[];
+  __shared__ int sym3_tab[kMaxVert * kMaxVert * kMaxVert];
   Smem s;
   s.nh = p.nh;
   s.n = p.nh + p.aug;
-  s.n1p = s.n + 1;
   s.L = p.nvert + 1;
-  const int n = s.n, nh = s.nh;
-  s.K0 = sm;
-  s.MM = s.K0 + n * n;
-  s.G = s.MM + n * n;
-  s.J = s.G + n * n;
-  s.c = s.J + s.n1p * s.n1p;
-  s.Mc = s.c + n;
-  s.Hc = s.Mc + n;
-  s.x = s.Hc + n;
-  s.loc = s.x + s.n1p;
-  s.red = s.loc + (size_t)p.ntri * s.L * s.L;
+  const int n = s.n, nh = s.nh, nv = p.nvert;
+  double* q = sm;
+  s.K0 = q; q += (size_t)n * n;
+  s.MM = q; q += (size_t)n * n;
+  s.G = q; q += (size_t)n * n;
+  s.A = q; q += (size_t)n * n;
+  s.loc = q; q += (size_t)p.ntri * s.L * s.L;
+  s.q4 = q; q += nv * nv * nv * nv;
+  s.c = q; q += n;
+  s.Mc = q; q += n;
+  s.Hc = q; q += n;
+  s.Gc = q; q += n;
+  s.r = q; q += n;
+  s.y1 = q; q += n;
+  s.y2 = q; q += n;
+  s.dinv = q; q += n;
+  s.red = q; q += kThreads;
+  s.t1 = q; q += nh;
+  s.t3 = q; q += p.aug ? (size_t)p.ntri * p.nt3 : 0;
+  s.tri = reinterpret_cast<int*>(q); q += ((size_t)p.ntri * nv + 1) / 2;
+  s.adj = reinterpret_cast<int*>(q); q += ((size_t)nh * p.maxadj + 1) / 2;
+  s.B1 = q;  // nh * nh when aug
+  s.sym3 = sym3_tab;
 
-  const int m1 = p.n1 - 1;
   const double zeta = p.params->zeta;
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
-    const int a = e / n, b = e % n;
+    const int a = e / n, b = e - (e / n) * n;
     double kv, mv;
     if (a < nh && b < nh) {
       kv = p.L1[a * nh + b];
@@ -327,42 +315,57 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
       kv = p.auu[0];
       mv = p.buu[0];
     } else {
-      const int q = a < nh ? a : b;
-      const size_t pad = (size_t)(1 + q / m1) * p.pitch1 + 1 + q % m1;
-      kv = p.gA[pad];
-      mv = p.gM[pad];
+      const int qq = a < nh ? a : b;
+      kv = p.gA[qq];
+      mv = p.gM[qq];
     }
     s.K0[e] = kv;
     s.MM[e] = mv;
   }
+  if (p.aug) {
+    for (int e = threadIdx.x; e < nh * nh; e += kThreads) s.B1[e] = p.B1[e];
+    for (int e = threadIdx.x; e < nh; e += kThreads) s.t1[e] = p.t1[e];
+    for (int e = threadIdx.x; e < p.ntri * p.nt3; e += kThreads) s.t3[e] = p.t3[e];
+  }
+  for (int e = threadIdx.x; e < p.ntri * nv; e += kThreads) s.tri[e] = p.tri[e];
+  for (int e = threadIdx.x; e < nh * p.maxadj; e += kThreads) s.adj[e] = p.adj[e];
+  for (int e = threadIdx.x; e < nv * nv * nv * nv; e += kThreads) s.q4[e] = p.q4[e];
+  for (int e = threadIdx.x; e < nv * nv * nv; e += kThreads) {
+    int a = e / (nv * nv), b = (e / nv) % nv, c = e % nv;
+    if (a > b) { const int t = a; a = b; b = t; }
+    if (b > c) { const int t = b; b = c; c = t; }
+    if (a > b) { const int t = a; a = b; b = t; }
+    int idx = 0;
+    for (int x = 0; x < a; ++x) idx += (nv - x) * (nv - x + 1) / 2;
+    for (int y = a; y < b; ++y) idx += nv - y;
+    sym3_tab[e] = idx + (c - b);
+  }
   for (int i = threadIdx.x; i < n; i += kThreads)
     s.c[i] = p.c_init ? p.c_init[i] : (i == nh ? 1.0 : 0.0);
   __syncthreads();
+  if (p.K_out) {  // assemble-only mode: K0, M and G(c_init) as given
+    build_G(p, s);
+    for (int e = threadIdx.x; e < n * n; e += kThreads) {
+      p.K_out[e] = s.K0[e];
+      p.M_out[e] = s.MM[e];
+      p.G_out[e] = s.G[e];
+    }
+    return;
+  }
   normalise_and_sign(p, s);
 
   int it = 0, status = 1;
   double lam = 0.0;
   for (;; ++it) {
     build_G(p, s);
-    // H c, M c, lambda, residual
-    for (int a = threadIdx.x; a < n; a += kThreads) {
-      double hk = 0.0, hg = 0.0, mc = 0.0;
-      const double* kr = s.K0 + (size_t)a * n;
-      const double* gr = s.G + (size_t)a * n;
-      const double* mr = s.MM + (size_t)a * n;
-      for (int b = 0; b < n; ++b) {
-        hk = fma(kr[b], s.c[b], hk);
-        hg = fma(gr[b], s.c[b], hg);
-        mc = fma(mr[b], s.c[b], mc);
-      }
-      s.Hc[a] = fma(zeta, hg, hk);
-      s.Mc[a] = mc;
-    }
+    apply_all(s);  // Hc = K0 c, Gc = G c, Mc = M c
+    for (int a = threadIdx.x; a < n; a += kThreads) s.Hc[a] = fma(zeta, s.Gc[a], s.Hc[a]);
     __syncthreads();
     lam = dotv(s.c, s.Hc, n, s.red);
     double rr = 0.0, mm = 0.0;
     for (int a = threadIdx.x; a < n; a += kThreads) {
       const double r = fma(-lam, s.Mc[a], s.Hc[a]);
+      s.r[a] = r;
       rr = fma(r, r, rr);
       mm = fma(s.Mc[a], s.Mc[a], mm);
     }
@@ -374,33 +377,43 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
       break;
     }
     if (it >= p.max_iter) break;
-    if (rn > kSwitch) {
-      // inverse-power step: c <- (K0 + zeta G)^{-1} M c
-      for (int e = threadIdx.x; e < n * n; e += kThreads) s.J[e] = fma(zeta, s.G[e], s.K0[e]);
-      for (int a = threadIdx.x; a < n; a += kThreads) s.x[a] = s.Mc[a];
-      __syncthreads();
-      if (!cholesky(s.J, n, s.red)) break;
-      chol_solve(s.J, n, s.x);
-      for (int a = threadIdx.x; a < n; a += kThreads) s.c[a] = s.x[a];
-      __syncthreads();
-    } else {
-      const int m = s.n1p;
-      for (int e = threadIdx.x; e < m * m; e += kThreads) {
-        const int a = e / m, b = e % m;
-        double v;
-        if (a < n && b < n)
-          v = fma(3.0 * zeta, s.G[a * n + b], fma(-lam, s.MM[a * n + b], s.K0[a * n + b]));
-        else if (a == n && b == n)
-          v = 0.0;
-        else
-          v = -s.Mc[a < n ? a : b];
-        s.J[e] = v;
+    bool newton = rn <= kSwitch;
+    if (newton) {
+      // A' = K0 + 3 zeta G - lambda M + |lambda| (Mc)(Mc)^T
+      const double tau = fabs(lam);
+      for (int e = threadIdx.x; e < n * n; e += kThreads) {
+        const int a = e / n, b = e - (e / n) * n;
+        s.A[e] = fma(tau * s.Mc[a], s.Mc[b],
+                     fma(3.0 * zeta, s.G[e], fma(-lam, s.MM[e], s.K0[e])));
       }
-      for (int a = threadIdx.x; a < m; a += kThreads)
-        s.x[a] = a < n ? -fma(-lam, s.Mc[a], s.Hc[a]) : 0.0;
+      for (int a = threadIdx.x; a < n; a += kThreads) {
+        s.y1[a] = s.r[a];
+        s.y2[a] = s.Mc[a];
+      }
       __syncthreads();
-      if (!lu_solve(s.J, m, s.x)) break;
-      for (int a = threadIdx.x; a < n; a += kThreads) s.c[a] += s.x[a];
+      newton = ldlt(s.A, n);
+      if (newton) {
+        invert_pivots(s.A, n, s.dinv);
+        if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
+        else if ((threadIdx.x >> 5) == 1) ldlt_solve_warp(s.A, s.dinv, n, s.y2);
+        __syncthreads();
+        const double m1 = dotv(s.Mc, s.y1, n, s.red);
+        const double m2 = dotv(s.Mc, s.y2, n, s.red);
+        const double dl = m1 / m2;
+        for (int a = threadIdx.x; a < n; a += kThreads) s.c[a] += fma(dl, s.y2[a], -s.y1[a]);
+        __syncthreads();
+      }
+    }
+    if (!newton) {
+      // inverse-power step: c <- (K0 + zeta G)^{-1} M c
+      for (int e = threadIdx.x; e < n * n; e += kThreads) s.A[e] = fma(zeta, s.G[e], s.K0[e]);
+      for (int a = threadIdx.x; a < n; a += kThreads) s.y1[a] = s.Mc[a];
+      __syncthreads();
+      if (!ldlt(s.A, n)) break;
+      invert_pivots(s.A, n, s.dinv);
+      if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
+      __syncthreads();
+      for (int a = threadIdx.x; a < n; a += kThreads) s.c[a] = s.y1[a];
       __syncthreads();
     }
     normalise_and_sign(p, s);
@@ -413,53 +426,85 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   }
 }
 
+// L^{-1} for an SPD matrix: L = C D C^T, then all columns of C D C^T X = I at once (rows
+// sequential, columns spread over the threads), everything in shared memory.
 __global__ void __launch_bounds__(kThreads) k_spd_inverse(const double* L, double* Linv, int n) {
   extern __shared__ double sm[];
   double* A = sm;
-  double* red = A + n * n;
-  for (int e = threadIdx.x; e < n * n; e += kThreads) A[e] = L[e];
+  double* Y = A + n * n;
+  for (int e = threadIdx.x; e < n * n; e += kThreads) {
+    A[e] = L[e];
+    const int i = e / n, j = e - (e / n) * n;
+    Y[e] = i == j ? 1.0 : 0.0;
+  }
   __syncthreads();
-  if (!cholesky(A, n, red)) {
+  if (!ldlt(A, n)) {
     for (int e = threadIdx.x; e < n * n; e += kThreads) Linv[e] = nan("");
     return;
   }
-  // column j of the inverse: forward then backward substitution, one thread per column
-  for (int j = threadIdx.x; j < n; j += kThreads) {
-    for (int i = 0; i < n; ++i) {
-      double s = i == j ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s = fma(-A[i * n + k], Linv[k * n + j], s);
-      Linv[i * n + j] = s / A[i * n + i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // forward: rows of W with (C D) W = I: W_k = (Y_k - sum_{i<k} A_ki W_i) / D_k
+  for (int k = 0; k < n; ++k) {
+    const double inv = recip(A[k * n + k]);
+    for (int j = threadIdx.x; j < n; j += kThreads) Y[k * n + j] *= inv;
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += kWarps) {
+      const double l = A[i * n + k];
+      for (int j = lane; j < n; j += 32) Y[i * n + j] = fma(-l, Y[k * n + j], Y[i * n + j]);
     }
-    for (int i = n - 1; i >= 0; --i) {
-      double s = Linv[i * n + j];
-      for (int k = i + 1; k < n; ++k) s = fma(-A[k * n + i], Linv[k * n + j], s);
-      Linv[i * n + j] = s / A[i * n + i];
-    }
+    __syncthreads();
   }
+  // backward: C^T X = W, X_k = W_k - sum_{i>k} (A_ki / D_k) X_i
+  for (int k = n - 1; k >= 0; --k) {
+    for (int i = warp; i < k; i += kWarps) {
+      const double l = A[i * n + k] * recip(A[i * n + i]);
+      for (int j = lane; j < n; j += 32) Y[i * n + j] = fma(-l, Y[k * n + j], Y[i * n + j]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += kThreads) Linv[e] = Y[e];
 }
 
-__global__ void k_coarse_matvec2d(int n, int pitch, const double* __restrict__ Linv,
-                                  const double* __restrict__ x, double* __restrict__ y) {
-  const int m = n - 1;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= m * m) return;
-  const double* row = Linv + (size_t)p * m * m;
-  double s = 0.0;
-  for (int q = 0; q < m * m; ++q) s = fma(row[q], x[(size_t)(1 + q / m) * pitch + 1 + q % m], s);
-  y[(size_t)(1 + p / m) * pitch + 1 + p % m] = s;
+// y = Linv x on the interior of level 1: one CTA, x gathered to shared memory, one warp per
+// row with coalesced loads and a shuffle reduction.
+__device__ __forceinline__ size_t level1_index(int dim, int m, int pitch, int q) {
+  if (dim == 2) return (size_t)(1 + q / m) * pitch + 1 + q % m;
+  return ((size_t)(1 + q / (m * m)) * (m + 2) + 1 + (q / m) % m) * pitch + 1 + q % m;
+}
+
+__global__ void __launch_bounds__(kThreads) k_coarse_matvec(int dim, int n, int pitch,
+                                                            const double* __restrict__ Linv,
+                                                            const double* __restrict__ x,
+                                                            double* __restrict__ y) {
+  __shared__ double xs[1024];
+  const int m = n - 1, nh = dim == 2 ? m * m : m * m * m;
+  for (int q = threadIdx.x; q < nh; q += kThreads) xs[q] = x[level1_index(dim, m, pitch, q)];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int p = warp; p < nh; p += kWarps) {
+    const double* row = Linv + (size_t)p * nh;
+    double s = 0.0;
+    for (int q = lane; q < nh; q += 32) s = fma(row[q], xs[q], s);
+    s = warp_sum(s);
+    if (lane == 0) y[level1_index(dim, m, pitch, p)] = s;
+  }
 }
 
 }  // namespace
 
-size_t dense_smem_bytes(int n, int ntri, int nvert) {
-  const int n1p = n + 1, L = nvert + 1;
-  return sizeof(double) * ((size_t)3 * n * n + (size_t)n1p * n1p + 3 * n + n1p +
-                           (size_t)ntri * L * L + kThreads);
+size_t dense_smem_bytes(int n, int ntri, int nvert, int aug) {
+  const int L = nvert + 1, nh = n - aug;
+  const size_t nt3 = nvert == 3 ? 10 : 20;
+  const size_t maxadj = nvert == 3 ? 6 : 24;
+  return sizeof(double) * ((size_t)4 * n * n + (size_t)ntri * L * L +
+                           (size_t)nvert * nvert * nvert * nvert + 8 * (size_t)n + kThreads +
+                           nh + (aug ? (size_t)ntri * nt3 : 0) + ((size_t)ntri * nvert + 1) / 2 +
+                           ((size_t)nh * maxadj + 1) / 2 + (aug ? (size_t)nh * nh : 0));
 }
 
 void dense_scf(const DenseProblem& p, cudaStream_t s) {
   const int n = p.nh + p.aug;
-  k_dense_scf<<<1, kThreads, dense_smem_bytes(n, p.ntri, p.nvert), s>>>(p);
+  k_dense_scf<<<1, kThreads, dense_smem_bytes(n, p.ntri, p.nvert, p.aug), s>>>(p);
 }
 
 // The attribute is per function, shared by every handle in the process, so it is always set
@@ -474,13 +519,12 @@ cudaError_t dense_prepare(size_t need) {
 }
 
 void dense_spd_inverse(const double* L, double* Linv, int n, cudaStream_t s) {
-  k_spd_inverse<<<1, kThreads, sizeof(double) * ((size_t)n * n + kThreads), s>>>(L, Linv, n);
+  k_spd_inverse<<<1, kThreads, sizeof(double) * (2 * (size_t)n * n), s>>>(L, Linv, n);
 }
 
-void coarse_matvec2d(const Grid& g, const double* Linv, const double* x, double* y,
-                     cudaStream_t s) {
-  const int m = g.n - 1;
-  k_coarse_matvec2d<<<(m * m + 63) / 64, 64, 0, s>>>(g.n, g.pitch, Linv, x, y);
+void coarse_matvec(const Grid& g, const double* Linv, const double* x, double* y,
+                   cudaStream_t s) {
+  k_coarse_matvec<<<1, kThreads, 0, s>>>(g.dim, g.n, g.pitch, Linv, x, y);
 }
 
 }  // namespace fmg

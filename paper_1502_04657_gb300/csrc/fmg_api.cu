@@ -16,64 +16,81 @@ namespace {
 struct Level {
   Grid g;
   Coef2D c{};
+  Coef3D c3{};
   double *x = nullptr, *xt = nullptr, *f = nullptr, *r = nullptr, *u = nullptr,
          *y = nullptr, *z = nullptr;
+  Density2D b{};          // density stencil of u~ (augmented pass), 2D
+  Density3D b3{};         // same, 3D
+  double* pw = nullptr;   // (x / r)^m table for the 2D T3 sums (levels >= 2)
+  double* t3map = nullptr;  // class sums -> T3 map of this level (levels >= 2)
 };
 
-// Symmetric 6-point rule of degree 4 on a triangle: two orbits of barycentric points
-// (a, b, b), b = (1 - a)/2, three points each with weight w_k / 3 (w_1 + w_2 = 1).  The three
-// parameters solve the exactness conditions for lambda_1^2, lambda_1 lambda_2 lambda_3 and
-// lambda_1^4, whose exact means over a triangle are 2 alpha! / (|alpha| + 2)!; with the
-// orbit symmetry these imply exactness for every polynomial of degree <= 4.
-bool six_point_rule(double out[4]) {
-  const double t[3] = {1.0 / 6.0, 1.0 / 60.0, 1.0 / 15.0};
-  double x[3] = {0.1, 0.8, 0.2};  // a1, a2, w1
-  auto eval = [&](const double* v, double* f) {
-    double m[2][3];
-    for (int o = 0; o < 2; ++o) {
-      const double a = v[o], b = 0.5 * (1.0 - a);
-      m[o][0] = (a * a + 2 * b * b) / 3.0;
-      m[o][1] = a * b * b;
-      m[o][2] = (a * a * a * a + 2 * b * b * b * b) / 3.0;
-    }
-    for (int q = 0; q < 3; ++q) f[q] = v[2] * m[0][q] + (1.0 - v[2]) * m[1][q] - t[q];
-  };
-  for (int it = 0; it < 100; ++it) {
-    double f[3], jac[3][3];
-    eval(x, f);
-    for (int c = 0; c < 3; ++c) {
-      double xp[3] = {x[0], x[1], x[2]}, fp[3];
-      const double hstep = 1e-7;
-      xp[c] += hstep;
-      eval(xp, fp);
-      for (int q = 0; q < 3; ++q) jac[q][c] = (fp[q] - f[q]) / hstep;
-    }
-    // solve jac d = -f (3x3 Cramer)
-    auto det3 = [](double m[3][3]) {
-      return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
-             m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
-             m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
-    };
-    const double d = det3(jac);
-    if (d == 0.0) return false;
-    double step[3];
-    for (int c = 0; c < 3; ++c) {
-      double m[3][3];
-      for (int q = 0; q < 3; ++q)
-        for (int k = 0; k < 3; ++k) m[q][k] = k == c ? -f[q] : jac[q][k];
-      step[c] = det3(m) / d;
-    }
-    for (int c = 0; c < 3; ++c) x[c] += step[c];
-    if (fabs(step[0]) + fabs(step[1]) + fabs(step[2]) < 1e-16) break;
+// ---- dimension dispatch of the level kernels -----------------------------------------------
+void lv_coef(Level& l, const PotentialParams* p, cudaStream_t s) {
+  if (l.g.dim == 2) coef2d_setup(l.g, p, l.c, s);
+  else coef3d_setup(l.g, p, l.c3, s);
+}
+void lv_apply(Level& l, const double* x, double* y, cudaStream_t s) {
+  if (l.g.dim == 2) apply2d(l.g, l.c, x, y, s);
+  else apply3d(l.g, l.c3, x, y, s);
+}
+void lv_mass(Level& l, const double* x, double* y, cudaStream_t s) {
+  if (l.g.dim == 2) mass2d(l.g, x, y, s);
+  else mass3d(l.g, x, y, s);
+}
+void lv_jacobi(Level& l, const double* f, const double* x, double* xo, bool zero, cudaStream_t s) {
+  if (l.g.dim == 2) jacobi2d(l.g, l.c, f, x, xo, zero, s);
+  else jacobi3d(l.g, l.c3, f, x, xo, zero, s);
+}
+void lv_residual(Level& l, const double* f, const double* x, double* r, cudaStream_t s) {
+  if (l.g.dim == 2) residual2d(l.g, l.c, f, x, r, s);
+  else residual3d(l.g, l.c3, f, x, r, s);
+}
+void lv_restrict(Level& fl, Level& cl, const double* rf, double* rc, cudaStream_t s) {
+  if (fl.g.dim == 2) restrict2d(fl.g, cl.g, rf, rc, s);
+  else restrict3d(fl.g, cl.g, rf, rc, s);
+}
+void lv_prolong(Level& fl, Level& cl, const double* ec, double* xf, bool add, const double* extra,
+                const double* scale, cudaStream_t s) {
+  if (fl.g.dim == 2) prolong2d(fl.g, cl.g, ec, xf, add, extra, scale, s);
+  else prolong3d(fl.g, cl.g, ec, xf, add, extra, scale, s);
+}
+void lv_nload(Level& l, const double* u, double* out, cudaStream_t s) {
+  if (l.g.dim == 2) nload2d(l.g, u, out, s);
+  else nload3d(l.g, u, out, s);
+}
+void lv_rhs(Level& l, const double* lam, const PotentialParams* p, const double* u, double* f,
+            cudaStream_t s) {
+  if (l.g.dim == 2) rhs2d(l.g, lam, p, u, f, s);
+  else rhs3d(l.g, lam, p, u, f, s);
+}
+void lv_nload_density(Level& l, const double* u, double* nl, cudaStream_t s) {
+  if (l.g.dim == 2) nload_density2d(l.g, u, nl, l.b, s);
+  else nload_density3d(l.g, u, nl, l.b3, s);
+}
+void lv_coarsen_density(Level& fl, Level& cl, cudaStream_t s) {
+  if (fl.g.dim == 2) coarsen_density2d(fl.g, cl.g, fl.b, cl.b, s);
+  else coarsen_density3d(fl.g, cl.g, fl.b3, cl.b3, s);
+}
+void lv_t3(Level& l, int n1, const double* u, double* partials, double* t3, cudaStream_t s) {
+  if (l.g.dim == 2) t3_moments2d(l.g, n1, u, l.pw, l.t3map, partials, t3, s);
+  else t3_moments3d(l.g, n1, u, l.t3map, partials, t3, s);
+}
+void lv_dense_level1(Level& l1, double* L, double* M, cudaStream_t s) {
+  if (l1.g.dim == 2) dense_level1_2d(l1.g, l1.c, L, M, s);
+  else dense_level1_3d(l1.g, l1.c3, L, M, s);
+}
+void lv_start(Level& l1, double box_len, double* c, cudaStream_t s) {
+  if (l1.g.dim == 2) start_vector(l1.g, box_len, c, s);
+  else start_vector3d(l1.g, c, s);
+}
+void lv_gather_level1(Level& l1, double* gA, double* gM, double* t1, double* B1, cudaStream_t s) {
+  if (l1.g.dim == 2) {
+    gather_level1_2d(l1.g, l1.y, l1.z, l1.r, l1.b, gA, gM, t1, B1, s);
+  } else {
+    gather_vec3d(l1.g, l1.y, l1.z, l1.r, gA, gM, t1, s);
+    density_dense3d(l1.g, l1.b3, B1, s);
   }
-  double f[3];
-  eval(x, f);
-  if (fabs(f[0]) + fabs(f[1]) + fabs(f[2]) > 1e-15) return false;
-  out[0] = x[0];
-  out[1] = x[2];
-  out[2] = x[1];
-  out[3] = 1.0 - x[2];
-  return true;
 }
 
 enum ProfId { kProfJacobi, kProfResidual, kProfRestrict, kProfProlong, kProfRhs,
@@ -95,11 +112,12 @@ struct fmg_eig_handle {
   std::vector<void*> allocs;
   int nh = 0, ntri = 0, nvert = 3, maxadj = 6;
   double tri_vol = 0.0;
-  double rule[4] = {0, 0, 0, 0};
   double *L1 = nullptr, *M1 = nullptr, *L1inv = nullptr, *q4 = nullptr;
   int *tri = nullptr, *adj = nullptr;
   double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr, *partials = nullptr,
-         *mom = nullptr, *mom_partials = nullptr, *lam_levels = nullptr, *scal = nullptr,
+         *t3 = nullptr, *t3_partials = nullptr, *cls_mom = nullptr, *gAd = nullptr,
+         *gMd = nullptr, *t1d = nullptr, *B1d = nullptr, *t0 = nullptr,
+         *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr,
          *uout = nullptr;
   int *iters = nullptr, *status = nullptr;
   PotentialParams* dparams = nullptr;  // device copy read by the kernels
@@ -162,8 +180,7 @@ int validate(const fmg_eig_problem* p) {
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
   if (p->smoother != FMG_SMOOTH_JACOBI) return FMG_ENOTSUP;
-  if (p->dim != 2 || p->precision != FMG_FP64 || p->operator_form != FMG_W_LEFT)
-    return FMG_ENOTSUP;
+  if (p->precision != FMG_FP64 || p->operator_form != FMG_W_LEFT) return FMG_ENOTSUP;
   return FMG_OK;
 }
 
@@ -181,21 +198,34 @@ PotentialParams potential(const fmg_eig_problem& p) {
 
 void build_levels(fmg_eig_handle* h) {
   const fmg_eig_problem& p = h->prob;
+  const int dim = p.dim;
   h->lv.resize(p.levels);
   for (int k = 1; k <= p.levels; ++k) {
     Level& l = h->L(k);
-    l.g.dim = 2;
+    l.g.dim = dim;
     l.g.n = p.coarse_cells << (k - 1);
     l.g.rows = l.g.n + 1;
     l.g.pitch = (l.g.n + 1 + 31) / 32 * 32;
-    l.g.stride = (size_t)l.g.rows * l.g.pitch;
+    l.g.stride = (size_t)l.g.rows * l.g.pitch * (dim == 3 ? (size_t)l.g.rows : 1);
     l.g.h = p.box_len / l.g.n;
     const size_t s = l.g.stride;
-    l.c.cC = h->alloc<double>(s);
-    l.c.cE = h->alloc<double>(s);
-    l.c.cN = h->alloc<double>(s);
-    l.c.cNE = h->alloc<double>(s);
-    l.c.dinv = h->alloc<double>(s);
+    if (dim == 2) {
+      l.c.cC = h->alloc<double>(s);
+      l.c.cE = h->alloc<double>(s);
+      l.c.cN = h->alloc<double>(s);
+      l.c.cNE = h->alloc<double>(s);
+      l.c.dinv = h->alloc<double>(s);
+      l.c.tab = h->alloc<double>(8 * (size_t)(l.g.n + 1));
+      l.b.C = h->alloc<double>(s);
+      l.b.E = h->alloc<double>(s);
+      l.b.N = h->alloc<double>(s);
+      l.b.NE = h->alloc<double>(s);
+    } else {
+      for (int q = 0; q < 8; ++q) l.c3.a[q] = h->alloc<double>(s);
+      l.c3.dinv = h->alloc<double>(s);
+      l.c3.tab = h->alloc<double>(15 * (size_t)(l.g.n + 1));
+      for (int q = 0; q < 8; ++q) l.b3.a[q] = h->alloc<double>(s);
+    }
     l.x = h->alloc<double>(s);
     l.xt = h->alloc<double>(s);
     l.f = h->alloc<double>(s);
@@ -203,50 +233,100 @@ void build_levels(fmg_eig_handle* h) {
     l.u = h->alloc<double>(s);
     l.y = h->alloc<double>(s);
     l.z = h->alloc<double>(s);
+    if (k >= 2) {
+      const int r = 1 << (k - 1);
+      if (dim == 2) {
+        std::vector<double> pw(4 * (r + 1));
+        t3_power_table(r, pw.data());
+        l.pw = h->alloc<double>(pw.size());
+        cudaMemcpy(l.pw, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice);
+        double map[2 * 10 * 25];
+        t3_map2d(r, map);
+        l.t3map = h->alloc<double>(2 * 10 * 25);
+        cudaMemcpy(l.t3map, map, sizeof(map), cudaMemcpyHostToDevice);
+      } else {
+        std::vector<double> map(20 * 15 * 20);
+        t3_map3d(r, map.data());
+        l.t3map = h->alloc<double>(map.size());
+        cudaMemcpy(l.t3map, map.data(), map.size() * sizeof(double), cudaMemcpyHostToDevice);
+      }
+    }
   }
 }
 
 void build_coarse(fmg_eig_handle* h) {
   const int n1 = h->prob.coarse_cells;
   const int m = n1 - 1;
-  h->nh = m * m;
-  h->nvert = 3;
-  h->ntri = 2 * n1 * n1;
-  h->maxadj = 6;
+  const int dim = h->prob.dim;
   const double H = h->prob.box_len / n1;
-  h->tri_vol = H * H / 2.0;
-  std::vector<int> tri(h->ntri * 3), adj(h->nh * h->maxadj, -1);
-  auto id = [&](int i, int j) { return (i < 1 || j < 1 || i >= n1 || j >= n1) ? -1 : (i - 1) + (j - 1) * m; };
-  for (int J = 0; J < n1; ++J)
-    for (int I = 0; I < n1; ++I) {
-      const int cell = I + n1 * J;
-      const int t0[3] = {id(I, J), id(I + 1, J), id(I + 1, J + 1)};
-      const int t1[3] = {id(I, J), id(I + 1, J + 1), id(I, J + 1)};
-      for (int v = 0; v < 3; ++v) {
-        tri[(2 * cell) * 3 + v] = t0[v];
-        tri[(2 * cell + 1) * 3 + v] = t1[v];
+  std::vector<int> tri, adj;
+  std::vector<double> q4;
+  if (dim == 2) {
+    h->nh = m * m;
+    h->nvert = 3;
+    h->ntri = 2 * n1 * n1;
+    h->maxadj = 6;
+    h->tri_vol = H * H / 2.0;
+    tri.resize(h->ntri * 3);
+    auto id = [&](int i, int j) { return (i < 1 || j < 1 || i >= n1 || j >= n1) ? -1 : (i - 1) + (j - 1) * m; };
+    for (int J = 0; J < n1; ++J)
+      for (int I = 0; I < n1; ++I) {
+        const int cell = I + n1 * J;
+        const int t0[3] = {id(I, J), id(I + 1, J), id(I + 1, J + 1)};
+        const int t1[3] = {id(I, J), id(I + 1, J + 1), id(I, J + 1)};
+        for (int v = 0; v < 3; ++v) {
+          tri[(2 * cell) * 3 + v] = t0[v];
+          tri[(2 * cell + 1) * 3 + v] = t1[v];
+        }
       }
-    }
+  } else {
+    h->nh = m * m * m;
+    h->nvert = 4;
+    h->ntri = 6 * n1 * n1 * n1;
+    h->maxadj = 24;
+    h->tri_vol = H * H * H / 6.0;
+    tri.resize(h->ntri * 4);
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    auto id = [&](int i, int j, int l) {
+      return (i < 1 || j < 1 || l < 1 || i >= n1 || j >= n1 || l >= n1)
+                 ? -1 : (i - 1) + (j - 1) * m + (l - 1) * m * m;
+    };
+    for (int L = 0; L < n1; ++L)
+      for (int J = 0; J < n1; ++J)
+        for (int I = 0; I < n1; ++I) {
+          const int cell = I + n1 * (J + n1 * L);
+          for (int sp = 0; sp < 6; ++sp) {
+            int v[3] = {I, J, L};
+            int* out = &tri[(6 * cell + sp) * 4];
+            out[0] = id(v[0], v[1], v[2]);
+            v[perm[sp][0]]++;
+            out[1] = id(v[0], v[1], v[2]);
+            v[perm[sp][1]]++;
+            out[2] = id(v[0], v[1], v[2]);
+            out[3] = id(I + 1, J + 1, L + 1);
+          }
+        }
+  }
+  const int nv = h->nvert;
+  adj.assign(h->nh * h->maxadj, -1);
   std::vector<int> fill(h->nh, 0);
   for (int t = 0; t < h->ntri; ++t)
-    for (int v = 0; v < 3; ++v) {
-      const int a = tri[t * 3 + v];
+    for (int v = 0; v < nv; ++v) {
+      const int a = tri[t * nv + v];
       if (a >= 0) adj[a * h->maxadj + fill[a]++] = (t << 3) | v;
     }
-  // q4[a][b][c][d] = int_T mu_a mu_b mu_c mu_d / |T| = 2! alpha! / (4 + 2)!
-  std::vector<double> q4(81);
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b)
-      for (int c = 0; c < 3; ++c)
-        for (int d = 0; d < 3; ++d) {
-          int cnt[3] = {0, 0, 0};
-          cnt[a]++;
-          cnt[b]++;
-          cnt[c]++;
-          cnt[d]++;
-          q4[((a * 3 + b) * 3 + c) * 3 + d] =
-              2.0 * factorial(cnt[0]) * factorial(cnt[1]) * factorial(cnt[2]) / factorial(6);
-        }
+  // q4[a][b][c][d] = int_T mu_a mu_b mu_c mu_d / |T| = d! alpha! / (4 + d)!
+  q4.resize(nv * nv * nv * nv);
+  for (int e = 0; e < nv * nv * nv * nv; ++e) {
+    int cnt[4] = {0, 0, 0, 0};
+    cnt[e % nv]++;
+    cnt[(e / nv) % nv]++;
+    cnt[(e / (nv * nv)) % nv]++;
+    cnt[e / (nv * nv * nv)]++;
+    double num = factorial(dim);
+    for (int q = 0; q < nv; ++q) num *= factorial(cnt[q]);
+    q4[e] = num / factorial(4 + dim);
+  }
   h->tri = h->alloc<int>(tri.size());
   h->adj = h->alloc<int>(adj.size());
   h->q4 = h->alloc<double>(q4.size());
@@ -263,14 +343,22 @@ void build_coarse(fmg_eig_handle* h) {
   h->buu = h->alloc<double>(1);
   h->scal = h->alloc<double>(8);
   h->partials = h->alloc<double>(kReduceBlocks);
-  h->mom = h->alloc<double>((size_t)h->ntri * kMom);
-  h->mom_partials =
-      h->alloc<double>(std::max<size_t>(1, moments2d_partials(h->L(h->levels()).g, n1)));
+  const int nt3 = dim == 2 ? 10 : 20;
+  h->t3 = h->alloc<double>((size_t)h->ntri * nt3);
+  const Grid& gf = h->L(h->levels()).g;
+  h->t3_partials = h->alloc<double>(
+      std::max<size_t>(1, dim == 2 ? t3_partials2d(gf, n1) : t3_partials3d(gf, n1)));
+  h->gAd = h->alloc<double>(h->nh);
+  h->gMd = h->alloc<double>(h->nh);
+  h->t1d = h->alloc<double>(h->nh);
+  h->B1d = h->alloc<double>((size_t)h->nh * h->nh);
+  h->t0 = h->alloc<double>(1);
+  h->kscratch = h->alloc<double>(3 * (size_t)(h->nh + 1) * (h->nh + 1) + h->nh + 1);
   h->lam_levels = h->alloc<double>(FMG_MAX_LEVELS);
   h->iters = h->alloc<int>(FMG_MAX_LEVELS);
   h->status = h->alloc<int>(FMG_MAX_LEVELS);
   h->uout = h->alloc<double>(h->L(h->levels()).g.interior());
-  h->dense_smem = dense_smem_bytes(h->nh + 1, h->ntri, h->nvert);
+  h->dense_smem = dense_smem_bytes(h->nh + 1, h->ntri, h->nvert, 1);
 }
 
 // ---- enqueue helpers (all work in stream order on s) ---------------------------------------
@@ -286,8 +374,8 @@ void prof_end(fmg_eig_handle* h, int id, int level, cudaStream_t s) {
 }
 
 void enqueue_setup(fmg_eig_handle* h, cudaStream_t s) {
-  for (int k = 1; k <= h->levels(); ++k) coef2d_setup(h->L(k).g, h->dparams, h->L(k).c, s);
-  dense_level1_2d(h->L(1).g, h->L(1).c, h->L1, h->M1, s);
+  for (int k = 1; k <= h->levels(); ++k) lv_coef(h->L(k), h->dparams, s);
+  lv_dense_level1(h->L(1), h->L1, h->M1, s);
   dense_spd_inverse(h->L1, h->L1inv, h->nh, s);
 }
 
@@ -303,8 +391,7 @@ DenseProblem dense_base(fmg_eig_handle* h) {
   d.tri_vol = h->tri_vol;
   d.L1 = h->L1;
   d.M1 = h->M1;
-  d.n1 = h->prob.coarse_cells;
-  d.pitch1 = h->L(1).g.pitch;
+  d.nt3 = h->prob.dim == 2 ? 10 : 20;
   d.params = h->dparams;
   d.tol = h->prob.scf_tol;
   d.max_iter = h->prob.scf_max_iter;
@@ -316,7 +403,7 @@ DenseProblem dense_base(fmg_eig_handle* h) {
 // Algorithm 3.2 step 1 into L(1).u and h->lam
 void enqueue_coarse(fmg_eig_handle* h, cudaStream_t s) {
   Level& l1 = h->L(1);
-  start_vector(l1.g, h->prob.box_len, h->cstart, s);
+  lv_start(l1, h->prob.box_len, h->cstart, s);
   DenseProblem d = dense_base(h);
   d.aug = 0;
   d.c_init = h->cstart;
@@ -330,7 +417,7 @@ void enqueue_coarse(fmg_eig_handle* h, cudaStream_t s) {
 void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   Level& l = h->L(j);
   if (j == 1) {
-    coarse_matvec2d(l.g, h->L1inv, l.f, l.x, s);
+    coarse_matvec(l.g, h->L1inv, l.f, l.x, s);
     return;
   }
   const fmg_eig_problem& p = h->prob;
@@ -339,7 +426,7 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   for (int it = 0; it < p.nu_pre; ++it) {
     const bool prof = !zero;
     if (prof) prof_begin(h, kProfJacobi, j, s);
-    jacobi2d(l.g, l.c, l.f, l.x, l.xt, zero, s);
+    lv_jacobi(l, l.f, l.x, l.xt, zero, s);
     if (prof) prof_end(h, kProfJacobi, j, s);
     std::swap(l.x, l.xt);
     zero = false;
@@ -347,17 +434,17 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   if (zero) cudaMemsetAsync(l.x, 0, l.g.stride * sizeof(double), s);
   Level& lc = h->L(j - 1);
   prof_begin(h, kProfResidual, j, s);
-  residual2d(l.g, l.c, l.f, l.x, l.r, s);
+  lv_residual(l, l.f, l.x, l.r, s);
   prof_end(h, kProfResidual, j, s);
   prof_begin(h, kProfRestrict, j, s);
-  restrict2d(l.g, lc.g, l.r, lc.f, s);
+  lv_restrict(l, lc, l.r, lc.f, s);
   prof_end(h, kProfRestrict, j, s);
   enqueue_vcycle(h, j - 1, true, s);
   prof_begin(h, kProfProlong, j, s);
-  prolong2d(l.g, lc.g, lc.x, l.x, true, nullptr, nullptr, s);
+  lv_prolong(l, lc, lc.x, l.x, true, nullptr, nullptr, s);
   prof_end(h, kProfProlong, j, s);
   for (int it = 0; it < p.nu_post; ++it) {
-    jacobi2d(l.g, l.c, l.f, l.x, l.xt, false, s);
+    lv_jacobi(l, l.f, l.x, l.xt, false, s);
     std::swap(l.x, l.xt);
   }
   prof_end(h, kProfVcycle, j, s);
@@ -367,36 +454,61 @@ void enqueue_multigrid(fmg_eig_handle* h, int k, cudaStream_t s) {
   for (int it = 0; it < h->prob.vcycles; ++it) enqueue_vcycle(h, k, false, s);
 }
 
+// Fine pass of the augmented problem on level k for u~ (Algorithm 3.1 step 2): the linear
+// blocks g_A = P^T..P^T L u~, g_M = P^T..P^T M u~, u~^T L u~, u~^T M u~, and the moments
+// T0, T1 (restricted cubic load), T2 (coarsened density stencil), T3 (per coarse triangle),
+// gathered into the dense level-1 arrays of the handle.
+void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s) {
+  Level& l = h->L(k);
+  lv_apply(l, ut, l.y, s);
+  lv_mass(l, ut, l.z, s);
+  dot(ut, l.y, l.g.stride, h->partials, h->auu, s);
+  dot(ut, l.z, l.g.stride, h->partials, h->buu, s);
+  prof_begin(h, kProfMoments, k, s);
+  lv_nload_density(l, ut, l.r, s);
+  lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, s);
+  prof_end(h, kProfMoments, k, s);
+  dot(ut, l.r, l.g.stride, h->partials, h->t0, s);
+  for (int j = k; j >= 2; --j) {
+    Level& f = h->L(j);
+    Level& c = h->L(j - 1);
+    lv_restrict(f, c, f.y, c.y, s);
+    lv_restrict(f, c, f.z, c.z, s);
+    lv_restrict(f, c, f.r, c.r, s);
+    lv_coarsen_density(f, c, s);
+  }
+  Level& l1 = h->L(1);
+  lv_gather_level1(l1, h->gAd, h->gMd, h->t1d, h->B1d, s);
+}
+
+DenseProblem dense_augmented(fmg_eig_handle* h) {
+  DenseProblem d = dense_base(h);
+  d.aug = 1;
+  d.gA = h->gAd;
+  d.gM = h->gMd;
+  d.t1 = h->t1d;
+  d.B1 = h->B1d;
+  d.t3 = h->t3;
+  d.auu = h->auu;
+  d.buu = h->buu;
+  d.t0 = h->t0;
+  return d;
+}
+
 // One correction step (Algorithm 3.1) on level k: (h->lam, L(k).u) -> (h->lam, L(k).u);
 // u~ stays in L(k).x.
 void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   Level& l = h->L(k);
   // step 1: auxiliary problem, m V-cycles from u
   prof_begin(h, kProfRhs, k, s);
-  rhs2d(l.g, h->lam, h->dparams, l.u, l.f, s);
+  lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
   prof_end(h, kProfRhs, k, s);
   cudaMemcpyAsync(l.x, l.u, l.g.stride * sizeof(double), cudaMemcpyDeviceToDevice, s);
   enqueue_multigrid(h, k, s);
   const double* ut = l.x;
   // step 2: augmented space V_H + span{u~}
-  apply2d(l.g, l.c, ut, l.y, s);
-  mass2d(l.g, ut, l.z, s);
-  dot(ut, l.y, l.g.stride, h->partials, h->auu, s);
-  dot(ut, l.z, l.g.stride, h->partials, h->buu, s);
-  for (int j = k; j >= 2; --j) {
-    restrict2d(h->L(j).g, h->L(j - 1).g, h->L(j).y, h->L(j - 1).y, s);
-    restrict2d(h->L(j).g, h->L(j - 1).g, h->L(j).z, h->L(j - 1).z, s);
-  }
-  prof_begin(h, kProfMoments, k, s);
-  moments2d(l.g, h->prob.coarse_cells, ut, h->mom_partials, h->mom, h->rule, s);
-  prof_end(h, kProfMoments, k, s);
-  DenseProblem d = dense_base(h);
-  d.aug = 1;
-  d.gA = h->L(1).y;
-  d.gM = h->L(1).z;
-  d.auu = h->auu;
-  d.buu = h->buu;
-  d.mom = h->mom;
+  enqueue_augment(h, k, ut, s);
+  DenseProblem d = dense_augmented(h);
   d.c_init = nullptr;
   d.iters_out = h->iters + (k - 1);
   d.status_out = h->status + (k - 1);
@@ -406,8 +518,8 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   // u = P_{k<-1} c_H + c_u u~
   scatter_level1(h->L(1).g, h->c, h->L(1).y, s);
   for (int j = 2; j < k; ++j)
-    prolong2d(h->L(j).g, h->L(j - 1).g, h->L(j - 1).y, h->L(j).y, false, nullptr, nullptr, s);
-  prolong2d(l.g, h->L(k - 1).g, h->L(k - 1).y, l.u, false, ut, h->c + h->nh, s);
+    lv_prolong(h->L(j), h->L(j - 1), h->L(j - 1).y, h->L(j).y, false, nullptr, nullptr, s);
+  lv_prolong(l, h->L(k - 1), h->L(k - 1).y, l.u, false, ut, h->c + h->nh, s);
 }
 
 void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s) {
@@ -415,7 +527,7 @@ void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s) {
   enqueue_coarse(h, s);
   cudaMemcpyAsync(h->lam_levels, h->lam, sizeof(double), cudaMemcpyDeviceToDevice, s);
   for (int k = 2; k <= h->levels(); ++k) {
-    prolong2d(h->L(k).g, h->L(k - 1).g, h->L(k - 1).u, h->L(k).u, false, nullptr, nullptr, s);
+    lv_prolong(h->L(k), h->L(k - 1), h->L(k - 1).u, h->L(k).u, false, nullptr, nullptr, s);
     for (int it = 0; it < h->prob.corrections; ++it) enqueue_correction(h, k, s);
     cudaMemcpyAsync(h->lam_levels + (k - 1), h->lam, sizeof(double), cudaMemcpyDeviceToDevice,
                     s);
@@ -453,10 +565,6 @@ int fmg_eig_create(const fmg_eig_problem* prob, fmg_eig_handle** out) {
   fmg_eig_handle* h = new (std::nothrow) fmg_eig_handle();
   if (!h) return FMG_ENOMEM;
   h->prob = *prob;
-  if (!six_point_rule(h->rule)) {
-    delete h;
-    return FMG_ECUDA;
-  }
   if (cudaGetDevice(&h->dev) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
@@ -629,9 +737,9 @@ int fmg_eig_solve(fmg_eig_handle* h, double* lambda, double* u_host, size_t u_le
     CK(cudaMemcpy(stats->scf_iters, h->iters, sizeof(int) * h->levels(), cudaMemcpyDeviceToHost));
     // b(u,u) - 1 and lambda - a(u,u) - (Wu,u) - zeta int u^4 on the finest level
     Level& l = h->L(h->levels());
-    apply2d(l.g, l.c, l.u, l.y, s);
-    mass2d(l.g, l.u, l.z, s);
-    nload2d(l.g, l.u, l.r, s);
+    lv_apply(l, l.u, l.y, s);
+    lv_mass(l, l.u, l.z, s);
+    lv_nload(l, l.u, l.r, s);
     dot(l.u, l.y, l.g.stride, h->partials, h->scal + 0, s);
     dot(l.u, l.z, l.g.stride, h->partials, h->scal + 1, s);
     dot(l.u, l.r, l.g.stride, h->partials, h->scal + 2, s);
@@ -651,7 +759,7 @@ int fmg_eig_apply_operator(fmg_eig_handle* h, int32_t level, const double* x_dev
   cudaStream_t s = pick(h, stream);
   Level& l = h->L(level);
   pack_interior(l.g, x_dev, l.r, s);
-  apply2d(l.g, l.c, l.r, l.y, s);
+  lv_apply(l, l.r, l.y, s);
   unpack_interior(l.g, l.y, y_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -663,7 +771,7 @@ int fmg_eig_apply_mass(fmg_eig_handle* h, int32_t level, const double* x_dev, do
   cudaStream_t s = pick(h, stream);
   Level& l = h->L(level);
   pack_interior(l.g, x_dev, l.r, s);
-  mass2d(l.g, l.r, l.y, s);
+  lv_mass(l, l.r, l.y, s);
   unpack_interior(l.g, l.y, y_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -676,7 +784,7 @@ int fmg_eig_jacobi(fmg_eig_handle* h, int32_t level, const double* f_dev,
   Level& l = h->L(level);
   pack_interior(l.g, f_dev, l.f, s);
   pack_interior(l.g, x_in_dev, l.r, s);
-  jacobi2d(l.g, l.c, l.f, l.r, l.y, false, s);
+  lv_jacobi(l, l.f, l.r, l.y, false, s);
   unpack_interior(l.g, l.y, x_out_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -690,8 +798,8 @@ int fmg_eig_residual_restrict(fmg_eig_handle* h, int32_t level, const double* f_
   Level& lc = h->L(level - 1);
   pack_interior(l.g, f_dev, l.f, s);
   pack_interior(l.g, x_dev, l.z, s);
-  residual2d(l.g, l.c, l.f, l.z, l.r, s);
-  restrict2d(l.g, lc.g, l.r, lc.y, s);
+  lv_residual(l, l.f, l.z, l.r, s);
+  lv_restrict(l, lc, l.r, lc.y, s);
   unpack_interior(lc.g, lc.y, rc_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -705,7 +813,7 @@ int fmg_eig_prolong_add(fmg_eig_handle* h, int32_t level, const double* ec_dev, 
   Level& lc = h->L(level - 1);
   pack_interior(lc.g, ec_dev, lc.y, s);
   pack_interior(l.g, x_dev, l.y, s);
-  prolong2d(l.g, lc.g, lc.y, l.y, true, nullptr, nullptr, s);
+  lv_prolong(l, lc, lc.y, l.y, true, nullptr, nullptr, s);
   unpack_interior(l.g, l.y, x_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -717,7 +825,7 @@ int fmg_eig_nonlinear_load(fmg_eig_handle* h, int32_t level, const double* u_dev
   cudaStream_t s = pick(h, stream);
   Level& l = h->L(level);
   pack_interior(l.g, u_dev, l.r, s);
-  nload2d(l.g, l.r, l.y, s);
+  lv_nload(l, l.r, l.y, s);
   unpack_interior(l.g, l.y, n_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -731,7 +839,7 @@ int fmg_eig_aux_rhs(fmg_eig_handle* h, int32_t level, double lambda, const doubl
   CK(cudaStreamSynchronize(s));
   CK(cudaMemcpy(h->scal + 7, &lambda, sizeof(double), cudaMemcpyHostToDevice));
   pack_interior(l.g, u_dev, l.r, s);
-  rhs2d(l.g, h->scal + 7, h->dparams, l.r, l.y, s);
+  lv_rhs(l, h->scal + 7, h->dparams, l.r, l.y, s);
   unpack_interior(l.g, l.y, f_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -770,6 +878,36 @@ int fmg_eig_correction(fmg_eig_handle* h, int32_t level, double lambda_in,
   CK(cudaStreamSynchronize(s));
   if (iters) *iters = it;
   return st == 0 ? FMG_OK : FMG_ENOCONV;
+}
+
+int fmg_eig_augmented_system(fmg_eig_handle* h, int32_t level, const double* u_tilde_dev,
+                             const double* c_host, int32_t n, double* K_host, double* M_host,
+                             double* G_host) {
+  if (!level_ok(h, level) || level < 2 || !u_tilde_dev || !c_host || !K_host || !M_host ||
+      !G_host || n != h->nh + 1)
+    return FMG_EINVAL;
+  cudaStream_t s = h->stream;
+  Level& l = h->L(level);
+  const size_t nn = (size_t)n * n;
+  double* kd = h->kscratch;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpy(kd + 3 * nn, c_host, n * sizeof(double), cudaMemcpyHostToDevice));
+  pack_interior(l.g, u_tilde_dev, l.x, s);
+  enqueue_augment(h, level, l.x, s);
+  DenseProblem d = dense_augmented(h);
+  d.c_init = kd + 3 * nn;
+  d.K_out = kd;
+  d.M_out = kd + nn;
+  d.G_out = kd + 2 * nn;
+  d.iters_out = h->iters;
+  d.status_out = h->status;
+  dense_scf(d, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(K_host, kd, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(M_host, kd + nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(G_host, kd + 2 * nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return FMG_OK;
 }
 
 int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev, int32_t* iters) {

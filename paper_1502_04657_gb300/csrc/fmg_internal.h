@@ -33,6 +33,7 @@ struct Coef2D {
   double* cN;    // coupling (i,j)-(i,j+1)
   double* cNE;   // coupling (i,j)-(i+1,j+1)
   double* dinv;  // omega / cC
+  double* tab;   // 8 * (n + 1) separable parts of the coefficients (setup scratch)
 };
 
 // Problem parameters that may change between solves of one handle.  They live in device
@@ -67,6 +68,53 @@ void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaS
 // sin-product start vector for the level-1 nonlinear solve
 void start_vector(const Grid& g, double box_len, double* c, cudaStream_t s);
 
+// ---- 3D level kernels (grid3d.cu) -------------------------------------------------------
+// Couplings of L on the Kuhn mesh: a[0] diagonal, a[1 + d] the coupling of p with p + d for
+// d = X, Y, Z, XY, XZ, YZ, XYZ (the coupling with p - d is a[1 + d] at p - d).
+struct Coef3D {
+  double* a[8];
+  double* dinv;  // omega / diagonal
+  double* tab;   // 15 * (n + 1) separable parts (setup scratch)
+};
+struct Density3D {
+  double* a[8];  // same layout as Coef3D::a
+};
+struct Stencil15 {
+  const double* a[8];
+};
+void coef3d_setup(const Grid& g, const PotentialParams* p_dev, const Coef3D& c, cudaStream_t s);
+void apply3d(const Grid& g, const Coef3D& c, const double* x, double* y, cudaStream_t s);
+void mass3d(const Grid& g, const double* x, double* y, cudaStream_t s);
+void jacobi3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* xo,
+              bool x_is_zero, cudaStream_t s);
+void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* r,
+                cudaStream_t s);
+void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
+                cudaStream_t s);
+void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
+               const double* extra, const double* scale, cudaStream_t s);
+void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s);
+void rhs3d(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
+           double* f, cudaStream_t s);
+void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
+                     cudaStream_t s);
+void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,
+                       const Density3D& bc, cudaStream_t s);
+void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaStream_t s);
+void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s);
+void gather_vec3d(const Grid& g, const double* a, const double* b, const double* c, double* oa,
+                  double* ob, double* oc, cudaStream_t s);
+void start_vector3d(const Grid& g, double* c, cudaStream_t s);
+
+// ---- 3D augmented pass (augment3d.cu) -----------------------------------------------------
+// T3 per coarse Kuhn tetrahedron (20 per tetrahedron, sorted triples of its 4 vertices),
+// tetrahedron index 6 * (I + n1 (J + n1 L)) + s, s the axis permutation in lexicographic
+// order, vertices (V, V + e_s0, V + e_s0 + e_s1, V + (1,1,1)).
+size_t t3_partials3d(const Grid& fine, int n1);
+void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
+                  double* partials, double* t3, cudaStream_t s);
+void t3_map3d(int r, double* out);  // 20 * 15 * 20 doubles
+
 // ---- Reductions (reduce.cu) -------------------------------------------------------------
 // out[0] = sum_i a[i] * b[i] over n entries; deterministic two-stage tree.  `partials` holds
 // at least kReduceBlocks doubles.
@@ -80,16 +128,31 @@ void unpack_interior(const Grid& g, const double* padded, double* interior, cuda
 // padded level-1 vector from a dense coefficient vector c (first n1 entries)
 void scatter_level1(const Grid& g, const double* c, double* padded, cudaStream_t s);
 
-// ---- Augmented-space moments (moments2d.cu) ----------------------------------------------
-// Per coarse triangle (2 per coarse cell, coarse cell index = I + n1 * J, triangle
-// 2 * cell + {0: (V00,V10,V11), 1: (V00,V11,V01)}): 20 moments of u~ against the coarse
-// barycentric coordinates mu_a of that triangle:
-//   [0] int u^4, [1..3] int u^3 mu_a, [4..9] int u^2 mu_a mu_b (a<=b: 00,01,02,11,12,22),
-//   [10..19] int u mu_a mu_b mu_c (a<=b<=c: 000,001,002,011,012,022,111,112,122,222).
-constexpr int kMom = 20;
-size_t moments2d_partials(const Grid& fine, int n1);  // doubles of scratch needed
-void moments2d(const Grid& fine, int n1, const double* u, double* partials, double* out,
-               const double rule[4], cudaStream_t s);
+// ---- Augmented-space fine pass (augment2d.cu) ---------------------------------------------
+// Density stencil B(u)_pq = int u^2 phi_p phi_q of one 2D level (couplings to p, E, N, NE).
+struct Density2D {
+  double *C, *E, *N, *NE;
+};
+// nl = N(u) (int u^3 phi_p) and the density stencil of u on level g, in one pass.
+void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D& b,
+                     cudaStream_t s);
+// Galerkin coarsening of the density stencil: bc = P^T bf P.
+void coarsen_density2d(const Grid& fine, const Grid& coarse, const Density2D& bf,
+                       const Density2D& bc, cudaStream_t s);
+// T3^T_abc = int_T u mu_a mu_b mu_c per coarse triangle (10 per triangle, a <= b <= c,
+// lexicographic), from per-class monomial sums.  pw: (x/r)^m table of the level, map: the
+// level's 2 x 10 x 25 map (t3_map2d), partials: t3_partials2d(fine, n1) doubles.
+size_t t3_partials2d(const Grid& fine, int n1);
+void t3_moments2d(const Grid& fine, int n1, const double* u, const double* pw,
+                  const double* map, double* partials, double* t3, cudaStream_t s);
+void t3_class_moments2d(double out[2 * 7 * 10]);
+void t3_map2d(int r, double out[2 * 10 * 25]);
+void t3_power_table(int r, double* out);  // 4 * (r + 1) doubles
+// dense level-1 data for the augmented solve: gA, gM, t1 (nh) and B1 (nh x nh) from padded
+// level-1 vectors and the level-1 density stencil
+void gather_level1_2d(const Grid& g1, const double* gA_pad, const double* gM_pad,
+                      const double* t1_pad, const Density2D& b1, double* gA, double* gM,
+                      double* t1, double* B1, cudaStream_t s);
 
 // ---- Dense small solves (dense.cu) -------------------------------------------------------
 struct DenseProblem {
@@ -97,20 +160,23 @@ struct DenseProblem {
   int aug;             // 1: basis (phi^H, u~), n = nh + 1; 0: basis phi^H, n = nh
   int ntri;            // coarse simplices
   int nvert;           // vertices per simplex (3 in 2D, 4 in 3D)
+  int nt3;             // entries of T3 per simplex (10 in 2D, 20 in 3D)
   const int* tri;      // ntri * nvert coarse interior indices, -1 on the boundary
   const int* adj;      // nh * maxadj codes (simplex << 3 | local vertex), -1 terminated
   int maxadj;
   const double* q4;    // nvert^4 table: int_T mu_a mu_b mu_c mu_d / |T|
   double tri_vol;      // |T|
-  const double* L1;    // nh*nh
-  const double* M1;    // nh*nh
-  const double* gA;    // padded level-1 vector P^T..P^T L u~        (aug)
-  const double* gM;    // padded level-1 vector P^T..P^T M u~        (aug)
-  const double* auu;   // u~^T L u~                                    (aug)
-  const double* buu;   // u~^T M u~                                    (aug)
-  const double* mom;   // ntri * kMom (2D) moments                     (aug)
-  int n1;              // cells per side of level 1 (to read padded gA/gM)
-  int pitch1;
+  const double* L1;    // nh*nh, operator of level 1
+  const double* M1;    // nh*nh, mass of level 1
+  // augmented problem only:
+  const double* gA;    // nh: P^T..P^T L u~
+  const double* gM;    // nh: P^T..P^T M u~
+  const double* t1;    // nh: int u~^3 phi^H_a
+  const double* B1;    // nh*nh: int u~^2 phi^H_a phi^H_b
+  const double* t3;    // ntri * nt3: int_T u~ mu_a mu_b mu_c (sorted triples)
+  const double* auu;   // u~^T L u~
+  const double* buu;   // u~^T M u~
+  const double* t0;    // int u~^4
   const PotentialParams* params;  // device; zeta read from here
   double tol;
   int max_iter;
@@ -119,15 +185,19 @@ struct DenseProblem {
   double* lam_out;       // 1
   int* iters_out;        // 1
   int* status_out;       // 1 (0 converged, 1 cap hit)
+  // optional: assemble only (K0, M, G(c_init)) into these n x n outputs and stop
+  double* K_out;
+  double* M_out;
+  double* G_out;
 };
 constexpr size_t kDenseSmemLimit = 200 * 1024;  // dynamic shared memory of the dense solve
-size_t dense_smem_bytes(int n, int ntri, int nvert);
+size_t dense_smem_bytes(int n, int ntri, int nvert, int aug);
 cudaError_t dense_prepare(size_t max_smem);  // opt in to large dynamic shared memory
 void dense_scf(const DenseProblem& p, cudaStream_t s);
 // Linv = L^{-1} for an SPD n x n matrix (Cholesky), one CTA.
 void dense_spd_inverse(const double* L, double* Linv, int n, cudaStream_t s);
-// y(padded level 1) = Linv * x(padded level 1) on the interior nodes
-void coarse_matvec2d(const Grid& g, const double* Linv, const double* x, double* y,
-                     cudaStream_t s);
+// y(padded level 1) = Linv * x(padded level 1) on the interior nodes (2D or 3D)
+void coarse_matvec(const Grid& g, const double* Linv, const double* x, double* y,
+                   cudaStream_t s);
 
 }  // namespace fmg

@@ -1,0 +1,491 @@
+// 3D level kernels: matrix-free P1 stencils on the structured Kuhn-tetrahedron mesh.
+//
+// Mesh (Section 3, regular refinement with beta = 2): cubes of side h split into the 6 Kuhn
+// tetrahedra {v, v+e_s1, v+e_s1+e_s2, v+(1,1,1)}, s a permutation of the axes; the same
+// pattern reappears under regular refinement.  Node p couples to the 14 neighbours p +- d,
+// d in {X, Y, Z, XY, XZ, YZ, XYZ} (the nonzero 0/1 vectors), and lies in 24 tetrahedra.
+// Exact integration over those (derived once by symbolic integration), with x = i h etc.:
+//   C  :  6h + w0 h^3 2/5  + h^5 sum_axes w_a (42 a^2 + 5)/105
+//   X  : -h  + w0 h^3 /20  + h^5 [wx (63i^2+63i+19)/1260 + wy (63j^2+5)/1260 + wz (63l^2+5)/1260]
+//   XY :       w0 h^3 /30  + h^5 [wx (84i^2+84i+25)/2520 + wy (84j^2+84j+25)/2520 + wz (21l^2+1)/630]
+//   XYZ:       w0 h^3 /20  + h^5 [wx (63i^2+63i+19)/1260 + wy (..j..) + wz (..l..)]
+// (Y, Z, XZ, YZ by permuting the axes; the coupling to p - d is the one of p - d to p).  The
+// mass stencil is h^3 (2/5 at C, 1/20 along axes and the body diagonal, 1/30 along face
+// diagonals).  As in 2D, the 8 coupling arrays and omega/D are materialised once per solve.
+#include "fmg_internal.h"
+
+namespace fmg {
+namespace {
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+
+// neighbour k = 2 d + (0: +d, 1: -d), d = X, Y, Z, XY, XZ, YZ, XYZ
+__device__ constexpr int kDir[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0},
+                                       {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
+// The 24 tetrahedra of a node's star as triples of neighbour indices (from the Kuhn split of
+// the 8 cells around the node).
+__device__ constexpr int kStar[24][3] = {
+    {0, 6, 12},  {0, 8, 12},  {2, 6, 12},  {2, 10, 12}, {4, 8, 12},  {4, 10, 12},
+    {5, 0, 6},   {5, 2, 6},   {3, 0, 8},   {3, 4, 8},   {11, 5, 0},  {11, 3, 0},
+    {1, 2, 10},  {1, 4, 10},  {9, 5, 2},   {9, 1, 2},   {7, 3, 4},   {7, 1, 4},
+    {13, 11, 5}, {13, 11, 3}, {13, 9, 5},  {13, 9, 1},  {13, 7, 3},  {13, 7, 1}};
+
+struct Idx3 {
+  size_t p;      // linear index of the node
+  long off[7];   // linear offset of +d
+};
+
+__device__ __forceinline__ long dir_off(int d, int pitch, long plane) {
+  return kDir[d][0] + (long)kDir[d][1] * pitch + (long)kDir[d][2] * plane;
+}
+
+#define INTERIOR_3D                                                       \
+  const int i = 1 + blockIdx.x * BX + threadIdx.x;                        \
+  const int j = 1 + blockIdx.y * BY + threadIdx.y;                        \
+  const int l = 1 + blockIdx.z;                                           \
+  if (i >= n || j >= n || l >= n) return;                                 \
+  const long plane = (long)(n + 1) * pitch;                               \
+  const size_t k = (size_t)l * plane + (size_t)j * pitch + i;
+
+// tables (n + 1 entries each), per axis a in {x, y, z}, weighted by w_a h^5:
+//   0: C part (42 a^2 + 5)/105, 1: along an axis or the body diagonal (63a^2+63a+19)/1260,
+//   2: across an axis direction (63a^2+5)/1260, 3: along a face diagonal (84a^2+84a+25)/2520,
+//   4: across a face diagonal (21a^2+1)/630.
+__global__ void k_coef1d_3d(int n, double h, const PotentialParams* __restrict__ pp,
+                            double* __restrict__ tab) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x > n) return;
+  const PotentialParams p = *pp;
+  const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
+  const double h2 = h * h, h5 = h2 * h2 * h;
+  const double a = x;
+  const double poly[5] = {(42.0 * a * a + 5.0) / 105.0, (63.0 * a * a + 63.0 * a + 19.0) / 1260.0,
+                          (63.0 * a * a + 5.0) / 1260.0, (84.0 * a * a + 84.0 * a + 25.0) / 2520.0,
+                          (21.0 * a * a + 1.0) / 630.0};
+  const double w[3] = {p.wx, p.wy, p.wz};
+  const int s = n + 1;
+  for (int ax = 0; ax < 3; ++ax)
+    for (int q = 0; q < 5; ++q) tab[(ax * 5 + q) * s + x] = wl * h5 * w[ax] * poly[q];
+}
+
+__device__ __forceinline__ double recip(double c) {
+  double y = (double)__frcp_rn((float)c);
+  y = fma(y, fma(-c, y, 1.0), y);
+  y = fma(y, fma(-c, y, 1.0), y);
+  return y;
+}
+
+__global__ void k_coef3d(int n, int pitch, double h, const double* __restrict__ tab,
+                         const PotentialParams* __restrict__ pp, Coef3D c) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int l = blockIdx.z;
+  if (i > n || j > n || l > n) return;
+  const PotentialParams p = *pp;
+  const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
+  const double h3 = h * h * h;
+  const int s = n + 1;
+  const int co[3] = {i, j, l};
+  auto T = [&](int ax, int q) { return tab[(ax * 5 + q) * s + co[ax]]; };
+  const size_t k = ((size_t)l * (n + 1) + j) * pitch + i;
+  const double cc = 6.0 * h + wl * 0.4 * h3 * p.w0 + T(0, 0) + T(1, 0) + T(2, 0);
+  c.a[0][k] = cc;
+  // axis directions: along = table 1 on that axis, across = table 2 on the others
+  for (int d = 0; d < 3; ++d) {
+    double v = -h + wl * h3 * p.w0 / 20.0;
+    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == d ? 1 : 2);
+    c.a[1 + d][k] = v;
+  }
+  // face diagonals XY, XZ, YZ: along on the two axes, across on the third
+  const int other[3] = {2, 1, 0};
+  for (int f = 0; f < 3; ++f) {
+    double v = wl * h3 * p.w0 / 30.0;
+    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == other[f] ? 4 : 3);
+    c.a[4 + f][k] = v;
+  }
+  c.a[7][k] = wl * h3 * p.w0 / 20.0 + T(0, 1) + T(1, 1) + T(2, 1);
+  c.dinv[k] = p.omega * recip(cc);
+}
+
+__device__ __forceinline__ double lop3(const Coef3D& c, const double* __restrict__ x, size_t k,
+                                       int pitch, long plane) {
+  double v = c.a[0][k] * x[k];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) {
+    const long o = dir_off(d, pitch, plane);
+    v = fma(c.a[1 + d][k], x[k + o], v);
+    v = fma(c.a[1 + d][k - o], x[k - o], v);
+  }
+  return v;
+}
+
+__global__ void k_apply3d(int n, int pitch, Coef3D c, const double* __restrict__ x,
+                          double* __restrict__ y) {
+  INTERIOR_3D
+  y[k] = lop3(c, x, k, pitch, plane);
+}
+
+__global__ void k_jacobi3d(int n, int pitch, Coef3D c, const double* __restrict__ f,
+                           const double* __restrict__ x, double* __restrict__ xo) {
+  INTERIOR_3D
+  xo[k] = fma(c.dinv[k], f[k] - lop3(c, x, k, pitch, plane), x[k]);
+}
+
+__global__ void k_jacobi3d_zero(int n, int pitch, Coef3D c, const double* __restrict__ f,
+                                double* __restrict__ xo) {
+  INTERIOR_3D
+  xo[k] = c.dinv[k] * f[k];
+}
+
+__global__ void k_residual3d(int n, int pitch, Coef3D c, const double* __restrict__ f,
+                             const double* __restrict__ x, double* __restrict__ r) {
+  INTERIOR_3D
+  r[k] = f[k] - lop3(c, x, k, pitch, plane);
+}
+
+__device__ __forceinline__ double mass_at(const double* __restrict__ x, size_t k, int pitch,
+                                          long plane) {
+  double ax = 0.0, fd = 0.0;
+#pragma unroll
+  for (int d = 0; d < 7; ++d) {
+    const long o = dir_off(d, pitch, plane);
+    const double s = x[k + o] + x[k - o];
+    if (d >= 3 && d < 6) fd += s;
+    else ax += s;
+  }
+  return fma(0.4, x[k], fma(1.0 / 20.0, ax, fd / 30.0));
+}
+
+__global__ void k_mass3d(int n, int pitch, double h3, const double* __restrict__ x,
+                         double* __restrict__ y) {
+  INTERIOR_3D
+  y[k] = h3 * mass_at(x, k, pitch, plane);
+}
+
+// r_c = P^T r_f: own fine value plus half of the 14 fine neighbours along the mesh edges.
+__global__ void k_restrict3d(int nc, int pc, int pf, const double* __restrict__ rf,
+                             double* __restrict__ rc) {
+  const int I = 1 + blockIdx.x * BX + threadIdx.x;
+  const int J = 1 + blockIdx.y * BY + threadIdx.y;
+  const int L = 1 + blockIdx.z;
+  if (I >= nc || J >= nc || L >= nc) return;
+  const long planef = (long)(2 * nc + 1) * pf;
+  const size_t kf = (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
+  double s = 0.0;
+#pragma unroll
+  for (int d = 0; d < 7; ++d) {
+    const long o = dir_off(d, pf, planef);
+    s += rf[kf + o] + rf[kf - o];
+  }
+  rc[((size_t)L * (nc + 1) + J) * pc + I] = fma(0.5, s, rf[kf]);
+}
+
+// x_f (+)= P e_c (+ scale * extra): fine node 2I + a (a in {0,1}^3) is the midpoint of coarse
+// nodes I and I + a, which are joined by a mesh edge.
+__global__ void k_prolong3d(int nf, int pf, int pc, const double* __restrict__ ec,
+                            double* __restrict__ xf, int add, const double* __restrict__ extra,
+                            const double* __restrict__ scale) {
+  const int n = nf, pitch = pf;
+  INTERIOR_3D
+  const int a = i & 1, b = j & 1, cc = l & 1;
+  const int nc = nf / 2;
+  const long planec = (long)(nc + 1) * pc;
+  const size_t kc = (size_t)(l >> 1) * planec + (size_t)(j >> 1) * pc + (i >> 1);
+  double e = ec[kc];
+  if (a | b | cc) e = 0.5 * (e + ec[kc + a + (size_t)b * pc + (size_t)cc * planec]);
+  if (add) e += xf[k];
+  if (extra) e = fma(scale[0], extra[k], e);
+  xf[k] = e;
+}
+
+// Star sums over the 24 tetrahedra of p (vertex values u_p, u_q, u_r, u_s; |K| = h^3/6):
+//   int u^3 lambda_p        = |K|/140 [h3 + u_p (h2 + u_p (s + u_p))]
+//   int u^2 lambda_p^2      = |K|/210 [3 u_p^2 + 2 u_p s + h2]
+//   int u^2 lambda_p lambda_q = |K|/420 [u_p^2 + u_q^2 + u_p u_q + h2 + (u_p + u_q) s]
+// with s, h2, h3 the complete homogeneous symmetric sums of degree 1, 2, 3 of the four
+// values (h2 = (s^2 + P2)/2, h3 = (s^3 + 3 s P2 + 2 P3)/6 from the power sums P2, P3).
+template <bool DENSITY>
+__device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, int pitch,
+                                      long plane, double& nl, double* b) {
+  double nv[14];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) {
+    const long o = dir_off(d, pitch, plane);
+    nv[2 * d] = u[k + o];
+    nv[2 * d + 1] = u[k - o];
+  }
+  const double up = u[k];
+  const double up2 = up * up;
+  double acc = 0.0, accC = 0.0;
+  double accE[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int t = 0; t < 24; ++t) {
+    const double a = nv[kStar[t][0]], b2 = nv[kStar[t][1]], c = nv[kStar[t][2]];
+    const double s = up + a + b2 + c;
+    const double p2 = fma(up, up, fma(a, a, fma(b2, b2, c * c)));
+    const double p3 = fma(up2, up, fma(a * a, a, fma(b2 * b2, b2, c * c * c)));
+    const double hh2 = 0.5 * fma(s, s, p2);
+    const double hh3 = fma(s, fma(s, s, 3.0 * p2), 2.0 * p3) * (1.0 / 6.0);
+    acc += fma(up, fma(up, s + up, hh2), hh3);
+    if (DENSITY) {
+      accC += fma(3.0, up2, fma(2.0 * up, s, hh2));
+      // edges to the "+" neighbours of this tetrahedron
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const int nb = kStar[t][v];
+        if ((nb & 1) == 0) {
+          const double q = nv[nb];
+          accE[nb >> 1] += fma(up + q, s, fma(q, q + up, up2) + hh2);
+        }
+      }
+    }
+  }
+  nl = acc;
+  if (DENSITY) {
+    b[0] = accC;
+#pragma unroll
+    for (int d = 0; d < 7; ++d) b[1 + d] = accE[d];
+  }
+}
+
+__global__ void k_nload3d(int n, int pitch, double scale, const double* __restrict__ u,
+                          double* __restrict__ out) {
+  INTERIOR_3D
+  double nl;
+  star3<false>(u, k, pitch, plane, nl, nullptr);
+  out[k] = scale * nl;
+}
+
+__global__ void k_rhs3d(int n, int pitch, double h3, double nscale,
+                        const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                        const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_3D
+  double nl;
+  star3<false>(u, k, pitch, plane, nl, nullptr);
+  const double mu = h3 * mass_at(u, k, pitch, plane);
+  f[k] = fma(lam[0], mu, -(pp->zeta * nscale) * nl);
+}
+
+__global__ void k_nload_density3d(int n, int pitch, double vol, const double* __restrict__ u,
+                                  double* __restrict__ nl, Density3D b) {
+  INTERIOR_3D
+  double v, e[8];
+  star3<true>(u, k, pitch, plane, v, e);
+  nl[k] = (vol / 140.0) * v;
+  b.a[0][k] = (vol / 210.0) * e[0];
+#pragma unroll
+  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = (vol / 420.0) * e[1 + d];
+}
+
+// Galerkin coarsening of the 15-point density stencil: Bc(a, b) = sum P_va P_wb B(v, w) over
+// the 15-node fine supports of the coarse hats (weights 1 at 2a, 1/2 at 2a +- d).
+__device__ __forceinline__ int nb_of(int dx, int dy, int dz) {
+  // index of the neighbour (dx,dy,dz) in {0: self, 1 + 2d: +d, 2 + 2d: -d}, -1 if not one
+  if (dx == 0 && dy == 0 && dz == 0) return 0;
+  for (int d = 0; d < 7; ++d) {
+    if (dx == kDir[d][0] && dy == kDir[d][1] && dz == kDir[d][2]) return 1 + 2 * d;
+    if (dx == -kDir[d][0] && dy == -kDir[d][1] && dz == -kDir[d][2]) return 2 + 2 * d;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ double fine_entry3(const Density3D& f, size_t kv, int code,
+                                              int pitch, long plane) {
+  if (code == 0) return f.a[0][kv];
+  const int d = (code - 1) >> 1;
+  if (((code - 1) & 1) == 0) return f.a[1 + d][kv];
+  return f.a[1 + d][kv - dir_off(d, pitch, plane)];
+}
+
+template <int T>
+__device__ __forceinline__ double coarse_entry3(const Density3D& f, size_t kf, int pf,
+                                                long planef) {
+  // target offset in coarse units: T = 0 self, 1 + d for +d
+  const int tx = T == 0 ? 0 : kDir[T - 1][0], ty = T == 0 ? 0 : kDir[T - 1][1],
+            tz = T == 0 ? 0 : kDir[T - 1][2];
+  double acc = 0.0;
+#pragma unroll
+  for (int p = 0; p < 15; ++p) {
+    const int px = p == 0 ? 0 : ((p - 1) & 1 ? -kDir[(p - 1) >> 1][0] : kDir[(p - 1) >> 1][0]);
+    const int py = p == 0 ? 0 : ((p - 1) & 1 ? -kDir[(p - 1) >> 1][1] : kDir[(p - 1) >> 1][1]);
+    const int pz = p == 0 ? 0 : ((p - 1) & 1 ? -kDir[(p - 1) >> 1][2] : kDir[(p - 1) >> 1][2]);
+#pragma unroll
+    for (int q = 0; q < 15; ++q) {
+      const int qx = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][0] : kDir[(q - 1) >> 1][0]);
+      const int qy = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][1] : kDir[(q - 1) >> 1][1]);
+      const int qz = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][2] : kDir[(q - 1) >> 1][2]);
+      const int code = nb_of(2 * tx + qx - px, 2 * ty + qy - py, 2 * tz + qz - pz);
+      if (code >= 0) {
+        const double w = (p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5);
+        const size_t kv = kf + px + (long)py * pf + (long)pz * planef;
+        acc = fma(w, fine_entry3(f, kv, code, pf, planef), acc);
+      }
+    }
+  }
+  return acc;
+}
+
+__global__ void k_coarsen_density3d(int nc, int pc, int pf, Density3D f, Density3D c) {
+  const int I = 1 + blockIdx.x * BX + threadIdx.x;
+  const int J = 1 + blockIdx.y * BY + threadIdx.y;
+  const int L = 1 + blockIdx.z;
+  if (I >= nc || J >= nc || L >= nc) return;
+  const long planef = (long)(2 * nc + 1) * pf;
+  const size_t kf = (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
+  const size_t kc = ((size_t)L * (nc + 1) + J) * pc + I;
+  c.a[0][kc] = coarse_entry3<0>(f, kf, pf, planef);
+  // couplings to coarse neighbours outside the interior are never read: skip them
+  if (I + 1 < nc) c.a[1][kc] = coarse_entry3<1>(f, kf, pf, planef);
+  if (J + 1 < nc) c.a[2][kc] = coarse_entry3<2>(f, kf, pf, planef);
+  if (L + 1 < nc) c.a[3][kc] = coarse_entry3<3>(f, kf, pf, planef);
+  if (I + 1 < nc && J + 1 < nc) c.a[4][kc] = coarse_entry3<4>(f, kf, pf, planef);
+  if (I + 1 < nc && L + 1 < nc) c.a[5][kc] = coarse_entry3<5>(f, kf, pf, planef);
+  if (J + 1 < nc && L + 1 < nc) c.a[6][kc] = coarse_entry3<6>(f, kf, pf, planef);
+  if (I + 1 < nc && J + 1 < nc && L + 1 < nc) c.a[7][kc] = coarse_entry3<7>(f, kf, pf, planef);
+}
+
+// dense level-1 matrices from a 15-point stencil given per node as (C, +d couplings)
+__global__ void k_dense15(int n, int pitch, Stencil15 st, int use_stencil, double* out,
+                          double mass_h3) {
+  const double* const* a = use_stencil ? st.a : nullptr;
+  const int m = n - 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m * m * m) return;
+  const int i = 1 + p % m, j = 1 + (p / m) % m, l = 1 + p / (m * m);
+  const long plane = (long)(n + 1) * pitch;
+  const size_t k = (size_t)l * plane + (size_t)j * pitch + i;
+  double* row = out + (size_t)p * m * m * m;
+  for (int q = 0; q < m * m * m; ++q) row[q] = 0.0;
+  row[p] = a ? a[0][k] : 0.4 * mass_h3;
+  for (int d = 0; d < 7; ++d)
+    for (int sg = -1; sg <= 1; sg += 2) {
+      const int ii = i + sg * kDir[d][0], jj = j + sg * kDir[d][1], ll = l + sg * kDir[d][2];
+      if (ii < 1 || jj < 1 || ll < 1 || ii >= n || jj >= n || ll >= n) continue;
+      const size_t kn = (size_t)ll * plane + (size_t)jj * pitch + ii;
+      double v;
+      if (a) v = sg > 0 ? a[1 + d][k] : a[1 + d][kn];
+      else v = mass_h3 * ((d >= 3 && d < 6) ? 1.0 / 30.0 : 1.0 / 20.0);
+      row[(ii - 1) + (size_t)(jj - 1) * m + (size_t)(ll - 1) * m * m] = v;
+    }
+}
+
+__global__ void k_start3d(int n, double* c) {
+  const int m = n - 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m * m * m) return;
+  const int i = 1 + p % m, j = 1 + (p / m) % m, l = 1 + p / (m * m);
+  c[p] = sinpi((double)i / n) * sinpi((double)j / n) * sinpi((double)l / n);
+}
+
+__global__ void k_gather_vec3d(int n, int pitch, const double* __restrict__ a,
+                               const double* __restrict__ b, const double* __restrict__ c,
+                               double* __restrict__ oa, double* __restrict__ ob,
+                               double* __restrict__ oc) {
+  const int m = n - 1;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m * m * m) return;
+  const int i = 1 + p % m, j = 1 + (p / m) % m, l = 1 + p / (m * m);
+  const size_t k = ((size_t)l * (n + 1) + j) * pitch + i;
+  oa[p] = a[k];
+  ob[p] = b[k];
+  oc[p] = c[k];
+}
+
+dim3 grid3(int cx, int cy, int cz) { return dim3((cx + BX - 1) / BX, (cy + BY - 1) / BY, cz); }
+
+}  // namespace
+
+void coef3d_setup(const Grid& g, const PotentialParams* p, const Coef3D& c, cudaStream_t s) {
+  k_coef1d_3d<<<(g.n + 1 + 127) / 128, 128, 0, s>>>(g.n, g.h, p, c.tab);
+  k_coef3d<<<grid3(g.n + 1, g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, g.h, c.tab, p, c);
+}
+
+void apply3d(const Grid& g, const Coef3D& c, const double* x, double* y, cudaStream_t s) {
+  k_apply3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, x, y);
+}
+
+void mass3d(const Grid& g, const double* x, double* y, cudaStream_t s) {
+  k_mass3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch,
+                                                                     g.h * g.h * g.h, x, y);
+}
+
+void jacobi3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* xo,
+              bool x_is_zero, cudaStream_t s) {
+  if (x_is_zero)
+    k_jacobi3d_zero<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f,
+                                                                              xo);
+  else
+    k_jacobi3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x,
+                                                                         xo);
+}
+
+void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* r,
+                cudaStream_t s) {
+  k_residual3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x, r);
+}
+
+void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
+                cudaStream_t s) {
+  k_restrict3d<<<grid3(coarse.n - 1, coarse.n - 1, coarse.n - 1), dim3(BX, BY), 0, s>>>(
+      coarse.n, coarse.pitch, fine.pitch, rf, rc);
+}
+
+void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
+               const double* extra, const double* scale, cudaStream_t s) {
+  k_prolong3d<<<grid3(fine.n - 1, fine.n - 1, fine.n - 1), dim3(BX, BY), 0, s>>>(
+      fine.n, fine.pitch, coarse.pitch, ec, xf, add ? 1 : 0, extra, scale);
+}
+
+void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s) {
+  const double vol = g.h * g.h * g.h / 6.0;
+  k_nload3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, vol / 140.0,
+                                                                      u, out);
+}
+
+void rhs3d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
+           double* f, cudaStream_t s) {
+  const double h3 = g.h * g.h * g.h;
+  k_rhs3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, h3,
+                                                                    h3 / 6.0 / 140.0, lam, p, u, f);
+}
+
+void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
+                     cudaStream_t s) {
+  k_nload_density3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(
+      g.n, g.pitch, g.h * g.h * g.h / 6.0, u, nl, b);
+}
+
+void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,
+                       const Density3D& bc, cudaStream_t s) {
+  k_coarsen_density3d<<<grid3(coarse.n - 1, coarse.n - 1, coarse.n - 1), dim3(BX, BY), 0, s>>>(
+      coarse.n, coarse.pitch, fine.pitch, bf, bc);
+}
+
+void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaStream_t s) {
+  const int m = g.n - 1, cnt = m * m * m;
+  Stencil15 st;
+  for (int q = 0; q < 8; ++q) st.a[q] = c.a[q];
+  k_dense15<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, st, 1, L, 0.0);
+  k_dense15<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, st, 0, M, g.h * g.h * g.h);
+}
+
+void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s) {
+  const int m = g.n - 1, cnt = m * m * m;
+  Stencil15 st;
+  for (int q = 0; q < 8; ++q) st.a[q] = b.a[q];
+  k_dense15<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, st, 1, B, 0.0);
+}
+
+void gather_vec3d(const Grid& g, const double* a, const double* b, const double* c, double* oa,
+                  double* ob, double* oc, cudaStream_t s) {
+  const int m = g.n - 1, cnt = m * m * m;
+  k_gather_vec3d<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, a, b, c, oa, ob, oc);
+}
+
+void start_vector3d(const Grid& g, double* c, cudaStream_t s) {
+  const int m = g.n - 1, cnt = m * m * m;
+  k_start3d<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, c);
+}
+
+}  // namespace fmg

@@ -22,7 +22,7 @@ namespace fmg {
 namespace {
 
 constexpr size_t kScratchDoubles = 32768;  // 256 KiB
-constexpr int kMaxCoarseCells = 10;        // 81 coarse unknowns: the dense solve's limit
+constexpr int kMaxCoarseCells = 9;         // 64 coarse unknowns: the dense solve's shared-memory limit
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
@@ -98,6 +98,7 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   c.cN = take(g.stride);
   c.cNE = take(g.stride);
   c.dinv = take(g.stride);
+  c.tab = take(8 * (size_t)(n1 + 1));
   double* L1 = take((size_t)nh * nh);
   double* M1 = take((size_t)nh * nh);
   double* cstart = take(nh);
@@ -166,8 +167,6 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   d.tri_vol = g.h * g.h / 2.0;
   d.L1 = L1;
   d.M1 = M1;
-  d.n1 = n1;
-  d.pitch1 = g.pitch;
   d.params = reinterpret_cast<const PotentialParams*>(params);
   d.tol = prob->scf_tol;
   d.max_iter = prob->scf_max_iter;
@@ -184,7 +183,7 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
       cudaMemcpyAsync(adj, adj_h, sizeof(int) * nh * 6, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(q4, q4_h, sizeof(q4_h), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(params, &pp, sizeof(pp), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      dense_prepare(dense_smem_bytes(nh, ntri, 3)) != cudaSuccess) {
+      dense_prepare(dense_smem_bytes(nh, ntri, 3, 0)) != cudaSuccess) {
     cudaGetLastError();
     return FMG_ECUDA;
   }

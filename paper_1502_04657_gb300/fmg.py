@@ -67,6 +67,7 @@ _SIGS = {
     "fmg_eig_multigrid": (C.c_int, [_P, _I32, _P, _P, _P]),
     "fmg_eig_correction": (C.c_int, [_P, _I32, C.c_double, _P, _D, _P, _P, C.POINTER(_I32)]),
     "fmg_eig_coarse_solve": (C.c_int, [_P, _D, _P, C.POINTER(_I32)]),
+    "fmg_eig_augmented_system": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _P]),
     "fmg_eig_coarse_solve_noalloc": (C.c_int, [C.POINTER(fmg_eig_problem), _D, _P, C.POINTER(_I32), _P]),
 }
 
@@ -256,6 +257,16 @@ class Solver:
                                          _ptr(u_tilde), C.byref(it))
         self._check(rc, "correction", allow=(FMG_ENOCONV,))
         return lo.value, it.value, rc
+
+    def augmented_system(self, k, u_tilde, c):
+        """(K, M, G(c)) of the augmented space V_H + span{u~} on level k, as numpy arrays."""
+        import numpy as np
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        n = c.size
+        K, M, G = (np.empty((n, n)) for _ in range(3))
+        rc = self.lib.fmg_eig_augmented_system(self.h, k, _ptr(u_tilde), _ptr(c), n, _ptr(K), _ptr(M), _ptr(G))
+        self._check(rc, "augmented_system")
+        return K, M, G
 
     def coarse_solve(self, u_out):
         lo = C.c_double()

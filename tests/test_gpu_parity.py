@@ -119,6 +119,23 @@ def test_multigrid_vcycles(setup, k):
     assert rel(host(xd), O.multigrid(lv, k, f, x, op.vcycles, op)) <= 1e-12
 
 
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_augmented_system(setup, k):
+    """Algorithm 3.1 step 2's small system from one fine pass (restricted loads, coarsened
+    density stencil, per-triangle moments) against its definition Psi^T A Psi, Psi^T M Psi,
+    Psi^T B(Psi c) Psi assembled on the fine grid by the oracle."""
+    op, gp, lv, s = setup
+    rng = np.random.default_rng(600 + k)
+    ut = rng.uniform(0.2, 1.0, size=gp.size(k))
+    psi, k0, mm = O.augmented_blocks(lv, k, ut)
+    c = rng.normal(size=psi.shape[1])
+    g_ref = (psi.T @ O.density_matrix(lv[k - 1].mesh, psi @ c) @ psi).toarray()
+    K, M, G = s.augmented_system(k, dev(ut), c)
+    assert rel(K, k0) <= 1e-12
+    assert rel(M, mm) <= 1e-12
+    assert rel(G, g_ref) <= 1e-12
+
+
 def test_coarse_solve(setup):
     op, gp, lv, s = setup
     lam_o, u_o, res = O.coarse_solve(op, lv[0])
