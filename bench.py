@@ -1,20 +1,20 @@
 #!/usr/bin/env python3
 """Benchmark of the full multigrid GP ground-state solver (one JSON line on rank 0).
 
-Workload (N = 1): the 16.8M-dof 2D configuration - unit square, P1 mesh with (1,1)
+Default workload (N = 1): the 16.8M-dof 2D configuration - unit square, P1 mesh with (1,1)
 diagonals, coarsest h = 1/8 refined 9 times to h = 1/4096 (16,769,025 interior dofs),
 W = x^2 + y^2, zeta = 10, 2 V-cycles of 2 + 2 damped Jacobi (omega = 2/3) per level, one
 correction per level, FP64 throughout.  A step is one complete solve (Algorithm 3.2,
 including the per-solve operator setup and the upload of the problem parameters); inputs are
-resident and the per-solve working set (~2.3 GB) is far larger than the 129 MB L2, so no
-flush is needed between steps.
+resident and the per-solve working set (>2 GB) is far larger than the 129 MB L2, so no flush
+is needed between steps.  --workload selects another configuration (config1, config3, or a
+"-mixed" variant with FP32 V-cycles inside the FP64 defect correction).
 
 --impl ours (default): the CUDA library.  value = solves/s over the timed steps (CUDA events
 on the launch stream), max over ranks; e2e = the same metric through fmg_eig_solve with a
 pinned host output buffer (parameter upload and the D2H copy of lambda and u inside).
---impl reference: the FP64 CPU oracle on this host's cores (rank 0 only), each step a
-bounded sample of the workload (h = 1/256), scaled to the full size by the method's linear
-work (Theorem 3.3).
+--impl reference: the FP64 CPU oracle on this host's cores (rank 0 only), each step a bounded
+sample of the workload, scaled to the full size by the method's linear work (Theorem 3.3).
 Multi-GPU: replicas only (instances are independent; no collective on the data path).
 """
 from __future__ import annotations
@@ -34,18 +34,36 @@ sys.path.insert(0, ROOT)
 from workloads import seeded_problem_2d  # noqa: E402
 
 METRIC = "GP ground-state solves/s and fine-grid MDOF/s at |Δλ|≤1e-8; p50/p99 latency"
-CONFIG = "config2"
-WORKLOAD = ("2D unit square, P1 right-triangle mesh, coarsest h=1/8 refined to h=1/4096 "
-            "(10 levels, 16,769,025 dofs), W=x^2+y^2, zeta=10, m=2 V-cycles, p=1, 2+2 damped "
-            "Jacobi omega=2/3, FP64 plain per-instance solve")
+WORKLOADS = {
+    "config2": ("config2", False,
+                "2D unit square, P1 right-triangle mesh, coarsest h=1/8 refined to h=1/4096 "
+                "(10 levels, 16,769,025 dofs), W=x^2+y^2, zeta=10, m=2 V-cycles, p=1, 2+2 damped "
+                "Jacobi omega=2/3, FP64 plain per-instance solve"),
+    "config2-mixed": ("config2", True,
+                      "config2 with FP32 V-cycles inside the FP64 defect correction"),
+    "config1": ("config1", False,
+                "2D unit square, h=1/8 refined to h=1/256 (6 levels, 65,025 dofs), W=x^2+y^2, "
+                "zeta=1, m=2, p=1, 2+2 Jacobi, FP64"),
+    "config3": ("config3", False,
+                "3D unit cube, Kuhn 6-tet mesh, h=1/4 refined to h=1/256 (7 levels, 16,581,375 "
+                "dofs), W=100(x^2+y^2+4z^2), zeta=100, m=2, p=1, 2+2 Jacobi, FP64"),
+    "config3-mixed": ("config3", True,
+                      "config3 with FP32 V-cycles inside the FP64 defect correction"),
+}
 FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA per clock per SM (1.25 TFLOP/s nominal at 2070 MHz)
 N_SM = 152
-# Algorithmic FP64 flops per finest-level launch unit ("Kernels"):
-#   Jacobi sweep: 7-point L x (7 mul + 6 add) + residual (1) + scale (1) + update (1) = 16 per node
-#   moments: per fine triangle 6 quadrature points x 68 flops = 408 (2 triangles per node)
-FLOPS_PER_UNIT = {"jacobi": 16.0, "moments": 816.0, "residual": 14.0, "rhs": 66.0}
-BYTES_PER_UNIT = {"jacobi": 24.0 + 40.0, "moments": 8.0, "residual": 24.0 + 40.0, "rhs": 16.0}
-DOMINANT = "moments"
+# Algorithmic FP64 flops and bytes per node of the finest-level launch:
+#   Jacobi 2D: 7-point L x (7 mul + 6 add) + residual + scale + update = 16 flop;
+#     24 B (x, f, x') + 40 B (4 couplings + omega/D)
+#   cubic load + density stencil 2D (closed forms over the 6 star triangles): 117 flop; 8 B
+#     read + 40 B written
+#   Jacobi 3D: 15-point = 29 + 3 = 32 flop; 24 B + 72 B
+#   cubic load + density stencil 3D (24 star tetrahedra, ~54 flop each): 1305 flop; 8 B + 72 B
+KERNELS = {
+    2: {"nload_density": (117.0, 48.0), "jacobi": (16.0, 64.0)},
+    3: {"nload_density": (1305.0, 80.0), "jacobi": (32.0, 96.0)},
+}
+DOMINANT = "nload_density"
 
 
 def rank_info():
@@ -61,17 +79,16 @@ class Clocks:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu: int):
-        self.gpu = gpu
-        self.proc = None
-        self.path = None
+        self.gpu, self.proc, self.path = gpu, None, None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
@@ -92,12 +109,13 @@ class Clocks:
         sm = [int(r[1]) for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3] not in ("[N/A]", "")]
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": int(rows[0][2]), "reasons": reasons,
-                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] != "[N/A]")}
+                "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
-def problem_kwargs(levels=None):
-    kw = seeded_problem_2d(CONFIG)
+def problem_kwargs(config: str, levels=None) -> dict:
+    kw = seeded_problem_2d(config)
     if levels is not None:
         kw["levels"] = levels
     return kw
@@ -115,54 +133,143 @@ for _ in range({reps}):
     prob = O.Problem(**kw)
     r = O.fmg_solve(prob)
     times.append(time.perf_counter() - t)
-print(json.dumps({{"times": times, "lam": r.lam, "dofs": (prob.cells(prob.levels) - 1) ** 2}}))
+print(json.dumps({{"times": times, "lam": r.lam, "dofs": (prob.cells(prob.levels) - 1) ** prob.dim}}))
 """
 
 
-def run_oracle(levels: int, reps: int) -> dict:
+def run_oracle(config: str, levels: int, reps: int) -> dict:
     """The oracle in a fresh single-threaded interpreter (exec'd, never forked from CUDA)."""
     env = {**os.environ, "OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
-    code = ORACLE_SNIPPET.format(root=ROOT, cfg=CONFIG, levels=levels, reps=reps)
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=config, levels=levels, reps=reps)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def full_dofs() -> int:
-    kw = problem_kwargs()
+def dofs_of(kw: dict) -> int:
     return ((kw["coarse_cells"] << (kw["levels"] - 1)) - 1) ** kw["dim"]
+
+
+# oracle samples sized for ~10-30 s (cpu_baseline) and a few s per step (reference arm)
+ORACLE_SAMPLE = {"config1": (6, 5), "config2": (7, 6), "config3": (4, 3)}
 
 
 def reference_arm(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return
-    sample_levels = 6
+    config, mixed, desc = WORKLOADS[args.workload]
+    levels = ORACLE_SAMPLE[config][1]
     steps = []
+    r = None
     for i in range(args.warmup + args.steps):
-        r = run_oracle(sample_levels, 1)
+        r = run_oracle(config, levels, 1)
         if i >= args.warmup:
             steps.append(r["times"][0])
-    scale = full_dofs() / r["dofs"]
+    full = dofs_of(problem_kwargs(config))
+    scale = full / r["dofs"]
     per_solve = statistics.mean(steps) * scale
     value = 1.0 / per_solve
-    sample = (f"oracle solve of the same discretisation truncated to 6 levels (h=1/256, {r['dofs']} dofs) "
-              f"per step, scaled x{scale:.1f} to 16,769,025 dofs by the method's linear work (Theorem 3.3)")
+    sample = (f"oracle solve of the same discretisation truncated to {levels} levels "
+              f"({r['dofs']} dofs) per step, scaled x{scale:.1f} to {full} dofs by the method's "
+              f"linear work (Theorem 3.3)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+        "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def ours_arm(args):
-    import numpy as np
+def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist=None,
+            with_e2e: bool = True, clocks: bool = True) -> dict:
     import torch
 
     from paper_1502_04657_gb300 import fmg
+
+    config, mixed, desc = WORKLOADS[workload]
+    kw = problem_kwargs(config)
+    gp = fmg.Problem(**{k: v for k, v in kw.items() if k in fmg.Problem.__dataclass_fields__})
+    if mixed:
+        gp.precision = fmg.FMG_MIXED_FP32
+    n = gp.size(gp.levels)
+    solver = fmg.Solver(gp)
+    stream = torch.cuda.Stream()
+    lam_d = torch.empty(1, dtype=torch.float64, device="cuda")
+    u_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            solver.solve_dev(lam_d, u_d, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk_s = Clocks(local) if clocks else None
+        if clk_s:
+            clk_s.start()
+            time.sleep(0.25)
+        evs[0].record(stream)
+        for i in range(steps):
+            solver.solve_dev(lam_d, u_d, stream=stream.cuda_stream)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        clk = clk_s.stop() if clk_s else None
+        if dist:
+            dist.barrier()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    out = {"value": world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+           "step_ms": step_ms, "lambda": float(lam_d.item()), "dofs": n, "desc": desc,
+           "profile": solver.profile(), "kernels": solver.kernel_count(), "clocks": clk,
+           "dim": gp.dim, "mixed": mixed}
+    if with_e2e:
+        u_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        e2e_steps = max(3, min(steps, 10))
+        solver.solve(u_host)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            lam_e2e, _, _ = solver.solve(u_host)
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        out["e2e"] = {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
+                      "h2d_bytes_per_step": 112, "d2h_bytes_per_step": 8 + 8 * n + 4 * 16}
+        out["lambda_e2e"] = lam_e2e
+    solver.close()
+    return out
+
+
+def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
+    sm_max = (clk or {}).get("sm_max_mhz") or 2070
+    peak = FP64_FLOP_PER_CLK_SM * N_SM * sm_max * 1e6 / 1e12
+    roof = {}
+    for name, (flops, nbytes) in KERNELS[m["dim"]].items():
+        ms = m["profile"].get(name, -1.0)
+        if ms and ms > 0:
+            ach = flops * m["dofs"] / (ms * 1e-3) / 1e12
+            roof[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "traffic": None, "launch_ms": ms,
+                          "hbm_gbs_algorithmic": nbytes * m["dofs"] / (ms * 1e-3) / 1e9}
+    main = dict(roof.get(DOMINANT, {}))
+    main["kernel"] = DOMINANT
+    main["peak_source"] = ("FP64 (the kernel is FP64-ALU bound): 152 SMs x 2 DFMA/clk x sm_max_mhz, "
+                           "nominal 1.25 TFLOP/s; of fallback (no FP64 figure in the measured peaks)")
+    return main, {k: v for k, v in roof.items() if k != DOMINANT}
+
+
+def ours_arm(args):
+    import torch
 
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
@@ -170,103 +277,44 @@ def ours_arm(args):
     if world > 1:
         import torch.distributed as dist  # noqa: F811
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    kw = problem_kwargs()
-    gp = fmg.Problem(**{k: v for k, v in kw.items() if k in fmg.Problem.__dataclass_fields__})
-    n = gp.size(gp.levels)
-    solver = fmg.Solver(gp)
-    stream = torch.cuda.Stream()
-    lam_d = torch.empty(1, dtype=torch.float64, device="cuda")
-    u_d = torch.empty(n, dtype=torch.float64, device="cuda")
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            solver.solve_dev(lam_d, u_d, stream=stream.cuda_stream)
-        torch.cuda.synchronize()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        clocks = Clocks(local)
-        clocks.start()
-        time.sleep(0.25)
-        evs[0].record(stream)
-        for i in range(args.steps):
-            solver.solve_dev(lam_d, u_d, stream=stream.cuda_stream)
-            evs[i + 1].record(stream)
-        torch.cuda.synchronize()
-        clk = clocks.stop()
-        if dist:
-            dist.barrier()
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
-    prof = solver.profile()  # finest-level launches of the last timed solve
-    lam = float(lam_d.item())
-
-    # end to end: public host-buffer call, parameter upload + D2H of lambda and u inside
-    u_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-    e2e_steps = max(3, min(args.steps, 10))
-    solver.solve(u_host)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        lam_e2e, _, _ = solver.solve(u_host)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 112,
-           "d2h_bytes_per_step": 8 + 8 * n + 4 * 16}
-
-    kernels_per_solve = solver.kernel_count()
-    gpu_launches = args.steps * (kernels_per_solve)
-    sm_max = clk.get("sm_max_mhz") or 2070
-    peak_tflops = FP64_FLOP_PER_CLK_SM * N_SM * sm_max * 1e6 / 1e12
-    roof = {}
-    for name in ("moments", "jacobi"):
-        ms = prof.get(name, -1.0)
-        if ms and ms > 0:
-            units = n
-            ach = FLOPS_PER_UNIT[name] * units / (ms * 1e-3) / 1e12
-            roof[name] = {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
-                          "frac": ach / peak_tflops, "traffic": None, "launch_ms": ms,
-                          "hbm_gbs": BYTES_PER_UNIT[name] * units / (ms * 1e-3) / 1e9}
-    roofline = dict(roof.get(DOMINANT, {}))
-    roofline["kernel"] = DOMINANT
-    roofline["peak_source"] = "FP64: 152 SMs x 2 DFMA/clk x sm_max_mhz (nominal 1.25 TFLOP/s)"
-
+    m = measure(args.workload, args.steps, args.warmup, world, local, dist)
+    main, other = roofline(m, m["clocks"])
+    step_ms = m["step_ms"]
     line = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dofs": n, "parallelism": "replicas",
-                   "l2": "per-step working set ~2.3 GB >> 129 MB L2; no flush"},
-        "mdof_per_s": value * n / 1e6,
+        "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if m["mixed"] else "f64", "data": "synthetic",
+        "config": {"workload": m["desc"], "dofs": m["dofs"], "parallelism": "replicas",
+                   "l2": "per-step working set > 2 GB >> 129 MB L2; no flush"},
+        "mdof_per_s": m["value"] * m["dofs"] / 1e6,
         "latency_ms": {"p50": statistics.median(step_ms),
                        "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
-        "lambda": lam, "lambda_e2e": lam_e2e,
-        "clocks": clk, "e2e": e2e, "gpu_launches": gpu_launches,
-        "kernels_per_step": kernels_per_solve, "roofline": roofline,
-        "kernel_ms_finest": prof, "roofline_other": {k: v for k, v in roof.items() if k != DOMINANT},
+        "lambda": m["lambda"], "lambda_e2e": m["lambda_e2e"],
+        "clocks": m["clocks"], "e2e": m["e2e"], "gpu_launches": args.steps * m["kernels"],
+        "kernels_per_step": m["kernels"], "roofline": main, "roofline_other": other,
+        "kernel_ms_finest": m["profile"],
     }
+    if args.workload == "config2" and not args.no_extras:
+        mx = measure("config2-mixed", max(3, args.steps // 2), 3, world, local, dist,
+                     with_e2e=False, clocks=False)
+        line["mixed_fp32"] = {"value": mx["value"], "unit": "solves/s", "ms_per_step": mx["ms_per_step"],
+                              "lambda": mx["lambda"],
+                              "dlambda_rel_vs_fp64": abs(mx["lambda"] - m["lambda"]) / m["lambda"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = run_oracle(7, 1)
-        scale = full_dofs() / r["dofs"]
+        config = WORKLOADS[args.workload][0]
+        levels = ORACLE_SAMPLE[config][0]
+        r = run_oracle(config, levels, 1)
+        full = dofs_of(problem_kwargs(config))
+        scale = full / r["dofs"]
         t = r["times"][0]
         line["cpu_baseline"] = {
             "value": 1.0 / (t * scale), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one oracle solve of the same discretisation truncated to 7 levels (h=1/512, "
-                       f"{r['dofs']} dofs) took {t:.1f} s on 1 host core; scaled x{scale:.1f} to "
-                       f"16,769,025 dofs by the method's linear work (Theorem 3.3)"),
+            "sample": (f"one oracle solve of the same discretisation truncated to {levels} levels "
+                       f"({r['dofs']} dofs) took {t:.1f} s on 1 host core; scaled x{scale:.1f} to "
+                       f"{full} dofs by the method's linear work (Theorem 3.3)"),
             "lambda_sample": r["lam"],
         }
-    solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -279,10 +327,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         reference_arm(args)
     else:

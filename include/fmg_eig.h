@@ -120,9 +120,10 @@ int fmg_eig_set_params(fmg_eig_handle* h, const fmg_eig_problem* prob);
 /* Instrumentation (no counterpart in the paper).  fmg_eig_kernel_count: kernel launches
  * per solve (nodes of the solve's CUDA graph).  fmg_eig_profile: device time in ms of the
  * finest-level launch of each step in the most recent solve, in the order
- * [Jacobi sweep, residual, restriction, prolongation, auxiliary RHS, moments, augmented
- * nonlinear solve, one whole V-cycle]; writes min(count, 8) entries and returns that number
- * (FMG_EINVAL for bad arguments).  Synchronises the handle's stream.                       */
+ * [Jacobi sweep, residual, restriction, prolongation, auxiliary RHS, cubic load + density
+ * stencil of u~, augmented nonlinear solve, one whole V-cycle, T3 moments, operator setup];
+ * writes min(count, 10) entries and returns that number (FMG_EINVAL for bad arguments).
+ * Entries a solve does not contain read -1.  Synchronises the handle's stream.             */
 int fmg_eig_kernel_count(const fmg_eig_handle* h);
 int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count);
 

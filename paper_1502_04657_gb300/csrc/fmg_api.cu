@@ -21,6 +21,10 @@ struct Level {
          *y = nullptr, *z = nullptr;
   Density2D b{};          // density stencil of u~ (augmented pass), 2D
   Density3D b3{};         // same, 3D
+  // mixed precision: FP32 copies of the coefficients and FP32 V-cycle vectors
+  CoefF2D cf{};
+  CoefF3D cf3{};
+  float *x32 = nullptr, *xt32 = nullptr, *f32 = nullptr, *r32 = nullptr;
   double* pw = nullptr;   // (x / r)^m table for the 2D T3 sums (levels >= 2)
   double* t3map = nullptr;  // class sums -> T3 map of this level (levels >= 2)
 };
@@ -94,7 +98,7 @@ void lv_gather_level1(Level& l1, double* gA, double* gM, double* t1, double* B1,
 }
 
 enum ProfId { kProfJacobi, kProfResidual, kProfRestrict, kProfProlong, kProfRhs,
-              kProfMoments, kProfDense, kProfVcycle, kProfCount };
+              kProfMoments, kProfDense, kProfVcycle, kProfT3, kProfCoef, kProfCount };
 
 double factorial(int k) {
   double r = 1.0;
@@ -180,7 +184,9 @@ int validate(const fmg_eig_problem* p) {
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
   if (p->smoother != FMG_SMOOTH_JACOBI) return FMG_ENOTSUP;
-  if (p->precision != FMG_FP64 || p->operator_form != FMG_W_LEFT) return FMG_ENOTSUP;
+  if ((p->precision != FMG_FP64 && p->precision != FMG_MIXED_FP32) ||
+      p->operator_form != FMG_W_LEFT)
+    return FMG_ENOTSUP;
   return FMG_OK;
 }
 
@@ -225,6 +231,22 @@ void build_levels(fmg_eig_handle* h) {
       l.c3.dinv = h->alloc<double>(s);
       l.c3.tab = h->alloc<double>(15 * (size_t)(l.g.n + 1));
       for (int q = 0; q < 8; ++q) l.b3.a[q] = h->alloc<double>(s);
+    }
+    if (p.precision == FMG_MIXED_FP32) {
+      if (dim == 2) {
+        l.cf.cC = h->alloc<float>(s);
+        l.cf.cE = h->alloc<float>(s);
+        l.cf.cN = h->alloc<float>(s);
+        l.cf.cNE = h->alloc<float>(s);
+        l.cf.dinv = h->alloc<float>(s);
+      } else {
+        for (int q = 0; q < 8; ++q) l.cf3.a[q] = h->alloc<float>(s);
+        l.cf3.dinv = h->alloc<float>(s);
+      }
+      l.x32 = h->alloc<float>(s);
+      l.xt32 = h->alloc<float>(s);
+      l.f32 = h->alloc<float>(s);
+      l.r32 = h->alloc<float>(s);
     }
     l.x = h->alloc<double>(s);
     l.xt = h->alloc<double>(s);
@@ -374,7 +396,25 @@ void prof_end(fmg_eig_handle* h, int id, int level, cudaStream_t s) {
 }
 
 void enqueue_setup(fmg_eig_handle* h, cudaStream_t s) {
-  for (int k = 1; k <= h->levels(); ++k) lv_coef(h->L(k), h->dparams, s);
+  for (int k = 1; k <= h->levels(); ++k) {
+    Level& l = h->L(k);
+    prof_begin(h, kProfCoef, k, s);
+    lv_coef(l, h->dparams, s);
+    prof_end(h, kProfCoef, k, s);
+    if (h->prob.precision == FMG_MIXED_FP32) {
+      const size_t n = l.g.stride;
+      if (l.g.dim == 2) {
+        to_f32(l.c.cC, l.cf.cC, n, s);
+        to_f32(l.c.cE, l.cf.cE, n, s);
+        to_f32(l.c.cN, l.cf.cN, n, s);
+        to_f32(l.c.cNE, l.cf.cNE, n, s);
+        to_f32(l.c.dinv, l.cf.dinv, n, s);
+      } else {
+        for (int q = 0; q < 8; ++q) to_f32(l.c3.a[q], l.cf3.a[q], n, s);
+        to_f32(l.c3.dinv, l.cf3.dinv, n, s);
+      }
+    }
+  }
   lv_dense_level1(h->L(1), h->L1, h->M1, s);
   dense_spd_inverse(h->L1, h->L1inv, h->nh, s);
 }
@@ -450,7 +490,45 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   prof_end(h, kProfVcycle, j, s);
 }
 
+// One FP32 V-cycle on level j for L_j e = r (e, r in L(j).x32, L(j).f32), e starting at 0.
+void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
+  Level& l = h->L(j);
+  if (j == 1) {
+    coarse32(l.g, h->L1inv, l.f32, l.x32, s);
+    return;
+  }
+  const fmg_eig_problem& p = h->prob;
+  bool zero = true;
+  for (int it = 0; it < p.nu_pre; ++it) {
+    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, zero, s);
+    std::swap(l.x32, l.xt32);
+    zero = false;
+  }
+  if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * sizeof(float), s);
+  Level& lc = h->L(j - 1);
+  residual32(l.g, l.cf, l.cf3, l.f32, l.x32, l.r32, s);
+  restrict32(l.g, lc.g, l.r32, lc.f32, s);
+  enqueue_vcycle32(h, j - 1, s);
+  prolong32_add(l.g, lc.g, lc.x32, l.x32, s);
+  for (int it = 0; it < p.nu_post; ++it) {
+    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s);
+    std::swap(l.x32, l.xt32);
+  }
+}
+
 void enqueue_multigrid(fmg_eig_handle* h, int k, cudaStream_t s) {
+  if (h->prob.precision == FMG_MIXED_FP32) {
+    // FP64 defect correction around FP32 V-cycles
+    Level& l = h->L(k);
+    for (int it = 0; it < h->prob.vcycles; ++it) {
+      prof_begin(h, kProfVcycle, k, s);
+      residual_mixed(l.g, l.c, l.c3, l.f, l.x, l.f32, s);
+      enqueue_vcycle32(h, k, s);
+      add_f32(l.x32, l.x, l.g.stride, s);
+      prof_end(h, kProfVcycle, k, s);
+    }
+    return;
+  }
   for (int it = 0; it < h->prob.vcycles; ++it) enqueue_vcycle(h, k, false, s);
 }
 
@@ -466,8 +544,10 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
   dot(ut, l.z, l.g.stride, h->partials, h->buu, s);
   prof_begin(h, kProfMoments, k, s);
   lv_nload_density(l, ut, l.r, s);
-  lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, s);
   prof_end(h, kProfMoments, k, s);
+  prof_begin(h, kProfT3, k, s);
+  lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, s);
+  prof_end(h, kProfT3, k, s);
   dot(ut, l.r, l.g.stride, h->partials, h->t0, s);
   for (int j = k; j >= 2; --j) {
     Level& f = h->L(j);

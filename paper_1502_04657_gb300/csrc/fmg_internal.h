@@ -115,6 +115,29 @@ void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
                   double* partials, double* t3, cudaStream_t s);
 void t3_map3d(int r, double* out);  // 20 * 15 * 20 doubles
 
+// ---- Mixed precision (mixed.cu) ------------------------------------------------------------
+struct CoefF2D {
+  float *cC, *cE, *cN, *cNE, *dinv;
+};
+struct CoefF3D {
+  float* a[8];
+  float* dinv;
+};
+void to_f32(const double* a, float* b, size_t n, cudaStream_t s);
+void add_f32(const float* e, double* x, size_t n, cudaStream_t s);  // x += e (all entries)
+// r = (float)(f - L x) with the FP64 operator of the level (2D uses c2, 3D c3)
+void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const double* f,
+                    const double* x, float* r, cudaStream_t s);
+void jacobi32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
+              const float* x, float* xo, bool zero, cudaStream_t s);
+void residual32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
+                const float* x, float* r, cudaStream_t s);
+void restrict32(const Grid& fine, const Grid& coarse, const float* rf, float* rc,
+                cudaStream_t s);
+void prolong32_add(const Grid& fine, const Grid& coarse, const float* ec, float* xf,
+                   cudaStream_t s);
+void coarse32(const Grid& g, const double* Linv, const float* x, float* y, cudaStream_t s);
+
 // ---- Reductions (reduce.cu) -------------------------------------------------------------
 // out[0] = sum_i a[i] * b[i] over n entries; deterministic two-stage tree.  `partials` holds
 // at least kReduceBlocks doubles.

@@ -188,7 +188,8 @@ class Solver:
     def level_size(self, k: int) -> int:
         return self.lib.fmg_eig_level_size(self.h, k)
 
-    PROFILE_KEYS = ("jacobi", "residual", "restrict", "prolong", "rhs", "moments", "dense", "vcycle")
+    PROFILE_KEYS = ("jacobi", "residual", "restrict", "prolong", "rhs", "nload_density", "dense",
+                    "vcycle", "t3", "coef")
 
     def set_params(self, problem: Problem):
         cp = problem.to_c()
@@ -199,8 +200,8 @@ class Solver:
         return self.lib.fmg_eig_kernel_count(self.h)
 
     def profile(self) -> dict:
-        buf = (C.c_double * 8)()
-        n = self.lib.fmg_eig_profile(self.h, buf, 8)
+        buf = (C.c_double * 10)()
+        n = self.lib.fmg_eig_profile(self.h, buf, 10)
         if n < 0:
             raise FmgError(n, "profile")
         return {k: buf[i] for i, k in enumerate(self.PROFILE_KEYS[:n])}

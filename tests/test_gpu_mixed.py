@@ -1,0 +1,62 @@
+"""Mixed precision (FP32 V-cycles inside the FP64 defect correction) against the FP64 solve
+and the FP64 oracle.  The accuracy target is the benchmark's |delta lambda| <= 1e-8, read
+relative to lambda, against the FP64 result; the eigenvector is compared in relative L2 norm."""
+import numpy as np
+import pytest
+
+from oracle import fmg_oracle as O
+from tests.test_gpu_parity import _fmg, _pair
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DLAM = 1e-8
+U_MIXED = 1e-6
+
+CASES = [
+    dict(dim=2, coarse_cells=8, levels=5, w_quad=(1.0, 1.0, 0.0), zeta=10.0),
+    dict(dim=2, coarse_cells=8, levels=4, w_quad=(1.0, 9.0, 0.0), zeta=150.0),
+    dict(dim=3, coarse_cells=4, levels=3, w_quad=(100.0, 100.0, 400.0), zeta=100.0),
+    dict(dim=3, coarse_cells=2, levels=4, w_quad=(1.0, 1.0, 1.0), zeta=1.0),
+]
+
+
+@pytest.mark.parametrize("kw", CASES, ids=[f"case{i}" for i in range(len(CASES))])
+def test_mixed_matches_fp64_and_oracle(kw):
+    fmg = _fmg()
+    op, gp = _pair(**kw)
+    n = gp.size(gp.levels)
+    with fmg.Solver(gp) as s:
+        u64 = np.empty(n)
+        lam64, _, rc = s.solve(u64)
+    assert rc == 0
+    gp.precision = fmg.FMG_MIXED_FP32
+    with fmg.Solver(gp) as s:
+        u32 = np.empty(n)
+        lam32, st, rc = s.solve(u32, stats=True)
+    assert rc == 0
+    assert abs(lam32 - lam64) <= DLAM * lam64
+    assert np.linalg.norm(u32 - u64) <= U_MIXED * np.linalg.norm(u64)
+    ref = O.fmg_solve(op)
+    assert abs(lam32 - ref.lam) <= DLAM * ref.lam
+    assert abs(st.identity_defect) < 1e-10 * lam32
+
+
+def test_mixed_multigrid_converges_like_fp64():
+    """The defect correction keeps the FP64 fixed point: repeated mixed multigrid calls drive
+    the FP64 residual of L x = f to the FP64 rounding level."""
+    fmg = _fmg()
+    op, gp = _pair(dim=2, coarse_cells=4, levels=5, w_quad=(1.0, 2.0, 0.0), zeta=3.0)
+    lv = O.build_hierarchy(op)
+    gp.precision = fmg.FMG_MIXED_FP32
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=gp.size(5))
+    x = torch.zeros(gp.size(5), dtype=torch.float64, device="cuda")
+    with fmg.Solver(gp) as s:
+        fd = torch.from_numpy(f).cuda()
+        for _ in range(12):
+            s.multigrid(5, fd, x)
+        torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    r = f - lv[-1].L @ xh
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(f)
