@@ -49,6 +49,9 @@ extern "C" {
 #define FMG_MIXED_FP32 1
 #define FMG_W_LEFT 0        /* (A + W) u^ = lambda M u - N(u)              */
 #define FMG_PAPER_LITERAL 1 /*  A u^      = lambda M u - W u - N(u)        */
+/* flags: keep the default 32 x 8 thread blocks instead of timing the candidate block shapes
+ * of every level when the handle is created (results do not depend on the shapes).        */
+#define FMG_FLAG_NO_AUTOTUNE 1
 
 /* Problem and method parameters.  Example 4.1 fixes the PDE; Algorithm 3.1 fixes m (vcycles)
  * and Algorithm 3.2 fixes p (corrections) and the level count n.                            */
@@ -64,7 +67,7 @@ typedef struct fmg_eig_problem {
   int32_t precision;    /* FMG_FP64 | FMG_MIXED_FP32                                       */
   int32_t operator_form;/* FMG_W_LEFT | FMG_PAPER_LITERAL                                  */
   int32_t scf_max_iter; /* cap on nonlinear iterations per small solve (e.g. 100)          */
-  int32_t reserved;
+  int32_t flags;        /* FMG_FLAG_* bits (0 = defaults)                                  */
   double box_len;       /* L > 0                                                           */
   double w_const;       /* W(x) = w_const + sum_d w_quad[d] x_d^2                          */
   double w_quad[3];
@@ -129,6 +132,40 @@ int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count);
 
 /* Static description of a return code.                                                    */
 const char* fmg_eig_strerror(int code);
+
+/* ------------------------------------------------------------------------------------------
+ * Batches: many independent instances of Example 4.1 solved together (no counterpart in the
+ * paper, whose algorithms solve one problem).  The instances may differ in the level count
+ * (mesh size), w_const, w_quad, zeta and omega; every other field must be equal (FMG_EINVAL
+ * otherwise).  Every step of Algorithm 3.2 on level k runs as one launch over all instances
+ * that have a level k, and the whole batch is one CUDA graph.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Create a batch handle for probs[0 .. count-1] (count >= 1).  Errors as fmg_eig_create,
+ * plus FMG_ENOTSUP when a 3D level holds more instances than one launch can address.       */
+int fmg_eig_batch_create(const fmg_eig_problem* probs, int32_t count, fmg_eig_handle** out);
+
+/* Instances of a handle (1 for fmg_eig_create).                                           */
+int32_t fmg_eig_batch_count(const fmg_eig_handle* h);
+
+/* Solve every instance of a batch handle.  lambdas: count doubles (host).  u_hosts
+ * (nullable): count host pointers, each NULL or a buffer of u_lens[i] doubles, u_lens[i]
+ * equal to instance i's finest level size.  stats (nullable): count records; statuses
+ * (nullable): count codes.  Returns FMG_OK when every instance converged, FMG_ENOCONV when
+ * some did not (their partial results are written), or an error code.  Synchronous.      */
+int fmg_eig_batch_solve(fmg_eig_handle* h, double* lambdas, double* const* u_hosts,
+                        const size_t* u_lens, fmg_eig_stats* stats, int32_t* statuses);
+
+/* One-shot batch: groups probs by the fields that must agree, creates one batch handle per
+ * group, runs the groups concurrently on their own streams, writes the outputs as
+ * fmg_eig_batch_solve does (in the caller's order) and releases everything.              */
+int fmg_eig_solve_batch(const fmg_eig_problem* probs, int32_t count, double* lambdas,
+                        double* const* u_hosts, const size_t* u_lens, fmg_eig_stats* stats,
+                        int32_t* statuses);
+
+/* Thread-block shape (x, y threads) the handle uses for the stencil kernels of level k,
+ * as chosen by the autotuner when the handle was created.                                 */
+int fmg_eig_level_tile(const fmg_eig_handle* h, int32_t level, int32_t* bx, int32_t* by);
 
 /* ------------------------------------------------------------------------------------------
  * Component entry points: the steps of the hot path, one call each, on device vectors in the

@@ -21,9 +21,6 @@
 namespace fmg {
 namespace {
 
-constexpr int BX = 32;
-constexpr int BY = 8;
-
 __device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j * pitch + i; }
 
 // N(u)_p and the density stencil B(u) at p (coupling to p, E, N, NE).  Star triangles of p
@@ -31,14 +28,14 @@ __device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j
 // (p, q, r) of area |K|:
 //   int u^2 lambda_p^2       = |K|/90  [6u_p^2 + u_q^2 + u_r^2 + 3u_p u_q + 3u_p u_r + u_q u_r]
 //   int u^2 lambda_p lambda_q = |K|/180 [3u_p^2 + 3u_q^2 + u_r^2 + 4u_p u_q + 2u_p u_r + 2u_q u_r]
-__global__ void k_nload_density2d(int n, int pitch, double area, const double* __restrict__ u,
-                                  double* __restrict__ nl, double* __restrict__ bC,
-                                  double* __restrict__ bE, double* __restrict__ bN,
-                                  double* __restrict__ bNE) {
-  const int i = 1 + blockIdx.x * BX + threadIdx.x;
-  const int j = 1 + blockIdx.y * BY + threadIdx.y;
+__global__ void k_nload_density2d(int n, int pitch, size_t st, double area,
+                                  const double* __restrict__ u, double* __restrict__ nl,
+                                  double* __restrict__ bC, double* __restrict__ bE,
+                                  double* __restrict__ bN, double* __restrict__ bNE) {
+  const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
-  const size_t k = at(i, j, pitch);
+  const size_t k = blockIdx.z * st + at(i, j, pitch);
   const double up = u[k];
   const double nE = u[k + 1], nNE = u[k + pitch + 1], nN = u[k + pitch];
   const double nW = u[k - 1], nSW = u[k - pitch - 1], nS = u[k - pitch];
@@ -123,17 +120,18 @@ __device__ __forceinline__ double coarse_entry(const double* bC, const double* b
   return acc;
 }
 
-__global__ void k_coarsen_density2d(int nc, int pc, int pf, const double* __restrict__ fC,
+__global__ void k_coarsen_density2d(int nc, int pc, int pf, size_t stc, size_t stf,
+                                    const double* __restrict__ fC,
                                     const double* __restrict__ fE,
                                     const double* __restrict__ fN,
                                     const double* __restrict__ fNE, double* __restrict__ cC,
                                     double* __restrict__ cE, double* __restrict__ cN,
                                     double* __restrict__ cNE) {
-  const int I = 1 + blockIdx.x * BX + threadIdx.x;
-  const int J = 1 + blockIdx.y * BY + threadIdx.y;
+  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nc || J >= nc) return;
-  const size_t kf = at(2 * I, 2 * J, pf);
-  const size_t kc = at(I, J, pc);
+  const size_t kf = blockIdx.z * stf + at(2 * I, 2 * J, pf);
+  const size_t kc = blockIdx.z * stc + at(I, J, pc);
   cC[kc] = coarse_entry<0, 0>(fC, fE, fN, fNE, kf, pf);
   // couplings to coarse neighbours outside the interior are never read; skip them so no
   // fine entry beyond the interior is touched
@@ -171,6 +169,7 @@ template <int T>
 __device__ void t3_sums_body(int pf, int n1, int r, const double* __restrict__ u,
                              const double* __restrict__ pw, double* __restrict__ partials,
                              int col_blocks) {
+  // instance blockIdx.z: u and partials arrive offset to it
   __shared__ double sh[kSumThreads];
   const int tri = blockIdx.y;
   const int cell = tri >> 1;
@@ -262,8 +261,10 @@ __device__ void t3_sums_body(int pf, int n1, int r, const double* __restrict__ u
 }
 
 __global__ void __launch_bounds__(kSumThreads)
-    k_t3_sums2d(int pf, int n1, int r, const double* __restrict__ u,
+    k_t3_sums2d(int pf, int n1, int r, size_t st, size_t pst, const double* __restrict__ u,
                 const double* __restrict__ pw, double* __restrict__ partials, int col_blocks) {
+  u += blockIdx.z * st;
+  partials += blockIdx.z * pst;
   if (blockIdx.y & 1)
     t3_sums_body<1>(pf, n1, r, u, pw, partials, col_blocks);
   else
@@ -272,8 +273,11 @@ __global__ void __launch_bounds__(kSumThreads)
 
 // Finalise: T3^T_e = h^2 sum_m map[T][e][m] S_m, a fixed linear map of the 25 class sums per
 // triangle type, built on the host for the level's r (t3_map2d).
-__global__ void k_t3_finalize2d(int chunks, double h2, const double* __restrict__ partials,
+__global__ void k_t3_finalize2d(int chunks, double h2, size_t pst, size_t tst,
+                                const double* __restrict__ partials,
                                 const double* __restrict__ map, double* __restrict__ t3) {
+  partials += blockIdx.y * pst;
+  t3 += blockIdx.y * tst;
   const int tri = blockIdx.x;
   const int T = tri & 1;
   __shared__ double sums[kSums];
@@ -291,7 +295,7 @@ __global__ void k_t3_finalize2d(int chunks, double h2, const double* __restrict_
   t3[(size_t)tri * 10 + e] = h2 * acc;
 }
 
-__global__ void k_gather_level1_2d(int n, int pitch, const double* __restrict__ gA_pad,
+__global__ void k_gather_level1_2d(int n, int pitch, size_t st, const double* __restrict__ gA_pad,
                                    const double* __restrict__ gM_pad,
                                    const double* __restrict__ t1_pad, Density2D b,
                                    double* __restrict__ gA, double* __restrict__ gM,
@@ -300,11 +304,13 @@ __global__ void k_gather_level1_2d(int n, int pitch, const double* __restrict__ 
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m * m) return;
   const int i = 1 + p % m, j = 1 + p / m;
-  const size_t k = at(i, j, pitch);
-  gA[p] = gA_pad[k];
-  gM[p] = gM_pad[k];
-  t1[p] = t1_pad[k];
-  double* row = B1 + (size_t)p * m * m;
+  const size_t nh = (size_t)m * m;
+  const size_t k = blockIdx.y * st + at(i, j, pitch);
+  const size_t q = blockIdx.y * nh + p;
+  gA[q] = gA_pad[k];
+  gM[q] = gM_pad[k];
+  t1[q] = t1_pad[k];
+  double* row = B1 + blockIdx.y * nh * nh + (size_t)p * nh;
   for (int q = 0; q < m * m; ++q) row[q] = 0.0;
   row[p] = b.C[k];
   auto put = [&](int di, int dj, double v) {
@@ -323,28 +329,31 @@ __global__ void k_gather_level1_2d(int n, int pitch, const double* __restrict__ 
 int t3_col_blocks(int r) { return (r + 1 + kSumThreads - 1) / kSumThreads; }
 int t3_row_blocks(int r) { return (r + 1 + kSumRows - 1) / kSumRows; }
 
-dim3 grid_of(int cx, int cy) { return dim3((cx + BX - 1) / BX, (cy + BY - 1) / BY); }
+dim3 grid_of(const Grid& g, int cx, int cy) {
+  return dim3((cx + g.bx - 1) / g.bx, (cy + g.by - 1) / g.by, g.nb);
+}
 
 }  // namespace
 
 void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D& b,
                      cudaStream_t s) {
-  k_nload_density2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(
-      g.n, g.pitch, g.h * g.h / 2.0, u, nl, b.C, b.E, b.N, b.NE);
+  k_nload_density2d<<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
+      g.n, g.pitch, g.stride, g.h * g.h / 2.0, u, nl, b.C, b.E, b.N, b.NE);
 }
 
 void coarsen_density2d(const Grid& fine, const Grid& coarse, const Density2D& bf,
                        const Density2D& bc, cudaStream_t s) {
-  k_coarsen_density2d<<<grid_of(coarse.n - 1, coarse.n - 1), dim3(BX, BY), 0, s>>>(
-      coarse.n, coarse.pitch, fine.pitch, bf.C, bf.E, bf.N, bf.NE, bc.C, bc.E, bc.N, bc.NE);
+  k_coarsen_density2d<<<grid_of(fine, coarse.n - 1, coarse.n - 1), dim3(fine.bx, fine.by), 0,
+                        s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride,
+                             bf.C, bf.E, bf.N, bf.NE, bc.C, bc.E, bc.N, bc.NE);
 }
 
 void gather_level1_2d(const Grid& g1, const double* gA_pad, const double* gM_pad,
                       const double* t1_pad, const Density2D& b1, double* gA, double* gM,
                       double* t1, double* B1, cudaStream_t s) {
   const int m = g1.n - 1;
-  k_gather_level1_2d<<<(m * m + 63) / 64, 64, 0, s>>>(g1.n, g1.pitch, gA_pad, gM_pad, t1_pad, b1,
-                                                      gA, gM, t1, B1);
+  k_gather_level1_2d<<<dim3((m * m + 63) / 64, g1.nb), 64, 0, s>>>(
+      g1.n, g1.pitch, g1.stride, gA_pad, gM_pad, t1_pad, b1, gA, gM, t1, B1);
 }
 
 size_t t3_partials2d(const Grid& fine, int n1) {
@@ -356,9 +365,11 @@ void t3_moments2d(const Grid& fine, int n1, const double* u, const double* pw,
                   const double* map, double* partials, double* t3, cudaStream_t s) {
   const int r = fine.n / n1;
   const int cb = t3_col_blocks(r), rb = t3_row_blocks(r);
-  dim3 grid(cb * rb, 2 * n1 * n1);
-  k_t3_sums2d<<<grid, kSumThreads, 0, s>>>(fine.pitch, n1, r, u, pw, partials, cb);
-  k_t3_finalize2d<<<2 * n1 * n1, 32, 0, s>>>(cb * rb, fine.h * fine.h, partials, map, t3);
+  const size_t pst = t3_partials2d(fine, n1);
+  k_t3_sums2d<<<dim3(cb * rb, 2 * n1 * n1, fine.nb), kSumThreads, 0, s>>>(
+      fine.pitch, n1, r, fine.stride, pst, u, pw, partials, cb);
+  k_t3_finalize2d<<<dim3(2 * n1 * n1, fine.nb), 32, 0, s>>>(
+      cb * rb, fine.h * fine.h, pst, (size_t)2 * n1 * n1 * 10, partials, map, t3);
 }
 
 // Host: moments m_ij = int_K lambda_v (ds)^i (dt)^j over each star triangle of a node (fine

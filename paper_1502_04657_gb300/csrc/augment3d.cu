@@ -52,9 +52,11 @@ __device__ void block_reduce(double* acc, int count, double* sh, double* out) {
 
 // Interior class: block (chunk, tet); nodes of the coarse cell in flat order.
 __global__ void __launch_bounds__(kThreads)
-    k_t3_interior3d(int pf, long planef, int n1, int r, const double* __restrict__ u,
-                    double* __restrict__ partials) {
+    k_t3_interior3d(int pf, long planef, int n1, int r, size_t st, size_t pst,
+                    const double* __restrict__ u, double* __restrict__ partials) {
   __shared__ double sh[kThreads];
+  u += blockIdx.z * st;  // instance blockIdx.z
+  partials += blockIdx.z * pst;
   const int tet = blockIdx.y;
   const int cell = tet / 6, s = tet % 6;
   const int I = cell % n1, J = (cell / n1) % n1, L = cell / (n1 * n1);
@@ -103,9 +105,11 @@ __device__ __forceinline__ bool class_node(int cls, int r, int p, int q, int* ab
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_t3_boundary3d(int pf, long planef, int n1, int r, const double* __restrict__ u,
-                    double* __restrict__ partials) {
+    k_t3_boundary3d(int pf, long planef, int n1, int r, size_t st, size_t pst,
+                    const double* __restrict__ u, double* __restrict__ partials) {
   __shared__ double sh[kThreads];
+  u += blockIdx.z * st;  // instance blockIdx.z
+  partials += blockIdx.z * pst;
   const int cls = 1 + blockIdx.x;
   const int tet = blockIdx.y;
   const int cell = tet / 6, s = tet % 6;
@@ -135,9 +139,12 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // T3_e = h^3 sum_{class, g} map[e][class][g] S^class_g
-__global__ void k_t3_finalize3d(int chunks, double h3, const double* __restrict__ pin,
-                                const double* __restrict__ pbd, const double* __restrict__ map,
-                                double* __restrict__ t3) {
+__global__ void k_t3_finalize3d(int chunks, double h3, size_t pst, size_t tst,
+                                const double* __restrict__ pin, const double* __restrict__ pbd,
+                                const double* __restrict__ map, double* __restrict__ t3) {
+  pin += blockIdx.y * pst;  // instance blockIdx.y
+  pbd += blockIdx.y * pst;
+  t3 += blockIdx.y * tst;
   const int tet = blockIdx.x;
   __shared__ double S[kClasses * kMono];
   for (int m = threadIdx.x; m < kMono; m += blockDim.x) {
@@ -280,11 +287,15 @@ void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
   const int tets = 6 * n1 * n1 * n1;
   const int chunks = interior_chunks(r);
   const long planef = (long)(fine.n + 1) * fine.pitch;
+  const size_t pst = t3_partials3d(fine, n1);  // per instance
   double* pin = partials;
   double* pbd = partials + (size_t)tets * chunks * kMono;
-  k_t3_interior3d<<<dim3(chunks, tets), kThreads, 0, s>>>(fine.pitch, planef, n1, r, u, pin);
-  k_t3_boundary3d<<<dim3(kClasses - 1, tets), kThreads, 0, s>>>(fine.pitch, planef, n1, r, u, pbd);
-  k_t3_finalize3d<<<tets, 32, 0, s>>>(chunks, fine.h * fine.h * fine.h, pin, pbd, map, t3);
+  k_t3_interior3d<<<dim3(chunks, tets, fine.nb), kThreads, 0, s>>>(fine.pitch, planef, n1, r,
+                                                                    fine.stride, pst, u, pin);
+  k_t3_boundary3d<<<dim3(kClasses - 1, tets, fine.nb), kThreads, 0, s>>>(
+      fine.pitch, planef, n1, r, fine.stride, pst, u, pbd);
+  k_t3_finalize3d<<<dim3(tets, fine.nb), 32, 0, s>>>(chunks, fine.h * fine.h * fine.h, pst,
+                                                     (size_t)tets * 20, pin, pbd, map, t3);
 }
 
 // Host: map[e][class][g] for T3_e = h^3 sum map S^class_g (r fine cells per coarse cell),

@@ -25,7 +25,7 @@
 //   G_uu = c_H^T B1 c_H + 2 c_u t1.c_H + c_u^2 T0
 // with w_c the coarse coefficients at T's vertices (0 on the boundary).
 //
-// One CTA of 512 threads per problem (enough warps to hide shared-memory and FP64 latency),
+// One CTA of 512 threads per problem, a batch of problems one CTA each (enough warps to hide shared-memory and FP64 latency),
 // everything in shared memory, fixed-order reductions, one barrier per elimination step and
 // warp-synchronous triangular solves.  The iteration count is bounded by max_iter; hitting it
 // sets status 1.
@@ -275,6 +275,27 @@ __device__ void normalise_and_sign(const DenseProblem& p, Smem& s) {
 
 __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   extern __shared__ double sm[];
+  if (blockIdx.x) {  // instance blockIdx.x of a batch: its slices of the per-instance arrays
+    const size_t b = blockIdx.x, nh = p.nh, cs = nh + 1;
+    p.L1 += b * nh * nh;
+    p.M1 += b * nh * nh;
+    p.params += b;
+    p.c_out += b * cs;
+    p.lam_out += b;
+    p.iters_out += b;
+    p.status_out += b;
+    if (p.c_init) p.c_init += b * cs;
+    if (p.aug) {
+      p.gA += b * nh;
+      p.gM += b * nh;
+      p.t1 += b * nh;
+      p.B1 += b * nh * nh;
+      p.t3 += b * (size_t)p.ntri * p.nt3;
+      p.auu += b;
+      p.buu += b;
+      p.t0 += b;
+    }
+  }
   __shared__ int sym3_tab[kMaxVert * kMaxVert * kMaxVert];
   Smem s;
   s.nh = p.nh;
@@ -430,6 +451,8 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
 // sequential, columns spread over the threads), everything in shared memory.
 __global__ void __launch_bounds__(kThreads) k_spd_inverse(const double* L, double* Linv, int n) {
   extern __shared__ double sm[];
+  L += blockIdx.x * (size_t)n * n;  // instance blockIdx.x
+  Linv += blockIdx.x * (size_t)n * n;
   double* A = sm;
   double* Y = A + n * n;
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
@@ -472,12 +495,15 @@ __device__ __forceinline__ size_t level1_index(int dim, int m, int pitch, int q)
   return ((size_t)(1 + q / (m * m)) * (m + 2) + 1 + (q / m) % m) * pitch + 1 + q % m;
 }
 
-__global__ void __launch_bounds__(kThreads) k_coarse_matvec(int dim, int n, int pitch,
+__global__ void __launch_bounds__(kThreads) k_coarse_matvec(int dim, int n, int pitch, size_t st,
                                                             const double* __restrict__ Linv,
                                                             const double* __restrict__ x,
                                                             double* __restrict__ y) {
   __shared__ double xs[1024];
   const int m = n - 1, nh = dim == 2 ? m * m : m * m * m;
+  Linv += blockIdx.x * (size_t)nh * nh;  // instance blockIdx.x
+  x += blockIdx.x * st;
+  y += blockIdx.x * st;
   for (int q = threadIdx.x; q < nh; q += kThreads) xs[q] = x[level1_index(dim, m, pitch, q)];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -502,9 +528,9 @@ size_t dense_smem_bytes(int n, int ntri, int nvert, int aug) {
                            ((size_t)nh * maxadj + 1) / 2 + (aug ? (size_t)nh * nh : 0));
 }
 
-void dense_scf(const DenseProblem& p, cudaStream_t s) {
+void dense_scf(const DenseProblem& p, int nb, cudaStream_t s) {
   const int n = p.nh + p.aug;
-  k_dense_scf<<<1, kThreads, dense_smem_bytes(n, p.ntri, p.nvert, p.aug), s>>>(p);
+  k_dense_scf<<<nb, kThreads, dense_smem_bytes(n, p.ntri, p.nvert, p.aug), s>>>(p);
 }
 
 // The attribute is per function, shared by every handle in the process, so it is always set
@@ -518,13 +544,13 @@ cudaError_t dense_prepare(size_t need) {
                               (int)kDenseSmemLimit);
 }
 
-void dense_spd_inverse(const double* L, double* Linv, int n, cudaStream_t s) {
-  k_spd_inverse<<<1, kThreads, sizeof(double) * (2 * (size_t)n * n), s>>>(L, Linv, n);
+void dense_spd_inverse(const double* L, double* Linv, int n, int nb, cudaStream_t s) {
+  k_spd_inverse<<<nb, kThreads, sizeof(double) * (2 * (size_t)n * n), s>>>(L, Linv, n);
 }
 
 void coarse_matvec(const Grid& g, const double* Linv, const double* x, double* y,
                    cudaStream_t s) {
-  k_coarse_matvec<<<1, kThreads, 0, s>>>(g.dim, g.n, g.pitch, Linv, x, y);
+  k_coarse_matvec<<<g.nb, kThreads, 0, s>>>(g.dim, g.n, g.pitch, g.stride, Linv, x, y);
 }
 
 }  // namespace fmg

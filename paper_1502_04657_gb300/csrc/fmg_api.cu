@@ -1,10 +1,21 @@
 // C ABI of libfmg_eig: level hierarchy, the full multigrid scheme (Algorithm 3.2) as one
-// CUDA graph per handle, and the component entry points used to check each step.
+// CUDA graph per handle, batches of independent instances, and the component entry points
+// used to check each step.
+//
+// A handle holds a batch of nb instances (nb = 1 for fmg_eig_create) sorted by level count,
+// largest first.  Level k's arrays hold the cnt[k] instances that have a level k back to
+// back, so on the FMG stage of level k the active instances are 0 .. cnt[k] - 1 of every
+// array and each step of the stage is one launch over all of them (Grid::nb).
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <map>
+#include <mutex>
 #include <new>
+#include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "fmg_internal.h"
@@ -15,6 +26,7 @@ namespace {
 
 struct Level {
   Grid g;
+  int cap = 0;  // instances allocated (cnt[k])
   Coef2D c{};
   Coef3D c3{};
   double *x = nullptr, *xt = nullptr, *f = nullptr, *r = nullptr, *u = nullptr,
@@ -28,6 +40,29 @@ struct Level {
   double* pw = nullptr;   // (x / r)^m table for the 2D T3 sums (levels >= 2)
   double* t3map = nullptr;  // class sums -> T3 map of this level (levels >= 2)
 };
+
+// The same level restricted to instances first .. first + count - 1.
+Level view(const Level& l, int first, int count) {
+  Level v = l;
+  const size_t o = (size_t)first * l.g.stride;
+  auto adv = [o](auto*& p) {
+    if (p) p += o;
+  };
+  adv(v.c.cC); adv(v.c.cE); adv(v.c.cN); adv(v.c.cNE); adv(v.c.dinv);
+  for (int q = 0; q < 8; ++q) {
+    adv(v.c3.a[q]);
+    adv(v.b3.a[q]);
+    adv(v.cf3.a[q]);
+  }
+  adv(v.c3.dinv); adv(v.cf3.dinv);
+  adv(v.x); adv(v.xt); adv(v.f); adv(v.r); adv(v.u); adv(v.y); adv(v.z);
+  adv(v.b.C); adv(v.b.E); adv(v.b.N); adv(v.b.NE);
+  adv(v.cf.cC); adv(v.cf.cE); adv(v.cf.cN); adv(v.cf.cNE); adv(v.cf.dinv);
+  adv(v.x32); adv(v.xt32); adv(v.f32); adv(v.r32);
+  v.c.tab = v.c3.tab = nullptr;  // setup scratch is not sliced
+  v.g.nb = count;
+  return v;
+}
 
 // ---- dimension dispatch of the level kernels -----------------------------------------------
 void lv_coef(Level& l, const PotentialParams* p, cudaStream_t s) {
@@ -55,9 +90,9 @@ void lv_restrict(Level& fl, Level& cl, const double* rf, double* rc, cudaStream_
   else restrict3d(fl.g, cl.g, rf, rc, s);
 }
 void lv_prolong(Level& fl, Level& cl, const double* ec, double* xf, bool add, const double* extra,
-                const double* scale, cudaStream_t s) {
-  if (fl.g.dim == 2) prolong2d(fl.g, cl.g, ec, xf, add, extra, scale, s);
-  else prolong3d(fl.g, cl.g, ec, xf, add, extra, scale, s);
+                const double* scale, int scale_stride, cudaStream_t s) {
+  if (fl.g.dim == 2) prolong2d(fl.g, cl.g, ec, xf, add, extra, scale, scale_stride, s);
+  else prolong3d(fl.g, cl.g, ec, xf, add, extra, scale, scale_stride, s);
 }
 void lv_nload(Level& l, const double* u, double* out, cudaStream_t s) {
   if (l.g.dim == 2) nload2d(l.g, u, out, s);
@@ -84,9 +119,9 @@ void lv_dense_level1(Level& l1, double* L, double* M, cudaStream_t s) {
   if (l1.g.dim == 2) dense_level1_2d(l1.g, l1.c, L, M, s);
   else dense_level1_3d(l1.g, l1.c3, L, M, s);
 }
-void lv_start(Level& l1, double box_len, double* c, cudaStream_t s) {
-  if (l1.g.dim == 2) start_vector(l1.g, box_len, c, s);
-  else start_vector3d(l1.g, c, s);
+void lv_start(Level& l1, double* c, int cstride, cudaStream_t s) {
+  if (l1.g.dim == 2) start_vector(l1.g, c, cstride, s);
+  else start_vector3d(l1.g, c, cstride, s);
 }
 void lv_gather_level1(Level& l1, double* gA, double* gM, double* t1, double* B1, cudaStream_t s) {
   if (l1.g.dim == 2) {
@@ -109,23 +144,28 @@ double factorial(int k) {
 }  // namespace
 
 struct fmg_eig_handle {
-  fmg_eig_problem prob{};
+  fmg_eig_problem prob{};  // settings shared by the batch; levels = the largest instance's
+  int nb = 1;              // instances
+  std::vector<fmg_eig_problem> probs;  // per instance, sorted by level count (descending)
+  std::vector<int> order;              // order[b]: caller's index of sorted instance b
+  std::vector<int> cnt;                // cnt[k], k = 1..levels (+ cnt[levels + 1] = 0)
+  std::vector<size_t> uoff;            // offset of sorted instance b's output in uout
   int dev = 0;
   cudaStream_t stream = nullptr;
   std::vector<Level> lv;  // lv[0] = level 1
   std::vector<void*> allocs;
   int nh = 0, ntri = 0, nvert = 3, maxadj = 6;
   double tri_vol = 0.0;
+  // per-instance arrays (sorted order): L1, M1, L1inv nh*nh; c, cstart nh + 1; scalars 1
   double *L1 = nullptr, *M1 = nullptr, *L1inv = nullptr, *q4 = nullptr;
   int *tri = nullptr, *adj = nullptr;
-  double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr, *partials = nullptr,
-         *t3 = nullptr, *t3_partials = nullptr, *cls_mom = nullptr, *gAd = nullptr,
+  double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr,
+         *partials = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,
          *gMd = nullptr, *t1d = nullptr, *B1d = nullptr, *t0 = nullptr,
-         *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr,
-         *uout = nullptr;
-  int *iters = nullptr, *status = nullptr;
-  PotentialParams* dparams = nullptr;  // device copy read by the kernels
-  PotentialParams* hparams = nullptr;  // pinned host staging, uploaded at every solve
+         *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr, *uout = nullptr;
+  int *iters = nullptr, *status = nullptr;  // [level][instance]
+  PotentialParams* dparams = nullptr;  // device copy read by the kernels (nb)
+  PotentialParams* hparams = nullptr;  // pinned host staging, uploaded at every solve (nb)
   // profiling: event pairs around the first finest-level launch of each profiled step
   cudaEvent_t prof[kProfCount][2] = {};
   bool prof_armed[kProfCount] = {};
@@ -138,12 +178,12 @@ struct fmg_eig_handle {
   template <typename T>
   T* alloc(size_t count) {
     void* p = nullptr;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
       cudaGetLastError();
       throw std::bad_alloc();
     }
     allocs.push_back(p);
-    cudaMemset(p, 0, count * sizeof(T));
+    cudaMemset(p, 0, std::max<size_t>(count, 1) * sizeof(T));
     return static_cast<T*>(p);
   }
   ~fmg_eig_handle() {
@@ -160,6 +200,10 @@ struct fmg_eig_handle {
   }
   Level& L(int k) { return lv[k - 1]; }
   int levels() const { return prob.levels; }
+  // every level launches over `count` instances (the active prefix of the stage)
+  void activate(int count) {
+    for (Level& l : lv) l.g.nb = std::min(count, l.cap);
+  }
 };
 
 namespace {
@@ -181,6 +225,7 @@ int validate(const fmg_eig_problem* p) {
   if (!(p->box_len > 0.0) || !(p->zeta >= 0.0) || !(p->omega > 0.0 && p->omega <= 1.0))
     return FMG_EINVAL;
   if (!(p->scf_tol > 0.0) || p->scf_max_iter < 1) return FMG_EINVAL;
+  if (p->flags & ~FMG_FLAG_NO_AUTOTUNE) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
   if (p->smoother != FMG_SMOOTH_JACOBI) return FMG_ENOTSUP;
@@ -188,6 +233,13 @@ int validate(const fmg_eig_problem* p) {
       p->operator_form != FMG_W_LEFT)
     return FMG_ENOTSUP;
   return FMG_OK;
+}
+
+// the fields every instance of a batch shares (all but levels and the PDE coefficients)
+auto shared_key(const fmg_eig_problem& p) {
+  return std::make_tuple(p.dim, p.coarse_cells, p.nu_pre, p.nu_post, p.vcycles, p.corrections,
+                         p.smoother, p.precision, p.operator_form, p.scf_max_iter, p.flags,
+                         p.box_len, p.scf_tol);
 }
 
 PotentialParams potential(const fmg_eig_problem& p) {
@@ -208,20 +260,22 @@ void build_levels(fmg_eig_handle* h) {
   h->lv.resize(p.levels);
   for (int k = 1; k <= p.levels; ++k) {
     Level& l = h->L(k);
+    l.cap = h->cnt[k];
     l.g.dim = dim;
     l.g.n = p.coarse_cells << (k - 1);
     l.g.rows = l.g.n + 1;
     l.g.pitch = (l.g.n + 1 + 31) / 32 * 32;
     l.g.stride = (size_t)l.g.rows * l.g.pitch * (dim == 3 ? (size_t)l.g.rows : 1);
     l.g.h = p.box_len / l.g.n;
-    const size_t s = l.g.stride;
+    l.g.nb = l.cap;
+    const size_t s = l.g.stride * l.cap;
     if (dim == 2) {
       l.c.cC = h->alloc<double>(s);
       l.c.cE = h->alloc<double>(s);
       l.c.cN = h->alloc<double>(s);
       l.c.cNE = h->alloc<double>(s);
       l.c.dinv = h->alloc<double>(s);
-      l.c.tab = h->alloc<double>(8 * (size_t)(l.g.n + 1));
+      l.c.tab = h->alloc<double>(8 * (size_t)(l.g.n + 1) * l.cap);
       l.b.C = h->alloc<double>(s);
       l.b.E = h->alloc<double>(s);
       l.b.N = h->alloc<double>(s);
@@ -229,7 +283,7 @@ void build_levels(fmg_eig_handle* h) {
     } else {
       for (int q = 0; q < 8; ++q) l.c3.a[q] = h->alloc<double>(s);
       l.c3.dinv = h->alloc<double>(s);
-      l.c3.tab = h->alloc<double>(15 * (size_t)(l.g.n + 1));
+      l.c3.tab = h->alloc<double>(15 * (size_t)(l.g.n + 1) * l.cap);
       for (int q = 0; q < 8; ++q) l.b3.a[q] = h->alloc<double>(s);
     }
     if (p.precision == FMG_MIXED_FP32) {
@@ -280,6 +334,7 @@ void build_coarse(fmg_eig_handle* h) {
   const int n1 = h->prob.coarse_cells;
   const int m = n1 - 1;
   const int dim = h->prob.dim;
+  const int nb = h->nb;
   const double H = h->prob.box_len / n1;
   std::vector<int> tri, adj;
   std::vector<double> q4;
@@ -355,31 +410,41 @@ void build_coarse(fmg_eig_handle* h) {
   cudaMemcpy(h->tri, tri.data(), tri.size() * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(h->adj, adj.data(), adj.size() * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(h->q4, q4.data(), q4.size() * sizeof(double), cudaMemcpyHostToDevice);
-  h->L1 = h->alloc<double>((size_t)h->nh * h->nh);
-  h->M1 = h->alloc<double>((size_t)h->nh * h->nh);
-  h->L1inv = h->alloc<double>((size_t)h->nh * h->nh);
-  h->lam = h->alloc<double>(1);
-  h->c = h->alloc<double>(h->nh + 1);
-  h->cstart = h->alloc<double>(h->nh + 1);
-  h->auu = h->alloc<double>(1);
-  h->buu = h->alloc<double>(1);
-  h->scal = h->alloc<double>(8);
-  h->partials = h->alloc<double>(kReduceBlocks);
+  const size_t nn = (size_t)h->nh * h->nh;
+  h->L1 = h->alloc<double>(nn * nb);
+  h->M1 = h->alloc<double>(nn * nb);
+  h->L1inv = h->alloc<double>(nn * nb);
+  h->lam = h->alloc<double>(nb);
+  h->c = h->alloc<double>((size_t)(h->nh + 1) * nb);
+  h->cstart = h->alloc<double>((size_t)(h->nh + 1) * nb);
+  h->auu = h->alloc<double>(nb);
+  h->buu = h->alloc<double>(nb);
+  h->scal = h->alloc<double>(3 * (size_t)nb + 8);
+  h->partials = h->alloc<double>((size_t)kReduceBlocks * nb);
   const int nt3 = dim == 2 ? 10 : 20;
-  h->t3 = h->alloc<double>((size_t)h->ntri * nt3);
-  const Grid& gf = h->L(h->levels()).g;
-  h->t3_partials = h->alloc<double>(
-      std::max<size_t>(1, dim == 2 ? t3_partials2d(gf, n1) : t3_partials3d(gf, n1)));
-  h->gAd = h->alloc<double>(h->nh);
-  h->gMd = h->alloc<double>(h->nh);
-  h->t1d = h->alloc<double>(h->nh);
-  h->B1d = h->alloc<double>((size_t)h->nh * h->nh);
-  h->t0 = h->alloc<double>(1);
+  h->t3 = h->alloc<double>((size_t)h->ntri * nt3 * nb);
+  size_t tp = 1;
+  for (int k = 2; k <= h->levels(); ++k) {
+    const Grid& g = h->L(k).g;
+    tp = std::max(tp, (dim == 2 ? t3_partials2d(g, n1) : t3_partials3d(g, n1)) * h->cnt[k]);
+  }
+  h->t3_partials = h->alloc<double>(tp);
+  h->gAd = h->alloc<double>((size_t)h->nh * nb);
+  h->gMd = h->alloc<double>((size_t)h->nh * nb);
+  h->t1d = h->alloc<double>((size_t)h->nh * nb);
+  h->B1d = h->alloc<double>(nn * nb);
+  h->t0 = h->alloc<double>(nb);
   h->kscratch = h->alloc<double>(3 * (size_t)(h->nh + 1) * (h->nh + 1) + h->nh + 1);
-  h->lam_levels = h->alloc<double>(FMG_MAX_LEVELS);
-  h->iters = h->alloc<int>(FMG_MAX_LEVELS);
-  h->status = h->alloc<int>(FMG_MAX_LEVELS);
-  h->uout = h->alloc<double>(h->L(h->levels()).g.interior());
+  h->lam_levels = h->alloc<double>((size_t)FMG_MAX_LEVELS * nb);
+  h->iters = h->alloc<int>((size_t)FMG_MAX_LEVELS * nb);
+  h->status = h->alloc<int>((size_t)FMG_MAX_LEVELS * nb);
+  size_t tot = 0;
+  h->uoff.resize(nb);
+  for (int b = 0; b < nb; ++b) {
+    h->uoff[b] = tot;
+    tot += h->L(h->probs[b].levels).g.interior();
+  }
+  h->uout = h->alloc<double>(tot);
   h->dense_smem = dense_smem_bytes(h->nh + 1, h->ntri, h->nvert, 1);
 }
 
@@ -395,14 +460,16 @@ void prof_end(fmg_eig_handle* h, int id, int level, cudaStream_t s) {
   }
 }
 
+// Operators of every level for every instance that has the level, and the level-1 inverse.
 void enqueue_setup(fmg_eig_handle* h, cudaStream_t s) {
+  h->activate(h->nb);
   for (int k = 1; k <= h->levels(); ++k) {
     Level& l = h->L(k);
     prof_begin(h, kProfCoef, k, s);
     lv_coef(l, h->dparams, s);
     prof_end(h, kProfCoef, k, s);
     if (h->prob.precision == FMG_MIXED_FP32) {
-      const size_t n = l.g.stride;
+      const size_t n = l.g.stride * l.g.nb;
       if (l.g.dim == 2) {
         to_f32(l.c.cC, l.cf.cC, n, s);
         to_f32(l.c.cE, l.cf.cE, n, s);
@@ -416,7 +483,7 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s) {
     }
   }
   lv_dense_level1(h->L(1), h->L1, h->M1, s);
-  dense_spd_inverse(h->L1, h->L1inv, h->nh, s);
+  dense_spd_inverse(h->L1, h->L1inv, h->nh, h->L(1).g.nb, s);
 }
 
 DenseProblem dense_base(fmg_eig_handle* h) {
@@ -440,17 +507,17 @@ DenseProblem dense_base(fmg_eig_handle* h) {
   return d;
 }
 
-// Algorithm 3.2 step 1 into L(1).u and h->lam
+// Algorithm 3.2 step 1 into L(1).u and h->lam for the active instances
 void enqueue_coarse(fmg_eig_handle* h, cudaStream_t s) {
   Level& l1 = h->L(1);
-  lv_start(l1, h->prob.box_len, h->cstart, s);
+  lv_start(l1, h->cstart, h->nh + 1, s);
   DenseProblem d = dense_base(h);
   d.aug = 0;
   d.c_init = h->cstart;
   d.iters_out = h->iters;
   d.status_out = h->status;
-  dense_scf(d, s);
-  scatter_level1(l1.g, h->c, l1.u, s);
+  dense_scf(d, l1.g.nb, s);
+  scatter_level1(l1.g, h->c, h->nh + 1, l1.u, s);
 }
 
 // One V-cycle on level j for L_j x = f (x, f in L(j).x, L(j).f).
@@ -471,7 +538,7 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
     std::swap(l.x, l.xt);
     zero = false;
   }
-  if (zero) cudaMemsetAsync(l.x, 0, l.g.stride * sizeof(double), s);
+  if (zero) cudaMemsetAsync(l.x, 0, l.g.stride * l.g.nb * sizeof(double), s);
   Level& lc = h->L(j - 1);
   prof_begin(h, kProfResidual, j, s);
   lv_residual(l, l.f, l.x, l.r, s);
@@ -481,7 +548,7 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   prof_end(h, kProfRestrict, j, s);
   enqueue_vcycle(h, j - 1, true, s);
   prof_begin(h, kProfProlong, j, s);
-  lv_prolong(l, lc, lc.x, l.x, true, nullptr, nullptr, s);
+  lv_prolong(l, lc, lc.x, l.x, true, nullptr, nullptr, 0, s);
   prof_end(h, kProfProlong, j, s);
   for (int it = 0; it < p.nu_post; ++it) {
     lv_jacobi(l, l.f, l.x, l.xt, false, s);
@@ -504,7 +571,7 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
     std::swap(l.x32, l.xt32);
     zero = false;
   }
-  if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * sizeof(float), s);
+  if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * l.g.nb * sizeof(float), s);
   Level& lc = h->L(j - 1);
   residual32(l.g, l.cf, l.cf3, l.f32, l.x32, l.r32, s);
   restrict32(l.g, lc.g, l.r32, lc.f32, s);
@@ -524,7 +591,7 @@ void enqueue_multigrid(fmg_eig_handle* h, int k, cudaStream_t s) {
       prof_begin(h, kProfVcycle, k, s);
       residual_mixed(l.g, l.c, l.c3, l.f, l.x, l.f32, s);
       enqueue_vcycle32(h, k, s);
-      add_f32(l.x32, l.x, l.g.stride, s);
+      add_f32(l.x32, l.x, l.g.stride * l.g.nb, s);
       prof_end(h, kProfVcycle, k, s);
     }
     return;
@@ -538,17 +605,19 @@ void enqueue_multigrid(fmg_eig_handle* h, int k, cudaStream_t s) {
 // gathered into the dense level-1 arrays of the handle.
 void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s) {
   Level& l = h->L(k);
+  const int nb = l.g.nb;
+  const size_t st = l.g.stride;
   lv_apply(l, ut, l.y, s);
   lv_mass(l, ut, l.z, s);
-  dot(ut, l.y, l.g.stride, h->partials, h->auu, s);
-  dot(ut, l.z, l.g.stride, h->partials, h->buu, s);
+  dot(ut, l.y, st, h->partials, h->auu, s, nb, st);
+  dot(ut, l.z, st, h->partials, h->buu, s, nb, st);
   prof_begin(h, kProfMoments, k, s);
   lv_nload_density(l, ut, l.r, s);
   prof_end(h, kProfMoments, k, s);
   prof_begin(h, kProfT3, k, s);
   lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, s);
   prof_end(h, kProfT3, k, s);
-  dot(ut, l.r, l.g.stride, h->partials, h->t0, s);
+  dot(ut, l.r, st, h->partials, h->t0, s, nb, st);
   for (int j = k; j >= 2; --j) {
     Level& f = h->L(j);
     Level& c = h->L(j - 1);
@@ -575,42 +644,75 @@ DenseProblem dense_augmented(fmg_eig_handle* h) {
   return d;
 }
 
-// One correction step (Algorithm 3.1) on level k: (h->lam, L(k).u) -> (h->lam, L(k).u);
-// u~ stays in L(k).x.
+// One correction step (Algorithm 3.1) on level k for the active instances:
+// (h->lam, L(k).u) -> (h->lam, L(k).u); u~ stays in L(k).x.
 void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   Level& l = h->L(k);
+  const int nb = l.g.nb;
   // step 1: auxiliary problem, m V-cycles from u
   prof_begin(h, kProfRhs, k, s);
   lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
   prof_end(h, kProfRhs, k, s);
-  cudaMemcpyAsync(l.x, l.u, l.g.stride * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(l.x, l.u, l.g.stride * nb * sizeof(double), cudaMemcpyDeviceToDevice, s);
   enqueue_multigrid(h, k, s);
   const double* ut = l.x;
   // step 2: augmented space V_H + span{u~}
   enqueue_augment(h, k, ut, s);
   DenseProblem d = dense_augmented(h);
   d.c_init = nullptr;
-  d.iters_out = h->iters + (k - 1);
-  d.status_out = h->status + (k - 1);
+  d.iters_out = h->iters + (size_t)(k - 1) * h->nb;
+  d.status_out = h->status + (size_t)(k - 1) * h->nb;
   prof_begin(h, kProfDense, k, s);
-  dense_scf(d, s);
+  dense_scf(d, nb, s);
   prof_end(h, kProfDense, k, s);
   // u = P_{k<-1} c_H + c_u u~
-  scatter_level1(h->L(1).g, h->c, h->L(1).y, s);
+  scatter_level1(h->L(1).g, h->c, h->nh + 1, h->L(1).y, s);
   for (int j = 2; j < k; ++j)
-    lv_prolong(h->L(j), h->L(j - 1), h->L(j - 1).y, h->L(j).y, false, nullptr, nullptr, s);
-  lv_prolong(l, h->L(k - 1), h->L(k - 1).y, l.u, false, ut, h->c + h->nh, s);
+    lv_prolong(h->L(j), h->L(j - 1), h->L(j - 1).y, h->L(j).y, false, nullptr, nullptr, 0, s);
+  lv_prolong(l, h->L(k - 1), h->L(k - 1).y, l.u, false, ut, h->c + h->nh, h->nh + 1, s);
 }
 
 void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s) {
   enqueue_setup(h, s);
+  h->activate(h->nb);
   enqueue_coarse(h, s);
-  cudaMemcpyAsync(h->lam_levels, h->lam, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(h->lam_levels, h->lam, sizeof(double) * h->nb, cudaMemcpyDeviceToDevice, s);
   for (int k = 2; k <= h->levels(); ++k) {
-    lv_prolong(h->L(k), h->L(k - 1), h->L(k - 1).u, h->L(k).u, false, nullptr, nullptr, s);
+    h->activate(h->cnt[k]);
+    lv_prolong(h->L(k), h->L(k - 1), h->L(k - 1).u, h->L(k).u, false, nullptr, nullptr, 0, s);
     for (int it = 0; it < h->prob.corrections; ++it) enqueue_correction(h, k, s);
-    cudaMemcpyAsync(h->lam_levels + (k - 1), h->lam, sizeof(double), cudaMemcpyDeviceToDevice,
-                    s);
+    cudaMemcpyAsync(h->lam_levels + (size_t)(k - 1) * h->nb, h->lam, sizeof(double) * h->cnt[k],
+                    cudaMemcpyDeviceToDevice, s);
+  }
+  h->activate(1);
+}
+
+// u of every instance, unpacked from its finest level into h->uout (per level group).
+void enqueue_outputs(fmg_eig_handle* h, cudaStream_t s) {
+  for (int k = 1; k <= h->levels(); ++k) {
+    const int first = h->cnt[k + 1], count = h->cnt[k] - h->cnt[k + 1];
+    if (count <= 0) continue;
+    Level v = view(h->L(k), first, count);
+    unpack_interior(v.g, v.u, h->uout + h->uoff[first], s);
+  }
+}
+
+// b(u,u), a(u,u) + (Wu,u) and int u^4 of every instance's final u into h->scal (3 x nb).
+void enqueue_checks(fmg_eig_handle* h, cudaStream_t s) {
+  double* sa = h->scal;
+  double* sb = h->scal + h->nb;
+  double* sn = h->scal + 2 * h->nb;
+  for (int k = 1; k <= h->levels(); ++k) {
+    const int first = h->cnt[k + 1], count = h->cnt[k] - h->cnt[k + 1];
+    if (count <= 0) continue;
+    Level v = view(h->L(k), first, count);
+    const size_t st = v.g.stride;
+    lv_apply(v, v.u, v.y, s);
+    lv_mass(v, v.u, v.z, s);
+    lv_nload(v, v.u, v.r, s);
+    dot(v.u, v.y, st, h->partials, sa + first, s, count, st);
+    dot(v.u, v.z, st, h->partials, sb + first, s, count, st);
+    dot(v.u, v.r, st, h->partials, sn + first, s, count, st);
   }
 }
 
@@ -619,6 +721,274 @@ cudaStream_t pick(fmg_eig_handle* h, void* stream) {
 }
 
 bool level_ok(const fmg_eig_handle* h, int k) { return h && k >= 1 && k <= h->prob.levels; }
+
+// ---- autotuner: thread-block shape per level -----------------------------------------------
+// The stencil kernels of a level compute every node with the same expression whatever the
+// block shape, so the shape only changes the time.  For each level the tuner times a small
+// mix of that level's launches (4 Jacobi sweeps, one cubic-load + density pass, one RHS) per
+// candidate shape on the handle's own buffers, keeps the fastest, and remembers the choice
+// per (dim, n, instances rounded up to a power of two, precision) for the process.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+void time_mix(fmg_eig_handle* h, Level& l, int k, cudaStream_t s) {
+  for (int q = 0; q < 4; ++q) {
+    if (h->prob.precision == FMG_MIXED_FP32 && k >= 2)
+      jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s);
+    else
+      lv_jacobi(l, l.f, l.x, l.xt, false, s);
+  }
+  lv_nload_density(l, l.u, l.r, s);
+  lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
+}
+
+int autotune(fmg_eig_handle* h) {
+  if (h->prob.flags & FMG_FLAG_NO_AUTOTUNE) return FMG_OK;
+  static const int k2d[][2] = {{32, 8}, {32, 4}, {64, 4}, {32, 16}, {128, 2},
+                               {64, 8}, {16, 16}, {16, 8}, {8, 8},  {8, 4}};
+  static const int k3d[][2] = {{32, 8}, {32, 4}, {64, 2}, {32, 2}, {64, 4},
+                               {16, 8}, {8, 8},  {16, 4}};
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return FMG_ECUDA;
+  }
+  int rc = FMG_OK;
+  for (int k = 1; k <= h->levels() && rc == FMG_OK; ++k) {
+    Level& l = h->L(k);
+    l.g.nb = l.cap;
+    int nbq = 1;
+    while (nbq < l.cap) nbq <<= 1;
+    const auto key = std::make_tuple(l.g.dim, l.g.n, nbq, h->prob.precision);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        l.g.bx = it->second.first;
+        l.g.by = it->second.second;
+        continue;
+      }
+    }
+    const size_t nodes = l.g.interior() * (size_t)l.cap;
+    const bool big = nodes >= ((size_t)1 << 20);
+    const int ncand = l.g.dim == 2 ? (big ? 4 : 10) : (big ? 4 : 8);
+    const int reps = big ? 1 : 5;
+    float best = 1e30f;
+    int bx = 32, by = 8;
+    for (int ci = 0; ci < ncand; ++ci) {
+      l.g.bx = l.g.dim == 2 ? k2d[ci][0] : k3d[ci][0];
+      l.g.by = l.g.dim == 2 ? k2d[ci][1] : k3d[ci][1];
+      time_mix(h, l, k, s);  // warm-up
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) time_mix(h, l, k, s);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        cudaGetLastError();
+        rc = FMG_ECUDA;
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        bx = l.g.bx;
+        by = l.g.by;
+      }
+    }
+    l.g.bx = bx;
+    l.g.by = by;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {bx, by};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->activate(1);
+  return rc;
+}
+
+int create_handle(const fmg_eig_problem* probs, int count, fmg_eig_handle** out) {
+  if (!out || !probs || count < 1) return FMG_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    const int v = validate(&probs[i]);
+    if (v != FMG_OK) return v;
+    if (shared_key(probs[i]) != shared_key(probs[0])) return FMG_EINVAL;
+  }
+  fmg_eig_handle* h = new (std::nothrow) fmg_eig_handle();
+  if (!h) return FMG_ENOMEM;
+  h->nb = count;
+  h->order.resize(count);
+  std::iota(h->order.begin(), h->order.end(), 0);
+  std::stable_sort(h->order.begin(), h->order.end(),
+                   [&](int a, int b) { return probs[a].levels > probs[b].levels; });
+  for (int b = 0; b < count; ++b) h->probs.push_back(probs[h->order[b]]);
+  h->prob = h->probs[0];
+  h->cnt.assign(h->prob.levels + 2, 0);
+  for (int k = 1; k <= h->prob.levels; ++k)
+    for (const auto& p : h->probs) h->cnt[k] += p.levels >= k ? 1 : 0;
+  if (h->prob.dim == 3)  // planes and instances share gridDim.z of the 3D launches
+    for (int k = 1; k <= h->prob.levels; ++k)
+      if ((size_t)((h->prob.coarse_cells << (k - 1)) + 1) * h->cnt[k] > 65535) {
+        delete h;
+        return FMG_ENOTSUP;
+      }
+  if (cudaGetDevice(&h->dev) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return FMG_ECUDA;
+  }
+  try {
+    build_levels(h);
+    build_coarse(h);
+    h->dparams = h->alloc<PotentialParams>(count);
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return FMG_ENOMEM;
+  }
+  if (cudaMallocHost(&h->hparams, sizeof(PotentialParams) * count) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return FMG_ENOMEM;
+  }
+  for (int b = 0; b < count; ++b) h->hparams[b] = potential(h->probs[b]);
+  for (int i = 0; i < kProfCount; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (cudaEventCreate(&h->prof[i][j]) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return FMG_ECUDA;
+      }
+  cudaMemcpy(h->dparams, h->hparams, sizeof(PotentialParams) * count, cudaMemcpyHostToDevice);
+  if (h->dense_smem > kDenseSmemLimit) {  // the small dense solve keeps everything in shared memory
+    delete h;
+    return FMG_ENOTSUP;
+  }
+  if (dense_prepare(h->dense_smem) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return FMG_ECUDA;
+  }
+  // component entry points need the operators; the solve graph recomputes them itself
+  enqueue_setup(h, h->stream);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return FMG_ECUDA;
+  }
+  if (autotune(h) != FMG_OK) {
+    delete h;
+    return FMG_ECUDA;
+  }
+  for (int i = 0; i < kProfCount; ++i) h->prof_armed[i] = true;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_fmg(h, h->stream);
+    e = cudaStreamEndCapture(h->stream, &h->graph);
+  }
+  for (int i = 0; i < kProfCount; ++i) h->prof_armed[i] = false;
+  if (e == cudaSuccess) {
+    size_t n = 0;
+    e = cudaGraphGetNodes(h->graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(h->graph, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[i], &t);
+      if (t == cudaGraphNodeTypeKernel) h->kernel_nodes++;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+  h->activate(1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return FMG_ECUDA;
+  }
+  *out = h;
+  return FMG_OK;
+}
+
+// Launch the solve graph of every handle (each on its own stream), then collect the outputs
+// of each in the callers' order.  out_index[h][b] is the caller's index of h's instance b.
+int run_handles(const std::vector<fmg_eig_handle*>& hs,
+                const std::vector<std::vector<int>>& out_index, double* lambdas,
+                double* const* u_hosts, const size_t* u_lens, fmg_eig_stats* stats,
+                int32_t* statuses) {
+  for (size_t g = 0; g < hs.size(); ++g) {
+    fmg_eig_handle* h = hs[g];
+    for (int b = 0; b < h->nb; ++b) {
+      const int i = out_index[g][b];
+      if (u_hosts && u_hosts[i]) {
+        if (!u_lens || u_lens[i] != h->L(h->probs[b].levels).g.interior()) return FMG_EINVAL;
+      }
+    }
+  }
+  for (fmg_eig_handle* h : hs) {
+    cudaStream_t s = h->stream;
+    CK(cudaEventRecord(h->ev0, s));
+    CK(cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * h->nb,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaGraphLaunch(h->exec, s));
+    CK(cudaEventRecord(h->ev1, s));
+    if (u_hosts) enqueue_outputs(h, s);
+    if (stats) enqueue_checks(h, s);
+    h->activate(1);
+  }
+  int rc = FMG_OK;
+  for (size_t g = 0; g < hs.size(); ++g) {
+    fmg_eig_handle* h = hs[g];
+    cudaStream_t s = h->stream;
+    const int nb = h->nb, L = h->levels();
+    std::vector<double> lam(nb), lv((size_t)L * nb), sc(3 * (size_t)nb);
+    std::vector<int> st((size_t)L * nb), it((size_t)L * nb);
+    CK(cudaMemcpyAsync(lam.data(), h->lam, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(st.data(), h->status, sizeof(int) * L * nb, cudaMemcpyDeviceToHost, s));
+    if (stats) {
+      CK(cudaMemcpyAsync(lv.data(), h->lam_levels, sizeof(double) * L * nb,
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(it.data(), h->iters, sizeof(int) * L * nb, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(sc.data(), h->scal, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, s));
+    }
+    for (int b = 0; u_hosts && b < nb; ++b) {
+      const int i = out_index[g][b];
+      if (u_hosts[i])
+        CK(cudaMemcpyAsync(u_hosts[i], h->uout + h->uoff[b], sizeof(double) * u_lens[i],
+                           cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    for (int b = 0; b < nb; ++b) {
+      const int i = out_index[g][b];
+      const int lb = h->probs[b].levels;
+      int code = FMG_OK;
+      for (int k = 1; k <= lb; ++k)
+        if (st[(size_t)(k - 1) * nb + b] != 0) code = FMG_ENOCONV;
+      if (code != FMG_OK) rc = FMG_ENOCONV;
+      lambdas[i] = lam[b];
+      if (statuses) statuses[i] = code;
+      if (stats) {
+        fmg_eig_stats& o = stats[i];
+        memset(&o, 0, sizeof(o));
+        o.lambda = lam[b];
+        o.solve_ms = ms;
+        o.levels = lb;
+        o.status = code;
+        for (int k = 1; k <= lb; ++k) {
+          o.lambda_levels[k - 1] = lv[(size_t)(k - 1) * nb + b];
+          o.scf_iters[k - 1] = it[(size_t)(k - 1) * nb + b];
+        }
+        // b(u,u) - 1 and lambda - a(u,u) - (Wu,u) - zeta int u^4 on the finest level
+        o.norm_defect = sc[nb + b] - 1.0;
+        o.identity_defect = lam[b] - (sc[b] + h->probs[b].zeta * sc[2 * nb + b]);
+      }
+    }
+  }
+  return rc;
+}
 
 }  // namespace
 
@@ -638,83 +1008,23 @@ const char* fmg_eig_strerror(int code) {
 }
 
 int fmg_eig_create(const fmg_eig_problem* prob, fmg_eig_handle** out) {
-  if (!out) return FMG_EINVAL;
-  *out = nullptr;
-  const int v = validate(prob);
-  if (v != FMG_OK) return v;
-  fmg_eig_handle* h = new (std::nothrow) fmg_eig_handle();
-  if (!h) return FMG_ENOMEM;
-  h->prob = *prob;
-  if (cudaGetDevice(&h->dev) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return FMG_ECUDA;
+  if (!prob) {
+    if (out) *out = nullptr;
+    return FMG_EINVAL;
   }
-  try {
-    build_levels(h);
-    build_coarse(h);
-    h->dparams = h->alloc<PotentialParams>(1);
-  } catch (const std::bad_alloc&) {
-    delete h;
-    return FMG_ENOMEM;
-  }
-  if (cudaMallocHost(&h->hparams, sizeof(PotentialParams)) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return FMG_ENOMEM;
-  }
-  *h->hparams = potential(*prob);
-  for (int i = 0; i < kProfCount; ++i)
-    for (int j = 0; j < 2; ++j)
-      if (cudaEventCreate(&h->prof[i][j]) != cudaSuccess) {
-        cudaGetLastError();
-        delete h;
-        return FMG_ECUDA;
-      }
-  cudaMemcpy(h->dparams, h->hparams, sizeof(PotentialParams), cudaMemcpyHostToDevice);
-  if (h->dense_smem > kDenseSmemLimit) {  // the small dense solve keeps everything in shared memory
-    delete h;
-    return FMG_ENOTSUP;
-  }
-  if (dense_prepare(h->dense_smem) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return FMG_ECUDA;
-  }
-  // component entry points need the operators; the solve graph recomputes them itself
-  enqueue_setup(h, h->stream);
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return FMG_ECUDA;
-  }
-  for (int i = 0; i < kProfCount; ++i) h->prof_armed[i] = true;
-  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    enqueue_fmg(h, h->stream);
-    e = cudaStreamEndCapture(h->stream, &h->graph);
-  }
-  for (int i = 0; i < kProfCount; ++i) h->prof_armed[i] = false;
-  if (e == cudaSuccess) {
-    size_t count = 0;
-    e = cudaGraphGetNodes(h->graph, nullptr, &count);
-    std::vector<cudaGraphNode_t> nodes(count);
-    if (e == cudaSuccess && count) e = cudaGraphGetNodes(h->graph, nodes.data(), &count);
-    for (size_t i = 0; e == cudaSuccess && i < count; ++i) {
-      cudaGraphNodeType t;
-      e = cudaGraphNodeGetType(nodes[i], &t);
-      if (t == cudaGraphNodeTypeKernel) h->kernel_nodes++;
-    }
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return FMG_ECUDA;
-  }
-  *out = h;
+  return create_handle(prob, 1, out);
+}
+
+int fmg_eig_batch_create(const fmg_eig_problem* probs, int32_t count, fmg_eig_handle** out) {
+  return create_handle(probs, count, out);
+}
+
+int32_t fmg_eig_batch_count(const fmg_eig_handle* h) { return h ? h->nb : 0; }
+
+int fmg_eig_level_tile(const fmg_eig_handle* h, int32_t level, int32_t* bx, int32_t* by) {
+  if (!level_ok(h, level) || !bx || !by) return FMG_EINVAL;
+  *bx = h->lv[level - 1].g.bx;
+  *by = h->lv[level - 1].g.by;
   return FMG_OK;
 }
 
@@ -726,29 +1036,25 @@ size_t fmg_eig_level_size(const fmg_eig_handle* h, int32_t level) {
 void fmg_eig_destroy(fmg_eig_handle* h) { delete h; }
 
 int fmg_eig_set_params(fmg_eig_handle* h, const fmg_eig_problem* prob) {
-  if (!h || !prob) return FMG_EINVAL;
+  if (!h || !prob || h->nb != 1) return FMG_EINVAL;
   const int v = validate(prob);
   if (v != FMG_OK) return v;
   const fmg_eig_problem& a = h->prob;
-  if (prob->dim != a.dim || prob->coarse_cells != a.coarse_cells || prob->levels != a.levels ||
-      prob->nu_pre != a.nu_pre || prob->nu_post != a.nu_post || prob->vcycles != a.vcycles ||
-      prob->corrections != a.corrections || prob->precision != a.precision ||
-      prob->operator_form != a.operator_form || prob->smoother != a.smoother ||
-      prob->box_len != a.box_len || prob->scf_tol != a.scf_tol ||
-      prob->scf_max_iter != a.scf_max_iter)
-    return FMG_EINVAL;
+  if (prob->levels != a.levels || shared_key(*prob) != shared_key(a)) return FMG_EINVAL;
   // the pinned staging copy is read by the next solve's upload, in stream order
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return FMG_ECUDA;
   h->prob.w_const = prob->w_const;
   for (int d = 0; d < 3; ++d) h->prob.w_quad[d] = prob->w_quad[d];
   h->prob.zeta = prob->zeta;
   h->prob.omega = prob->omega;
+  h->probs[0] = h->prob;
   *h->hparams = potential(h->prob);
   if (cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams), cudaMemcpyHostToDevice,
                       h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return FMG_ECUDA;
   enqueue_setup(h, h->stream);  // keep the component entry points' operators current
+  h->activate(1);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return FMG_ECUDA;
   return FMG_OK;
 }
@@ -769,7 +1075,7 @@ int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count) {
 
 int fmg_eig_solve_dev(fmg_eig_handle* h, double* lambda_dev, double* u_dev, size_t u_len,
                       void* stream) {
-  if (!h || !lambda_dev) return FMG_EINVAL;
+  if (!h || !lambda_dev || h->nb != 1) return FMG_EINVAL;
   const Level& fine = h->L(h->levels());
   if (u_dev && u_len != fine.g.interior()) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
@@ -783,60 +1089,67 @@ int fmg_eig_solve_dev(fmg_eig_handle* h, double* lambda_dev, double* u_dev, size
 
 int fmg_eig_solve(fmg_eig_handle* h, double* lambda, double* u_host, size_t u_len,
                   fmg_eig_stats* stats) {
-  if (!h || !lambda) return FMG_EINVAL;
-  const Level& fine = h->L(h->levels());
-  if (u_host && u_len != fine.g.interior()) return FMG_EINVAL;
-  cudaStream_t s = h->stream;
-  CK(cudaEventRecord(h->ev0, s));
-  CK(cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams), cudaMemcpyHostToDevice, s));
-  CK(cudaGraphLaunch(h->exec, s));
-  CK(cudaEventRecord(h->ev1, s));
-  double lam = 0.0;
-  CK(cudaMemcpyAsync(&lam, h->lam, sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (u_host) {
-    unpack_interior(fine.g, fine.u, h->uout, s);
-    CK(cudaMemcpyAsync(u_host, h->uout, u_len * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (!h || !lambda || h->nb != 1) return FMG_EINVAL;
+  double* const uh[1] = {u_host};
+  const size_t ul[1] = {u_len};
+  std::vector<fmg_eig_handle*> hs{h};
+  std::vector<std::vector<int>> idx{{0}};
+  return run_handles(hs, idx, lambda, u_host ? uh : nullptr, ul, stats, nullptr);
+}
+
+int fmg_eig_batch_solve(fmg_eig_handle* h, double* lambdas, double* const* u_hosts,
+                        const size_t* u_lens, fmg_eig_stats* stats, int32_t* statuses) {
+  if (!h || !lambdas) return FMG_EINVAL;
+  std::vector<fmg_eig_handle*> hs{h};
+  std::vector<std::vector<int>> idx{h->order};
+  return run_handles(hs, idx, lambdas, u_hosts, u_lens, stats, statuses);
+}
+
+int fmg_eig_solve_batch(const fmg_eig_problem* probs, int32_t count, double* lambdas,
+                        double* const* u_hosts, const size_t* u_lens, fmg_eig_stats* stats,
+                        int32_t* statuses) {
+  if (!probs || count < 1 || !lambdas) return FMG_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    const int v = validate(&probs[i]);
+    if (v != FMG_OK) return v;
   }
-  int st[FMG_MAX_LEVELS];
-  CK(cudaMemcpyAsync(st, h->status, sizeof(st), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  *lambda = lam;
+  // group by the shared fields, keeping the callers' order inside each group
+  std::vector<std::vector<int>> groups;
+  for (int i = 0; i < count; ++i) {
+    bool placed = false;
+    for (auto& g : groups)
+      if (shared_key(probs[g[0]]) == shared_key(probs[i])) {
+        g.push_back(i);
+        placed = true;
+        break;
+      }
+    if (!placed) groups.push_back({i});
+  }
+  std::vector<fmg_eig_handle*> hs;
+  std::vector<std::vector<int>> idx;
   int rc = FMG_OK;
-  for (int k = 0; k < h->levels(); ++k)
-    if (st[k] != 0) rc = FMG_ENOCONV;
-  if (stats) {
-    memset(stats, 0, sizeof(*stats));
-    stats->lambda = lam;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-    stats->solve_ms = ms;
-    stats->levels = h->levels();
-    stats->status = rc;
-    CK(cudaMemcpy(stats->lambda_levels, h->lam_levels, sizeof(double) * h->levels(),
-                  cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(stats->scf_iters, h->iters, sizeof(int) * h->levels(), cudaMemcpyDeviceToHost));
-    // b(u,u) - 1 and lambda - a(u,u) - (Wu,u) - zeta int u^4 on the finest level
-    Level& l = h->L(h->levels());
-    lv_apply(l, l.u, l.y, s);
-    lv_mass(l, l.u, l.z, s);
-    lv_nload(l, l.u, l.r, s);
-    dot(l.u, l.y, l.g.stride, h->partials, h->scal + 0, s);
-    dot(l.u, l.z, l.g.stride, h->partials, h->scal + 1, s);
-    dot(l.u, l.r, l.g.stride, h->partials, h->scal + 2, s);
-    double sc[3];
-    CK(cudaMemcpyAsync(sc, h->scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    stats->norm_defect = sc[1] - 1.0;
-    stats->identity_defect = lam - (sc[0] + h->prob.zeta * sc[2]);
+  for (auto& g : groups) {
+    std::vector<fmg_eig_problem> ps;
+    for (int i : g) ps.push_back(probs[i]);
+    fmg_eig_handle* h = nullptr;
+    rc = create_handle(ps.data(), (int)ps.size(), &h);
+    if (rc != FMG_OK) break;
+    hs.push_back(h);
+    std::vector<int> map(h->nb);
+    for (int b = 0; b < h->nb; ++b) map[b] = g[h->order[b]];
+    idx.push_back(map);
   }
+  if (rc == FMG_OK) rc = run_handles(hs, idx, lambdas, u_hosts, u_lens, stats, statuses);
+  for (fmg_eig_handle* h : hs) delete h;
   return rc;
 }
 
-// ---- component entry points ------------------------------------------------------------
+// ---- component entry points (instance 0 of the handle) ------------------------------------
 int fmg_eig_apply_operator(fmg_eig_handle* h, int32_t level, const double* x_dev,
                            double* y_dev, void* stream) {
   if (!level_ok(h, level) || !x_dev || !y_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   pack_interior(l.g, x_dev, l.r, s);
   lv_apply(l, l.r, l.y, s);
@@ -849,6 +1162,7 @@ int fmg_eig_apply_mass(fmg_eig_handle* h, int32_t level, const double* x_dev, do
                        void* stream) {
   if (!level_ok(h, level) || !x_dev || !y_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   pack_interior(l.g, x_dev, l.r, s);
   lv_mass(l, l.r, l.y, s);
@@ -861,6 +1175,7 @@ int fmg_eig_jacobi(fmg_eig_handle* h, int32_t level, const double* f_dev,
                    const double* x_in_dev, double* x_out_dev, void* stream) {
   if (!level_ok(h, level) || !f_dev || !x_in_dev || !x_out_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   pack_interior(l.g, f_dev, l.f, s);
   pack_interior(l.g, x_in_dev, l.r, s);
@@ -874,6 +1189,7 @@ int fmg_eig_residual_restrict(fmg_eig_handle* h, int32_t level, const double* f_
                               const double* x_dev, double* rc_dev, void* stream) {
   if (!level_ok(h, level) || level < 2 || !f_dev || !x_dev || !rc_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   Level& lc = h->L(level - 1);
   pack_interior(l.g, f_dev, l.f, s);
@@ -889,11 +1205,12 @@ int fmg_eig_prolong_add(fmg_eig_handle* h, int32_t level, const double* ec_dev, 
                         void* stream) {
   if (!level_ok(h, level) || level < 2 || !ec_dev || !x_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   Level& lc = h->L(level - 1);
   pack_interior(lc.g, ec_dev, lc.y, s);
   pack_interior(l.g, x_dev, l.y, s);
-  lv_prolong(l, lc, lc.y, l.y, true, nullptr, nullptr, s);
+  lv_prolong(l, lc, lc.y, l.y, true, nullptr, nullptr, 0, s);
   unpack_interior(l.g, l.y, x_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -903,6 +1220,7 @@ int fmg_eig_nonlinear_load(fmg_eig_handle* h, int32_t level, const double* u_dev
                            double* n_dev, void* stream) {
   if (!level_ok(h, level) || !u_dev || !n_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   pack_interior(l.g, u_dev, l.r, s);
   lv_nload(l, l.r, l.y, s);
@@ -915,11 +1233,13 @@ int fmg_eig_aux_rhs(fmg_eig_handle* h, int32_t level, double lambda, const doubl
                     double* f_dev, void* stream) {
   if (!level_ok(h, level) || !u_dev || !f_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   CK(cudaStreamSynchronize(s));
-  CK(cudaMemcpy(h->scal + 7, &lambda, sizeof(double), cudaMemcpyHostToDevice));
+  double* lam_tmp = h->scal + 3 * (size_t)h->nb;
+  CK(cudaMemcpy(lam_tmp, &lambda, sizeof(double), cudaMemcpyHostToDevice));
   pack_interior(l.g, u_dev, l.r, s);
-  lv_rhs(l, h->scal + 7, h->dparams, l.r, l.y, s);
+  lv_rhs(l, lam_tmp, h->dparams, l.r, l.y, s);
   unpack_interior(l.g, l.y, f_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;
@@ -929,6 +1249,7 @@ int fmg_eig_multigrid(fmg_eig_handle* h, int32_t level, const double* f_dev, dou
                       void* stream) {
   if (!level_ok(h, level) || !f_dev || !x_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
+  h->activate(1);
   Level& l = h->L(level);
   pack_interior(l.g, f_dev, l.f, s);
   pack_interior(l.g, x_dev, l.x, s);
@@ -944,6 +1265,7 @@ int fmg_eig_correction(fmg_eig_handle* h, int32_t level, double lambda_in,
   if (!level_ok(h, level) || level < 2 || !u_in_dev || !lambda_out || !u_out_dev)
     return FMG_EINVAL;
   cudaStream_t s = h->stream;
+  h->activate(1);
   Level& l = h->L(level);
   CK(cudaStreamSynchronize(s));
   CK(cudaMemcpy(h->lam, &lambda_in, sizeof(double), cudaMemcpyHostToDevice));
@@ -952,9 +1274,10 @@ int fmg_eig_correction(fmg_eig_handle* h, int32_t level, double lambda_in,
   unpack_interior(l.g, l.u, u_out_dev, s);
   if (u_tilde_dev) unpack_interior(l.g, l.x, u_tilde_dev, s);
   int st = 0, it = 0;
+  const size_t row = (size_t)(level - 1) * h->nb;
   CK(cudaMemcpyAsync(lambda_out, h->lam, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&st, h->status + (level - 1), sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&it, h->iters + (level - 1), sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&st, h->status + row, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&it, h->iters + row, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (iters) *iters = it;
   return st == 0 ? FMG_OK : FMG_ENOCONV;
@@ -967,6 +1290,7 @@ int fmg_eig_augmented_system(fmg_eig_handle* h, int32_t level, const double* u_t
       !G_host || n != h->nh + 1)
     return FMG_EINVAL;
   cudaStream_t s = h->stream;
+  h->activate(1);
   Level& l = h->L(level);
   const size_t nn = (size_t)n * n;
   double* kd = h->kscratch;
@@ -981,7 +1305,7 @@ int fmg_eig_augmented_system(fmg_eig_handle* h, int32_t level, const double* u_t
   d.G_out = kd + 2 * nn;
   d.iters_out = h->iters;
   d.status_out = h->status;
-  dense_scf(d, s);
+  dense_scf(d, 1, s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(K_host, kd, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(M_host, kd + nn, nn * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -993,6 +1317,7 @@ int fmg_eig_augmented_system(fmg_eig_handle* h, int32_t level, const double* u_t
 int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev, int32_t* iters) {
   if (!h || !lambda_out || !u_dev) return FMG_EINVAL;
   cudaStream_t s = h->stream;
+  h->activate(1);
   enqueue_coarse(h, s);
   unpack_interior(h->L(1).g, h->L(1).u, u_dev, s);
   int st = 0, it = 0;

@@ -13,13 +13,18 @@
 
 namespace fmg {
 
+// Batched launches: every per-level array holds its instances back to back, instance b's
+// vector starting at element b * stride; every launcher runs instances 0 .. nb - 1 of the
+// arrays it is given, and per-instance scalars (lambda, parameters, dots) are indexed by b.
 struct Grid {
   int dim = 2;
   int n = 0;          // cells per side
   int pitch = 0;      // elements per row
   int rows = 0;       // rows per plane (n + 1)
-  size_t stride = 0;  // elements per vector
+  size_t stride = 0;  // elements per vector of one instance
   double h = 0;
+  int nb = 1;         // instances of a launch
+  int bx = 32, by = 8;  // thread-block shape of the stencil kernels on this level
   size_t interior() const {
     size_t m = (size_t)(n - 1);
     return dim == 2 ? m * m : m * m * m;
@@ -56,17 +61,19 @@ void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x
                 cudaStream_t s);
 void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s);
-// xf = (add ? xf : 0) + P ec (+ scale[0] * extra when extra != nullptr)
+// xf = (add ? xf : 0) + P ec (+ scale[b * scale_stride] * extra for instance b when extra is
+// given)
 void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
-               const double* extra, const double* scale, cudaStream_t s);
+               const double* extra, const double* scale, int scale_stride, cudaStream_t s);
 void nload2d(const Grid& g, const double* u, double* out, cudaStream_t s);
-// f = lam[0] * M u - p->zeta * N(u)
+// f = lam[b] * M u - p[b].zeta * N(u) for instance b
 void rhs2d(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
            double* f, cudaStream_t s);
-// Dense level-1 matrices L_1 and M_1 (n1-1)^2 square, row-major, interior numbering.
+// Dense level-1 matrices L_1 and M_1 (n1-1)^2 square, row-major, interior numbering (one
+// pair per instance, back to back).
 void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s);
-// sin-product start vector for the level-1 nonlinear solve
-void start_vector(const Grid& g, double box_len, double* c, cudaStream_t s);
+// sin-product start vector for the level-1 nonlinear solve (instance b at c + b * cstride)
+void start_vector(const Grid& g, double* c, int cstride, cudaStream_t s);
 
 // ---- 3D level kernels (grid3d.cu) -------------------------------------------------------
 // Couplings of L on the Kuhn mesh: a[0] diagonal, a[1 + d] the coupling of p with p + d for
@@ -92,7 +99,7 @@ void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x
 void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s);
 void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
-               const double* extra, const double* scale, cudaStream_t s);
+               const double* extra, const double* scale, int scale_stride, cudaStream_t s);
 void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s);
 void rhs3d(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
            double* f, cudaStream_t s);
@@ -104,10 +111,11 @@ void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaS
 void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s);
 void gather_vec3d(const Grid& g, const double* a, const double* b, const double* c, double* oa,
                   double* ob, double* oc, cudaStream_t s);
-void start_vector3d(const Grid& g, double* c, cudaStream_t s);
+void start_vector3d(const Grid& g, double* c, int cstride, cudaStream_t s);
 
 // ---- 3D augmented pass (augment3d.cu) -----------------------------------------------------
-// T3 per coarse Kuhn tetrahedron (20 per tetrahedron, sorted triples of its 4 vertices),
+// T3 per coarse Kuhn tetrahedron (20 per tetrahedron, sorted triples of its 4 vertices;
+// partials: t3_partials3d doubles per instance, t3: 20 per tetrahedron per instance),
 // tetrahedron index 6 * (I + n1 (J + n1 L)) + s, s the axis permutation in lexicographic
 // order, vertices (V, V + e_s0, V + e_s0 + e_s1, V + (1,1,1)).
 size_t t3_partials3d(const Grid& fine, int n1);
@@ -123,6 +131,7 @@ struct CoefF3D {
   float* a[8];
   float* dinv;
 };
+// contiguous conversions over n entries (all instances of a level at once)
 void to_f32(const double* a, float* b, size_t n, cudaStream_t s);
 void add_f32(const float* e, double* x, size_t n, cudaStream_t s);  // x += e (all entries)
 // r = (float)(f - L x) with the FP64 operator of the level (2D uses c2, 3D c3)
@@ -139,17 +148,20 @@ void prolong32_add(const Grid& fine, const Grid& coarse, const float* ec, float*
 void coarse32(const Grid& g, const double* Linv, const float* x, float* y, cudaStream_t s);
 
 // ---- Reductions (reduce.cu) -------------------------------------------------------------
-// out[0] = sum_i a[i] * b[i] over n entries; deterministic two-stage tree.  `partials` holds
-// at least kReduceBlocks doubles.
+// out[b] = sum_i a[b vst + i] * b[b vst + i] over n entries for instances b < nb;
+// deterministic two-stage tree whose order depends on n only.  `partials` holds
+// nb * kReduceBlocks doubles.
 constexpr int kReduceBlocks = 1024;
 void dot(const double* a, const double* b, size_t n, double* partials, double* out,
-         cudaStream_t s);
+         cudaStream_t s, int nb = 1, size_t vst = 0);
 
 // ---- Interior <-> padded packing (pack.cu) ----------------------------------------------
+// (instance b: interior vector at b * g.interior(), padded one at b * g.stride)
 void pack_interior(const Grid& g, const double* interior, double* padded, cudaStream_t s);
 void unpack_interior(const Grid& g, const double* padded, double* interior, cudaStream_t s);
-// padded level-1 vector from a dense coefficient vector c (first n1 entries)
-void scatter_level1(const Grid& g, const double* c, double* padded, cudaStream_t s);
+// padded level-1 vectors from dense coefficient vectors c (instance b at c + b * cstride)
+void scatter_level1(const Grid& g, const double* c, size_t cstride, double* padded,
+                    cudaStream_t s);
 
 // ---- Augmented-space fine pass (augment2d.cu) ---------------------------------------------
 // Density stencil B(u)_pq = int u^2 phi_p phi_q of one 2D level (couplings to p, E, N, NE).
@@ -172,12 +184,15 @@ void t3_class_moments2d(double out[2 * 7 * 10]);
 void t3_map2d(int r, double out[2 * 10 * 25]);
 void t3_power_table(int r, double* out);  // 4 * (r + 1) doubles
 // dense level-1 data for the augmented solve: gA, gM, t1 (nh) and B1 (nh x nh) from padded
-// level-1 vectors and the level-1 density stencil
+// level-1 vectors and the level-1 density stencil (per instance, back to back)
 void gather_level1_2d(const Grid& g1, const double* gA_pad, const double* gM_pad,
                       const double* t1_pad, const Density2D& b1, double* gA, double* gM,
                       double* t1, double* B1, cudaStream_t s);
 
 // ---- Dense small solves (dense.cu) -------------------------------------------------------
+// A batch of problems shares the geometry (tri, adj, q4) and keeps the per-instance arrays
+// back to back: L1, M1, B1 nh*nh; gA, gM, t1 nh; t3 ntri*nt3; c_init, c_out nh + 1;
+// auu, buu, t0, lam_out, iters_out, status_out and params one each.
 struct DenseProblem {
   int nh;              // coarse unknowns (interior nodes of level 1)
   int aug;             // 1: basis (phi^H, u~), n = nh + 1; 0: basis phi^H, n = nh
@@ -208,7 +223,7 @@ struct DenseProblem {
   double* lam_out;       // 1
   int* iters_out;        // 1
   int* status_out;       // 1 (0 converged, 1 cap hit)
-  // optional: assemble only (K0, M, G(c_init)) into these n x n outputs and stop
+  // optional (a single problem only): assemble K0, M, G(c_init) into these n x n outputs
   double* K_out;
   double* M_out;
   double* G_out;
@@ -216,9 +231,9 @@ struct DenseProblem {
 constexpr size_t kDenseSmemLimit = 200 * 1024;  // dynamic shared memory of the dense solve
 size_t dense_smem_bytes(int n, int ntri, int nvert, int aug);
 cudaError_t dense_prepare(size_t max_smem);  // opt in to large dynamic shared memory
-void dense_scf(const DenseProblem& p, cudaStream_t s);
-// Linv = L^{-1} for an SPD n x n matrix (Cholesky), one CTA.
-void dense_spd_inverse(const double* L, double* Linv, int n, cudaStream_t s);
+void dense_scf(const DenseProblem& p, int nb, cudaStream_t s);  // one CTA per problem
+// Linv = L^{-1} for SPD n x n matrices (LDL^T), one CTA per instance.
+void dense_spd_inverse(const double* L, double* Linv, int n, int nb, cudaStream_t s);
 // y(padded level 1) = Linv * x(padded level 1) on the interior nodes (2D or 3D)
 void coarse_matvec(const Grid& g, const double* Linv, const double* x, double* y,
                    cudaStream_t s);

@@ -20,9 +20,6 @@
 namespace fmg {
 namespace {
 
-constexpr int BX = 32;
-constexpr int BY = 8;
-
 __device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j * pitch + i; }
 
 // The stencil is separable: every coefficient is (constant + part in i) + (part in j).  A 1D
@@ -32,7 +29,8 @@ __global__ void k_coef1d(int n, double h, const PotentialParams* __restrict__ pp
                          double* __restrict__ tab) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x > n) return;
-  const PotentialParams p = *pp;
+  const PotentialParams p = pp[blockIdx.y];
+  tab += (size_t)blockIdx.y * 8 * (n + 1);
   const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
   const double h2 = h * h, h4 = h2 * h2;
   const double d = x, m = h2 * p.w0;
@@ -59,13 +57,16 @@ __device__ __forceinline__ double recip(double c) {
   return y;
 }
 
-__global__ void k_coef2d(int n, int pitch, const double* __restrict__ tab,
+__global__ void k_coef2d(int n, int pitch, size_t st, const double* __restrict__ tab,
                          const PotentialParams* __restrict__ pp, Coef2D c) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > n || j > n) return;
   const int s = n + 1;
-  const size_t k = at(i, j, pitch);
+  const int ib = blockIdx.z;
+  tab += (size_t)ib * 8 * s;
+  pp += ib;
+  const size_t k = ib * st + at(i, j, pitch);
   const double cc = tab[i] + tab[4 * s + j];
   c.cC[k] = cc;
   c.cE[k] = tab[s + i] + tab[5 * s + j];
@@ -87,19 +88,21 @@ __device__ __forceinline__ double lop(const Coef2D& c, const double* __restrict_
   return v;
 }
 
-#define INTERIOR_2D                                 \
-  const int i = 1 + blockIdx.x * BX + threadIdx.x;  \
-  const int j = 1 + blockIdx.y * BY + threadIdx.y;  \
-  if (i >= n || j >= n) return;                     \
-  const size_t k = at(i, j, pitch);
+// thread (i, j) of instance ib = blockIdx.z; k is its element index in the batched arrays
+#define INTERIOR_2D                                             \
+  const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;      \
+  const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;      \
+  if (i >= n || j >= n) return;                                 \
+  const int ib = blockIdx.z;                                     \
+  const size_t k = ib * st + at(i, j, pitch);
 
-__global__ void k_apply2d(int n, int pitch, Coef2D c, const double* __restrict__ x,
+__global__ void k_apply2d(int n, int pitch, size_t st, Coef2D c, const double* __restrict__ x,
                           double* __restrict__ y) {
   INTERIOR_2D
   y[k] = lop(c, x, k, pitch);
 }
 
-__global__ void k_mass2d(int n, int pitch, double h2_12, const double* __restrict__ x,
+__global__ void k_mass2d(int n, int pitch, size_t st, double h2_12, const double* __restrict__ x,
                          double* __restrict__ y) {
   INTERIOR_2D
   const double s = ((x[k + 1] + x[k - 1]) + (x[k + pitch] + x[k - pitch])) +
@@ -107,19 +110,19 @@ __global__ void k_mass2d(int n, int pitch, double h2_12, const double* __restric
   y[k] = h2_12 * fma(6.0, x[k], s);
 }
 
-__global__ void k_jacobi2d(int n, int pitch, Coef2D c, const double* __restrict__ f,
+__global__ void k_jacobi2d(int n, int pitch, size_t st, Coef2D c, const double* __restrict__ f,
                            const double* __restrict__ x, double* __restrict__ xo) {
   INTERIOR_2D
   xo[k] = fma(c.dinv[k], f[k] - lop(c, x, k, pitch), x[k]);
 }
 
-__global__ void k_jacobi2d_zero(int n, int pitch, Coef2D c, const double* __restrict__ f,
+__global__ void k_jacobi2d_zero(int n, int pitch, size_t st, Coef2D c, const double* __restrict__ f,
                                 double* __restrict__ xo) {
   INTERIOR_2D
   xo[k] = c.dinv[k] * f[k];
 }
 
-__global__ void k_residual2d(int n, int pitch, Coef2D c, const double* __restrict__ f,
+__global__ void k_residual2d(int n, int pitch, size_t st, Coef2D c, const double* __restrict__ f,
                              const double* __restrict__ x, double* __restrict__ r) {
   INTERIOR_2D
   r[k] = f[k] - lop(c, x, k, pitch);
@@ -127,30 +130,33 @@ __global__ void k_residual2d(int n, int pitch, Coef2D c, const double* __restric
 
 // r_c = P^T r_f: a coarse node takes its own fine value plus half of the six fine nodes on
 // the coarse edges through it (the (1,1)-diagonal edges included).
-__global__ void k_restrict2d(int nc, int pc, int pf, const double* __restrict__ rf,
-                             double* __restrict__ rc) {
-  const int I = 1 + blockIdx.x * BX + threadIdx.x;
-  const int J = 1 + blockIdx.y * BY + threadIdx.y;
+__global__ void k_restrict2d(int nc, int pc, int pf, size_t stc, size_t stf,
+                             const double* __restrict__ rf, double* __restrict__ rc) {
+  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nc || J >= nc) return;
-  const size_t kf = at(2 * I, 2 * J, pf);
+  const int ib = blockIdx.z;
+  const size_t kf = ib * stf + at(2 * I, 2 * J, pf);
   const double s = ((rf[kf + 1] + rf[kf - 1]) + (rf[kf + pf] + rf[kf - pf])) +
                    (rf[kf + pf + 1] + rf[kf - pf - 1]);
-  rc[at(I, J, pc)] = fma(0.5, s, rf[kf]);
+  rc[ib * stc + at(I, J, pc)] = fma(0.5, s, rf[kf]);
 }
 
 // x_f (+)= P e_c (+ scale * extra): fine node (2I+a, 2J+b) is the midpoint of coarse nodes
 // (I,J) and (I+a, J+b), a, b in {0,1}.
-__global__ void k_prolong2d(int nf, int pf, int pc, const double* __restrict__ ec,
-                            double* __restrict__ xf, int add, const double* __restrict__ extra,
-                            const double* __restrict__ scale) {
+// scale[ib * scale_stride] is instance ib's factor.
+__global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
+                            const double* __restrict__ ec, double* __restrict__ xf, int add,
+                            const double* __restrict__ extra, const double* __restrict__ scale,
+                            int scale_stride) {
   const int n = nf, pitch = pf;
   INTERIOR_2D
-  const int a = i & 1, b = j & 1;
-  const size_t kc = at(i >> 1, j >> 1, pc);
+  const int ai = i & 1, aj = j & 1;
+  const size_t kc = ib * stc + at(i >> 1, j >> 1, pc);
   double e = ec[kc];
-  if (a | b) e = 0.5 * (e + ec[kc + a + (size_t)b * pc]);
+  if (ai | aj) e = 0.5 * (e + ec[kc + ai + (size_t)aj * pc]);
   if (add) e += xf[k];
-  if (extra) e = fma(scale[0], extra[k], e);
+  if (extra) e = fma(scale[(size_t)ib * scale_stride], extra[k], e);
   xf[k] = e;
 }
 
@@ -190,36 +196,37 @@ __device__ __forceinline__ double nload_at(const double* __restrict__ u, size_t 
   return v + qq;
 }
 
-__global__ void k_nload2d(int n, int pitch, double scale, const double* __restrict__ u,
+__global__ void k_nload2d(int n, int pitch, size_t st, double scale, const double* __restrict__ u,
                           double* __restrict__ out) {
   INTERIOR_2D
   out[k] = scale * nload_at(u, k, pitch);
 }
 
-__global__ void k_rhs2d(int n, int pitch, double h2_12, double h2_120,
+__global__ void k_rhs2d(int n, int pitch, size_t st, double h2_12, double h2_120,
                         const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
                         const double* __restrict__ u, double* __restrict__ f) {
   INTERIOR_2D
-  const double nscale = pp->zeta * h2_120;
+  const double nscale = pp[ib].zeta * h2_120;
   const double s = ((u[k + 1] + u[k - 1]) + (u[k + pitch] + u[k - pitch])) +
                    (u[k + pitch + 1] + u[k - pitch - 1]);
   const double mu = h2_12 * fma(6.0, u[k], s);
-  f[k] = fma(lam[0], mu, -nscale * nload_at(u, k, pitch));
+  f[k] = fma(lam[ib], mu, -nscale * nload_at(u, k, pitch));
 }
 
-__global__ void k_dense_level1_2d(int n, int pitch, double h2_12, Coef2D c, double* L,
-                                  double* M) {
+__global__ void k_dense_level1_2d(int n, int pitch, size_t st, double h2_12, Coef2D c,
+                                  double* L, double* M) {
   const int m = n - 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m * m) return;
   const int i = 1 + p % m, j = 1 + p / m;
-  double* lr = L + (size_t)p * m * m;
-  double* mr = M + (size_t)p * m * m;
+  const size_t nn = (size_t)m * m * m * m;
+  double* lr = L + blockIdx.y * nn + (size_t)p * m * m;
+  double* mr = M + blockIdx.y * nn + (size_t)p * m * m;
   for (int q = 0; q < m * m; ++q) {
     lr[q] = 0.0;
     mr[q] = 0.0;
   }
-  const size_t k = at(i, j, pitch);
+  const size_t k = blockIdx.y * st + at(i, j, pitch);
   lr[p] = c.cC[k];
   mr[p] = 6.0 * h2_12;
   auto put = [&](int di, int dj, double v) {
@@ -237,78 +244,87 @@ __global__ void k_dense_level1_2d(int n, int pitch, double h2_12, Coef2D c, doub
   put(-1, -1, c.cNE[k - pitch - 1]);
 }
 
-__global__ void k_start2d(int n, double* c) {
+__global__ void k_start2d(int n, double* c, int cstride) {
   const int m = n - 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m * m) return;
   const int i = 1 + p % m, j = 1 + p / m;
-  c[p] = sinpi((double)i / n) * sinpi((double)j / n);
+  c[(size_t)blockIdx.y * cstride + p] = sinpi((double)i / n) * sinpi((double)j / n);
 }
 
-dim3 grid_of(int count_x, int count_y) {
-  return dim3((count_x + BX - 1) / BX, (count_y + BY - 1) / BY);
+// launch shape over count_x x count_y nodes of every instance of g
+dim3 grid_of(const Grid& g, int count_x, int count_y) {
+  return dim3((count_x + g.bx - 1) / g.bx, (count_y + g.by - 1) / g.by, g.nb);
 }
+dim3 block_of(const Grid& g) { return dim3(g.bx, g.by); }
 
 }  // namespace
 
 void coef2d_setup(const Grid& g, const PotentialParams* p, const Coef2D& c, cudaStream_t s) {
-  k_coef1d<<<(g.n + 1 + 127) / 128, 128, 0, s>>>(g.n, g.h, p, c.tab);
-  k_coef2d<<<grid_of(g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c.tab, p, c);
+  k_coef1d<<<dim3((g.n + 1 + 127) / 128, g.nb), 128, 0, s>>>(g.n, g.h, p, c.tab);
+  k_coef2d<<<grid_of(g, g.n + 1, g.n + 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride, c.tab,
+                                                                 p, c);
 }
 
 void apply2d(const Grid& g, const Coef2D& c, const double* x, double* y, cudaStream_t s) {
-  k_apply2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, x, y);
+  k_apply2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride, c, x,
+                                                                  y);
 }
 
 void mass2d(const Grid& g, const double* x, double* y, cudaStream_t s) {
-  k_mass2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, g.h * g.h / 12.0,
-                                                              x, y);
+  k_mass2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride,
+                                                                 g.h * g.h / 12.0, x, y);
 }
 
 void jacobi2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* xo,
               bool x_is_zero, cudaStream_t s) {
   if (x_is_zero)
-    k_jacobi2d_zero<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, xo);
+    k_jacobi2d_zero<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride,
+                                                                          c, f, xo);
   else
-    k_jacobi2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x, xo);
+    k_jacobi2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride, c,
+                                                                     f, x, xo);
 }
 
 void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* r,
                 cudaStream_t s) {
-  k_residual2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x, r);
+  k_residual2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride, c,
+                                                                     f, x, r);
 }
 
 void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s) {
-  k_restrict2d<<<grid_of(coarse.n - 1, coarse.n - 1), dim3(BX, BY), 0, s>>>(
-      coarse.n, coarse.pitch, fine.pitch, rf, rc);
+  k_restrict2d<<<grid_of(fine, coarse.n - 1, coarse.n - 1), block_of(fine), 0, s>>>(
+      coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, rf, rc);
 }
 
 void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
-               const double* extra, const double* scale, cudaStream_t s) {
-  k_prolong2d<<<grid_of(fine.n - 1, fine.n - 1), dim3(BX, BY), 0, s>>>(
-      fine.n, fine.pitch, coarse.pitch, ec, xf, add ? 1 : 0, extra, scale);
+               const double* extra, const double* scale, int scale_stride, cudaStream_t s) {
+  k_prolong2d<<<grid_of(fine, fine.n - 1, fine.n - 1), block_of(fine), 0, s>>>(
+      fine.n, fine.pitch, coarse.pitch, fine.stride, coarse.stride, ec, xf, add ? 1 : 0, extra,
+      scale, scale_stride);
 }
 
 void nload2d(const Grid& g, const double* u, double* out, cudaStream_t s) {
-  k_nload2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch,
-                                                               g.h * g.h / 120.0, u, out);
+  k_nload2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride,
+                                                                  g.h * g.h / 120.0, u, out);
 }
 
 void rhs2d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
            double* f, cudaStream_t s) {
-  k_rhs2d<<<grid_of(g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(
-      g.n, g.pitch, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
+  k_rhs2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
+      g.n, g.pitch, g.stride, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
 }
 
 void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s) {
   const int m = g.n - 1;
-  k_dense_level1_2d<<<(m * m + 63) / 64, 64, 0, s>>>(g.n, g.pitch, g.h * g.h / 12.0, c, L, M);
+  k_dense_level1_2d<<<dim3((m * m + 63) / 64, g.nb), 64, 0, s>>>(g.n, g.pitch, g.stride,
+                                                                 g.h * g.h / 12.0, c, L, M);
 }
 
-void start_vector(const Grid& g, double /*box_len*/, double* c, cudaStream_t s) {
+void start_vector(const Grid& g, double* c, int cstride, cudaStream_t s) {
   const int m = g.n - 1;
-  k_start2d<<<(m * m + 63) / 64, 64, 0, s>>>(g.n, c);
+  k_start2d<<<dim3((m * m + 63) / 64, g.nb), 64, 0, s>>>(g.n, c, cstride);
 }
 
 }  // namespace fmg

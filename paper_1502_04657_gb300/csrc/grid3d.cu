@@ -17,9 +17,6 @@
 namespace fmg {
 namespace {
 
-constexpr int BX = 32;
-constexpr int BY = 8;
-
 // neighbour k = 2 d + (0: +d, 1: -d), d = X, Y, Z, XY, XZ, YZ, XYZ
 __device__ constexpr int kDir[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0},
                                        {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
@@ -31,22 +28,20 @@ __device__ constexpr int kStar[24][3] = {
     {1, 2, 10},  {1, 4, 10},  {9, 5, 2},   {9, 1, 2},   {7, 3, 4},   {7, 1, 4},
     {13, 11, 5}, {13, 11, 3}, {13, 9, 5},  {13, 9, 1},  {13, 7, 3},  {13, 7, 1}};
 
-struct Idx3 {
-  size_t p;      // linear index of the node
-  long off[7];   // linear offset of +d
-};
-
 __device__ __forceinline__ long dir_off(int d, int pitch, long plane) {
   return kDir[d][0] + (long)kDir[d][1] * pitch + (long)kDir[d][2] * plane;
 }
 
+// blockIdx.z = ib * (n - 1) + (l - 1): plane l of instance ib; k is the element index of node
+// (i, j, l) of instance ib in the batched arrays
 #define INTERIOR_3D                                                       \
-  const int i = 1 + blockIdx.x * BX + threadIdx.x;                        \
-  const int j = 1 + blockIdx.y * BY + threadIdx.y;                        \
-  const int l = 1 + blockIdx.z;                                           \
-  if (i >= n || j >= n || l >= n) return;                                 \
+  const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;                \
+  const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;                \
+  const int ib = blockIdx.z / (n - 1);                                     \
+  const int l = 1 + (int)blockIdx.z - ib * (n - 1);                        \
+  if (i >= n || j >= n) return;                                           \
   const long plane = (long)(n + 1) * pitch;                               \
-  const size_t k = (size_t)l * plane + (size_t)j * pitch + i;
+  const size_t k = ib * st + (size_t)l * plane + (size_t)j * pitch + i;
 
 // tables (n + 1 entries each), per axis a in {x, y, z}, weighted by w_a h^5:
 //   0: C part (42 a^2 + 5)/105, 1: along an axis or the body diagonal (63a^2+63a+19)/1260,
@@ -56,7 +51,8 @@ __global__ void k_coef1d_3d(int n, double h, const PotentialParams* __restrict__
                             double* __restrict__ tab) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x > n) return;
-  const PotentialParams p = *pp;
+  const PotentialParams p = pp[blockIdx.y];
+  tab += (size_t)blockIdx.y * 15 * (n + 1);
   const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
   const double h2 = h * h, h5 = h2 * h2 * h;
   const double a = x;
@@ -76,19 +72,21 @@ __device__ __forceinline__ double recip(double c) {
   return y;
 }
 
-__global__ void k_coef3d(int n, int pitch, double h, const double* __restrict__ tab,
+__global__ void k_coef3d(int n, int pitch, size_t st, double h, const double* __restrict__ tab,
                          const PotentialParams* __restrict__ pp, Coef3D c) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int l = blockIdx.z;
-  if (i > n || j > n || l > n) return;
-  const PotentialParams p = *pp;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ib = blockIdx.z / (n + 1);
+  const int l = (int)blockIdx.z - ib * (n + 1);
+  if (i > n || j > n) return;
+  const PotentialParams p = pp[ib];
+  tab += (size_t)ib * 15 * (n + 1);
   const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
   const double h3 = h * h * h;
   const int s = n + 1;
   const int co[3] = {i, j, l};
   auto T = [&](int ax, int q) { return tab[(ax * 5 + q) * s + co[ax]]; };
-  const size_t k = ((size_t)l * (n + 1) + j) * pitch + i;
+  const size_t k = ib * st + ((size_t)l * (n + 1) + j) * pitch + i;
   const double cc = 6.0 * h + wl * 0.4 * h3 * p.w0 + T(0, 0) + T(1, 0) + T(2, 0);
   c.a[0][k] = cc;
   // axis directions: along = table 1 on that axis, across = table 2 on the others
@@ -120,25 +118,25 @@ __device__ __forceinline__ double lop3(const Coef3D& c, const double* __restrict
   return v;
 }
 
-__global__ void k_apply3d(int n, int pitch, Coef3D c, const double* __restrict__ x,
+__global__ void k_apply3d(int n, int pitch, size_t st, Coef3D c, const double* __restrict__ x,
                           double* __restrict__ y) {
   INTERIOR_3D
   y[k] = lop3(c, x, k, pitch, plane);
 }
 
-__global__ void k_jacobi3d(int n, int pitch, Coef3D c, const double* __restrict__ f,
+__global__ void k_jacobi3d(int n, int pitch, size_t st, Coef3D c, const double* __restrict__ f,
                            const double* __restrict__ x, double* __restrict__ xo) {
   INTERIOR_3D
   xo[k] = fma(c.dinv[k], f[k] - lop3(c, x, k, pitch, plane), x[k]);
 }
 
-__global__ void k_jacobi3d_zero(int n, int pitch, Coef3D c, const double* __restrict__ f,
+__global__ void k_jacobi3d_zero(int n, int pitch, size_t st, Coef3D c, const double* __restrict__ f,
                                 double* __restrict__ xo) {
   INTERIOR_3D
   xo[k] = c.dinv[k] * f[k];
 }
 
-__global__ void k_residual3d(int n, int pitch, Coef3D c, const double* __restrict__ f,
+__global__ void k_residual3d(int n, int pitch, size_t st, Coef3D c, const double* __restrict__ f,
                              const double* __restrict__ x, double* __restrict__ r) {
   INTERIOR_3D
   r[k] = f[k] - lop3(c, x, k, pitch, plane);
@@ -157,45 +155,48 @@ __device__ __forceinline__ double mass_at(const double* __restrict__ x, size_t k
   return fma(0.4, x[k], fma(1.0 / 20.0, ax, fd / 30.0));
 }
 
-__global__ void k_mass3d(int n, int pitch, double h3, const double* __restrict__ x,
+__global__ void k_mass3d(int n, int pitch, size_t st, double h3, const double* __restrict__ x,
                          double* __restrict__ y) {
   INTERIOR_3D
   y[k] = h3 * mass_at(x, k, pitch, plane);
 }
 
 // r_c = P^T r_f: own fine value plus half of the 14 fine neighbours along the mesh edges.
-__global__ void k_restrict3d(int nc, int pc, int pf, const double* __restrict__ rf,
-                             double* __restrict__ rc) {
-  const int I = 1 + blockIdx.x * BX + threadIdx.x;
-  const int J = 1 + blockIdx.y * BY + threadIdx.y;
-  const int L = 1 + blockIdx.z;
-  if (I >= nc || J >= nc || L >= nc) return;
+__global__ void k_restrict3d(int nc, int pc, int pf, size_t stc, size_t stf,
+                             const double* __restrict__ rf, double* __restrict__ rc) {
+  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  const int ib = blockIdx.z / (nc - 1);
+  const int L = 1 + (int)blockIdx.z - ib * (nc - 1);
+  if (I >= nc || J >= nc) return;
   const long planef = (long)(2 * nc + 1) * pf;
-  const size_t kf = (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
+  const size_t kf = ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
   double s = 0.0;
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pf, planef);
     s += rf[kf + o] + rf[kf - o];
   }
-  rc[((size_t)L * (nc + 1) + J) * pc + I] = fma(0.5, s, rf[kf]);
+  rc[ib * stc + ((size_t)L * (nc + 1) + J) * pc + I] = fma(0.5, s, rf[kf]);
 }
 
 // x_f (+)= P e_c (+ scale * extra): fine node 2I + a (a in {0,1}^3) is the midpoint of coarse
 // nodes I and I + a, which are joined by a mesh edge.
-__global__ void k_prolong3d(int nf, int pf, int pc, const double* __restrict__ ec,
-                            double* __restrict__ xf, int add, const double* __restrict__ extra,
-                            const double* __restrict__ scale) {
+// scale[ib * scale_stride] is instance ib's factor.
+__global__ void k_prolong3d(int nf, int pf, int pc, size_t st, size_t stc,
+                            const double* __restrict__ ec, double* __restrict__ xf, int add,
+                            const double* __restrict__ extra, const double* __restrict__ scale,
+                            int scale_stride) {
   const int n = nf, pitch = pf;
   INTERIOR_3D
-  const int a = i & 1, b = j & 1, cc = l & 1;
+  const int ai = i & 1, aj = j & 1, al = l & 1;
   const int nc = nf / 2;
   const long planec = (long)(nc + 1) * pc;
-  const size_t kc = (size_t)(l >> 1) * planec + (size_t)(j >> 1) * pc + (i >> 1);
+  const size_t kc = ib * stc + (size_t)(l >> 1) * planec + (size_t)(j >> 1) * pc + (i >> 1);
   double e = ec[kc];
-  if (a | b | cc) e = 0.5 * (e + ec[kc + a + (size_t)b * pc + (size_t)cc * planec]);
+  if (ai | aj | al) e = 0.5 * (e + ec[kc + ai + (size_t)aj * pc + (size_t)al * planec]);
   if (add) e += xf[k];
-  if (extra) e = fma(scale[0], extra[k], e);
+  if (extra) e = fma(scale[(size_t)ib * scale_stride], extra[k], e);
   xf[k] = e;
 }
 
@@ -249,7 +250,7 @@ __device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, in
   }
 }
 
-__global__ void k_nload3d(int n, int pitch, double scale, const double* __restrict__ u,
+__global__ void k_nload3d(int n, int pitch, size_t st, double scale, const double* __restrict__ u,
                           double* __restrict__ out) {
   INTERIOR_3D
   double nl;
@@ -257,17 +258,17 @@ __global__ void k_nload3d(int n, int pitch, double scale, const double* __restri
   out[k] = scale * nl;
 }
 
-__global__ void k_rhs3d(int n, int pitch, double h3, double nscale,
+__global__ void k_rhs3d(int n, int pitch, size_t st, double h3, double nscale,
                         const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
                         const double* __restrict__ u, double* __restrict__ f) {
   INTERIOR_3D
   double nl;
   star3<false>(u, k, pitch, plane, nl, nullptr);
   const double mu = h3 * mass_at(u, k, pitch, plane);
-  f[k] = fma(lam[0], mu, -(pp->zeta * nscale) * nl);
+  f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * nl);
 }
 
-__global__ void k_nload_density3d(int n, int pitch, double vol, const double* __restrict__ u,
+__global__ void k_nload_density3d(int n, int pitch, size_t st, double vol, const double* __restrict__ u,
                                   double* __restrict__ nl, Density3D b) {
   INTERIOR_3D
   double v, e[8];
@@ -326,14 +327,16 @@ __device__ __forceinline__ double coarse_entry3(const Density3D& f, size_t kf, i
   return acc;
 }
 
-__global__ void k_coarsen_density3d(int nc, int pc, int pf, Density3D f, Density3D c) {
-  const int I = 1 + blockIdx.x * BX + threadIdx.x;
-  const int J = 1 + blockIdx.y * BY + threadIdx.y;
-  const int L = 1 + blockIdx.z;
-  if (I >= nc || J >= nc || L >= nc) return;
+__global__ void k_coarsen_density3d(int nc, int pc, int pf, size_t stc, size_t stf,
+                                    Density3D f, Density3D c) {
+  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  const int ib = blockIdx.z / (nc - 1);
+  const int L = 1 + (int)blockIdx.z - ib * (nc - 1);
+  if (I >= nc || J >= nc) return;
   const long planef = (long)(2 * nc + 1) * pf;
-  const size_t kf = (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
-  const size_t kc = ((size_t)L * (nc + 1) + J) * pc + I;
+  const size_t kf = ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
+  const size_t kc = ib * stc + ((size_t)L * (nc + 1) + J) * pc + I;
   c.a[0][kc] = coarse_entry3<0>(f, kf, pf, planef);
   // couplings to coarse neighbours outside the interior are never read: skip them
   if (I + 1 < nc) c.a[1][kc] = coarse_entry3<1>(f, kf, pf, planef);
@@ -346,23 +349,25 @@ __global__ void k_coarsen_density3d(int nc, int pc, int pf, Density3D f, Density
 }
 
 // dense level-1 matrices from a 15-point stencil given per node as (C, +d couplings)
-__global__ void k_dense15(int n, int pitch, Stencil15 st, int use_stencil, double* out,
-                          double mass_h3) {
+__global__ void k_dense15(int n, int pitch, size_t vst, Stencil15 st, int use_stencil,
+                          double* out, double mass_h3) {
   const double* const* a = use_stencil ? st.a : nullptr;
   const int m = n - 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m * m * m) return;
   const int i = 1 + p % m, j = 1 + (p / m) % m, l = 1 + p / (m * m);
   const long plane = (long)(n + 1) * pitch;
-  const size_t k = (size_t)l * plane + (size_t)j * pitch + i;
-  double* row = out + (size_t)p * m * m * m;
+  const size_t base = blockIdx.y * vst;
+  const size_t k = base + (size_t)l * plane + (size_t)j * pitch + i;
+  const size_t nh = (size_t)m * m * m;
+  double* row = out + blockIdx.y * nh * nh + (size_t)p * nh;
   for (int q = 0; q < m * m * m; ++q) row[q] = 0.0;
   row[p] = a ? a[0][k] : 0.4 * mass_h3;
   for (int d = 0; d < 7; ++d)
     for (int sg = -1; sg <= 1; sg += 2) {
       const int ii = i + sg * kDir[d][0], jj = j + sg * kDir[d][1], ll = l + sg * kDir[d][2];
       if (ii < 1 || jj < 1 || ll < 1 || ii >= n || jj >= n || ll >= n) continue;
-      const size_t kn = (size_t)ll * plane + (size_t)jj * pitch + ii;
+      const size_t kn = base + (size_t)ll * plane + (size_t)jj * pitch + ii;
       double v;
       if (a) v = sg > 0 ? a[1 + d][k] : a[1 + d][kn];
       else v = mass_h3 * ((d >= 3 && d < 6) ? 1.0 / 30.0 : 1.0 / 20.0);
@@ -370,15 +375,15 @@ __global__ void k_dense15(int n, int pitch, Stencil15 st, int use_stencil, doubl
     }
 }
 
-__global__ void k_start3d(int n, double* c) {
+__global__ void k_start3d(int n, double* c, int cstride) {
   const int m = n - 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m * m * m) return;
   const int i = 1 + p % m, j = 1 + (p / m) % m, l = 1 + p / (m * m);
-  c[p] = sinpi((double)i / n) * sinpi((double)j / n) * sinpi((double)l / n);
+  c[(size_t)blockIdx.y * cstride + p] = sinpi((double)i / n) * sinpi((double)j / n) * sinpi((double)l / n);
 }
 
-__global__ void k_gather_vec3d(int n, int pitch, const double* __restrict__ a,
+__global__ void k_gather_vec3d(int n, int pitch, size_t st, const double* __restrict__ a,
                                const double* __restrict__ b, const double* __restrict__ c,
                                double* __restrict__ oa, double* __restrict__ ob,
                                double* __restrict__ oc) {
@@ -386,106 +391,111 @@ __global__ void k_gather_vec3d(int n, int pitch, const double* __restrict__ a,
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m * m * m) return;
   const int i = 1 + p % m, j = 1 + (p / m) % m, l = 1 + p / (m * m);
-  const size_t k = ((size_t)l * (n + 1) + j) * pitch + i;
-  oa[p] = a[k];
-  ob[p] = b[k];
-  oc[p] = c[k];
+  const size_t k = blockIdx.y * st + ((size_t)l * (n + 1) + j) * pitch + i;
+  const size_t q = blockIdx.y * (size_t)m * m * m + p;
+  oa[q] = a[k];
+  ob[q] = b[k];
+  oc[q] = c[k];
 }
 
-dim3 grid3(int cx, int cy, int cz) { return dim3((cx + BX - 1) / BX, (cy + BY - 1) / BY, cz); }
+// launch shape over cx x cy x cz nodes of every instance of g (planes and instances share z)
+dim3 grid3(const Grid& g, int cx, int cy, int cz) {
+  return dim3((cx + g.bx - 1) / g.bx, (cy + g.by - 1) / g.by, cz * g.nb);
+}
+dim3 block3(const Grid& g) { return dim3(g.bx, g.by); }
 
 }  // namespace
 
 void coef3d_setup(const Grid& g, const PotentialParams* p, const Coef3D& c, cudaStream_t s) {
-  k_coef1d_3d<<<(g.n + 1 + 127) / 128, 128, 0, s>>>(g.n, g.h, p, c.tab);
-  k_coef3d<<<grid3(g.n + 1, g.n + 1, g.n + 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, g.h, c.tab, p, c);
+  k_coef1d_3d<<<dim3((g.n + 1 + 127) / 128, g.nb), 128, 0, s>>>(g.n, g.h, p, c.tab);
+  k_coef3d<<<grid3(g, g.n + 1, g.n + 1, g.n + 1), block3(g), 0, s>>>(g.n, g.pitch, g.stride, g.h,
+                                                                      c.tab, p, c);
 }
 
+#define INTERIOR_LAUNCH(g) grid3(g, g.n - 1, g.n - 1, g.n - 1), block3(g), 0, s
+
 void apply3d(const Grid& g, const Coef3D& c, const double* x, double* y, cudaStream_t s) {
-  k_apply3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, x, y);
+  k_apply3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, x, y);
 }
 
 void mass3d(const Grid& g, const double* x, double* y, cudaStream_t s) {
-  k_mass3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch,
-                                                                     g.h * g.h * g.h, x, y);
+  k_mass3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, g.h * g.h * g.h, x, y);
 }
 
 void jacobi3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* xo,
               bool x_is_zero, cudaStream_t s) {
-  if (x_is_zero)
-    k_jacobi3d_zero<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f,
-                                                                              xo);
-  else
-    k_jacobi3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x,
-                                                                         xo);
+  if (x_is_zero) k_jacobi3d_zero<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, f, xo);
+  else k_jacobi3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, f, x, xo);
 }
 
 void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* r,
                 cudaStream_t s) {
-  k_residual3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, c, f, x, r);
+  k_residual3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, f, x, r);
 }
 
 void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s) {
-  k_restrict3d<<<grid3(coarse.n - 1, coarse.n - 1, coarse.n - 1), dim3(BX, BY), 0, s>>>(
-      coarse.n, coarse.pitch, fine.pitch, rf, rc);
+  k_restrict3d<<<grid3(fine, coarse.n - 1, coarse.n - 1, coarse.n - 1), block3(fine), 0, s>>>(
+      coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, rf, rc);
 }
 
 void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
-               const double* extra, const double* scale, cudaStream_t s) {
-  k_prolong3d<<<grid3(fine.n - 1, fine.n - 1, fine.n - 1), dim3(BX, BY), 0, s>>>(
-      fine.n, fine.pitch, coarse.pitch, ec, xf, add ? 1 : 0, extra, scale);
+               const double* extra, const double* scale, int scale_stride, cudaStream_t s) {
+  k_prolong3d<<<INTERIOR_LAUNCH(fine)>>>(fine.n, fine.pitch, coarse.pitch, fine.stride,
+                                         coarse.stride, ec, xf, add ? 1 : 0, extra, scale,
+                                         scale_stride);
 }
 
 void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s) {
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, vol / 140.0,
-                                                                      u, out);
+  k_nload3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, vol / 140.0, u, out);
 }
 
 void rhs3d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
            double* f, cudaStream_t s) {
   const double h3 = g.h * g.h * g.h;
-  k_rhs3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(g.n, g.pitch, h3,
-                                                                    h3 / 6.0 / 140.0, lam, p, u, f);
+  k_rhs3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, h3, h3 / 6.0 / 140.0, lam, p, u, f);
 }
 
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s) {
-  k_nload_density3d<<<grid3(g.n - 1, g.n - 1, g.n - 1), dim3(BX, BY), 0, s>>>(
-      g.n, g.pitch, g.h * g.h * g.h / 6.0, u, nl, b);
+  k_nload_density3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, g.h * g.h * g.h / 6.0, u,
+                                            nl, b);
 }
 
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,
                        const Density3D& bc, cudaStream_t s) {
-  k_coarsen_density3d<<<grid3(coarse.n - 1, coarse.n - 1, coarse.n - 1), dim3(BX, BY), 0, s>>>(
-      coarse.n, coarse.pitch, fine.pitch, bf, bc);
+  k_coarsen_density3d<<<grid3(fine, coarse.n - 1, coarse.n - 1, coarse.n - 1), block3(fine), 0,
+                        s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, bf,
+                             bc);
 }
 
 void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaStream_t s) {
   const int m = g.n - 1, cnt = m * m * m;
   Stencil15 st;
   for (int q = 0; q < 8; ++q) st.a[q] = c.a[q];
-  k_dense15<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, st, 1, L, 0.0);
-  k_dense15<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, st, 0, M, g.h * g.h * g.h);
+  const dim3 grid((cnt + 63) / 64, g.nb);
+  k_dense15<<<grid, 64, 0, s>>>(g.n, g.pitch, g.stride, st, 1, L, 0.0);
+  k_dense15<<<grid, 64, 0, s>>>(g.n, g.pitch, g.stride, st, 0, M, g.h * g.h * g.h);
 }
 
 void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s) {
   const int m = g.n - 1, cnt = m * m * m;
   Stencil15 st;
   for (int q = 0; q < 8; ++q) st.a[q] = b.a[q];
-  k_dense15<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, st, 1, B, 0.0);
+  k_dense15<<<dim3((cnt + 63) / 64, g.nb), 64, 0, s>>>(g.n, g.pitch, g.stride, st, 1, B, 0.0);
 }
 
 void gather_vec3d(const Grid& g, const double* a, const double* b, const double* c, double* oa,
                   double* ob, double* oc, cudaStream_t s) {
   const int m = g.n - 1, cnt = m * m * m;
-  k_gather_vec3d<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, g.pitch, a, b, c, oa, ob, oc);
+  k_gather_vec3d<<<dim3((cnt + 63) / 64, g.nb), 64, 0, s>>>(g.n, g.pitch, g.stride, a, b, c, oa,
+                                                            ob, oc);
 }
 
-void start_vector3d(const Grid& g, double* c, cudaStream_t s) {
+void start_vector3d(const Grid& g, double* c, int cstride, cudaStream_t s) {
   const int m = g.n - 1, cnt = m * m * m;
-  k_start3d<<<(cnt + 63) / 64, 64, 0, s>>>(g.n, c);
+  k_start3d<<<dim3((cnt + 63) / 64, g.nb), 64, 0, s>>>(g.n, c, cstride);
 }
 
 }  // namespace fmg

@@ -189,8 +189,8 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   }
   coef2d_setup(g, d.params, c, s);
   dense_level1_2d(g, c, L1, M1, s);
-  start_vector(g, prob->box_len, cstart, s);
-  dense_scf(d, s);
+  start_vector(g, cstart, nh + 1, s);
+  dense_scf(d, 1, s);
   double lam_h = 0.0;
   int st[2] = {1, 0};
   if (cudaMemcpyAsync(&lam_h, lam, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -13,34 +13,38 @@ __device__ __forceinline__ size_t padded_index(int dim, int n, int pitch, size_t
   return (l * (size_t)(n + 1) + j) * pitch + i;
 }
 
-__global__ void k_pack(int dim, int n, int pitch, size_t count, const double* __restrict__ in,
-                       double* __restrict__ out) {
+// instance blockIdx.y: interior vector at blockIdx.y * ist, padded one at blockIdx.y * pst
+__global__ void k_pack(int dim, int n, int pitch, size_t count, size_t ist, size_t pst,
+                       const double* __restrict__ in, double* __restrict__ out) {
   const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (p < count) out[padded_index(dim, n, pitch, p)] = in[p];
+  if (p < count) out[blockIdx.y * pst + padded_index(dim, n, pitch, p)] = in[blockIdx.y * ist + p];
 }
 
-__global__ void k_unpack(int dim, int n, int pitch, size_t count, const double* __restrict__ in,
-                         double* __restrict__ out) {
+__global__ void k_unpack(int dim, int n, int pitch, size_t count, size_t ist, size_t pst,
+                         const double* __restrict__ in, double* __restrict__ out) {
   const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (p < count) out[p] = in[padded_index(dim, n, pitch, p)];
+  if (p < count) out[blockIdx.y * ist + p] = in[blockIdx.y * pst + padded_index(dim, n, pitch, p)];
 }
 
 }  // namespace
 
 void pack_interior(const Grid& g, const double* interior, double* padded, cudaStream_t s) {
   const size_t count = g.interior();
-  k_pack<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(g.dim, g.n, g.pitch, count, interior,
-                                                         padded);
+  k_pack<<<dim3((unsigned)((count + 255) / 256), g.nb), 256, 0, s>>>(
+      g.dim, g.n, g.pitch, count, count, g.stride, interior, padded);
 }
 
 void unpack_interior(const Grid& g, const double* padded, double* interior, cudaStream_t s) {
   const size_t count = g.interior();
-  k_unpack<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(g.dim, g.n, g.pitch, count, padded,
-                                                           interior);
+  k_unpack<<<dim3((unsigned)((count + 255) / 256), g.nb), 256, 0, s>>>(
+      g.dim, g.n, g.pitch, count, count, g.stride, padded, interior);
 }
 
-void scatter_level1(const Grid& g, const double* c, double* padded, cudaStream_t s) {
-  pack_interior(g, c, padded, s);
+void scatter_level1(const Grid& g, const double* c, size_t cstride, double* padded,
+                    cudaStream_t s) {
+  const size_t count = g.interior();
+  k_pack<<<dim3((unsigned)((count + 255) / 256), g.nb), 256, 0, s>>>(
+      g.dim, g.n, g.pitch, count, cstride, g.stride, c, padded);
 }
 
 }  // namespace fmg

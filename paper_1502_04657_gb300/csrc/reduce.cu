@@ -17,9 +17,13 @@ __device__ double block_sum(double v, double* sh) {
   return sh[0];
 }
 
+// instance blockIdx.y: a, b at blockIdx.y * vst, partials at blockIdx.y * kReduceBlocks
 __global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b,
-                              size_t n, size_t chunk, double* __restrict__ partials) {
+                              size_t n, size_t vst, size_t chunk, double* __restrict__ partials) {
   __shared__ double sh[kThreads];
+  a += blockIdx.y * vst;
+  b += blockIdx.y * vst;
+  partials += (size_t)blockIdx.y * kReduceBlocks;
   const size_t beg = blockIdx.x * chunk;
   const size_t end = beg + chunk < n ? beg + chunk : n;
   double s = 0.0;
@@ -30,6 +34,8 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
 
 __global__ void k_sum_final(const double* __restrict__ partials, int m, double* out) {
   __shared__ double sh[kThreads];
+  partials += (size_t)blockIdx.x * kReduceBlocks;  // instance blockIdx.x
+  out += blockIdx.x;
   double s = 0.0;
   for (int i = threadIdx.x; i < m; i += kThreads) s += partials[i];
   const double t = block_sum(s, sh);
@@ -39,13 +45,13 @@ __global__ void k_sum_final(const double* __restrict__ partials, int m, double* 
 }  // namespace
 
 void dot(const double* a, const double* b, size_t n, double* partials, double* out,
-         cudaStream_t s) {
+         cudaStream_t s, int nb, size_t vst) {
   size_t blocks = (n + 4 * kThreads - 1) / (4 * kThreads);
   if (blocks > (size_t)kReduceBlocks) blocks = kReduceBlocks;
   if (blocks < 1) blocks = 1;
   const size_t chunk = (n + blocks - 1) / blocks;
-  k_dot_partial<<<(unsigned)blocks, kThreads, 0, s>>>(a, b, n, chunk, partials);
-  k_sum_final<<<1, kThreads, 0, s>>>(partials, (int)blocks, out);
+  k_dot_partial<<<dim3((unsigned)blocks, nb), kThreads, 0, s>>>(a, b, n, vst, chunk, partials);
+  k_sum_final<<<nb, kThreads, 0, s>>>(partials, (int)blocks, out);
 }
 
 }  // namespace fmg

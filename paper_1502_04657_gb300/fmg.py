@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libfmg_eig.so")
 FMG_OK, FMG_EINVAL, FMG_ENOMEM, FMG_ENOCONV, FMG_ECUDA, FMG_ETIMEOUT, FMG_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 FMG_FP64, FMG_MIXED_FP32 = 0, 1
 FMG_W_LEFT, FMG_PAPER_LITERAL = 0, 1
+FMG_FLAG_NO_AUTOTUNE = 1
 FMG_MAX_LEVELS = 16
 
 
@@ -22,7 +23,7 @@ class fmg_eig_problem(C.Structure):
         ("dim", C.c_int32), ("coarse_cells", C.c_int32), ("levels", C.c_int32),
         ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("vcycles", C.c_int32),
         ("corrections", C.c_int32), ("smoother", C.c_int32), ("precision", C.c_int32),
-        ("operator_form", C.c_int32), ("scf_max_iter", C.c_int32), ("reserved", C.c_int32),
+        ("operator_form", C.c_int32), ("scf_max_iter", C.c_int32), ("flags", C.c_int32),
         ("box_len", C.c_double), ("w_const", C.c_double), ("w_quad", C.c_double * 3),
         ("zeta", C.c_double), ("omega", C.c_double), ("scf_tol", C.c_double),
     ]
@@ -69,6 +70,14 @@ _SIGS = {
     "fmg_eig_coarse_solve": (C.c_int, [_P, _D, _P, C.POINTER(_I32)]),
     "fmg_eig_augmented_system": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _P]),
     "fmg_eig_coarse_solve_noalloc": (C.c_int, [C.POINTER(fmg_eig_problem), _D, _P, C.POINTER(_I32), _P]),
+    "fmg_eig_batch_create": (C.c_int, [C.POINTER(fmg_eig_problem), _I32, C.POINTER(_P)]),
+    "fmg_eig_batch_count": (_I32, [_P]),
+    "fmg_eig_batch_solve": (C.c_int, [_P, _D, C.POINTER(_P), C.POINTER(C.c_size_t),
+                                      C.POINTER(fmg_eig_stats), C.POINTER(_I32)]),
+    "fmg_eig_solve_batch": (C.c_int, [C.POINTER(fmg_eig_problem), _I32, _D, C.POINTER(_P),
+                                      C.POINTER(C.c_size_t), C.POINTER(fmg_eig_stats),
+                                      C.POINTER(_I32)]),
+    "fmg_eig_level_tile": (C.c_int, [_P, _I32, C.POINTER(_I32), C.POINTER(_I32)]),
 }
 
 
@@ -132,12 +141,13 @@ class Problem:
     zeta: float = 1.0
     omega: float = 2.0 / 3.0
     scf_tol: float = 1e-13
+    flags: int = 0
 
     def to_c(self) -> fmg_eig_problem:
         p = fmg_eig_problem()
         for f in ("dim", "coarse_cells", "levels", "nu_pre", "nu_post", "vcycles", "corrections",
                   "precision", "operator_form", "scf_max_iter", "box_len", "w_const", "zeta",
-                  "omega", "scf_tol"):
+                  "omega", "scf_tol", "flags"):
             setattr(p, f, getattr(self, f))
         p.smoother = 0
         p.w_quad[:] = [float(x) for x in self.w_quad]
@@ -187,6 +197,11 @@ class Solver:
 
     def level_size(self, k: int) -> int:
         return self.lib.fmg_eig_level_size(self.h, k)
+
+    def level_tile(self, k: int) -> tuple:
+        bx, by = _I32(), _I32()
+        self._check(self.lib.fmg_eig_level_tile(self.h, k, C.byref(bx), C.byref(by)), "level_tile")
+        return bx.value, by.value
 
     PROFILE_KEYS = ("jacobi", "residual", "restrict", "prolong", "rhs", "nload_density", "dense",
                     "vcycle", "t3", "coef")
@@ -275,3 +290,52 @@ class Solver:
         rc = self.lib.fmg_eig_coarse_solve(self.h, C.byref(lo), _ptr(u_out), C.byref(it))
         self._check(rc, "coarse_solve", allow=(FMG_ENOCONV,))
         return lo.value, it.value, rc
+
+
+def _batch_outputs(problems, with_u, stats):
+    import numpy as np
+    n = len(problems)
+    lams = (C.c_double * n)()
+    us = [np.empty(p.size(p.levels)) for p in problems] if with_u else None
+    ptrs = (_P * n)(*[u.ctypes.data for u in us]) if with_u else None
+    lens = (C.c_size_t * n)(*[u.size for u in us]) if with_u else None
+    st = (fmg_eig_stats * n)() if stats else None
+    codes = (_I32 * n)()
+    return lams, us, ptrs, lens, st, codes
+
+
+class BatchSolver(Solver):
+    """A batch handle (fmg_eig_batch_create): instances that may differ in level count, W and
+    zeta, solved by one CUDA graph with one launch per step and level for all of them."""
+
+    def __init__(self, problems: list):
+        self.lib = load_library()
+        self.problems = list(problems)
+        self.problem = self.problems[0]
+        arr = (fmg_eig_problem * len(self.problems))(*[p.to_c() for p in self.problems])
+        h = _P()
+        rc = self.lib.fmg_eig_batch_create(arr, len(self.problems), C.byref(h))
+        if rc != FMG_OK:
+            raise FmgError(rc, "fmg_eig_batch_create")
+        self.h = h
+
+    def count(self) -> int:
+        return self.lib.fmg_eig_batch_count(self.h)
+
+    def solve_all(self, with_u: bool = True, stats: bool = False):
+        """lambdas (list), u per instance (numpy, or None), stats records (or None), codes."""
+        lams, us, ptrs, lens, st, codes = _batch_outputs(self.problems, with_u, stats)
+        rc = self.lib.fmg_eig_batch_solve(self.h, lams, ptrs, lens, st, codes)
+        self._check(rc, "fmg_eig_batch_solve", allow=(FMG_ENOCONV,))
+        return list(lams), us, (list(st) if stats else None), list(codes)
+
+
+def solve_batch(problems: list, with_u: bool = True, stats: bool = False):
+    """fmg_eig_solve_batch: one-shot batch over problems of any mix of settings."""
+    lib = load_library()
+    arr = (fmg_eig_problem * len(problems))(*[p.to_c() for p in problems])
+    lams, us, ptrs, lens, st, codes = _batch_outputs(problems, with_u, stats)
+    rc = lib.fmg_eig_solve_batch(arr, len(problems), lams, ptrs, lens, st, codes)
+    if rc not in (FMG_OK, FMG_ENOCONV):
+        raise FmgError(rc, "fmg_eig_solve_batch")
+    return list(lams), us, (list(st) if stats else None), list(codes)
