@@ -156,12 +156,71 @@ int32_t fmg_eig_batch_count(const fmg_eig_handle* h);
 int fmg_eig_batch_solve(fmg_eig_handle* h, double* lambdas, double* const* u_hosts,
                         const size_t* u_lens, fmg_eig_stats* stats, int32_t* statuses);
 
+/* Device-side batch solve without host synchronisation: lambdas_dev (count doubles, device,
+ * caller's order) is written in stream order on `stream` (NULL = the handle's stream).    */
+int fmg_eig_batch_solve_dev(fmg_eig_handle* h, double* lambdas_dev, void* stream);
+
 /* One-shot batch: groups probs by the fields that must agree, creates one batch handle per
  * group, runs the groups concurrently on their own streams, writes the outputs as
  * fmg_eig_batch_solve does (in the caller's order) and releases everything.              */
 int fmg_eig_solve_batch(const fmg_eig_problem* probs, int32_t count, double* lambdas,
                         double* const* u_hosts, const size_t* u_lens, fmg_eig_stats* stats,
                         int32_t* statuses);
+
+/* ------------------------------------------------------------------------------------------
+ * Serving (no counterpart in the paper): a stream of independent solve requests, each with an
+ * arrival time, served with continuous batching on one GPU.  Requests that have arrived are
+ * admitted as a cohort (one batch handle: every step of each level one launch for all of
+ * them) as soon as fewer than max_inflight cohorts are resident and the cohort's hierarchy
+ * fits the device-memory budget; each cohort runs on its own stream, so newly admitted
+ * cohorts overlap with the ones already on the GPU.  Hierarchies stay resident in device
+ * memory until their cohort finishes and are then released (stream-ordered) for new ones.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct fmg_eig_serve_config {
+  double hbm_budget_bytes; /* device bytes for resident hierarchies; <= 0: 80% of free    */
+  double batch_window_s;   /* a queued request waits at most this long for others to join */
+  int32_t max_batch;       /* instances per cohort (>= 1)                                 */
+  int32_t max_inflight;    /* cohorts resident at once (>= 1)                             */
+} fmg_eig_serve_config;
+
+typedef struct fmg_eig_request {
+  fmg_eig_problem problem;
+  double arrival_s; /* seconds after the start of the fmg_eig_serve call (non-decreasing)  */
+  double* u;        /* nullable host buffer for u (u_len doubles, the finest level size)   */
+  size_t u_len;
+} fmg_eig_request;
+
+typedef struct fmg_eig_result {
+  double lambda;
+  double latency_s; /* arrival -> lambda copied to host memory (GPU clock of that copy)    */
+  double admit_s;   /* when its cohort was admitted, seconds after the start              */
+  double done_s;    /* arrival_s + latency_s                                              */
+  int32_t status;   /* FMG_OK, FMG_ENOCONV, or an error code of its cohort                */
+  int32_t cohort;   /* index of the cohort it ran in                                      */
+} fmg_eig_result;
+
+typedef struct fmg_eig_serve_stats {
+  double p50_s, p99_s, mean_s, max_s; /* latency percentiles (nearest rank)               */
+  double solves_per_s;                /* requests / (last done - first arrival)           */
+  double makespan_s;                  /* last done - first arrival                        */
+  double peak_bytes;                  /* most device bytes held by resident hierarchies   */
+  double budget_bytes;                /* the budget admission used                        */
+  int32_t cohorts;                    /* cohorts admitted                                 */
+  int32_t max_cohort;                 /* largest cohort                                   */
+  int32_t max_inflight_seen;          /* most cohorts resident at once                    */
+  int32_t completed;                  /* requests with a result                           */
+} fmg_eig_serve_stats;
+
+/* Device bytes a batch handle for probs[0 .. count-1] allocates (an upper bound; 0 for bad
+ * arguments).  The server admits cohorts against its budget with these figures.          */
+size_t fmg_eig_estimate_bytes(const fmg_eig_problem* probs, int32_t count);
+
+/* Serve reqs[0 .. n-1] (arrival order) and return when every request has a result.  Each
+ * result is the request's solve alone (a cohort changes which launches an instance shares,
+ * not its arithmetic).  Returns FMG_OK, FMG_ENOCONV when some request did not converge,
+ * FMG_EINVAL for bad arguments (a request that can never fit the budget included).         */
+int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_request* reqs, int32_t n,
+                  fmg_eig_result* results, fmg_eig_serve_stats* stats);
 
 /* Thread-block shape (x, y threads) the handle uses for the stencil kernels of level k,
  * as chosen by the autotuner when the handle was created.                                 */

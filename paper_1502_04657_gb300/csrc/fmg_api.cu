@@ -18,30 +18,12 @@
 #include <tuple>
 #include <vector>
 
-#include "fmg_internal.h"
+#include "engine.h"
 
 using namespace fmg;
 
-namespace {
+namespace fmg {
 
-struct Level {
-  Grid g;
-  int cap = 0;  // instances allocated (cnt[k])
-  Coef2D c{};
-  Coef3D c3{};
-  double *x = nullptr, *xt = nullptr, *f = nullptr, *r = nullptr, *u = nullptr,
-         *y = nullptr, *z = nullptr;
-  Density2D b{};          // density stencil of u~ (augmented pass), 2D
-  Density3D b3{};         // same, 3D
-  // mixed precision: FP32 copies of the coefficients and FP32 V-cycle vectors
-  CoefF2D cf{};
-  CoefF3D cf3{};
-  float *x32 = nullptr, *xt32 = nullptr, *f32 = nullptr, *r32 = nullptr;
-  double* pw = nullptr;   // (x / r)^m table for the 2D T3 sums (levels >= 2)
-  double* t3map = nullptr;  // class sums -> T3 map of this level (levels >= 2)
-};
-
-// The same level restricted to instances first .. first + count - 1.
 Level view(const Level& l, int first, int count) {
   Level v = l;
   const size_t o = (size_t)first * l.g.stride;
@@ -63,6 +45,10 @@ Level view(const Level& l, int first, int count) {
   v.g.nb = count;
   return v;
 }
+
+}  // namespace fmg
+
+namespace {
 
 // ---- dimension dispatch of the level kernels -----------------------------------------------
 void lv_coef(Level& l, const PotentialParams* p, cudaStream_t s) {
@@ -132,9 +118,6 @@ void lv_gather_level1(Level& l1, double* gA, double* gM, double* t1, double* B1,
   }
 }
 
-enum ProfId { kProfJacobi, kProfResidual, kProfRestrict, kProfProlong, kProfRhs,
-              kProfMoments, kProfDense, kProfVcycle, kProfT3, kProfCoef, kProfCount };
-
 double factorial(int k) {
   double r = 1.0;
   for (int i = 2; i <= k; ++i) r *= i;
@@ -143,70 +126,26 @@ double factorial(int k) {
 
 }  // namespace
 
-struct fmg_eig_handle {
-  fmg_eig_problem prob{};  // settings shared by the batch; levels = the largest instance's
-  int nb = 1;              // instances
-  std::vector<fmg_eig_problem> probs;  // per instance, sorted by level count (descending)
-  std::vector<int> order;              // order[b]: caller's index of sorted instance b
-  std::vector<int> cnt;                // cnt[k], k = 1..levels (+ cnt[levels + 1] = 0)
-  std::vector<size_t> uoff;            // offset of sorted instance b's output in uout
-  int dev = 0;
-  cudaStream_t stream = nullptr;
-  std::vector<Level> lv;  // lv[0] = level 1
-  std::vector<void*> allocs;
-  int nh = 0, ntri = 0, nvert = 3, maxadj = 6;
-  double tri_vol = 0.0;
-  // per-instance arrays (sorted order): L1, M1, L1inv nh*nh; c, cstart nh + 1; scalars 1
-  double *L1 = nullptr, *M1 = nullptr, *L1inv = nullptr, *q4 = nullptr;
-  int *tri = nullptr, *adj = nullptr;
-  double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr,
-         *partials = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,
-         *gMd = nullptr, *t1d = nullptr, *B1d = nullptr, *t0 = nullptr,
-         *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr, *uout = nullptr;
-  int *iters = nullptr, *status = nullptr;  // [level][instance]
-  PotentialParams* dparams = nullptr;  // device copy read by the kernels (nb)
-  PotentialParams* hparams = nullptr;  // pinned host staging, uploaded at every solve (nb)
-  // profiling: event pairs around the first finest-level launch of each profiled step
-  cudaEvent_t prof[kProfCount][2] = {};
-  bool prof_armed[kProfCount] = {};
-  int kernel_nodes = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  size_t dense_smem = 0;
+fmg_eig_handle::~fmg_eig_handle() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  for (int i = 0; i < kProfCount; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (prof[i][j]) cudaEventDestroy(prof[i][j]);
+  for (void* p : allocs) {
+    if (opt.async_alloc) cudaFreeAsync(p, stream);
+    else cudaFree(p);
+  }
+  if (hparams) {
+    if (opt.async_alloc) delete[] hparams;
+    else cudaFreeHost(hparams);
+  }
+  if (stream) cudaStreamDestroy(stream);
+}
 
-  template <typename T>
-  T* alloc(size_t count) {
-    void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      throw std::bad_alloc();
-    }
-    allocs.push_back(p);
-    cudaMemset(p, 0, std::max<size_t>(count, 1) * sizeof(T));
-    return static_cast<T*>(p);
-  }
-  ~fmg_eig_handle() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    for (int i = 0; i < kProfCount; ++i)
-      for (int j = 0; j < 2; ++j)
-        if (prof[i][j]) cudaEventDestroy(prof[i][j]);
-    for (void* p : allocs) cudaFree(p);
-    if (hparams) cudaFreeHost(hparams);
-    if (stream) cudaStreamDestroy(stream);
-  }
-  Level& L(int k) { return lv[k - 1]; }
-  int levels() const { return prob.levels; }
-  // every level launches over `count` instances (the active prefix of the stage)
-  void activate(int count) {
-    for (Level& l : lv) l.g.nb = std::min(count, l.cap);
-  }
-};
-
-namespace {
+namespace fmg {
 
 #define CK(expr)                                     \
   do {                                               \
@@ -240,6 +179,10 @@ auto shared_key(const fmg_eig_problem& p) {
   return std::make_tuple(p.dim, p.coarse_cells, p.nu_pre, p.nu_post, p.vcycles, p.corrections,
                          p.smoother, p.precision, p.operator_form, p.scf_max_iter, p.flags,
                          p.box_len, p.scf_tol);
+}
+
+bool same_shared_settings(const fmg_eig_problem& a, const fmg_eig_problem& b) {
+  return shared_key(a) == shared_key(b);
 }
 
 PotentialParams potential(const fmg_eig_problem& p) {
@@ -315,16 +258,19 @@ void build_levels(fmg_eig_handle* h) {
         std::vector<double> pw(4 * (r + 1));
         t3_power_table(r, pw.data());
         l.pw = h->alloc<double>(pw.size());
-        cudaMemcpy(l.pw, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (!h->dry) cudaMemcpyAsync(l.pw, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice,
+                  h->stream);
         double map[2 * 10 * 25];
         t3_map2d(r, map);
         l.t3map = h->alloc<double>(2 * 10 * 25);
-        cudaMemcpy(l.t3map, map, sizeof(map), cudaMemcpyHostToDevice);
+        if (!h->dry) cudaMemcpyAsync(l.t3map, map, sizeof(map), cudaMemcpyHostToDevice,
+                  h->stream);
       } else {
         std::vector<double> map(20 * 15 * 20);
         t3_map3d(r, map.data());
         l.t3map = h->alloc<double>(map.size());
-        cudaMemcpy(l.t3map, map.data(), map.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (!h->dry) cudaMemcpyAsync(l.t3map, map.data(), map.size() * sizeof(double), cudaMemcpyHostToDevice,
+                  h->stream);
       }
     }
   }
@@ -407,9 +353,12 @@ void build_coarse(fmg_eig_handle* h) {
   h->tri = h->alloc<int>(tri.size());
   h->adj = h->alloc<int>(adj.size());
   h->q4 = h->alloc<double>(q4.size());
-  cudaMemcpy(h->tri, tri.data(), tri.size() * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(h->adj, adj.data(), adj.size() * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(h->q4, q4.data(), q4.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (!h->dry) cudaMemcpyAsync(h->tri, tri.data(), tri.size() * sizeof(int), cudaMemcpyHostToDevice,
+                  h->stream);
+  if (!h->dry) cudaMemcpyAsync(h->adj, adj.data(), adj.size() * sizeof(int), cudaMemcpyHostToDevice,
+                  h->stream);
+  if (!h->dry) cudaMemcpyAsync(h->q4, q4.data(), q4.size() * sizeof(double), cudaMemcpyHostToDevice,
+                  h->stream);
   const size_t nn = (size_t)h->nh * h->nh;
   h->L1 = h->alloc<double>(nn * nb);
   h->M1 = h->alloc<double>(nn * nb);
@@ -445,8 +394,17 @@ void build_coarse(fmg_eig_handle* h) {
     tot += h->L(h->probs[b].levels).g.interior();
   }
   h->uout = h->alloc<double>(tot);
+  std::vector<int> inv(nb);
+  for (int b = 0; b < nb; ++b) inv[h->order[b]] = b;
+  h->inv_order = h->alloc<int>(nb);
+  if (!h->dry) cudaMemcpyAsync(h->inv_order, inv.data(), sizeof(int) * nb, cudaMemcpyHostToDevice,
+                  h->stream);
   h->dense_smem = dense_smem_bytes(h->nh + 1, h->ntri, h->nvert, 1);
 }
+
+// (Every build-time upload above goes through the handle's stream from pageable host memory:
+// the call returns once the source is staged, and the allocations it targets are ordered on
+// the same stream.)
 
 // ---- enqueue helpers (all work in stream order on s) ---------------------------------------
 void prof_begin(fmg_eig_handle* h, int id, int level, cudaStream_t s) {
@@ -672,17 +630,20 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   lv_prolong(l, h->L(k - 1), h->L(k - 1).y, l.u, false, ut, h->c + h->nh, h->nh + 1, s);
 }
 
-void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s) {
+void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s, const StageHook* after_stage) {
   enqueue_setup(h, s);
   h->activate(h->nb);
   enqueue_coarse(h, s);
   cudaMemcpyAsync(h->lam_levels, h->lam, sizeof(double) * h->nb, cudaMemcpyDeviceToDevice, s);
+  if (after_stage && h->cnt[1] > h->cnt[2]) (*after_stage)(1, h->cnt[2], h->cnt[1] - h->cnt[2]);
   for (int k = 2; k <= h->levels(); ++k) {
     h->activate(h->cnt[k]);
     lv_prolong(h->L(k), h->L(k - 1), h->L(k - 1).u, h->L(k).u, false, nullptr, nullptr, 0, s);
     for (int it = 0; it < h->prob.corrections; ++it) enqueue_correction(h, k, s);
     cudaMemcpyAsync(h->lam_levels + (size_t)(k - 1) * h->nb, h->lam, sizeof(double) * h->cnt[k],
                     cudaMemcpyDeviceToDevice, s);
+    if (after_stage && h->cnt[k] > h->cnt[k + 1])
+      (*after_stage)(k, h->cnt[k + 1], h->cnt[k] - h->cnt[k + 1]);
   }
   h->activate(1);
 }
@@ -743,7 +704,7 @@ void time_mix(fmg_eig_handle* h, Level& l, int k, cudaStream_t s) {
 }
 
 int autotune(fmg_eig_handle* h) {
-  if (h->prob.flags & FMG_FLAG_NO_AUTOTUNE) return FMG_OK;
+  if ((h->prob.flags & FMG_FLAG_NO_AUTOTUNE) || h->opt.tune == 0) return FMG_OK;
   static const int k2d[][2] = {{32, 8}, {32, 4}, {64, 4}, {32, 16}, {128, 2},
                                {64, 8}, {16, 16}, {16, 8}, {8, 8},  {8, 4}};
   static const int k3d[][2] = {{32, 8}, {32, 4}, {64, 2}, {32, 2}, {64, 4},
@@ -771,6 +732,7 @@ int autotune(fmg_eig_handle* h) {
         continue;
       }
     }
+    if (h->opt.tune < 2) continue;  // cache only: keep the default shape
     const size_t nodes = l.g.interior() * (size_t)l.cap;
     const bool big = nodes >= ((size_t)1 << 20);
     const int ncand = l.g.dim == 2 ? (big ? 4 : 10) : (big ? 4 : 8);
@@ -807,16 +769,13 @@ int autotune(fmg_eig_handle* h) {
   return rc;
 }
 
-int create_handle(const fmg_eig_problem* probs, int count, fmg_eig_handle** out) {
-  if (!out || !probs || count < 1) return FMG_EINVAL;
-  *out = nullptr;
+// Validation, the sorted instance order and the per-level counts of a new handle.
+int init_instances(fmg_eig_handle* h, const fmg_eig_problem* probs, int count) {
   for (int i = 0; i < count; ++i) {
     const int v = validate(&probs[i]);
     if (v != FMG_OK) return v;
     if (shared_key(probs[i]) != shared_key(probs[0])) return FMG_EINVAL;
   }
-  fmg_eig_handle* h = new (std::nothrow) fmg_eig_handle();
-  if (!h) return FMG_ENOMEM;
   h->nb = count;
   h->order.resize(count);
   std::iota(h->order.begin(), h->order.end(), 0);
@@ -829,10 +788,33 @@ int create_handle(const fmg_eig_problem* probs, int count, fmg_eig_handle** out)
     for (const auto& p : h->probs) h->cnt[k] += p.levels >= k ? 1 : 0;
   if (h->prob.dim == 3)  // planes and instances share gridDim.z of the 3D launches
     for (int k = 1; k <= h->prob.levels; ++k)
-      if ((size_t)((h->prob.coarse_cells << (k - 1)) + 1) * h->cnt[k] > 65535) {
-        delete h;
-        return FMG_ENOTSUP;
-      }
+      if ((size_t)((h->prob.coarse_cells << (k - 1)) + 1) * h->cnt[k] > 65535) return FMG_ENOTSUP;
+  return FMG_OK;
+}
+
+size_t estimate_bytes(const fmg_eig_problem* probs, int count) {
+  if (!probs || count < 1) return 0;
+  fmg_eig_handle h;
+  h.dry = true;
+  if (init_instances(&h, probs, count) != FMG_OK) return 0;
+  build_levels(&h);
+  build_coarse(&h);
+  h.alloc<PotentialParams>(count);
+  return h.bytes;
+}
+
+int create_handle(const fmg_eig_problem* probs, int count, const CreateOptions& opt,
+                  fmg_eig_handle** out) {
+  if (!out || !probs || count < 1) return FMG_EINVAL;
+  *out = nullptr;
+  fmg_eig_handle* h = new (std::nothrow) fmg_eig_handle();
+  if (!h) return FMG_ENOMEM;
+  h->opt = opt;
+  const int vi = init_instances(h, probs, count);
+  if (vi != FMG_OK) {
+    delete h;
+    return vi;
+  }
   if (cudaGetDevice(&h->dev) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
@@ -848,8 +830,17 @@ int create_handle(const fmg_eig_problem* probs, int count, fmg_eig_handle** out)
     delete h;
     return FMG_ENOMEM;
   }
-  if (cudaMallocHost(&h->hparams, sizeof(PotentialParams) * count) != cudaSuccess) {
+  // pinned staging for the per-solve upload of a reusable handle; a one-shot handle (the
+  // server's) uses pageable memory, whose release never waits for the device
+  if (opt.async_alloc) {
+    h->hparams = new (std::nothrow) PotentialParams[count];
+    if (!h->hparams) {
+      delete h;
+      return FMG_ENOMEM;
+    }
+  } else if (cudaMallocHost(&h->hparams, sizeof(PotentialParams) * count) != cudaSuccess) {
     cudaGetLastError();
+    h->hparams = nullptr;
     delete h;
     return FMG_ENOMEM;
   }
@@ -861,7 +852,8 @@ int create_handle(const fmg_eig_problem* probs, int count, fmg_eig_handle** out)
         delete h;
         return FMG_ECUDA;
       }
-  cudaMemcpy(h->dparams, h->hparams, sizeof(PotentialParams) * count, cudaMemcpyHostToDevice);
+  cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * count,
+                  cudaMemcpyHostToDevice, h->stream);
   if (h->dense_smem > kDenseSmemLimit) {  // the small dense solve keeps everything in shared memory
     delete h;
     return FMG_ENOTSUP;
@@ -871,16 +863,25 @@ int create_handle(const fmg_eig_problem* probs, int count, fmg_eig_handle** out)
     delete h;
     return FMG_ECUDA;
   }
-  // component entry points need the operators; the solve graph recomputes them itself
-  enqueue_setup(h, h->stream);
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return FMG_ECUDA;
+  // component entry points need the operators (the solve recomputes them itself), and the
+  // tuner times launches on them
+  const bool tune_runs = opt.tune == 2 && !(h->prob.flags & FMG_FLAG_NO_AUTOTUNE);
+  if (opt.component_setup || tune_runs) {
+    enqueue_setup(h, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      delete h;
+      return FMG_ECUDA;
+    }
   }
   if (autotune(h) != FMG_OK) {
     delete h;
     return FMG_ECUDA;
+  }
+  h->activate(1);
+  if (!opt.graph) {
+    *out = h;
+    return FMG_OK;
   }
   for (int i = 0; i < kProfCount; ++i) h->prof_armed[i] = true;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
@@ -990,7 +991,7 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
   return rc;
 }
 
-}  // namespace
+}  // namespace fmg
 
 extern "C" {
 
@@ -1012,11 +1013,11 @@ int fmg_eig_create(const fmg_eig_problem* prob, fmg_eig_handle** out) {
     if (out) *out = nullptr;
     return FMG_EINVAL;
   }
-  return create_handle(prob, 1, out);
+  return create_handle(prob, 1, CreateOptions{}, out);
 }
 
 int fmg_eig_batch_create(const fmg_eig_problem* probs, int32_t count, fmg_eig_handle** out) {
-  return create_handle(probs, count, out);
+  return create_handle(probs, count, CreateOptions{}, out);
 }
 
 int32_t fmg_eig_batch_count(const fmg_eig_handle* h) { return h ? h->nb : 0; }
@@ -1105,6 +1106,17 @@ int fmg_eig_batch_solve(fmg_eig_handle* h, double* lambdas, double* const* u_hos
   return run_handles(hs, idx, lambdas, u_hosts, u_lens, stats, statuses);
 }
 
+int fmg_eig_batch_solve_dev(fmg_eig_handle* h, double* lambdas_dev, void* stream) {
+  if (!h || !lambdas_dev) return FMG_EINVAL;
+  cudaStream_t s = pick(h, stream);
+  CK(cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * h->nb,
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaGraphLaunch(h->exec, s));
+  gather_by_index(h->lam, h->inv_order, lambdas_dev, h->nb, s);
+  CK(cudaGetLastError());
+  return FMG_OK;
+}
+
 int fmg_eig_solve_batch(const fmg_eig_problem* probs, int32_t count, double* lambdas,
                         double* const* u_hosts, const size_t* u_lens, fmg_eig_stats* stats,
                         int32_t* statuses) {
@@ -1132,7 +1144,7 @@ int fmg_eig_solve_batch(const fmg_eig_problem* probs, int32_t count, double* lam
     std::vector<fmg_eig_problem> ps;
     for (int i : g) ps.push_back(probs[i]);
     fmg_eig_handle* h = nullptr;
-    rc = create_handle(ps.data(), (int)ps.size(), &h);
+    rc = create_handle(ps.data(), (int)ps.size(), CreateOptions{}, &h);
     if (rc != FMG_OK) break;
     hs.push_back(h);
     std::vector<int> map(h->nb);

@@ -159,6 +159,8 @@ void dot(const double* a, const double* b, size_t n, double* partials, double* o
 // (instance b: interior vector at b * g.interior(), padded one at b * g.stride)
 void pack_interior(const Grid& g, const double* interior, double* padded, cudaStream_t s);
 void unpack_interior(const Grid& g, const double* padded, double* interior, cudaStream_t s);
+// dst[i] = src[idx[i]], i < n
+void gather_by_index(const double* src, const int* idx, double* dst, int n, cudaStream_t s);
 // padded level-1 vectors from dense coefficient vectors c (instance b at c + b * cstride)
 void scatter_level1(const Grid& g, const double* c, size_t cstride, double* padded,
                     cudaStream_t s);

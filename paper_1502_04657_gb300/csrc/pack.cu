@@ -26,7 +26,17 @@ __global__ void k_unpack(int dim, int n, int pitch, size_t count, size_t ist, si
   if (p < count) out[blockIdx.y * ist + p] = in[blockIdx.y * pst + padded_index(dim, n, pitch, p)];
 }
 
+__global__ void k_gather_index(const double* __restrict__ src, const int* __restrict__ idx,
+                               double* __restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
 }  // namespace
+
+void gather_by_index(const double* src, const int* idx, double* dst, int n, cudaStream_t s) {
+  k_gather_index<<<(n + 255) / 256, 256, 0, s>>>(src, idx, dst, n);
+}
 
 void pack_interior(const Grid& g, const double* interior, double* padded, cudaStream_t s) {
   const size_t count = g.interior();

@@ -37,6 +37,29 @@ class fmg_eig_stats(C.Structure):
     ]
 
 
+class fmg_eig_serve_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("batch_window_s", C.c_double),
+                ("max_batch", C.c_int32), ("max_inflight", C.c_int32)]
+
+
+class fmg_eig_request(C.Structure):
+    _fields_ = [("problem", fmg_eig_problem), ("arrival_s", C.c_double),
+                ("u", C.c_void_p), ("u_len", C.c_size_t)]
+
+
+class fmg_eig_result(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("latency_s", C.c_double), ("admit_s", C.c_double),
+                ("done_s", C.c_double), ("status", C.c_int32), ("cohort", C.c_int32)]
+
+
+class fmg_eig_serve_stats(C.Structure):
+    _fields_ = [("p50_s", C.c_double), ("p99_s", C.c_double), ("mean_s", C.c_double),
+                ("max_s", C.c_double), ("solves_per_s", C.c_double), ("makespan_s", C.c_double),
+                ("peak_bytes", C.c_double), ("budget_bytes", C.c_double), ("cohorts", C.c_int32),
+                ("max_cohort", C.c_int32), ("max_inflight_seen", C.c_int32),
+                ("completed", C.c_int32)]
+
+
 class FmgError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {strerror(code)} ({code})")
@@ -78,6 +101,10 @@ _SIGS = {
                                       C.POINTER(C.c_size_t), C.POINTER(fmg_eig_stats),
                                       C.POINTER(_I32)]),
     "fmg_eig_level_tile": (C.c_int, [_P, _I32, C.POINTER(_I32), C.POINTER(_I32)]),
+    "fmg_eig_batch_solve_dev": (C.c_int, [_P, _P, _P]),
+    "fmg_eig_estimate_bytes": (C.c_size_t, [C.POINTER(fmg_eig_problem), _I32]),
+    "fmg_eig_serve": (C.c_int, [C.POINTER(fmg_eig_serve_config), C.POINTER(fmg_eig_request), _I32,
+                                C.POINTER(fmg_eig_result), C.POINTER(fmg_eig_serve_stats)]),
 }
 
 
@@ -322,6 +349,11 @@ class BatchSolver(Solver):
     def count(self) -> int:
         return self.lib.fmg_eig_batch_count(self.h)
 
+    def solve_dev_all(self, lams_dev, stream=None):
+        """fmg_eig_batch_solve_dev: lambdas into a device tensor, no host synchronisation."""
+        return self._check(self.lib.fmg_eig_batch_solve_dev(self.h, _ptr(lams_dev), stream),
+                           "fmg_eig_batch_solve_dev")
+
     def solve_all(self, with_u: bool = True, stats: bool = False):
         """lambdas (list), u per instance (numpy, or None), stats records (or None), codes."""
         lams, us, ptrs, lens, st, codes = _batch_outputs(self.problems, with_u, stats)
@@ -339,3 +371,40 @@ def solve_batch(problems: list, with_u: bool = True, stats: bool = False):
     if rc not in (FMG_OK, FMG_ENOCONV):
         raise FmgError(rc, "fmg_eig_solve_batch")
     return list(lams), us, (list(st) if stats else None), list(codes)
+
+
+def estimate_bytes(problems: list) -> int:
+    """fmg_eig_estimate_bytes: device bytes of a batch handle for these problems."""
+    arr = (fmg_eig_problem * len(problems))(*[p.to_c() for p in problems])
+    return load_library().fmg_eig_estimate_bytes(arr, len(problems))
+
+
+def serve(problems: list, arrivals: list, *, budget_bytes: float = 0.0, max_batch: int = 32,
+          max_inflight: int = 4, batch_window_s: float = 0.0, with_u: bool = False):
+    """fmg_eig_serve over requests (problem, arrival time in s): per-request results as dicts
+    (lambda, latency_s, admit_s, done_s, status, cohort, u) and the serve statistics."""
+    import numpy as np
+    lib = load_library()
+    n = len(problems)
+    reqs = (fmg_eig_request * n)()
+    us = []
+    for i, (p, t) in enumerate(zip(problems, arrivals)):
+        reqs[i].problem = p.to_c()
+        reqs[i].arrival_s = float(t)
+        if with_u:
+            u = np.empty(p.size(p.levels))
+            us.append(u)
+            reqs[i].u = u.ctypes.data
+            reqs[i].u_len = u.size
+    cfg = fmg_eig_serve_config(float(budget_bytes), float(batch_window_s), int(max_batch),
+                               int(max_inflight))
+    res = (fmg_eig_result * n)()
+    st = fmg_eig_serve_stats()
+    rc = lib.fmg_eig_serve(C.byref(cfg), reqs, n, res, C.byref(st))
+    if rc not in (FMG_OK, FMG_ENOCONV):
+        raise FmgError(rc, "fmg_eig_serve")
+    out = [{"lambda": r.lambda_, "latency_s": r.latency_s, "admit_s": r.admit_s,
+            "done_s": r.done_s, "status": r.status, "cohort": r.cohort,
+            "u": us[i] if with_u else None} for i, r in enumerate(res)]
+    stats = {k: getattr(st, k) for k, _ in fmg_eig_serve_stats._fields_}
+    return out, stats
