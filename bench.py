@@ -74,6 +74,10 @@ KERNELS = {
     3: {"nload_density": (1305.0, 80.0), "jacobi": (32.0, 96.0)},
 }
 DOMINANT = "nload_density"
+# DRAM bytes per node of a finest-level launch from one ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum of the 9-level 2D launch, 4,190,209 nodes;
+# profiles/ncu_k_nload_density2d_h1-2048.md), scaled by the nodes a launch processes.
+TRAFFIC_PER_NODE = {(2, "nload_density"): (34.053376e6 + 105.419264e6) / 4190209}
 
 
 def rank_info():
@@ -214,16 +218,21 @@ def reference_arm(args):
 
 
 def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist=None,
-            with_e2e: bool = True, clocks: bool = True) -> dict:
+            with_e2e: bool = True, clocks: bool = True, levels: int | None = None,
+            autotune: bool = True) -> dict:
     import torch
 
     from paper_1502_04657_gb300 import fmg
 
     config, mixed, desc = WORKLOADS[workload]
-    kw = problem_kwargs(config)
+    kw = problem_kwargs(config, levels)
+    if levels is not None:
+        desc = f"{desc} [truncated to {levels} levels for profiling]"
     gp = fmg.Problem(**{k: v for k, v in kw.items() if k in fmg.Problem.__dataclass_fields__})
     if mixed:
         gp.precision = fmg.FMG_MIXED_FP32
+    if not autotune:
+        gp.flags = fmg.FMG_FLAG_NO_AUTOTUNE
     n = gp.size(gp.levels)
     solver = fmg.Solver(gp)
     stream = torch.cuda.Stream()
@@ -481,8 +490,10 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
         ms = m["profile"].get(name, -1.0)
         if ms and ms > 0:
             ach = flops * nodes / (ms * 1e-3) / 1e12
+            tpn = TRAFFIC_PER_NODE.get((m["dim"], name))
             roof[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                          "frac": ach / peak, "traffic": None, "launch_ms": ms,
+                          "frac": ach / peak, "traffic": tpn * nodes if tpn else None,
+                          "launch_ms": ms,
                           "hbm_gbs_algorithmic": nbytes * nodes / (ms * 1e-3) / 1e9}
     main = dict(roof.get(DOMINANT, {}))
     main["kernel"] = DOMINANT
@@ -504,7 +515,8 @@ def ours_arm(args):
         return batch_arm(args, world, local, dist)
     if args.workload == "config5":
         return serve_arm(args, world, local, dist)
-    m = measure(args.workload, args.steps, args.warmup, world, local, dist)
+    m = measure(args.workload, args.steps, args.warmup, world, local, dist, levels=args.levels,
+                autotune=not args.no_autotune)
     main, other = roofline(m, m["clocks"])
     step_ms = m["step_ms"]
     line = {
@@ -623,6 +635,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--levels", type=int, default=None,
+                    help="truncate a single-solve workload's level count (small profiling cases)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default 32x8 tiles (a fixed launch sequence for ncu captures)")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-batch", type=int, default=32)
     ap.add_argument("--serve-inflight", type=int, default=6)

@@ -28,8 +28,10 @@ __device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j
 // (p, q, r) of area |K|:
 //   int u^2 lambda_p^2       = |K|/90  [6u_p^2 + u_q^2 + u_r^2 + 3u_p u_q + 3u_p u_r + u_q u_r]
 //   int u^2 lambda_p lambda_q = |K|/180 [3u_p^2 + 3u_q^2 + u_r^2 + 4u_p u_q + 2u_p u_r + 2u_q u_r]
-__global__ void k_nload_density2d(int n, int pitch, size_t st, double area,
-                                  const double* __restrict__ u, double* __restrict__ nl,
+// s60, s90, s180 = |K| / 60, / 90, / 180 (computed on the host: an FP64 division per node
+// would cost as much as a quarter of the kernel's arithmetic)
+__global__ void k_nload_density2d(int n, int pitch, size_t st, double s60, double s90,
+                                  double s180, const double* __restrict__ u, double* __restrict__ nl,
                                   double* __restrict__ bC, double* __restrict__ bE,
                                   double* __restrict__ bN, double* __restrict__ bNE) {
   const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,16 +65,16 @@ __global__ void k_nload_density2d(int n, int pitch, size_t st, double area,
   v = fma(6.0 * u2, s1, v);
   v = fma(2.0 * up, fma(2.0, s2, pp), v);
   v = fma(2.0, s3, v);
-  nl[k] = (area / 60.0) * (v + qq);
+  nl[k] = s60 * (v + qq);
   // diagonal: sum over the six triangles
-  bC[k] = (area / 90.0) * fma(36.0, u2, fma(2.0, s2, fma(6.0 * up, s1, pp)));
+  bC[k] = s90 * fma(36.0, u2, fma(2.0, s2, fma(6.0 * up, s1, pp)));
   // edge p-q shared by the triangles closed by r1 and r2
   const double u26 = 6.0 * u2;
-  bE[k] = (area / 180.0) *
+  bE[k] = s180 *
           fma(6.0, qE, u26 + fma(8.0 * up, nE, fma(2.0 * (up + nE), nNE + nS, qNE + qS)));
-  bN[k] = (area / 180.0) *
+  bN[k] = s180 *
           fma(6.0, qN, u26 + fma(8.0 * up, nN, fma(2.0 * (up + nN), nNE + nW, qNE + qW)));
-  bNE[k] = (area / 180.0) *
+  bNE[k] = s180 *
            fma(6.0, qNE, u26 + fma(8.0 * up, nNE, fma(2.0 * (up + nNE), nE + nN, qE + qN)));
 }
 
@@ -338,7 +340,8 @@ dim3 grid_of(const Grid& g, int cx, int cy) {
 void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D& b,
                      cudaStream_t s) {
   k_nload_density2d<<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
-      g.n, g.pitch, g.stride, g.h * g.h / 2.0, u, nl, b.C, b.E, b.N, b.NE);
+      g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 180.0, g.h * g.h / 360.0, u, nl,
+      b.C, b.E, b.N, b.NE);
 }
 
 void coarsen_density2d(const Grid& fine, const Grid& coarse, const Density2D& bf,

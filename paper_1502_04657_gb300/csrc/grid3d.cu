@@ -91,18 +91,18 @@ __global__ void k_coef3d(int n, int pitch, size_t st, double h, const double* __
   c.a[0][k] = cc;
   // axis directions: along = table 1 on that axis, across = table 2 on the others
   for (int d = 0; d < 3; ++d) {
-    double v = -h + wl * h3 * p.w0 / 20.0;
+    double v = -h + wl * h3 * p.w0 * (1.0 / 20.0);
     for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == d ? 1 : 2);
     c.a[1 + d][k] = v;
   }
   // face diagonals XY, XZ, YZ: along on the two axes, across on the third
   const int other[3] = {2, 1, 0};
   for (int f = 0; f < 3; ++f) {
-    double v = wl * h3 * p.w0 / 30.0;
+    double v = wl * h3 * p.w0 * (1.0 / 30.0);
     for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == other[f] ? 4 : 3);
     c.a[4 + f][k] = v;
   }
-  c.a[7][k] = wl * h3 * p.w0 / 20.0 + T(0, 1) + T(1, 1) + T(2, 1);
+  c.a[7][k] = wl * h3 * p.w0 * (1.0 / 20.0) + T(0, 1) + T(1, 1) + T(2, 1);
   c.dinv[k] = p.omega * recip(cc);
 }
 
@@ -152,7 +152,7 @@ __device__ __forceinline__ double mass_at(const double* __restrict__ x, size_t k
     if (d >= 3 && d < 6) fd += s;
     else ax += s;
   }
-  return fma(0.4, x[k], fma(1.0 / 20.0, ax, fd / 30.0));
+  return fma(0.4, x[k], fma(1.0 / 20.0, ax, fd * (1.0 / 30.0)));
 }
 
 __global__ void k_mass3d(int n, int pitch, size_t st, double h3, const double* __restrict__ x,
@@ -268,15 +268,17 @@ __global__ void k_rhs3d(int n, int pitch, size_t st, double h3, double nscale,
   f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * nl);
 }
 
-__global__ void k_nload_density3d(int n, int pitch, size_t st, double vol, const double* __restrict__ u,
+// s140, s210, s420 = |K| / 140, / 210, / 420 (host-side: no FP64 division per node)
+__global__ void k_nload_density3d(int n, int pitch, size_t st, double s140, double s210,
+                                  double s420, const double* __restrict__ u,
                                   double* __restrict__ nl, Density3D b) {
   INTERIOR_3D
   double v, e[8];
   star3<true>(u, k, pitch, plane, v, e);
-  nl[k] = (vol / 140.0) * v;
-  b.a[0][k] = (vol / 210.0) * e[0];
+  nl[k] = s140 * v;
+  b.a[0][k] = s210 * e[0];
 #pragma unroll
-  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = (vol / 420.0) * e[1 + d];
+  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = s420 * e[1 + d];
 }
 
 // Galerkin coarsening of the 15-point density stencil: Bc(a, b) = sum P_va P_wb B(v, w) over
@@ -459,8 +461,9 @@ void rhs3d(const Grid& g, const double* lam, const PotentialParams* p, const dou
 
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s) {
-  k_nload_density3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, g.h * g.h * g.h / 6.0, u,
-                                            nl, b);
+  const double vol = g.h * g.h * g.h / 6.0;
+  k_nload_density3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0,
+                                            vol / 420.0, u, nl, b);
 }
 
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,
