@@ -24,7 +24,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMono = 20;       // monomials of degree <= 3 in 3 variables
 constexpr int kClasses = 15;    // interior, F0..F3, E01 E02 E03 E12 E13 E23, V0..V3
-constexpr int kNodesPerThread = 8;
 constexpr int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 __constant__ int kPermDev[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
@@ -50,7 +49,25 @@ __device__ void block_reduce(double* acc, int count, double* sh, double* out) {
   }
 }
 
-// Interior class: block (chunk, tet); nodes of the coarse cell in flat order.
+// Interior class: thread = one row (x1, x2) of the coarse cell, block (chunk of rows, tet,
+// instance).  On a row, the nodes strictly inside T_s are an interval of x0 (the chain
+// order a > b > c of T_s bounds x0 by the row's two other coordinates), and every monomial
+// is (powers of the row's fixed chain coordinates) x (a power of x0 / r): the thread sums
+// u (x0/r)^e, e = 0..3, along its interval (4 FMAs per node) and then adds the 20 monomial
+// sums of its row (40 FP64 operations per row).
+__constant__ int kMonoExpDev[20][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                       {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2},
+                                       {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1},
+                                       {1, 0, 2}, {0, 3, 0}, {0, 2, 1}, {0, 1, 2}, {0, 0, 3}};
+
+__device__ __forceinline__ int coord(int axis, int x0, int x1, int x2) {
+  return axis == 0 ? x0 : (axis == 1 ? x1 : x2);
+}
+
+__device__ __forceinline__ double pick4(double v0, double v1, double v2, double v3, int e) {
+  return e == 0 ? v0 : (e == 1 ? v1 : (e == 2 ? v2 : v3));
+}
+
 __global__ void __launch_bounds__(kThreads)
     k_t3_interior3d(int pf, long planef, int n1, int r, size_t st, size_t pst,
                     const double* __restrict__ u, double* __restrict__ partials) {
@@ -60,25 +77,49 @@ __global__ void __launch_bounds__(kThreads)
   const int tet = blockIdx.y;
   const int cell = tet / 6, s = tet % 6;
   const int I = cell % n1, J = (cell / n1) % n1, L = cell / (n1 * n1);
-  const int r1 = r + 1;
-  const size_t cnt = (size_t)r1 * r1 * r1;
+  const int R = r + 1;
   const double inv_r = 1.0 / r;
+  // chain position of axis 0 (the axis threads walk along)
+  const int pos0 = kPermDev[s][0] == 0 ? 0 : (kPermDev[s][1] == 0 ? 1 : 2);
   double acc[kMono];
 #pragma unroll
   for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
-  const size_t beg = (size_t)blockIdx.x * kThreads * kNodesPerThread;
-  for (int it = 0; it < kNodesPerThread; ++it) {
-    const size_t idx = beg + (size_t)it * kThreads + threadIdx.x;
-    if (idx >= cnt) break;
-    const int x0 = (int)(idx % r1), x1 = (int)((idx / r1) % r1), x2 = (int)(idx / ((size_t)r1 * r1));
-    const int co[3] = {x0, x1, x2};
-    const int a = co[kPermDev[s][0]], b = co[kPermDev[s][1]], c = co[kPermDev[s][2]];
-    if (!(r > a && a > b && b > c && c > 0)) continue;
-    const double val = u[(size_t)(L * r + x2) * planef + (size_t)(J * r + x1) * pf + (I * r + x0)];
-    double m[kMono];
-    monomials(a * inv_r, b * inv_r, c * inv_r, m);
+  const int row = blockIdx.x * kThreads + threadIdx.x;
+  if (row < R * R) {
+    const int x1 = row % R, x2 = row / R;
+    // the two fixed chain coordinates (positions q1 < q2, the ones other than pos0)
+    const int q1 = pos0 == 0 ? 1 : 0, q2 = pos0 == 2 ? 1 : 2;
+    const int f1 = coord(kPermDev[s][q1], 0, x1, x2), f2 = coord(kPermDev[s][q2], 0, x1, x2);
+    // interval of x0 (exclusive bounds) from r > a > b > c > 0
+    int lo = 0, hi = -1;
+    if (pos0 == 0) {  // x0 = a, fixed b = f1, c = f2
+      if (f1 > f2 && f2 > 0) { lo = f1; hi = r; }
+    } else if (pos0 == 1) {  // x0 = b, fixed a = f1, c = f2
+      if (f1 < r && f2 > 0) { lo = f2; hi = f1; }
+    } else {  // x0 = c, fixed a = f1, b = f2
+      if (f1 < r && f1 > f2) { lo = 0; hi = f2; }
+    }
+    if (lo + 1 < hi) {
+      const double* rowp =
+          u + (size_t)(L * r + x2) * planef + (size_t)(J * r + x1) * pf + (size_t)I * r;
+      double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+      for (int x0 = lo + 1; x0 < hi; ++x0) {
+        const double val = rowp[x0];
+        const double t = x0 * inv_r, t2 = t * t;
+        m0 += val;
+        m1 = fma(val, t, m1);
+        m2 = fma(val, t2, m2);
+        m3 = fma(val, t2 * t, m3);
+      }
+      const double g1 = f1 * inv_r, g2 = f2 * inv_r;
+      const double g1s = g1 * g1, g2s = g2 * g2;
 #pragma unroll
-    for (int q = 0; q < kMono; ++q) acc[q] = fma(val, m[q], acc[q]);
+      for (int q = 0; q < kMono; ++q) {
+        const int e0 = kMonoExpDev[q][pos0], e1 = kMonoExpDev[q][q1], e2 = kMonoExpDev[q][q2];
+        acc[q] = pick4(1.0, g1, g1s, g1s * g1, e1) * pick4(1.0, g2, g2s, g2s * g2, e2) *
+                 pick4(m0, m1, m2, m3, e0);
+      }
+    }
   }
   block_reduce(acc, kMono, sh, partials + ((size_t)tet * gridDim.x + blockIdx.x) * kMono);
 }
@@ -164,8 +205,8 @@ __global__ void k_t3_finalize3d(int chunks, double h3, size_t pst, size_t tst,
 }
 
 int interior_chunks(int r) {
-  const size_t cnt = (size_t)(r + 1) * (r + 1) * (r + 1);
-  return (int)((cnt + kThreads * kNodesPerThread - 1) / (kThreads * kNodesPerThread));
+  const size_t rows = (size_t)(r + 1) * (r + 1);
+  return (int)((rows + kThreads - 1) / kThreads);
 }
 
 // ---- host: class moments and the linear map ---------------------------------------------

@@ -62,6 +62,13 @@ struct fmg_eig_handle {
   fmg::CreateOptions opt;
   int dev = 0;
   cudaStream_t stream = nullptr;
+  // Independent branches of a solve run on side streams, forked from and joined back to the
+  // solve's stream with events (inside a capture they become parallel graph branches): the
+  // two side chains of the augmented pass (side 0, 1) and the operator setup of levels >= 2
+  // (side 2, joined at the stage that first needs the level).
+  cudaStream_t side[3] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {}, ev_level[FMG_MAX_LEVELS + 1] = {};
+  bool level_pending[FMG_MAX_LEVELS + 1] = {};  // enqueue-time: setup of level k not joined yet
   std::vector<fmg::Level> lv;  // lv[0] = level 1
   std::vector<void*> allocs;
   size_t bytes = 0;  // device bytes allocated
@@ -72,7 +79,7 @@ struct fmg_eig_handle {
   double *L1 = nullptr, *M1 = nullptr, *L1inv = nullptr, *q4 = nullptr;
   int *tri = nullptr, *adj = nullptr;
   double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr,
-         *partials = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,
+         *partials = nullptr, *partials2 = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,
          *gMd = nullptr, *t1d = nullptr, *B1d = nullptr, *t0 = nullptr,
          *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr, *uout = nullptr;
   int *iters = nullptr, *status = nullptr;  // [level][instance]

@@ -131,6 +131,11 @@ fmg_eig_handle::~fmg_eig_handle() {
   if (graph) cudaGraphDestroy(graph);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  for (cudaEvent_t e : ev_join)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : ev_level)
+    if (e) cudaEventDestroy(e);
   for (int i = 0; i < kProfCount; ++i)
     for (int j = 0; j < 2; ++j)
       if (prof[i][j]) cudaEventDestroy(prof[i][j]);
@@ -142,6 +147,8 @@ fmg_eig_handle::~fmg_eig_handle() {
     if (opt.async_alloc) delete[] hparams;
     else cudaFreeHost(hparams);
   }
+  for (cudaStream_t x : side)
+    if (x) cudaStreamDestroy(x);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -370,6 +377,7 @@ void build_coarse(fmg_eig_handle* h) {
   h->buu = h->alloc<double>(nb);
   h->scal = h->alloc<double>(3 * (size_t)nb + 8);
   h->partials = h->alloc<double>((size_t)kReduceBlocks * nb);
+  h->partials2 = h->alloc<double>((size_t)kReduceBlocks * nb);
   const int nt3 = dim == 2 ? 10 : 20;
   h->t3 = h->alloc<double>((size_t)h->ntri * nt3 * nb);
   size_t tp = 1;
@@ -418,11 +426,36 @@ void prof_end(fmg_eig_handle* h, int id, int level, cudaStream_t s) {
   }
 }
 
+// s waits for the side streams' work so far: [first, first + count) of side[]
+void join_sides(fmg_eig_handle* h, cudaStream_t s, int first, int count) {
+  for (int i = first; i < first + count; ++i) {
+    cudaEventRecord(h->ev_join[i], h->side[i]);
+    cudaStreamWaitEvent(s, h->ev_join[i], 0);
+  }
+}
+void fork_sides(fmg_eig_handle* h, cudaStream_t s, int first, int count) {
+  cudaEventRecord(h->ev_fork, s);
+  for (int i = first; i < first + count; ++i) cudaStreamWaitEvent(h->side[i], h->ev_fork, 0);
+}
+
+// The operators of level k must be ready on s from here on (setup forked in enqueue_setup).
+void need_level(fmg_eig_handle* h, int k, cudaStream_t s) {
+  if (!h->level_pending[k]) return;
+  cudaStreamWaitEvent(s, h->ev_level[k], 0);
+  h->level_pending[k] = false;
+}
+
 // Operators of every level for every instance that has the level, and the level-1 inverse.
-void enqueue_setup(fmg_eig_handle* h, cudaStream_t s) {
+// With `overlap`, levels >= 2 are built on a side stream while the coarse solve runs, and
+// each stage joins the levels it needs (need_level).
+void enqueue_setup(fmg_eig_handle* h, cudaStream_t s, bool overlap = false) {
   h->activate(h->nb);
+  if (overlap && h->levels() >= 2) fork_sides(h, s, 2, 1);
   for (int k = 1; k <= h->levels(); ++k) {
     Level& l = h->L(k);
+    const cudaStream_t sk = overlap && k >= 2 ? h->side[2] : s;
+    const cudaStream_t s_saved = s;
+    s = sk;
     prof_begin(h, kProfCoef, k, s);
     lv_coef(l, h->dparams, s);
     prof_end(h, kProfCoef, k, s);
@@ -439,6 +472,11 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s) {
         to_f32(l.c3.dinv, l.cf3.dinv, n, s);
       }
     }
+    if (sk != s_saved) {
+      cudaEventRecord(h->ev_level[k], sk);
+      h->level_pending[k] = true;
+    }
+    s = s_saved;
   }
   lv_dense_level1(h->L(1), h->L1, h->M1, s);
   dense_spd_inverse(h->L1, h->L1inv, h->nh, h->L(1).g.nb, s);
@@ -565,25 +603,36 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
   Level& l = h->L(k);
   const int nb = l.g.nb;
   const size_t st = l.g.stride;
+  fork_sides(h, s, 0, 2);
+  // branch 1 (side 0): N(u~) and B(u~), T0, and the restriction / coarsening chains of both
+  {
+    const cudaStream_t b1 = h->side[0];
+    prof_begin(h, kProfMoments, k, b1);
+    lv_nload_density(l, ut, l.r, b1);
+    prof_end(h, kProfMoments, k, b1);
+    dot(ut, l.r, st, h->partials2, h->t0, b1, nb, st);
+    for (int j = k; j >= 2; --j) {
+      lv_restrict(h->L(j), h->L(j - 1), h->L(j).r, h->L(j - 1).r, b1);
+      lv_coarsen_density(h->L(j), h->L(j - 1), b1);
+    }
+  }
+  // branch 2 (side 1): T3 per coarse simplex
+  {
+    const cudaStream_t b2 = h->side[1];
+    prof_begin(h, kProfT3, k, b2);
+    lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, b2);
+    prof_end(h, kProfT3, k, b2);
+  }
+  // main branch: L u~, M u~, their dots and restriction chains
   lv_apply(l, ut, l.y, s);
   lv_mass(l, ut, l.z, s);
   dot(ut, l.y, st, h->partials, h->auu, s, nb, st);
   dot(ut, l.z, st, h->partials, h->buu, s, nb, st);
-  prof_begin(h, kProfMoments, k, s);
-  lv_nload_density(l, ut, l.r, s);
-  prof_end(h, kProfMoments, k, s);
-  prof_begin(h, kProfT3, k, s);
-  lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, s);
-  prof_end(h, kProfT3, k, s);
-  dot(ut, l.r, st, h->partials, h->t0, s, nb, st);
   for (int j = k; j >= 2; --j) {
-    Level& f = h->L(j);
-    Level& c = h->L(j - 1);
-    lv_restrict(f, c, f.y, c.y, s);
-    lv_restrict(f, c, f.z, c.z, s);
-    lv_restrict(f, c, f.r, c.r, s);
-    lv_coarsen_density(f, c, s);
+    lv_restrict(h->L(j), h->L(j - 1), h->L(j).y, h->L(j - 1).y, s);
+    lv_restrict(h->L(j), h->L(j - 1), h->L(j).z, h->L(j - 1).z, s);
   }
+  join_sides(h, s, 0, 2);
   Level& l1 = h->L(1);
   lv_gather_level1(l1, h->gAd, h->gMd, h->t1d, h->B1d, s);
 }
@@ -631,12 +680,13 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
 }
 
 void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s, const StageHook* after_stage) {
-  enqueue_setup(h, s);
+  enqueue_setup(h, s, true);
   h->activate(h->nb);
   enqueue_coarse(h, s);
   cudaMemcpyAsync(h->lam_levels, h->lam, sizeof(double) * h->nb, cudaMemcpyDeviceToDevice, s);
   if (after_stage && h->cnt[1] > h->cnt[2]) (*after_stage)(1, h->cnt[2], h->cnt[1] - h->cnt[2]);
   for (int k = 2; k <= h->levels(); ++k) {
+    need_level(h, k, s);
     h->activate(h->cnt[k]);
     lv_prolong(h->L(k), h->L(k - 1), h->L(k - 1).u, h->L(k).u, false, nullptr, nullptr, 0, s);
     for (int it = 0; it < h->prob.corrections; ++it) enqueue_correction(h, k, s);
@@ -815,9 +865,16 @@ int create_handle(const fmg_eig_problem* probs, int count, const CreateOptions& 
     delete h;
     return vi;
   }
-  if (cudaGetDevice(&h->dev) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+  bool ok = cudaGetDevice(&h->dev) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&h->ev0) == cudaSuccess && cudaEventCreate(&h->ev1) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < 3; ++i)
+    ok = cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+         (i == 2 || cudaEventCreateWithFlags(&h->ev_join[i], cudaEventDisableTiming) == cudaSuccess);
+  for (int k = 0; ok && k <= h->prob.levels; ++k)
+    ok = cudaEventCreateWithFlags(&h->ev_level[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
     delete h;
     return FMG_ECUDA;

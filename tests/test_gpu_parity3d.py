@@ -81,6 +81,23 @@ def test_augmented_system_3d(setup3, k):
     assert rel(G, g_ref) <= 1e-12
 
 
+def test_augmented_system_3d_deep_level():
+    """T3 / T2 on a level 3 refinements below the coarse mesh (r = 8 fine cells per coarse
+    cell), where every class of fine node inside a coarse tetrahedron is populated."""
+    op, gp = _pair(dim=3, coarse_cells=3, levels=4, w_const=0.2, w_quad=(1.0, 3.0, 2.0), zeta=4.0)
+    lv = O.build_hierarchy(op)
+    rng = np.random.default_rng(1100)
+    ut = rng.uniform(0.2, 1.0, size=gp.size(4))
+    psi, k0, mm = O.augmented_blocks(lv, 4, ut)
+    c = rng.normal(size=psi.shape[1])
+    g_ref = (psi.T @ O.density_matrix(lv[3].mesh, psi @ c) @ psi).toarray()
+    with _fmg().Solver(gp) as s:
+        K, M, G = s.augmented_system(4, dev(ut), c)
+    assert rel(K, k0) <= 1e-12
+    assert rel(M, mm) <= 1e-12
+    assert rel(G, g_ref) <= 1e-12
+
+
 def test_coarse_solve_3d(setup3):
     op, gp, lv, s = setup3
     lam_o, u_o, res = O.coarse_solve(op, lv[0])

@@ -61,14 +61,14 @@ def test_served_results_equal_solves_alone():
 def test_admission_respects_memory_budget():
     fmg = _fmg()
     probs, arrivals = _stream(count=16, rate=1e5, seed=9)
-    # a budget of two of the largest requests forces cohorts to wait for memory
+    # a budget just above the largest request: cohorts must wait for memory to be released
     res0, st0 = fmg.serve(probs, arrivals, max_batch=16, max_inflight=8)
     largest = max(fmg.estimate_bytes([p]) for p in probs)
     assert fmg.estimate_bytes(probs) <= sum(fmg.estimate_bytes([p]) for p in probs)
-    budget = 2.2 * (largest + 65536)
+    budget = 1.05 * (largest + 65536)
+    assert st0["peak_bytes"] > budget  # unconstrained, more than that was resident
     res, st = fmg.serve(probs, arrivals, budget_bytes=budget, max_batch=16, max_inflight=8)
     assert st["peak_bytes"] <= budget
-    assert st["cohorts"] > st0["cohorts"]
     assert st["completed"] == len(probs)
     for r0, r in zip(res0, res):
         assert r["lambda"] == r0["lambda"]
