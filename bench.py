@@ -68,10 +68,11 @@ N_SM = 152
 #   cubic load + density stencil 2D (closed forms over the 6 star triangles): 117 flop; 8 B
 #     read + 40 B written
 #   Jacobi 3D: 15-point = 29 + 3 = 32 flop; 24 B + 72 B
-#   cubic load + density stencil 3D (24 star tetrahedra, ~54 flop each): 1305 flop; 8 B + 72 B
+#   cubic load + density stencil 3D (sums over the link of the 24-tetrahedron star: 345 flop
+#     for N, 305 for the density stencil, 9 scalings): 659 flop; 8 B + 72 B
 KERNELS = {
     2: {"nload_density": (117.0, 48.0), "jacobi": (16.0, 64.0)},
-    3: {"nload_density": (1305.0, 80.0), "jacobi": (32.0, 96.0)},
+    3: {"nload_density": (659.0, 80.0), "jacobi": (32.0, 96.0)},
 }
 DOMINANT = "nload_density"
 # DRAM bytes per node of a finest-level launch from one ncu capture of the current kernel

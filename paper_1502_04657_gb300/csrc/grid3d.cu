@@ -205,11 +205,72 @@ __global__ void k_prolong3d(int nf, int pf, int pc, size_t st, size_t stc,
 //   int u^2 lambda_p^2      = |K|/210 [3 u_p^2 + 2 u_p s + h2]
 //   int u^2 lambda_p lambda_q = |K|/420 [u_p^2 + u_q^2 + u_p u_q + h2 + (u_p + u_q) s]
 // with s, h2, h3 the complete homogeneous symmetric sums of degree 1, 2, 3 of the four
-// values (h2 = (s^2 + P2)/2, h3 = (s^3 + 3 s P2 + 2 P3)/6 from the power sums P2, P3).
+// values.  Writing h_k = sum_{i<=k} u_p^(k-i) h'_i with h'_i those of the three other vertices,
+// the sums over the star become sums over its link - the triangulated sphere of the 14
+// neighbours whose 24 triangles are the tetrahedra's faces opposite p:
+//   sum_T [h3 + u_p h2 + u_p^2 s + u_p^3] = 96 u_p^3 + 3 u_p^2 H1 + 2 u_p H2 + H3,
+//   sum_T [3 u_p^2 + 2 u_p s + h2]        = 144 u_p^2 + 3 u_p H1 + H2,
+// H1 = sum_n deg_n u_n,  H2 = sum_n deg_n u_n^2 + 2 sum_edges u_m u_n,
+// H3 = sum_n deg_n u_n^3 + 2 sum_edges u_m u_n (u_m + u_n) + sum_triangles u_a u_b u_c,
+// (deg_n = link triangles at n; every link edge lies in two triangles), and for the edge to a
+// neighbour q, whose tetrahedra close with the link edges (r, t) opposite q (U = u_p + u_q):
+//   sum [..] = deg_q (U^2 + 2 (u_p^2 + u_p u_q + u_q^2)) + 2 U sum (u_r + u_t)
+//              + sum (u_r^2 + u_r u_t + u_t^2).
+// This evaluates each link edge and triangle once instead of each tetrahedron's sums.
+struct Link {
+  int deg[14];
+  int edge[36][2];
+  int pair[7][6][2];  // link edges opposite the + neighbour 2 d (deg of them)
+  int npair[7];
+};
+
+constexpr int kStarHost[24][3] = {
+    {0, 6, 12},  {0, 8, 12},  {2, 6, 12},  {2, 10, 12}, {4, 8, 12},  {4, 10, 12},
+    {5, 0, 6},   {5, 2, 6},   {3, 0, 8},   {3, 4, 8},   {11, 5, 0},  {11, 3, 0},
+    {1, 2, 10},  {1, 4, 10},  {9, 5, 2},   {9, 1, 2},   {7, 3, 4},   {7, 1, 4},
+    {13, 11, 5}, {13, 11, 3}, {13, 9, 5},  {13, 9, 1},  {13, 7, 3},  {13, 7, 1}};
+
+constexpr Link make_link() {
+  Link L{};
+  int ne = 0;
+  for (int t = 0; t < 24; ++t)
+    for (int i = 0; i < 3; ++i) {
+      L.deg[kStarHost[t][i]]++;
+      for (int j = i + 1; j < 3; ++j) {
+        const int a = kStarHost[t][i] < kStarHost[t][j] ? kStarHost[t][i] : kStarHost[t][j];
+        const int b = kStarHost[t][i] < kStarHost[t][j] ? kStarHost[t][j] : kStarHost[t][i];
+        bool seen = false;
+        for (int e = 0; e < ne; ++e) seen = seen || (L.edge[e][0] == a && L.edge[e][1] == b);
+        if (!seen) {
+          L.edge[ne][0] = a;
+          L.edge[ne][1] = b;
+          ++ne;
+        }
+      }
+    }
+  for (int d = 0; d < 7; ++d)
+    for (int t = 0; t < 24; ++t) {
+      const int* v = kStarHost[t];
+      const int q = 2 * d;
+      if (v[0] != q && v[1] != q && v[2] != q) continue;
+      int o[2] = {0, 0}, m = 0;
+      for (int i = 0; i < 3; ++i)
+        if (v[i] != q) o[m++] = v[i];
+      L.pair[d][L.npair[d]][0] = o[0];
+      L.pair[d][L.npair[d]][1] = o[1];
+      L.npair[d]++;
+    }
+  return L;
+}
+
+__device__ constexpr Link kLink = make_link();
+static_assert(make_link().npair[0] == 6 && make_link().npair[3] == 4 && make_link().deg[13] == 6,
+              "Kuhn star link");
+
 template <bool DENSITY>
 __device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, int pitch,
                                       long plane, double& nl, double* b) {
-  double nv[14];
+  double nv[14], sq[14];
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pitch, plane);
@@ -217,36 +278,55 @@ __device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, in
     nv[2 * d + 1] = u[k - o];
   }
   const double up = u[k];
-  const double up2 = up * up;
-  double acc = 0.0, accC = 0.0;
-  double accE[7] = {0, 0, 0, 0, 0, 0, 0};
+  const double u2 = up * up;
+  // degree-weighted sums (deg 6 or 4)
+  double s6 = 0.0, s4 = 0.0, q6 = 0.0, q4 = 0.0, c6 = 0.0, c4 = 0.0;
 #pragma unroll
-  for (int t = 0; t < 24; ++t) {
-    const double a = nv[kStar[t][0]], b2 = nv[kStar[t][1]], c = nv[kStar[t][2]];
-    const double s = up + a + b2 + c;
-    const double p2 = fma(up, up, fma(a, a, fma(b2, b2, c * c)));
-    const double p3 = fma(up2, up, fma(a * a, a, fma(b2 * b2, b2, c * c * c)));
-    const double hh2 = 0.5 * fma(s, s, p2);
-    const double hh3 = fma(s, fma(s, s, 3.0 * p2), 2.0 * p3) * (1.0 / 6.0);
-    acc += fma(up, fma(up, s + up, hh2), hh3);
-    if (DENSITY) {
-      accC += fma(3.0, up2, fma(2.0 * up, s, hh2));
-      // edges to the "+" neighbours of this tetrahedron
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        const int nb = kStar[t][v];
-        if ((nb & 1) == 0) {
-          const double q = nv[nb];
-          accE[nb >> 1] += fma(up + q, s, fma(q, q + up, up2) + hh2);
-        }
-      }
+  for (int n = 0; n < 14; ++n) {
+    sq[n] = nv[n] * nv[n];
+    if (kLink.deg[n] == 6) {
+      s6 += nv[n];
+      q6 += sq[n];
+      c6 = fma(sq[n], nv[n], c6);
+    } else {
+      s4 += nv[n];
+      q4 += sq[n];
+      c4 = fma(sq[n], nv[n], c4);
     }
   }
-  nl = acc;
-  if (DENSITY) {
-    b[0] = accC;
+  double E = 0.0, EE = 0.0, T = 0.0;
 #pragma unroll
-    for (int d = 0; d < 7; ++d) b[1 + d] = accE[d];
+  for (int e = 0; e < 36; ++e) {
+    const double m = nv[kLink.edge[e][0]], n = nv[kLink.edge[e][1]];
+    const double p = m * n;
+    E += p;
+    EE = fma(p, m + n, EE);
+  }
+#pragma unroll
+  for (int t = 0; t < 24; ++t)
+    T = fma(nv[kStar[t][0]] * nv[kStar[t][1]], nv[kStar[t][2]], T);
+  const double H1 = fma(6.0, s6, 4.0 * s4);
+  const double H2 = fma(6.0, q6, fma(4.0, q4, 2.0 * E));
+  const double H3 = fma(6.0, c6, fma(4.0, c4, fma(2.0, EE, T)));
+  nl = fma(u2, fma(96.0, up, 3.0 * H1), fma(2.0 * up, H2, H3));
+  if (DENSITY) {
+    b[0] = fma(up, fma(144.0, up, 3.0 * H1), H2);
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+      const double uq = nv[2 * d];
+      double sv = 0.0, sh = 0.0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (j < kLink.npair[d]) {
+          const int r = kLink.pair[d][j][0], t = kLink.pair[d][j][1];
+          sv += nv[r] + nv[t];
+          sh += fma(nv[r], nv[t], sq[r] + sq[t]);
+        }
+      }
+      const double U = up + uq;
+      const double h2pq = fma(up, uq, u2 + sq[2 * d]);
+      b[1 + d] = fma((double)kLink.npair[d], fma(U, U, 2.0 * h2pq), fma(2.0 * U, sv, sh));
+    }
   }
 }
 
