@@ -220,7 +220,7 @@ def reference_arm(args):
 
 def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist=None,
             with_e2e: bool = True, clocks: bool = True, levels: int | None = None,
-            autotune: bool = True) -> dict:
+            autotune: bool = True, flags: int = 0) -> dict:
     import torch
 
     from paper_1502_04657_gb300 import fmg
@@ -232,8 +232,7 @@ def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist
     gp = fmg.Problem(**{k: v for k, v in kw.items() if k in fmg.Problem.__dataclass_fields__})
     if mixed:
         gp.precision = fmg.FMG_MIXED_FP32
-    if not autotune:
-        gp.flags = fmg.FMG_FLAG_NO_AUTOTUNE
+    gp.flags = flags | (0 if autotune else fmg.FMG_FLAG_NO_AUTOTUNE)
     n = gp.size(gp.levels)
     solver = fmg.Solver(gp)
     stream = torch.cuda.Stream()
@@ -286,6 +285,9 @@ def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist
         out["e2e"] = {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                       "h2d_bytes_per_step": 112, "d2h_bytes_per_step": 8 + 8 * n + 4 * 16}
         out["lambda_e2e"] = lam_e2e
+        _, st, _ = solver.solve(u_host, stats=True)
+        out["scf_iters"] = list(st.scf_iters)[:gp.levels]
+        out["identity_defect"] = st.identity_defect
     solver.close()
     return out
 
@@ -534,13 +536,16 @@ def ours_arm(args):
         "clocks": m["clocks"], "e2e": m["e2e"], "gpu_launches": args.steps * m["kernels"],
         "kernels_per_step": m["kernels"], "roofline": main, "roofline_other": other,
         "kernel_ms_finest": m["profile"],
+        "small_solve_iters_per_level": m.get("scf_iters"),
+        "identity_defect": m.get("identity_defect"),
     }
     if args.workload == "config2" and not args.no_extras:
-        mx = measure("config2-mixed", max(3, args.steps // 2), 3, world, local, dist,
-                     with_e2e=False, clocks=False)
-        line["mixed_fp32"] = {"value": mx["value"], "unit": "solves/s", "ms_per_step": mx["ms_per_step"],
-                              "lambda": mx["lambda"],
-                              "dlambda_rel_vs_fp64": abs(mx["lambda"] - m["lambda"]) / m["lambda"]}
+        for key, flags in (("mixed_fp32", 0), ("mixed_fp32_rhs32", 2)):
+            mx = measure("config2-mixed", max(3, args.steps // 2), 3, world, local, dist,
+                         with_e2e=False, clocks=False, flags=flags)
+            line[key] = {"value": mx["value"], "unit": "solves/s", "ms_per_step": mx["ms_per_step"],
+                         "lambda": mx["lambda"],
+                         "dlambda_rel_vs_fp64": abs(mx["lambda"] - m["lambda"]) / m["lambda"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         config = WORKLOADS[args.workload][0]
         levels = ORACLE_SAMPLE[config][0]

@@ -89,6 +89,11 @@ void lv_rhs(Level& l, const double* lam, const PotentialParams* p, const double*
   if (l.g.dim == 2) rhs2d(l.g, lam, p, u, f, s);
   else rhs3d(l.g, lam, p, u, f, s);
 }
+void lv_rhs_f32(Level& l, const double* lam, const PotentialParams* p, const double* u,
+                double* f, cudaStream_t s) {
+  if (l.g.dim == 2) rhs2d_f32(l.g, lam, p, u, f, s);
+  else rhs3d_f32(l.g, lam, p, u, f, s);
+}
 void lv_nload_density(Level& l, const double* u, double* nl, cudaStream_t s) {
   if (l.g.dim == 2) nload_density2d(l.g, u, nl, l.b, s);
   else nload_density3d(l.g, u, nl, l.b3, s);
@@ -171,7 +176,8 @@ int validate(const fmg_eig_problem* p) {
   if (!(p->box_len > 0.0) || !(p->zeta >= 0.0) || !(p->omega > 0.0 && p->omega <= 1.0))
     return FMG_EINVAL;
   if (!(p->scf_tol > 0.0) || p->scf_max_iter < 1) return FMG_EINVAL;
-  if (p->flags & ~FMG_FLAG_NO_AUTOTUNE) return FMG_EINVAL;
+  if (p->flags & ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS)) return FMG_EINVAL;
+  if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision != FMG_MIXED_FP32) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
   if (p->smoother != FMG_SMOOTH_JACOBI) return FMG_ENOTSUP;
@@ -658,7 +664,9 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   const int nb = l.g.nb;
   // step 1: auxiliary problem, m V-cycles from u
   prof_begin(h, kProfRhs, k, s);
-  lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
+  if (h->prob.precision == FMG_MIXED_FP32 && (h->prob.flags & FMG_FLAG_FP32_RHS))
+    lv_rhs_f32(l, h->lam, h->dparams, l.u, l.f, s);
+  else lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
   prof_end(h, kProfRhs, k, s);
   cudaMemcpyAsync(l.x, l.u, l.g.stride * nb * sizeof(double), cudaMemcpyDeviceToDevice, s);
   enqueue_multigrid(h, k, s);

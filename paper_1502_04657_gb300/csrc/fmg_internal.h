@@ -69,6 +69,9 @@ void nload2d(const Grid& g, const double* u, double* out, cudaStream_t s);
 // f = lam[b] * M u - p[b].zeta * N(u) for instance b
 void rhs2d(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
            double* f, cudaStream_t s);
+// the same right-hand side evaluated in FP32 (mixed-precision iteration), stored in FP64
+void rhs2d_f32(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
+               double* f, cudaStream_t s);
 // Dense level-1 matrices L_1 and M_1 (n1-1)^2 square, row-major, interior numbering (one
 // pair per instance, back to back).
 void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s);
@@ -103,6 +106,8 @@ void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* x
 void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s);
 void rhs3d(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
            double* f, cudaStream_t s);
+void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
+               double* f, cudaStream_t s);
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s);
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,

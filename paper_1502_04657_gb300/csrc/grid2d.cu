@@ -165,34 +165,35 @@ __global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
 // triangle with p), summing int_K u^3 lambda_p = |K|/60 sum_{|b|=3} u^b (b_p + 1) gives
 //   |K|/60 [24u^3 + 6u^2 S1 + 2u(2 S2 + P) + 2 S3 + Q],
 // S_q = sum n_k^q, P = sum n_k n_{k+1}, Q = sum n_k n_{k+1} (n_k + n_{k+1}), |K| = h^2/2.
-__device__ __forceinline__ double nload_at(const double* __restrict__ u, size_t k, int pitch) {
-  const double up = u[k];
-  const double n0 = u[k + 1], n1 = u[k + pitch + 1], n2 = u[k + pitch];
-  const double n3 = u[k - 1], n4 = u[k - pitch - 1], n5 = u[k - pitch];
-  const double s1 = ((n0 + n1) + (n2 + n3)) + (n4 + n5);
-  const double q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = n3 * n3, q4 = n4 * n4,
-               q5 = n5 * n5;
-  const double s2 = ((q0 + q1) + (q2 + q3)) + (q4 + q5);
-  double s3 = q0 * n0;
+// T is the arithmetic type: double except in the FP32 auxiliary right-hand side of the
+// mixed-precision iteration (k_rhs2d_f32).
+template <typename T = double>
+__device__ __forceinline__ T nload_at(const double* __restrict__ u, size_t k, int pitch) {
+  const T up = (T)u[k];
+  const T n0 = (T)u[k + 1], n1 = (T)u[k + pitch + 1], n2 = (T)u[k + pitch];
+  const T n3 = (T)u[k - 1], n4 = (T)u[k - pitch - 1], n5 = (T)u[k - pitch];
+  const T s1 = ((n0 + n1) + (n2 + n3)) + (n4 + n5);
+  const T q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = n3 * n3, q4 = n4 * n4, q5 = n5 * n5;
+  const T s2 = ((q0 + q1) + (q2 + q3)) + (q4 + q5);
+  T s3 = q0 * n0;
   s3 = fma(q1, n1, s3);
   s3 = fma(q2, n2, s3);
   s3 = fma(q3, n3, s3);
   s3 = fma(q4, n4, s3);
   s3 = fma(q5, n5, s3);
-  const double p0 = n0 * n1, p1 = n1 * n2, p2 = n2 * n3, p3 = n3 * n4, p4 = n4 * n5,
-               p5 = n5 * n0;
-  const double pp = ((p0 + p1) + (p2 + p3)) + (p4 + p5);
-  double qq = p0 * (n0 + n1);
+  const T p0 = n0 * n1, p1 = n1 * n2, p2 = n2 * n3, p3 = n3 * n4, p4 = n4 * n5, p5 = n5 * n0;
+  const T pp = ((p0 + p1) + (p2 + p3)) + (p4 + p5);
+  T qq = p0 * (n0 + n1);
   qq = fma(p1, n1 + n2, qq);
   qq = fma(p2, n2 + n3, qq);
   qq = fma(p3, n3 + n4, qq);
   qq = fma(p4, n4 + n5, qq);
   qq = fma(p5, n5 + n0, qq);
-  const double u2 = up * up;
-  double v = 24.0 * u2 * up;
-  v = fma(6.0 * u2, s1, v);
-  v = fma(2.0 * up, fma(2.0, s2, pp), v);
-  v = fma(2.0, s3, v);
+  const T u2 = up * up;
+  T v = T(24) * u2 * up;
+  v = fma(T(6) * u2, s1, v);
+  v = fma(T(2) * up, fma(T(2), s2, pp), v);
+  v = fma(T(2), s3, v);
   return v + qq;
 }
 
@@ -211,6 +212,21 @@ __global__ void k_rhs2d(int n, int pitch, size_t st, double h2_12, double h2_120
                    (u[k + pitch + 1] + u[k - pitch - 1]);
   const double mu = h2_12 * fma(6.0, u[k], s);
   f[k] = fma(lam[ib], mu, -nscale * nload_at(u, k, pitch));
+}
+
+// FP32 auxiliary right-hand side of the mixed-precision iteration (same closed forms in
+// single precision, FP64 result): the V-cycles that consume it are FP32 as well, and its
+// rounding moves u~ by ~1e-7, which reaches lambda only at second order through the
+// augmented solve.
+__global__ void k_rhs2d_f32(int n, int pitch, size_t st, float h2_12, float h2_120,
+                            const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                            const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_2D
+  const float nscale = (float)pp[ib].zeta * h2_120;
+  const float s = (((float)u[k + 1] + (float)u[k - 1]) + ((float)u[k + pitch] + (float)u[k - pitch])) +
+                  ((float)u[k + pitch + 1] + (float)u[k - pitch - 1]);
+  const float mu = h2_12 * fmaf(6.0f, (float)u[k], s);
+  f[k] = (double)fmaf((float)lam[ib], mu, -nscale * nload_at<float>(u, k, pitch));
 }
 
 __global__ void k_dense_level1_2d(int n, int pitch, size_t st, double h2_12, Coef2D c,
@@ -314,6 +330,12 @@ void rhs2d(const Grid& g, const double* lam, const PotentialParams* p, const dou
            double* f, cudaStream_t s) {
   k_rhs2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
       g.n, g.pitch, g.stride, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
+}
+
+void rhs2d_f32(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
+               double* f, cudaStream_t s) {
+  k_rhs2d_f32<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
+      g.n, g.pitch, g.stride, (float)(g.h * g.h / 12.0), (float)(g.h * g.h / 120.0), lam, p, u, f);
 }
 
 void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s) {

@@ -142,17 +142,18 @@ __global__ void k_residual3d(int n, int pitch, size_t st, Coef3D c, const double
   r[k] = f[k] - lop3(c, x, k, pitch, plane);
 }
 
-__device__ __forceinline__ double mass_at(const double* __restrict__ x, size_t k, int pitch,
-                                          long plane) {
-  double ax = 0.0, fd = 0.0;
+template <typename T = double>
+__device__ __forceinline__ T mass_at(const double* __restrict__ x, size_t k, int pitch,
+                                     long plane) {
+  T ax = 0, fd = 0;
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pitch, plane);
-    const double s = x[k + o] + x[k - o];
+    const T s = (T)x[k + o] + (T)x[k - o];
     if (d >= 3 && d < 6) fd += s;
     else ax += s;
   }
-  return fma(0.4, x[k], fma(1.0 / 20.0, ax, fd * (1.0 / 30.0)));
+  return fma(T(0.4), (T)x[k], fma(T(1.0 / 20.0), ax, fd * T(1.0 / 30.0)));
 }
 
 __global__ void k_mass3d(int n, int pitch, size_t st, double h3, const double* __restrict__ x,
@@ -267,20 +268,22 @@ __device__ constexpr Link kLink = make_link();
 static_assert(make_link().npair[0] == 6 && make_link().npair[3] == 4 && make_link().deg[13] == 6,
               "Kuhn star link");
 
-template <bool DENSITY>
+// T is the arithmetic type: double everywhere except the FP32 auxiliary right-hand side of
+// the mixed-precision iteration (k_rhs3d_f32).
+template <typename T, bool DENSITY>
 __device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, int pitch,
-                                      long plane, double& nl, double* b) {
-  double nv[14], sq[14];
+                                      long plane, T& nl, T* b) {
+  T nv[14], sq[14];
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pitch, plane);
-    nv[2 * d] = u[k + o];
-    nv[2 * d + 1] = u[k - o];
+    nv[2 * d] = (T)u[k + o];
+    nv[2 * d + 1] = (T)u[k - o];
   }
-  const double up = u[k];
-  const double u2 = up * up;
+  const T up = (T)u[k];
+  const T u2 = up * up;
   // degree-weighted sums (deg 6 or 4)
-  double s6 = 0.0, s4 = 0.0, q6 = 0.0, q4 = 0.0, c6 = 0.0, c4 = 0.0;
+  T s6 = 0, s4 = 0, q6 = 0, q4 = 0, c6 = 0, c4 = 0;
 #pragma unroll
   for (int n = 0; n < 14; ++n) {
     sq[n] = nv[n] * nv[n];
@@ -294,27 +297,27 @@ __device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, in
       c4 = fma(sq[n], nv[n], c4);
     }
   }
-  double E = 0.0, EE = 0.0, T = 0.0;
+  T E = 0, EE = 0, Tr = 0;
 #pragma unroll
   for (int e = 0; e < 36; ++e) {
-    const double m = nv[kLink.edge[e][0]], n = nv[kLink.edge[e][1]];
-    const double p = m * n;
+    const T m = nv[kLink.edge[e][0]], n = nv[kLink.edge[e][1]];
+    const T p = m * n;
     E += p;
     EE = fma(p, m + n, EE);
   }
 #pragma unroll
   for (int t = 0; t < 24; ++t)
-    T = fma(nv[kStar[t][0]] * nv[kStar[t][1]], nv[kStar[t][2]], T);
-  const double H1 = fma(6.0, s6, 4.0 * s4);
-  const double H2 = fma(6.0, q6, fma(4.0, q4, 2.0 * E));
-  const double H3 = fma(6.0, c6, fma(4.0, c4, fma(2.0, EE, T)));
-  nl = fma(u2, fma(96.0, up, 3.0 * H1), fma(2.0 * up, H2, H3));
+    Tr = fma(nv[kStar[t][0]] * nv[kStar[t][1]], nv[kStar[t][2]], Tr);
+  const T H1 = fma(T(6), s6, T(4) * s4);
+  const T H2 = fma(T(6), q6, fma(T(4), q4, T(2) * E));
+  const T H3 = fma(T(6), c6, fma(T(4), c4, fma(T(2), EE, Tr)));
+  nl = fma(u2, fma(T(96), up, T(3) * H1), fma(T(2) * up, H2, H3));
   if (DENSITY) {
-    b[0] = fma(up, fma(144.0, up, 3.0 * H1), H2);
+    b[0] = fma(up, fma(T(144), up, T(3) * H1), H2);
 #pragma unroll
     for (int d = 0; d < 7; ++d) {
-      const double uq = nv[2 * d];
-      double sv = 0.0, sh = 0.0;
+      const T uq = nv[2 * d];
+      T sv = 0, sh = 0;
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
         if (j < kLink.npair[d]) {
@@ -323,9 +326,9 @@ __device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, in
           sh += fma(nv[r], nv[t], sq[r] + sq[t]);
         }
       }
-      const double U = up + uq;
-      const double h2pq = fma(up, uq, u2 + sq[2 * d]);
-      b[1 + d] = fma((double)kLink.npair[d], fma(U, U, 2.0 * h2pq), fma(2.0 * U, sv, sh));
+      const T U = up + uq;
+      const T h2pq = fma(up, uq, u2 + sq[2 * d]);
+      b[1 + d] = fma((T)kLink.npair[d], fma(U, U, T(2) * h2pq), fma(T(2) * U, sv, sh));
     }
   }
 }
@@ -334,7 +337,7 @@ __global__ void k_nload3d(int n, int pitch, size_t st, double scale, const doubl
                           double* __restrict__ out) {
   INTERIOR_3D
   double nl;
-  star3<false>(u, k, pitch, plane, nl, nullptr);
+  star3<double, false>(u, k, pitch, plane, nl, nullptr);
   out[k] = scale * nl;
 }
 
@@ -343,18 +346,32 @@ __global__ void k_rhs3d(int n, int pitch, size_t st, double h3, double nscale,
                         const double* __restrict__ u, double* __restrict__ f) {
   INTERIOR_3D
   double nl;
-  star3<false>(u, k, pitch, plane, nl, nullptr);
+  star3<double, false>(u, k, pitch, plane, nl, nullptr);
   const double mu = h3 * mass_at(u, k, pitch, plane);
   f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * nl);
 }
 
 // s140, s210, s420 = |K| / 140, / 210, / 420 (host-side: no FP64 division per node)
+// FP32 auxiliary right-hand side of the mixed-precision iteration (same closed forms in
+// single precision, FP64 result): the V-cycles that consume it are FP32 as well, and its
+// rounding moves u~ by ~1e-7, which reaches lambda only at second order through the
+// augmented solve.
+__global__ void k_rhs3d_f32(int n, int pitch, size_t st, float h3, float nscale,
+                            const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                            const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_3D
+  float nl;
+  star3<float, false>(u, k, pitch, plane, nl, nullptr);
+  const float mu = h3 * mass_at<float>(u, k, pitch, plane);
+  f[k] = (double)fmaf((float)lam[ib], mu, -((float)pp[ib].zeta * nscale) * nl);
+}
+
 __global__ void k_nload_density3d(int n, int pitch, size_t st, double s140, double s210,
                                   double s420, const double* __restrict__ u,
                                   double* __restrict__ nl, Density3D b) {
   INTERIOR_3D
   double v, e[8];
-  star3<true>(u, k, pitch, plane, v, e);
+  star3<double, true>(u, k, pitch, plane, v, e);
   nl[k] = s140 * v;
   b.a[0][k] = s210 * e[0];
 #pragma unroll
@@ -537,6 +554,13 @@ void rhs3d(const Grid& g, const double* lam, const PotentialParams* p, const dou
            double* f, cudaStream_t s) {
   const double h3 = g.h * g.h * g.h;
   k_rhs3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, h3, h3 / 6.0 / 140.0, lam, p, u, f);
+}
+
+void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
+               double* f, cudaStream_t s) {
+  const double h3 = g.h * g.h * g.h;
+  k_rhs3d_f32<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, (float)h3,
+                                      (float)(h3 / 6.0 / 140.0), lam, p, u, f);
 }
 
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,

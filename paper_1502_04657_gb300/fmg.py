@@ -15,6 +15,7 @@ FMG_OK, FMG_EINVAL, FMG_ENOMEM, FMG_ENOCONV, FMG_ECUDA, FMG_ETIMEOUT, FMG_ENOTSU
 FMG_FP64, FMG_MIXED_FP32 = 0, 1
 FMG_W_LEFT, FMG_PAPER_LITERAL = 0, 1
 FMG_FLAG_NO_AUTOTUNE = 1
+FMG_FLAG_FP32_RHS = 2
 FMG_MAX_LEVELS = 16
 
 

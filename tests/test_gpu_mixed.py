@@ -60,3 +60,29 @@ def test_mixed_multigrid_converges_like_fp64():
     xh = x.cpu().numpy()
     r = f - lv[-1].L @ xh
     assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(f)
+
+
+def test_fp32_rhs_flag_stays_within_dlambda():
+    """FMG_FLAG_FP32_RHS (right-hand side in FP32 too) on the 3D trap: still |dlambda| <= 1e-8
+    relative to FP64, with a larger error than the default mixed mode."""
+    fmg = _fmg()
+    kw = dict(dim=3, coarse_cells=4, levels=4, w_quad=(100.0, 100.0, 400.0), zeta=100.0)
+    op, gp = _pair(**kw)
+    with fmg.Solver(gp) as s:
+        lam64, _, rc = s.solve()
+    assert rc == 0
+    gp.precision = fmg.FMG_MIXED_FP32
+    gp.flags = fmg.FMG_FLAG_FP32_RHS
+    with fmg.Solver(gp) as s:
+        lam32, _, rc = s.solve()
+    assert rc == 0
+    assert abs(lam32 - lam64) <= DLAM * lam64
+
+
+def test_fp32_rhs_flag_needs_mixed_precision():
+    fmg = _fmg()
+    _, gp = _pair(dim=2, coarse_cells=4, levels=3)
+    gp.flags = fmg.FMG_FLAG_FP32_RHS
+    with pytest.raises(fmg.FmgError) as e:
+        fmg.Solver(gp)
+    assert e.value.code == fmg.FMG_EINVAL
