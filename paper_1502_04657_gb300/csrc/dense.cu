@@ -43,7 +43,7 @@ constexpr double kSwitch = 1e-2;  // relative residual below which Newton takes 
 
 struct Smem {
   double *K0, *MM, *G, *A, *B1, *loc, *q4;
-  double *c, *Mc, *Hc, *Gc, *r, *y1, *y2, *dinv, *red;
+  double *c, *Mc, *Hc, *Gc, *r, *y1, *y2, *dinv, *red, *sv;
   int* sym3;  // nv^3 table of sorted-triple indices
   int *tri, *adj;  // shared copies of the simplex and adjacency tables
   double *t3, *t1;  // shared copies of the fine-pass integrals (augmented problem)
@@ -81,117 +81,134 @@ __device__ double dotv(const double* a, const double* b, int n, double* red) {
   return block_sum(s, red);
 }
 
-// rows of (K0 c, G c, M c), one warp per row
-__device__ void apply_all(Smem& s) {
-  const int n = s.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int a = warp; a < n; a += kWarps) {
-    const double* kr = s.K0 + (size_t)a * n;
-    const double* gr = s.G + (size_t)a * n;
-    const double* mr = s.MM + (size_t)a * n;
-    double hk = 0.0, hg = 0.0, mc = 0.0;
-    for (int b = lane; b < n; b += 32) {
-      const double cb = s.c[b];
-      hk = fma(kr[b], cb, hk);
-      hg = fma(gr[b], cb, hg);
-      mc = fma(mr[b], cb, mc);
+// y_q = sum_b X_q[a][b] x_b for up to three symmetric n x n matrices X_q and every row a:
+// thread t takes row a = t % n and the columns b = part, part + parts, ... (part = t / n), so
+// the lanes of a warp read consecutive rows of one column (conflict-free, X symmetric); the
+// row's thread then adds the parts in a fixed order.  `red` holds parts * n * 3 doubles.
+template <int NM>
+__device__ void symv(const double* const* X, const double* x, double* const* y, int n,
+                     double* red) {
+  const int parts = n <= kThreads ? kThreads / n : 1;
+  const int t = threadIdx.x;
+  const int a = t % n, part = t / n;
+  if (part < parts && t < parts * n) {
+    double acc[NM];
+#pragma unroll
+    for (int q = 0; q < NM; ++q) acc[q] = 0.0;
+    for (int b = part; b < n; b += parts) {
+      const double xb = x[b];
+#pragma unroll
+      for (int q = 0; q < NM; ++q) acc[q] = fma(X[q][(size_t)b * n + a], xb, acc[q]);
     }
-    hk = warp_sum(hk);
-    hg = warp_sum(hg);
-    mc = warp_sum(mc);
-    if (lane == 0) {
-      s.Hc[a] = hk;
-      s.Gc[a] = hg;
-      s.Mc[a] = mc;
+#pragma unroll
+    for (int q = 0; q < NM; ++q) red[((size_t)q * parts + part) * n + a] = acc[q];
+  }
+  __syncthreads();
+  for (int r = t; r < n; r += kThreads) {
+#pragma unroll
+    for (int q = 0; q < NM; ++q) {
+      double v = 0.0;
+      for (int pp = 0; pp < parts; ++pp) v += red[((size_t)q * parts + pp) * n + r];
+      y[q][r] = v;
     }
   }
   __syncthreads();
+}
+
+// rows of (K0 c, G c, M c)
+__device__ void apply_all(Smem& s) {
+  const double* X[3] = {s.K0, s.G, s.MM};
+  double* Y[3] = {s.Hc, s.Gc, s.Mc};
+  symv<3>(X, s.c, Y, s.n, s.sv);
 }
 
 __device__ void build_G(const DenseProblem& p, Smem& s) {
   const int nv = p.nvert, L = s.L, nh = s.nh, n = s.n;
   const double cu = p.aug ? s.c[nh] : 0.0;
   const int npair = nv * (nv + 1) / 2;
-  const int items = npair + (p.aug ? nv : 0);
-  // local contributions: one work item = (simplex, entry)
-  for (int w = threadIdx.x; w < p.ntri * items; w += kThreads) {
-    const int t = w / items, e = w - t * items;
+  // local contributions of each simplex: the pair entries (a <= b) ...
+  for (int w = threadIdx.x; w < p.ntri * npair; w += kThreads) {
+    const int t = w / npair;
+    int a = 0, b = w - t * npair;  // the e-th pair (a <= b)
+    while (b >= nv - a) {
+      b -= nv - a;
+      ++a;
+    }
+    b += a;
     double wv[kMaxVert];
     for (int v = 0; v < nv; ++v) {
       const int id = s.tri[t * nv + v];
       wv[v] = id >= 0 ? s.c[id] : 0.0;
     }
-    const double* t3 = p.aug ? s.t3 + (size_t)t * p.nt3 : nullptr;
+    double q = 0.0;
+    const double* q4 = s.q4 + (size_t)(a * nv + b) * nv * nv;
+    for (int c = 0; c < nv; ++c) {
+      double qc = 0.0;
+      for (int d = 0; d < nv; ++d) qc = fma(wv[d], q4[c * nv + d], qc);
+      q = fma(wv[c], qc, q);
+    }
+    double v = p.tri_vol * q;
+    if (p.aug) {
+      const double* t3 = s.t3 + (size_t)t * p.nt3;
+      double x3 = 0.0;
+      for (int c = 0; c < nv; ++c) x3 = fma(wv[c], t3[s.sym3[(a * nv + b) * nv + c]], x3);
+      v = fma(2.0 * cu, x3, v);
+    }
     double* lt = s.loc + (size_t)t * L * L;
-    if (e < npair) {
-      int a = 0, b = e;  // e-th pair (a <= b)
-      while (b >= nv - a) {
-        b -= nv - a;
-        ++a;
+    lt[a * L + b] = v;
+    lt[b * L + a] = v;
+  }
+  // ... and the coupling of each vertex with u~ (augmented space)
+  if (p.aug) {
+    for (int w = threadIdx.x; w < p.ntri * nv; w += kThreads) {
+      const int t = w / nv, a = w - t * nv;
+      double wv[kMaxVert];
+      for (int v = 0; v < nv; ++v) {
+        const int id = s.tri[t * nv + v];
+        wv[v] = id >= 0 ? s.c[id] : 0.0;
       }
-      b += a;
-      double q = 0.0;
-      const double* q4 = s.q4 + (size_t)(a * nv + b) * nv * nv;
-      for (int c = 0; c < nv; ++c) {
-        double qc = 0.0;
-        for (int d = 0; d < nv; ++d) qc = fma(wv[d], q4[c * nv + d], qc);
-        q = fma(wv[c], qc, q);
-      }
-      double v = p.tri_vol * q;
-      if (p.aug) {
-        double x3 = 0.0;
-        for (int c = 0; c < nv; ++c) x3 = fma(wv[c], t3[s.sym3[(a * nv + b) * nv + c]], x3);
-        v = fma(2.0 * cu, x3, v);
-      }
-      lt[a * L + b] = v;
-      lt[b * L + a] = v;
-    } else {
-      const int a = e - npair;
+      const double* t3 = s.t3 + (size_t)t * p.nt3;
       double x3 = 0.0;
       for (int c = 0; c < nv; ++c) {
         double xc = 0.0;
         for (int d = 0; d < nv; ++d) xc = fma(wv[d], t3[s.sym3[(a * nv + c) * nv + d]], xc);
         x3 = fma(wv[c], xc, x3);
       }
-      lt[a * L + nv] = x3;
-    }
-  }
-  if (p.aug) {  // Hc <- B1 c_H (scratch; recomputed by apply_all afterwards)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int a = warp; a < nh; a += kWarps) {
-      const double* row = s.B1 + (size_t)a * nh;
-      double acc = 0.0;
-      for (int b = lane; b < nh; b += 32) acc = fma(row[b], s.c[b], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) s.Hc[a] = acc;
+      s.loc[(size_t)t * L * L + a * L + nv] = x3;
     }
   }
   __syncthreads();
-  // coarse rows: a warp per row; lanes fill the global part, lane 0 adds the simplices
+  if (p.aug) {  // Hc <- B1 c_H (scratch; recomputed by apply_all afterwards)
+    const double* X[1] = {s.B1};
+    double* Y[1] = {s.Hc};
+    symv<1>(X, s.c, Y, nh, s.sv);
+  }
+  // coarse rows: lanes fill the B1 part of a row, then each row's thread adds its simplices
+  const double cu2 = cu * cu;
   {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double cu2 = cu * cu;
     for (int a = warp; a < nh; a += kWarps) {
       double* row = s.G + (size_t)a * n;
       const double* brow = p.aug ? s.B1 + (size_t)a * nh : nullptr;
       for (int b = lane; b < nh; b += 32) row[b] = p.aug ? cu2 * brow[b] : 0.0;
-      __syncwarp();
-      if (lane == 0) {
-        double au = 0.0;
-        for (int e = 0; e < p.maxadj; ++e) {
-          const int code = s.adj[a * p.maxadj + e];
-          if (code < 0) break;
-          const int t = code >> 3, la = code & 7;
-          const double* lt = s.loc + (size_t)t * L * L;
-          for (int lb = 0; lb < nv; ++lb) {
-            const int vb = s.tri[t * nv + lb];
-            if (vb >= 0) row[vb] += lt[la * L + lb];
-          }
-          if (p.aug) au += lt[la * L + nv];
-        }
-        if (p.aug) row[nh] = fma(cu2, s.t1[a], fma(2.0 * cu, s.Hc[a], au));
-      }
-      __syncwarp();
     }
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < nh; a += kThreads) {
+    double* row = s.G + (size_t)a * n;
+    double au = 0.0;
+    for (int e = 0; e < p.maxadj; ++e) {
+      const int code = s.adj[a * p.maxadj + e];
+      if (code < 0) break;
+      const int t = code >> 3, la = code & 7;
+      const double* lt = s.loc + (size_t)t * L * L;
+      for (int lb = 0; lb < nv; ++lb) {
+        const int vb = s.tri[t * nv + lb];
+        if (vb >= 0) row[vb] += lt[la * L + lb];
+      }
+      if (p.aug) au += lt[la * L + nv];
+    }
+    if (p.aug) row[nh] = fma(cu2, s.t1[a], fma(2.0 * cu, s.Hc[a], au));
   }
   if (p.aug) {
     double part = 0.0;
@@ -204,20 +221,30 @@ __device__ void build_G(const DenseProblem& p, Smem& s) {
   __syncthreads();
 }
 
-// In-place symmetric elimination A = L D L^T (no pivoting; the full trailing block is kept,
-// so it stays symmetric and rows are read contiguously).  One barrier per step.  Returns
-// false at a non-positive pivot (every thread sees the same pivot, so all return together).
-__device__ bool ldlt(double* A, int n) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// In-place symmetric elimination A = L D L^T (no pivoting) on the lower triangle: after it,
+// A_kk = D_k and A_ik = L_ik D_k (i > k); dinv[k] = 1 / D_k.  At step k every thread updates
+// its elements (i >= j > k) of the trailing triangle, and the thread that updates the next
+// pivot also forms its reciprocal, so each step needs one barrier.  Returns false at a
+// non-positive pivot (every thread reads the same pivot, so all return together).
+__device__ bool ldlt(double* A, int n, double* dinv) {
+  if (threadIdx.x == 0) dinv[0] = A[0] > 0.0 ? recip(A[0]) : 0.0;
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
     const double d = A[k * n + k];
     if (!(d > 0.0)) return false;
-    const double inv = recip(d);
-    const double* rk = A + (size_t)k * n;
-    for (int i = k + 1 + warp; i < n; i += kWarps) {
-      const double l = A[i * n + k] * inv;
-      double* ri = A + (size_t)i * n;
-      for (int j = k + 1 + lane; j < n; j += 32) ri[j] = fma(-l, rk[j], ri[j]);
+    const double inv = dinv[k];
+    const int m = n - k - 1;
+    const int tri = m * (m + 1) / 2;
+    for (int e = threadIdx.x; e < tri; e += kThreads) {
+      // e -> (r, c), c <= r, rows of the trailing lower triangle in order
+      int r = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      while ((r + 1) * (r + 2) / 2 <= e) ++r;
+      while (r * (r + 1) / 2 > e) --r;
+      const int c = e - r * (r + 1) / 2;
+      const int i = k + 1 + r, j = k + 1 + c;
+      const double v = fma(-(A[i * n + k] * inv), A[j * n + k], A[i * n + j]);
+      A[i * n + j] = v;
+      if (e == 0) dinv[k + 1] = v > 0.0 ? recip(v) : 0.0;  // (k+1, k+1): the next pivot
     }
     __syncthreads();
   }
@@ -226,7 +253,7 @@ __device__ bool ldlt(double* A, int n) {
 
 // Solve (L D L^T) x = b for x held in `x` (b on entry), by one warp, column by column: once
 // an entry is final, the lanes update the remaining ones (only warp-level synchronisation).
-// The factor is stored as A_ik = L_ik D_k (symmetric); dinv holds 1 / D.
+// Reads the lower triangle written by ldlt.
 __device__ void ldlt_solve_warp(const double* A, const double* dinv, int n, double* x) {
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < n; ++k) {  // forward: w_k = z_k / D_k, z_i -= A_ik w_k (i > k)
@@ -236,28 +263,20 @@ __device__ void ldlt_solve_warp(const double* A, const double* dinv, int n, doub
     for (int i = k + 1 + lane; i < n; i += 32) x[i] = fma(-A[i * n + k], wk, x[i]);
     __syncwarp();
   }
-  for (int k = n - 1; k >= 0; --k) {  // backward: x_i -= (A_ik / D_i) x_k (i < k)
+  for (int k = n - 1; k >= 0; --k) {  // backward: x_i -= (A_ki / D_i) x_k (i < k)
     const double xk = x[k];
-    for (int i = lane; i < k; i += 32) x[i] = fma(-A[i * n + k] * dinv[i], xk, x[i]);
+    for (int i = lane; i < k; i += 32) x[i] = fma(-A[k * n + i] * dinv[i], xk, x[i]);
     __syncwarp();
   }
 }
 
-__device__ void invert_pivots(const double* A, int n, double* dinv) {
-  for (int k = threadIdx.x; k < n; k += kThreads) dinv[k] = recip(A[k * n + k]);
-  __syncthreads();
-}
-
 __device__ void normalise_and_sign(const DenseProblem& p, Smem& s) {
-  const int n = s.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int a = warp; a < n; a += kWarps) {
-    const double* mr = s.MM + (size_t)a * n;
-    double mc = 0.0;
-    for (int b = lane; b < n; b += 32) mc = fma(mr[b], s.c[b], mc);
-    mc = warp_sum(mc);
-    if (lane == 0) s.Mc[a] = mc;
+  const int n = s.n;
+  {
+    const double* X[1] = {s.MM};
+    double* Y[1] = {s.Mc};
+    symv<1>(X, s.c, Y, n, s.sv);
   }
-  __syncthreads();
   const double cmc = dotv(s.c, s.Mc, n, s.red);
   double sg;
   if (p.aug) {
@@ -318,6 +337,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   s.y2 = q; q += n;
   s.dinv = q; q += n;
   s.red = q; q += kThreads;
+  s.sv = q; q += 3 * kThreads;
   s.t1 = q; q += nh;
   s.t3 = q; q += p.aug ? (size_t)p.ntri * p.nt3 : 0;
   s.tri = reinterpret_cast<int*>(q); q += ((size_t)p.ntri * nv + 1) / 2;
@@ -412,9 +432,8 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
         s.y2[a] = s.Mc[a];
       }
       __syncthreads();
-      newton = ldlt(s.A, n);
+      newton = ldlt(s.A, n, s.dinv);
       if (newton) {
-        invert_pivots(s.A, n, s.dinv);
         if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
         else if ((threadIdx.x >> 5) == 1) ldlt_solve_warp(s.A, s.dinv, n, s.y2);
         __syncthreads();
@@ -430,8 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
       for (int e = threadIdx.x; e < n * n; e += kThreads) s.A[e] = fma(zeta, s.G[e], s.K0[e]);
       for (int a = threadIdx.x; a < n; a += kThreads) s.y1[a] = s.Mc[a];
       __syncthreads();
-      if (!ldlt(s.A, n)) break;
-      invert_pivots(s.A, n, s.dinv);
+      if (!ldlt(s.A, n, s.dinv)) break;
       if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
       __syncthreads();
       for (int a = threadIdx.x; a < n; a += kThreads) s.c[a] = s.y1[a];
@@ -455,20 +473,21 @@ __global__ void __launch_bounds__(kThreads) k_spd_inverse(const double* L, doubl
   Linv += blockIdx.x * (size_t)n * n;
   double* A = sm;
   double* Y = A + n * n;
+  double* dinv = Y + n * n;
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
     A[e] = L[e];
     const int i = e / n, j = e - (e / n) * n;
     Y[e] = i == j ? 1.0 : 0.0;
   }
   __syncthreads();
-  if (!ldlt(A, n)) {
+  if (!ldlt(A, n, dinv)) {
     for (int e = threadIdx.x; e < n * n; e += kThreads) Linv[e] = nan("");
     return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // forward: rows of W with (C D) W = I: W_k = (Y_k - sum_{i<k} A_ki W_i) / D_k
   for (int k = 0; k < n; ++k) {
-    const double inv = recip(A[k * n + k]);
+    const double inv = dinv[k];
     for (int j = threadIdx.x; j < n; j += kThreads) Y[k * n + j] *= inv;
     __syncthreads();
     for (int i = k + 1 + warp; i < n; i += kWarps) {
@@ -477,10 +496,10 @@ __global__ void __launch_bounds__(kThreads) k_spd_inverse(const double* L, doubl
     }
     __syncthreads();
   }
-  // backward: C^T X = W, X_k = W_k - sum_{i>k} (A_ki / D_k) X_i
+  // backward: C^T X = W, X_i = W_i - sum_{k>i} (A_ki / D_i) X_k
   for (int k = n - 1; k >= 0; --k) {
     for (int i = warp; i < k; i += kWarps) {
-      const double l = A[i * n + k] * recip(A[i * n + i]);
+      const double l = A[k * n + i] * dinv[i];
       for (int j = lane; j < n; j += 32) Y[i * n + j] = fma(-l, Y[k * n + j], Y[i * n + j]);
     }
     __syncthreads();
@@ -523,7 +542,7 @@ size_t dense_smem_bytes(int n, int ntri, int nvert, int aug) {
   const size_t nt3 = nvert == 3 ? 10 : 20;
   const size_t maxadj = nvert == 3 ? 6 : 24;
   return sizeof(double) * ((size_t)4 * n * n + (size_t)ntri * L * L +
-                           (size_t)nvert * nvert * nvert * nvert + 8 * (size_t)n + kThreads +
+                           (size_t)nvert * nvert * nvert * nvert + 8 * (size_t)n + 4 * kThreads +
                            nh + (aug ? (size_t)ntri * nt3 : 0) + ((size_t)ntri * nvert + 1) / 2 +
                            ((size_t)nh * maxadj + 1) / 2 + (aug ? (size_t)nh * nh : 0));
 }
@@ -545,7 +564,7 @@ cudaError_t dense_prepare(size_t need) {
 }
 
 void dense_spd_inverse(const double* L, double* Linv, int n, int nb, cudaStream_t s) {
-  k_spd_inverse<<<nb, kThreads, sizeof(double) * (2 * (size_t)n * n), s>>>(L, Linv, n);
+  k_spd_inverse<<<nb, kThreads, sizeof(double) * (2 * (size_t)n * n + n), s>>>(L, Linv, n);
 }
 
 void coarse_matvec(const Grid& g, const double* Linv, const double* x, double* y,
