@@ -19,8 +19,10 @@ namespace fmg {
 struct Level {
   Grid g;
   int cap = 0;  // instances allocated (cnt[k])
-  Coef2D c{};
+  Coef2D c{};   // operator of the auxiliary problem (A + W, or A in the paper-literal form)
   Coef3D c3{};
+  Coef2D cw{};  // A + W (the same arrays as c unless the form is paper-literal)
+  Coef3D cw3{};
   double *x = nullptr, *xt = nullptr, *f = nullptr, *r = nullptr, *u = nullptr,
          *y = nullptr, *z = nullptr;
   Density2D b{};          // density stencil of u~ (augmented pass), 2D
@@ -76,7 +78,9 @@ struct fmg_eig_handle {
   int nh = 0, ntri = 0, nvert = 3, maxadj = 6;
   double tri_vol = 0.0;
   // per-instance arrays (sorted order): L1, M1, L1inv nh*nh; c, cstart nh + 1; scalars 1
-  double *L1 = nullptr, *M1 = nullptr, *L1inv = nullptr, *q4 = nullptr;
+  // L1 = A + W on level 1 (the small nonlinear solves), L1A the operator whose inverse is the
+  // coarsest V-cycle solve (the same array unless the form is paper-literal)
+  double *L1 = nullptr, *L1A = nullptr, *M1 = nullptr, *L1inv = nullptr, *q4 = nullptr;
   int *tri = nullptr, *adj = nullptr;
   double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr,
          *partials = nullptr, *partials2 = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,
@@ -84,8 +88,14 @@ struct fmg_eig_handle {
          *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr, *uout = nullptr;
   int *iters = nullptr, *status = nullptr;  // [level][instance]
   int* inv_order = nullptr;                 // sorted index of the caller's instance i
-  fmg::PotentialParams* dparams = nullptr;  // device copy read by the kernels (nb)
-  fmg::PotentialParams* hparams = nullptr;  // pinned host staging, uploaded at every solve (nb)
+  // device copy read by the kernels (nparams), and its pinned host staging uploaded at every
+  // solve; the paper-literal form keeps nb more entries with the form set to W_LEFT, from
+  // which the A + W coefficients are built (dparams_full)
+  int nparams = 1;
+  fmg::PotentialParams* dparams = nullptr;
+  fmg::PotentialParams* dparams_full = nullptr;
+  fmg::PotentialParams* hparams = nullptr;
+  bool literal() const { return prob.operator_form == FMG_PAPER_LITERAL; }
   // profiling: event pairs around the first finest-level launch of each profiled step
   cudaEvent_t prof[fmg::kProfCount][2] = {};
   bool prof_armed[fmg::kProfCount] = {};
@@ -136,6 +146,8 @@ size_t estimate_bytes(const fmg_eig_problem* probs, int count);
 // is enqueued, with the sorted instances [first, first + count) whose last level is k.
 using StageHook = std::function<void(int k, int first, int count)>;
 void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s, const StageHook* after_stage = nullptr);
+// upload the host staging of the parameters (every solve starts with it)
+cudaError_t upload_params(fmg_eig_handle* h, cudaStream_t s);
 // every instance's u from its finest level into h->uout (interior layout)
 void enqueue_outputs(fmg_eig_handle* h, cudaStream_t s);
 

@@ -31,7 +31,10 @@ Level view(const Level& l, int first, int count) {
     if (p) p += o;
   };
   adv(v.c.cC); adv(v.c.cE); adv(v.c.cN); adv(v.c.cNE); adv(v.c.dinv);
+  adv(v.cw.cC); adv(v.cw.cE); adv(v.cw.cN); adv(v.cw.cNE); adv(v.cw.dinv);
+  adv(v.cw3.dinv);
   for (int q = 0; q < 8; ++q) {
+    adv(v.cw3.a[q]);
     adv(v.c3.a[q]);
     adv(v.b3.a[q]);
     adv(v.cf3.a[q]);
@@ -41,7 +44,7 @@ Level view(const Level& l, int first, int count) {
   adv(v.b.C); adv(v.b.E); adv(v.b.N); adv(v.b.NE);
   adv(v.cf.cC); adv(v.cf.cE); adv(v.cf.cN); adv(v.cf.cNE); adv(v.cf.dinv);
   adv(v.x32); adv(v.xt32); adv(v.f32); adv(v.r32);
-  v.c.tab = v.c3.tab = nullptr;  // setup scratch is not sliced
+  v.c.tab = v.c3.tab = v.cw.tab = v.cw3.tab = nullptr;  // setup scratch is not sliced
   v.g.nb = count;
   return v;
 }
@@ -51,13 +54,23 @@ Level view(const Level& l, int first, int count) {
 namespace {
 
 // ---- dimension dispatch of the level kernels -----------------------------------------------
-void lv_coef(Level& l, const PotentialParams* p, cudaStream_t s) {
-  if (l.g.dim == 2) coef2d_setup(l.g, p, l.c, s);
-  else coef3d_setup(l.g, p, l.c3, s);
+void lv_coef(Level& l, const PotentialParams* p, cudaStream_t s, bool full = false) {
+  if (l.g.dim == 2) coef2d_setup(l.g, p, full ? l.cw : l.c, s);
+  else coef3d_setup(l.g, p, full ? l.cw3 : l.c3, s);
 }
 void lv_apply(Level& l, const double* x, double* y, cudaStream_t s) {
   if (l.g.dim == 2) apply2d(l.g, l.c, x, y, s);
   else apply3d(l.g, l.c3, x, y, s);
+}
+// y = (A + W) x, whatever the form of the auxiliary operator
+void lv_apply_full(Level& l, const double* x, double* y, cudaStream_t s) {
+  if (l.g.dim == 2) apply2d(l.g, l.cw, x, y, s);
+  else apply3d(l.g, l.cw3, x, y, s);
+}
+// f -= W u (paper-literal form: W moves to the right-hand side)
+void lv_sub_wmass(Level& l, const double* u, double* f, cudaStream_t s) {
+  if (l.g.dim == 2) sub_wmass2d(l.g, l.cw, l.c, u, f, s);
+  else sub_wmass3d(l.g, l.cw3, l.c3, u, f, s);
 }
 void lv_mass(Level& l, const double* x, double* y, cudaStream_t s) {
   if (l.g.dim == 2) mass2d(l.g, x, y, s);
@@ -106,9 +119,9 @@ void lv_t3(Level& l, int n1, const double* u, double* partials, double* t3, cuda
   if (l.g.dim == 2) t3_moments2d(l.g, n1, u, l.pw, l.t3map, partials, t3, s);
   else t3_moments3d(l.g, n1, u, l.t3map, partials, t3, s);
 }
-void lv_dense_level1(Level& l1, double* L, double* M, cudaStream_t s) {
-  if (l1.g.dim == 2) dense_level1_2d(l1.g, l1.c, L, M, s);
-  else dense_level1_3d(l1.g, l1.c3, L, M, s);
+void lv_dense_level1(Level& l1, double* L, double* M, cudaStream_t s, bool full) {
+  if (l1.g.dim == 2) dense_level1_2d(l1.g, full ? l1.cw : l1.c, L, M, s);
+  else dense_level1_3d(l1.g, full ? l1.cw3 : l1.c3, L, M, s);
 }
 void lv_start(Level& l1, double* c, int cstride, cudaStream_t s) {
   if (l1.g.dim == 2) start_vector(l1.g, c, cstride, s);
@@ -182,7 +195,7 @@ int validate(const fmg_eig_problem* p) {
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
   if (p->smoother != FMG_SMOOTH_JACOBI) return FMG_ENOTSUP;
   if ((p->precision != FMG_FP64 && p->precision != FMG_MIXED_FP32) ||
-      p->operator_form != FMG_W_LEFT)
+      (p->operator_form != FMG_W_LEFT && p->operator_form != FMG_PAPER_LITERAL))
     return FMG_ENOTSUP;
   return FMG_OK;
 }
@@ -210,6 +223,26 @@ PotentialParams potential(const fmg_eig_problem& p) {
   return q;
 }
 
+// host staging of every instance's parameters (and their W_LEFT copies, paper-literal form)
+void fill_params(fmg_eig_handle* h) {
+  for (int b = 0; b < h->nb; ++b) {
+    h->hparams[b] = potential(h->probs[b]);
+    if (h->literal()) {
+      h->hparams[h->nb + b] = h->hparams[b];
+      h->hparams[h->nb + b].operator_form = FMG_W_LEFT;
+    }
+  }
+}
+
+}  // namespace fmg
+
+cudaError_t fmg::upload_params(fmg_eig_handle* h, cudaStream_t s) {
+  return cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * h->nparams,
+                         cudaMemcpyHostToDevice, s);
+}
+
+namespace fmg {
+
 void build_levels(fmg_eig_handle* h) {
   const fmg_eig_problem& p = h->prob;
   const int dim = p.dim;
@@ -236,11 +269,26 @@ void build_levels(fmg_eig_handle* h) {
       l.b.E = h->alloc<double>(s);
       l.b.N = h->alloc<double>(s);
       l.b.NE = h->alloc<double>(s);
+      l.cw = l.c;
+      if (h->literal()) {
+        l.cw.cC = h->alloc<double>(s);
+        l.cw.cE = h->alloc<double>(s);
+        l.cw.cN = h->alloc<double>(s);
+        l.cw.cNE = h->alloc<double>(s);
+        l.cw.dinv = h->alloc<double>(s);
+        l.cw.tab = h->alloc<double>(8 * (size_t)(l.g.n + 1) * l.cap);
+      }
     } else {
       for (int q = 0; q < 8; ++q) l.c3.a[q] = h->alloc<double>(s);
       l.c3.dinv = h->alloc<double>(s);
       l.c3.tab = h->alloc<double>(15 * (size_t)(l.g.n + 1) * l.cap);
       for (int q = 0; q < 8; ++q) l.b3.a[q] = h->alloc<double>(s);
+      l.cw3 = l.c3;
+      if (h->literal()) {
+        for (int q = 0; q < 8; ++q) l.cw3.a[q] = h->alloc<double>(s);
+        l.cw3.dinv = h->alloc<double>(s);
+        l.cw3.tab = h->alloc<double>(15 * (size_t)(l.g.n + 1) * l.cap);
+      }
     }
     if (p.precision == FMG_MIXED_FP32) {
       if (dim == 2) {
@@ -374,6 +422,7 @@ void build_coarse(fmg_eig_handle* h) {
                   h->stream);
   const size_t nn = (size_t)h->nh * h->nh;
   h->L1 = h->alloc<double>(nn * nb);
+  h->L1A = h->literal() ? h->alloc<double>(nn * nb) : h->L1;
   h->M1 = h->alloc<double>(nn * nb);
   h->L1inv = h->alloc<double>(nn * nb);
   h->lam = h->alloc<double>(nb);
@@ -464,6 +513,7 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s, bool overlap = false) {
     s = sk;
     prof_begin(h, kProfCoef, k, s);
     lv_coef(l, h->dparams, s);
+    if (h->literal()) lv_coef(l, h->dparams_full, s, true);
     prof_end(h, kProfCoef, k, s);
     if (h->prob.precision == FMG_MIXED_FP32) {
       const size_t n = l.g.stride * l.g.nb;
@@ -484,8 +534,9 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s, bool overlap = false) {
     }
     s = s_saved;
   }
-  lv_dense_level1(h->L(1), h->L1, h->M1, s);
-  dense_spd_inverse(h->L1, h->L1inv, h->nh, h->L(1).g.nb, s);
+  lv_dense_level1(h->L(1), h->L1, h->M1, s, true);
+  if (h->literal()) lv_dense_level1(h->L(1), h->L1A, h->M1, s, false);
+  dense_spd_inverse(h->L1A, h->L1inv, h->nh, h->L(1).g.nb, s);
 }
 
 DenseProblem dense_base(fmg_eig_handle* h) {
@@ -629,8 +680,8 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
     lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, b2);
     prof_end(h, kProfT3, k, b2);
   }
-  // main branch: L u~, M u~, their dots and restriction chains
-  lv_apply(l, ut, l.y, s);
+  // main branch: (A + W) u~, M u~, their dots and restriction chains
+  lv_apply_full(l, ut, l.y, s);
   lv_mass(l, ut, l.z, s);
   dot(ut, l.y, st, h->partials, h->auu, s, nb, st);
   dot(ut, l.z, st, h->partials, h->buu, s, nb, st);
@@ -667,6 +718,7 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   if (h->prob.precision == FMG_MIXED_FP32 && (h->prob.flags & FMG_FLAG_FP32_RHS))
     lv_rhs_f32(l, h->lam, h->dparams, l.u, l.f, s);
   else lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
+  if (h->literal()) lv_sub_wmass(l, l.u, l.f, s);
   prof_end(h, kProfRhs, k, s);
   cudaMemcpyAsync(l.x, l.u, l.g.stride * nb * sizeof(double), cudaMemcpyDeviceToDevice, s);
   enqueue_multigrid(h, k, s);
@@ -726,7 +778,7 @@ void enqueue_checks(fmg_eig_handle* h, cudaStream_t s) {
     if (count <= 0) continue;
     Level v = view(h->L(k), first, count);
     const size_t st = v.g.stride;
-    lv_apply(v, v.u, v.y, s);
+    lv_apply_full(v, v.u, v.y, s);
     lv_mass(v, v.u, v.z, s);
     lv_nload(v, v.u, v.r, s);
     dot(v.u, v.y, st, h->partials, sa + first, s, count, st);
@@ -857,7 +909,7 @@ size_t estimate_bytes(const fmg_eig_problem* probs, int count) {
   if (init_instances(&h, probs, count) != FMG_OK) return 0;
   build_levels(&h);
   build_coarse(&h);
-  h.alloc<PotentialParams>(count);
+  h.alloc<PotentialParams>(h.literal() ? 2 * count : count);
   return h.bytes;
 }
 
@@ -890,7 +942,9 @@ int create_handle(const fmg_eig_problem* probs, int count, const CreateOptions& 
   try {
     build_levels(h);
     build_coarse(h);
-    h->dparams = h->alloc<PotentialParams>(count);
+    h->nparams = h->literal() ? 2 * count : count;
+    h->dparams = h->alloc<PotentialParams>(h->nparams);
+    h->dparams_full = h->literal() ? h->dparams + count : h->dparams;
   } catch (const std::bad_alloc&) {
     delete h;
     return FMG_ENOMEM;
@@ -898,18 +952,18 @@ int create_handle(const fmg_eig_problem* probs, int count, const CreateOptions& 
   // pinned staging for the per-solve upload of a reusable handle; a one-shot handle (the
   // server's) uses pageable memory, whose release never waits for the device
   if (opt.async_alloc) {
-    h->hparams = new (std::nothrow) PotentialParams[count];
+    h->hparams = new (std::nothrow) PotentialParams[h->nparams];
     if (!h->hparams) {
       delete h;
       return FMG_ENOMEM;
     }
-  } else if (cudaMallocHost(&h->hparams, sizeof(PotentialParams) * count) != cudaSuccess) {
+  } else if (cudaMallocHost(&h->hparams, sizeof(PotentialParams) * h->nparams) != cudaSuccess) {
     cudaGetLastError();
     h->hparams = nullptr;
     delete h;
     return FMG_ENOMEM;
   }
-  for (int b = 0; b < count; ++b) h->hparams[b] = potential(h->probs[b]);
+  fill_params(h);
   for (int i = 0; i < kProfCount; ++i)
     for (int j = 0; j < 2; ++j)
       if (cudaEventCreate(&h->prof[i][j]) != cudaSuccess) {
@@ -917,8 +971,7 @@ int create_handle(const fmg_eig_problem* probs, int count, const CreateOptions& 
         delete h;
         return FMG_ECUDA;
       }
-  cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * count,
-                  cudaMemcpyHostToDevice, h->stream);
+  upload_params(h, h->stream);
   if (h->dense_smem > kDenseSmemLimit) {  // the small dense solve keeps everything in shared memory
     delete h;
     return FMG_ENOTSUP;
@@ -995,8 +1048,7 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
   for (fmg_eig_handle* h : hs) {
     cudaStream_t s = h->stream;
     CK(cudaEventRecord(h->ev0, s));
-    CK(cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * h->nb,
-                       cudaMemcpyHostToDevice, s));
+    CK(upload_params(h, s));
     CK(cudaGraphLaunch(h->exec, s));
     CK(cudaEventRecord(h->ev1, s));
     if (u_hosts) enqueue_outputs(h, s);
@@ -1114,9 +1166,8 @@ int fmg_eig_set_params(fmg_eig_handle* h, const fmg_eig_problem* prob) {
   h->prob.zeta = prob->zeta;
   h->prob.omega = prob->omega;
   h->probs[0] = h->prob;
-  *h->hparams = potential(h->prob);
-  if (cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams), cudaMemcpyHostToDevice,
-                      h->stream) != cudaSuccess ||
+  fill_params(h);
+  if (upload_params(h, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return FMG_ECUDA;
   enqueue_setup(h, h->stream);  // keep the component entry points' operators current
@@ -1145,7 +1196,7 @@ int fmg_eig_solve_dev(fmg_eig_handle* h, double* lambda_dev, double* u_dev, size
   const Level& fine = h->L(h->levels());
   if (u_dev && u_len != fine.g.interior()) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
-  CK(cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams), cudaMemcpyHostToDevice, s));
+  CK(upload_params(h, s));
   CK(cudaGraphLaunch(h->exec, s));
   CK(cudaMemcpyAsync(lambda_dev, h->lam, sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (u_dev) unpack_interior(fine.g, fine.u, u_dev, s);
@@ -1174,8 +1225,7 @@ int fmg_eig_batch_solve(fmg_eig_handle* h, double* lambdas, double* const* u_hos
 int fmg_eig_batch_solve_dev(fmg_eig_handle* h, double* lambdas_dev, void* stream) {
   if (!h || !lambdas_dev) return FMG_EINVAL;
   cudaStream_t s = pick(h, stream);
-  CK(cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * h->nb,
-                     cudaMemcpyHostToDevice, s));
+  CK(upload_params(h, s));
   CK(cudaGraphLaunch(h->exec, s));
   gather_by_index(h->lam, h->inv_order, lambdas_dev, h->nb, s);
   CK(cudaGetLastError());
@@ -1317,6 +1367,7 @@ int fmg_eig_aux_rhs(fmg_eig_handle* h, int32_t level, double lambda, const doubl
   CK(cudaMemcpy(lam_tmp, &lambda, sizeof(double), cudaMemcpyHostToDevice));
   pack_interior(l.g, u_dev, l.r, s);
   lv_rhs(l, lam_tmp, h->dparams, l.r, l.y, s);
+  if (h->literal()) lv_sub_wmass(l, l.r, l.y, s);
   unpack_interior(l.g, l.y, f_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;

@@ -102,6 +102,14 @@ __global__ void k_apply2d(int n, int pitch, size_t st, Coef2D c, const double* _
   y[k] = lop(c, x, k, pitch);
 }
 
+// f -= (Lw - La) u = W u (the potential's mass matrix) for the paper-literal form, whose
+// auxiliary operator La = A leaves W u on the right-hand side; Lw = A + W
+__global__ void k_sub_wmass2d(int n, int pitch, size_t st, Coef2D cw, Coef2D ca,
+                              const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_2D
+  f[k] -= lop(cw, u, k, pitch) - lop(ca, u, k, pitch);
+}
+
 __global__ void k_mass2d(int n, int pitch, size_t st, double h2_12, const double* __restrict__ x,
                          double* __restrict__ y) {
   INTERIOR_2D
@@ -285,6 +293,12 @@ void coef2d_setup(const Grid& g, const PotentialParams* p, const Coef2D& c, cuda
 void apply2d(const Grid& g, const Coef2D& c, const double* x, double* y, cudaStream_t s) {
   k_apply2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride, c, x,
                                                                   y);
+}
+
+void sub_wmass2d(const Grid& g, const Coef2D& cw, const Coef2D& ca, const double* u, double* f,
+                 cudaStream_t s) {
+  k_sub_wmass2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride, cw,
+                                                                     ca, u, f);
 }
 
 void mass2d(const Grid& g, const double* x, double* y, cudaStream_t s) {

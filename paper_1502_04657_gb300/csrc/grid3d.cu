@@ -124,6 +124,13 @@ __global__ void k_apply3d(int n, int pitch, size_t st, Coef3D c, const double* _
   y[k] = lop3(c, x, k, pitch, plane);
 }
 
+// f -= (Lw - La) u = W u for the paper-literal form (La = A, Lw = A + W)
+__global__ void k_sub_wmass3d(int n, int pitch, size_t st, Coef3D cw, Coef3D ca,
+                              const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_3D
+  f[k] -= lop3(cw, u, k, pitch, plane) - lop3(ca, u, k, pitch, plane);
+}
+
 __global__ void k_jacobi3d(int n, int pitch, size_t st, Coef3D c, const double* __restrict__ f,
                            const double* __restrict__ x, double* __restrict__ xo) {
   INTERIOR_3D
@@ -515,6 +522,11 @@ void coef3d_setup(const Grid& g, const PotentialParams* p, const Coef3D& c, cuda
 
 void apply3d(const Grid& g, const Coef3D& c, const double* x, double* y, cudaStream_t s) {
   k_apply3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, x, y);
+}
+
+void sub_wmass3d(const Grid& g, const Coef3D& cw, const Coef3D& ca, const double* u, double* f,
+                 cudaStream_t s) {
+  k_sub_wmass3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, cw, ca, u, f);
 }
 
 void mass3d(const Grid& g, const double* x, double* y, cudaStream_t s) {

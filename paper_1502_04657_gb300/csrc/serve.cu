@@ -278,8 +278,7 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
                     cudaEventRecord(m.ev, h->stream) == cudaSuccess;
         c.marks.push_back(m);
       };
-      launch_ok = cudaMemcpyAsync(h->dparams, h->hparams, sizeof(PotentialParams) * h->nb,
-                                  cudaMemcpyHostToDevice, h->stream) == cudaSuccess;
+      launch_ok = upload_params(h, h->stream) == cudaSuccess;
       enqueue_fmg(h, h->stream, &hook);
       if (!launch_ok || cudaGetLastError() != cudaSuccess) {
         rc = FMG_ECUDA;
