@@ -44,7 +44,10 @@ extern "C" {
 #define FMG_ETIMEOUT (-5) /* a bounded device wait gave up */
 #define FMG_ENOTSUP (-6)  /* combination of options not built */
 
-#define FMG_SMOOTH_JACOBI 0
+#define FMG_SMOOTH_JACOBI 0    /* damped Jacobi, omega, nu_pre / nu_post sweeps            */
+/* Chebyshev semi-iteration of degree nu_pre / nu_post on [0.3, 2] for the spectrum of
+ * D^{-1} L (2 = Gershgorin's bound for these operators; omega is not used); FMG_FP64 only */
+#define FMG_SMOOTH_CHEBYSHEV 1
 #define FMG_FP64 0
 #define FMG_MIXED_FP32 1
 #define FMG_W_LEFT 0        /* (A + W) u^ = lambda M u - N(u)              */
@@ -69,7 +72,7 @@ typedef struct fmg_eig_problem {
   int32_t nu_post;      /* post-smoothing sweeps (>= 0)                                    */
   int32_t vcycles;      /* m of Algorithm 3.1 (>= 1)                                       */
   int32_t corrections;  /* p of Algorithm 3.2 (>= 1)                                       */
-  int32_t smoother;     /* FMG_SMOOTH_JACOBI                                               */
+  int32_t smoother;     /* FMG_SMOOTH_JACOBI | FMG_SMOOTH_CHEBYSHEV                        */
   int32_t precision;    /* FMG_FP64 | FMG_MIXED_FP32                                       */
   int32_t operator_form;/* FMG_W_LEFT | FMG_PAPER_LITERAL                                  */
   int32_t scf_max_iter; /* cap on nonlinear iterations per small solve (e.g. 100)          */
@@ -248,7 +251,8 @@ int fmg_eig_apply_mass(fmg_eig_handle* h, int32_t level, const double* x_dev, do
                        void* stream);
 
 /* One damped Jacobi sweep x_out = x_in + omega D^{-1} (f - L_k x_in) (the smoother of the
- * multigrid iteration of Algorithm 3.1 step 1).                                             */
+ * multigrid iteration of Algorithm 3.1 step 1); omega = 1 on a handle whose smoother is
+ * FMG_SMOOTH_CHEBYSHEV.                                                                     */
 int fmg_eig_jacobi(fmg_eig_handle* h, int32_t level, const double* f_dev,
                    const double* x_in_dev, double* x_out_dev, void* stream);
 

@@ -52,6 +52,17 @@ import scipy.sparse as sp
 
 W_LEFT = 0
 PAPER_LITERAL = 1
+SMOOTH_JACOBI = 0
+SMOOTH_CHEBYSHEV = 1
+# Chebyshev smoothing interval [CHEB_LOW, CHEB_HIGH] for the spectrum of D^{-1} L: the upper
+# end is Gershgorin's bound for these operators (the stiffness rows sum to zero and the
+# potential mass has the P1 mass pattern, so every row of D^{-1} L has |off-diagonal| sum at
+# most 1, and the spectrum does reach close to 2); the smoother damps the part above the
+# lower end and leaves the smooth part to the coarse grid.  0.3 gave the fastest V-cycle
+# among 0.1..0.7 on 2D and 3D model problems (0.21 / 0.24 per cycle with degree 2 + 2,
+# against 0.27 / 0.38 for 2 + 2 damped Jacobi).
+CHEB_LOW = 0.3
+CHEB_HIGH = 2.0
 
 
 # --------------------------------------------------------------------------------------
@@ -287,6 +298,7 @@ class Problem:
     vcycles: int = 2               # m of Algorithm 3.1
     corrections: int = 1           # p of Algorithm 3.2
     operator_form: int = W_LEFT
+    smoother: int = SMOOTH_JACOBI  # Chebyshev: degree nu_pre / nu_post on [CHEB_LOW, CHEB_HIGH]
     scf_tol: float = 1e-13
     scf_max_iter: int = 500
 
@@ -331,20 +343,52 @@ def jacobi(lev: Level, f: np.ndarray, x: np.ndarray, omega: float) -> np.ndarray
     return x + omega * (f - lev.L @ x) / lev.D
 
 
+def chebyshev_coefficients(degree: int, low: float = CHEB_LOW, high: float = CHEB_HIGH):
+    """(alpha_k, beta_k), k < degree, of the Chebyshev semi-iteration on [low, high]
+    (the three-term recurrence of Chebyshev acceleration, e.g. Saad, Iterative Methods for
+    Sparse Linear Systems, Sec. 12.3): with theta = (high + low)/2, delta = (high - low)/2,
+    sigma = theta/delta, rho_0 = 1/sigma, rho_k = 1/(2 sigma - rho_{k-1}),
+        d_0 = D^{-1} r_0 / theta,  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) D^{-1} r_k,
+        x_{k+1} = x_k + d_k."""
+    theta, delta = 0.5 * (high + low), 0.5 * (high - low)
+    sigma = theta / delta
+    out = [(0.0, 1.0 / theta)]
+    rho = 1.0 / sigma
+    for _ in range(1, degree):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        out.append((rho_new * rho, 2.0 * rho_new / delta))
+        rho = rho_new
+    return out
+
+
+def chebyshev(lev: Level, f: np.ndarray, x: np.ndarray, degree: int) -> np.ndarray:
+    """degree steps of the Chebyshev semi-iteration for L x = f preconditioned by D."""
+    d = np.zeros_like(x)
+    for alpha, beta in chebyshev_coefficients(degree):
+        d = alpha * d + beta * (f - lev.L @ x) / lev.D
+        x = x + d
+    return x
+
+
+def smooth(lev: Level, f: np.ndarray, x: np.ndarray, nu: int, prob: Problem) -> np.ndarray:
+    if prob.smoother == SMOOTH_CHEBYSHEV:
+        return chebyshev(lev, f, x, nu) if nu > 0 else x
+    for _ in range(nu):
+        x = jacobi(lev, f, x, prob.omega)
+    return x
+
+
 def vcycle(levels: list[Level], j: int, f: np.ndarray, x: np.ndarray, prob: Problem) -> np.ndarray:
     """One V-cycle on level j (1-based) for L_j x = f."""
     lev = levels[j - 1]
     if j == 1:
         return sla.cho_solve(sla.cho_factor(lev.L.toarray()), f)
-    for _ in range(prob.nu_pre):
-        x = jacobi(lev, f, x, prob.omega)
+    x = smooth(lev, f, x, prob.nu_pre, prob)
     r = f - lev.L @ x
     rc = lev.P.T @ r
     ec = vcycle(levels, j - 1, rc, np.zeros_like(rc), prob)
     x = x + lev.P @ ec
-    for _ in range(prob.nu_post):
-        x = jacobi(lev, f, x, prob.omega)
-    return x
+    return smooth(lev, f, x, prob.nu_post, prob)
 
 
 def multigrid(levels, j, f, x0, m, prob):

@@ -80,6 +80,11 @@ void lv_jacobi(Level& l, const double* f, const double* x, double* xo, bool zero
   if (l.g.dim == 2) jacobi2d(l.g, l.c, f, x, xo, zero, s);
   else jacobi3d(l.g, l.c3, f, x, xo, zero, s);
 }
+void lv_cheb(Level& l, const double* f, const double* x, double* d, double* xo, double alpha,
+             double beta, bool first, bool zero, cudaStream_t s) {
+  if (l.g.dim == 2) cheb2d(l.g, l.c, f, x, d, xo, alpha, beta, first, zero, s);
+  else cheb3d(l.g, l.c3, f, x, d, xo, alpha, beta, first, zero, s);
+}
 void lv_residual(Level& l, const double* f, const double* x, double* r, cudaStream_t s) {
   if (l.g.dim == 2) residual2d(l.g, l.c, f, x, r, s);
   else residual3d(l.g, l.c3, f, x, r, s);
@@ -193,7 +198,8 @@ int validate(const fmg_eig_problem* p) {
   if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision != FMG_MIXED_FP32) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
-  if (p->smoother != FMG_SMOOTH_JACOBI) return FMG_ENOTSUP;
+  if (p->smoother != FMG_SMOOTH_JACOBI && p->smoother != FMG_SMOOTH_CHEBYSHEV) return FMG_EINVAL;
+  if (p->smoother == FMG_SMOOTH_CHEBYSHEV && p->precision != FMG_FP64) return FMG_ENOTSUP;
   if ((p->precision != FMG_FP64 && p->precision != FMG_MIXED_FP32) ||
       (p->operator_form != FMG_W_LEFT && p->operator_form != FMG_PAPER_LITERAL))
     return FMG_ENOTSUP;
@@ -218,7 +224,7 @@ PotentialParams potential(const fmg_eig_problem& p) {
   q.wy = p.w_quad[1];
   q.wz = p.w_quad[2];
   q.zeta = p.zeta;
-  q.omega = p.omega;
+  q.omega = p.smoother == FMG_SMOOTH_CHEBYSHEV ? 1.0 : p.omega;  // dinv = omega / D
   q.operator_form = p.operator_form;
   return q;
 }
@@ -573,6 +579,56 @@ void enqueue_coarse(fmg_eig_handle* h, cudaStream_t s) {
   scatter_level1(l1.g, h->c, h->nh + 1, l1.u, s);
 }
 
+// Chebyshev semi-iteration of degree nu on the interval [kChebLow, kChebHigh] of the spectrum
+// of D^{-1} L: the upper end is Gershgorin's bound for these operators (stiffness rows sum
+// to zero, the potential mass has the P1 mass pattern, so |off-diagonal| row sums of
+// D^{-1} L are at most 1); the smoother damps the spectrum above the lower end.  Three-term
+// recurrence of Chebyshev acceleration: theta, delta the interval's centre and half-width,
+// sigma = theta / delta, rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1});
+// step 0: d = D^{-1} r / theta; step k: d = rho_k rho_{k-1} d + (2 rho_k / delta) D^{-1} r.
+constexpr double kChebLow = 0.3, kChebHigh = 2.0;
+
+void cheb_coefficients(int nu, std::vector<double>& alpha, std::vector<double>& beta) {
+  const double theta = 0.5 * (kChebHigh + kChebLow), delta = 0.5 * (kChebHigh - kChebLow);
+  const double sigma = theta / delta;
+  alpha.assign(nu, 0.0);
+  beta.assign(nu, 0.0);
+  if (nu < 1) return;
+  beta[0] = 1.0 / theta;
+  double rho = 1.0 / sigma;
+  for (int k = 1; k < nu; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    alpha[k] = rn * rho;
+    beta[k] = 2.0 * rn / delta;
+    rho = rn;
+  }
+}
+
+// nu smoothing steps on level l (x, f in l.x, l.f; the result ends in l.x)
+void enqueue_smooth(fmg_eig_handle* h, Level& l, int j, int nu, bool& zero, cudaStream_t s) {
+  if (h->prob.smoother == FMG_SMOOTH_CHEBYSHEV) {
+    std::vector<double> al, be;
+    cheb_coefficients(nu, al, be);
+    for (int it = 0; it < nu; ++it) {
+      const bool prof = !zero;
+      if (prof) prof_begin(h, kProfJacobi, j, s);
+      lv_cheb(l, l.f, l.x, l.z, l.xt, al[it], be[it], it == 0, zero, s);
+      if (prof) prof_end(h, kProfJacobi, j, s);
+      std::swap(l.x, l.xt);
+      zero = false;
+    }
+    return;
+  }
+  for (int it = 0; it < nu; ++it) {
+    const bool prof = !zero;
+    if (prof) prof_begin(h, kProfJacobi, j, s);
+    lv_jacobi(l, l.f, l.x, l.xt, zero, s);
+    if (prof) prof_end(h, kProfJacobi, j, s);
+    std::swap(l.x, l.xt);
+    zero = false;
+  }
+}
+
 // One V-cycle on level j for L_j x = f (x, f in L(j).x, L(j).f).
 void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   Level& l = h->L(j);
@@ -583,14 +639,7 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   const fmg_eig_problem& p = h->prob;
   bool zero = x_zero;
   prof_begin(h, kProfVcycle, j, s);
-  for (int it = 0; it < p.nu_pre; ++it) {
-    const bool prof = !zero;
-    if (prof) prof_begin(h, kProfJacobi, j, s);
-    lv_jacobi(l, l.f, l.x, l.xt, zero, s);
-    if (prof) prof_end(h, kProfJacobi, j, s);
-    std::swap(l.x, l.xt);
-    zero = false;
-  }
+  enqueue_smooth(h, l, j, p.nu_pre, zero, s);
   if (zero) cudaMemsetAsync(l.x, 0, l.g.stride * l.g.nb * sizeof(double), s);
   Level& lc = h->L(j - 1);
   prof_begin(h, kProfResidual, j, s);
@@ -603,10 +652,8 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   prof_begin(h, kProfProlong, j, s);
   lv_prolong(l, lc, lc.x, l.x, true, nullptr, nullptr, 0, s);
   prof_end(h, kProfProlong, j, s);
-  for (int it = 0; it < p.nu_post; ++it) {
-    lv_jacobi(l, l.f, l.x, l.xt, false, s);
-    std::swap(l.x, l.xt);
-  }
+  bool post_zero = false;
+  enqueue_smooth(h, l, j, p.nu_post, post_zero, s);
   prof_end(h, kProfVcycle, j, s);
 }
 

@@ -62,6 +62,10 @@ void jacobi2d(const Grid& g, const Coef2D& c, const double* f, const double* x, 
               bool x_is_zero, cudaStream_t s);
 void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* r,
                 cudaStream_t s);
+// Chebyshev step: d = (first ? 0 : alpha d) + beta D^{-1} (f - L x), xo = x + d (x = 0 when
+// x_zero); needs the coefficients built with omega = 1 (dinv = 1/D)
+void cheb2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* d,
+            double* xo, double alpha, double beta, bool first, bool x_zero, cudaStream_t s);
 void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s);
 // xf = (add ? xf : 0) + P ec (+ scale[b * scale_stride] * extra for instance b when extra is
@@ -104,6 +108,8 @@ void jacobi3d(const Grid& g, const Coef3D& c, const double* f, const double* x, 
               bool x_is_zero, cudaStream_t s);
 void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* r,
                 cudaStream_t s);
+void cheb3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* d,
+            double* xo, double alpha, double beta, bool first, bool x_zero, cudaStream_t s);
 void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s);
 void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,

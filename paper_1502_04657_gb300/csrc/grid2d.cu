@@ -124,6 +124,20 @@ __global__ void k_jacobi2d(int n, int pitch, size_t st, Coef2D c, const double* 
   xo[k] = fma(c.dinv[k], f[k] - lop(c, x, k, pitch), x[k]);
 }
 
+// One step of the Chebyshev semi-iteration: d <- alpha d + beta D^{-1} (f - L x), xo = x + d
+// (dinv = 1/D for this smoother).  first: d is not read (alpha = 0).  x_zero: x = 0.
+__global__ void k_cheb2d(int n, int pitch, size_t st, Coef2D c, const double* __restrict__ f,
+                         const double* __restrict__ x, double* __restrict__ d,
+                         double* __restrict__ xo, double alpha, double beta, int first,
+                         int x_zero) {
+  INTERIOR_2D
+  const double r = x_zero ? f[k] : f[k] - lop(c, x, k, pitch);
+  double dn = beta * c.dinv[k] * r;
+  if (!first) dn = fma(alpha, d[k], dn);
+  d[k] = dn;
+  xo[k] = x_zero ? dn : x[k] + dn;
+}
+
 __global__ void k_jacobi2d_zero(int n, int pitch, size_t st, Coef2D c, const double* __restrict__ f,
                                 double* __restrict__ xo) {
   INTERIOR_2D
@@ -314,6 +328,12 @@ void jacobi2d(const Grid& g, const Coef2D& c, const double* f, const double* x, 
   else
     k_jacobi2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride, c,
                                                                      f, x, xo);
+}
+
+void cheb2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* d,
+            double* xo, double alpha, double beta, bool first, bool x_zero, cudaStream_t s) {
+  k_cheb2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
+      g.n, g.pitch, g.stride, c, f, x, d, xo, alpha, beta, first ? 1 : 0, x_zero ? 1 : 0);
 }
 
 void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* r,

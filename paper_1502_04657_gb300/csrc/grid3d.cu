@@ -137,6 +137,19 @@ __global__ void k_jacobi3d(int n, int pitch, size_t st, Coef3D c, const double* 
   xo[k] = fma(c.dinv[k], f[k] - lop3(c, x, k, pitch, plane), x[k]);
 }
 
+// One step of the Chebyshev semi-iteration (see grid2d.cu)
+__global__ void k_cheb3d(int n, int pitch, size_t st, Coef3D c, const double* __restrict__ f,
+                         const double* __restrict__ x, double* __restrict__ d,
+                         double* __restrict__ xo, double alpha, double beta, int first,
+                         int x_zero) {
+  INTERIOR_3D
+  const double r = x_zero ? f[k] : f[k] - lop3(c, x, k, pitch, plane);
+  double dn = beta * c.dinv[k] * r;
+  if (!first) dn = fma(alpha, d[k], dn);
+  d[k] = dn;
+  xo[k] = x_zero ? dn : x[k] + dn;
+}
+
 __global__ void k_jacobi3d_zero(int n, int pitch, size_t st, Coef3D c, const double* __restrict__ f,
                                 double* __restrict__ xo) {
   INTERIOR_3D
@@ -537,6 +550,12 @@ void jacobi3d(const Grid& g, const Coef3D& c, const double* f, const double* x, 
               bool x_is_zero, cudaStream_t s) {
   if (x_is_zero) k_jacobi3d_zero<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, f, xo);
   else k_jacobi3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, f, x, xo);
+}
+
+void cheb3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* d,
+            double* xo, double alpha, double beta, bool first, bool x_zero, cudaStream_t s) {
+  k_cheb3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, c, f, x, d, xo, alpha, beta,
+                                   first ? 1 : 0, x_zero ? 1 : 0);
 }
 
 void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* r,

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libfmg_eig.so")
 FMG_OK, FMG_EINVAL, FMG_ENOMEM, FMG_ENOCONV, FMG_ECUDA, FMG_ETIMEOUT, FMG_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 FMG_FP64, FMG_MIXED_FP32 = 0, 1
 FMG_W_LEFT, FMG_PAPER_LITERAL = 0, 1
+FMG_SMOOTH_JACOBI, FMG_SMOOTH_CHEBYSHEV = 0, 1
 FMG_FLAG_NO_AUTOTUNE = 1
 FMG_FLAG_FP32_RHS = 2
 FMG_MAX_LEVELS = 16
@@ -162,6 +163,7 @@ class Problem:
     corrections: int = 1
     precision: int = FMG_FP64
     operator_form: int = FMG_W_LEFT
+    smoother: int = FMG_SMOOTH_JACOBI
     scf_max_iter: int = 100
     box_len: float = 1.0
     w_const: float = 0.0
@@ -175,9 +177,8 @@ class Problem:
         p = fmg_eig_problem()
         for f in ("dim", "coarse_cells", "levels", "nu_pre", "nu_post", "vcycles", "corrections",
                   "precision", "operator_form", "scf_max_iter", "box_len", "w_const", "zeta",
-                  "omega", "scf_tol", "flags"):
+                  "omega", "scf_tol", "flags", "smoother"):
             setattr(p, f, getattr(self, f))
-        p.smoother = 0
         p.w_quad[:] = [float(x) for x in self.w_quad]
         return p
 

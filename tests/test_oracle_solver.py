@@ -208,3 +208,53 @@ def test_fmg_3d_kuhn_small():
     lam_h, _, _ = O.discrete_ground_state(prob, lv[-1])
     lam_2h, _, _ = O.discrete_ground_state(prob, lv[-2])
     assert abs(r.lam - lam_h) < 0.1 * abs(lam_2h - lam_h)
+
+
+
+def _cheb_poly(t, degree, low=O.CHEB_LOW, high=O.CHEB_HIGH):
+    """The closed-form residual polynomial T_k((theta - t) / delta) / T_k(theta / delta)."""
+    theta, delta = 0.5 * (high + low), 0.5 * (high - low)
+    tk = np.polynomial.chebyshev.Chebyshev.basis(degree)
+    return tk((theta - t) / delta) / tk(theta / delta)
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 5])
+def test_chebyshev_error_is_the_chebyshev_polynomial_of_the_spectrum(degree):
+    """The error after the semi-iteration is p(D^-1 L) e0 with p the scaled Chebyshev
+    polynomial: on each eigenvector of D^-1 L the error shrinks by p(its eigenvalue)."""
+    prob = O.Problem(dim=2, coarse_cells=6, levels=1, w_const=0.5, w_quad=(2.0, 1.0, 0.0))
+    lev = O.build_hierarchy(prob)[0]
+    L = lev.L.toarray()
+    Dm = np.diag(1.0 / lev.D)
+    lam, V = np.linalg.eig(Dm @ L)
+    lam, V = lam.real, V.real
+    rng = np.random.default_rng(degree)
+    x_true = rng.normal(size=L.shape[0])
+    f = L @ x_true
+    x0 = rng.normal(size=L.shape[0])
+    x = O.chebyshev(lev, f, x0, degree)
+    coef0 = np.linalg.solve(V, x0 - x_true)
+    coef1 = np.linalg.solve(V, x - x_true)
+    assert np.allclose(coef1, _cheb_poly(lam, degree) * coef0, rtol=1e-9, atol=1e-12)
+
+
+def test_gershgorin_interval_contains_the_spectrum():
+    for dim, nc in ((2, 8), (3, 4)):
+        prob = O.Problem(dim=dim, coarse_cells=nc, levels=1, w_const=3.0, w_quad=(50.0, 20.0, 80.0))
+        lev = O.build_hierarchy(prob)[0]
+        lam = np.linalg.eigvals(np.diag(1.0 / lev.D) @ lev.L.toarray()).real
+        assert lam.max() <= O.CHEB_HIGH and lam.min() > 0.0
+
+
+def test_chebyshev_vcycle_converges_faster_than_jacobi():
+    errs = {}
+    for sm in (O.SMOOTH_JACOBI, O.SMOOTH_CHEBYSHEV):
+        prob = O.Problem(dim=2, coarse_cells=4, levels=4, w_quad=(1.0, 1.0, 0.0), smoother=sm)
+        lv = O.build_hierarchy(prob)
+        lev = lv[-1]
+        rng = np.random.default_rng(3)
+        x_true = rng.normal(size=lev.L.shape[0])
+        f = lev.L @ x_true
+        x = O.multigrid(lv, 4, f, np.zeros_like(f), 4, prob)
+        errs[sm] = np.linalg.norm(x - x_true) / np.linalg.norm(x_true)
+    assert errs[O.SMOOTH_CHEBYSHEV] < 0.8 * errs[O.SMOOTH_JACOBI]
