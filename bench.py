@@ -49,11 +49,23 @@ WORKLOADS = {
                 "dofs), W=100(x^2+y^2+4z^2), zeta=100, m=2, p=1, 2+2 Jacobi, FP64"),
     "config3-mixed": ("config3", True,
                       "config3 with FP32 V-cycles inside the FP64 defect correction"),
+    "config2-bf16": ("config2", "bf16",
+                     "config2 with bfloat16-stored (FP32-computed) V-cycles inside the FP64 "
+                     "defect correction (storage ablation)"),
+    "config3-bf16": ("config3", "bf16",
+                     "config3 with bfloat16-stored (FP32-computed) V-cycles inside the FP64 "
+                     "defect correction (storage ablation)"),
     "config4": ("config4", True,
                 "batch of 256 seeded 2D instances, coarsest h=1/8, finest h uniform on "
                 "{1/64..1/1024}, W=x^2+g^2 y^2 with g~U[1,4], zeta~U[0,200], FP32 V-cycles in "
                 "FP64 defect correction, one launch per step and level for the batch, one CUDA "
                 "graph, autotuned tiles; vs 256 sequential FP64 single solves"),
+    "paper-examples": ("paper-examples", False,
+                       "the paper's Examples 4.1 / 4.2 (Section 4): [0,1]^3, Kuhn P1 meshes, "
+                       "W = x1^2 + x2^2 + x3^2, zeta = 1 and 100, finest h = 1/8 .. 1/128 (the "
+                       "element counts of Tables 1-2); coarse space h = 1/4 (the paper's is its "
+                       "h = 1/8 initial mesh, solved with ARPACK); m = 1, p = 1; 3 + 3 Chebyshev "
+                       "smoothing (the paper: 3 + 3 conjugate-gradient steps); FP64"),
     "config5": ("config5", True,
                 "serving: seeded Poisson stream, 200 req/s, 10,000 requests, 70% 2D (h 1/64..1/2048, "
                 "coarsest 1/8) / 30% 3D (h 1/16..1/128, coarsest 1/4), zeta~U[0,200], anisotropic "
@@ -173,6 +185,11 @@ def reference_arm(args):
     if rank != 0:
         return
     config, mixed, desc = WORKLOADS[args.workload]
+    if config == "paper-examples":
+        print(json.dumps({"impl": "reference", "unavailable": "context workload (the paper's "
+                          "examples beside its Tables 1-2); the oracle is timed on configs 1-5"}),
+              flush=True)
+        return
     if config in ("config4", "config5"):
         vals = []
         for i in range(args.warmup + args.steps):
@@ -231,7 +248,7 @@ def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist
         desc = f"{desc} [truncated to {levels} levels for profiling]"
     gp = fmg.Problem(**{k: v for k, v in kw.items() if k in fmg.Problem.__dataclass_fields__})
     if mixed:
-        gp.precision = fmg.FMG_MIXED_FP32
+        gp.precision = fmg.FMG_MIXED_BF16 if mixed == "bf16" else fmg.FMG_MIXED_FP32
     gp.flags = flags | (0 if autotune else fmg.FMG_FLAG_NO_AUTOTUNE)
     n = gp.size(gp.levels)
     solver = fmg.Solver(gp)
@@ -380,6 +397,68 @@ def measure_batch(steps: int, warmup: int, world: int, local: int, dist=None) ->
                 {str(v): levels.count(v) for v in sorted(set(levels))}}
 
 
+# Tables 1 and 2 of the paper (Section 4): seconds of Algorithm 3.2 per finest mesh on a
+# PowerEdge R720 with ARPACK, by number of elements (context only: other hardware and coarse
+# space).  The tables print 1572846 for 8 x 196608 = 1572864.
+PAPER_TABLE = {1.0: {3072: 0.45, 24576: 1.55, 196608: 8.08, 1572864: 63.01, 12582912: 519.86},
+               100.0: {24576: 4.32, 196608: 11.43, 1572864: 70.88, 12582912: 577.52}}
+
+
+def paper_examples_arm(args, world, local, dist):
+    """The paper's two examples on its meshes (context run beside Tables 1-2)."""
+    import torch
+
+    from paper_1502_04657_gb300 import fmg
+
+    rank = rank_info()[0]
+    rows = []
+    stream = torch.cuda.Stream()
+    for zeta in (1.0, 100.0):
+        for levels in range(2, 7):  # finest h = 1/8 .. 1/128 from the h = 1/4 coarse space
+            p = fmg.Problem(dim=3, coarse_cells=4, levels=levels, w_const=0.0,
+                            w_quad=(1.0, 1.0, 1.0), zeta=zeta, vcycles=1, corrections=1,
+                            nu_pre=3, nu_post=3, smoother=fmg.FMG_SMOOTH_CHEBYSHEV)
+            elements = 6 * (4 << (levels - 1)) ** 3
+            with fmg.Solver(p) as s:
+                lam = torch.empty(1, dtype=torch.float64, device="cuda")
+                with torch.cuda.stream(stream):
+                    for _ in range(args.warmup):
+                        s.solve_dev(lam, stream=stream.cuda_stream)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(args.steps):
+                        s.solve_dev(lam, stream=stream.cuda_stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                _, st, rc = s.solve(stats=True)
+            # the discrete eigenvalue of the same mesh: 10 corrections per level
+            p.corrections = 10
+            with fmg.Solver(p) as s:
+                lam_ref, _, _ = s.solve()
+            lam1 = float(lam.item())
+            rows.append({"zeta": zeta, "h": f"1/{4 << (levels - 1)}", "elements": elements,
+                         "dofs": p.size(levels), "ms": ms, "lambda": lam1,
+                         "lambda_p10": lam_ref, "fmg_error_rel": abs(lam1 - lam_ref) / lam_ref,
+                         "identity_defect": st.identity_defect, "status": rc,
+                         "paper_s": PAPER_TABLE[zeta].get(elements)})
+    big = [r for r in rows if r["zeta"] == 1.0][-1]
+    line = {
+        "metric": METRIC, "value": 1e3 / big["ms"], "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": big["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOADS["paper-examples"][2],
+                                        "parallelism": "replicas"},
+        "rows": rows,
+        "note": "paper_s: seconds the paper reports for the same element count (PowerEdge R720, "
+                "ARPACK, coarse space h = 1/8); context, not a target",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def serve_arm(args, world, local, dist):
     """config5: fmg_eig_serve over the request stream (rank r serves every world-th request)."""
     import numpy as np
@@ -518,6 +597,8 @@ def ours_arm(args):
         return batch_arm(args, world, local, dist)
     if args.workload == "config5":
         return serve_arm(args, world, local, dist)
+    if args.workload == "paper-examples":
+        return paper_examples_arm(args, world, local, dist)
     m = measure(args.workload, args.steps, args.warmup, world, local, dist, levels=args.levels,
                 autotune=not args.no_autotune)
     main, other = roofline(m, m["clocks"])
@@ -526,7 +607,8 @@ def ours_arm(args):
         "metric": METRIC, "value": m["value"], "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32" if m["mixed"] else "f64", "data": "synthetic",
+        "dtype": ("f64+bf16" if m["mixed"] == "bf16" else "f64+f32") if m["mixed"] else "f64",
+        "data": "synthetic",
         "config": {"workload": m["desc"], "dofs": m["dofs"], "parallelism": "replicas",
                    "l2": "per-step working set > 2 GB >> 129 MB L2; no flush"},
         "mdof_per_s": m["value"] * m["dofs"] / 1e6,
@@ -540,8 +622,10 @@ def ours_arm(args):
         "identity_defect": m.get("identity_defect"),
     }
     if args.workload == "config2" and not args.no_extras:
-        for key, flags in (("mixed_fp32", 0), ("mixed_fp32_rhs32", 2)):
-            mx = measure("config2-mixed", max(3, args.steps // 2), 3, world, local, dist,
+        for key, wl, flags in (("mixed_fp32", "config2-mixed", 0),
+                               ("mixed_fp32_rhs32", "config2-mixed", 2),
+                               ("mixed_bf16_storage", "config2-bf16", 0)):
+            mx = measure(wl, max(3, args.steps // 2), 3, world, local, dist,
                          with_e2e=False, clocks=False, flags=flags)
             line[key] = {"value": mx["value"], "unit": "solves/s", "ms_per_step": mx["ms_per_step"],
                          "lambda": mx["lambda"],

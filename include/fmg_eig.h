@@ -50,12 +50,15 @@ extern "C" {
 #define FMG_SMOOTH_CHEBYSHEV 1
 #define FMG_FP64 0
 #define FMG_MIXED_FP32 1
+/* the same FP64 defect correction with the V-cycle's vectors and coefficients stored in
+ * bfloat16 (arithmetic in FP32): a storage ablation of FMG_MIXED_FP32                      */
+#define FMG_MIXED_BF16 2
 #define FMG_W_LEFT 0        /* (A + W) u^ = lambda M u - N(u)              */
 #define FMG_PAPER_LITERAL 1 /*  A u^      = lambda M u - W u - N(u)        */
 /* flags: keep the default 32 x 8 thread blocks instead of timing the candidate block shapes
  * of every level when the handle is created (results do not depend on the shapes).        */
 #define FMG_FLAG_NO_AUTOTUNE 1
-/* flags (with FMG_MIXED_FP32 only): evaluate the auxiliary right-hand side lambda M u - N(u)
+/* flags (with FMG_MIXED_FP32 / FMG_MIXED_BF16 only): evaluate the auxiliary right-hand side lambda M u - N(u)
  * of Algorithm 3.1 step 1 in FP32 as well.  Faster (the FP64 evaluation is a large share of
  * a mixed solve) but its rounding, ~1e-7 of |f|, enters u~ directly: measured |d lambda| up
  * to 7.6e-9 relative against FP64 (3D, W = 100(x^2 + y^2 + 4z^2), zeta = 100), against
@@ -73,7 +76,7 @@ typedef struct fmg_eig_problem {
   int32_t vcycles;      /* m of Algorithm 3.1 (>= 1)                                       */
   int32_t corrections;  /* p of Algorithm 3.2 (>= 1)                                       */
   int32_t smoother;     /* FMG_SMOOTH_JACOBI | FMG_SMOOTH_CHEBYSHEV                        */
-  int32_t precision;    /* FMG_FP64 | FMG_MIXED_FP32                                       */
+  int32_t precision;    /* FMG_FP64 | FMG_MIXED_FP32 | FMG_MIXED_BF16                      */
   int32_t operator_form;/* FMG_W_LEFT | FMG_PAPER_LITERAL                                  */
   int32_t scf_max_iter; /* cap on nonlinear iterations per small solve (e.g. 100)          */
   int32_t flags;        /* FMG_FLAG_* bits (0 = defaults)                                  */

@@ -96,6 +96,8 @@ struct fmg_eig_handle {
   fmg::PotentialParams* dparams_full = nullptr;
   fmg::PotentialParams* hparams = nullptr;
   bool literal() const { return prob.operator_form == FMG_PAPER_LITERAL; }
+  bool mixed() const { return prob.precision != FMG_FP64; }
+  bool bf16() const { return prob.precision == FMG_MIXED_BF16; }
   // profiling: event pairs around the first finest-level launch of each profiled step
   cudaEvent_t prof[fmg::kProfCount][2] = {};
   bool prof_armed[fmg::kProfCount] = {};

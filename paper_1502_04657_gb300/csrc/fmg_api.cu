@@ -195,12 +195,13 @@ int validate(const fmg_eig_problem* p) {
     return FMG_EINVAL;
   if (!(p->scf_tol > 0.0) || p->scf_max_iter < 1) return FMG_EINVAL;
   if (p->flags & ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS)) return FMG_EINVAL;
-  if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision != FMG_MIXED_FP32) return FMG_EINVAL;
+  if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision == FMG_FP64) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
   if (p->smoother != FMG_SMOOTH_JACOBI && p->smoother != FMG_SMOOTH_CHEBYSHEV) return FMG_EINVAL;
   if (p->smoother == FMG_SMOOTH_CHEBYSHEV && p->precision != FMG_FP64) return FMG_ENOTSUP;
-  if ((p->precision != FMG_FP64 && p->precision != FMG_MIXED_FP32) ||
+  if ((p->precision != FMG_FP64 && p->precision != FMG_MIXED_FP32 &&
+       p->precision != FMG_MIXED_BF16) ||
       (p->operator_form != FMG_W_LEFT && p->operator_form != FMG_PAPER_LITERAL))
     return FMG_ENOTSUP;
   return FMG_OK;
@@ -296,21 +297,25 @@ void build_levels(fmg_eig_handle* h) {
         l.cw3.tab = h->alloc<double>(15 * (size_t)(l.g.n + 1) * l.cap);
       }
     }
-    if (p.precision == FMG_MIXED_FP32) {
+    if (h->mixed()) {
+      // single-precision V-cycle arrays: FP32, or bfloat16 storage (2 bytes) behind float*
+      auto single = [&]() {
+        return h->bf16() ? reinterpret_cast<float*>(h->alloc<uint16_t>(s)) : h->alloc<float>(s);
+      };
       if (dim == 2) {
-        l.cf.cC = h->alloc<float>(s);
-        l.cf.cE = h->alloc<float>(s);
-        l.cf.cN = h->alloc<float>(s);
-        l.cf.cNE = h->alloc<float>(s);
-        l.cf.dinv = h->alloc<float>(s);
+        l.cf.cC = single();
+        l.cf.cE = single();
+        l.cf.cN = single();
+        l.cf.cNE = single();
+        l.cf.dinv = single();
       } else {
-        for (int q = 0; q < 8; ++q) l.cf3.a[q] = h->alloc<float>(s);
-        l.cf3.dinv = h->alloc<float>(s);
+        for (int q = 0; q < 8; ++q) l.cf3.a[q] = single();
+        l.cf3.dinv = single();
       }
-      l.x32 = h->alloc<float>(s);
-      l.xt32 = h->alloc<float>(s);
-      l.f32 = h->alloc<float>(s);
-      l.r32 = h->alloc<float>(s);
+      l.x32 = single();
+      l.xt32 = single();
+      l.f32 = single();
+      l.r32 = single();
     }
     l.x = h->alloc<double>(s);
     l.xt = h->alloc<double>(s);
@@ -521,17 +526,18 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s, bool overlap = false) {
     lv_coef(l, h->dparams, s);
     if (h->literal()) lv_coef(l, h->dparams_full, s, true);
     prof_end(h, kProfCoef, k, s);
-    if (h->prob.precision == FMG_MIXED_FP32) {
+    if (h->mixed()) {
       const size_t n = l.g.stride * l.g.nb;
+      const bool bf = h->bf16();
       if (l.g.dim == 2) {
-        to_f32(l.c.cC, l.cf.cC, n, s);
-        to_f32(l.c.cE, l.cf.cE, n, s);
-        to_f32(l.c.cN, l.cf.cN, n, s);
-        to_f32(l.c.cNE, l.cf.cNE, n, s);
-        to_f32(l.c.dinv, l.cf.dinv, n, s);
+        to_f32(l.c.cC, l.cf.cC, n, s, bf);
+        to_f32(l.c.cE, l.cf.cE, n, s, bf);
+        to_f32(l.c.cN, l.cf.cN, n, s, bf);
+        to_f32(l.c.cNE, l.cf.cNE, n, s, bf);
+        to_f32(l.c.dinv, l.cf.dinv, n, s, bf);
       } else {
-        for (int q = 0; q < 8; ++q) to_f32(l.c3.a[q], l.cf3.a[q], n, s);
-        to_f32(l.c3.dinv, l.cf3.dinv, n, s);
+        for (int q = 0; q < 8; ++q) to_f32(l.c3.a[q], l.cf3.a[q], n, s, bf);
+        to_f32(l.c3.dinv, l.cf3.dinv, n, s, bf);
       }
     }
     if (sk != s_saved) {
@@ -660,38 +666,39 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
 // One FP32 V-cycle on level j for L_j e = r (e, r in L(j).x32, L(j).f32), e starting at 0.
 void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
   Level& l = h->L(j);
+  const bool bf = h->bf16();
   if (j == 1) {
-    coarse32(l.g, h->L1inv, l.f32, l.x32, s);
+    coarse32(l.g, h->L1inv, l.f32, l.x32, s, bf);
     return;
   }
   const fmg_eig_problem& p = h->prob;
   bool zero = true;
   for (int it = 0; it < p.nu_pre; ++it) {
-    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, zero, s);
+    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, zero, s, bf);
     std::swap(l.x32, l.xt32);
     zero = false;
   }
-  if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * l.g.nb * sizeof(float), s);
+  if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * l.g.nb * mixed_elem_bytes(bf), s);
   Level& lc = h->L(j - 1);
-  residual32(l.g, l.cf, l.cf3, l.f32, l.x32, l.r32, s);
-  restrict32(l.g, lc.g, l.r32, lc.f32, s);
+  residual32(l.g, l.cf, l.cf3, l.f32, l.x32, l.r32, s, bf);
+  restrict32(l.g, lc.g, l.r32, lc.f32, s, bf);
   enqueue_vcycle32(h, j - 1, s);
-  prolong32_add(l.g, lc.g, lc.x32, l.x32, s);
+  prolong32_add(l.g, lc.g, lc.x32, l.x32, s, bf);
   for (int it = 0; it < p.nu_post; ++it) {
-    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s);
+    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s, bf);
     std::swap(l.x32, l.xt32);
   }
 }
 
 void enqueue_multigrid(fmg_eig_handle* h, int k, cudaStream_t s) {
-  if (h->prob.precision == FMG_MIXED_FP32) {
-    // FP64 defect correction around FP32 V-cycles
+  if (h->mixed()) {
+    // FP64 defect correction around single-precision V-cycles
     Level& l = h->L(k);
     for (int it = 0; it < h->prob.vcycles; ++it) {
       prof_begin(h, kProfVcycle, k, s);
-      residual_mixed(l.g, l.c, l.c3, l.f, l.x, l.f32, s);
+      residual_mixed(l.g, l.c, l.c3, l.f, l.x, l.f32, s, h->bf16());
       enqueue_vcycle32(h, k, s);
-      add_f32(l.x32, l.x, l.g.stride * l.g.nb, s);
+      add_f32(l.x32, l.x, l.g.stride * l.g.nb, s, h->bf16());
       prof_end(h, kProfVcycle, k, s);
     }
     return;
@@ -762,7 +769,7 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   const int nb = l.g.nb;
   // step 1: auxiliary problem, m V-cycles from u
   prof_begin(h, kProfRhs, k, s);
-  if (h->prob.precision == FMG_MIXED_FP32 && (h->prob.flags & FMG_FLAG_FP32_RHS))
+  if (h->mixed() && (h->prob.flags & FMG_FLAG_FP32_RHS))
     lv_rhs_f32(l, h->lam, h->dparams, l.u, l.f, s);
   else lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
   if (h->literal()) lv_sub_wmass(l, l.u, l.f, s);
@@ -851,8 +858,8 @@ std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 void time_mix(fmg_eig_handle* h, Level& l, int k, cudaStream_t s) {
   for (int q = 0; q < 4; ++q) {
-    if (h->prob.precision == FMG_MIXED_FP32 && k >= 2)
-      jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s);
+    if (h->mixed() && k >= 2)
+      jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s, h->bf16());
     else
       lv_jacobi(l, l.f, l.x, l.xt, false, s);
   }

@@ -147,21 +147,25 @@ struct CoefF3D {
   float* a[8];
   float* dinv;
 };
+// Storage of the single-precision V-cycle arrays (the float* below): FP32, or bfloat16 when
+// `bf` is set (FMG_MIXED_BF16; arithmetic stays FP32).  Bytes per element:
+size_t mixed_elem_bytes(bool bf16_storage);
 // contiguous conversions over n entries (all instances of a level at once)
-void to_f32(const double* a, float* b, size_t n, cudaStream_t s);
-void add_f32(const float* e, double* x, size_t n, cudaStream_t s);  // x += e (all entries)
-// r = (float)(f - L x) with the FP64 operator of the level (2D uses c2, 3D c3)
+void to_f32(const double* a, float* b, size_t n, cudaStream_t s, bool bf = false);
+void add_f32(const float* e, double* x, size_t n, cudaStream_t s, bool bf = false);  // x += e
+// r = f - L x with the FP64 operator of the level (2D uses c2, 3D c3), stored single
 void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const double* f,
-                    const double* x, float* r, cudaStream_t s);
+                    const double* x, float* r, cudaStream_t s, bool bf = false);
 void jacobi32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
-              const float* x, float* xo, bool zero, cudaStream_t s);
+              const float* x, float* xo, bool zero, cudaStream_t s, bool bf = false);
 void residual32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
-                const float* x, float* r, cudaStream_t s);
+                const float* x, float* r, cudaStream_t s, bool bf = false);
 void restrict32(const Grid& fine, const Grid& coarse, const float* rf, float* rc,
-                cudaStream_t s);
+                cudaStream_t s, bool bf = false);
 void prolong32_add(const Grid& fine, const Grid& coarse, const float* ec, float* xf,
-                   cudaStream_t s);
-void coarse32(const Grid& g, const double* Linv, const float* x, float* y, cudaStream_t s);
+                   cudaStream_t s, bool bf = false);
+void coarse32(const Grid& g, const double* Linv, const float* x, float* y, cudaStream_t s,
+              bool bf = false);
 
 // ---- Reductions (reduce.cu) -------------------------------------------------------------
 // out[b] = sum_i a[b vst + i] * b[b vst + i] over n entries for instances b < nb;
