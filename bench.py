@@ -98,6 +98,25 @@ def rank_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+# Multi-GPU is replicas only: instances are independent, so each rank solves its own share
+# and the only collectives are the barrier around the timed region and the max over ranks of
+# its duration (no collective on the data path).
+def shard(items, rank: int, world: int):
+    """Rank r's share of independent instances: every world-th one, starting at r."""
+    return items[rank::world]
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    """The slowest rank's time (the whole job's time); value itself with one rank."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
 
@@ -277,10 +296,7 @@ def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist
             dist.barrier()
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
     out = {"value": world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
            "step_ms": step_ms, "lambda": float(lam_d.item()), "dofs": n, "desc": desc,
            "profile": solver.profile(), "kernels": solver.kernel_count(), "clocks": clk,
@@ -295,10 +311,7 @@ def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist
         for _ in range(e2e_steps):
             lam_e2e, _, _ = solver.solve(u_host)
         e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(dist, e2e_s, "cuda")
         out["e2e"] = {"value": world * e2e_steps / e2e_s, "unit": "solves/s",
                       "h2d_bytes_per_step": 112, "d2h_bytes_per_step": 8 + 8 * n + 4 * 16}
         out["lambda_e2e"] = lam_e2e
@@ -347,10 +360,7 @@ def measure_batch(steps: int, warmup: int, world: int, local: int, dist=None) ->
         clk = clk_s.stop()
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
     lam_batch = lams.cpu().numpy()
     prof = batch.profile()
     kernels = batch.kernel_count()
@@ -467,7 +477,7 @@ def serve_arm(args, world, local, dist):
     from paper_1502_04657_gb300 import fmg
 
     rank = rank_info()[0]
-    reqs = serve_stream(args.serve_requests)[rank::world]
+    reqs = shard(serve_stream(args.serve_requests), rank, world)
     fields = fmg.Problem.__dataclass_fields__
     probs = [fmg.Problem(**{k: v for k, v in r.items() if k in fields},
                          precision=fmg.FMG_MIXED_FP32) for r in reqs]
@@ -494,9 +504,7 @@ def serve_arm(args, world, local, dist):
         worst = max(worst, abs(res[i]["lambda"] - lam) / lam)
     value = st["solves_per_s"]
     if dist:
-        t = torch.tensor([st["makespan_s"]], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        value = args.serve_requests / float(t.item())
+        value = args.serve_requests / max_over_ranks(dist, st["makespan_s"], "cuda")
     dofs = sum(p.size(p.levels) for p in probs)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
