@@ -1,0 +1,76 @@
+"""Edge and degenerate cases of the GPU path against the oracle, and the full 16.8M-dof 2D
+configuration checked through properties that hold at any size (the oracle cannot run it)."""
+import numpy as np
+import pytest
+
+from oracle import fmg_oracle as O
+from tests.test_gpu_parity import LAM_TOL, U_TOL, _fmg, _pair
+from workloads import seeded_problem_2d
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(dim=2, coarse_cells=4, levels=3, w_quad=(1.0, 1.0, 0.0), zeta=0.0),     # linear
+    dict(dim=2, coarse_cells=4, levels=3, w_quad=(0.0, 0.0, 0.0), zeta=0.0),     # Laplacian
+    dict(dim=2, coarse_cells=2, levels=4, w_quad=(1.0, 2.0, 0.0), zeta=3.0),     # 1 coarse dof
+    dict(dim=2, coarse_cells=5, levels=1, w_quad=(1.0, 2.0, 0.0), zeta=3.0),     # coarse only
+    dict(dim=3, coarse_cells=2, levels=2, w_quad=(0.0, 0.0, 0.0), zeta=0.0),     # 3D Laplacian
+    dict(dim=2, coarse_cells=4, levels=3, w_const=5.0, w_quad=(0.0, 0.0, 0.0), zeta=200.0),
+]
+
+
+@pytest.mark.parametrize("kw", CASES, ids=["linear", "laplace", "one-coarse-dof", "one-level",
+                                           "laplace-3d", "strong-zeta"])
+def test_degenerate_cases_match_oracle(kw):
+    op, gp = _pair(**kw)
+    ref = O.fmg_solve(op)
+    assert ref.converged
+    with _fmg().Solver(gp) as s:
+        u = np.empty(gp.size(gp.levels))
+        lam, st, rc = s.solve(u, stats=True)
+    assert rc == 0
+    assert abs(lam - ref.lam) <= LAM_TOL * ref.lam
+    assert np.linalg.norm(u - ref.u) <= U_TOL * np.linalg.norm(ref.u)
+
+
+def test_laplace_eigenvalue_approaches_two_pi_squared():
+    """zeta = 0, W = 0: the discrete lambda_h decreases to 2 pi^2 at O(h^2)."""
+    fmg = _fmg()
+    lams = []
+    for levels in (5, 6, 7):
+        p = fmg.Problem(dim=2, coarse_cells=8, levels=levels, w_quad=(0.0, 0.0, 0.0), zeta=0.0,
+                        corrections=3)
+        with fmg.Solver(p) as s:
+            lam, _, rc = s.solve()
+        assert rc == 0
+        lams.append(lam)
+    e = [l - 2 * np.pi ** 2 for l in lams]
+    assert all(x > 0 for x in e)
+    assert 3.5 < e[0] / e[1] < 4.5 and 3.5 < e[1] / e[2] < 4.5
+
+
+def test_full_size_2d_configuration_properties():
+    """The 16,769,025-dof configuration: lambda identity, normalisation, the x <-> y symmetry
+    of W = x^2 + y^2, and O(h^2) consistency with the coarser solves of the same problem."""
+    fmg = _fmg()
+    kw = seeded_problem_2d("config2")
+    fields = fmg.Problem.__dataclass_fields__
+    lams = {}
+    for levels in (8, 9, 10):
+        p = fmg.Problem(**{k: v for k, v in kw.items() if k in fields})
+        p.levels = levels
+        n = p.cells(levels) - 1
+        with fmg.Solver(p) as s:
+            u = np.empty(n * n)
+            lam, st, rc = s.solve(u, stats=True)
+        assert rc == 0
+        lams[levels] = lam
+        if levels == 10:
+            assert abs(st.identity_defect) < 1e-10 * lam
+            assert abs(st.norm_defect) < 1e-12
+            U = u.reshape(n, n)
+            assert np.max(np.abs(U - U.T)) <= 1e-9 * np.max(np.abs(U))
+            assert U.min() > 0.0
+    d1, d2 = lams[8] - lams[9], lams[9] - lams[10]
+    assert d1 > 0 and d2 > 0 and 3.0 < d1 / d2 < 5.0
