@@ -520,7 +520,9 @@ def serve_arm(args, world, local, dist):
                        "mean": st["mean_s"] * 1e3, "max": st["max_s"] * 1e3},
         "mdof_per_s": dofs / st["makespan_s"] / 1e6,
         "peak_hbm_gb": st["peak_bytes"] / 1e9, "hbm_budget_gb": st["budget_bytes"] / 1e9,
+        "peak_hbm_note": "in-flight and pooled (reusable) hierarchies",
         "cohorts": st["cohorts"], "max_cohort": st["max_cohort"],
+        "cohorts_replaying_pooled_graph": st["reused"], "pooled_evicted": st["evicted"],
         "max_inflight_seen": st["max_inflight_seen"], "completed": st["completed"],
         "max_dlambda_rel_vs_fp64_alone": worst, "dlambda_sample": int(len(idx)),
         "all_converged": all(r["status"] == 0 for r in res),

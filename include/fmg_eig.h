@@ -183,10 +183,12 @@ int fmg_eig_solve_batch(const fmg_eig_problem* probs, int32_t count, double* lam
  * Serving (no counterpart in the paper): a stream of independent solve requests, each with an
  * arrival time, served with continuous batching on one GPU.  Requests that have arrived are
  * admitted as a cohort (one batch handle: every step of each level one launch for all of
- * them) as soon as fewer than max_inflight cohorts are resident and the cohort's hierarchy
+ * them) as soon as fewer than max_inflight cohorts are in flight and the cohort's hierarchy
  * fits the device-memory budget; each cohort runs on its own stream, so newly admitted
  * cohorts overlap with the ones already on the GPU.  Hierarchies stay resident in device
- * memory until their cohort finishes and are then released (stream-ordered) for new ones.
+ * memory: a finished cohort's hierarchy (with its recorded CUDA graph) is pooled and replayed
+ * by a later cohort with the same level counts and settings, and pooled hierarchies are
+ * released (stream-ordered, oldest first) when an admission needs their memory.
  * ---------------------------------------------------------------------------------------- */
 typedef struct fmg_eig_serve_config {
   double hbm_budget_bytes; /* device bytes for resident hierarchies; <= 0: 80% of free    */
@@ -221,6 +223,8 @@ typedef struct fmg_eig_serve_stats {
   int32_t max_cohort;                 /* largest cohort                                   */
   int32_t max_inflight_seen;          /* most cohorts resident at once                    */
   int32_t completed;                  /* requests with a result                           */
+  int32_t reused;                     /* cohorts that replayed a pooled hierarchy's graph */
+  int32_t evicted;                    /* pooled hierarchies released to admit others      */
 } fmg_eig_serve_stats;
 
 /* Device bytes a batch handle for probs[0 .. count-1] allocates (an upper bound; 0 for bad

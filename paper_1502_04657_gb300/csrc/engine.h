@@ -50,6 +50,10 @@ struct CreateOptions {
   bool component_setup = true;  // operators ready for the component entry points
   bool async_alloc = false;     // cudaMallocAsync / cudaFreeAsync on the handle's stream
   int tune = 2;                 // 0: default tiles, 1: tuned tiles from the cache only, 2: tune
+  // When set (nb pinned doubles owned by the caller): after the coarse solve and after each
+  // finer FMG stage, the solve copies the eigenvalues of the instances that finish there to
+  // stage_lam[first..] and records one of the handle's stage events (inside the graph too).
+  double* stage_lam = nullptr;
 };
 
 }  // namespace fmg
@@ -105,6 +109,12 @@ struct fmg_eig_handle {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // stage marks (CreateOptions::stage_lam): event and sorted instance range per mark
+  struct StageMark {
+    cudaEvent_t ev;
+    int first, count;
+  };
+  std::vector<StageMark> marks;
   size_t dense_smem = 0;
 
   template <typename T>
@@ -148,6 +158,8 @@ size_t estimate_bytes(const fmg_eig_problem* probs, int count);
 // is enqueued, with the sorted instances [first, first + count) whose last level is k.
 using StageHook = std::function<void(int k, int first, int count)>;
 void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s, const StageHook* after_stage = nullptr);
+// host staging of the per-instance parameters from h->probs (before an upload)
+void fill_params(fmg_eig_handle* h);
 // upload the host staging of the parameters (every solve starts with it)
 cudaError_t upload_params(fmg_eig_handle* h, cudaStream_t s);
 // every instance's u from its finest level into h->uout (interior layout)

@@ -155,6 +155,8 @@ fmg_eig_handle::~fmg_eig_handle() {
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (ev_fork) cudaEventDestroy(ev_fork);
+  for (StageMark& m : marks)
+    if (m.ev) cudaEventDestroy(m.ev);
   for (cudaEvent_t e : ev_join)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : ev_level)
@@ -1056,11 +1058,23 @@ int create_handle(const fmg_eig_problem* probs, int count, const CreateOptions& 
     return FMG_OK;
   }
   for (int i = 0; i < kProfCount; ++i) h->prof_armed[i] = true;
+  // stage marks: one event per stage that finishes instances
+  StageHook mark_hook = [h](int, int first, int count) {
+    fmg_eig_handle::StageMark m{nullptr, first, count};
+    if (cudaEventCreate(&m.ev) == cudaSuccess) {
+      cudaMemcpyAsync(h->opt.stage_lam + first, h->lam + first, sizeof(double) * count,
+                      cudaMemcpyDeviceToHost, h->stream);
+      cudaEventRecordWithFlags(m.ev, h->stream, cudaEventRecordExternal);
+    }
+    h->marks.push_back(m);
+  };
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    enqueue_fmg(h, h->stream);
+    enqueue_fmg(h, h->stream, opt.stage_lam ? &mark_hook : nullptr);
     e = cudaStreamEndCapture(h->stream, &h->graph);
   }
+  for (const auto& m : h->marks)
+    if (!m.ev && e == cudaSuccess) e = cudaErrorMemoryAllocation;
   for (int i = 0; i < kProfCount; ++i) h->prof_armed[i] = false;
   if (e == cudaSuccess) {
     size_t n = 0;

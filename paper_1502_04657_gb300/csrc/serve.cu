@@ -1,17 +1,21 @@
 // Request server: continuous batching of independent solves on one GPU (fmg_eig_serve).
 //
 // One host thread runs the loop.  Requests that have arrived wait in a FIFO queue.  Whenever
-// fewer than max_inflight cohorts are resident, the queue's front request and the queued
+// fewer than max_inflight cohorts are in flight, the queue's front request and the queued
 // requests with the same shared settings (up to max_batch, while their hierarchies fit what
-// is left of the device-memory budget) are admitted as a cohort: one batch handle, built with
-// stream-ordered allocation on its own stream and launched directly.  Its FMG stages run
-// every step of a level as one launch over the cohort's instances with that level (see
-// engine.h), and after the stage that finishes some instances their eigenvalues are copied to
-// pinned host memory and an event is recorded.  Cohorts admitted later run on other streams
-// and overlap on the GPU with the ones already there.  A request's latency is read from the
-// GPU clock (the event of its copy against an event recorded when serving started).  When
-// all of a cohort's instances are done its outputs are collected and its memory returns to
-// the device pool for the next admissions.
+// is left of the device-memory budget) are admitted as a cohort: one batch handle on its own
+// stream, whose FMG stages run every step of a level as one launch over the cohort's
+// instances with that level (see engine.h).  Cohorts admitted later run on other streams and
+// overlap on the GPU with the ones already there.
+//
+// The handle of a cohort is recorded once as a CUDA graph that, after the stage which
+// finishes some instances, copies their eigenvalues to pinned host memory and records an
+// event.  A request's latency is read from the GPU clock: the event of its copy against an
+// event recorded when serving started.  When a cohort is done its hierarchy stays resident in
+// a pool keyed by its settings and sorted level counts; a later cohort with the same key
+// uploads its own parameters and replays the graph (no allocation, no capture, no per-kernel
+// launches).  Pooled hierarchies count against the budget and are released oldest first
+// (stream-ordered frees, which wait for no other cohort) when an admission needs room.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -19,6 +23,7 @@
 #include <chrono>
 #include <deque>
 #include <map>
+#include <string>
 #include <thread>
 #include <tuple>
 #include <vector>
@@ -28,22 +33,22 @@
 namespace fmg {
 namespace {
 
-struct StageMark {
-  cudaEvent_t ev = nullptr;
-  int first = 0, count = 0;
-  bool seen = false;
-};
-
 struct Cohort {
   fmg_eig_handle* h = nullptr;
+  std::string key;
   int id = 0;
   std::vector<int> req;  // req[b]: request index of the handle's sorted instance b
-  std::vector<StageMark> marks;
-  double* plam = nullptr;  // pinned region receiving the eigenvalues (nb)
+  std::vector<char> seen;
   size_t bytes = 0;
   double admit_s = 0.0;
   int pending = 0;
   bool failed = false;
+};
+
+struct Pooled {
+  fmg_eig_handle* h;
+  size_t bytes;
+  uint64_t stamp;  // release order (oldest first)
 };
 
 using Clock = std::chrono::steady_clock;
@@ -56,9 +61,9 @@ double since(Clock::time_point t0) {
 // footprints (the per-level arrays scale with the instance count, shared tables are counted
 // once per instance instead of once per cohort).
 struct Footprints {
-  std::map<std::tuple<int, int, int, int>, size_t> cache;
+  std::map<std::tuple<int, int, int, int, int>, size_t> cache;
   size_t of(const fmg_eig_problem& p) {
-    const auto key = std::make_tuple(p.dim, p.coarse_cells, p.levels, p.precision);
+    const auto key = std::make_tuple(p.dim, p.coarse_cells, p.levels, p.precision, p.operator_form);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     const size_t b = estimate_bytes(&p, 1) + ((size_t)1 << 16);
@@ -66,6 +71,40 @@ struct Footprints {
     return b;
   }
 };
+
+// Pinned eigenvalue slots of the pooled graphs (each graph copies to fixed addresses): a bump
+// arena with per-size free lists for the slots of released hierarchies.
+struct PinnedSlots {
+  double* base = nullptr;
+  size_t cap = 0, next = 0;
+  std::map<int, std::vector<double*>> free_by_size;
+  double* take(int n) {
+    auto it = free_by_size.find(n);
+    if (it != free_by_size.end() && !it->second.empty()) {
+      double* p = it->second.back();
+      it->second.pop_back();
+      return p;
+    }
+    if (next + n > cap) return nullptr;
+    double* p = base + next;
+    next += n;
+    return p;
+  }
+  void give(double* p, int n) { free_by_size[n].push_back(p); }
+};
+
+// the settings every instance of a cohort shares, and its sorted level counts
+std::string cohort_key(const fmg_eig_problem& p, const std::vector<int>& levels_desc) {
+  std::string k;
+  auto put = [&k](const void* v, size_t n) { k.append(static_cast<const char*>(v), n); };
+  const int32_t ints[] = {p.dim, p.coarse_cells, p.nu_pre, p.nu_post, p.vcycles, p.corrections,
+                          p.smoother, p.precision, p.operator_form, p.scf_max_iter, p.flags};
+  put(ints, sizeof(ints));
+  put(&p.box_len, sizeof(double));
+  put(&p.scf_tol, sizeof(double));
+  for (int l : levels_desc) put(&l, sizeof(int));
+  return k;
+}
 
 }  // namespace
 }  // namespace fmg
@@ -101,7 +140,7 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
   for (int i = 0; i < n; ++i)
     if ((double)fp.of(reqs[i].problem) > budget) return FMG_EINVAL;  // could never be admitted
 
-  // keep released cohort memory in the device pool for the next admissions
+  // keep released hierarchies' memory in the device pool for the next admissions
   cudaMemPool_t pool = nullptr;
   uint64_t old_threshold = 0, keep = UINT64_MAX;
   if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
@@ -110,11 +149,12 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
     cudaGetLastError();
     return FMG_ECUDA;
   }
-  double* plam_all = nullptr;
+  PinnedSlots slots;
+  slots.cap = std::max<size_t>((size_t)1 << 20, 4 * (size_t)n);
   cudaStream_t ref_stream = nullptr;
   cudaEvent_t ev_ref = nullptr;
   int rc = FMG_OK;
-  if (cudaMallocHost(&plam_all, sizeof(double) * n) != cudaSuccess ||
+  if (cudaMallocHost(&slots.base, sizeof(double) * slots.cap) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ref_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&ev_ref) != cudaSuccess || cudaEventRecord(ev_ref, ref_stream) != cudaSuccess ||
       cudaEventSynchronize(ev_ref) != cudaSuccess) {
@@ -130,14 +170,50 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
   }
   std::deque<int> queue;
   std::vector<Cohort> inflight;
-  int next = 0, done = 0, cohorts = 0, max_cohort = 0, max_inflight_seen = 0;
-  size_t plam_next = 0;
-  double used = 0.0, peak = 0.0;
+  std::map<std::string, std::vector<Pooled>> pooled;
+  uint64_t stamp = 0;
+  int next = 0, done = 0, cohorts = 0, max_cohort = 0, max_inflight_seen = 0, reused = 0,
+      evicted = 0;
+  double used = 0.0, peak = 0.0;  // bytes of in-flight and pooled hierarchies
   CreateOptions opt;
-  opt.graph = false;
   opt.component_setup = false;
   opt.async_alloc = true;
   opt.tune = 1;
+
+  auto release = [&](fmg_eig_handle* h, size_t bytes) {
+    slots.give(h->opt.stage_lam, h->nb);
+    delete h;  // stream-ordered frees: do not wait for other cohorts
+    used -= (double)bytes;
+  };
+  // release the oldest pooled hierarchy; false when none is left
+  auto evict_oldest = [&]() {
+    std::string best_key;
+    size_t best_i = 0;
+    uint64_t best = UINT64_MAX;
+    for (auto& kv : pooled)
+      for (size_t i = 0; i < kv.second.size(); ++i)
+        if (kv.second[i].stamp < best) {
+          best = kv.second[i].stamp;
+          best_key = kv.first;
+          best_i = i;
+        }
+    if (best == UINT64_MAX) return false;
+    Pooled p = pooled[best_key][best_i];
+    pooled[best_key].erase(pooled[best_key].begin() + best_i);
+    release(p.h, p.bytes);
+    ++evicted;
+    return true;
+  };
+  auto by_levels = [&](std::vector<int>& v) {  // the order a handle sorts its instances in
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+      return reqs[a].problem.levels > reqs[b].problem.levels;
+    });
+  };
+  auto levels_of = [&](const std::vector<int>& v) {
+    std::vector<int> lv;
+    for (int i : v) lv.push_back(reqs[i].problem.levels);
+    return lv;
+  };
 
   auto finish = [&](Cohort& c) {
     fmg_eig_handle* h = c.h;
@@ -169,10 +245,12 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
         if (st[(size_t)(k - 1) * nb + b] != 0) code = FMG_ENOCONV;
       o.status = code;
     }
-    if (!ok) cudaGetLastError();
-    for (StageMark& m : c.marks) cudaEventDestroy(m.ev);
-    delete h;  // stream-ordered release: does not wait for other cohorts
-    used -= (double)c.bytes;
+    if (!ok) {
+      cudaGetLastError();
+      release(h, c.bytes);
+      return;
+    }
+    pooled[c.key].push_back({h, c.bytes, stamp++});  // resident for the next such cohort
   };
 
   while (rc == FMG_OK && done < n) {
@@ -184,22 +262,23 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
     }
     // completions, in stage order per cohort
     for (Cohort& c : inflight) {
-      for (StageMark& m : c.marks) {
-        if (m.seen) continue;
-        const cudaError_t q = cudaEventQuery(m.ev);
+      const auto& marks = c.h->marks;
+      for (size_t m = 0; m < marks.size(); ++m) {
+        if (c.seen[m]) continue;
+        const cudaError_t q = cudaEventQuery(marks[m].ev);
         if (q == cudaErrorNotReady) break;
-        m.seen = true;
+        c.seen[m] = 1;
         progress = true;
         float ms = 0.f;
-        if (q != cudaSuccess || cudaEventElapsedTime(&ms, ev_ref, m.ev) != cudaSuccess) {
+        if (q != cudaSuccess || cudaEventElapsedTime(&ms, ev_ref, marks[m].ev) != cudaSuccess) {
           cudaGetLastError();
           c.failed = true;
           ms = (float)(since(t0) * 1e3);
         }
-        for (int b = m.first; b < m.first + m.count; ++b) {
+        for (int b = marks[m].first; b < marks[m].first + marks[m].count; ++b) {
           const int i = c.req[b];
           fmg_eig_result& o = results[i];
-          o.lambda = c.plam[b];
+          o.lambda = c.h->opt.stage_lam[b];
           o.done_s = ms * 1e-3;
           o.latency_s = o.done_s - reqs[i].arrival_s;
           o.admit_s = c.admit_s;
@@ -220,8 +299,6 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
     // admissions
     while (!queue.empty() && (int)inflight.size() < cfg->max_inflight) {
       const fmg_eig_problem& front = reqs[queue.front()].problem;
-      std::vector<int> pick;
-      double bytes = 0.0;
       int same = 0;
       for (int i : queue)
         if (same_shared_settings(reqs[i].problem, front)) ++same;
@@ -229,62 +306,91 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
       if (same < cfg->max_batch && next < n &&
           since(t0) - reqs[queue.front()].arrival_s < cfg->batch_window_s)
         break;
+      std::vector<int> pick;
       for (int i : queue) {
         if ((int)pick.size() >= cfg->max_batch) break;
-        if (!same_shared_settings(reqs[i].problem, front)) continue;
-        const double b = (double)fp.of(reqs[i].problem);
-        if (used + bytes + b > budget) continue;
-        pick.push_back(i);
-        bytes += b;
+        if (same_shared_settings(reqs[i].problem, front)) pick.push_back(i);
       }
-      if (pick.empty() || pick[0] != queue.front()) break;  // wait for memory (FIFO front first)
-      std::vector<fmg_eig_problem> ps;
-      for (int i : pick) ps.push_back(reqs[i].problem);
+      std::vector<int> sorted = pick;
+      by_levels(sorted);
       fmg_eig_handle* h = nullptr;
-      const int crc = create_handle(ps.data(), (int)ps.size(), opt, &h);
-      if (crc == FMG_ENOMEM && !inflight.empty()) break;  // retry once memory is released
+      size_t bytes = 0;
+      auto pit = pooled.find(cohort_key(front, levels_of(sorted)));
+      if (pit != pooled.end() && !pit->second.empty()) {  // replay a pooled hierarchy
+        h = pit->second.back().h;
+        bytes = pit->second.back().bytes;
+        pit->second.pop_back();
+        for (int b = 0; b < h->nb; ++b) {
+          h->probs[b] = reqs[sorted[b]].problem;
+          h->order[b] = b;
+        }
+        fill_params(h);
+        ++reused;
+      } else {
+        double need = 0.0;
+        for (int i : pick) need += (double)fp.of(reqs[i].problem);
+        while (used + need > budget && evict_oldest()) {
+        }
+        if (used + need > budget) {  // shrink to what fits (FIFO front first)
+          std::vector<int> fit;
+          double b2 = 0.0;
+          for (int i : pick) {
+            const double b = (double)fp.of(reqs[i].problem);
+            if (used + b2 + b <= budget) {
+              fit.push_back(i);
+              b2 += b;
+            }
+          }
+          if (fit.empty() || fit[0] != queue.front()) break;  // wait for memory
+          pick = fit;
+          sorted = pick;
+          by_levels(sorted);
+        }
+        std::vector<fmg_eig_problem> ps;
+        for (int i : sorted) ps.push_back(reqs[i].problem);
+        opt.stage_lam = slots.take((int)ps.size());
+        while (!opt.stage_lam && evict_oldest()) opt.stage_lam = slots.take((int)ps.size());
+        if (!opt.stage_lam) break;  // every slot is in flight: wait
+        const int crc = create_handle(ps.data(), (int)ps.size(), opt, &h);
+        if (crc != FMG_OK) {
+          slots.give(opt.stage_lam, (int)ps.size());
+          if (crc == FMG_ENOMEM && (!inflight.empty() || evict_oldest())) break;  // retry later
+          std::deque<int> rest;
+          for (int i : queue)
+            if (std::find(pick.begin(), pick.end(), i) == pick.end()) rest.push_back(i);
+          queue.swap(rest);
+          for (int i : pick) {  // fails alone as well: report it on these requests
+            results[i].status = crc;
+            results[i].done_s = since(t0);
+            results[i].latency_s = results[i].done_s - reqs[i].arrival_s;
+            ++done;
+          }
+          progress = true;
+          continue;
+        }
+        bytes = h->bytes;
+        used += (double)bytes;
+      }
       std::deque<int> rest;
       for (int i : queue)
         if (std::find(pick.begin(), pick.end(), i) == pick.end()) rest.push_back(i);
       queue.swap(rest);
       progress = true;
-      if (crc != FMG_OK) {  // fails alone as well: report it on these requests
-        for (int i : pick) {
-          results[i].status = crc;
-          results[i].done_s = since(t0);
-          results[i].latency_s = results[i].done_s - reqs[i].arrival_s;
-          ++done;
-        }
-        continue;
-      }
       Cohort c;
       c.h = h;
+      c.key = cohort_key(front, levels_of(sorted));
       c.id = cohorts++;
-      c.req.resize(h->nb);
-      for (int b = 0; b < h->nb; ++b) c.req[b] = pick[h->order[b]];
-      c.plam = plam_all + plam_next;
-      plam_next += h->nb;
-      c.bytes = h->bytes;
+      c.req = sorted;
+      c.seen.assign(h->marks.size(), 0);
+      c.bytes = bytes;
       c.admit_s = since(t0);
       c.pending = h->nb;
-      bool launch_ok = true;
-      const StageHook hook = [&](int, int first, int count) {
-        StageMark m;
-        m.first = first;
-        m.count = count;
-        launch_ok = launch_ok && cudaEventCreate(&m.ev) == cudaSuccess &&
-                    cudaMemcpyAsync(c.plam + first, h->lam + first, sizeof(double) * count,
-                                    cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
-                    cudaEventRecord(m.ev, h->stream) == cudaSuccess;
-        c.marks.push_back(m);
-      };
-      launch_ok = upload_params(h, h->stream) == cudaSuccess;
-      enqueue_fmg(h, h->stream, &hook);
-      if (!launch_ok || cudaGetLastError() != cudaSuccess) {
+      if (upload_params(h, h->stream) != cudaSuccess ||
+          cudaGraphLaunch(h->exec, h->stream) != cudaSuccess) {
+        cudaGetLastError();
         rc = FMG_ECUDA;
         c.failed = true;
       }
-      used += (double)c.bytes;
       peak = std::max(peak, used);
       max_cohort = std::max(max_cohort, h->nb);
       inflight.push_back(std::move(c));
@@ -293,16 +399,20 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
     }
     if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
-  // drain (error paths): wait for and release everything still resident
+  // drain (error paths): wait for and release everything still in flight
   for (Cohort& c : inflight) {
     cudaStreamSynchronize(c.h->stream);
     c.failed = true;
     finish(c);
   }
   inflight.clear();
+  for (auto& kv : pooled)
+    for (Pooled& p : kv.second) release(p.h, p.bytes);
+  pooled.clear();
+  cudaDeviceSynchronize();  // the frees above are stream-ordered
   cudaMemPoolTrimTo(pool, 0);
   cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &old_threshold);
-  if (plam_all) cudaFreeHost(plam_all);
+  if (slots.base) cudaFreeHost(slots.base);
   if (ev_ref) cudaEventDestroy(ev_ref);
   if (ref_stream) cudaStreamDestroy(ref_stream);
   cudaGetLastError();
@@ -344,6 +454,8 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
     stats->max_cohort = max_cohort;
     stats->max_inflight_seen = max_inflight_seen;
     stats->completed = completed;
+    stats->reused = reused;
+    stats->evicted = evicted;
   }
   return rc != FMG_OK ? rc : conv;
 }

@@ -59,7 +59,7 @@ class fmg_eig_serve_stats(C.Structure):
                 ("max_s", C.c_double), ("solves_per_s", C.c_double), ("makespan_s", C.c_double),
                 ("peak_bytes", C.c_double), ("budget_bytes", C.c_double), ("cohorts", C.c_int32),
                 ("max_cohort", C.c_int32), ("max_inflight_seen", C.c_int32),
-                ("completed", C.c_int32)]
+                ("completed", C.c_int32), ("reused", C.c_int32), ("evicted", C.c_int32)]
 
 
 class FmgError(RuntimeError):

@@ -74,6 +74,24 @@ def test_admission_respects_memory_budget():
         assert r["lambda"] == r0["lambda"]
 
 
+def test_pooled_hierarchies_are_replayed():
+    """Cohorts with the level counts of an earlier cohort replay its pooled hierarchy (and
+    graph) with their own parameters: results still equal the solves alone."""
+    fmg = _fmg()
+    rng = np.random.default_rng(17)
+    probs = []
+    for i in range(12):
+        g = rng.uniform(1.0, 4.0)
+        probs.append(fmg.Problem(dim=2, coarse_cells=8, levels=3 + (i % 2), w_quad=(1.0, g * g, 0.0),
+                                 zeta=float(rng.uniform(0, 200)), scf_max_iter=100))
+    arrivals = [0.004 * i for i in range(12)]  # one at a time: single-instance cohorts
+    res, st = fmg.serve(probs, arrivals, max_batch=1, max_inflight=2)
+    assert st["cohorts"] == 12 and st["reused"] >= 8
+    for p, r in zip(probs, res):
+        lam, _, rc = _alone(p)
+        assert r["status"] == rc == 0 and r["lambda"] == lam
+
+
 def test_request_larger_than_budget_is_rejected():
     fmg = _fmg()
     probs, arrivals = _stream(count=3)
