@@ -90,7 +90,9 @@ DOMINANT = "nload_density"
 # DRAM bytes per node of a finest-level launch from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum of the 9-level 2D launch, 4,190,209 nodes;
 # profiles/ncu_k_nload_density2d_h1-2048.md), scaled by the nodes a launch processes.
-TRAFFIC_PER_NODE = {(2, "nload_density"): (34.053376e6 + 105.419264e6) / 4190209}
+TRAFFIC_PER_NODE = {(2, "nload_density"): (34.053376e6 + 105.419264e6) / 4190209,
+                    # 3D: the 6-level launch, 2,048,383 nodes (profiles/ncu_k_nload_density3d_h1-128.md)
+                    (3, "nload_density"): (22.148608e6 + 82.583040e6) / 2048383}
 
 
 def rank_info():

@@ -124,25 +124,17 @@ __global__ void __launch_bounds__(kThreads)
   block_reduce(acc, kMono, sh, partials + ((size_t)tet * gridDim.x + blockIdx.x) * kMono);
 }
 
-// Boundary classes: block (class - 1, tet); each class is a 0-, 1- or 2-parameter set of
-// chain coordinates.
-__device__ __forceinline__ bool class_node(int cls, int r, int p, int q, int* abc) {
-  switch (cls) {
-    case 1: abc[0] = r; abc[1] = p; abc[2] = q; return r > p && p > q && q > 0;  // F0
-    case 2: abc[0] = p; abc[1] = p; abc[2] = q; return r > p && p > q && q > 0;  // F1
-    case 3: abc[0] = p; abc[1] = q; abc[2] = q; return r > p && p > q && q > 0;  // F2
-    case 4: abc[0] = p; abc[1] = q; abc[2] = 0; return r > p && p > q && q > 0;  // F3
-    case 5: abc[0] = r; abc[1] = r; abc[2] = p; return q == 1 && r > p && p > 0; // E01
-    case 6: abc[0] = r; abc[1] = p; abc[2] = p; return q == 1 && r > p && p > 0; // E02
-    case 7: abc[0] = r; abc[1] = p; abc[2] = 0; return q == 1 && r > p && p > 0; // E03
-    case 8: abc[0] = p; abc[1] = p; abc[2] = p; return q == 1 && r > p && p > 0; // E12
-    case 9: abc[0] = p; abc[1] = p; abc[2] = 0; return q == 1 && r > p && p > 0; // E13
-    case 10: abc[0] = p; abc[1] = 0; abc[2] = 0; return q == 1 && r > p && p > 0; // E23
-    case 11: abc[0] = 0; abc[1] = 0; abc[2] = 0; return p == 1 && q == 1;         // V0
-    case 12: abc[0] = r; abc[1] = 0; abc[2] = 0; return p == 1 && q == 1;         // V1
-    case 13: abc[0] = r; abc[1] = r; abc[2] = 0; return p == 1 && q == 1;         // V2
-    default: abc[0] = r; abc[1] = r; abc[2] = r; return p == 1 && q == 1;         // V3
-  }
+// Boundary classes: block (class - 1, tet, instance).
+//  * faces (F0..F3): two free chain coordinates p > q; a thread takes a row (fixed p) and
+//    walks q, summing u (q/r)^e, e = 0..3, then adds the row's 20 monomial sums (each
+//    monomial is a power of p/r times a power of q/r on a face);
+//  * edges: one free coordinate, a thread per node; vertices: one node.
+// Chain coordinates (a, b, c) of each class as functions of the free ones p > q > 0 (r fine
+// cells per coarse cell): faces F0 (r, p, q), F1 (p, p, q), F2 (p, q, q), F3 (p, q, 0); edges
+// E01 (r, r, p), E02 (r, p, p), E03 (r, p, 0), E12 (p, p, p), E13 (p, p, 0), E23 (p, 0, 0);
+// vertices (0,0,0), (r,0,0), (r,r,0), (r,r,r).
+__device__ __forceinline__ double pw3(double v, int e) {
+  return e == 0 ? 1.0 : (e == 1 ? v : (e == 2 ? v * v : v * v * v));
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -156,24 +148,75 @@ __global__ void __launch_bounds__(kThreads)
   const int cell = tet / 6, s = tet % 6;
   const int I = cell % n1, J = (cell / n1) % n1, L = cell / (n1 * n1);
   const double inv_r = 1.0 / r;
+  const double* base = u + (size_t)(L * r) * planef + (size_t)(J * r) * pf + (size_t)I * r;
+  auto node = [&](int a, int b, int c) {
+    int co[3];
+    co[kPermDev[s][0]] = a;
+    co[kPermDev[s][1]] = b;
+    co[kPermDev[s][2]] = c;
+    return base[(size_t)co[2] * planef + (size_t)co[1] * pf + co[0]];
+  };
   double acc[kMono];
 #pragma unroll
   for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
-  const int span = r + 1;
-  for (size_t idx = threadIdx.x; idx < (size_t)span * span; idx += kThreads) {
-    const int p = (int)(idx % span), q = (int)(idx / span);
-    int abc[3];
-    if (!class_node(cls, r, p, q, abc)) continue;
-    int co[3];
-    co[kPermDev[s][0]] = abc[0];
-    co[kPermDev[s][1]] = abc[1];
-    co[kPermDev[s][2]] = abc[2];
-    const double val =
-        u[(size_t)(L * r + co[2]) * planef + (size_t)(J * r + co[1]) * pf + (I * r + co[0])];
-    double m[kMono];
-    monomials(abc[0] * inv_r, abc[1] * inv_r, abc[2] * inv_r, m);
+  if (cls <= 4) {
+    // face rows: p = 2 .. r - 1 (F0..F2) with q in (0, p), F0 with p < r; F3: a = p, b = q
+    for (int p = 2 + threadIdx.x; p < r; p += kThreads) {
+      double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+      for (int q = 1; q < p; ++q) {
+        double v;
+        switch (cls) {
+          case 1: v = node(r, p, q); break;
+          case 2: v = node(p, p, q); break;
+          case 3: v = node(p, q, q); break;
+          default: v = node(p, q, 0); break;
+        }
+        const double t = q * inv_r, t2 = t * t;
+        m0 += v;
+        m1 = fma(v, t, m1);
+        m2 = fma(v, t2, m2);
+        m3 = fma(v, t2 * t, m3);
+      }
+      const double g = p * inv_r;
 #pragma unroll
-    for (int k = 0; k < kMono; ++k) acc[k] = fma(val, m[k], acc[k]);
+      for (int k = 0; k < kMono; ++k) {
+        const int ea = kMonoExpDev[k][0], eb = kMonoExpDev[k][1], ec = kMonoExpDev[k][2];
+        int ep, eq;  // exponents of p / r and q / r of a^ea b^eb c^ec on the face
+        bool zero = false;
+        switch (cls) {
+          case 1: ep = eb; eq = ec; break;           // (r, p, q)
+          case 2: ep = ea + eb; eq = ec; break;      // (p, p, q)
+          case 3: ep = ea; eq = eb + ec; break;      // (p, q, q)
+          default: ep = ea; eq = eb; zero = ec > 0; break;  // (p, q, 0)
+        }
+        if (!zero && ep <= 3 && eq <= 3)
+          acc[k] = fma(pw3(g, ep), pick4(m0, m1, m2, m3, eq), acc[k]);
+      }
+    }
+  } else {
+    // edges (one free coordinate p in (0, r)) and vertices (one node)
+    const bool vertex = cls >= 11;
+    for (int p = 1 + threadIdx.x; vertex ? (p == 1 && threadIdx.x == 0) : p < r;
+         p += kThreads) {
+      int abc[3];
+      switch (cls) {
+        case 5: abc[0] = r; abc[1] = r; abc[2] = p; break;   // E01
+        case 6: abc[0] = r; abc[1] = p; abc[2] = p; break;   // E02
+        case 7: abc[0] = r; abc[1] = p; abc[2] = 0; break;   // E03
+        case 8: abc[0] = p; abc[1] = p; abc[2] = p; break;   // E12
+        case 9: abc[0] = p; abc[1] = p; abc[2] = 0; break;   // E13
+        case 10: abc[0] = p; abc[1] = 0; abc[2] = 0; break;  // E23
+        case 11: abc[0] = 0; abc[1] = 0; abc[2] = 0; break;  // V0
+        case 12: abc[0] = r; abc[1] = 0; abc[2] = 0; break;  // V1
+        case 13: abc[0] = r; abc[1] = r; abc[2] = 0; break;  // V2
+        default: abc[0] = r; abc[1] = r; abc[2] = r; break;  // V3
+      }
+      const double val = node(abc[0], abc[1], abc[2]);
+      double m[kMono];
+      monomials(abc[0] * inv_r, abc[1] * inv_r, abc[2] * inv_r, m);
+#pragma unroll
+      for (int k = 0; k < kMono; ++k) acc[k] = fma(val, m[k], acc[k]);
+    }
   }
   block_reduce(acc, kMono, sh,
                partials + ((size_t)tet * (kClasses - 1) + blockIdx.x) * kMono);
