@@ -86,11 +86,17 @@ KERNELS = {
     2: {"nload_density": (117.0, 48.0), "jacobi": (16.0, 64.0)},
     3: {"nload_density": (659.0, 80.0), "jacobi": (32.0, 96.0)},
 }
-DOMINANT = "nload_density"
+# the kernel with the largest share of the solve in the ncu launch lists
+# (profiles/launches_config2_fp64.md: k_jacobi2d 20.6 %; launches_config3_fp64.md:
+# k_nload_density3d 32.8 %)
+DOMINANT = {2: "jacobi", 3: "nload_density"}
 # DRAM bytes per node of a finest-level launch from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum of the 9-level 2D launch, 4,190,209 nodes;
 # profiles/ncu_k_nload_density2d_h1-2048.md), scaled by the nodes a launch processes.
 TRAFFIC_PER_NODE = {(2, "nload_density"): (34.053376e6 + 105.419264e6) / 4190209,
+                    # the first level-9 sweep of the 9-level 2D solve, 4,190,209 nodes
+                    # (profiles/ncu_k_jacobi2d_h1-2048.md)
+                    (2, "jacobi"): (235150336 + 24169728) / 4190209,
                     # 3D: the 6-level launch, 2,048,383 nodes (profiles/ncu_k_nload_density3d_h1-128.md)
                     (3, "nload_density"): (22.148608e6 + 82.583040e6) / 2048383}
 
@@ -589,11 +595,14 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
                           "frac": ach / peak, "traffic": tpn * nodes if tpn else None,
                           "launch_ms": ms,
                           "hbm_gbs_algorithmic": nbytes * nodes / (ms * 1e-3) / 1e9}
-    main = dict(roof.get(DOMINANT, {}))
-    main["kernel"] = DOMINANT
+    dom = DOMINANT[m["dim"]]
+    if dom not in roof:  # FP32 V-cycles (mixed modes): the FP64 nonlinear pass dominates
+        dom = "nload_density"
+    main = dict(roof.get(dom, {}))
+    main["kernel"] = dom
     main["peak_source"] = ("FP64 (the kernel is FP64-ALU bound): 152 SMs x 2 DFMA/clk x sm_max_mhz, "
                            "nominal 1.25 TFLOP/s; of fallback (no FP64 figure in the measured peaks)")
-    return main, {k: v for k, v in roof.items() if k != DOMINANT}
+    return main, {k: v for k, v in roof.items() if k != dom}
 
 
 def ours_arm(args):
