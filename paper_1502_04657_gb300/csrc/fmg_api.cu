@@ -1113,13 +1113,42 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
       }
     }
   }
-  for (fmg_eig_handle* h : hs) {
+  // A pinned (or registered) host buffer is written by the GPU directly through its device
+  // alias (over the CPU-GPU link, no staging copy); pageable buffers are staged in h->uout and
+  // copied.
+  std::vector<std::vector<double*>> alias(hs.size());
+  for (size_t g = 0; g < hs.size(); ++g) {
+    fmg_eig_handle* h = hs[g];
+    alias[g].assign(h->nb, nullptr);
+    for (int b = 0; u_hosts && b < h->nb; ++b) {
+      const int i = out_index[g][b];
+      cudaPointerAttributes attr;
+      if (u_hosts[i] && cudaPointerGetAttributes(&attr, u_hosts[i]) == cudaSuccess &&
+          attr.type == cudaMemoryTypeHost && attr.devicePointer)
+        alias[g][b] = static_cast<double*>(attr.devicePointer);
+      cudaGetLastError();
+    }
+  }
+  for (size_t g = 0; g < hs.size(); ++g) {
+    fmg_eig_handle* h = hs[g];
     cudaStream_t s = h->stream;
     CK(cudaEventRecord(h->ev0, s));
     CK(upload_params(h, s));
     CK(cudaGraphLaunch(h->exec, s));
     CK(cudaEventRecord(h->ev1, s));
-    if (u_hosts) enqueue_outputs(h, s);
+    if (u_hosts) {
+      bool staged = false;
+      for (int b = 0; b < h->nb; ++b) {
+        if (!u_hosts[out_index[g][b]]) continue;
+        if (alias[g][b]) {
+          Level v = view(h->L(h->probs[b].levels), b, 1);
+          unpack_interior(v.g, v.u, alias[g][b], s);
+        } else {
+          staged = true;
+        }
+      }
+      if (staged) enqueue_outputs(h, s);
+    }
     if (stats) enqueue_checks(h, s);
     h->activate(1);
   }
@@ -1140,7 +1169,7 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
     }
     for (int b = 0; u_hosts && b < nb; ++b) {
       const int i = out_index[g][b];
-      if (u_hosts[i])
+      if (u_hosts[i] && !alias[g][b])
         CK(cudaMemcpyAsync(u_hosts[i], h->uout + h->uoff[b], sizeof(double) * u_lens[i],
                            cudaMemcpyDeviceToHost, s));
     }

@@ -230,3 +230,19 @@ def test_invalid_arguments_are_rejected():
     with fmg.Solver(fmg.Problem(coarse_cells=4, levels=2)) as s:
         with pytest.raises(fmg.FmgError):
             s.solve(np.empty(5))
+
+
+def test_pinned_and_pageable_outputs_agree():
+    """fmg_eig_solve writes a pinned host buffer directly from the GPU and stages a pageable
+    one: both give the same u."""
+    fmg = _fmg()
+    _, gp = _pair(dim=2, coarse_cells=4, levels=5, w_quad=(1.0, 2.0, 0.0), zeta=6.0)
+    n = gp.size(gp.levels)
+    with fmg.Solver(gp) as s:
+        pageable = np.empty(n)
+        lam1, _, rc1 = s.solve(pageable)
+        pinned = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        pinned[:] = np.nan
+        lam2, _, rc2 = s.solve(pinned)
+    assert rc1 == rc2 == 0 and lam1 == lam2
+    assert np.array_equal(pageable, pinned)
