@@ -27,9 +27,8 @@ struct Level {
          *y = nullptr, *z = nullptr;
   Density2D b{};          // density stencil of u~ (augmented pass), 2D
   Density3D b3{};         // same, 3D
-  // mixed precision: FP32 copies of the coefficients and FP32 V-cycle vectors
-  CoefF2D cf{};
-  CoefF3D cf3{};
+  // mixed precision: FP32 coefficient tables and single-precision V-cycle vectors
+  CoefT ct{};
   float *x32 = nullptr, *xt32 = nullptr, *f32 = nullptr, *r32 = nullptr;
   double* pw = nullptr;   // (x / r)^m table for the 2D T3 sums (levels >= 2)
   double* t3map = nullptr;  // class sums -> T3 map of this level (levels >= 2)

@@ -37,14 +37,13 @@ Level view(const Level& l, int first, int count) {
     adv(v.cw3.a[q]);
     adv(v.c3.a[q]);
     adv(v.b3.a[q]);
-    adv(v.cf3.a[q]);
   }
-  adv(v.c3.dinv); adv(v.cf3.dinv);
+  adv(v.c3.dinv);
   adv(v.x); adv(v.xt); adv(v.f); adv(v.r); adv(v.u); adv(v.y); adv(v.z);
   adv(v.b.C); adv(v.b.E); adv(v.b.N); adv(v.b.NE);
-  adv(v.cf.cC); adv(v.cf.cE); adv(v.cf.cN); adv(v.cf.cNE); adv(v.cf.dinv);
   adv(v.x32); adv(v.xt32); adv(v.f32); adv(v.r32);
-  v.c.tab = v.c3.tab = v.cw.tab = v.cw3.tab = nullptr;  // setup scratch is not sliced
+  v.c.tab = v.c3.tab = v.cw.tab = v.cw3.tab = nullptr;  // per-instance tables are not sliced
+  v.ct = CoefT{};
   v.g.nb = count;
   return v;
 }
@@ -304,16 +303,8 @@ void build_levels(fmg_eig_handle* h) {
       auto single = [&]() {
         return h->bf16() ? reinterpret_cast<float*>(h->alloc<uint16_t>(s)) : h->alloc<float>(s);
       };
-      if (dim == 2) {
-        l.cf.cC = single();
-        l.cf.cE = single();
-        l.cf.cN = single();
-        l.cf.cNE = single();
-        l.cf.dinv = single();
-      } else {
-        for (int q = 0; q < 8; ++q) l.cf3.a[q] = single();
-        l.cf3.dinv = single();
-      }
+      l.ct.tab = h->alloc<float>((size_t)(dim == 2 ? 8 : 15) * (l.g.n + 1) * l.cap);
+      l.ct.cst = h->alloc<float>(4 * (size_t)l.cap);
       l.x32 = single();
       l.xt32 = single();
       l.f32 = single();
@@ -528,20 +519,7 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s, bool overlap = false) {
     lv_coef(l, h->dparams, s);
     if (h->literal()) lv_coef(l, h->dparams_full, s, true);
     prof_end(h, kProfCoef, k, s);
-    if (h->mixed()) {
-      const size_t n = l.g.stride * l.g.nb;
-      const bool bf = h->bf16();
-      if (l.g.dim == 2) {
-        to_f32(l.c.cC, l.cf.cC, n, s, bf);
-        to_f32(l.c.cE, l.cf.cE, n, s, bf);
-        to_f32(l.c.cN, l.cf.cN, n, s, bf);
-        to_f32(l.c.cNE, l.cf.cNE, n, s, bf);
-        to_f32(l.c.dinv, l.cf.dinv, n, s, bf);
-      } else {
-        for (int q = 0; q < 8; ++q) to_f32(l.c3.a[q], l.cf3.a[q], n, s, bf);
-        to_f32(l.c3.dinv, l.cf3.dinv, n, s, bf);
-      }
-    }
+    if (h->mixed()) tables_f32(l.g, l.c, l.c3, h->dparams, l.ct, s);
     if (sk != s_saved) {
       cudaEventRecord(h->ev_level[k], sk);
       h->level_pending[k] = true;
@@ -676,18 +654,18 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
   const fmg_eig_problem& p = h->prob;
   bool zero = true;
   for (int it = 0; it < p.nu_pre; ++it) {
-    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, zero, s, bf);
+    jacobi32(l.g, l.ct, h->dparams, l.f32, l.x32, l.xt32, zero, s, bf);
     std::swap(l.x32, l.xt32);
     zero = false;
   }
   if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * l.g.nb * mixed_elem_bytes(bf), s);
   Level& lc = h->L(j - 1);
-  residual32(l.g, l.cf, l.cf3, l.f32, l.x32, l.r32, s, bf);
+  residual32(l.g, l.ct, l.f32, l.x32, l.r32, s, bf);
   restrict32(l.g, lc.g, l.r32, lc.f32, s, bf);
   enqueue_vcycle32(h, j - 1, s);
   prolong32_add(l.g, lc.g, lc.x32, l.x32, s, bf);
   for (int it = 0; it < p.nu_post; ++it) {
-    jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s, bf);
+    jacobi32(l.g, l.ct, h->dparams, l.f32, l.x32, l.xt32, false, s, bf);
     std::swap(l.x32, l.xt32);
   }
 }
@@ -861,7 +839,7 @@ std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 void time_mix(fmg_eig_handle* h, Level& l, int k, cudaStream_t s) {
   for (int q = 0; q < 4; ++q) {
     if (h->mixed() && k >= 2)
-      jacobi32(l.g, l.cf, l.cf3, l.f32, l.x32, l.xt32, false, s, h->bf16());
+      jacobi32(l.g, l.ct, h->dparams, l.f32, l.x32, l.xt32, false, s, h->bf16());
     else
       lv_jacobi(l, l.f, l.x, l.xt, false, s);
   }

@@ -140,12 +140,12 @@ void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
 void t3_map3d(int r, double* out);  // 20 * 15 * 20 doubles
 
 // ---- Mixed precision (mixed.cu) ------------------------------------------------------------
-struct CoefF2D {
-  float *cC, *cE, *cN, *cNE, *dinv;
-};
-struct CoefF3D {
-  float* a[8];
-  float* dinv;
+// FP32 separable coefficient tables of one level for the single-precision V-cycle: tab =
+// the level's FP64 tables (2D: 8, 3D: 15 per instance, n + 1 entries each) in FP32, cst = the
+// 3D constants (C, axis, face, body) per instance.
+struct CoefT {
+  float* tab;
+  float* cst;
 };
 // Storage of the single-precision V-cycle arrays (the float* below): FP32, or bfloat16 when
 // `bf` is set (FMG_MIXED_BF16; arithmetic stays FP32).  Bytes per element:
@@ -156,10 +156,15 @@ void add_f32(const float* e, double* x, size_t n, cudaStream_t s, bool bf = fals
 // r = f - L x with the FP64 operator of the level (2D uses c2, 3D c3), stored single
 void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const double* f,
                     const double* x, float* r, cudaStream_t s, bool bf = false);
-void jacobi32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
+// the FP32 tables of level g from its FP64 ones (after the level's operator setup)
+void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
+                const PotentialParams* pp, const CoefT& ct, cudaStream_t s);
+// damped Jacobi sweep / residual with coefficients rebuilt from the FP32 tables (omega from
+// the parameters)
+void jacobi32(const Grid& g, const CoefT& ct, const PotentialParams* pp, const float* f,
               const float* x, float* xo, bool zero, cudaStream_t s, bool bf = false);
-void residual32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
-                const float* x, float* r, cudaStream_t s, bool bf = false);
+void residual32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* r,
+                cudaStream_t s, bool bf = false);
 void restrict32(const Grid& fine, const Grid& coarse, const float* rf, float* rc,
                 cudaStream_t s, bool bf = false);
 void prolong32_add(const Grid& fine, const Grid& coarse, const float* ec, float* xf,

@@ -4,9 +4,13 @@
 //     r = f - L x  (FP64 operator, stored in S),   e = V32(r),   x <- x + e  (FP64),
 // so only the residual and the update touch FP64 arithmetic.  FP32 issues at ~64x the FP64
 // rate on this part, which leaves the V-cycle's smoothing, residual and transfer kernels bound
-// by HBM bandwidth.  Their vectors and coefficients are stored in S = float or (the storage
-// ablation) bfloat16, always computed in FP32; the FP64 residual keeps the outer iteration
-// converging to the FP64 solution of L x = f.
+// by HBM bandwidth.  Their vectors are stored in S = float or (the storage ablation)
+// bfloat16, always computed in FP32.  The stencil coefficients are not stored at all: they are
+// separable (2D: an x table plus a y table per coupling; 3D: a constant plus one table per
+// axis, see grid2d.cu / grid3d.cu), so a sweep rebuilds them in FP32 from the level's small
+// tables (L1-resident) and reads only x and f: 12 bytes per node instead of 32 (2D) or 48
+// (3D).  The FP64 residual keeps the outer iteration converging to the FP64 solution of
+// L x = f.
 #include <cuda_bf16.h>
 
 #include "fmg_internal.h"
@@ -23,29 +27,6 @@ __device__ __forceinline__ float ld(const bf16* p, size_t k) { return __bfloat16
 __device__ __forceinline__ void st(float* p, size_t k, float v) { p[k] = v; }
 __device__ __forceinline__ void st(bf16* p, size_t k, float v) { p[k] = __float2bfloat16_rn(v); }
 
-template <typename S>
-struct CS2 {
-  const S *cC, *cE, *cN, *cNE, *dinv;
-};
-template <typename S>
-struct CS3 {
-  const S* a[8];
-  const S* dinv;
-};
-
-template <typename S>
-CS2<S> cs(const CoefF2D& c) {
-  return {reinterpret_cast<const S*>(c.cC), reinterpret_cast<const S*>(c.cE),
-          reinterpret_cast<const S*>(c.cN), reinterpret_cast<const S*>(c.cNE),
-          reinterpret_cast<const S*>(c.dinv)};
-}
-template <typename S>
-CS3<S> cs(const CoefF3D& c) {
-  CS3<S> o;
-  for (int q = 0; q < 8; ++q) o.a[q] = reinterpret_cast<const S*>(c.a[q]);
-  o.dinv = reinterpret_cast<const S*>(c.dinv);
-  return o;
-}
 template <typename S>
 S* sp(float* p) {
   return reinterpret_cast<S*>(p);
@@ -94,39 +75,49 @@ __global__ void k_residual_mixed2d(int n, int pitch, size_t st_, Coef2D c,
   st(r, k, (float)(f[k] - v));
 }
 
-// ---- single-precision 2D stencil kernels ----------------------------------------------------
+// ---- single-precision 2D stencil kernels -----------------------------------------------------
+// Coefficients of node (i, j) from the instance's tables (X = x tables C, E, N, NE; Y the y
+// ones, s = n + 1 entries each): c = X[i] + Y[j]; the W and S couplings are those of (i-1, j)
+// and (i, j-1).
 template <typename S>
-__device__ __forceinline__ float lop32(const CS2<S>& c, const S* __restrict__ x, size_t k,
-                                       int pitch) {
-  float v = ld(c.cC, k) * ld(x, k);
-  v = fmaf(ld(c.cE, k), ld(x, k + 1), v);
-  v = fmaf(ld(c.cE, k - 1), ld(x, k - 1), v);
-  v = fmaf(ld(c.cN, k), ld(x, k + pitch), v);
-  v = fmaf(ld(c.cN, k - pitch), ld(x, k - pitch), v);
-  v = fmaf(ld(c.cNE, k), ld(x, k + pitch + 1), v);
-  v = fmaf(ld(c.cNE, k - pitch - 1), ld(x, k - pitch - 1), v);
+__device__ __forceinline__ float lop_t2(const float* __restrict__ X, const float* __restrict__ Y,
+                                        int s, int i, int j, float cc, const S* __restrict__ x,
+                                        size_t k, int pitch) {
+  float v = cc * ld(x, k);
+  v = fmaf(X[s + i] + Y[s + j], ld(x, k + 1), v);
+  v = fmaf(X[s + i - 1] + Y[s + j], ld(x, k - 1), v);
+  v = fmaf(X[2 * s + i] + Y[2 * s + j], ld(x, k + pitch), v);
+  v = fmaf(X[2 * s + i] + Y[2 * s + j - 1], ld(x, k - pitch), v);
+  v = fmaf(X[3 * s + i] + Y[3 * s + j], ld(x, k + pitch + 1), v);
+  v = fmaf(X[3 * s + i - 1] + Y[3 * s + j - 1], ld(x, k - pitch - 1), v);
   return v;
 }
 
+#define TABLES_2D                                       \
+  const int s = n + 1;                                  \
+  const float* X = tab + (size_t)ib * 8 * s;            \
+  const float* Y = X + 4 * s;                           \
+  const float cc = X[i] + Y[j];
+
+// damped Jacobi sweep (x = 0 on entry when zero)
 template <typename S>
-__global__ void k_jacobi32_2d(int n, int pitch, size_t st_, CS2<S> c, const S* __restrict__ f,
-                              const S* __restrict__ x, S* __restrict__ xo) {
+__global__ void k_jacobi32_2d(int n, int pitch, size_t st_, const float* __restrict__ tab,
+                              const PotentialParams* __restrict__ pp, const S* __restrict__ f,
+                              const S* __restrict__ x, S* __restrict__ xo, int zero) {
   INTERIOR_2D
-  st(xo, k, fmaf(ld(c.dinv, k), ld(f, k) - lop32(c, x, k, pitch), ld(x, k)));
+  TABLES_2D
+  const float dinv = (float)pp[ib].omega / cc;
+  if (zero) st(xo, k, dinv * ld(f, k));
+  else st(xo, k, fmaf(dinv, ld(f, k) - lop_t2(X, Y, s, i, j, cc, x, k, pitch), ld(x, k)));
 }
 
 template <typename S>
-__global__ void k_jacobi32z_2d(int n, int pitch, size_t st_, CS2<S> c, const S* __restrict__ f,
-                               S* __restrict__ xo) {
+__global__ void k_residual32_2d(int n, int pitch, size_t st_, const float* __restrict__ tab,
+                                const S* __restrict__ f, const S* __restrict__ x,
+                                S* __restrict__ r) {
   INTERIOR_2D
-  st(xo, k, ld(c.dinv, k) * ld(f, k));
-}
-
-template <typename S>
-__global__ void k_residual32_2d(int n, int pitch, size_t st_, CS2<S> c, const S* __restrict__ f,
-                                const S* __restrict__ x, S* __restrict__ r) {
-  INTERIOR_2D
-  st(r, k, ld(f, k) - lop32(c, x, k, pitch));
+  TABLES_2D
+  st(r, k, ld(f, k) - lop_t2(X, Y, s, i, j, cc, x, k, pitch));
 }
 
 template <typename S>
@@ -186,38 +177,93 @@ __global__ void k_residual_mixed3d(int n, int pitch, size_t st_, Coef3D c,
   st(r, k, (float)(f[k] - v));
 }
 
+// Coefficients of a 3D node from the instance's tables T(ax, q)[c] = tab[(ax 5 + q) s + c]
+// (s = n + 1) and constants cst = (C, axis, face, body), as in grid3d.cu:
+//   C = cst0 + T(x,0) + T(y,0) + T(z,0);  axis d: cst1 + T(d,1) + sum_{ax != d} T(ax,2);
+//   face with third axis o: cst2 + T(o,4) + sum_{ax != o} T(ax,3);  body: cst3 + sum T(ax,1).
+// The coupling to p - d is the one of p - d to p.
 template <typename S>
-__device__ __forceinline__ float lop32_3(const CS3<S>& c, const S* __restrict__ x, size_t k,
-                                         int pitch, long plane) {
-  float v = ld(c.a[0], k) * ld(x, k);
+__device__ __forceinline__ float lop_t3(const float* __restrict__ T, int s, const float* cst,
+                                        const int co[3], float& cc, const S* __restrict__ x,
+                                        size_t k, int pitch, long plane) {
+  float tv[3][5][2];  // table q of axis ax at co[ax] (0) and co[ax] - 1 (1)
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      tv[ax][q][0] = T[(ax * 5 + q) * s + co[ax]];
+      tv[ax][q][1] = T[(ax * 5 + q) * s + co[ax] - 1];
+    }
+  cc = cst[0] + tv[0][0][0] + tv[1][0][0] + tv[2][0][0];
+  float v = cc * ld(x, k);
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pitch, plane);
-    v = fmaf(ld(c.a[1 + d], k), ld(x, k + o), v);
-    v = fmaf(ld(c.a[1 + d], k - o), ld(x, k - o), v);
+    float a[2];  // the coupling at p (0) and at p - d (1)
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      float c;
+      const int s0 = side ? kDir[d][0] : 0, s1 = side ? kDir[d][1] : 0, s2 = side ? kDir[d][2] : 0;
+      if (d < 3) {
+        c = cst[1] + tv[0][d == 0 ? 1 : 2][s0] + tv[1][d == 1 ? 1 : 2][s1] + tv[2][d == 2 ? 1 : 2][s2];
+      } else if (d < 6) {
+        const int oth = 5 - d;  // XY -> z, XZ -> y, YZ -> x
+        c = cst[2] + tv[0][oth == 0 ? 4 : 3][s0] + tv[1][oth == 1 ? 4 : 3][s1] +
+            tv[2][oth == 2 ? 4 : 3][s2];
+      } else {
+        c = cst[3] + tv[0][1][s0] + tv[1][1][s1] + tv[2][1][s2];
+      }
+      a[side] = c;
+    }
+    v = fmaf(a[0], ld(x, k + o), v);
+    v = fmaf(a[1], ld(x, k - o), v);
   }
   return v;
 }
 
+#define TABLES_3D                                        \
+  const int s = n + 1;                                   \
+  const float* T = tab + (size_t)ib * 15 * s;            \
+  const float* C = cst + 4 * ib;                         \
+  const int co[3] = {i, j, l};
+
 template <typename S>
-__global__ void k_jacobi32_3d(int n, int pitch, size_t st_, CS3<S> c, const S* __restrict__ f,
-                              const S* __restrict__ x, S* __restrict__ xo) {
+__global__ void k_jacobi32_3d(int n, int pitch, size_t st_, const float* __restrict__ tab,
+                              const float* __restrict__ cst, const PotentialParams* __restrict__ pp,
+                              const S* __restrict__ f, const S* __restrict__ x, S* __restrict__ xo,
+                              int zero) {
   INTERIOR_3D
-  st(xo, k, fmaf(ld(c.dinv, k), ld(f, k) - lop32_3(c, x, k, pitch, plane), ld(x, k)));
+  TABLES_3D
+  float cc;
+  const float lx = lop_t3(T, s, C, co, cc, x, k, pitch, plane);
+  const float dinv = (float)pp[ib].omega / cc;
+  if (zero) st(xo, k, dinv * ld(f, k));
+  else st(xo, k, fmaf(dinv, ld(f, k) - lx, ld(x, k)));
 }
 
 template <typename S>
-__global__ void k_jacobi32z_3d(int n, int pitch, size_t st_, CS3<S> c, const S* __restrict__ f,
-                               S* __restrict__ xo) {
-  INTERIOR_3D
-  st(xo, k, ld(c.dinv, k) * ld(f, k));
-}
-
-template <typename S>
-__global__ void k_residual32_3d(int n, int pitch, size_t st_, CS3<S> c, const S* __restrict__ f,
+__global__ void k_residual32_3d(int n, int pitch, size_t st_, const float* __restrict__ tab,
+                                const float* __restrict__ cst, const S* __restrict__ f,
                                 const S* __restrict__ x, S* __restrict__ r) {
   INTERIOR_3D
-  st(r, k, ld(f, k) - lop32_3(c, x, k, pitch, plane));
+  TABLES_3D
+  float cc;
+  st(r, k, ld(f, k) - lop_t3(T, s, C, co, cc, x, k, pitch, plane));
+}
+
+// constants of the 3D coefficient tables per instance (grid3d.cu's k_coef3d): C, axis, face,
+// body; wl = 0 drops W (paper-literal form)
+__global__ void k_consts3d(int nb, double h, const PotentialParams* __restrict__ pp,
+                           float* __restrict__ cst) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const PotentialParams p = pp[b];
+  const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
+  const double h3w = wl * h * h * h * p.w0;
+  cst[4 * b + 0] = (float)(6.0 * h + 0.4 * h3w);
+  cst[4 * b + 1] = (float)(-h + h3w * (1.0 / 20.0));
+  cst[4 * b + 2] = (float)(h3w * (1.0 / 30.0));
+  cst[4 * b + 3] = (float)(h3w * (1.0 / 20.0));
 }
 
 template <typename S>
@@ -292,26 +338,25 @@ unsigned blocks_for(size_t n) {
 }
 
 template <typename S>
-void jacobi_t(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
+void jacobi_t(const Grid& g, const CoefT& ct, const PotentialParams* pp, const float* f,
               const float* x, float* xo, bool zero, cudaStream_t s) {
-  if (g.dim == 2) {
-    const dim3 gr = grid2(g, g.n - 1, g.n - 1);
-    if (zero) k_jacobi32z_2d<S><<<gr, blk(g), 0, s>>>(g.n, g.pitch, g.stride, cs<S>(c2), sp<S>(f), sp<S>(xo));
-    else k_jacobi32_2d<S><<<gr, blk(g), 0, s>>>(g.n, g.pitch, g.stride, cs<S>(c2), sp<S>(f), sp<S>(x), sp<S>(xo));
-  } else {
-    const dim3 gr = grid3(g, g.n - 1, g.n - 1, g.n - 1);
-    if (zero) k_jacobi32z_3d<S><<<gr, blk(g), 0, s>>>(g.n, g.pitch, g.stride, cs<S>(c3), sp<S>(f), sp<S>(xo));
-    else k_jacobi32_3d<S><<<gr, blk(g), 0, s>>>(g.n, g.pitch, g.stride, cs<S>(c3), sp<S>(f), sp<S>(x), sp<S>(xo));
-  }
+  if (g.dim == 2)
+    k_jacobi32_2d<S><<<grid2(g, g.n - 1, g.n - 1), blk(g), 0, s>>>(
+        g.n, g.pitch, g.stride, ct.tab, pp, sp<S>(f), sp<S>(x), sp<S>(xo), zero ? 1 : 0);
+  else
+    k_jacobi32_3d<S><<<grid3(g, g.n - 1, g.n - 1, g.n - 1), blk(g), 0, s>>>(
+        g.n, g.pitch, g.stride, ct.tab, ct.cst, pp, sp<S>(f), sp<S>(x), sp<S>(xo), zero ? 1 : 0);
 }
 
 template <typename S>
-void residual_t(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
-                const float* x, float* r, cudaStream_t s) {
+void residual_t(const Grid& g, const CoefT& ct, const float* f, const float* x, float* r,
+                cudaStream_t s) {
   if (g.dim == 2)
-    k_residual32_2d<S><<<grid2(g, g.n - 1, g.n - 1), blk(g), 0, s>>>(g.n, g.pitch, g.stride, cs<S>(c2), sp<S>(f), sp<S>(x), sp<S>(r));
+    k_residual32_2d<S><<<grid2(g, g.n - 1, g.n - 1), blk(g), 0, s>>>(
+        g.n, g.pitch, g.stride, ct.tab, sp<S>(f), sp<S>(x), sp<S>(r));
   else
-    k_residual32_3d<S><<<grid3(g, g.n - 1, g.n - 1, g.n - 1), blk(g), 0, s>>>(g.n, g.pitch, g.stride, cs<S>(c3), sp<S>(f), sp<S>(x), sp<S>(r));
+    k_residual32_3d<S><<<grid3(g, g.n - 1, g.n - 1, g.n - 1), blk(g), 0, s>>>(
+        g.n, g.pitch, g.stride, ct.tab, ct.cst, sp<S>(f), sp<S>(x), sp<S>(r));
 }
 
 template <typename S>
@@ -363,16 +408,23 @@ void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const dou
   }
 }
 
-void jacobi32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
-              const float* x, float* xo, bool zero, cudaStream_t s, bool bf) {
-  if (bf) jacobi_t<bf16>(g, c2, c3, f, x, xo, zero, s);
-  else jacobi_t<float>(g, c2, c3, f, x, xo, zero, s);
+void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
+                const PotentialParams* pp, const CoefT& ct, cudaStream_t s) {
+  const size_t n = (size_t)(g.dim == 2 ? 8 : 15) * (g.n + 1) * g.nb;
+  k_to_s<float><<<blocks_for(n), 256, 0, s>>>(n, g.dim == 2 ? c2.tab : c3.tab, ct.tab);
+  if (g.dim == 3) k_consts3d<<<(g.nb + 127) / 128, 128, 0, s>>>(g.nb, g.h, pp, ct.cst);
 }
 
-void residual32(const Grid& g, const CoefF2D& c2, const CoefF3D& c3, const float* f,
-                const float* x, float* r, cudaStream_t s, bool bf) {
-  if (bf) residual_t<bf16>(g, c2, c3, f, x, r, s);
-  else residual_t<float>(g, c2, c3, f, x, r, s);
+void jacobi32(const Grid& g, const CoefT& ct, const PotentialParams* pp, const float* f,
+              const float* x, float* xo, bool zero, cudaStream_t s, bool bf) {
+  if (bf) jacobi_t<bf16>(g, ct, pp, f, x, xo, zero, s);
+  else jacobi_t<float>(g, ct, pp, f, x, xo, zero, s);
+}
+
+void residual32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* r,
+                cudaStream_t s, bool bf) {
+  if (bf) residual_t<bf16>(g, ct, f, x, r, s);
+  else residual_t<float>(g, ct, f, x, r, s);
 }
 
 void restrict32(const Grid& fine, const Grid& coarse, const float* rf, float* rc,
