@@ -90,6 +90,18 @@ KERNELS = {
 # (profiles/launches_config2_fp64.md: k_jacobi2d 20.6 %; launches_config3_fp64.md:
 # k_nload_density3d 32.8 %)
 DOMINANT = {2: "jacobi", 3: "nload_density"}
+# The single-precision V-cycle (mixed modes) is HBM-bound: a Jacobi sweep or residual reads x
+# and f and writes one vector, 3 x 4 bytes per node (3 x 2 with BF16 storage); the
+# coefficients are rebuilt from per-axis tables that stay in L1.
+MIXED_HBM_KERNELS = ("jacobi", "residual")
+
+
+def hbm_peak() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
 # DRAM bytes per node of a finest-level launch from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum of the 9-level 2D launch, 4,190,209 nodes;
 # profiles/ncu_k_nload_density2d_h1-2048.md), scaled by the nodes a launch processes.
@@ -586,7 +598,20 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
     peak = FP64_FLOP_PER_CLK_SM * N_SM * sm_max * 1e6 / 1e12
     roof = {}
     nodes = m.get("dofs_finest_launch", m["dofs"])  # nodes one finest-level launch processes
+    mixed = m.get("mixed")
+    if mixed:  # FP32 / BF16 V-cycle kernels against the HBM peak
+        bpn = 6.0 if mixed == "bf16" else 12.0
+        hpeak, hsrc = hbm_peak()
+        for name in MIXED_HBM_KERNELS:
+            ms = m["profile"].get(name, -1.0)
+            if ms and ms > 0:
+                ach = bpn * nodes / (ms * 1e-3) / 1e9
+                roof[name + "32"] = {"bound": "hbm", "achieved": ach, "peak": hpeak, "unit": "GB/s",
+                                     "frac": ach / hpeak, "traffic": None, "launch_ms": ms,
+                                     "bytes_per_node": bpn, "peak_source": hsrc}
     for name, (flops, nbytes) in KERNELS[m["dim"]].items():
+        if mixed and name in MIXED_HBM_KERNELS:
+            continue
         ms = m["profile"].get(name, -1.0)
         if ms and ms > 0:
             ach = flops * nodes / (ms * 1e-3) / 1e12
@@ -648,9 +673,12 @@ def ours_arm(args):
                                ("mixed_bf16_storage", "config2-bf16", 0)):
             mx = measure(wl, max(3, args.steps // 2), 3, world, local, dist,
                          with_e2e=False, clocks=False, flags=flags)
+            _, mroof = roofline(mx, m["clocks"])
             line[key] = {"value": mx["value"], "unit": "solves/s", "ms_per_step": mx["ms_per_step"],
                          "lambda": mx["lambda"],
-                         "dlambda_rel_vs_fp64": abs(mx["lambda"] - m["lambda"]) / m["lambda"]}
+                         "dlambda_rel_vs_fp64": abs(mx["lambda"] - m["lambda"]) / m["lambda"],
+                         "roofline_v_cycle": {k: v for k, v in mroof.items() if k.endswith("32")},
+                         "kernel_ms_finest": mx["profile"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         config = WORKLOADS[args.workload][0]
         levels = ORACLE_SAMPLE[config][0]

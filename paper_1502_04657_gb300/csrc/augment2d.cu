@@ -17,6 +17,7 @@
 // depend only on v's class (interior of T, one of T's three edges, one of its vertices), so
 // T3 follows from monomial sums of u~ per class: 4 FP64 FMAs per interior node.
 #include "fmg_internal.h"
+#include "reduce_dev.cuh"
 
 namespace fmg {
 namespace {
@@ -154,19 +155,6 @@ constexpr int kSums = 25;
 constexpr int kSumThreads = 256;
 constexpr int kSumRows = 64;
 
-__device__ void block_reduce(double* acc, int count, double* sh, double* out) {
-  for (int m = 0; m < count; ++m) {
-    sh[threadIdx.x] = acc[m];
-    __syncthreads();
-    for (int st = kSumThreads / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[m] = sh[0];
-    __syncthreads();
-  }
-}
-
 template <int T>
 __device__ void t3_sums_body(int pf, int n1, int r, const double* __restrict__ u,
                              const double* __restrict__ pw, double* __restrict__ partials,
@@ -177,7 +165,7 @@ __device__ void t3_sums_body(int pf, int n1, int r, const double* __restrict__ u
   const int cell = tri >> 1;
   const int I = cell % n1, J = cell / n1;
   const int cb = blockIdx.x % col_blocks, rb = blockIdx.x / col_blocks;
-  const int s = cb * kSumThreads + threadIdx.x;
+  const int s = cb * blockDim.x + threadIdx.x;
   const int t0 = rb * kSumRows;
   const int t1 = min(t0 + kSumRows, r + 1);
   double c[4] = {0.0, 0.0, 0.0, 0.0};  // interior: sum_t u tg^l for this column
@@ -258,8 +246,7 @@ __device__ void t3_sums_body(int pf, int n1, int r, const double* __restrict__ u
   acc[22] = ok * vtx[0];
   acc[23] = ok * vtx[1];
   acc[24] = ok * vtx[2];
-  block_reduce(acc, kSums, sh,
-               partials + ((size_t)tri * gridDim.x + blockIdx.x) * kSums);
+  block_sum_to<kSums>(acc, sh, partials + ((size_t)tri * gridDim.x + blockIdx.x) * kSums);
 }
 
 __global__ void __launch_bounds__(kSumThreads)
@@ -328,7 +315,9 @@ __global__ void k_gather_level1_2d(int n, int pitch, size_t st, const double* __
   put(-1, -1, b.NE[k - pitch - 1]);
 }
 
-int t3_col_blocks(int r) { return (r + 1 + kSumThreads - 1) / kSumThreads; }
+// a block takes blockDim.x columns (whole warps, up to kSumThreads) of kSumRows rows
+int t3_threads2d(int r) { return warps_for(r + 1, kSumThreads); }
+int t3_col_blocks(int r) { return (r + 1 + t3_threads2d(r) - 1) / t3_threads2d(r); }
 int t3_row_blocks(int r) { return (r + 1 + kSumRows - 1) / kSumRows; }
 
 dim3 grid_of(const Grid& g, int cx, int cy) {
@@ -369,7 +358,7 @@ void t3_moments2d(const Grid& fine, int n1, const double* u, const double* pw,
   const int r = fine.n / n1;
   const int cb = t3_col_blocks(r), rb = t3_row_blocks(r);
   const size_t pst = t3_partials2d(fine, n1);
-  k_t3_sums2d<<<dim3(cb * rb, 2 * n1 * n1, fine.nb), kSumThreads, 0, s>>>(
+  k_t3_sums2d<<<dim3(cb * rb, 2 * n1 * n1, fine.nb), t3_threads2d(r), 0, s>>>(
       fine.pitch, n1, r, fine.stride, pst, u, pw, partials, cb);
   k_t3_finalize2d<<<dim3(2 * n1 * n1, fine.nb), 32, 0, s>>>(
       cb * rb, fine.h * fine.h, pst, (size_t)2 * n1 * n1 * 10, partials, map, t3);

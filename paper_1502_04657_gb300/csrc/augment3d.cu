@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "fmg_internal.h"
+#include "reduce_dev.cuh"
 
 namespace fmg {
 namespace {
@@ -34,19 +35,6 @@ __device__ __forceinline__ void monomials(double a, double b, double c, double* 
   m[4] = a * a; m[5] = a * b; m[6] = a * c; m[7] = b * b; m[8] = b * c; m[9] = c * c;
   m[10] = m[4] * a; m[11] = m[4] * b; m[12] = m[4] * c; m[13] = a * m[7]; m[14] = m[5] * c;
   m[15] = a * m[9]; m[16] = m[7] * b; m[17] = m[7] * c; m[18] = b * m[9]; m[19] = m[9] * c;
-}
-
-__device__ void block_reduce(double* acc, int count, double* sh, double* out) {
-  for (int m = 0; m < count; ++m) {
-    sh[threadIdx.x] = acc[m];
-    __syncthreads();
-    for (int st = kThreads / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[m] = sh[0];
-    __syncthreads();
-  }
 }
 
 // Interior class: thread = one row (x1, x2) of the coarse cell, block (chunk of rows, tet,
@@ -84,7 +72,7 @@ __global__ void __launch_bounds__(kThreads)
   double acc[kMono];
 #pragma unroll
   for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
-  const int row = blockIdx.x * kThreads + threadIdx.x;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row < R * R) {
     const int x1 = row % R, x2 = row / R;
     // the two fixed chain coordinates (positions q1 < q2, the ones other than pos0)
@@ -121,7 +109,7 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
   }
-  block_reduce(acc, kMono, sh, partials + ((size_t)tet * gridDim.x + blockIdx.x) * kMono);
+  block_sum_to<kMono>(acc, sh, partials + ((size_t)tet * gridDim.x + blockIdx.x) * kMono);
 }
 
 // Boundary classes: block (class - 1, tet, instance).
@@ -161,7 +149,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
   if (cls <= 4) {
     // face rows: p = 2 .. r - 1 (F0..F2) with q in (0, p), F0 with p < r; F3: a = p, b = q
-    for (int p = 2 + threadIdx.x; p < r; p += kThreads) {
+    for (int p = 2 + threadIdx.x; p < r; p += blockDim.x) {
       double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
       for (int q = 1; q < p; ++q) {
         double v;
@@ -197,7 +185,7 @@ __global__ void __launch_bounds__(kThreads)
     // edges (one free coordinate p in (0, r)) and vertices (one node)
     const bool vertex = cls >= 11;
     for (int p = 1 + threadIdx.x; vertex ? (p == 1 && threadIdx.x == 0) : p < r;
-         p += kThreads) {
+         p += blockDim.x) {
       int abc[3];
       switch (cls) {
         case 5: abc[0] = r; abc[1] = r; abc[2] = p; break;   // E01
@@ -218,8 +206,7 @@ __global__ void __launch_bounds__(kThreads)
       for (int k = 0; k < kMono; ++k) acc[k] = fma(val, m[k], acc[k]);
     }
   }
-  block_reduce(acc, kMono, sh,
-               partials + ((size_t)tet * (kClasses - 1) + blockIdx.x) * kMono);
+  block_sum_to<kMono>(acc, sh, partials + ((size_t)tet * (kClasses - 1) + blockIdx.x) * kMono);
 }
 
 // T3_e = h^3 sum_{class, g} map[e][class][g] S^class_g
@@ -247,10 +234,15 @@ __global__ void k_t3_finalize3d(int chunks, double h3, size_t pst, size_t tst,
   t3[(size_t)tet * 20 + e] = h3 * acc;
 }
 
+// Interior: a block takes interior_threads(r) rows (whole warps, up to kThreads) of the
+// (r + 1)^2 rows of a tetrahedron.  Boundary: the face rows and edge nodes of a class number
+// fewer than r, so a block of boundary_threads(r) covers them in one or a few passes.
+int interior_threads(int r) { return warps_for((long)(r + 1) * (r + 1), kThreads); }
 int interior_chunks(int r) {
-  const size_t rows = (size_t)(r + 1) * (r + 1);
-  return (int)((rows + kThreads - 1) / kThreads);
+  const long rows = (long)(r + 1) * (r + 1);
+  return (int)((rows + interior_threads(r) - 1) / interior_threads(r));
 }
+int boundary_threads(int r) { return warps_for(r, kThreads); }
 
 // ---- host: class moments and the linear map ---------------------------------------------
 // Polynomials in the 4 barycentrics of a tetrahedron, exponents packed in a key.
@@ -374,9 +366,9 @@ void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
   const size_t pst = t3_partials3d(fine, n1);  // per instance
   double* pin = partials;
   double* pbd = partials + (size_t)tets * chunks * kMono;
-  k_t3_interior3d<<<dim3(chunks, tets, fine.nb), kThreads, 0, s>>>(fine.pitch, planef, n1, r,
-                                                                    fine.stride, pst, u, pin);
-  k_t3_boundary3d<<<dim3(kClasses - 1, tets, fine.nb), kThreads, 0, s>>>(
+  k_t3_interior3d<<<dim3(chunks, tets, fine.nb), interior_threads(r), 0, s>>>(
+      fine.pitch, planef, n1, r, fine.stride, pst, u, pin);
+  k_t3_boundary3d<<<dim3(kClasses - 1, tets, fine.nb), boundary_threads(r), 0, s>>>(
       fine.pitch, planef, n1, r, fine.stride, pst, u, pbd);
   k_t3_finalize3d<<<dim3(tets, fine.nb), 32, 0, s>>>(chunks, fine.h * fine.h * fine.h, pst,
                                                      (size_t)tets * 20, pin, pbd, map, t3);

@@ -304,7 +304,7 @@ void build_levels(fmg_eig_handle* h) {
         return h->bf16() ? reinterpret_cast<float*>(h->alloc<uint16_t>(s)) : h->alloc<float>(s);
       };
       l.ct.tab = h->alloc<float>((size_t)(dim == 2 ? 8 : 15) * (l.g.n + 1) * l.cap);
-      l.ct.cst = h->alloc<float>(4 * (size_t)l.cap);
+      l.ct.cst = h->alloc<float>(kCst * (size_t)l.cap);
       l.x32 = single();
       l.xt32 = single();
       l.f32 = single();
@@ -654,18 +654,28 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
   const fmg_eig_problem& p = h->prob;
   bool zero = true;
   for (int it = 0; it < p.nu_pre; ++it) {
-    jacobi32(l.g, l.ct, h->dparams, l.f32, l.x32, l.xt32, zero, s, bf);
+    // the profiled sweep is the first one that reads x (the zero-start sweep reads only f)
+    const bool prof = !zero;
+    if (prof) prof_begin(h, kProfJacobi, j, s);
+    jacobi32(l.g, l.ct, l.f32, l.x32, l.xt32, zero, s, bf);
+    if (prof) prof_end(h, kProfJacobi, j, s);
     std::swap(l.x32, l.xt32);
     zero = false;
   }
   if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * l.g.nb * mixed_elem_bytes(bf), s);
   Level& lc = h->L(j - 1);
+  prof_begin(h, kProfResidual, j, s);
   residual32(l.g, l.ct, l.f32, l.x32, l.r32, s, bf);
+  prof_end(h, kProfResidual, j, s);
+  prof_begin(h, kProfRestrict, j, s);
   restrict32(l.g, lc.g, l.r32, lc.f32, s, bf);
+  prof_end(h, kProfRestrict, j, s);
   enqueue_vcycle32(h, j - 1, s);
+  prof_begin(h, kProfProlong, j, s);
   prolong32_add(l.g, lc.g, lc.x32, l.x32, s, bf);
+  prof_end(h, kProfProlong, j, s);
   for (int it = 0; it < p.nu_post; ++it) {
-    jacobi32(l.g, l.ct, h->dparams, l.f32, l.x32, l.xt32, false, s, bf);
+    jacobi32(l.g, l.ct, l.f32, l.x32, l.xt32, false, s, bf);
     std::swap(l.x32, l.xt32);
   }
 }
@@ -839,7 +849,7 @@ std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 void time_mix(fmg_eig_handle* h, Level& l, int k, cudaStream_t s) {
   for (int q = 0; q < 4; ++q) {
     if (h->mixed() && k >= 2)
-      jacobi32(l.g, l.ct, h->dparams, l.f32, l.x32, l.xt32, false, s, h->bf16());
+      jacobi32(l.g, l.ct, l.f32, l.x32, l.xt32, false, s, h->bf16());
     else
       lv_jacobi(l, l.f, l.x, l.xt, false, s);
   }

@@ -141,12 +141,14 @@ void t3_map3d(int r, double* out);  // 20 * 15 * 20 doubles
 
 // ---- Mixed precision (mixed.cu) ------------------------------------------------------------
 // FP32 separable coefficient tables of one level for the single-precision V-cycle: tab =
-// the level's FP64 tables (2D: 8, 3D: 15 per instance, n + 1 entries each) in FP32, cst = the
-// 3D constants (C, axis, face, body) per instance.
+// the level's FP64 tables (2D: 8, 3D: 15 per instance, n + 1 entries each) in FP32; cst =
+// kCst floats per instance: the 3D constants (C, axis, face, body) and omega.
 struct CoefT {
   float* tab;
   float* cst;
 };
+constexpr int kCst = 8;
+constexpr int kCstOmega = 4;
 // Storage of the single-precision V-cycle arrays (the float* below): FP32, or bfloat16 when
 // `bf` is set (FMG_MIXED_BF16; arithmetic stays FP32).  Bytes per element:
 size_t mixed_elem_bytes(bool bf16_storage);
@@ -159,10 +161,9 @@ void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const dou
 // the FP32 tables of level g from its FP64 ones (after the level's operator setup)
 void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
                 const PotentialParams* pp, const CoefT& ct, cudaStream_t s);
-// damped Jacobi sweep / residual with coefficients rebuilt from the FP32 tables (omega from
-// the parameters)
-void jacobi32(const Grid& g, const CoefT& ct, const PotentialParams* pp, const float* f,
-              const float* x, float* xo, bool zero, cudaStream_t s, bool bf = false);
+// damped Jacobi sweep / residual with coefficients rebuilt from the FP32 tables
+void jacobi32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* xo,
+              bool zero, cudaStream_t s, bool bf = false);
 void residual32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* r,
                 cudaStream_t s, bool bf = false);
 void restrict32(const Grid& fine, const Grid& coarse, const float* rf, float* rc,

@@ -76,48 +76,71 @@ __global__ void k_residual_mixed2d(int n, int pitch, size_t st_, Coef2D c,
 }
 
 // ---- single-precision 2D stencil kernels -----------------------------------------------------
-// Coefficients of node (i, j) from the instance's tables (X = x tables C, E, N, NE; Y the y
-// ones, s = n + 1 entries each): c = X[i] + Y[j]; the W and S couplings are those of (i-1, j)
-// and (i, j-1).
-template <typename S>
-__device__ __forceinline__ float lop_t2(const float* __restrict__ X, const float* __restrict__ Y,
-                                        int s, int i, int j, float cc, const S* __restrict__ x,
-                                        size_t k, int pitch) {
-  float v = cc * ld(x, k);
-  v = fmaf(X[s + i] + Y[s + j], ld(x, k + 1), v);
-  v = fmaf(X[s + i - 1] + Y[s + j], ld(x, k - 1), v);
-  v = fmaf(X[2 * s + i] + Y[2 * s + j], ld(x, k + pitch), v);
-  v = fmaf(X[2 * s + i] + Y[2 * s + j - 1], ld(x, k - pitch), v);
-  v = fmaf(X[3 * s + i] + Y[3 * s + j], ld(x, k + pitch + 1), v);
-  v = fmaf(X[3 * s + i - 1] + Y[3 * s + j - 1], ld(x, k - pitch - 1), v);
-  return v;
-}
+// Sweep modes: residual r = f - L x; damped Jacobi x' = x + omega D^-1 (f - L x); the same
+// from x = 0 (x' = omega D^-1 f, x not read).
+enum SweepMode { kResidual = 0, kJacobi = 1, kJacobiZero = 2 };
+constexpr int kRows2 = 4;  // rows per thread: four f and six x rows in flight per thread
 
-#define TABLES_2D                                       \
-  const int s = n + 1;                                  \
-  const float* X = tab + (size_t)ib * 8 * s;            \
-  const float* Y = X + 4 * s;                           \
-  const float cc = X[i] + Y[j];
-
-// damped Jacobi sweep (x = 0 on entry when zero)
-template <typename S>
-__global__ void k_jacobi32_2d(int n, int pitch, size_t st_, const float* __restrict__ tab,
-                              const PotentialParams* __restrict__ pp, const S* __restrict__ f,
-                              const S* __restrict__ x, S* __restrict__ xo, int zero) {
-  INTERIOR_2D
-  TABLES_2D
-  const float dinv = (float)pp[ib].omega / cc;
-  if (zero) st(xo, k, dinv * ld(f, k));
-  else st(xo, k, fmaf(dinv, ld(f, k) - lop_t2(X, Y, s, i, j, cc, x, k, pitch), ld(x, k)));
-}
-
-template <typename S>
-__global__ void k_residual32_2d(int n, int pitch, size_t st_, const float* __restrict__ tab,
-                                const S* __restrict__ f, const S* __restrict__ x,
-                                S* __restrict__ r) {
-  INTERIOR_2D
-  TABLES_2D
-  st(r, k, ld(f, k) - lop_t2(X, Y, s, i, j, cc, x, k, pitch));
+// A thread takes column i and rows j0 .. j0 + kRows2 - 1 of instance ib = blockIdx.z.  The
+// coefficients of node (i, j) come from the instance's tables (X = x tables C, E, N, NE, Y the
+// y ones, s = n + 1 entries each): c = X[i] + Y[j]; the W and S couplings are those of
+// (i - 1, j) and (i, j - 1).  All loads of the thread are issued before the first result is
+// formed; rows past n - 1 are clamped (loaded, never stored).
+template <typename S, int MODE>
+__global__ void k_sweep32_2d(int n, int pitch, size_t st_, const float* __restrict__ tab,
+                             const float* __restrict__ cst, const S* __restrict__ f,
+                             const S* __restrict__ x, S* __restrict__ y) {
+  const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = 1 + (blockIdx.y * blockDim.y + threadIdx.y) * kRows2;
+  if (i >= n || j0 >= n) return;
+  const int ib = blockIdx.z;
+  const int s = n + 1;
+  const float* X = tab + (size_t)ib * 8 * s;
+  const float* Y = X + 4 * s;
+  const size_t base = (size_t)ib * st_;
+  f += base;
+  x += base;
+  y += base;
+  float fv[kRows2];
+#pragma unroll
+  for (int q = 0; q < kRows2; ++q) fv[q] = ld(f, at(i, min(j0 + q, n - 1), pitch));
+  float xv[kRows2 + 2][3];  // rows j0 - 1 .. j0 + kRows2, columns i - 1 .. i + 1
+  if (MODE != kJacobiZero) {
+#pragma unroll
+    for (int q = 0; q < kRows2 + 2; ++q) {
+      const size_t k = at(i, min(j0 - 1 + q, n), pitch);
+      xv[q][0] = ld(x, k - 1);
+      xv[q][1] = ld(x, k);
+      xv[q][2] = ld(x, k + 1);
+    }
+  }
+  const float xc = X[i], xe = X[s + i], xw = X[s + i - 1], xn = X[2 * s + i];
+  const float xne = X[3 * s + i], xsw = X[3 * s + i - 1];
+  const float w = MODE == kResidual ? 0.0f : cst[kCst * ib + kCstOmega];
+#pragma unroll
+  for (int q = 0; q < kRows2; ++q) {
+    const int j = j0 + q;
+    if (j < n) {
+      const float cc = xc + Y[j];
+      float out;
+      if (MODE == kJacobiZero) {
+        out = __fdividef(w, cc) * fv[q];
+      } else {
+        const float* r0 = xv[q];      // row j - 1
+        const float* r1 = xv[q + 1];  // row j
+        const float* r2 = xv[q + 2];  // row j + 1
+        float v = cc * r1[1];
+        v = fmaf(xe + Y[s + j], r1[2], v);
+        v = fmaf(xw + Y[s + j], r1[0], v);
+        v = fmaf(xn + Y[2 * s + j], r2[1], v);
+        v = fmaf(xn + Y[2 * s + j - 1], r0[1], v);
+        v = fmaf(xne + Y[3 * s + j], r2[2], v);
+        v = fmaf(xsw + Y[3 * s + j - 1], r0[0], v);
+        out = MODE == kResidual ? fv[q] - v : fmaf(__fdividef(w, cc), fv[q] - v, r1[1]);
+      }
+      st(y, at(i, j, pitch), out);
+    }
+  }
 }
 
 template <typename S>
@@ -177,93 +200,97 @@ __global__ void k_residual_mixed3d(int n, int pitch, size_t st_, Coef3D c,
   st(r, k, (float)(f[k] - v));
 }
 
-// Coefficients of a 3D node from the instance's tables T(ax, q)[c] = tab[(ax 5 + q) s + c]
+// Coefficients of a 3D node p from the instance's tables T(ax, q)[c] = tab[(ax 5 + q) s + c]
 // (s = n + 1) and constants cst = (C, axis, face, body), as in grid3d.cu:
 //   C = cst0 + T(x,0) + T(y,0) + T(z,0);  axis d: cst1 + T(d,1) + sum_{ax != d} T(ax,2);
 //   face with third axis o: cst2 + T(o,4) + sum_{ax != o} T(ax,3);  body: cst3 + sum T(ax,1).
-// The coupling to p - d is the one of p - d to p.
-template <typename S>
-__device__ __forceinline__ float lop_t3(const float* __restrict__ T, int s, const float* cst,
-                                        const int co[3], float& cc, const S* __restrict__ x,
-                                        size_t k, int pitch, long plane) {
-  float tv[3][5][2];  // table q of axis ax at co[ax] (0) and co[ax] - 1 (1)
+// The coupling to p - o_d is the one of p - o_d to p.  q_of(d, ax) is the table a direction
+// takes on an axis.
+__device__ __forceinline__ constexpr int q_of(int d, int ax) {
+  return d < 3 ? (ax == d ? 1 : 2) : (d < 6 ? (ax == 5 - d ? 4 : 3) : 1);
+}
+constexpr int kPlanes3 = 4;  // planes per thread
+
+// A thread takes (i, j) and planes l0 .. l0 + kPlanes3 - 1 of instance ib, blockIdx.z =
+// ib * chunks + (l0 - 1) / kPlanes3.  The x and y parts of its 15 coefficients (the centre and
+// both ends of the 7 directions) are summed once; each plane adds its z-table entries.
+template <typename S, int MODE>
+__global__ void k_sweep32_3d(int n, int pitch, size_t st_, int chunks,
+                             const float* __restrict__ tab, const float* __restrict__ cst,
+                             const S* __restrict__ f, const S* __restrict__ x,
+                             S* __restrict__ y) {
+  const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  const int ib = blockIdx.z / chunks;
+  const int l0 = 1 + ((int)blockIdx.z - ib * chunks) * kPlanes3;
+  if (i >= n || j >= n) return;
+  const int s = n + 1;
+  const float* T = tab + (size_t)ib * 15 * s;
+  const float* C = cst + kCst * ib;
+  const long plane = (long)(n + 1) * pitch;
+  const size_t base = (size_t)ib * st_;
+  const size_t col = (size_t)j * pitch + i;  // (i, j) in plane 0
+  f += base;
+  x += base;
+  y += base;
+  float fv[kPlanes3];
 #pragma unroll
-  for (int ax = 0; ax < 3; ++ax)
+  for (int q = 0; q < kPlanes3; ++q) fv[q] = ld(f, (size_t)min(l0 + q, n - 1) * plane + col);
+  // x and y parts: cxy[0] the centre, cxy[1 + 2 d + e] direction d at p (e = 0) or p - o_d
+  float cxy[15];
+  cxy[0] = C[0] + T[i] + T[5 * s + j];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      tv[ax][q][0] = T[(ax * 5 + q) * s + co[ax]];
-      tv[ax][q][1] = T[(ax * 5 + q) * s + co[ax] - 1];
+  for (int d = 0; d < 7; ++d)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int ci = i - (e ? kDir[d][0] : 0), cj = j - (e ? kDir[d][1] : 0);
+      cxy[1 + 2 * d + e] = C[d < 3 ? 1 : (d < 6 ? 2 : 3)] + T[q_of(d, 0) * s + ci] +
+                           T[(5 + q_of(d, 1)) * s + cj];
     }
-  cc = cst[0] + tv[0][0][0] + tv[1][0][0] + tv[2][0][0];
-  float v = cc * ld(x, k);
+  const float w = MODE == kResidual ? 0.0f : C[kCstOmega];
+  const float* Tz = T + 10 * s;
 #pragma unroll
-  for (int d = 0; d < 7; ++d) {
-    const long o = dir_off(d, pitch, plane);
-    float a[2];  // the coupling at p (0) and at p - d (1)
+  for (int q = 0; q < kPlanes3; ++q) {
+    const int l = min(l0 + q, n - 1);  // planes past n - 1: computed on n - 1, not stored
+    const size_t k = (size_t)l * plane + col;
+    const float cc = cxy[0] + Tz[l];
+    float out;
+    if (MODE == kJacobiZero) {
+      out = __fdividef(w, cc) * fv[q];
+    } else {
+      float v = cc * ld(x, k);
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      float c;
-      const int s0 = side ? kDir[d][0] : 0, s1 = side ? kDir[d][1] : 0, s2 = side ? kDir[d][2] : 0;
-      if (d < 3) {
-        c = cst[1] + tv[0][d == 0 ? 1 : 2][s0] + tv[1][d == 1 ? 1 : 2][s1] + tv[2][d == 2 ? 1 : 2][s2];
-      } else if (d < 6) {
-        const int oth = 5 - d;  // XY -> z, XZ -> y, YZ -> x
-        c = cst[2] + tv[0][oth == 0 ? 4 : 3][s0] + tv[1][oth == 1 ? 4 : 3][s1] +
-            tv[2][oth == 2 ? 4 : 3][s2];
-      } else {
-        c = cst[3] + tv[0][1][s0] + tv[1][1][s1] + tv[2][1][s2];
+      for (int d = 0; d < 7; ++d) {
+        const long o = dir_off(d, pitch, plane);
+        const float a0 = cxy[1 + 2 * d] + Tz[q_of(d, 2) * s + l];
+        const float a1 = cxy[2 + 2 * d] + Tz[q_of(d, 2) * s + l - kDir[d][2]];
+        v = fmaf(a0, ld(x, k + o), v);
+        v = fmaf(a1, ld(x, k - o), v);
       }
-      a[side] = c;
+      out = MODE == kResidual ? fv[q] - v : fmaf(__fdividef(w, cc), fv[q] - v, ld(x, k));
     }
-    v = fmaf(a[0], ld(x, k + o), v);
-    v = fmaf(a[1], ld(x, k - o), v);
+    if (l0 + q < n) st(y, k, out);
   }
-  return v;
 }
 
-#define TABLES_3D                                        \
-  const int s = n + 1;                                   \
-  const float* T = tab + (size_t)ib * 15 * s;            \
-  const float* C = cst + 4 * ib;                         \
-  const int co[3] = {i, j, l};
-
-template <typename S>
-__global__ void k_jacobi32_3d(int n, int pitch, size_t st_, const float* __restrict__ tab,
-                              const float* __restrict__ cst, const PotentialParams* __restrict__ pp,
-                              const S* __restrict__ f, const S* __restrict__ x, S* __restrict__ xo,
-                              int zero) {
-  INTERIOR_3D
-  TABLES_3D
-  float cc;
-  const float lx = lop_t3(T, s, C, co, cc, x, k, pitch, plane);
-  const float dinv = (float)pp[ib].omega / cc;
-  if (zero) st(xo, k, dinv * ld(f, k));
-  else st(xo, k, fmaf(dinv, ld(f, k) - lx, ld(x, k)));
-}
-
-template <typename S>
-__global__ void k_residual32_3d(int n, int pitch, size_t st_, const float* __restrict__ tab,
-                                const float* __restrict__ cst, const S* __restrict__ f,
-                                const S* __restrict__ x, S* __restrict__ r) {
-  INTERIOR_3D
-  TABLES_3D
-  float cc;
-  st(r, k, ld(f, k) - lop_t3(T, s, C, co, cc, x, k, pitch, plane));
-}
-
-// constants of the 3D coefficient tables per instance (grid3d.cu's k_coef3d): C, axis, face,
-// body; wl = 0 drops W (paper-literal form)
-__global__ void k_consts3d(int nb, double h, const PotentialParams* __restrict__ pp,
-                           float* __restrict__ cst) {
+// per-instance constants of the single-precision sweeps: omega and, in 3D, the constant parts
+// of the coefficients (grid3d.cu's k_coef3d): C, axis, face, body; wl = 0 drops W (the
+// paper-literal form)
+__global__ void k_consts(int dim, int nb, double h, const PotentialParams* __restrict__ pp,
+                         float* __restrict__ cst) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const PotentialParams p = pp[b];
-  const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
-  const double h3w = wl * h * h * h * p.w0;
-  cst[4 * b + 0] = (float)(6.0 * h + 0.4 * h3w);
-  cst[4 * b + 1] = (float)(-h + h3w * (1.0 / 20.0));
-  cst[4 * b + 2] = (float)(h3w * (1.0 / 30.0));
-  cst[4 * b + 3] = (float)(h3w * (1.0 / 20.0));
+  float* c = cst + kCst * b;
+  c[kCstOmega] = (float)p.omega;
+  if (dim == 3) {
+    const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
+    const double h3w = wl * h * h * h * p.w0;
+    c[0] = (float)(6.0 * h + 0.4 * h3w);
+    c[1] = (float)(-h + h3w * (1.0 / 20.0));
+    c[2] = (float)(h3w * (1.0 / 30.0));
+    c[3] = (float)(h3w * (1.0 / 20.0));
+  }
 }
 
 template <typename S>
@@ -337,26 +364,25 @@ unsigned blocks_for(size_t n) {
   return (unsigned)(b < 152 * 32 ? b : 152 * 32);
 }
 
-template <typename S>
-void jacobi_t(const Grid& g, const CoefT& ct, const PotentialParams* pp, const float* f,
-              const float* x, float* xo, bool zero, cudaStream_t s) {
-  if (g.dim == 2)
-    k_jacobi32_2d<S><<<grid2(g, g.n - 1, g.n - 1), blk(g), 0, s>>>(
-        g.n, g.pitch, g.stride, ct.tab, pp, sp<S>(f), sp<S>(x), sp<S>(xo), zero ? 1 : 0);
-  else
-    k_jacobi32_3d<S><<<grid3(g, g.n - 1, g.n - 1, g.n - 1), blk(g), 0, s>>>(
-        g.n, g.pitch, g.stride, ct.tab, ct.cst, pp, sp<S>(f), sp<S>(x), sp<S>(xo), zero ? 1 : 0);
+template <typename S, int MODE>
+void sweep_t(const Grid& g, const CoefT& ct, const float* f, const float* x, float* y,
+             cudaStream_t s) {
+  const int m = g.n - 1;
+  if (g.dim == 2) {
+    k_sweep32_2d<S, MODE><<<grid2(g, m, (m + kRows2 - 1) / kRows2), blk(g), 0, s>>>(
+        g.n, g.pitch, g.stride, ct.tab, ct.cst, sp<S>(f), sp<S>(x), sp<S>(y));
+  } else {
+    const int chunks = (m + kPlanes3 - 1) / kPlanes3;
+    k_sweep32_3d<S, MODE><<<grid3(g, m, m, chunks), blk(g), 0, s>>>(
+        g.n, g.pitch, g.stride, chunks, ct.tab, ct.cst, sp<S>(f), sp<S>(x), sp<S>(y));
+  }
 }
 
 template <typename S>
-void residual_t(const Grid& g, const CoefT& ct, const float* f, const float* x, float* r,
-                cudaStream_t s) {
-  if (g.dim == 2)
-    k_residual32_2d<S><<<grid2(g, g.n - 1, g.n - 1), blk(g), 0, s>>>(
-        g.n, g.pitch, g.stride, ct.tab, sp<S>(f), sp<S>(x), sp<S>(r));
-  else
-    k_residual32_3d<S><<<grid3(g, g.n - 1, g.n - 1, g.n - 1), blk(g), 0, s>>>(
-        g.n, g.pitch, g.stride, ct.tab, ct.cst, sp<S>(f), sp<S>(x), sp<S>(r));
+void jacobi_t(const Grid& g, const CoefT& ct, const float* f, const float* x, float* xo,
+              bool zero, cudaStream_t s) {
+  if (zero) sweep_t<S, kJacobiZero>(g, ct, f, x, xo, s);
+  else sweep_t<S, kJacobi>(g, ct, f, x, xo, s);
 }
 
 template <typename S>
@@ -412,19 +438,19 @@ void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
                 const PotentialParams* pp, const CoefT& ct, cudaStream_t s) {
   const size_t n = (size_t)(g.dim == 2 ? 8 : 15) * (g.n + 1) * g.nb;
   k_to_s<float><<<blocks_for(n), 256, 0, s>>>(n, g.dim == 2 ? c2.tab : c3.tab, ct.tab);
-  if (g.dim == 3) k_consts3d<<<(g.nb + 127) / 128, 128, 0, s>>>(g.nb, g.h, pp, ct.cst);
+  k_consts<<<(g.nb + 127) / 128, 128, 0, s>>>(g.dim, g.nb, g.h, pp, ct.cst);
 }
 
-void jacobi32(const Grid& g, const CoefT& ct, const PotentialParams* pp, const float* f,
-              const float* x, float* xo, bool zero, cudaStream_t s, bool bf) {
-  if (bf) jacobi_t<bf16>(g, ct, pp, f, x, xo, zero, s);
-  else jacobi_t<float>(g, ct, pp, f, x, xo, zero, s);
+void jacobi32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* xo,
+              bool zero, cudaStream_t s, bool bf) {
+  if (bf) jacobi_t<bf16>(g, ct, f, x, xo, zero, s);
+  else jacobi_t<float>(g, ct, f, x, xo, zero, s);
 }
 
 void residual32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* r,
                 cudaStream_t s, bool bf) {
-  if (bf) residual_t<bf16>(g, ct, f, x, r, s);
-  else residual_t<float>(g, ct, f, x, r, s);
+  if (bf) sweep_t<bf16, kResidual>(g, ct, f, x, r, s);
+  else sweep_t<float, kResidual>(g, ct, f, x, r, s);
 }
 
 void restrict32(const Grid& fine, const Grid& coarse, const float* rf, float* rc,
