@@ -18,6 +18,7 @@
 // T3 follows from monomial sums of u~ per class: 4 FP64 FMAs per interior node.
 #include "fmg_internal.h"
 #include "reduce_dev.cuh"
+#include "dfloat.cuh"
 
 namespace fmg {
 namespace {
@@ -31,52 +32,55 @@ __device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j
 //   int u^2 lambda_p lambda_q = |K|/180 [3u_p^2 + 3u_q^2 + u_r^2 + 4u_p u_q + 2u_p u_r + 2u_q u_r]
 // s60, s90, s180 = |K| / 60, / 90, / 180 (computed on the host: an FP64 division per node
 // would cost as much as a quarter of the kernel's arithmetic)
+// T is the arithmetic type and U the source of u: FP64 (double, const double*) or, in the
+// mixed-precision modes, double-float from the split u (dfloat, SplitVec).
+template <typename T, typename U>
 __global__ void k_nload_density2d(int n, int pitch, size_t st, double s60, double s90,
-                                  double s180, const double* __restrict__ u, double* __restrict__ nl,
+                                  double s180, U u, double* __restrict__ nl,
                                   double* __restrict__ bC, double* __restrict__ bE,
                                   double* __restrict__ bN, double* __restrict__ bNE) {
   const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
   const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
   const size_t k = blockIdx.z * st + at(i, j, pitch);
-  const double up = u[k];
-  const double nE = u[k + 1], nNE = u[k + pitch + 1], nN = u[k + pitch];
-  const double nW = u[k - 1], nSW = u[k - pitch - 1], nS = u[k - pitch];
-  const double s1 = ((nE + nNE) + (nN + nW)) + (nSW + nS);
-  const double qE = nE * nE, qNE = nNE * nNE, qN = nN * nN, qW = nW * nW, qSW = nSW * nSW,
-               qS = nS * nS;
-  const double s2 = ((qE + qNE) + (qN + qW)) + (qSW + qS);
-  double s3 = qE * nE;
+  const T up = get<T>(u, k);
+  const T nE = get<T>(u, k + 1), nNE = get<T>(u, k + pitch + 1), nN = get<T>(u, k + pitch);
+  const T nW = get<T>(u, k - 1), nSW = get<T>(u, k - pitch - 1), nS = get<T>(u, k - pitch);
+  const T s1 = ((nE + nNE) + (nN + nW)) + (nSW + nS);
+  const T qE = nE * nE, qNE = nNE * nNE, qN = nN * nN, qW = nW * nW, qSW = nSW * nSW,
+          qS = nS * nS;
+  const T s2 = ((qE + qNE) + (qN + qW)) + (qSW + qS);
+  T s3 = qE * nE;
   s3 = fma(qNE, nNE, s3);
   s3 = fma(qN, nN, s3);
   s3 = fma(qW, nW, s3);
   s3 = fma(qSW, nSW, s3);
   s3 = fma(qS, nS, s3);
-  const double p0 = nE * nNE, p1 = nNE * nN, p2 = nN * nW, p3 = nW * nSW, p4 = nSW * nS,
-               p5 = nS * nE;
-  const double pp = ((p0 + p1) + (p2 + p3)) + (p4 + p5);
-  double qq = p0 * (nE + nNE);
+  const T p0 = nE * nNE, p1 = nNE * nN, p2 = nN * nW, p3 = nW * nSW, p4 = nSW * nS,
+          p5 = nS * nE;
+  const T pp = ((p0 + p1) + (p2 + p3)) + (p4 + p5);
+  T qq = p0 * (nE + nNE);
   qq = fma(p1, nNE + nN, qq);
   qq = fma(p2, nN + nW, qq);
   qq = fma(p3, nW + nSW, qq);
   qq = fma(p4, nSW + nS, qq);
   qq = fma(p5, nS + nE, qq);
-  const double u2 = up * up;
-  double v = 24.0 * u2 * up;
-  v = fma(6.0 * u2, s1, v);
-  v = fma(2.0 * up, fma(2.0, s2, pp), v);
-  v = fma(2.0, s3, v);
-  nl[k] = s60 * (v + qq);
+  const T u2 = up * up;
+  T v = T(24) * u2 * up;
+  v = fma(T(6) * u2, s1, v);
+  v = fma(T(2) * up, fma(T(2), s2, pp), v);
+  v = fma(T(2), s3, v);
+  nl[k] = s60 * out_of(v + qq);
   // diagonal: sum over the six triangles
-  bC[k] = s90 * fma(36.0, u2, fma(2.0, s2, fma(6.0 * up, s1, pp)));
+  bC[k] = s90 * out_of(fma(T(36), u2, fma(T(2), s2, fma(T(6) * up, s1, pp))));
   // edge p-q shared by the triangles closed by r1 and r2
-  const double u26 = 6.0 * u2;
-  bE[k] = s180 *
-          fma(6.0, qE, u26 + fma(8.0 * up, nE, fma(2.0 * (up + nE), nNE + nS, qNE + qS)));
-  bN[k] = s180 *
-          fma(6.0, qN, u26 + fma(8.0 * up, nN, fma(2.0 * (up + nN), nNE + nW, qNE + qW)));
-  bNE[k] = s180 *
-           fma(6.0, qNE, u26 + fma(8.0 * up, nNE, fma(2.0 * (up + nNE), nE + nN, qE + qN)));
+  const T u26 = T(6) * u2;
+  bE[k] = s180 * out_of(fma(T(6), qE,
+                            u26 + fma(T(8) * up, nE, fma(T(2) * (up + nE), nNE + nS, qNE + qS))));
+  bN[k] = s180 * out_of(fma(T(6), qN,
+                            u26 + fma(T(8) * up, nN, fma(T(2) * (up + nN), nNE + nW, qNE + qW))));
+  bNE[k] = s180 * out_of(fma(T(6), qNE,
+                             u26 + fma(T(8) * up, nNE, fma(T(2) * (up + nNE), nE + nN, qE + qN))));
 }
 
 // Galerkin coarsening of a 7-point stencil: Bc(a,b) = sum_{v,w} P_va P_wb B(v,w).  The
@@ -328,7 +332,15 @@ dim3 grid_of(const Grid& g, int cx, int cy) {
 
 void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D& b,
                      cudaStream_t s) {
-  k_nload_density2d<<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
+  k_nload_density2d<double, const double*><<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0,
+                                              s>>>(
+      g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 180.0, g.h * g.h / 360.0, u, nl,
+      b.C, b.E, b.N, b.NE);
+}
+
+void nload_density2d_df(const Grid& g, SplitVec u, double* nl, const Density2D& b,
+                        cudaStream_t s) {
+  k_nload_density2d<dfloat, SplitVec><<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
       g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 180.0, g.h * g.h / 360.0, u, nl,
       b.C, b.E, b.N, b.NE);
 }

@@ -30,6 +30,8 @@ struct Level {
   // mixed precision: FP32 coefficient tables and single-precision V-cycle vectors
   CoefT ct{};
   float *x32 = nullptr, *xt32 = nullptr, *f32 = nullptr, *r32 = nullptr;
+  // mixed precision: double-float split (hi + lo) of the vector the nonlinear kernels read
+  float *uhi = nullptr, *ulo = nullptr;
   double* pw = nullptr;   // (x / r)^m table for the 2D T3 sums (levels >= 2)
   double* t3map = nullptr;  // class sums -> T3 map of this level (levels >= 2)
 };

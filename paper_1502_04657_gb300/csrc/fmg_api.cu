@@ -41,7 +41,7 @@ Level view(const Level& l, int first, int count) {
   adv(v.c3.dinv);
   adv(v.x); adv(v.xt); adv(v.f); adv(v.r); adv(v.u); adv(v.y); adv(v.z);
   adv(v.b.C); adv(v.b.E); adv(v.b.N); adv(v.b.NE);
-  adv(v.x32); adv(v.xt32); adv(v.f32); adv(v.r32);
+  adv(v.x32); adv(v.xt32); adv(v.f32); adv(v.r32); adv(v.uhi); adv(v.ulo);
   v.c.tab = v.c3.tab = v.cw.tab = v.cw3.tab = nullptr;  // per-instance tables are not sliced
   v.ct = CoefT{};
   v.g.nb = count;
@@ -114,6 +114,23 @@ void lv_rhs_f32(Level& l, const double* lam, const PotentialParams* p, const dou
 void lv_nload_density(Level& l, const double* u, double* nl, cudaStream_t s) {
   if (l.g.dim == 2) nload_density2d(l.g, u, nl, l.b, s);
   else nload_density3d(l.g, u, nl, l.b3, s);
+}
+// Mixed-precision modes: the nonlinear kernels compute in double-float arithmetic from the
+// split of u into l.uhi + l.ulo (written here, on the same stream, just before).
+SplitVec lv_split(Level& l, const double* u, cudaStream_t s) {
+  split_df(u, l.uhi, l.ulo, l.g.stride * l.g.nb, s);
+  return SplitVec{l.uhi, l.ulo};
+}
+void lv_rhs_df(Level& l, const double* lam, const PotentialParams* p, const double* u, double* f,
+               cudaStream_t s) {
+  const SplitVec v = lv_split(l, u, s);
+  if (l.g.dim == 2) rhs2d_df(l.g, lam, p, v, f, s);
+  else rhs3d_df(l.g, lam, p, v, f, s);
+}
+void lv_nload_density_df(Level& l, const double* u, double* nl, cudaStream_t s) {
+  const SplitVec v = lv_split(l, u, s);
+  if (l.g.dim == 2) nload_density2d_df(l.g, v, nl, l.b, s);
+  else nload_density3d_df(l.g, v, nl, l.b3, s);
 }
 void lv_coarsen_density(Level& fl, Level& cl, cudaStream_t s) {
   if (fl.g.dim == 2) coarsen_density2d(fl.g, cl.g, fl.b, cl.b, s);
@@ -309,6 +326,8 @@ void build_levels(fmg_eig_handle* h) {
       l.xt32 = single();
       l.f32 = single();
       l.r32 = single();
+      l.uhi = h->alloc<float>(s);
+      l.ulo = h->alloc<float>(s);
     }
     l.x = h->alloc<double>(s);
     l.xt = h->alloc<double>(s);
@@ -709,7 +728,8 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
   {
     const cudaStream_t b1 = h->side[0];
     prof_begin(h, kProfMoments, k, b1);
-    lv_nload_density(l, ut, l.r, b1);
+    if (h->mixed()) lv_nload_density_df(l, ut, l.r, b1);
+    else lv_nload_density(l, ut, l.r, b1);
     prof_end(h, kProfMoments, k, b1);
     dot(ut, l.r, st, h->partials2, h->t0, b1, nb, st);
     for (int j = k; j >= 2; --j) {
@@ -761,6 +781,8 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
   prof_begin(h, kProfRhs, k, s);
   if (h->mixed() && (h->prob.flags & FMG_FLAG_FP32_RHS))
     lv_rhs_f32(l, h->lam, h->dparams, l.u, l.f, s);
+  else if (h->mixed())
+    lv_rhs_df(l, h->lam, h->dparams, l.u, l.f, s);
   else lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
   if (h->literal()) lv_sub_wmass(l, l.u, l.f, s);
   prof_end(h, kProfRhs, k, s);
@@ -853,8 +875,13 @@ void time_mix(fmg_eig_handle* h, Level& l, int k, cudaStream_t s) {
     else
       lv_jacobi(l, l.f, l.x, l.xt, false, s);
   }
-  lv_nload_density(l, l.u, l.r, s);
-  lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
+  if (h->mixed()) {
+    lv_nload_density_df(l, l.u, l.r, s);
+    lv_rhs_df(l, h->lam, h->dparams, l.u, l.f, s);
+  } else {
+    lv_nload_density(l, l.u, l.r, s);
+    lv_rhs(l, h->lam, h->dparams, l.u, l.f, s);
+  }
 }
 
 int autotune(fmg_eig_handle* h) {

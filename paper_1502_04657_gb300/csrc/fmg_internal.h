@@ -31,6 +31,13 @@ struct Grid {
   }
 };
 
+// A vector split into double-float halves (hi + lo, FP32 each) for the nonlinear kernels of
+// the mixed-precision modes, which compute in double-float arithmetic on the FP32 pipes.
+struct SplitVec {
+  const float* hi;
+  const float* lo;
+};
+
 // Stencil coefficients of L = A + W on one 2D level (see grid2d.cu for the closed forms).
 struct Coef2D {
   double* cC;    // diagonal
@@ -79,6 +86,9 @@ void rhs2d(const Grid& g, const double* lam, const PotentialParams* p_dev, const
 // the same right-hand side evaluated in FP32 (mixed-precision iteration), stored in FP64
 void rhs2d_f32(const Grid& g, const double* lam, const PotentialParams* p_dev, const double* u,
                double* f, cudaStream_t s);
+// the same right-hand side in double-float arithmetic from the split u (mixed-precision modes)
+void rhs2d_df(const Grid& g, const double* lam, const PotentialParams* p_dev, SplitVec u,
+              double* f, cudaStream_t s);
 // Dense level-1 matrices L_1 and M_1 (n1-1)^2 square, row-major, interior numbering (one
 // pair per instance, back to back).
 void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s);
@@ -121,6 +131,11 @@ void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p_dev, c
                double* f, cudaStream_t s);
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s);
+// double-float versions from the split u (mixed-precision modes)
+void rhs3d_df(const Grid& g, const double* lam, const PotentialParams* p_dev, SplitVec u,
+              double* f, cudaStream_t s);
+void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& b,
+                        cudaStream_t s);
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,
                        const Density3D& bc, cudaStream_t s);
 void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaStream_t s);
@@ -149,6 +164,9 @@ struct CoefT {
 };
 constexpr int kCst = 8;
 constexpr int kCstOmega = 4;
+
+// hi[i] + lo[i] = u[i] to ~2^-48 relative, i < n
+void split_df(const double* u, float* hi, float* lo, size_t n, cudaStream_t s);
 // Storage of the single-precision V-cycle arrays (the float* below): FP32, or bfloat16 when
 // `bf` is set (FMG_MIXED_BF16; arithmetic stays FP32).  Bytes per element:
 size_t mixed_elem_bytes(bool bf16_storage);
@@ -199,6 +217,8 @@ struct Density2D {
 // nl = N(u) (int u^3 phi_p) and the density stencil of u on level g, in one pass.
 void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D& b,
                      cudaStream_t s);
+void nload_density2d_df(const Grid& g, SplitVec u, double* nl, const Density2D& b,
+                        cudaStream_t s);
 // Galerkin coarsening of the density stencil: bc = P^T bf P.
 void coarsen_density2d(const Grid& fine, const Grid& coarse, const Density2D& bf,
                        const Density2D& bc, cudaStream_t s);

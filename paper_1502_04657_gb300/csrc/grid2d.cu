@@ -16,6 +16,7 @@
 // FP64 instructions: the four coupling arrays and omega/D are materialised once per solve
 // (40 B/node extra traffic) and every sweep then costs 9 FP64 instructions per node.
 #include "fmg_internal.h"
+#include "dfloat.cuh"
 
 namespace fmg {
 namespace {
@@ -187,13 +188,13 @@ __global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
 // triangle with p), summing int_K u^3 lambda_p = |K|/60 sum_{|b|=3} u^b (b_p + 1) gives
 //   |K|/60 [24u^3 + 6u^2 S1 + 2u(2 S2 + P) + 2 S3 + Q],
 // S_q = sum n_k^q, P = sum n_k n_{k+1}, Q = sum n_k n_{k+1} (n_k + n_{k+1}), |K| = h^2/2.
-// T is the arithmetic type: double except in the FP32 auxiliary right-hand side of the
-// mixed-precision iteration (k_rhs2d_f32).
-template <typename T = double>
-__device__ __forceinline__ T nload_at(const double* __restrict__ u, size_t k, int pitch) {
-  const T up = (T)u[k];
-  const T n0 = (T)u[k + 1], n1 = (T)u[k + pitch + 1], n2 = (T)u[k + pitch];
-  const T n3 = (T)u[k - 1], n4 = (T)u[k - pitch - 1], n5 = (T)u[k - pitch];
+// T is the arithmetic type: double in FP64 mode, double-float (u read as a SplitVec) in the
+// mixed-precision modes, float in the FP32 auxiliary right-hand side (k_rhs2d_f32).
+template <typename T = double, typename U = const double*>
+__device__ __forceinline__ T nload_at(const U& u, size_t k, int pitch) {
+  const T up = get<T>(u, k);
+  const T n0 = get<T>(u, k + 1), n1 = get<T>(u, k + pitch + 1), n2 = get<T>(u, k + pitch);
+  const T n3 = get<T>(u, k - 1), n4 = get<T>(u, k - pitch - 1), n5 = get<T>(u, k - pitch);
   const T s1 = ((n0 + n1) + (n2 + n3)) + (n4 + n5);
   const T q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = n3 * n3, q4 = n4 * n4, q5 = n5 * n5;
   const T s2 = ((q0 + q1) + (q2 + q3)) + (q4 + q5);
@@ -234,6 +235,21 @@ __global__ void k_rhs2d(int n, int pitch, size_t st, double h2_12, double h2_120
                    (u[k + pitch + 1] + u[k - pitch - 1]);
   const double mu = h2_12 * fma(6.0, u[k], s);
   f[k] = fma(lam[ib], mu, -nscale * nload_at(u, k, pitch));
+}
+
+// The same right-hand side in double-float arithmetic from the split u (mixed-precision
+// modes): ~2^-47 relative rounding per operation on the FP32 pipes; the FP64 result combines
+// the two FP64-converted parts.
+__global__ void k_rhs2d_df(int n, int pitch, size_t st, double h2_12, double h2_120,
+                           const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                           SplitVec u, double* __restrict__ f) {
+  INTERIOR_2D
+  const dfloat s = ((get<dfloat>(u, k + 1) + get<dfloat>(u, k - 1)) +
+                    (get<dfloat>(u, k + pitch) + get<dfloat>(u, k - pitch))) +
+                   (get<dfloat>(u, k + pitch + 1) + get<dfloat>(u, k - pitch - 1));
+  const double mu = h2_12 * to_double(fma(dfloat(6), get<dfloat>(u, k), s));
+  const double nl = to_double(nload_at<dfloat>(u, k, pitch));
+  f[k] = fma(lam[ib], mu, -(pp[ib].zeta * h2_120) * nl);
 }
 
 // FP32 auxiliary right-hand side of the mixed-precision iteration (same closed forms in
@@ -370,6 +386,12 @@ void rhs2d_f32(const Grid& g, const double* lam, const PotentialParams* p, const
                double* f, cudaStream_t s) {
   k_rhs2d_f32<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
       g.n, g.pitch, g.stride, (float)(g.h * g.h / 12.0), (float)(g.h * g.h / 120.0), lam, p, u, f);
+}
+
+void rhs2d_df(const Grid& g, const double* lam, const PotentialParams* p, SplitVec u, double* f,
+              cudaStream_t s) {
+  k_rhs2d_df<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
+      g.n, g.pitch, g.stride, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
 }
 
 void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s) {

@@ -13,6 +13,7 @@
 // mass stencil is h^3 (2/5 at C, 1/20 along axes and the body diagonal, 1/30 along face
 // diagonals).  As in 2D, the 8 coupling arrays and omega/D are materialised once per solve.
 #include "fmg_internal.h"
+#include "dfloat.cuh"
 
 namespace fmg {
 namespace {
@@ -162,18 +163,17 @@ __global__ void k_residual3d(int n, int pitch, size_t st, Coef3D c, const double
   r[k] = f[k] - lop3(c, x, k, pitch, plane);
 }
 
-template <typename T = double>
-__device__ __forceinline__ T mass_at(const double* __restrict__ x, size_t k, int pitch,
-                                     long plane) {
+template <typename T = double, typename U = const double*>
+__device__ __forceinline__ T mass_at(const U& x, size_t k, int pitch, long plane) {
   T ax = 0, fd = 0;
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pitch, plane);
-    const T s = (T)x[k + o] + (T)x[k - o];
+    const T s = get<T>(x, k + o) + get<T>(x, k - o);
     if (d >= 3 && d < 6) fd += s;
     else ax += s;
   }
-  return fma(T(0.4), (T)x[k], fma(T(1.0 / 20.0), ax, fd * T(1.0 / 30.0)));
+  return fma(T(0.4), get<T>(x, k), fma(T(1.0 / 20.0), ax, fd * T(1.0 / 30.0)));
 }
 
 __global__ void k_mass3d(int n, int pitch, size_t st, double h3, const double* __restrict__ x,
@@ -288,19 +288,18 @@ __device__ constexpr Link kLink = make_link();
 static_assert(make_link().npair[0] == 6 && make_link().npair[3] == 4 && make_link().deg[13] == 6,
               "Kuhn star link");
 
-// T is the arithmetic type: double everywhere except the FP32 auxiliary right-hand side of
-// the mixed-precision iteration (k_rhs3d_f32).
-template <typename T, bool DENSITY>
-__device__ __forceinline__ void star3(const double* __restrict__ u, size_t k, int pitch,
-                                      long plane, T& nl, T* b) {
+// T is the arithmetic type: double in FP64 mode, double-float (u read as a SplitVec) in the
+// mixed-precision modes, float in the FP32 auxiliary right-hand side (k_rhs3d_f32).
+template <typename T, bool DENSITY, typename U = const double*>
+__device__ __forceinline__ void star3(const U& u, size_t k, int pitch, long plane, T& nl, T* b) {
   T nv[14], sq[14];
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pitch, plane);
-    nv[2 * d] = (T)u[k + o];
-    nv[2 * d + 1] = (T)u[k - o];
+    nv[2 * d] = get<T>(u, k + o);
+    nv[2 * d + 1] = get<T>(u, k - o);
   }
-  const T up = (T)u[k];
+  const T up = get<T>(u, k);
   const T u2 = up * up;
   // degree-weighted sums (deg 6 or 4)
   T s6 = 0, s4 = 0, q6 = 0, q4 = 0, c6 = 0, c4 = 0;
@@ -386,16 +385,29 @@ __global__ void k_rhs3d_f32(int n, int pitch, size_t st, float h3, float nscale,
   f[k] = (double)fmaf((float)lam[ib], mu, -((float)pp[ib].zeta * nscale) * nl);
 }
 
-__global__ void k_nload_density3d(int n, int pitch, size_t st, double s140, double s210,
-                                  double s420, const double* __restrict__ u,
-                                  double* __restrict__ nl, Density3D b) {
+// The same right-hand side in double-float arithmetic from the split u (mixed-precision
+// modes), combined in FP64.
+__global__ void k_rhs3d_df(int n, int pitch, size_t st, double h3, double nscale,
+                           const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                           SplitVec u, double* __restrict__ f) {
   INTERIOR_3D
-  double v, e[8];
-  star3<double, true>(u, k, pitch, plane, v, e);
-  nl[k] = s140 * v;
-  b.a[0][k] = s210 * e[0];
+  dfloat nl;
+  star3<dfloat, false>(u, k, pitch, plane, nl, nullptr);
+  const double mu = h3 * to_double(mass_at<dfloat>(u, k, pitch, plane));
+  f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * to_double(nl));
+}
+
+// T, U: FP64 (double, const double*) or double-float from the split u (dfloat, SplitVec)
+template <typename T, typename U>
+__global__ void k_nload_density3d(int n, int pitch, size_t st, double s140, double s210,
+                                  double s420, U u, double* __restrict__ nl, Density3D b) {
+  INTERIOR_3D
+  T v, e[8];
+  star3<T, true>(u, k, pitch, plane, v, e);
+  nl[k] = s140 * out_of(v);
+  b.a[0][k] = s210 * out_of(e[0]);
 #pragma unroll
-  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = s420 * e[1 + d];
+  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = s420 * out_of(e[1 + d]);
 }
 
 // Galerkin coarsening of the 15-point density stencil: Bc(a, b) = sum P_va P_wb B(v, w) over
@@ -597,8 +609,21 @@ void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p, const
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s) {
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload_density3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0,
-                                            vol / 420.0, u, nl, b);
+  k_nload_density3d<double, const double*><<<INTERIOR_LAUNCH(g)>>>(
+      g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0, vol / 420.0, u, nl, b);
+}
+
+void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& b,
+                        cudaStream_t s) {
+  const double vol = g.h * g.h * g.h / 6.0;
+  k_nload_density3d<dfloat, SplitVec><<<INTERIOR_LAUNCH(g)>>>(
+      g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0, vol / 420.0, u, nl, b);
+}
+
+void rhs3d_df(const Grid& g, const double* lam, const PotentialParams* p, SplitVec u, double* f,
+              cudaStream_t s) {
+  const double h3 = g.h * g.h * g.h;
+  k_rhs3d_df<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, h3, h3 / 6.0 / 140.0, lam, p, u, f);
 }
 
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,

@@ -45,6 +45,18 @@ __global__ void k_to_s(size_t n, const double* __restrict__ a, S* __restrict__ b
     st(b, i, (float)a[i]);
 }
 
+// double-float split of an FP64 vector (the nonlinear kernels of the mixed modes read it)
+__global__ void k_split_df(size_t n, const double* __restrict__ u, float* __restrict__ hi,
+                           float* __restrict__ lo) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = u[i];
+    const float h = __double2float_rn(v);
+    hi[i] = h;
+    lo[i] = __double2float_rn(v - (double)h);
+  }
+}
+
 template <typename S>
 __global__ void k_add_s(size_t n, const S* __restrict__ e, double* __restrict__ x) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -439,6 +451,10 @@ void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
   const size_t n = (size_t)(g.dim == 2 ? 8 : 15) * (g.n + 1) * g.nb;
   k_to_s<float><<<blocks_for(n), 256, 0, s>>>(n, g.dim == 2 ? c2.tab : c3.tab, ct.tab);
   k_consts<<<(g.nb + 127) / 128, 128, 0, s>>>(g.dim, g.nb, g.h, pp, ct.cst);
+}
+
+void split_df(const double* u, float* hi, float* lo, size_t n, cudaStream_t s) {
+  k_split_df<<<blocks_for(n), 256, 0, s>>>(n, u, hi, lo);
 }
 
 void jacobi32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* xo,
