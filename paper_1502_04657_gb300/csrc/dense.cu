@@ -17,10 +17,11 @@
 //     y1 = A'^{-1} r,  y2 = A'^{-1} M c,  dl = (Mc.y1)/(Mc.y2),  dc = -y1 + dl y2.
 // lambda is reported as c^T (K0 + zeta G(c)) c at the final c.
 //
-// G(c) is assembled per coarse simplex T from the exact quartic table q4 of the coarse
-// barycentrics and, on the augmented space (w = w_H + c_u u~), from the fine-pass integrals
-// (augment2d.cu): T3^T (per simplex), B1 = int u~^2 phi phi, t1 = int u~^3 phi, T0 = int u~^4:
-//   G_ab = sum_T [|T| sum w_c w_d q4_abcd + 2 c_u sum w_c T3_abc] + c_u^2 B1_ab
+// G(c) is assembled per coarse simplex T from the exact integrals of products of its
+// barycentrics (local_G) and, on the augmented space (w = w_H + c_u u~), from the fine-pass
+// integrals (augment2d.cu): T3^T (per simplex), B1 = int u~^2 phi phi, t1 = int u~^3 phi,
+// T0 = int u~^4:
+//   G_ab = sum_T [int_T w_H^2 mu_a mu_b + 2 c_u sum w_c T3_abc] + c_u^2 B1_ab
 //   G_au = sum_T sum w_c w_d T3_acd + 2 c_u (B1 c_H)_a + c_u^2 t1_a
 //   G_uu = c_H^T B1 c_H + 2 c_u t1.c_H + c_u^2 T0
 // with w_c the coarse coefficients at T's vertices (0 on the boundary).
@@ -42,7 +43,7 @@ constexpr int kMaxVert = 4;
 constexpr double kSwitch = 1e-2;  // relative residual below which Newton takes over
 
 struct Smem {
-  double *K0, *MM, *G, *A, *B1, *loc, *q4;
+  double *K0, *MM, *G, *A, *B1, *loc;
   double *c, *Mc, *Hc, *Gc, *r, *y1, *y2, *dinv, *red, *sv;
   int* sym3;  // nv^3 table of sorted-triple indices
   int *tri, *adj;  // shared copies of the simplex and adjacency tables
@@ -122,61 +123,68 @@ __device__ void apply_all(Smem& s) {
   symv<3>(X, s.c, Y, s.n, s.sv);
 }
 
+// Local contributions of each simplex T (one thread per simplex): the pair entries
+// int_T w^2 mu_a mu_b (+ 2 c_u sum_c w_c T3_abc) and, on the augmented space, the coupling
+// sum_cd w_c w_d T3_acd of vertex a with u~.  By the barycentric monomial rule
+// int_T mu^alpha = d! |T| alpha! / (|alpha| + d)!,
+//   int_T w^2 mu_a mu_b = |T| 2 d! / (d + 4)! h_2(w_1 .. w_nv, w_a, w_b)   (a != b),
+// and twice that for a = b, with h_2 the complete homogeneous symmetric polynomial of degree
+// 2 (the count of ways to share the exponent of w_a between the copies of w_a is exactly the
+// factor alpha_a + 1 the rule produces), so a simplex needs h_1 = sum w, h_2 and a few
+// products per pair.  The u~ coupling reuses the pair sums x3_ac = sum_d w_d T3_acd.
+template <int NV>
+__device__ void local_G(const DenseProblem& p, Smem& s, double cu) {
+  const int L = s.L;
+  for (int t = threadIdx.x; t < p.ntri; t += kThreads) {
+    double wv[NV], sq[NV];
+    double h1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int id = s.tri[t * NV + v];
+      wv[v] = id >= 0 ? s.c[id] : 0.0;
+      sq[v] = wv[v] * wv[v];
+      h1 += wv[v];
+      s2 += sq[v];
+    }
+    const double h2 = 0.5 * fma(h1, h1, s2);  // sum_{i <= j} w_i w_j
+    const double* t3 = s.t3 + (size_t)t * p.nt3;
+    double* lt = s.loc + (size_t)t * L * L;
+    double x3[NV][NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+      for (int b = a; b < NV; ++b) {
+        double v;
+        if (a == b) v = 2.0 * p.quart_off * fma(3.0, sq[a], fma(2.0 * wv[a], h1, h2));
+        else v = p.quart_off * (fma(wv[a] + wv[b], h1, h2) + fma(wv[a], wv[b], sq[a] + sq[b]));
+        if (p.aug) {
+          double x = 0.0;
+#pragma unroll
+          for (int c = 0; c < NV; ++c) x = fma(wv[c], t3[s.sym3[(a * NV + b) * NV + c]], x);
+          x3[a][b] = x;
+          x3[b][a] = x;
+          v = fma(2.0 * cu, x, v);
+        }
+        lt[a * L + b] = v;
+        lt[b * L + a] = v;
+      }
+    if (p.aug) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        double x = 0.0;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) x = fma(wv[c], x3[a][c], x);
+        lt[a * L + NV] = x;
+      }
+    }
+  }
+}
+
 __device__ void build_G(const DenseProblem& p, Smem& s) {
   const int nv = p.nvert, L = s.L, nh = s.nh, n = s.n;
   const double cu = p.aug ? s.c[nh] : 0.0;
-  const int npair = nv * (nv + 1) / 2;
-  // local contributions of each simplex: the pair entries (a <= b) ...
-  for (int w = threadIdx.x; w < p.ntri * npair; w += kThreads) {
-    const int t = w / npair;
-    int a = 0, b = w - t * npair;  // the e-th pair (a <= b)
-    while (b >= nv - a) {
-      b -= nv - a;
-      ++a;
-    }
-    b += a;
-    double wv[kMaxVert];
-    for (int v = 0; v < nv; ++v) {
-      const int id = s.tri[t * nv + v];
-      wv[v] = id >= 0 ? s.c[id] : 0.0;
-    }
-    double q = 0.0;
-    const double* q4 = s.q4 + (size_t)(a * nv + b) * nv * nv;
-    for (int c = 0; c < nv; ++c) {
-      double qc = 0.0;
-      for (int d = 0; d < nv; ++d) qc = fma(wv[d], q4[c * nv + d], qc);
-      q = fma(wv[c], qc, q);
-    }
-    double v = p.tri_vol * q;
-    if (p.aug) {
-      const double* t3 = s.t3 + (size_t)t * p.nt3;
-      double x3 = 0.0;
-      for (int c = 0; c < nv; ++c) x3 = fma(wv[c], t3[s.sym3[(a * nv + b) * nv + c]], x3);
-      v = fma(2.0 * cu, x3, v);
-    }
-    double* lt = s.loc + (size_t)t * L * L;
-    lt[a * L + b] = v;
-    lt[b * L + a] = v;
-  }
-  // ... and the coupling of each vertex with u~ (augmented space)
-  if (p.aug) {
-    for (int w = threadIdx.x; w < p.ntri * nv; w += kThreads) {
-      const int t = w / nv, a = w - t * nv;
-      double wv[kMaxVert];
-      for (int v = 0; v < nv; ++v) {
-        const int id = s.tri[t * nv + v];
-        wv[v] = id >= 0 ? s.c[id] : 0.0;
-      }
-      const double* t3 = s.t3 + (size_t)t * p.nt3;
-      double x3 = 0.0;
-      for (int c = 0; c < nv; ++c) {
-        double xc = 0.0;
-        for (int d = 0; d < nv; ++d) xc = fma(wv[d], t3[s.sym3[(a * nv + c) * nv + d]], xc);
-        x3 = fma(wv[c], xc, x3);
-      }
-      s.loc[(size_t)t * L * L + a * L + nv] = x3;
-    }
-  }
+  if (p.nvert == 3) local_G<3>(p, s, cu);
+  else local_G<4>(p, s, cu);
   __syncthreads();
   if (p.aug) {  // Hc <- B1 c_H (scratch; recomputed by apply_all afterwards)
     const double* X[1] = {s.B1};
@@ -327,7 +335,6 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   s.G = q; q += (size_t)n * n;
   s.A = q; q += (size_t)n * n;
   s.loc = q; q += (size_t)p.ntri * s.L * s.L;
-  s.q4 = q; q += nv * nv * nv * nv;
   s.c = q; q += n;
   s.Mc = q; q += n;
   s.Hc = q; q += n;
@@ -370,7 +377,6 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   }
   for (int e = threadIdx.x; e < p.ntri * nv; e += kThreads) s.tri[e] = p.tri[e];
   for (int e = threadIdx.x; e < nh * p.maxadj; e += kThreads) s.adj[e] = p.adj[e];
-  for (int e = threadIdx.x; e < nv * nv * nv * nv; e += kThreads) s.q4[e] = p.q4[e];
   for (int e = threadIdx.x; e < nv * nv * nv; e += kThreads) {
     int a = e / (nv * nv), b = (e / nv) % nv, c = e % nv;
     if (a > b) { const int t = a; a = b; b = t; }
@@ -541,8 +547,7 @@ size_t dense_smem_bytes(int n, int ntri, int nvert, int aug) {
   const int L = nvert + 1, nh = n - aug;
   const size_t nt3 = nvert == 3 ? 10 : 20;
   const size_t maxadj = nvert == 3 ? 6 : 24;
-  return sizeof(double) * ((size_t)4 * n * n + (size_t)ntri * L * L +
-                           (size_t)nvert * nvert * nvert * nvert + 8 * (size_t)n + 4 * kThreads +
+  return sizeof(double) * ((size_t)4 * n * n + (size_t)ntri * L * L + 8 * (size_t)n + 4 * kThreads +
                            nh + (aug ? (size_t)ntri * nt3 : 0) + ((size_t)ntri * nvert + 1) / 2 +
                            ((size_t)nh * maxadj + 1) / 2 + (aug ? (size_t)nh * nh : 0));
 }

@@ -85,7 +85,7 @@ struct fmg_eig_handle {
   // per-instance arrays (sorted order): L1, M1, L1inv nh*nh; c, cstart nh + 1; scalars 1
   // L1 = A + W on level 1 (the small nonlinear solves), L1A the operator whose inverse is the
   // coarsest V-cycle solve (the same array unless the form is paper-literal)
-  double *L1 = nullptr, *L1A = nullptr, *M1 = nullptr, *L1inv = nullptr, *q4 = nullptr;
+  double *L1 = nullptr, *L1A = nullptr, *M1 = nullptr, *L1inv = nullptr;
   int *tri = nullptr, *adj = nullptr;
   double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr,
          *partials = nullptr, *partials2 = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,

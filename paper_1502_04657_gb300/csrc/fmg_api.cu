@@ -367,7 +367,6 @@ void build_coarse(fmg_eig_handle* h) {
   const int nb = h->nb;
   const double H = h->prob.box_len / n1;
   std::vector<int> tri, adj;
-  std::vector<double> q4;
   if (dim == 2) {
     h->nh = m * m;
     h->nvert = 3;
@@ -422,26 +421,11 @@ void build_coarse(fmg_eig_handle* h) {
       const int a = tri[t * nv + v];
       if (a >= 0) adj[a * h->maxadj + fill[a]++] = (t << 3) | v;
     }
-  // q4[a][b][c][d] = int_T mu_a mu_b mu_c mu_d / |T| = d! alpha! / (4 + d)!
-  q4.resize(nv * nv * nv * nv);
-  for (int e = 0; e < nv * nv * nv * nv; ++e) {
-    int cnt[4] = {0, 0, 0, 0};
-    cnt[e % nv]++;
-    cnt[(e / nv) % nv]++;
-    cnt[(e / (nv * nv)) % nv]++;
-    cnt[e / (nv * nv * nv)]++;
-    double num = factorial(dim);
-    for (int q = 0; q < nv; ++q) num *= factorial(cnt[q]);
-    q4[e] = num / factorial(4 + dim);
-  }
   h->tri = h->alloc<int>(tri.size());
   h->adj = h->alloc<int>(adj.size());
-  h->q4 = h->alloc<double>(q4.size());
   if (!h->dry) cudaMemcpyAsync(h->tri, tri.data(), tri.size() * sizeof(int), cudaMemcpyHostToDevice,
                   h->stream);
   if (!h->dry) cudaMemcpyAsync(h->adj, adj.data(), adj.size() * sizeof(int), cudaMemcpyHostToDevice,
-                  h->stream);
-  if (!h->dry) cudaMemcpyAsync(h->q4, q4.data(), q4.size() * sizeof(double), cudaMemcpyHostToDevice,
                   h->stream);
   const size_t nn = (size_t)h->nh * h->nh;
   h->L1 = h->alloc<double>(nn * nb);
@@ -558,7 +542,7 @@ DenseProblem dense_base(fmg_eig_handle* h) {
   d.tri = h->tri;
   d.adj = h->adj;
   d.maxadj = h->maxadj;
-  d.q4 = h->q4;
+  d.quart_off = h->tri_vol * 2.0 * factorial(h->prob.dim) / factorial(h->prob.dim + 4);
   d.tri_vol = h->tri_vol;
   d.L1 = h->L1;
   d.M1 = h->M1;

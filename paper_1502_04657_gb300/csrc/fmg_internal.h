@@ -238,7 +238,7 @@ void gather_level1_2d(const Grid& g1, const double* gA_pad, const double* gM_pad
                       double* t1, double* B1, cudaStream_t s);
 
 // ---- Dense small solves (dense.cu) -------------------------------------------------------
-// A batch of problems shares the geometry (tri, adj, q4) and keeps the per-instance arrays
+// A batch of problems shares the geometry (tri, adj) and keeps the per-instance arrays
 // back to back: L1, M1, B1 nh*nh; gA, gM, t1 nh; t3 ntri*nt3; c_init, c_out nh + 1;
 // auu, buu, t0, lam_out, iters_out, status_out and params one each.
 struct DenseProblem {
@@ -250,8 +250,8 @@ struct DenseProblem {
   const int* tri;      // ntri * nvert coarse interior indices, -1 on the boundary
   const int* adj;      // nh * maxadj codes (simplex << 3 | local vertex), -1 terminated
   int maxadj;
-  const double* q4;    // nvert^4 table: int_T mu_a mu_b mu_c mu_d / |T|
   double tri_vol;      // |T|
+  double quart_off;    // |T| 2 d! / (d + 4)!, d = nvert - 1 (int_T w^2 mu_a mu_b / h_2)
   const double* L1;    // nh*nh, operator of level 1
   const double* M1;    // nh*nh, mass of level 1
   // augmented problem only:

@@ -47,12 +47,6 @@ cudaError_t scratch_on_current_device(double** out) {
   return cudaSuccess;
 }
 
-double factorial(int k) {
-  double r = 1.0;
-  for (int i = 2; i <= k; ++i) r *= i;
-  return r;
-}
-
 }  // namespace
 }  // namespace fmg
 
@@ -108,14 +102,12 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   int* it = status + 1;
   int* tri = reinterpret_cast<int*>(take((size_t)ntri * 3 / 2 + 1));
   int* adj = reinterpret_cast<int*>(take((size_t)nh * 6 / 2 + 1));
-  double* q4 = take(81);
   if (off > kScratchDoubles) return FMG_EINVAL;
 
   // host-side tables on the stack (no heap use), copied into the fixed array
   int tri_h[2 * kMaxCoarseCells * kMaxCoarseCells * 3];
   int adj_h[(kMaxCoarseCells - 1) * (kMaxCoarseCells - 1) * 6];
   int fill[(kMaxCoarseCells - 1) * (kMaxCoarseCells - 1)];
-  double q4_h[81];
   auto id = [&](int i, int j) { return (i < 1 || j < 1 || i >= n1 || j >= n1) ? -1 : (i - 1) + (j - 1) * m; };
   for (int J = 0; J < n1; ++J)
     for (int I = 0; I < n1; ++I) {
@@ -134,18 +126,6 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
       const int a = tri_h[t * 3 + v];
       if (a >= 0) adj_h[a * 6 + fill[a]++] = (t << 3) | v;
     }
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b)
-      for (int cc = 0; cc < 3; ++cc)
-        for (int d = 0; d < 3; ++d) {
-          int cnt[3] = {0, 0, 0};
-          cnt[a]++;
-          cnt[b]++;
-          cnt[cc]++;
-          cnt[d]++;
-          q4_h[((a * 3 + b) * 3 + cc) * 3 + d] =
-              2.0 * factorial(cnt[0]) * factorial(cnt[1]) * factorial(cnt[2]) / factorial(6);
-        }
   PotentialParams pp{};
   pp.w0 = prob->w_const;
   pp.wx = prob->w_quad[0];
@@ -163,8 +143,8 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   d.tri = tri;
   d.adj = adj;
   d.maxadj = 6;
-  d.q4 = q4;
   d.tri_vol = g.h * g.h / 2.0;
+  d.quart_off = d.tri_vol / 180.0;  // |T| 2 d! / (d + 4)! with d = 2
   d.L1 = L1;
   d.M1 = M1;
   d.params = reinterpret_cast<const PotentialParams*>(params);
@@ -181,7 +161,6 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   if (cudaMemsetAsync(base, 0, off * sizeof(double), s) != cudaSuccess ||
       cudaMemcpyAsync(tri, tri_h, sizeof(int) * ntri * 3, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(adj, adj_h, sizeof(int) * nh * 6, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(q4, q4_h, sizeof(q4_h), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(params, &pp, sizeof(pp), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       dense_prepare(dense_smem_bytes(nh, ntri, 3, 0)) != cudaSuccess) {
     cudaGetLastError();
