@@ -94,6 +94,14 @@ DOMINANT = {2: "jacobi", 3: "nload_density"}
 # and f and writes one vector, 3 x 4 bytes per node (3 x 2 with BF16 storage); the
 # coefficients are rebuilt from per-axis tables that stay in L1.
 MIXED_HBM_KERNELS = ("jacobi", "residual")
+# The mixed modes evaluate the cubic load + density stencil in double-float arithmetic on the
+# FP32 pipes: the kernel is bound by instruction issue (4 warp instructions per SM per clock).
+# Thread instructions per node (smsp__inst_executed.sum x 32 / nodes) and DRAM bytes per node
+# from one ncu capture of the finest launch (profiles/ncu_nonlinear_df_mixed.md).
+ISSUE_PER_CLK_SM = 4 * 32
+DF_INSTR_PER_NODE = {2: 618510721 * 32 / 16769025, 3: 2830436764 * 32 / 16581375}
+DF_TRAFFIC_PER_NODE = {2: (136027392 + 609443328) / 16769025,
+                       3: (169865472 + 1133905920) / 16581375}
 
 
 def hbm_peak() -> tuple[float, str]:
@@ -613,6 +621,15 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
         if mixed and name in MIXED_HBM_KERNELS:
             continue
         ms = m["profile"].get(name, -1.0)
+        if mixed and name == "nload_density" and ms and ms > 0:
+            ipeak = ISSUE_PER_CLK_SM * N_SM * sm_max * 1e6 / 1e12
+            ach = DF_INSTR_PER_NODE[m["dim"]] * nodes / (ms * 1e-3) / 1e12
+            roof[name] = {"bound": "alu", "achieved": ach, "peak": ipeak, "unit": "Tinst/s",
+                          "frac": ach / ipeak, "traffic": DF_TRAFFIC_PER_NODE[m["dim"]] * nodes,
+                          "launch_ms": ms, "arithmetic": "double-float on the FP32 pipes",
+                          "peak_source": ("instruction issue: 152 SMs x 4 schedulers x 32 lanes "
+                                          "x sm_max_mhz (derived from unit counts and clock)")}
+            continue
         if ms and ms > 0:
             ach = flops * nodes / (ms * 1e-3) / 1e12
             tpn = TRAFFIC_PER_NODE.get((m["dim"], name))
@@ -625,8 +642,9 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
         dom = "nload_density"
     main = dict(roof.get(dom, {}))
     main["kernel"] = dom
-    main["peak_source"] = ("FP64 (the kernel is FP64-ALU bound): 152 SMs x 2 DFMA/clk x sm_max_mhz, "
-                           "nominal 1.25 TFLOP/s; of fallback (no FP64 figure in the measured peaks)")
+    main.setdefault("peak_source", "FP64 (the kernel is FP64-ALU bound): 152 SMs x 2 DFMA/clk x "
+                    "sm_max_mhz, nominal 1.25 TFLOP/s; of fallback (no FP64 figure in the "
+                    "measured peaks)")
     return main, {k: v for k, v in roof.items() if k != dom}
 
 
