@@ -35,8 +35,8 @@ __device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j
 // T is the arithmetic type and U the source of u: FP64 (double, const double*) or, in the
 // mixed-precision modes, double-float from the split u (dfloat, SplitVec).
 template <typename T, typename U>
-__global__ void k_nload_density2d(int n, int pitch, size_t st, double s60, double s90,
-                                  double s180, U u, double* __restrict__ nl,
+__global__ void k_nload_density2d(int n, int pitch, size_t st, T s60, T s90, T s180, U u,
+                                  double* __restrict__ nl,
                                   double* __restrict__ bC, double* __restrict__ bE,
                                   double* __restrict__ bN, double* __restrict__ bNE) {
   const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -70,16 +70,16 @@ __global__ void k_nload_density2d(int n, int pitch, size_t st, double s60, doubl
   v = fma(T(6) * u2, s1, v);
   v = fma(T(2) * up, fma(T(2), s2, pp), v);
   v = fma(T(2), s3, v);
-  nl[k] = s60 * out_of(v + qq);
+  nl[k] = out_of(s60 * (v + qq));
   // diagonal: sum over the six triangles
-  bC[k] = s90 * out_of(fma(T(36), u2, fma(T(2), s2, fma(T(6) * up, s1, pp))));
+  bC[k] = out_of(s90 * fma(T(36), u2, fma(T(2), s2, fma(T(6) * up, s1, pp))));
   // edge p-q shared by the triangles closed by r1 and r2
   const T u26 = T(6) * u2;
-  bE[k] = s180 * out_of(fma(T(6), qE,
+  bE[k] = out_of(s180 * fma(T(6), qE,
                             u26 + fma(T(8) * up, nE, fma(T(2) * (up + nE), nNE + nS, qNE + qS))));
-  bN[k] = s180 * out_of(fma(T(6), qN,
+  bN[k] = out_of(s180 * fma(T(6), qN,
                             u26 + fma(T(8) * up, nN, fma(T(2) * (up + nN), nNE + nW, qNE + qW))));
-  bNE[k] = s180 * out_of(fma(T(6), qNE,
+  bNE[k] = out_of(s180 * fma(T(6), qNE,
                              u26 + fma(T(8) * up, nNE, fma(T(2) * (up + nNE), nE + nN, qE + qN))));
 }
 
@@ -341,8 +341,8 @@ void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D
 void nload_density2d_df(const Grid& g, SplitVec u, double* nl, const Density2D& b,
                         cudaStream_t s) {
   k_nload_density2d<dfloat, SplitVec><<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
-      g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 180.0, g.h * g.h / 360.0, u, nl,
-      b.C, b.E, b.N, b.NE);
+      g.n, g.pitch, g.stride, dfloat(g.h * g.h / 120.0), dfloat(g.h * g.h / 180.0),
+      dfloat(g.h * g.h / 360.0), u, nl, b.C, b.E, b.N, b.NE);
 }
 
 void coarsen_density2d(const Grid& fine, const Grid& coarse, const Density2D& bf,

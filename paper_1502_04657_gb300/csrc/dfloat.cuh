@@ -53,6 +53,8 @@ __device__ __forceinline__ dfloat operator+(dfloat x, dfloat y) {
 
 __device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) { return x = x + y; }
 
+__device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
+
 __device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
   const float p = __fmul_rn(x.hi, y.hi);
   float e = fmaf(x.hi, y.hi, -p);  // exact: x.hi y.hi = p + e

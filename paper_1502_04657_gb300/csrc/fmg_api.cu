@@ -321,6 +321,7 @@ void build_levels(fmg_eig_handle* h) {
         return h->bf16() ? reinterpret_cast<float*>(h->alloc<uint16_t>(s)) : h->alloc<float>(s);
       };
       l.ct.tab = h->alloc<float>((size_t)(dim == 2 ? 8 : 15) * (l.g.n + 1) * l.cap);
+      l.ct.tablo = h->alloc<float>((size_t)(dim == 2 ? 8 : 15) * (l.g.n + 1) * l.cap);
       l.ct.cst = h->alloc<float>(kCst * (size_t)l.cap);
       l.x32 = single();
       l.xt32 = single();
@@ -519,10 +520,17 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s, bool overlap = false) {
     const cudaStream_t s_saved = s;
     s = sk;
     prof_begin(h, kProfCoef, k, s);
-    lv_coef(l, h->dparams, s);
+    if (h->mixed() && l.g.dim == 3) {
+      // mixed precision, 3D: the split tables first, then the coefficients in double-float
+      coef1d_3d(l.g, h->dparams, l.c3, s);
+      tables_f32(l.g, l.c, l.c3, h->dparams, l.ct, s);
+      coef3d_df(l.g, l.ct, l.c3, s);
+    } else {
+      lv_coef(l, h->dparams, s);
+    }
     if (h->literal()) lv_coef(l, h->dparams_full, s, true);
     prof_end(h, kProfCoef, k, s);
-    if (h->mixed()) tables_f32(l.g, l.c, l.c3, h->dparams, l.ct, s);
+    if (h->mixed() && l.g.dim == 2) tables_f32(l.g, l.c, l.c3, h->dparams, l.ct, s);
     if (sk != s_saved) {
       cudaEventRecord(h->ev_level[k], sk);
       h->level_pending[k] = true;

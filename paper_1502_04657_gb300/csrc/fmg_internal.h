@@ -156,14 +156,19 @@ void t3_map3d(int r, double* out);  // 20 * 15 * 20 doubles
 
 // ---- Mixed precision (mixed.cu) ------------------------------------------------------------
 // FP32 separable coefficient tables of one level for the single-precision V-cycle: tab =
-// the level's FP64 tables (2D: 8, 3D: 15 per instance, n + 1 entries each) in FP32; cst =
-// kCst floats per instance: the 3D constants (C, axis, face, body) and omega.
+// the level's FP64 tables (2D: 8, 3D: 15 per instance, n + 1 entries each) rounded to FP32
+// and tablo their remainders (tab + tablo is their double-float split); cst = kCst floats
+// per instance: the 3D constants (C, axis, face, body) at 0..3 with their remainders at
+// kCstLo + 0..3, and omega at kCstOmega with its remainder at kCstOmegaLo.
 struct CoefT {
   float* tab;
+  float* tablo;
   float* cst;
 };
-constexpr int kCst = 8;
+constexpr int kCst = 16;
 constexpr int kCstOmega = 4;
+constexpr int kCstOmegaLo = 5;
+constexpr int kCstLo = 8;
 
 // hi[i] + lo[i] = u[i] to ~2^-48 relative, i < n
 void split_df(const double* u, float* hi, float* lo, size_t n, cudaStream_t s);
@@ -176,9 +181,14 @@ void add_f32(const float* e, double* x, size_t n, cudaStream_t s, bool bf = fals
 // r = f - L x with the FP64 operator of the level (2D uses c2, 3D c3), stored single
 void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const double* f,
                     const double* x, float* r, cudaStream_t s, bool bf = false);
-// the FP32 tables of level g from its FP64 ones (after the level's operator setup)
+// the split tables and constants of level g from its FP64 tables (c2.tab / c3.tab written)
 void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
                 const PotentialParams* pp, const CoefT& ct, cudaStream_t s);
+// 3D coefficients (c.a, c.dinv) in double-float arithmetic from the split tables of
+// tables_f32, written in FP64 (mixed-precision modes)
+void coef3d_df(const Grid& g, const CoefT& ct, const Coef3D& c, cudaStream_t s);
+// 3D separable tables only (k_coef1d_3d of coef3d_setup)
+void coef1d_3d(const Grid& g, const PotentialParams* p_dev, const Coef3D& c, cudaStream_t s);
 // damped Jacobi sweep / residual with coefficients rebuilt from the FP32 tables
 void jacobi32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* xo,
               bool zero, cudaStream_t s, bool bf = false);

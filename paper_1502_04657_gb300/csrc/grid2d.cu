@@ -240,16 +240,18 @@ __global__ void k_rhs2d(int n, int pitch, size_t st, double h2_12, double h2_120
 // The same right-hand side in double-float arithmetic from the split u (mixed-precision
 // modes): ~2^-47 relative rounding per operation on the FP32 pipes; the FP64 result combines
 // the two FP64-converted parts.
-__global__ void k_rhs2d_df(int n, int pitch, size_t st, double h2_12, double h2_120,
+// The scales h^2/12 and h^2/120 arrive as double-float constants, so each node spends only
+// the two FP64 conversions and the final combination on the FP64 pipe.
+__global__ void k_rhs2d_df(int n, int pitch, size_t st, dfloat h2_12, dfloat h2_120,
                            const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
                            SplitVec u, double* __restrict__ f) {
   INTERIOR_2D
   const dfloat s = ((get<dfloat>(u, k + 1) + get<dfloat>(u, k - 1)) +
                     (get<dfloat>(u, k + pitch) + get<dfloat>(u, k - pitch))) +
                    (get<dfloat>(u, k + pitch + 1) + get<dfloat>(u, k - pitch - 1));
-  const double mu = h2_12 * to_double(fma(dfloat(6), get<dfloat>(u, k), s));
-  const double nl = to_double(nload_at<dfloat>(u, k, pitch));
-  f[k] = fma(lam[ib], mu, -(pp[ib].zeta * h2_120) * nl);
+  const double mu = to_double(h2_12 * fma(dfloat(6), get<dfloat>(u, k), s));
+  const double nl = to_double(h2_120 * nload_at<dfloat>(u, k, pitch));
+  f[k] = fma(lam[ib], mu, -pp[ib].zeta * nl);
 }
 
 // FP32 auxiliary right-hand side of the mixed-precision iteration (same closed forms in
@@ -391,7 +393,7 @@ void rhs2d_f32(const Grid& g, const double* lam, const PotentialParams* p, const
 void rhs2d_df(const Grid& g, const double* lam, const PotentialParams* p, SplitVec u, double* f,
               cudaStream_t s) {
   k_rhs2d_df<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
-      g.n, g.pitch, g.stride, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
+      g.n, g.pitch, g.stride, dfloat(g.h * g.h / 12.0), dfloat(g.h * g.h / 120.0), lam, p, u, f);
 }
 
 void dense_level1_2d(const Grid& g, const Coef2D& c, double* L, double* M, cudaStream_t s) {

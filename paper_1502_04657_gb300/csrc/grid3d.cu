@@ -107,6 +107,53 @@ __global__ void k_coef3d(int n, int pitch, size_t st, double h, const double* __
   c.dinv[k] = p.omega * recip(cc);
 }
 
+// The same coefficients in double-float arithmetic (mixed-precision modes) from the split
+// tables (thi + tlo) and split constants of the single-precision V-cycle: every coefficient
+// is a constant plus three table entries, so the FP64 pipe only converts the 9 outputs.
+// omega / C: a Newton step in double-float from the FP32 reciprocal of C.
+__global__ void k_coef3d_df(int n, int pitch, size_t st, const float* __restrict__ thi,
+                            const float* __restrict__ tlo, const float* __restrict__ cst,
+                            Coef3D c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ib = blockIdx.z / (n + 1);
+  const int l = (int)blockIdx.z - ib * (n + 1);
+  if (i > n || j > n) return;
+  const int s = n + 1;
+  const size_t to = (size_t)ib * 15 * s;
+  const int co[3] = {i, j, l};
+  auto T = [&](int ax, int q) {
+    const size_t e = to + (size_t)(ax * 5 + q) * s + co[ax];
+    return dfloat(thi[e], tlo[e]);
+  };
+  const float* C = cst + (size_t)kCst * ib;
+  auto K = [&](int q) { return dfloat(C[q], C[kCstLo + q]); };
+  const size_t k = ib * st + ((size_t)l * (n + 1) + j) * pitch + i;
+  const dfloat cc = ((K(0) + T(0, 0)) + T(1, 0)) + T(2, 0);
+  c.a[0][k] = to_double(cc);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dfloat v = K(1);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == d ? 1 : 2);
+    c.a[1 + d][k] = to_double(v);
+  }
+  const int other[3] = {2, 1, 0};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    dfloat v = K(2);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == other[f] ? 4 : 3);
+    c.a[4 + f][k] = to_double(v);
+  }
+  c.a[7][k] = to_double(((K(3) + T(0, 1)) + T(1, 1)) + T(2, 1));
+  // r = 1 / cc: FP32 seed, one Newton step r + r (1 - cc r) in double-float
+  const dfloat r0(__frcp_rn(cc.hi), 0.0f);
+  const dfloat e = dfloat(1) + -(cc * r0);
+  const dfloat r = fma(r0, e, r0);
+  c.dinv[k] = to_double(dfloat(C[kCstOmega], C[kCstOmegaLo]) * r);
+}
+
 __device__ __forceinline__ double lop3(const Coef3D& c, const double* __restrict__ x, size_t k,
                                        int pitch, long plane) {
   double v = c.a[0][k] * x[k];
@@ -387,27 +434,31 @@ __global__ void k_rhs3d_f32(int n, int pitch, size_t st, float h3, float nscale,
 
 // The same right-hand side in double-float arithmetic from the split u (mixed-precision
 // modes), combined in FP64.
-__global__ void k_rhs3d_df(int n, int pitch, size_t st, double h3, double nscale,
+__global__ void k_rhs3d_df(int n, int pitch, size_t st, dfloat h3, dfloat nscale,
                            const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
                            SplitVec u, double* __restrict__ f) {
   INTERIOR_3D
   dfloat nl;
   star3<dfloat, false>(u, k, pitch, plane, nl, nullptr);
-  const double mu = h3 * to_double(mass_at<dfloat>(u, k, pitch, plane));
-  f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * to_double(nl));
+  const double mu = to_double(h3 * mass_at<dfloat>(u, k, pitch, plane));
+  f[k] = fma(lam[ib], mu, -pp[ib].zeta * to_double(nscale * nl));
 }
 
-// T, U: FP64 (double, const double*) or double-float from the split u (dfloat, SplitVec)
-template <typename T, typename U>
-__global__ void k_nload_density3d(int n, int pitch, size_t st, double s140, double s210,
-                                  double s420, U u, double* __restrict__ nl, Density3D b) {
+// T, U: FP64 (double, const double*) or double-float from the split u (dfloat, SplitVec); the
+// scales come in T, so the double-float version's only FP64 work is the output conversion.
+// MINB: resident blocks of 256 threads asked of the register allocator (the double-float
+// star needs 255 registers otherwise, which leaves 8 warps per SM).
+template <typename T, typename U, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_nload_density3d(int n, int pitch, size_t st, T s140, T s210, T s420, U u,
+                      double* __restrict__ nl, Density3D b) {
   INTERIOR_3D
   T v, e[8];
   star3<T, true>(u, k, pitch, plane, v, e);
-  nl[k] = s140 * out_of(v);
-  b.a[0][k] = s210 * out_of(e[0]);
+  nl[k] = out_of(s140 * v);
+  b.a[0][k] = out_of(s210 * e[0]);
 #pragma unroll
-  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = s420 * out_of(e[1 + d]);
+  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = out_of(s420 * e[1 + d]);
 }
 
 // Galerkin coarsening of the 15-point density stencil: Bc(a, b) = sum P_va P_wb B(v, w) over
@@ -537,6 +588,15 @@ dim3 block3(const Grid& g) { return dim3(g.bx, g.by); }
 
 }  // namespace
 
+void coef1d_3d(const Grid& g, const PotentialParams* p, const Coef3D& c, cudaStream_t s) {
+  k_coef1d_3d<<<dim3((g.n + 1 + 127) / 128, g.nb), 128, 0, s>>>(g.n, g.h, p, c.tab);
+}
+
+void coef3d_df(const Grid& g, const CoefT& ct, const Coef3D& c, cudaStream_t s) {
+  k_coef3d_df<<<grid3(g, g.n + 1, g.n + 1, g.n + 1), block3(g), 0, s>>>(
+      g.n, g.pitch, g.stride, ct.tab, ct.tablo, ct.cst, c);
+}
+
 void coef3d_setup(const Grid& g, const PotentialParams* p, const Coef3D& c, cudaStream_t s) {
   k_coef1d_3d<<<dim3((g.n + 1 + 127) / 128, g.nb), 128, 0, s>>>(g.n, g.h, p, c.tab);
   k_coef3d<<<grid3(g, g.n + 1, g.n + 1, g.n + 1), block3(g), 0, s>>>(g.n, g.pitch, g.stride, g.h,
@@ -609,21 +669,23 @@ void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p, const
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s) {
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload_density3d<double, const double*><<<INTERIOR_LAUNCH(g)>>>(
+  k_nload_density3d<double, const double*, 1><<<INTERIOR_LAUNCH(g)>>>(
       g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0, vol / 420.0, u, nl, b);
 }
 
 void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& b,
                         cudaStream_t s) {
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload_density3d<dfloat, SplitVec><<<INTERIOR_LAUNCH(g)>>>(
-      g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0, vol / 420.0, u, nl, b);
+  k_nload_density3d<dfloat, SplitVec, 2><<<INTERIOR_LAUNCH(g)>>>(
+      g.n, g.pitch, g.stride, dfloat(vol / 140.0), dfloat(vol / 210.0), dfloat(vol / 420.0), u,
+      nl, b);
 }
 
 void rhs3d_df(const Grid& g, const double* lam, const PotentialParams* p, SplitVec u, double* f,
               cudaStream_t s) {
   const double h3 = g.h * g.h * g.h;
-  k_rhs3d_df<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, h3, h3 / 6.0 / 140.0, lam, p, u, f);
+  k_rhs3d_df<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, dfloat(h3), dfloat(h3 / 6.0 / 140.0),
+                                     lam, p, u, f);
 }
 
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,

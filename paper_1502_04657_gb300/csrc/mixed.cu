@@ -288,20 +288,26 @@ __global__ void k_sweep32_3d(int n, int pitch, size_t st_, int chunks,
 // per-instance constants of the single-precision sweeps: omega and, in 3D, the constant parts
 // of the coefficients (grid3d.cu's k_coef3d): C, axis, face, body; wl = 0 drops W (the
 // paper-literal form)
+__device__ __forceinline__ void put_split(float* c, int hi, int lo, double v) {
+  const float f = __double2float_rn(v);
+  c[hi] = f;
+  c[lo] = __double2float_rn(v - (double)f);
+}
+
 __global__ void k_consts(int dim, int nb, double h, const PotentialParams* __restrict__ pp,
                          float* __restrict__ cst) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const PotentialParams p = pp[b];
   float* c = cst + kCst * b;
-  c[kCstOmega] = (float)p.omega;
+  put_split(c, kCstOmega, kCstOmegaLo, p.omega);
   if (dim == 3) {
     const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
     const double h3w = wl * h * h * h * p.w0;
-    c[0] = (float)(6.0 * h + 0.4 * h3w);
-    c[1] = (float)(-h + h3w * (1.0 / 20.0));
-    c[2] = (float)(h3w * (1.0 / 30.0));
-    c[3] = (float)(h3w * (1.0 / 20.0));
+    put_split(c, 0, kCstLo + 0, 6.0 * h + 0.4 * h3w);
+    put_split(c, 1, kCstLo + 1, -h + h3w * (1.0 / 20.0));
+    put_split(c, 2, kCstLo + 2, h3w * (1.0 / 30.0));
+    put_split(c, 3, kCstLo + 3, h3w * (1.0 / 20.0));
   }
 }
 
@@ -449,7 +455,7 @@ void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const dou
 void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
                 const PotentialParams* pp, const CoefT& ct, cudaStream_t s) {
   const size_t n = (size_t)(g.dim == 2 ? 8 : 15) * (g.n + 1) * g.nb;
-  k_to_s<float><<<blocks_for(n), 256, 0, s>>>(n, g.dim == 2 ? c2.tab : c3.tab, ct.tab);
+  k_split_df<<<blocks_for(n), 256, 0, s>>>(n, g.dim == 2 ? c2.tab : c3.tab, ct.tab, ct.tablo);
   k_consts<<<(g.nb + 127) / 128, 128, 0, s>>>(g.dim, g.nb, g.h, pp, ct.cst);
 }
 
