@@ -64,6 +64,12 @@ extern "C" {
  * to 7.6e-9 relative against FP64 (3D, W = 100(x^2 + y^2 + 4z^2), zeta = 100), against
  * 1.9e-9 with the default FP64 right-hand side.                                            */
 #define FMG_FLAG_FP32_RHS 2
+/* flags (with FMG_MIXED_FP32 / FMG_MIXED_BF16): run every single-precision Jacobi sweep and
+ * residual with the register-blocked kernels instead of the TMA-fed ones that the levels
+ * with at least 512 (2D) or 128 (3D) cells per side use by default.  Both compute every node with the same
+ * expression, so the results are bit-identical; the flag exists for comparison and for
+ * drivers where tensor maps cannot be encoded (the library also falls back by itself).     */
+#define FMG_FLAG_NO_TMA 4
 
 /* Problem and method parameters.  Example 4.1 fixes the PDE; Algorithm 3.1 fixes m (vcycles)
  * and Algorithm 3.2 fixes p (corrections) and the level count n.                            */

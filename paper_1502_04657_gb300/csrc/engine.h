@@ -32,6 +32,11 @@ struct Level {
   float *x32 = nullptr, *xt32 = nullptr, *f32 = nullptr, *r32 = nullptr;
   // mixed precision: double-float split (hi + lo) of the vector the nonlinear kernels read
   float *uhi = nullptr, *ulo = nullptr;
+  // mixed precision, large 2D levels: tensor maps of the two x buffers (tile + halo box) and
+  // of f32 (tile box) for the TMA-fed sweeps; tm_base[q] is the buffer tm_x[q] describes
+  bool tma = false;
+  const float* tm_base[2] = {};
+  TMAMap tm_x[2]{}, tm_f{};
   double* pw = nullptr;   // (x / r)^m table for the 2D T3 sums (levels >= 2)
   double* t3map = nullptr;  // class sums -> T3 map of this level (levels >= 2)
 };

@@ -212,7 +212,8 @@ int validate(const fmg_eig_problem* p) {
   if (!(p->box_len > 0.0) || !(p->zeta >= 0.0) || !(p->omega > 0.0 && p->omega <= 1.0))
     return FMG_EINVAL;
   if (!(p->scf_tol > 0.0) || p->scf_max_iter < 1) return FMG_EINVAL;
-  if (p->flags & ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS)) return FMG_EINVAL;
+  if (p->flags & ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS | FMG_FLAG_NO_TMA))
+    return FMG_EINVAL;
   if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision == FMG_FP64) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
@@ -329,6 +330,14 @@ void build_levels(fmg_eig_handle* h) {
       l.r32 = single();
       l.uhi = h->alloc<float>(s);
       l.ulo = h->alloc<float>(s);
+      if (!h->dry && tma_sweep_applies(l.g) && !(h->prob.flags & FMG_FLAG_NO_TMA)) {
+        const bool bf = h->bf16();
+        l.tma = encode_level_map(l.g, l.cap, l.x32, bf, true, &l.tm_x[0]) &&
+                encode_level_map(l.g, l.cap, l.xt32, bf, true, &l.tm_x[1]) &&
+                encode_level_map(l.g, l.cap, l.f32, bf, false, &l.tm_f);
+        l.tm_base[0] = l.x32;
+        l.tm_base[1] = l.xt32;
+      }
     }
     l.x = h->alloc<double>(s);
     l.xt = h->alloc<double>(s);
@@ -654,6 +663,20 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   prof_end(h, kProfVcycle, j, s);
 }
 
+// Single-precision sweep (mode 0 residual into r32, 1 Jacobi, 2 Jacobi from zero, both into
+// xt32) of level l: TMA-fed on the large 2D levels, register-blocked otherwise.
+void lv_sweep32(fmg_eig_handle* h, Level& l, int mode, cudaStream_t s) {
+  const bool bf = h->bf16();
+  if (l.tma) {
+    const TMAMap& mx = l.x32 == l.tm_base[0] ? l.tm_x[0] : l.tm_x[1];
+    sweep32_tma(l.g, l.ct, mx, l.tm_f, mode == 0 ? l.r32 : l.xt32, mode, s, bf);
+  } else if (mode == 0) {
+    residual32(l.g, l.ct, l.f32, l.x32, l.r32, s, bf);
+  } else {
+    jacobi32(l.g, l.ct, l.f32, l.x32, l.xt32, mode == 2, s, bf);
+  }
+}
+
 // One FP32 V-cycle on level j for L_j e = r (e, r in L(j).x32, L(j).f32), e starting at 0.
 void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
   Level& l = h->L(j);
@@ -668,7 +691,7 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
     // the profiled sweep is the first one that reads x (the zero-start sweep reads only f)
     const bool prof = !zero;
     if (prof) prof_begin(h, kProfJacobi, j, s);
-    jacobi32(l.g, l.ct, l.f32, l.x32, l.xt32, zero, s, bf);
+    lv_sweep32(h, l, zero ? 2 : 1, s);
     if (prof) prof_end(h, kProfJacobi, j, s);
     std::swap(l.x32, l.xt32);
     zero = false;
@@ -676,7 +699,7 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
   if (zero) cudaMemsetAsync(l.x32, 0, l.g.stride * l.g.nb * mixed_elem_bytes(bf), s);
   Level& lc = h->L(j - 1);
   prof_begin(h, kProfResidual, j, s);
-  residual32(l.g, l.ct, l.f32, l.x32, l.r32, s, bf);
+  lv_sweep32(h, l, 0, s);
   prof_end(h, kProfResidual, j, s);
   prof_begin(h, kProfRestrict, j, s);
   restrict32(l.g, lc.g, l.r32, lc.f32, s, bf);
@@ -686,7 +709,7 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
   prolong32_add(l.g, lc.g, lc.x32, l.x32, s, bf);
   prof_end(h, kProfProlong, j, s);
   for (int it = 0; it < p.nu_post; ++it) {
-    jacobi32(l.g, l.ct, l.f32, l.x32, l.xt32, false, s, bf);
+    lv_sweep32(h, l, 1, s);
     std::swap(l.x32, l.xt32);
   }
 }

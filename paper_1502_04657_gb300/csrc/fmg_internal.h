@@ -189,6 +189,20 @@ void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
 void coef3d_df(const Grid& g, const CoefT& ct, const Coef3D& c, cudaStream_t s);
 // 3D separable tables only (k_coef1d_3d of coef3d_setup)
 void coef1d_3d(const Grid& g, const PotentialParams* p_dev, const Coef3D& c, cudaStream_t s);
+// TMA-fed single-precision sweeps of the large levels (sweep_tma.cu).  A TMAMap holds a
+// tensor map (CUtensorMap) of one level vector: columns, rows and instances, with a box of
+// one tile (halo = true: the x box, 2 rows taller).
+struct TMAMap {
+  alignas(64) unsigned char bytes[128];
+};
+constexpr int kTMAMinCells2 = 512;  // 2D levels with n >= this use the TMA sweeps
+constexpr int kTMAMinCells3 = 128;  // 3D levels likewise
+bool tma_sweep_applies(const Grid& g);
+bool encode_level_map(const Grid& g, int cap, const float* base, bool bf, bool halo,
+                      TMAMap* out);
+// mode 0: residual y = f - L x; 1: Jacobi y = x + omega D^-1 (f - L x); 2: Jacobi from x = 0
+void sweep32_tma(const Grid& g, const CoefT& ct, const TMAMap& mx, const TMAMap& mf, float* y,
+                 int mode, cudaStream_t s, bool bf = false);
 // damped Jacobi sweep / residual with coefficients rebuilt from the FP32 tables
 void jacobi32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* xo,
               bool zero, cudaStream_t s, bool bf = false);

@@ -17,6 +17,7 @@ FMG_W_LEFT, FMG_PAPER_LITERAL = 0, 1
 FMG_SMOOTH_JACOBI, FMG_SMOOTH_CHEBYSHEV = 0, 1
 FMG_FLAG_NO_AUTOTUNE = 1
 FMG_FLAG_FP32_RHS = 2
+FMG_FLAG_NO_TMA = 4
 FMG_MAX_LEVELS = 16
 
 

@@ -105,3 +105,41 @@ def test_bf16_storage_ablation(kw):
     assert rc == 0
     print(f"bf16 storage: |dlambda|/lambda = {abs(lam16 - lam64) / lam64:.3e}")
     assert abs(lam16 - lam64) <= 1e-4 * lam64
+
+
+@pytest.mark.parametrize("precision", [1, 2], ids=["fp32", "bf16"])
+def test_tma_sweeps_bit_identical_to_register_blocked(precision):
+    """The levels with >= 512 (2D) or 128 (3D) cells per side run their single-precision sweeps
+    through the TMA-fed kernels; they compute every node like the register-blocked kernels, so
+    a solve and a batch give bit-identical results with FMG_FLAG_NO_TMA, and stay within the
+    mixed acceptance bound of the FP64 solve."""
+    fmg = _fmg()
+    kws = [dict(dim=2, coarse_cells=8, levels=8, w_quad=(1.0, 4.0, 0.0), zeta=25.0),
+           dict(dim=2, coarse_cells=8, levels=7, w_quad=(1.0, 1.0, 0.0), zeta=80.0),
+           dict(dim=2, coarse_cells=4, levels=9, w_quad=(1.0, 9.0, 0.0), zeta=5.0),
+           dict(dim=3, coarse_cells=4, levels=6, w_quad=(1.0, 1.0, 4.0), zeta=30.0)]
+    probs = [fmg.Problem(**kw, precision=precision) for kw in kws]
+    plain = [fmg.Problem(**kw, precision=precision, flags=fmg.FMG_FLAG_NO_TMA) for kw in kws]
+    for p, q in zip(probs, plain):
+        n = p.size(p.levels)
+        with fmg.Solver(p) as s:
+            u1 = np.empty(n)
+            lam1, _, rc1 = s.solve(u1)
+        with fmg.Solver(q) as s:
+            u2 = np.empty(n)
+            lam2, _, rc2 = s.solve(u2)
+        assert rc1 == rc2 == 0
+        assert lam1 == lam2
+        assert np.array_equal(u1, u2)
+    with fmg.BatchSolver(probs[:2]) as b:
+        lb, ub, _, cb = b.solve_all()
+    with fmg.BatchSolver(plain[:2]) as b:
+        lp, up, _, cp = b.solve_all()
+    assert list(cb) == list(cp) == [0, 0]
+    assert lb == lp
+    assert all(np.array_equal(a, c) for a, c in zip(ub, up))
+    if precision == 1:
+        p64 = fmg.Problem(**kws[0])
+        with fmg.Solver(p64) as s:
+            lam64, _, _ = s.solve()
+        assert abs(lb[0] - lam64) <= DLAM * lam64
