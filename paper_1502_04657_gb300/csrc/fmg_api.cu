@@ -714,8 +714,15 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
   }
 }
 
-void enqueue_multigrid(fmg_eig_handle* h, int k, cudaStream_t s) {
-  if (h->mixed()) {
+// The m multigrid iterations of Algorithm 3.1 step 1 on level k.  In the mixed modes an FMG
+// stage whose level is large enough for bandwidth to matter (the levels of the TMA-fed
+// sweeps: n >= 512 in 2D, >= 128 in 3D) runs FP64 defect correction around single-precision
+// V-cycles; smaller stages, where the V-cycle is bound by latency rather than bandwidth, run
+// the FP64 V-cycles (in_fmg = false, the component call, always takes the mixed path).  The
+// early stages then match the FP64 solve exactly: with a strong nonlinearity (3D, zeta ~
+// 150-200) single-precision rounding entering there grew to |d lambda| ~1e-8 at the end.
+void enqueue_multigrid(fmg_eig_handle* h, int k, cudaStream_t s, bool in_fmg = true) {
+  if (h->mixed() && (!in_fmg || tma_sweep_applies(h->L(k).g))) {
     // FP64 defect correction around single-precision V-cycles
     Level& l = h->L(k);
     for (int it = 0; it < h->prob.vcycles; ++it) {
@@ -1508,7 +1515,7 @@ int fmg_eig_multigrid(fmg_eig_handle* h, int32_t level, const double* f_dev, dou
   Level& l = h->L(level);
   pack_interior(l.g, f_dev, l.f, s);
   pack_interior(l.g, x_dev, l.x, s);
-  enqueue_multigrid(h, level, s);
+  enqueue_multigrid(h, level, s, false);
   unpack_interior(l.g, l.x, x_dev, s);
   CK(cudaGetLastError());
   return FMG_OK;

@@ -165,6 +165,11 @@ struct CoefT {
   float* tablo;
   float* cst;
 };
+// 3D single-precision sweeps: coupling = ((x part + y part) + z part) + class constant, the
+// large constant (6h, -h) added last so that each coefficient is one rounding from its FP64
+// value.  (Adding the constant first and three rounded table entries after it left the
+// smooth-mode part of the operator off by several roundings of the constant, which showed
+// as |d lambda| up to 3e-8 on strongly nonlinear 3D problems.)
 constexpr int kCst = 16;
 constexpr int kCstOmega = 4;
 constexpr int kCstOmegaLo = 5;

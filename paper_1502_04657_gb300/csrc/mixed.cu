@@ -217,7 +217,9 @@ __global__ void k_residual_mixed3d(int n, int pitch, size_t st_, Coef3D c,
 //   C = cst0 + T(x,0) + T(y,0) + T(z,0);  axis d: cst1 + T(d,1) + sum_{ax != d} T(ax,2);
 //   face with third axis o: cst2 + T(o,4) + sum_{ax != o} T(ax,3);  body: cst3 + sum T(ax,1).
 // The coupling to p - o_d is the one of p - o_d to p.  q_of(d, ax) is the table a direction
-// takes on an axis.
+// takes on an axis.  In FP32 the sum runs ((T(x) + T(y)) + T(z)) + constant: the constant
+// (6h, -h) is much larger than the potential terms, and adding it last keeps each
+// coefficient one rounding from its FP64 value (see CoefT in fmg_internal.h).
 __device__ __forceinline__ constexpr int q_of(int d, int ax) {
   return d < 3 ? (ax == d ? 1 : 2) : (d < 6 ? (ax == 5 - d ? 4 : 3) : 1);
 }
@@ -225,7 +227,8 @@ constexpr int kPlanes3 = 4;  // planes per thread
 
 // A thread takes (i, j) and planes l0 .. l0 + kPlanes3 - 1 of instance ib, blockIdx.z =
 // ib * chunks + (l0 - 1) / kPlanes3.  The x and y parts of its 15 coefficients (the centre and
-// both ends of the 7 directions) are summed once; each plane adds its z-table entries.
+// both ends of the 7 directions) are summed once; each plane adds its z-table entries and
+// then the class constants.
 template <typename S, int MODE>
 __global__ void k_sweep32_3d(int n, int pitch, size_t st_, int chunks,
                              const float* __restrict__ tab, const float* __restrict__ cst,
@@ -250,22 +253,22 @@ __global__ void k_sweep32_3d(int n, int pitch, size_t st_, int chunks,
   for (int q = 0; q < kPlanes3; ++q) fv[q] = ld(f, (size_t)min(l0 + q, n - 1) * plane + col);
   // x and y parts: cxy[0] the centre, cxy[1 + 2 d + e] direction d at p (e = 0) or p - o_d
   float cxy[15];
-  cxy[0] = C[0] + T[i] + T[5 * s + j];
+  cxy[0] = T[i] + T[5 * s + j];
 #pragma unroll
   for (int d = 0; d < 7; ++d)
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int ci = i - (e ? kDir[d][0] : 0), cj = j - (e ? kDir[d][1] : 0);
-      cxy[1 + 2 * d + e] = C[d < 3 ? 1 : (d < 6 ? 2 : 3)] + T[q_of(d, 0) * s + ci] +
-                           T[(5 + q_of(d, 1)) * s + cj];
+      cxy[1 + 2 * d + e] = T[q_of(d, 0) * s + ci] + T[(5 + q_of(d, 1)) * s + cj];
     }
   const float w = MODE == kResidual ? 0.0f : C[kCstOmega];
   const float* Tz = T + 10 * s;
+  const float K0 = C[0], K1 = C[1], K2 = C[2], K3 = C[3];
 #pragma unroll
   for (int q = 0; q < kPlanes3; ++q) {
     const int l = min(l0 + q, n - 1);  // planes past n - 1: computed on n - 1, not stored
     const size_t k = (size_t)l * plane + col;
-    const float cc = cxy[0] + Tz[l];
+    const float cc = (cxy[0] + Tz[l]) + K0;
     float out;
     if (MODE == kJacobiZero) {
       out = __fdividef(w, cc) * fv[q];
@@ -274,8 +277,9 @@ __global__ void k_sweep32_3d(int n, int pitch, size_t st_, int chunks,
 #pragma unroll
       for (int d = 0; d < 7; ++d) {
         const long o = dir_off(d, pitch, plane);
-        const float a0 = cxy[1 + 2 * d] + Tz[q_of(d, 2) * s + l];
-        const float a1 = cxy[2 + 2 * d] + Tz[q_of(d, 2) * s + l - kDir[d][2]];
+        const float K = d < 3 ? K1 : (d < 6 ? K2 : K3);
+        const float a0 = (cxy[1 + 2 * d] + Tz[q_of(d, 2) * s + l]) + K;
+        const float a1 = (cxy[2 + 2 * d] + Tz[q_of(d, 2) * s + l - kDir[d][2]]) + K;
         v = fmaf(a0, ld(x, k + o), v);
         v = fmaf(a1, ld(x, k - o), v);
       }

@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kThreads)
                      S* __restrict__ y) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStages3 * stage_bytes3<S>());
-  __shared__ float sTz[5][kTZ3 + 1];  // z tables q of the tile's planes l0 - 1 + p
+  __shared__ float sTz[5][kTZ3 + 1];  // z tables at the tile's planes l0 - 1 + p
   const int tid = threadIdx.x;
   const uint32_t tx_bytes = (MODE == kJacobiZero ? 0 : x_bytes3<S>()) + f_bytes3<S>();
   if (tid == 0) {
@@ -352,17 +352,17 @@ __global__ void __launch_bounds__(kThreads)
     float cxy[15];
     float w = 0.0f;
     if (act) {
-      cxy[0] = C[0] + T[i] + T[5 * s + j];
+      cxy[0] = T[i] + T[5 * s + j];
 #pragma unroll
       for (int d = 0; d < 7; ++d)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int ci = i - (e ? kDir3[d][0] : 0), cj = j - (e ? kDir3[d][1] : 0);
-          cxy[1 + 2 * d + e] = C[d < 3 ? 1 : (d < 6 ? 2 : 3)] + T[q_of3(d, 0) * s + ci] +
-                               T[(5 + q_of3(d, 1)) * s + cj];
+          cxy[1 + 2 * d + e] = T[q_of3(d, 0) * s + ci] + T[(5 + q_of3(d, 1)) * s + cj];
         }
       w = MODE == kResidual ? 0.0f : C[kCstOmega];
     }
+    const float K0 = C[0], K1 = C[1], K2 = C[2], K3 = C[3];
     const bool ok = mbar_wait(&bar[stage], (uint32_t)((it / kStages3) & 1));
     const bool lost = __syncthreads_or(!ok);  // also publishes sTz
     const S* xs = reinterpret_cast<const S*>(smem + (size_t)stage * stage_bytes3<S>());
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kThreads)
         const int l = l0 + q;
         if (l >= n) break;
         const float fv = ld(fs, (q * kTY3 + r) * kBoxW3 + lc);
-        const float cc = cxy[0] + sTz[0][q + 1];
+        const float cc = (cxy[0] + sTz[0][q + 1]) + K0;
         float out;
         if (MODE == kJacobiZero) {
           out = __fdividef(w, cc) * fv;
@@ -391,8 +391,9 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
           for (int d = 0; d < 7; ++d) {
             const int o = kDir3[d][0] + kDir3[d][1] * RW + kDir3[d][2] * PL;
-            const float a0 = cxy[1 + 2 * d] + sTz[q_of3(d, 2)][q + 1];
-            const float a1 = cxy[2 + 2 * d] + sTz[q_of3(d, 2)][q + 1 - kDir3[d][2]];
+            const float K = d < 3 ? K1 : (d < 6 ? K2 : K3);
+            const float a0 = (cxy[1 + 2 * d] + sTz[q_of3(d, 2)][q + 1]) + K;
+            const float a1 = (cxy[2 + 2 * d] + sTz[q_of3(d, 2)][q + 1 - kDir3[d][2]]) + K;
             v = fmaf(a0, ld(xs, k0 + o), v);
             v = fmaf(a1, ld(xs, k0 - o), v);
           }
