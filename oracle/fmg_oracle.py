@@ -54,6 +54,7 @@ W_LEFT = 0
 PAPER_LITERAL = 1
 SMOOTH_JACOBI = 0
 SMOOTH_CHEBYSHEV = 1
+SMOOTH_CG = 2  # Section 4: "3 conjugate gradient smooth steps" (plain CG on L_j x = f)
 # Chebyshev smoothing interval [CHEB_LOW, CHEB_HIGH] for the spectrum of D^{-1} L: the upper
 # end is Gershgorin's bound for these operators (the stiffness rows sum to zero and the
 # potential mass has the P1 mass pattern, so every row of D^{-1} L has |off-diagonal| sum at
@@ -298,7 +299,8 @@ class Problem:
     vcycles: int = 2               # m of Algorithm 3.1
     corrections: int = 1           # p of Algorithm 3.2
     operator_form: int = W_LEFT
-    smoother: int = SMOOTH_JACOBI  # Chebyshev: degree nu_pre / nu_post on [CHEB_LOW, CHEB_HIGH]
+    smoother: int = SMOOTH_JACOBI  # Chebyshev: degree nu_pre / nu_post on [CHEB_LOW, CHEB_HIGH];
+    # CG: nu_pre / nu_post conjugate gradient steps
     scf_tol: float = 1e-13
     scf_max_iter: int = 500
 
@@ -370,9 +372,31 @@ def chebyshev(lev: Level, f: np.ndarray, x: np.ndarray, degree: int) -> np.ndarr
     return x
 
 
+def cg_steps(lev: Level, f: np.ndarray, x: np.ndarray, steps: int) -> np.ndarray:
+    """steps iterations of the conjugate gradient method (Hestenes-Stiefel, no
+    preconditioner) for L x = f from x: the smoother of the paper's experiments (Section 4).
+    A zero denominator (an exact x, or f = 0) ends the steps with a zero update."""
+    r = f - lev.L @ x
+    p = r.copy()
+    rr = float(r @ r)
+    for _ in range(steps):
+        q = lev.L @ p
+        pq = float(p @ q)
+        alpha = rr / pq if pq > 0.0 else 0.0
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(r @ r)
+        beta = rr_new / rr if rr > 0.0 else 0.0
+        p = r + beta * p
+        rr = rr_new
+    return x
+
+
 def smooth(lev: Level, f: np.ndarray, x: np.ndarray, nu: int, prob: Problem) -> np.ndarray:
     if prob.smoother == SMOOTH_CHEBYSHEV:
         return chebyshev(lev, f, x, nu) if nu > 0 else x
+    if prob.smoother == SMOOTH_CG:
+        return cg_steps(lev, f, x, nu)
     for _ in range(nu):
         x = jacobi(lev, f, x, prob.omega)
     return x

@@ -258,3 +258,69 @@ def test_chebyshev_vcycle_converges_faster_than_jacobi():
         x = O.multigrid(lv, 4, f, np.zeros_like(f), 4, prob)
         errs[sm] = np.linalg.norm(x - x_true) / np.linalg.norm(x_true)
     assert errs[O.SMOOTH_CHEBYSHEV] < 0.8 * errs[O.SMOOTH_JACOBI]
+
+
+def test_cg_steps_terminate_at_the_exact_solution():
+    """CG on an SPD system of N unknowns reaches the solution in N steps (finite
+    termination, exact arithmetic): pinned on a 9-unknown level against a dense solve."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=1, w_const=0.5, w_quad=(2.0, 1.0, 0.0))
+    lev = O.build_hierarchy(prob)[0]
+    L = lev.L.toarray()
+    rng = np.random.default_rng(17)
+    f = rng.normal(size=L.shape[0])
+    x0 = rng.normal(size=L.shape[0])
+    x = O.cg_steps(lev, f, x0, L.shape[0])
+    assert np.allclose(x, np.linalg.solve(L, f), rtol=1e-10, atol=1e-12)
+
+
+def test_cg_first_step_is_steepest_descent_with_exact_line_search():
+    prob = O.Problem(dim=3, coarse_cells=3, levels=1, w_quad=(1.0, 2.0, 3.0))
+    lev = O.build_hierarchy(prob)[0]
+    L = lev.L.toarray()
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=L.shape[0])
+    x0 = rng.normal(size=L.shape[0])
+    r = f - L @ x0
+    x1 = x0 + (r @ r) / (r @ L @ r) * r
+    assert np.allclose(O.cg_steps(lev, f, x0, 1), x1, rtol=1e-13, atol=1e-14)
+
+
+def test_cg_energy_error_decreases_and_minimises_over_the_krylov_space():
+    """The k-th CG iterate minimises the L-energy error over x0 + K_k(L, r0): checked
+    against the minimiser computed from an explicit Krylov basis."""
+    prob = O.Problem(dim=2, coarse_cells=6, levels=1, w_const=1.0, w_quad=(3.0, 1.0, 0.0))
+    lev = O.build_hierarchy(prob)[0]
+    L = lev.L.toarray()
+    rng = np.random.default_rng(9)
+    x_true = rng.normal(size=L.shape[0])
+    f = L @ x_true
+    x0 = np.zeros_like(f)
+    r0 = f - L @ x0
+    prev = np.inf
+    for k in (1, 2, 3):
+        x = O.cg_steps(lev, f, x0, k)
+        e = x - x_true
+        en = e @ L @ e
+        assert en < prev
+        prev = en
+        K = np.stack([np.linalg.matrix_power(L, i) @ r0 for i in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        c = np.linalg.solve(Q.T @ L @ Q, Q.T @ (f - L @ x0))
+        assert np.allclose(x, x0 + Q @ c, rtol=1e-9, atol=1e-11)
+
+
+def test_cg_smoothed_vcycle_converges():
+    """The paper's setting (3 + 3 CG smoothing steps) gives a convergent V-cycle."""
+    prob = O.Problem(dim=2, coarse_cells=4, levels=4, w_quad=(1.0, 1.0, 0.0),
+                     smoother=O.SMOOTH_CG, nu_pre=3, nu_post=3)
+    lv = O.build_hierarchy(prob)
+    lev = lv[-1]
+    rng = np.random.default_rng(3)
+    x_true = rng.normal(size=lev.L.shape[0])
+    f = lev.L @ x_true
+    e = [np.linalg.norm(x_true)]
+    x = np.zeros_like(f)
+    for _ in range(4):
+        x = O.vcycle(lv, 4, f, x, prob)
+        e.append(np.linalg.norm(x - x_true))
+    assert all(e[i + 1] < 0.5 * e[i] for i in range(4))
