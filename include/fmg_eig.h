@@ -48,6 +48,10 @@ extern "C" {
 /* Chebyshev semi-iteration of degree nu_pre / nu_post on [0.3, 2] for the spectrum of
  * D^{-1} L (2 = Gershgorin's bound for these operators; omega is not used); FMG_FP64 only */
 #define FMG_SMOOTH_CHEBYSHEV 1
+/* nu_pre / nu_post steps of the conjugate gradient method (no preconditioner) on L_j x = f
+ * from the current x: the smoother of the paper's experiments (Section 4, 3 + 3 steps);
+ * omega is not used; FMG_FP64 only                                                          */
+#define FMG_SMOOTH_CG 2
 #define FMG_FP64 0
 #define FMG_MIXED_FP32 1
 /* the same FP64 defect correction with the V-cycle's vectors and coefficients stored in
@@ -81,7 +85,7 @@ typedef struct fmg_eig_problem {
   int32_t nu_post;      /* post-smoothing sweeps (>= 0)                                    */
   int32_t vcycles;      /* m of Algorithm 3.1 (>= 1)                                       */
   int32_t corrections;  /* p of Algorithm 3.2 (>= 1)                                       */
-  int32_t smoother;     /* FMG_SMOOTH_JACOBI | FMG_SMOOTH_CHEBYSHEV                        */
+  int32_t smoother;     /* FMG_SMOOTH_JACOBI | FMG_SMOOTH_CHEBYSHEV | FMG_SMOOTH_CG        */
   int32_t precision;    /* FMG_FP64 | FMG_MIXED_FP32 | FMG_MIXED_BF16                      */
   int32_t operator_form;/* FMG_W_LEFT | FMG_PAPER_LITERAL                                  */
   int32_t scf_max_iter; /* cap on nonlinear iterations per small solve (e.g. 100)          */

@@ -96,6 +96,7 @@ struct fmg_eig_handle {
          *partials = nullptr, *partials2 = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,
          *gMd = nullptr, *t1d = nullptr, *B1d = nullptr, *t0 = nullptr,
          *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr, *uout = nullptr;
+  double* cg = nullptr;  // conjugate gradient smoother: r.r (2 slots) and p.L p per instance
   int *iters = nullptr, *status = nullptr;  // [level][instance]
   int* inv_order = nullptr;                 // sorted index of the caller's instance i
   // device copy read by the kernels (nparams), and its pinned host staging uploaded at every

@@ -217,8 +217,10 @@ int validate(const fmg_eig_problem* p) {
   if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision == FMG_FP64) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
   if (cells > (p->dim == 2 ? 32768.0 : 1024.0)) return FMG_EINVAL;
-  if (p->smoother != FMG_SMOOTH_JACOBI && p->smoother != FMG_SMOOTH_CHEBYSHEV) return FMG_EINVAL;
-  if (p->smoother == FMG_SMOOTH_CHEBYSHEV && p->precision != FMG_FP64) return FMG_ENOTSUP;
+  if (p->smoother != FMG_SMOOTH_JACOBI && p->smoother != FMG_SMOOTH_CHEBYSHEV &&
+      p->smoother != FMG_SMOOTH_CG)
+    return FMG_EINVAL;
+  if (p->smoother != FMG_SMOOTH_JACOBI && p->precision != FMG_FP64) return FMG_ENOTSUP;
   if ((p->precision != FMG_FP64 && p->precision != FMG_MIXED_FP32 &&
        p->precision != FMG_MIXED_BF16) ||
       (p->operator_form != FMG_W_LEFT && p->operator_form != FMG_PAPER_LITERAL))
@@ -449,6 +451,7 @@ void build_coarse(fmg_eig_handle* h) {
   h->buu = h->alloc<double>(nb);
   h->scal = h->alloc<double>(3 * (size_t)nb + 8);
   h->partials = h->alloc<double>((size_t)kReduceBlocks * nb);
+  if (h->prob.smoother == FMG_SMOOTH_CG) h->cg = h->alloc<double>(3 * (size_t)nb);
   h->partials2 = h->alloc<double>((size_t)kReduceBlocks * nb);
   const int nt3 = dim == 2 ? 10 : 20;
   h->t3 = h->alloc<double>((size_t)h->ntri * nt3 * nb);
@@ -612,6 +615,33 @@ void cheb_coefficients(int nu, std::vector<double>& alpha, std::vector<double>& 
 
 // nu smoothing steps on level l (x, f in l.x, l.f; the result ends in l.x)
 void enqueue_smooth(fmg_eig_handle* h, Level& l, int j, int nu, bool& zero, cudaStream_t s) {
+  if (h->prob.smoother == FMG_SMOOTH_CG) {
+    // nu CG steps on L x = f from x (Section 4): r in l.r, direction p in l.z, q = L p in l.y;
+    // per-instance scalars r.r (two slots, old / new) and p.q in h->cg
+    if (nu <= 0) return;
+    const size_t st = l.g.stride, n = st * l.g.nb;
+    if (zero) {
+      cudaMemsetAsync(l.x, 0, n * sizeof(double), s);
+      cudaMemcpyAsync(l.r, l.f, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    } else {
+      lv_residual(l, l.f, l.x, l.r, s);
+    }
+    zero = false;
+    cudaMemcpyAsync(l.z, l.r, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    double* rr = h->cg;
+    double* rr_new = h->cg + h->nb;
+    double* pq = h->cg + 2 * h->nb;
+    dot(l.r, l.r, st, h->partials, rr, s, l.g.nb, st);
+    for (int it = 0; it < nu; ++it) {
+      lv_apply(l, l.z, l.y, s);
+      dot(l.z, l.y, st, h->partials, pq, s, l.g.nb, st);
+      cg_update(n, st, rr, pq, l.z, l.y, l.x, l.r, s);
+      dot(l.r, l.r, st, h->partials, rr_new, s, l.g.nb, st);
+      cg_direction(n, st, rr_new, rr, l.r, l.z, s);
+      std::swap(rr, rr_new);
+    }
+    return;
+  }
   if (h->prob.smoother == FMG_SMOOTH_CHEBYSHEV) {
     std::vector<double> al, be;
     cheb_coefficients(nu, al, be);

@@ -227,6 +227,12 @@ void coarse32(const Grid& g, const double* Linv, const float* x, float* y, cudaS
 constexpr int kReduceBlocks = 1024;
 void dot(const double* a, const double* b, size_t n, double* partials, double* out,
          cudaStream_t s, int nb = 1, size_t vst = 0);
+// Conjugate gradient smoother steps over nb instances of `stride` elements (n = nb stride):
+// x += a p, r -= a q with a = rr[b] / pq[b]; then p = r + (rr_new[b] / rr_old[b]) p
+void cg_update(size_t n, size_t stride, const double* rr, const double* pq, const double* p,
+               const double* q, double* x, double* r, cudaStream_t s);
+void cg_direction(size_t n, size_t stride, const double* rr_new, const double* rr_old,
+                  const double* r, double* p, cudaStream_t s);
 
 // ---- Interior <-> padded packing (pack.cu) ----------------------------------------------
 // (instance b: interior vector at b * g.interior(), padded one at b * g.stride)

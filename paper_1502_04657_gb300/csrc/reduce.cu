@@ -54,4 +54,50 @@ void dot(const double* a, const double* b, size_t n, double* partials, double* o
   k_sum_final<<<nb, kThreads, 0, s>>>(partials, (int)blocks, out);
 }
 
+namespace {
+
+// Conjugate gradient updates over whole batched level vectors (boundary and padding entries
+// are zero in p, q and r and stay zero): instance ib = i / stride, with its scalars
+// rr = r.r, pq = p.L p (a zero denominator gives a zero step, as in the oracle).
+__global__ void k_cg_update(size_t n, size_t stride, const double* __restrict__ rr,
+                            const double* __restrict__ pq, const double* __restrict__ p,
+                            const double* __restrict__ q, double* __restrict__ x,
+                            double* __restrict__ r) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t ib = i / stride;
+    const double a = pq[ib] > 0.0 ? rr[ib] / pq[ib] : 0.0;
+    x[i] = fma(a, p[i], x[i]);
+    r[i] = fma(-a, q[i], r[i]);
+  }
+}
+
+__global__ void k_cg_direction(size_t n, size_t stride, const double* __restrict__ rr_new,
+                               const double* __restrict__ rr_old, const double* __restrict__ r,
+                               double* __restrict__ p) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t ib = i / stride;
+    const double b = rr_old[ib] > 0.0 ? rr_new[ib] / rr_old[ib] : 0.0;
+    p[i] = fma(b, p[i], r[i]);
+  }
+}
+
+unsigned cg_blocks(size_t n) {
+  const size_t b = (n + 255) / 256;
+  return (unsigned)(b < 152 * 16 ? b : 152 * 16);
+}
+
+}  // namespace
+
+void cg_update(size_t n, size_t stride, const double* rr, const double* pq, const double* p,
+               const double* q, double* x, double* r, cudaStream_t s) {
+  k_cg_update<<<cg_blocks(n), 256, 0, s>>>(n, stride, rr, pq, p, q, x, r);
+}
+
+void cg_direction(size_t n, size_t stride, const double* rr_new, const double* rr_old,
+                  const double* r, double* p, cudaStream_t s) {
+  k_cg_direction<<<cg_blocks(n), 256, 0, s>>>(n, stride, rr_new, rr_old, r, p);
+}
+
 }  // namespace fmg

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libfmg_eig.so")
 FMG_OK, FMG_EINVAL, FMG_ENOMEM, FMG_ENOCONV, FMG_ECUDA, FMG_ETIMEOUT, FMG_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 FMG_FP64, FMG_MIXED_FP32, FMG_MIXED_BF16 = 0, 1, 2
 FMG_W_LEFT, FMG_PAPER_LITERAL = 0, 1
-FMG_SMOOTH_JACOBI, FMG_SMOOTH_CHEBYSHEV = 0, 1
+FMG_SMOOTH_JACOBI, FMG_SMOOTH_CHEBYSHEV, FMG_SMOOTH_CG = 0, 1, 2
 FMG_FLAG_NO_AUTOTUNE = 1
 FMG_FLAG_FP32_RHS = 2
 FMG_FLAG_NO_TMA = 4
