@@ -684,6 +684,9 @@ def ours_arm(args):
         "config": {"workload": m["desc"], "dofs": m["dofs"], "parallelism": "replicas",
                    "l2": "per-step working set > 2 GB >> 129 MB L2; no flush"},
         "mdof_per_s": m["value"] * m["dofs"] / 1e6,
+        # one finest-level V-cycle (event-timed inside the solve graph): finest dofs / its time
+        "mdof_per_s_per_vcycle": (m["dofs"] / (m["profile"]["vcycle"] * 1e-3) / 1e6
+                                  if m["profile"].get("vcycle", -1) > 0 else None),
         "latency_ms": {"p50": statistics.median(step_ms),
                        "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
         "lambda": m["lambda"], "lambda_e2e": m["lambda_e2e"],
