@@ -71,16 +71,17 @@ __global__ void k_nload_density2d(int n, int pitch, size_t st, T s60, T s90, T s
   v = fma(T(2) * up, fma(T(2), s2, pp), v);
   v = fma(T(2), s3, v);
   nl[k] = out_of(s60 * (v + qq));
+  // density stencil: FP64, or kept split (double-float) in the mixed modes for the coarsening
   // diagonal: sum over the six triangles
-  bC[k] = out_of(s90 * fma(T(36), u2, fma(T(2), s2, fma(T(6) * up, s1, pp))));
+  put_entry(bC, k, s90 * fma(T(36), u2, fma(T(2), s2, fma(T(6) * up, s1, pp))));
   // edge p-q shared by the triangles closed by r1 and r2
   const T u26 = T(6) * u2;
-  bE[k] = out_of(s180 * fma(T(6), qE,
-                            u26 + fma(T(8) * up, nE, fma(T(2) * (up + nE), nNE + nS, qNE + qS))));
-  bN[k] = out_of(s180 * fma(T(6), qN,
-                            u26 + fma(T(8) * up, nN, fma(T(2) * (up + nN), nNE + nW, qNE + qW))));
-  bNE[k] = out_of(s180 * fma(T(6), qNE,
-                             u26 + fma(T(8) * up, nNE, fma(T(2) * (up + nNE), nE + nN, qE + qN))));
+  put_entry(bE, k, s180 * fma(T(6), qE,
+                              u26 + fma(T(8) * up, nE, fma(T(2) * (up + nE), nNE + nS, qNE + qS))));
+  put_entry(bN, k, s180 * fma(T(6), qN,
+                              u26 + fma(T(8) * up, nN, fma(T(2) * (up + nN), nNE + nW, qNE + qW))));
+  put_entry(bNE, k, s180 * fma(T(6), qNE,
+                               u26 + fma(T(8) * up, nNE, fma(T(2) * (up + nNE), nE + nN, qE + qN))));
 }
 
 // Galerkin coarsening of a 7-point stencil: Bc(a,b) = sum_{v,w} P_va P_wb B(v,w).  The
@@ -88,16 +89,17 @@ __global__ void k_nload_density2d(int n, int pitch, size_t st, T s60, T s90, T s
 __device__ constexpr int kSX[7] = {0, 1, -1, 0, 0, 1, -1};
 __device__ constexpr int kSY[7] = {0, 0, 0, 1, -1, 1, -1};
 
-__device__ __forceinline__ double fine_entry(const double* bC, const double* bE,
-                                             const double* bN, const double* bNE, size_t kv,
-                                             int dx, int dy, int pitch) {
-  if (dx == 0 && dy == 0) return bC[kv];
-  if (dx == 1 && dy == 0) return bE[kv];
-  if (dx == -1 && dy == 0) return bE[kv - 1];
-  if (dx == 0 && dy == 1) return bN[kv];
-  if (dx == 0 && dy == -1) return bN[kv - pitch];
-  if (dx == 1 && dy == 1) return bNE[kv];
-  return bNE[kv - pitch - 1];  // dx == dy == -1
+template <typename T>
+__device__ __forceinline__ T fine_entry(const double* bC, const double* bE, const double* bN,
+                                        const double* bNE, size_t kv, int dx, int dy,
+                                        int pitch) {
+  if (dx == 0 && dy == 0) return get_entry<T>(bC, kv);
+  if (dx == 1 && dy == 0) return get_entry<T>(bE, kv);
+  if (dx == -1 && dy == 0) return get_entry<T>(bE, kv - 1);
+  if (dx == 0 && dy == 1) return get_entry<T>(bN, kv);
+  if (dx == 0 && dy == -1) return get_entry<T>(bN, kv - pitch);
+  if (dx == 1 && dy == 1) return get_entry<T>(bNE, kv);
+  return get_entry<T>(bNE, kv - pitch - 1);  // dx == dy == -1
 }
 
 __host__ __device__ constexpr bool in_stencil(int dx, int dy) {
@@ -106,11 +108,10 @@ __host__ __device__ constexpr bool in_stencil(int dx, int dy) {
          (dx == -1 && dy == -1);
 }
 
-template <int TX, int TY>
-__device__ __forceinline__ double coarse_entry(const double* bC, const double* bE,
-                                               const double* bN, const double* bNE, size_t kf,
-                                               int pf) {
-  double acc = 0.0;
+template <typename T, int TX, int TY>
+__device__ __forceinline__ T coarse_entry(const double* bC, const double* bE, const double* bN,
+                                          const double* bNE, size_t kf, int pf) {
+  T acc = 0;
 #pragma unroll
   for (int p = 0; p < 7; ++p) {
 #pragma unroll
@@ -118,15 +119,17 @@ __device__ __forceinline__ double coarse_entry(const double* bC, const double* b
       const int dx = 2 * TX + kSX[q] - kSX[p];
       const int dy = 2 * TY + kSY[q] - kSY[p];
       if (in_stencil(dx, dy)) {
-        const double w = (p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5);
+        const T w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
         const size_t kv = kf + (long)kSY[p] * pf + kSX[p];
-        acc = fma(w, fine_entry(bC, bE, bN, bNE, kv, dx, dy, pf), acc);
+        acc = fma(w, fine_entry<T>(bC, bE, bN, bNE, kv, dx, dy, pf), acc);
       }
     }
   }
   return acc;
 }
 
+// T = double (FP64 mode) or dfloat (mixed modes: entries stored split, see put_entry)
+template <typename T>
 __global__ void k_coarsen_density2d(int nc, int pc, int pf, size_t stc, size_t stf,
                                     const double* __restrict__ fC,
                                     const double* __restrict__ fE,
@@ -139,12 +142,13 @@ __global__ void k_coarsen_density2d(int nc, int pc, int pf, size_t stc, size_t s
   if (I >= nc || J >= nc) return;
   const size_t kf = blockIdx.z * stf + at(2 * I, 2 * J, pf);
   const size_t kc = blockIdx.z * stc + at(I, J, pc);
-  cC[kc] = coarse_entry<0, 0>(fC, fE, fN, fNE, kf, pf);
+  put_entry(cC, kc, coarse_entry<T, 0, 0>(fC, fE, fN, fNE, kf, pf));
   // couplings to coarse neighbours outside the interior are never read; skip them so no
   // fine entry beyond the interior is touched
-  if (I + 1 < nc) cE[kc] = coarse_entry<1, 0>(fC, fE, fN, fNE, kf, pf);
-  if (J + 1 < nc) cN[kc] = coarse_entry<0, 1>(fC, fE, fN, fNE, kf, pf);
-  if (I + 1 < nc && J + 1 < nc) cNE[kc] = coarse_entry<1, 1>(fC, fE, fN, fNE, kf, pf);
+  if (I + 1 < nc) put_entry(cE, kc, coarse_entry<T, 1, 0>(fC, fE, fN, fNE, kf, pf));
+  if (J + 1 < nc) put_entry(cN, kc, coarse_entry<T, 0, 1>(fC, fE, fN, fNE, kf, pf));
+  if (I + 1 < nc && J + 1 < nc)
+    put_entry(cNE, kc, coarse_entry<T, 1, 1>(fC, fE, fN, fNE, kf, pf));
 }
 
 // ---- T3 class sums -----------------------------------------------------------------------
@@ -290,7 +294,7 @@ __global__ void k_t3_finalize2d(int chunks, double h2, size_t pst, size_t tst,
 
 __global__ void k_gather_level1_2d(int n, int pitch, size_t st, const double* __restrict__ gA_pad,
                                    const double* __restrict__ gM_pad,
-                                   const double* __restrict__ t1_pad, Density2D b,
+                                   const double* __restrict__ t1_pad, Density2D b, int split,
                                    double* __restrict__ gA, double* __restrict__ gM,
                                    double* __restrict__ t1, double* __restrict__ B1) {
   const int m = n - 1;
@@ -305,18 +309,19 @@ __global__ void k_gather_level1_2d(int n, int pitch, size_t st, const double* __
   t1[q] = t1_pad[k];
   double* row = B1 + blockIdx.y * nh * nh + (size_t)p * nh;
   for (int q = 0; q < m * m; ++q) row[q] = 0.0;
-  row[p] = b.C[k];
-  auto put = [&](int di, int dj, double v) {
+  const bool sp = split != 0;  // entries stored as double-float splits (mixed modes)
+  row[p] = entry_fp64(b.C, k, sp);
+  auto put = [&](int di, int dj, const double* a, size_t ka) {
     const int ii = i + di, jj = j + dj;
     if (ii < 1 || jj < 1 || ii >= n || jj >= n) return;
-    row[(ii - 1) + (jj - 1) * m] = v;
+    row[(ii - 1) + (jj - 1) * m] = entry_fp64(a, ka, sp);
   };
-  put(1, 0, b.E[k]);
-  put(-1, 0, b.E[k - 1]);
-  put(0, 1, b.N[k]);
-  put(0, -1, b.N[k - pitch]);
-  put(1, 1, b.NE[k]);
-  put(-1, -1, b.NE[k - pitch - 1]);
+  put(1, 0, b.E, k);
+  put(-1, 0, b.E, k - 1);
+  put(0, 1, b.N, k);
+  put(0, -1, b.N, k - pitch);
+  put(1, 1, b.NE, k);
+  put(-1, -1, b.NE, k - pitch - 1);
 }
 
 // a block takes blockDim.x columns (whole warps, up to kSumThreads) of kSumRows rows
@@ -346,18 +351,24 @@ void nload_density2d_df(const Grid& g, SplitVec u, double* nl, const Density2D& 
 }
 
 void coarsen_density2d(const Grid& fine, const Grid& coarse, const Density2D& bf,
-                       const Density2D& bc, cudaStream_t s) {
-  k_coarsen_density2d<<<grid_of(fine, coarse.n - 1, coarse.n - 1), dim3(fine.bx, fine.by), 0,
-                        s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride,
-                             bf.C, bf.E, bf.N, bf.NE, bc.C, bc.E, bc.N, bc.NE);
+                       const Density2D& bc, cudaStream_t s, bool split) {
+  const dim3 grid = grid_of(fine, coarse.n - 1, coarse.n - 1), block(fine.bx, fine.by);
+  if (split)
+    k_coarsen_density2d<dfloat><<<grid, block, 0, s>>>(
+        coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, bf.C, bf.E, bf.N,
+        bf.NE, bc.C, bc.E, bc.N, bc.NE);
+  else
+    k_coarsen_density2d<double><<<grid, block, 0, s>>>(
+        coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, bf.C, bf.E, bf.N,
+        bf.NE, bc.C, bc.E, bc.N, bc.NE);
 }
 
 void gather_level1_2d(const Grid& g1, const double* gA_pad, const double* gM_pad,
                       const double* t1_pad, const Density2D& b1, double* gA, double* gM,
-                      double* t1, double* B1, cudaStream_t s) {
+                      double* t1, double* B1, cudaStream_t s, bool split) {
   const int m = g1.n - 1;
   k_gather_level1_2d<<<dim3((m * m + 63) / 64, g1.nb), 64, 0, s>>>(
-      g1.n, g1.pitch, g1.stride, gA_pad, gM_pad, t1_pad, b1, gA, gM, t1, B1);
+      g1.n, g1.pitch, g1.stride, gA_pad, gM_pad, t1_pad, b1, split ? 1 : 0, gA, gM, t1, B1);
 }
 
 size_t t3_partials2d(const Grid& fine, int n1) {

@@ -105,6 +105,26 @@ __device__ __forceinline__ T get(const SplitVec& u, size_t k) {
   return dfloat(u.hi[k], u.lo[k]);
 }
 
+// A density-stencil entry: FP64, or (mixed-precision modes) its double-float split stored in
+// the same 8 bytes as (hi, lo), so the coarsening chain stays in double-float arithmetic.
+__device__ __forceinline__ void put_entry(double* p, size_t k, double v) { p[k] = v; }
+__device__ __forceinline__ void put_entry(double* p, size_t k, dfloat v) {
+  reinterpret_cast<float2*>(p)[k] = make_float2(v.hi, v.lo);
+}
+template <typename T>
+__device__ __forceinline__ T get_entry(const double* __restrict__ p, size_t k) {
+  return p[k];
+}
+template <>
+__device__ __forceinline__ dfloat get_entry<dfloat>(const double* __restrict__ p, size_t k) {
+  const float2 v = reinterpret_cast<const float2*>(p)[k];
+  return dfloat(v.x, v.y);
+}
+// an entry as FP64 whichever way it is stored
+__device__ __forceinline__ double entry_fp64(const double* __restrict__ p, size_t k, bool split) {
+  return split ? to_double(get_entry<dfloat>(p, k)) : p[k];
+}
+
 // result of a T computation as FP64
 __device__ __forceinline__ double out_of(double v) { return v; }
 __device__ __forceinline__ double out_of(float v) { return (double)v; }

@@ -132,9 +132,10 @@ void lv_nload_density_df(Level& l, const double* u, double* nl, cudaStream_t s) 
   if (l.g.dim == 2) nload_density2d_df(l.g, v, nl, l.b, s);
   else nload_density3d_df(l.g, v, nl, l.b3, s);
 }
-void lv_coarsen_density(Level& fl, Level& cl, cudaStream_t s) {
-  if (fl.g.dim == 2) coarsen_density2d(fl.g, cl.g, fl.b, cl.b, s);
-  else coarsen_density3d(fl.g, cl.g, fl.b3, cl.b3, s);
+// split: the density stencils hold double-float splits (mixed modes, from the _df kernels)
+void lv_coarsen_density(Level& fl, Level& cl, cudaStream_t s, bool split) {
+  if (fl.g.dim == 2) coarsen_density2d(fl.g, cl.g, fl.b, cl.b, s, split);
+  else coarsen_density3d(fl.g, cl.g, fl.b3, cl.b3, s, split);
 }
 void lv_t3(Level& l, int n1, const double* u, double* partials, double* t3, cudaStream_t s) {
   if (l.g.dim == 2) t3_moments2d(l.g, n1, u, l.pw, l.t3map, partials, t3, s);
@@ -148,12 +149,13 @@ void lv_start(Level& l1, double* c, int cstride, cudaStream_t s) {
   if (l1.g.dim == 2) start_vector(l1.g, c, cstride, s);
   else start_vector3d(l1.g, c, cstride, s);
 }
-void lv_gather_level1(Level& l1, double* gA, double* gM, double* t1, double* B1, cudaStream_t s) {
+void lv_gather_level1(Level& l1, double* gA, double* gM, double* t1, double* B1, cudaStream_t s,
+                      bool split) {
   if (l1.g.dim == 2) {
-    gather_level1_2d(l1.g, l1.y, l1.z, l1.r, l1.b, gA, gM, t1, B1, s);
+    gather_level1_2d(l1.g, l1.y, l1.z, l1.r, l1.b, gA, gM, t1, B1, s, split);
   } else {
     gather_vec3d(l1.g, l1.y, l1.z, l1.r, gA, gM, t1, s);
-    density_dense3d(l1.g, l1.b3, B1, s);
+    density_dense3d(l1.g, l1.b3, B1, s, split);
   }
 }
 
@@ -786,7 +788,7 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
     dot(ut, l.r, st, h->partials2, h->t0, b1, nb, st);
     for (int j = k; j >= 2; --j) {
       lv_restrict(h->L(j), h->L(j - 1), h->L(j).r, h->L(j - 1).r, b1);
-      lv_coarsen_density(h->L(j), h->L(j - 1), b1);
+      lv_coarsen_density(h->L(j), h->L(j - 1), b1, h->mixed());
     }
   }
   // branch 2 (side 1): T3 per coarse simplex
@@ -807,7 +809,7 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
   }
   join_sides(h, s, 0, 2);
   Level& l1 = h->L(1);
-  lv_gather_level1(l1, h->gAd, h->gMd, h->t1d, h->B1d, s);
+  lv_gather_level1(l1, h->gAd, h->gMd, h->t1d, h->B1d, s, h->mixed());
 }
 
 DenseProblem dense_augmented(fmg_eig_handle* h) {

@@ -134,12 +134,14 @@ void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D
 // double-float versions from the split u (mixed-precision modes)
 void rhs3d_df(const Grid& g, const double* lam, const PotentialParams* p_dev, SplitVec u,
               double* f, cudaStream_t s);
+// (the _df versions write the density stencil as double-float splits: see put_entry)
 void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& b,
                         cudaStream_t s);
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,
-                       const Density3D& bc, cudaStream_t s);
+                       const Density3D& bc, cudaStream_t s, bool split = false);
 void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaStream_t s);
-void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s);
+void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s,
+                     bool split = false);
 void gather_vec3d(const Grid& g, const double* a, const double* b, const double* c, double* oa,
                   double* ob, double* oc, cudaStream_t s);
 void start_vector3d(const Grid& g, double* c, int cstride, cudaStream_t s);
@@ -255,8 +257,9 @@ void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D
 void nload_density2d_df(const Grid& g, SplitVec u, double* nl, const Density2D& b,
                         cudaStream_t s);
 // Galerkin coarsening of the density stencil: bc = P^T bf P.
+// split: the entries are stored as double-float splits (mixed modes; see nload_density*_df)
 void coarsen_density2d(const Grid& fine, const Grid& coarse, const Density2D& bf,
-                       const Density2D& bc, cudaStream_t s);
+                       const Density2D& bc, cudaStream_t s, bool split = false);
 // T3^T_abc = int_T u mu_a mu_b mu_c per coarse triangle (10 per triangle, a <= b <= c,
 // lexicographic), from per-class monomial sums.  pw: (x/r)^m table of the level, map: the
 // level's 2 x 10 x 25 map (t3_map2d), partials: t3_partials2d(fine, n1) doubles.
@@ -270,7 +273,7 @@ void t3_power_table(int r, double* out);  // 4 * (r + 1) doubles
 // level-1 vectors and the level-1 density stencil (per instance, back to back)
 void gather_level1_2d(const Grid& g1, const double* gA_pad, const double* gM_pad,
                       const double* t1_pad, const Density2D& b1, double* gA, double* gM,
-                      double* t1, double* B1, cudaStream_t s);
+                      double* t1, double* B1, cudaStream_t s, bool split = false);
 
 // ---- Dense small solves (dense.cu) -------------------------------------------------------
 // A batch of problems shares the geometry (tri, adj) and keeps the per-instance arrays

@@ -456,9 +456,10 @@ __global__ void __launch_bounds__(256, MINB)
   T v, e[8];
   star3<T, true>(u, k, pitch, plane, v, e);
   nl[k] = out_of(s140 * v);
-  b.a[0][k] = out_of(s210 * e[0]);
+  // the density stencil: FP64, or kept split (double-float) in the mixed modes
+  put_entry(b.a[0], k, s210 * e[0]);
 #pragma unroll
-  for (int d = 0; d < 7; ++d) b.a[1 + d][k] = out_of(s420 * e[1 + d]);
+  for (int d = 0; d < 7; ++d) put_entry(b.a[1 + d], k, s420 * e[1 + d]);
 }
 
 // Galerkin coarsening of the 15-point density stencil: Bc(a, b) = sum P_va P_wb B(v, w) over
@@ -473,21 +474,21 @@ __device__ __forceinline__ int nb_of(int dx, int dy, int dz) {
   return -1;
 }
 
-__device__ __forceinline__ double fine_entry3(const Density3D& f, size_t kv, int code,
-                                              int pitch, long plane) {
-  if (code == 0) return f.a[0][kv];
+template <typename V>
+__device__ __forceinline__ V fine_entry3(const Density3D& f, size_t kv, int code, int pitch,
+                                         long plane) {
+  if (code == 0) return get_entry<V>(f.a[0], kv);
   const int d = (code - 1) >> 1;
-  if (((code - 1) & 1) == 0) return f.a[1 + d][kv];
-  return f.a[1 + d][kv - dir_off(d, pitch, plane)];
+  if (((code - 1) & 1) == 0) return get_entry<V>(f.a[1 + d], kv);
+  return get_entry<V>(f.a[1 + d], kv - dir_off(d, pitch, plane));
 }
 
-template <int T>
-__device__ __forceinline__ double coarse_entry3(const Density3D& f, size_t kf, int pf,
-                                                long planef) {
+template <typename V, int T>
+__device__ __forceinline__ V coarse_entry3(const Density3D& f, size_t kf, int pf, long planef) {
   // target offset in coarse units: T = 0 self, 1 + d for +d
   const int tx = T == 0 ? 0 : kDir[T - 1][0], ty = T == 0 ? 0 : kDir[T - 1][1],
             tz = T == 0 ? 0 : kDir[T - 1][2];
-  double acc = 0.0;
+  V acc = 0;
 #pragma unroll
   for (int p = 0; p < 15; ++p) {
     const int px = p == 0 ? 0 : ((p - 1) & 1 ? -kDir[(p - 1) >> 1][0] : kDir[(p - 1) >> 1][0]);
@@ -500,15 +501,17 @@ __device__ __forceinline__ double coarse_entry3(const Density3D& f, size_t kf, i
       const int qz = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][2] : kDir[(q - 1) >> 1][2]);
       const int code = nb_of(2 * tx + qx - px, 2 * ty + qy - py, 2 * tz + qz - pz);
       if (code >= 0) {
-        const double w = (p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5);
+        const V w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
         const size_t kv = kf + px + (long)py * pf + (long)pz * planef;
-        acc = fma(w, fine_entry3(f, kv, code, pf, planef), acc);
+        acc = fma(w, fine_entry3<V>(f, kv, code, pf, planef), acc);
       }
     }
   }
   return acc;
 }
 
+// V = double (FP64 mode) or dfloat (mixed modes: entries stored split, see put_entry)
+template <typename V>
 __global__ void k_coarsen_density3d(int nc, int pc, int pf, size_t stc, size_t stf,
                                     Density3D f, Density3D c) {
   const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -519,20 +522,22 @@ __global__ void k_coarsen_density3d(int nc, int pc, int pf, size_t stc, size_t s
   const long planef = (long)(2 * nc + 1) * pf;
   const size_t kf = ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
   const size_t kc = ib * stc + ((size_t)L * (nc + 1) + J) * pc + I;
-  c.a[0][kc] = coarse_entry3<0>(f, kf, pf, planef);
+  put_entry(c.a[0], kc, coarse_entry3<V, 0>(f, kf, pf, planef));
   // couplings to coarse neighbours outside the interior are never read: skip them
-  if (I + 1 < nc) c.a[1][kc] = coarse_entry3<1>(f, kf, pf, planef);
-  if (J + 1 < nc) c.a[2][kc] = coarse_entry3<2>(f, kf, pf, planef);
-  if (L + 1 < nc) c.a[3][kc] = coarse_entry3<3>(f, kf, pf, planef);
-  if (I + 1 < nc && J + 1 < nc) c.a[4][kc] = coarse_entry3<4>(f, kf, pf, planef);
-  if (I + 1 < nc && L + 1 < nc) c.a[5][kc] = coarse_entry3<5>(f, kf, pf, planef);
-  if (J + 1 < nc && L + 1 < nc) c.a[6][kc] = coarse_entry3<6>(f, kf, pf, planef);
-  if (I + 1 < nc && J + 1 < nc && L + 1 < nc) c.a[7][kc] = coarse_entry3<7>(f, kf, pf, planef);
+  if (I + 1 < nc) put_entry(c.a[1], kc, coarse_entry3<V, 1>(f, kf, pf, planef));
+  if (J + 1 < nc) put_entry(c.a[2], kc, coarse_entry3<V, 2>(f, kf, pf, planef));
+  if (L + 1 < nc) put_entry(c.a[3], kc, coarse_entry3<V, 3>(f, kf, pf, planef));
+  if (I + 1 < nc && J + 1 < nc) put_entry(c.a[4], kc, coarse_entry3<V, 4>(f, kf, pf, planef));
+  if (I + 1 < nc && L + 1 < nc) put_entry(c.a[5], kc, coarse_entry3<V, 5>(f, kf, pf, planef));
+  if (J + 1 < nc && L + 1 < nc) put_entry(c.a[6], kc, coarse_entry3<V, 6>(f, kf, pf, planef));
+  if (I + 1 < nc && J + 1 < nc && L + 1 < nc)
+    put_entry(c.a[7], kc, coarse_entry3<V, 7>(f, kf, pf, planef));
 }
 
 // dense level-1 matrices from a 15-point stencil given per node as (C, +d couplings)
+// split: the stencil entries are stored as double-float splits (density, mixed modes)
 __global__ void k_dense15(int n, int pitch, size_t vst, Stencil15 st, int use_stencil,
-                          double* out, double mass_h3) {
+                          double* out, double mass_h3, int split = 0) {
   const double* const* a = use_stencil ? st.a : nullptr;
   const int m = n - 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -544,14 +549,15 @@ __global__ void k_dense15(int n, int pitch, size_t vst, Stencil15 st, int use_st
   const size_t nh = (size_t)m * m * m;
   double* row = out + blockIdx.y * nh * nh + (size_t)p * nh;
   for (int q = 0; q < m * m * m; ++q) row[q] = 0.0;
-  row[p] = a ? a[0][k] : 0.4 * mass_h3;
+  const bool sp = split != 0;
+  row[p] = a ? entry_fp64(a[0], k, sp) : 0.4 * mass_h3;
   for (int d = 0; d < 7; ++d)
     for (int sg = -1; sg <= 1; sg += 2) {
       const int ii = i + sg * kDir[d][0], jj = j + sg * kDir[d][1], ll = l + sg * kDir[d][2];
       if (ii < 1 || jj < 1 || ll < 1 || ii >= n || jj >= n || ll >= n) continue;
       const size_t kn = base + (size_t)ll * plane + (size_t)jj * pitch + ii;
       double v;
-      if (a) v = sg > 0 ? a[1 + d][k] : a[1 + d][kn];
+      if (a) v = entry_fp64(a[1 + d], sg > 0 ? k : kn, sp);
       else v = mass_h3 * ((d >= 3 && d < 6) ? 1.0 / 30.0 : 1.0 / 20.0);
       row[(ii - 1) + (size_t)(jj - 1) * m + (size_t)(ll - 1) * m * m] = v;
     }
@@ -689,10 +695,14 @@ void rhs3d_df(const Grid& g, const double* lam, const PotentialParams* p, SplitV
 }
 
 void coarsen_density3d(const Grid& fine, const Grid& coarse, const Density3D& bf,
-                       const Density3D& bc, cudaStream_t s) {
-  k_coarsen_density3d<<<grid3(fine, coarse.n - 1, coarse.n - 1, coarse.n - 1), block3(fine), 0,
-                        s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, bf,
-                             bc);
+                       const Density3D& bc, cudaStream_t s, bool split) {
+  const dim3 grid = grid3(fine, coarse.n - 1, coarse.n - 1, coarse.n - 1);
+  if (split)
+    k_coarsen_density3d<dfloat><<<grid, block3(fine), 0, s>>>(
+        coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, bf, bc);
+  else
+    k_coarsen_density3d<double><<<grid, block3(fine), 0, s>>>(
+        coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, bf, bc);
 }
 
 void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaStream_t s) {
@@ -704,11 +714,12 @@ void dense_level1_3d(const Grid& g, const Coef3D& c, double* L, double* M, cudaS
   k_dense15<<<grid, 64, 0, s>>>(g.n, g.pitch, g.stride, st, 0, M, g.h * g.h * g.h);
 }
 
-void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s) {
+void density_dense3d(const Grid& g, const Density3D& b, double* B, cudaStream_t s, bool split) {
   const int m = g.n - 1, cnt = m * m * m;
   Stencil15 st;
   for (int q = 0; q < 8; ++q) st.a[q] = b.a[q];
-  k_dense15<<<dim3((cnt + 63) / 64, g.nb), 64, 0, s>>>(g.n, g.pitch, g.stride, st, 1, B, 0.0);
+  k_dense15<<<dim3((cnt + 63) / 64, g.nb), 64, 0, s>>>(g.n, g.pitch, g.stride, st, 1, B, 0.0,
+                                                       split ? 1 : 0);
 }
 
 void gather_vec3d(const Grid& g, const double* a, const double* b, const double* c, double* oa,
