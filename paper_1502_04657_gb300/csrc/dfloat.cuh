@@ -87,13 +87,6 @@ __device__ __forceinline__ double f2d_exact(float f) {
 
 __device__ __forceinline__ double to_double(dfloat x) { return f2d_exact(x.hi) + f2d_exact(x.lo); }
 
-// FP64 -> double-float, rounded to nearest in both halves (the 5 lowest bits of the FP64
-// significand are rounded away)
-__device__ __forceinline__ dfloat split_double(double v) {
-  const float hi = __double2float_rn(v);
-  return dfloat(hi, __double2float_rn(v - (double)hi));
-}
-
 // The nonlinear kernels read u either as FP64 or as its split copy (SplitVec: hi and lo
 // arrays written by split_df) and compute in T.
 template <typename T>

@@ -183,7 +183,6 @@ void split_df(const double* u, float* hi, float* lo, size_t n, cudaStream_t s);
 // `bf` is set (FMG_MIXED_BF16; arithmetic stays FP32).  Bytes per element:
 size_t mixed_elem_bytes(bool bf16_storage);
 // contiguous conversions over n entries (all instances of a level at once)
-void to_f32(const double* a, float* b, size_t n, cudaStream_t s, bool bf = false);
 void add_f32(const float* e, double* x, size_t n, cudaStream_t s, bool bf = false);  // x += e
 // r = f - L x with the FP64 operator of the level (2D uses c2, 3D c3), stored single
 void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const double* f,

@@ -38,13 +38,6 @@ const S* sp(const float* p) {
 
 // ---- conversions and the FP64 ends of the defect correction ----------------------------
 // (contiguous over all instances: the arrays hold the instances back to back)
-template <typename S>
-__global__ void k_to_s(size_t n, const double* __restrict__ a, S* __restrict__ b) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    st(b, i, (float)a[i]);
-}
-
 // double-float split of an FP64 vector (the nonlinear kernels of the mixed modes read it)
 __global__ void k_split_df(size_t n, const double* __restrict__ u, float* __restrict__ hi,
                            float* __restrict__ lo) {
@@ -430,11 +423,6 @@ void prolong_t(const Grid& fine, const Grid& coarse, const float* ec, float* xf,
 }  // namespace
 
 size_t mixed_elem_bytes(bool bf16_storage) { return bf16_storage ? sizeof(bf16) : sizeof(float); }
-
-void to_f32(const double* a, float* b, size_t n, cudaStream_t s, bool bf) {
-  if (bf) k_to_s<bf16><<<blocks_for(n), 256, 0, s>>>(n, a, sp<bf16>(b));
-  else k_to_s<float><<<blocks_for(n), 256, 0, s>>>(n, a, b);
-}
 
 void add_f32(const float* e, double* x, size_t n, cudaStream_t s, bool bf) {
   if (bf) k_add_s<bf16><<<blocks_for(n), 256, 0, s>>>(n, sp<bf16>(e), x);
