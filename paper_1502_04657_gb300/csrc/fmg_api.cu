@@ -777,14 +777,25 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
   Level& l = h->L(k);
   const int nb = l.g.nb;
   const size_t st = l.g.stride;
+  // FP64 mode: N(u~) and B(u~) run alone first.  Every kernel of the pass is bound by the
+  // FP64 pipe, so running the T3 sums and the operator applies beside it gains nothing; the
+  // branches below then overlap the short restriction / coarsening chains.  The mixed modes
+  // compute it in double-float on the FP32 pipes, beside the FP64 T3 sums and applies.
+  if (!h->mixed()) {
+    prof_begin(h, kProfMoments, k, s);
+    lv_nload_density(l, ut, l.r, s);
+    prof_end(h, kProfMoments, k, s);
+  }
   fork_sides(h, s, 0, 2);
-  // branch 1 (side 0): N(u~) and B(u~), T0, and the restriction / coarsening chains of both
+  // branch 1 (side 0): N(u~) and B(u~) (mixed modes), T0, and the restriction / coarsening
+  // chains of both
   {
     const cudaStream_t b1 = h->side[0];
-    prof_begin(h, kProfMoments, k, b1);
-    if (h->mixed()) lv_nload_density_df(l, ut, l.r, b1);
-    else lv_nload_density(l, ut, l.r, b1);
-    prof_end(h, kProfMoments, k, b1);
+    if (h->mixed()) {
+      prof_begin(h, kProfMoments, k, b1);
+      lv_nload_density_df(l, ut, l.r, b1);
+      prof_end(h, kProfMoments, k, b1);
+    }
     dot(ut, l.r, st, h->partials2, h->t0, b1, nb, st);
     for (int j = k; j >= 2; --j) {
       lv_restrict(h->L(j), h->L(j - 1), h->L(j).r, h->L(j - 1).r, b1);
