@@ -117,7 +117,11 @@ def test_tma_sweeps_bit_identical_to_register_blocked(precision):
     kws = [dict(dim=2, coarse_cells=8, levels=8, w_quad=(1.0, 4.0, 0.0), zeta=25.0),
            dict(dim=2, coarse_cells=8, levels=7, w_quad=(1.0, 1.0, 0.0), zeta=80.0),
            dict(dim=2, coarse_cells=4, levels=9, w_quad=(1.0, 9.0, 0.0), zeta=5.0),
-           dict(dim=3, coarse_cells=4, levels=6, w_quad=(1.0, 1.0, 4.0), zeta=30.0)]
+           dict(dim=3, coarse_cells=4, levels=6, w_quad=(1.0, 1.0, 4.0), zeta=30.0),
+           # ragged tiles: n = 768 (2D: 767 nodes per side, 5 full tiles + 127 columns) and
+           # n = 192 (3D: 191 nodes per side, partial tiles in every direction)
+           dict(dim=2, coarse_cells=6, levels=8, w_quad=(2.0, 1.0, 0.0), zeta=40.0),
+           dict(dim=3, coarse_cells=3, levels=7, w_quad=(1.0, 2.0, 1.0), zeta=20.0)]
     probs = [fmg.Problem(**kw, precision=precision) for kw in kws]
     plain = [fmg.Problem(**kw, precision=precision, flags=fmg.FMG_FLAG_NO_TMA) for kw in kws]
     for p, q in zip(probs, plain):
