@@ -46,34 +46,31 @@ __global__ void k_nload_density2d(int n, int pitch, size_t st, T s60, T s90, T s
   const T up = get<T>(u, k);
   const T nE = get<T>(u, k + 1), nNE = get<T>(u, k + pitch + 1), nN = get<T>(u, k + pitch);
   const T nW = get<T>(u, k - 1), nSW = get<T>(u, k - pitch - 1), nS = get<T>(u, k - pitch);
-  const T s1 = ((nE + nNE) + (nN + nW)) + (nSW + nS);
+  // the cubic load through the pair sums m_k = n_k + n_{k+1} (see nload_at in grid2d.cu)
+  const T m0 = nE + nNE, m1 = nNE + nN, m2 = nN + nW, m3 = nW + nSW, m4 = nSW + nS,
+          m5 = nS + nE;
   const T qE = nE * nE, qNE = nNE * nNE, qN = nN * nN, qW = nW * nW, qSW = nSW * nSW,
           qS = nS * nS;
+  const T M1 = ((m0 + m1) + (m2 + m3)) + (m4 + m5);  // 2 S1
+  T M2 = m0 * m0;
+  M2 = fma(m1, m1, M2);
+  M2 = fma(m2, m2, M2);
+  M2 = fma(m3, m3, M2);
+  M2 = fma(m4, m4, M2);
+  M2 = fma(m5, m5, M2);
   const T s2 = ((qE + qNE) + (qN + qW)) + (qSW + qS);
-  T s3 = qE * nE;
-  s3 = fma(qNE, nNE, s3);
-  s3 = fma(qN, nN, s3);
-  s3 = fma(qW, nW, s3);
-  s3 = fma(qSW, nSW, s3);
-  s3 = fma(qS, nS, s3);
-  const T p0 = nE * nNE, p1 = nNE * nN, p2 = nN * nW, p3 = nW * nSW, p4 = nSW * nS,
-          p5 = nS * nE;
-  const T pp = ((p0 + p1) + (p2 + p3)) + (p4 + p5);
-  T qq = p0 * (nE + nNE);
-  qq = fma(p1, nNE + nN, qq);
-  qq = fma(p2, nN + nW, qq);
-  qq = fma(p3, nW + nSW, qq);
-  qq = fma(p4, nSW + nS, qq);
-  qq = fma(p5, nS + nE, qq);
+  T M3 = m0 * (qE + qNE);
+  M3 = fma(m1, qNE + qN, M3);
+  M3 = fma(m2, qN + qW, M3);
+  M3 = fma(m3, qW + qSW, M3);
+  M3 = fma(m4, qSW + qS, M3);
+  M3 = fma(m5, qS + qE, M3);
   const T u2 = up * up;
-  T v = T(24) * u2 * up;
-  v = fma(T(6) * u2, s1, v);
-  v = fma(T(2) * up, fma(T(2), s2, pp), v);
-  v = fma(T(2), s3, v);
-  nl[k] = out_of(s60 * (v + qq));
+  const T s2p = fma(T(0.5), M2, s2);  // 2 S2 + P
+  nl[k] = out_of(s60 * (fma(T(2) * up, s2p, u2 * fma(T(24), up, T(3) * M1)) + M3));
   // density stencil: FP64, or kept split (double-float) in the mixed modes for the coarsening
   // diagonal: sum over the six triangles
-  put_entry(bC, k, s90 * fma(T(36), u2, fma(T(2), s2, fma(T(6) * up, s1, pp))));
+  put_entry(bC, k, s90 * fma(T(36), u2, fma(T(3) * up, M1, s2p)));
   // edge p-q shared by the triangles closed by r1 and r2
   const T u26 = T(6) * u2;
   put_entry(bE, k, s180 * fma(T(6), qE,

@@ -188,6 +188,10 @@ __global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
 // triangle with p), summing int_K u^3 lambda_p = |K|/60 sum_{|b|=3} u^b (b_p + 1) gives
 //   |K|/60 [24u^3 + 6u^2 S1 + 2u(2 S2 + P) + 2 S3 + Q],
 // S_q = sum n_k^q, P = sum n_k n_{k+1}, Q = sum n_k n_{k+1} (n_k + n_{k+1}), |K| = h^2/2.
+// Evaluated through the pair sums m_k = n_k + n_{k+1} and squares q_k = n_k^2, with
+// 2 S1 = M1 = sum m_k, 2 (2 S2 + P) = M2 + 2 S2 (M2 = sum m_k^2) and
+// 2 S3 + Q = M3 = sum m_k (q_k + q_{k+1}):
+//   |K|/60 [u^2 (24u + 3 M1) + u (M2 + 2 S2) + M3]   (47 FP64 instructions instead of 55).
 // T is the arithmetic type: double in FP64 mode, double-float (u read as a SplitVec) in the
 // mixed-precision modes, float in the FP32 auxiliary right-hand side (k_rhs2d_f32).
 template <typename T = double, typename U = const double*>
@@ -195,29 +199,25 @@ __device__ __forceinline__ T nload_at(const U& u, size_t k, int pitch) {
   const T up = get<T>(u, k);
   const T n0 = get<T>(u, k + 1), n1 = get<T>(u, k + pitch + 1), n2 = get<T>(u, k + pitch);
   const T n3 = get<T>(u, k - 1), n4 = get<T>(u, k - pitch - 1), n5 = get<T>(u, k - pitch);
-  const T s1 = ((n0 + n1) + (n2 + n3)) + (n4 + n5);
+  const T m0 = n0 + n1, m1 = n1 + n2, m2 = n2 + n3, m3 = n3 + n4, m4 = n4 + n5, m5 = n5 + n0;
   const T q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = n3 * n3, q4 = n4 * n4, q5 = n5 * n5;
-  const T s2 = ((q0 + q1) + (q2 + q3)) + (q4 + q5);
-  T s3 = q0 * n0;
-  s3 = fma(q1, n1, s3);
-  s3 = fma(q2, n2, s3);
-  s3 = fma(q3, n3, s3);
-  s3 = fma(q4, n4, s3);
-  s3 = fma(q5, n5, s3);
-  const T p0 = n0 * n1, p1 = n1 * n2, p2 = n2 * n3, p3 = n3 * n4, p4 = n4 * n5, p5 = n5 * n0;
-  const T pp = ((p0 + p1) + (p2 + p3)) + (p4 + p5);
-  T qq = p0 * (n0 + n1);
-  qq = fma(p1, n1 + n2, qq);
-  qq = fma(p2, n2 + n3, qq);
-  qq = fma(p3, n3 + n4, qq);
-  qq = fma(p4, n4 + n5, qq);
-  qq = fma(p5, n5 + n0, qq);
+  const T M1 = ((m0 + m1) + (m2 + m3)) + (m4 + m5);
+  T M2 = m0 * m0;
+  M2 = fma(m1, m1, M2);
+  M2 = fma(m2, m2, M2);
+  M2 = fma(m3, m3, M2);
+  M2 = fma(m4, m4, M2);
+  M2 = fma(m5, m5, M2);
+  const T S2 = ((q0 + q1) + (q2 + q3)) + (q4 + q5);
+  T M3 = m0 * (q0 + q1);
+  M3 = fma(m1, q1 + q2, M3);
+  M3 = fma(m2, q2 + q3, M3);
+  M3 = fma(m3, q3 + q4, M3);
+  M3 = fma(m4, q4 + q5, M3);
+  M3 = fma(m5, q5 + q0, M3);
   const T u2 = up * up;
-  T v = T(24) * u2 * up;
-  v = fma(T(6) * u2, s1, v);
-  v = fma(T(2) * up, fma(T(2), s2, pp), v);
-  v = fma(T(2), s3, v);
-  return v + qq;
+  const T v = fma(up, fma(T(2), S2, M2), u2 * fma(T(24), up, T(3) * M1));
+  return v + M3;
 }
 
 __global__ void k_nload2d(int n, int pitch, size_t st, double scale, const double* __restrict__ u,
