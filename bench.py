@@ -78,13 +78,13 @@ N_SM = 152
 # Algorithmic FP64 flops and bytes per node of the finest-level launch:
 #   Jacobi 2D: 7-point L x (7 mul + 6 add) + residual + scale + update = 16 flop;
 #     24 B (x, f, x') + 40 B (4 couplings + omega/D)
-#   cubic load + density stencil 2D (closed forms over the 6 star triangles): 117 flop; 8 B
-#     read + 40 B written
+#   cubic load + density stencil 2D (closed forms over the 6 star triangles, through the pair
+#     sums n_k + n_{k+1}): 106 flop; 8 B read + 40 B written
 #   Jacobi 3D: 15-point = 29 + 3 = 32 flop; 24 B + 72 B
 #   cubic load + density stencil 3D (sums over the link of the 24-tetrahedron star: 345 flop
 #     for N, 305 for the density stencil, 9 scalings): 659 flop; 8 B + 72 B
 KERNELS = {
-    2: {"nload_density": (117.0, 48.0), "jacobi": (16.0, 64.0)},
+    2: {"nload_density": (106.0, 48.0), "jacobi": (16.0, 64.0)},
     3: {"nload_density": (659.0, 80.0), "jacobi": (32.0, 96.0)},
 }
 # the kernel with the largest share of the solve in the ncu launch lists
@@ -114,12 +114,12 @@ def hbm_peak() -> tuple[float, str]:
 # DRAM bytes per node of a finest-level launch from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum of the 9-level 2D launch, 4,190,209 nodes;
 # profiles/ncu_k_nload_density2d_h1-2048.md), scaled by the nodes a launch processes.
-TRAFFIC_PER_NODE = {(2, "nload_density"): (34.053376e6 + 105.419264e6) / 4190209,
+TRAFFIC_PER_NODE = {(2, "nload_density"): (34.024448e6 + 105.473792e6) / 4190209,
                     # the first level-9 sweep of the 9-level 2D solve, 4,190,209 nodes
                     # (profiles/ncu_k_jacobi2d_h1-2048.md)
                     (2, "jacobi"): (235150336 + 24169728) / 4190209,
                     # 3D: the 6-level launch, 2,048,383 nodes (profiles/ncu_k_nload_density3d_h1-128.md)
-                    (3, "nload_density"): (22.148608e6 + 82.583040e6) / 2048383}
+                    (3, "nload_density"): (22.133248e6 + 82.609920e6) / 2048383}
 
 
 def rank_info():
