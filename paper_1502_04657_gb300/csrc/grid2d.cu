@@ -194,14 +194,17 @@ __global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
 //   |K|/60 [u^2 (24u + 3 M1) + u (M2 + 2 S2) + M3]   (47 FP64 instructions instead of 55).
 // T is the arithmetic type: double in FP64 mode, double-float (u read as a SplitVec) in the
 // mixed-precision modes, float in the FP32 auxiliary right-hand side (k_rhs2d_f32).
+// M1 (twice the neighbour sum) is returned through m1_out when given: the mass stencil of
+// the right-hand side needs the same sum.
 template <typename T = double, typename U = const double*>
-__device__ __forceinline__ T nload_at(const U& u, size_t k, int pitch) {
+__device__ __forceinline__ T nload_at(const U& u, size_t k, int pitch, T* m1_out = nullptr) {
   const T up = get<T>(u, k);
   const T n0 = get<T>(u, k + 1), n1 = get<T>(u, k + pitch + 1), n2 = get<T>(u, k + pitch);
   const T n3 = get<T>(u, k - 1), n4 = get<T>(u, k - pitch - 1), n5 = get<T>(u, k - pitch);
   const T m0 = n0 + n1, m1 = n1 + n2, m2 = n2 + n3, m3 = n3 + n4, m4 = n4 + n5, m5 = n5 + n0;
   const T q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = n3 * n3, q4 = n4 * n4, q5 = n5 * n5;
   const T M1 = ((m0 + m1) + (m2 + m3)) + (m4 + m5);
+  if (m1_out) *m1_out = M1;
   T M2 = m0 * m0;
   M2 = fma(m1, m1, M2);
   M2 = fma(m2, m2, M2);
@@ -231,10 +234,10 @@ __global__ void k_rhs2d(int n, int pitch, size_t st, double h2_12, double h2_120
                         const double* __restrict__ u, double* __restrict__ f) {
   INTERIOR_2D
   const double nscale = pp[ib].zeta * h2_120;
-  const double s = ((u[k + 1] + u[k - 1]) + (u[k + pitch] + u[k - pitch])) +
-                   (u[k + pitch + 1] + u[k - pitch - 1]);
-  const double mu = h2_12 * fma(6.0, u[k], s);
-  f[k] = fma(lam[ib], mu, -nscale * nload_at(u, k, pitch));
+  double m1;  // twice the sum of the six neighbours
+  const double nl = nload_at(u, k, pitch, &m1);
+  const double mu = h2_12 * fma(6.0, u[k], 0.5 * m1);
+  f[k] = fma(lam[ib], mu, -nscale * nl);
 }
 
 // The same right-hand side in double-float arithmetic from the split u (mixed-precision
@@ -246,11 +249,9 @@ __global__ void k_rhs2d_df(int n, int pitch, size_t st, dfloat h2_12, dfloat h2_
                            const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
                            SplitVec u, double* __restrict__ f) {
   INTERIOR_2D
-  const dfloat s = ((get<dfloat>(u, k + 1) + get<dfloat>(u, k - 1)) +
-                    (get<dfloat>(u, k + pitch) + get<dfloat>(u, k - pitch))) +
-                   (get<dfloat>(u, k + pitch + 1) + get<dfloat>(u, k - pitch - 1));
-  const double mu = to_double(h2_12 * fma(dfloat(6), get<dfloat>(u, k), s));
-  const double nl = to_double(h2_120 * nload_at<dfloat>(u, k, pitch));
+  dfloat m1;  // twice the sum of the six neighbours
+  const double nl = to_double(h2_120 * nload_at<dfloat>(u, k, pitch, &m1));
+  const double mu = to_double(h2_12 * fma(dfloat(6), get<dfloat>(u, k), dfloat(0.5) * m1));
   f[k] = fma(lam[ib], mu, -pp[ib].zeta * nl);
 }
 
