@@ -176,9 +176,11 @@ __global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
   INTERIOR_2D
   const int ai = i & 1, aj = j & 1;
   const size_t kc = ib * stc + at(i >> 1, j >> 1, pc);
-  double e = ec[kc];
-  if (ai | aj) e = 0.5 * (e + ec[kc + ai + (size_t)aj * pc]);
-  if (add) e += xf[k];
+  // the midpoint value 0.5 (a + b) is added with one FMA (0.5 s is exact, so this rounds
+  // exactly as the separate multiply and add would)
+  const double a = ec[kc];
+  const double x = add ? xf[k] : 0.0;
+  double e = (ai | aj) ? fma(0.5, a + ec[kc + ai + (size_t)aj * pc], x) : a + x;
   if (extra) e = fma(scale[(size_t)ib * scale_stride], extra[k], e);
   xf[k] = e;
 }

@@ -261,9 +261,12 @@ __global__ void k_prolong3d(int nf, int pf, int pc, size_t st, size_t stc,
   const int nc = nf / 2;
   const long planec = (long)(nc + 1) * pc;
   const size_t kc = ib * stc + (size_t)(l >> 1) * planec + (size_t)(j >> 1) * pc + (i >> 1);
-  double e = ec[kc];
-  if (ai | aj | al) e = 0.5 * (e + ec[kc + ai + (size_t)aj * pc + (size_t)al * planec]);
-  if (add) e += xf[k];
+  // the midpoint value 0.5 (a + b) is added with one FMA (0.5 s is exact, so this rounds
+  // exactly as the separate multiply and add would)
+  const double a = ec[kc];
+  const double x = add ? xf[k] : 0.0;
+  double e = (ai | aj | al) ? fma(0.5, a + ec[kc + ai + (size_t)aj * pc + (size_t)al * planec], x)
+                            : a + x;
   if (extra) e = fma(scale[(size_t)ib * scale_stride], extra[k], e);
   xf[k] = e;
 }
