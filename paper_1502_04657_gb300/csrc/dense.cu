@@ -26,7 +26,9 @@
 //   G_uu = c_H^T B1 c_H + 2 c_u t1.c_H + c_u^2 T0
 // with w_c the coarse coefficients at T's vertices (0 on the boundary).
 //
-// One CTA of 512 threads per problem, a batch of problems one CTA each (enough warps to hide shared-memory and FP64 latency),
+// One CTA of 256 threads per problem, a batch of problems one CTA each (measured against 128
+// and 512: the solve is bound by barriers and latency on one SM, and 256 threads balance the
+// work per thread against the cost of each block-wide barrier),
 // everything in shared memory, fixed-order reductions, one barrier per elimination step and
 // warp-synchronous triangular solves.  The iteration count is bounded by max_iter; hitting it
 // sets status 1.
@@ -37,13 +39,19 @@
 namespace fmg {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;
+
+// the simplex-local blocks (ntri (nvert + 1)^2 doubles) fit in the n x n work matrix A
+__host__ __device__ inline bool loc_in_A(int n, int ntri, int nvert) {
+  return (size_t)ntri * (nvert + 1) * (nvert + 1) <= (size_t)n * n;
+}
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxVert = 4;
 constexpr double kSwitch = 1e-2;  // relative residual below which Newton takes over
 
 struct Smem {
-  double *K0, *MM, *G, *A, *B1, *loc;
+  double *K0, *MM, *G, *A, *loc;
+  const double* B1;
   double *c, *Mc, *Hc, *Gc, *r, *y1, *y2, *dinv, *red, *sv;
   int* sym3;  // nv^3 table of sorted-triple indices
   int *tri, *adj;  // shared copies of the simplex and adjacency tables
@@ -334,7 +342,15 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   s.MM = q; q += (size_t)n * n;
   s.G = q; q += (size_t)n * n;
   s.A = q; q += (size_t)n * n;
-  s.loc = q; q += (size_t)p.ntri * s.L * s.L;
+  // the simplex-local blocks are only live inside build_G, when A is free: they share its
+  // space when they fit (2D), which with B1 read from global memory keeps a 2D CTA under
+  // half the shared memory of an SM (two instances of a batch per SM)
+  if (loc_in_A(n, p.ntri, p.nvert)) {
+    s.loc = s.A;
+  } else {
+    s.loc = q;
+    q += (size_t)p.ntri * s.L * s.L;
+  }
   s.c = q; q += n;
   s.Mc = q; q += n;
   s.Hc = q; q += n;
@@ -349,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   s.t3 = q; q += p.aug ? (size_t)p.ntri * p.nt3 : 0;
   s.tri = reinterpret_cast<int*>(q); q += ((size_t)p.ntri * nv + 1) / 2;
   s.adj = reinterpret_cast<int*>(q); q += ((size_t)nh * p.maxadj + 1) / 2;
-  s.B1 = q;  // nh * nh when aug
+  s.B1 = p.aug ? p.B1 : nullptr;  // nh * nh in global memory (read twice per build_G)
   s.sym3 = sym3_tab;
 
   const double zeta = p.params->zeta;
@@ -371,7 +387,6 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
     s.MM[e] = mv;
   }
   if (p.aug) {
-    for (int e = threadIdx.x; e < nh * nh; e += kThreads) s.B1[e] = p.B1[e];
     for (int e = threadIdx.x; e < nh; e += kThreads) s.t1[e] = p.t1[e];
     for (int e = threadIdx.x; e < p.ntri * p.nt3; e += kThreads) s.t3[e] = p.t3[e];
   }
@@ -547,9 +562,10 @@ size_t dense_smem_bytes(int n, int ntri, int nvert, int aug) {
   const int L = nvert + 1, nh = n - aug;
   const size_t nt3 = nvert == 3 ? 10 : 20;
   const size_t maxadj = nvert == 3 ? 6 : 24;
-  return sizeof(double) * ((size_t)4 * n * n + (size_t)ntri * L * L + 8 * (size_t)n + 4 * kThreads +
-                           nh + (aug ? (size_t)ntri * nt3 : 0) + ((size_t)ntri * nvert + 1) / 2 +
-                           ((size_t)nh * maxadj + 1) / 2 + (aug ? (size_t)nh * nh : 0));
+  const size_t loc = loc_in_A(n, ntri, nvert) ? 0 : (size_t)ntri * L * L;
+  return sizeof(double) * ((size_t)4 * n * n + loc + 8 * (size_t)n + 4 * kThreads + nh +
+                           (aug ? (size_t)ntri * nt3 : 0) + ((size_t)ntri * nvert + 1) / 2 +
+                           ((size_t)nh * maxadj + 1) / 2);
 }
 
 void dense_scf(const DenseProblem& p, int nb, cudaStream_t s) {
@@ -563,6 +579,10 @@ cudaError_t dense_prepare(size_t need) {
   if (need > kDenseSmemLimit) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_dense_scf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kDenseSmemLimit);
+  if (e != cudaSuccess) return e;
+  // all of the unified L1 as shared memory, so that two small (2D) instances share an SM
+  e = cudaFuncSetAttribute(k_dense_scf, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spd_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kDenseSmemLimit);
