@@ -75,21 +75,21 @@ WORKLOADS = {
 }
 FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA per clock per SM (1.25 TFLOP/s nominal at 2070 MHz)
 N_SM = 152
-# Algorithmic FP64 flops and bytes per node of the finest-level launch (see DESIGN.md):
+# Algorithmic FP64 flops and bytes per node of the finest-level launch:
 #   Jacobi 2D: 7-point L x (7 mul + 6 add) + residual + scale + update = 16 flop;
 #     24 B (x, f, x') + 40 B (4 couplings + omega/D)
-#   cubic load + density stencil 2D (closed forms over the 6 star triangles, through the pair
-#     sums n_k + n_{k+1}): 106 flop; 8 B read + 40 B written
+#   cubic load + density stencil 2D (closed forms over the 6 star triangles from per-edge
+#     numbers: 3 own edges x 5 + square 1 + 3 six-term sums 15 + cubic bracket 8 + diagonal 6
+#     + 3 off-diagonal entries x 8): 69 flop; 8 B read + 40 B written
 #   Jacobi 3D: 15-point = 29 + 3 = 32 flop; 24 B + 72 B
 #   cubic load + density stencil 3D (sums over the link of the 24-tetrahedron star: 345 flop
 #     for N, 305 for the density stencil, 9 scalings): 659 flop; 8 B + 72 B
 KERNELS = {
-    2: {"nload_density": (106.0, 48.0), "jacobi": (16.0, 64.0)},
+    2: {"nload_density": (69.0, 48.0), "jacobi": (16.0, 64.0)},
     3: {"nload_density": (659.0, 80.0), "jacobi": (32.0, 96.0)},
 }
-# the kernel with the largest share of the solve in the ncu launch lists
-# (profiles/launches_config2_fp64.md: k_jacobi2d 20.6 %; launches_config3_fp64.md:
-# k_nload_density3d 32.8 %)
+# the kernel with the largest share of the solve in the ncu launch lists (2D FP64 solve:
+# k_jacobi2d 21 %; 3D FP64 solve: k_nload_density3d 35 %)
 DOMINANT = {2: "jacobi", 3: "nload_density"}
 # The single-precision V-cycle (mixed modes) is HBM-bound: a Jacobi sweep or residual reads x
 # and f and writes one vector, 3 x 4 bytes per node (3 x 2 with BF16 storage); the
@@ -98,7 +98,7 @@ MIXED_HBM_KERNELS = ("jacobi", "residual")
 # The mixed modes evaluate the cubic load + density stencil in double-float arithmetic on the
 # FP32 pipes: the kernel is bound by instruction issue (4 warp instructions per SM per clock).
 # Thread instructions per node (smsp__inst_executed.sum x 32 / nodes) and DRAM bytes per node
-# from one ncu capture of the finest launch (profiles/ncu_nonlinear_df_mixed.md).
+# from one ncu capture of the finest launch of each mixed-precision solve.
 ISSUE_PER_CLK_SM = 4 * 32
 DF_INSTR_PER_NODE = {2: 618510721 * 32 / 16769025, 3: 2830436764 * 32 / 16581375}
 DF_TRAFFIC_PER_NODE = {2: (136027392 + 609443328) / 16769025,
@@ -112,13 +112,12 @@ def hbm_peak() -> tuple[float, str]:
     except (OSError, KeyError, ValueError):
         return 6800.0, "of fallback"
 # DRAM bytes per node of a finest-level launch from one ncu capture of the current kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum of the 9-level 2D launch, 4,190,209 nodes;
-# profiles/ncu_k_nload_density2d_h1-2048.md), scaled by the nodes a launch processes.
-TRAFFIC_PER_NODE = {(2, "nload_density"): (34.024448e6 + 105.473792e6) / 4190209,
+# (dram__bytes_read.sum + dram__bytes_write.sum of the level-9 launch of the 9-level 2D
+# solve, 4,190,209 nodes), scaled by the nodes a launch processes.
+TRAFFIC_PER_NODE = {(2, "nload_density"): (34.109952e6 + 106.015232e6) / 4190209,
                     # the first level-9 sweep of the 9-level 2D solve, 4,190,209 nodes
-                    # (profiles/ncu_k_jacobi2d_h1-2048.md)
                     (2, "jacobi"): (235150336 + 24169728) / 4190209,
-                    # 3D: the 6-level launch, 2,048,383 nodes (profiles/ncu_k_nload_density3d_h1-128.md)
+                    # 3D: the level-6 launch of the 6-level solve, 2,048,383 nodes
                     (3, "nload_density"): (22.133248e6 + 82.609920e6) / 2048383}
 
 

@@ -19,6 +19,7 @@
 #include "fmg_internal.h"
 #include "reduce_dev.cuh"
 #include "dfloat.cuh"
+#include "star2d.cuh"
 
 namespace fmg {
 namespace {
@@ -30,15 +31,39 @@ __device__ __forceinline__ size_t at(int i, int j, int pitch) { return (size_t)j
 // (p, q, r) of area |K|:
 //   int u^2 lambda_p^2       = |K|/90  [6u_p^2 + u_q^2 + u_r^2 + 3u_p u_q + 3u_p u_r + u_q u_r]
 //   int u^2 lambda_p lambda_q = |K|/180 [3u_p^2 + 3u_q^2 + u_r^2 + 4u_p u_q + 2u_p u_r + 2u_q u_r]
-// s60, s90, s180 = |K| / 60, / 90, / 180 (computed on the host: an FP64 division per node
-// would cost as much as a quarter of the kernel's arithmetic)
-// T is the arithmetic type and U the source of u: FP64 (double, const double*) or, in the
-// mixed-precision modes, double-float from the split u (dfloat, SplitVec).
-template <typename T, typename U>
-__global__ void k_nload_density2d(int n, int pitch, size_t st, T s60, T s90, T s180, U u,
-                                  double* __restrict__ nl,
-                                  double* __restrict__ bC, double* __restrict__ bE,
-                                  double* __restrict__ bN, double* __restrict__ bNE) {
+// Summed over the star, and written with the per-edge numbers of the column walk
+// (star2d.cuh: s, F = s^2 + a^2 + b^2 of an edge (a, b), M1 and sum F over the opposite
+// edges):
+//   B_pp = |K|/180 [u_p (72 u_p + 6 M1) + sum F]
+//   B_pq = |K|/180 [2 (F_pq + s_pq (s_pq + u_r1 + u_r2)) + u_r1^2 + u_r2^2]
+// for the edge p-q shared by the triangles closed by r1 and r2 (E: NE, S; N: NE, W;
+// NE: E, N).  s60, s180 = |K| / 60, / 180 (computed on the host: an FP64 division per node
+// would cost as much as a quarter of the kernel's arithmetic).
+// FP64 mode.
+__global__ void __launch_bounds__(32 * kStarWarps)
+    k_nload_density2d(int n, int pitch, size_t st, double s60, double s180,
+                      const double* __restrict__ u, double* __restrict__ nl,
+                      double* __restrict__ bC, double* __restrict__ bE,
+                      double* __restrict__ bN, double* __restrict__ bNE) {
+  using T = double;
+  star2d_walk<T>(n, pitch, st, u, [&](size_t k, const Star2D<T>& p) {
+    nl[k] = out_of(s60 * star_cubic(p));
+    put_entry(bC, k, s180 * fma(p.u, fma(T(72), p.u, T(6) * p.M1), p.SF));
+    put_entry(bE, k, s180 * fma(T(2), fma(p.H.s, p.H.s + (p.uNE + p.uS), p.H.F), p.qNE + p.qS));
+    put_entry(bN, k, s180 * fma(T(2), fma(p.V.s, p.V.s + (p.uNE + p.uW), p.V.F), p.qNE + p.qW));
+    put_entry(bNE, k, s180 * fma(T(2), fma(p.D.s, p.D.s + (p.uE + p.uN), p.D.F), p.qE + p.qN));
+  });
+}
+
+// The same quantities in double-float arithmetic from the split u (mixed-precision modes),
+// node by node: the cubic load through the pair sums m_k = n_k + n_{k+1} (nload_at in
+// grid2d.cu) and the density stencil from the two triangle formulas above, its entries kept
+// split (double-float) for the coarsening chain.  s60, s90, s180 = |K| / 60, / 90, / 180.
+__global__ void k_nload_density2d_df(int n, int pitch, size_t st, dfloat s60, dfloat s90,
+                                     dfloat s180, SplitVec u, double* __restrict__ nl,
+                                     double* __restrict__ bC, double* __restrict__ bE,
+                                     double* __restrict__ bN, double* __restrict__ bNE) {
+  using T = dfloat;
   const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
   const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -68,8 +93,7 @@ __global__ void k_nload_density2d(int n, int pitch, size_t st, T s60, T s90, T s
   const T u2 = up * up;
   const T s2p = fma(T(0.5), M2, s2);  // 2 S2 + P
   nl[k] = out_of(s60 * (fma(T(2) * up, s2p, u2 * fma(T(24), up, T(3) * M1)) + M3));
-  // density stencil: FP64, or kept split (double-float) in the mixed modes for the coarsening
-  // diagonal: sum over the six triangles
+  // density stencil, diagonal: sum over the six triangles
   put_entry(bC, k, s90 * fma(T(36), u2, fma(T(3) * up, M1, s2p)));
   // edge p-q shared by the triangles closed by r1 and r2
   const T u26 = T(6) * u2;
@@ -334,15 +358,13 @@ dim3 grid_of(const Grid& g, int cx, int cy) {
 
 void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D& b,
                      cudaStream_t s) {
-  k_nload_density2d<double, const double*><<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0,
-                                              s>>>(
-      g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 180.0, g.h * g.h / 360.0, u, nl,
-      b.C, b.E, b.N, b.NE);
+  k_nload_density2d<<<star2d_grid(g.n, g.nb), star2d_block(), 0, s>>>(
+      g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 360.0, u, nl, b.C, b.E, b.N, b.NE);
 }
 
 void nload_density2d_df(const Grid& g, SplitVec u, double* nl, const Density2D& b,
                         cudaStream_t s) {
-  k_nload_density2d<dfloat, SplitVec><<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
+  k_nload_density2d_df<<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
       g.n, g.pitch, g.stride, dfloat(g.h * g.h / 120.0), dfloat(g.h * g.h / 180.0),
       dfloat(g.h * g.h / 360.0), u, nl, b.C, b.E, b.N, b.NE);
 }

@@ -17,6 +17,7 @@
 // (40 B/node extra traffic) and every sweep then costs 9 FP64 instructions per node.
 #include "fmg_internal.h"
 #include "dfloat.cuh"
+#include "star2d.cuh"
 
 namespace fmg {
 namespace {
@@ -190,15 +191,16 @@ __global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
 // triangle with p), summing int_K u^3 lambda_p = |K|/60 sum_{|b|=3} u^b (b_p + 1) gives
 //   |K|/60 [24u^3 + 6u^2 S1 + 2u(2 S2 + P) + 2 S3 + Q],
 // S_q = sum n_k^q, P = sum n_k n_{k+1}, Q = sum n_k n_{k+1} (n_k + n_{k+1}), |K| = h^2/2.
-// Evaluated through the pair sums m_k = n_k + n_{k+1} and squares q_k = n_k^2, with
-// 2 S1 = M1 = sum m_k, 2 (2 S2 + P) = M2 + 2 S2 (M2 = sum m_k^2) and
-// 2 S3 + Q = M3 = sum m_k (q_k + q_{k+1}):
-//   |K|/60 [u^2 (24u + 3 M1) + u (M2 + 2 S2) + M3]   (47 FP64 instructions instead of 55).
-// T is the arithmetic type: double in FP64 mode, double-float (u read as a SplitVec) in the
-// mixed-precision modes, float in the FP32 auxiliary right-hand side (k_rhs2d_f32).
+// Through the pair sums m_k = n_k + n_{k+1} and squares q_k = n_k^2 (2 S1 = M1 = sum m_k,
+// 2 (2 S2 + P) = M2 + 2 S2 with M2 = sum m_k^2, 2 S3 + Q = M3 = sum m_k (q_k + q_{k+1})):
+//   |K|/60 [u^2 (24u + 3 M1) + u (M2 + 2 S2) + M3].
+// This per-node form serves the double-float and single-precision right-hand sides (T =
+// dfloat with u read as a SplitVec, or float); the FP64 kernels evaluate the same sums per
+// mesh edge (star2d.cuh), which saves FP64 instructions but, in double-float arithmetic,
+// loses more to the longer dependency chains and lane shuffles than it saves.
 // M1 (twice the neighbour sum) is returned through m1_out when given: the mass stencil of
 // the right-hand side needs the same sum.
-template <typename T = double, typename U = const double*>
+template <typename T, typename U = const double*>
 __device__ __forceinline__ T nload_at(const U& u, size_t k, int pitch, T* m1_out = nullptr) {
   const T up = get<T>(u, k);
   const T n0 = get<T>(u, k + 1), n1 = get<T>(u, k + pitch + 1), n2 = get<T>(u, k + pitch);
@@ -225,21 +227,27 @@ __device__ __forceinline__ T nload_at(const U& u, size_t k, int pitch, T* m1_out
   return v + M3;
 }
 
-__global__ void k_nload2d(int n, int pitch, size_t st, double scale, const double* __restrict__ u,
-                          double* __restrict__ out) {
-  INTERIOR_2D
-  out[k] = scale * nload_at(u, k, pitch);
+// The FP64 cubic-load kernels below walk columns (star2d.cuh): launch with star2d_grid /
+// star2d_block.
+__global__ void __launch_bounds__(32 * kStarWarps)
+    k_nload2d(int n, int pitch, size_t st, double scale, const double* __restrict__ u,
+              double* __restrict__ out) {
+  star2d_walk<double>(n, pitch, st, u, [&](size_t k, const Star2D<double>& p) {
+    out[k] = scale * star_cubic(p);
+  });
 }
 
-__global__ void k_rhs2d(int n, int pitch, size_t st, double h2_12, double h2_120,
-                        const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
-                        const double* __restrict__ u, double* __restrict__ f) {
-  INTERIOR_2D
-  const double nscale = pp[ib].zeta * h2_120;
-  double m1;  // twice the sum of the six neighbours
-  const double nl = nload_at(u, k, pitch, &m1);
-  const double mu = h2_12 * fma(6.0, u[k], 0.5 * m1);
-  f[k] = fma(lam[ib], mu, -nscale * nl);
+// f = lambda M u - N(u); the mass stencil h^2/12 (6 u_p + neighbour sum) reuses the cubic
+// load's M1 (twice the neighbour sum): h^2/24 (12 u_p + M1)
+__global__ void __launch_bounds__(32 * kStarWarps)
+    k_rhs2d(int n, int pitch, size_t st, double h2_24, double h2_120,
+            const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+            const double* __restrict__ u, double* __restrict__ f) {
+  const double nscale = pp[blockIdx.z].zeta * h2_120, l = lam[blockIdx.z];
+  star2d_walk<double>(n, pitch, st, u, [&](size_t k, const Star2D<double>& p) {
+    const double mu = h2_24 * fma(12.0, p.u, p.M1);
+    f[k] = fma(l, mu, -nscale * star_cubic(p));
+  });
 }
 
 // The same right-hand side in double-float arithmetic from the split u (mixed-precision
@@ -377,14 +385,14 @@ void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* x
 }
 
 void nload2d(const Grid& g, const double* u, double* out, cudaStream_t s) {
-  k_nload2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride,
-                                                                  g.h * g.h / 120.0, u, out);
+  k_nload2d<<<star2d_grid(g.n, g.nb), star2d_block(), 0, s>>>(g.n, g.pitch, g.stride,
+                                                               g.h * g.h / 120.0, u, out);
 }
 
 void rhs2d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
            double* f, cudaStream_t s) {
-  k_rhs2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
-      g.n, g.pitch, g.stride, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
+  k_rhs2d<<<star2d_grid(g.n, g.nb), star2d_block(), 0, s>>>(
+      g.n, g.pitch, g.stride, g.h * g.h / 24.0, g.h * g.h / 120.0, lam, p, u, f);
 }
 
 void rhs2d_f32(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
