@@ -82,11 +82,14 @@ N_SM = 152
 #     numbers: 3 own edges x 5 + square 1 + 3 six-term sums 15 + cubic bracket 8 + diagonal 6
 #     + 3 off-diagonal entries x 8): 69 flop; 8 B read + 40 B written
 #   Jacobi 3D: 15-point = 29 + 3 = 32 flop; 24 B + 72 B
-#   cubic load + density stencil 3D (sums over the link of the 24-tetrahedron star: 345 flop
-#     for N, 305 for the density stencil, 9 scalings): 659 flop; 8 B + 72 B
+#   cubic load + density stencil 3D (symmetric sums of the 6 tetrahedra of a cube formed once:
+#     98 flop with u^2, u^3; star and edge sums 73; N, diagonal and 7 edge entries 85):
+#     256 flop; 8 B + 72 B
+# The third number counts FP64 instructions (DADD, DMUL and DFMA alike take one issue slot of
+# the FP64 pipe, 2 per SM per clock): the unit these kernels are bound by.
 KERNELS = {
-    2: {"nload_density": (69.0, 48.0), "jacobi": (16.0, 64.0)},
-    3: {"nload_density": (659.0, 80.0), "jacobi": (32.0, 96.0)},
+    2: {"nload_density": (69.0, 48.0, 55.0), "jacobi": (16.0, 64.0, 9.0)},
+    3: {"nload_density": (256.0, 80.0, 218.0), "jacobi": (32.0, 96.0, 17.0)},
 }
 # the kernel with the largest share of the solve in the ncu launch lists (2D FP64 solve:
 # k_jacobi2d 21 %; 3D FP64 solve: k_nload_density3d 35 %)
@@ -118,7 +121,7 @@ TRAFFIC_PER_NODE = {(2, "nload_density"): (34.109952e6 + 106.015232e6) / 4190209
                     # the first level-9 sweep of the 9-level 2D solve, 4,190,209 nodes
                     (2, "jacobi"): (235150336 + 24169728) / 4190209,
                     # 3D: the level-6 launch of the 6-level solve, 2,048,383 nodes
-                    (3, "nload_density"): (22.133248e6 + 82.609920e6) / 2048383}
+                    (3, "nload_density"): (22.938624e6 + 83.353088e6) / 2048383}
 
 
 def rank_info():
@@ -624,7 +627,8 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
                 roof[name + "32"] = {"bound": "hbm", "achieved": ach, "peak": hpeak, "unit": "GB/s",
                                      "frac": ach / hpeak, "traffic": None, "launch_ms": ms,
                                      "bytes_per_node": bpn, "peak_source": hsrc}
-    for name, (flops, nbytes) in KERNELS[m["dim"]].items():
+    ops_peak = FP64_FLOP_PER_CLK_SM / 2 * N_SM * sm_max * 1e6 / 1e12
+    for name, (flops, nbytes, ops) in KERNELS[m["dim"]].items():
         if mixed and name in MIXED_HBM_KERNELS:
             continue
         ms = m["profile"].get(name, -1.0)
@@ -640,10 +644,14 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
         if ms and ms > 0:
             ach = flops * nodes / (ms * 1e-3) / 1e12
             tpn = TRAFFIC_PER_NODE.get((m["dim"], name))
+            ops_ach = ops * nodes / (ms * 1e-3) / 1e12
             roof[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                           "frac": ach / peak, "traffic": tpn * nodes if tpn else None,
                           "launch_ms": ms,
-                          "hbm_gbs_algorithmic": nbytes * nodes / (ms * 1e-3) / 1e9}
+                          "hbm_gbs_algorithmic": nbytes * nodes / (ms * 1e-3) / 1e9,
+                          "fp64_inst": {"per_node": ops, "achieved": ops_ach, "peak": ops_peak,
+                                        "unit": "T FP64 instructions/s",
+                                        "frac": ops_ach / ops_peak}}
     dom = DOMINANT[m["dim"]]
     if dom not in roof:  # FP32 V-cycles (mixed modes): the FP64 nonlinear pass dominates
         dom = "nload_density"

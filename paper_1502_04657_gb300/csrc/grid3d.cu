@@ -14,6 +14,7 @@
 // diagonals).  As in 2D, the 8 coupling arrays and omega/D are materialised once per solve.
 #include "fmg_internal.h"
 #include "dfloat.cuh"
+#include "star3d.cuh"
 
 namespace fmg {
 namespace {
@@ -402,22 +403,50 @@ __device__ __forceinline__ void star3(const U& u, size_t k, int pitch, long plan
   }
 }
 
-__global__ void k_nload3d(int n, int pitch, size_t st, double scale, const double* __restrict__ u,
-                          double* __restrict__ out) {
-  INTERIOR_3D
-  double nl;
-  star3<double, false>(u, k, pitch, plane, nl, nullptr);
-  out[k] = scale * nl;
+// FP64 kernels from the plane walk (star3d.cuh): 6 x the star sum of
+// h3 + u_p h2 + u_p^2 h1 + u_p^3 is S3 + 3 u_p S2 + 6 u_p^2 S1 + 144 u_p^3 in its sums of
+// h1, 2 h2, 6 h3; launch with star3_grid / star3_block and kS3Smem bytes.
+__device__ __forceinline__ double star3_cubic6(const Star3& p) {
+  return fma(p.u, fma(p.u, fma(144.0, p.u, 6.0 * p.S1), 3.0 * p.S2), p.S3);
 }
 
-__global__ void k_rhs3d(int n, int pitch, size_t st, double h3, double nscale,
-                        const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
-                        const double* __restrict__ u, double* __restrict__ f) {
-  INTERIOR_3D
-  double nl;
-  star3<double, false>(u, k, pitch, plane, nl, nullptr);
-  const double mu = h3 * mass_at(u, k, pitch, plane);
-  f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * nl);
+__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+    k_nload3d(int n, int pitch, size_t st, double scale6, const double* __restrict__ u,
+              double* __restrict__ out) {
+  star3_walk<false>(n, pitch, st, u, [&](size_t k, const Star3& p) {
+    out[k] = scale6 * star3_cubic6(p);
+  });
+}
+
+// f = lambda M u - zeta N(u); the mass stencil is h^3/120 (24 u_p + S1)
+__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+    k_rhs3d(int n, int pitch, size_t st, double h3_120, double nscale6,
+            const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+            const double* __restrict__ u, double* __restrict__ f) {
+  const int ib = blockIdx.z / star3_zchunks(n);
+  const double l = lam[ib], zn = pp[ib].zeta * nscale6;
+  star3_walk<false>(n, pitch, st, u, [&](size_t k, const Star3& p) {
+    f[k] = fma(l, h3_120 * fma(24.0, p.u, p.S1), -zn * star3_cubic6(p));
+  });
+}
+
+// N(u~) and the density stencil, FP64: s140_6, s210_2, s420_2 = |K|/140/6, |K|/210/2,
+// |K|/420/2 against the sums of h1, 2 h2, 6 h3 (an edge lies in 6 tetrahedra along an axis
+// or the body diagonal, 4 along a face diagonal)
+__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+    k_nload_density3d(int n, int pitch, size_t st, double s140_6, double s210_2,
+                      double s420_2, const double* __restrict__ u, double* __restrict__ nl,
+                      Density3D b) {
+  star3_walk<true>(n, pitch, st, u, [&](size_t k, const Star3& p) {
+    nl[k] = s140_6 * star3_cubic6(p);
+    b.a[0][k] = s210_2 * fma(p.u, fma(144.0, p.u, 4.0 * p.S1), p.S2);
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+      const double t = fma(p.u, p.un[d], p.q + p.qn[d]);  // u_p^2 + u_q^2 + u_p u_q
+      const double two_ne = (d >= 3 && d < 6) ? 8.0 : 12.0;
+      b.a[1 + d][k] = s420_2 * fma(two_ne, t, fma(p.u + p.un[d], 2.0 * p.E1[d], p.E2[d]));
+    }
+  });
 }
 
 // s140, s210, s420 = |K| / 140, / 210, / 420 (host-side: no FP64 division per node)
@@ -447,19 +476,19 @@ __global__ void k_rhs3d_df(int n, int pitch, size_t st, dfloat h3, dfloat nscale
   f[k] = fma(lam[ib], mu, -pp[ib].zeta * to_double(nscale * nl));
 }
 
-// T, U: FP64 (double, const double*) or double-float from the split u (dfloat, SplitVec); the
-// scales come in T, so the double-float version's only FP64 work is the output conversion.
-// MINB: resident blocks of 256 threads asked of the register allocator (the double-float
-// star needs 255 registers otherwise, which leaves 8 warps per SM).
+// The same in double-float arithmetic from the split u (mixed-precision modes), node by
+// node through the link sums of star3; the scales come in T, so the only FP64 work is the
+// output conversion.  MINB: resident blocks of 256 threads asked of the register allocator
+// (the double-float star needs 255 registers otherwise, which leaves 8 warps per SM).
 template <typename T, typename U, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-    k_nload_density3d(int n, int pitch, size_t st, T s140, T s210, T s420, U u,
-                      double* __restrict__ nl, Density3D b) {
+    k_nload_density3d_df(int n, int pitch, size_t st, T s140, T s210, T s420, U u,
+                         double* __restrict__ nl, Density3D b) {
   INTERIOR_3D
   T v, e[8];
   star3<T, true>(u, k, pitch, plane, v, e);
   nl[k] = out_of(s140 * v);
-  // the density stencil: FP64, or kept split (double-float) in the mixed modes
+  // the density stencil, kept split (double-float) for the coarsening
   put_entry(b.a[0], k, s210 * e[0]);
 #pragma unroll
   for (int d = 0; d < 7; ++d) put_entry(b.a[1 + d], k, s420 * e[1 + d]);
@@ -657,15 +686,28 @@ void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* x
                                          scale_stride);
 }
 
+// the plane-walk kernels take more than the default 48 KB of dynamic shared memory
+template <typename K>
+static cudaError_t star3_prepare(K* kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kS3Smem);
+}
+
 void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s) {
+  static const cudaError_t attr = star3_prepare(k_nload3d);
+  (void)attr;
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, vol / 140.0, u, out);
+  k_nload3d<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(g.n, g.pitch, g.stride,
+                                                                  vol / 140.0 / 6.0, u, out);
 }
 
 void rhs3d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
            double* f, cudaStream_t s) {
+  static const cudaError_t attr = star3_prepare(k_rhs3d);
+  (void)attr;
   const double h3 = g.h * g.h * g.h;
-  k_rhs3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, h3, h3 / 6.0 / 140.0, lam, p, u, f);
+  k_rhs3d<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(
+      g.n, g.pitch, g.stride, h3 / 120.0, h3 / 6.0 / 140.0 / 6.0, lam, p, u, f);
 }
 
 void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
@@ -677,15 +719,17 @@ void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p, const
 
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s) {
+  static const cudaError_t attr = star3_prepare(k_nload_density3d);
+  (void)attr;
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload_density3d<double, const double*, 1><<<INTERIOR_LAUNCH(g)>>>(
-      g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0, vol / 420.0, u, nl, b);
+  k_nload_density3d<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(
+      g.n, g.pitch, g.stride, vol / 140.0 / 6.0, vol / 210.0 / 2.0, vol / 420.0 / 2.0, u, nl, b);
 }
 
 void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& b,
                         cudaStream_t s) {
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload_density3d<dfloat, SplitVec, 2><<<INTERIOR_LAUNCH(g)>>>(
+  k_nload_density3d_df<dfloat, SplitVec, 2><<<INTERIOR_LAUNCH(g)>>>(
       g.n, g.pitch, g.stride, dfloat(vol / 140.0), dfloat(vol / 210.0), dfloat(vol / 420.0), u,
       nl, b);
 }
