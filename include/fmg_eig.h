@@ -74,6 +74,13 @@ extern "C" {
  * expression, so the results are bit-identical; the flag exists for comparison and for
  * drivers where tensor maps cannot be encoded (the library also falls back by itself).     */
 #define FMG_FLAG_NO_TMA 4
+/* flags: evaluate the FP64 cubic load, auxiliary right-hand side and density stencil as
+ * column (2D) or plane (3D) walks on every level.  The walks form each mesh edge's (2D) or
+ * tetrahedron's (3D) share of the exact integrals of Section 2 once, for all the nodes that
+ * need it; by default they are taken only where the launch gives them at least two blocks
+ * per SM, and smaller launches run node by node.  Both evaluate the same closed forms, so
+ * results agree to rounding; the flag exists for comparison and testing.                   */
+#define FMG_FLAG_STAR_WALKS 8
 
 /* Problem and method parameters.  Example 4.1 fixes the PDE; Algorithm 3.1 fixes m (vcycles)
  * and Algorithm 3.2 fixes p (corrections) and the level count n.                            */

@@ -55,15 +55,16 @@ __global__ void __launch_bounds__(32 * kStarWarps)
   });
 }
 
-// The same quantities in double-float arithmetic from the split u (mixed-precision modes),
-// node by node: the cubic load through the pair sums m_k = n_k + n_{k+1} (nload_at in
-// grid2d.cu) and the density stencil from the two triangle formulas above, its entries kept
-// split (double-float) for the coarsening chain.  s60, s90, s180 = |K| / 60, / 90, / 180.
-__global__ void k_nload_density2d_df(int n, int pitch, size_t st, dfloat s60, dfloat s90,
-                                     dfloat s180, SplitVec u, double* __restrict__ nl,
-                                     double* __restrict__ bC, double* __restrict__ bE,
-                                     double* __restrict__ bN, double* __restrict__ bNE) {
-  using T = dfloat;
+// The same quantities node by node: the cubic load through the pair sums
+// m_k = n_k + n_{k+1} (nload_at in grid2d.cu) and the density stencil from the two triangle
+// formulas above.  T, U: FP64 (double, const double*) for launches too small to fill the GPU
+// as column walks, or double-float from the split u (dfloat, SplitVec) in the mixed modes,
+// whose entries stay split for the coarsening chain.  s60, s90, s180 = |K| / 60, / 90, / 180.
+template <typename T, typename U>
+__global__ void k_nload_density2d_node(int n, int pitch, size_t st, T s60, T s90, T s180, U u,
+                                       double* __restrict__ nl, double* __restrict__ bC,
+                                       double* __restrict__ bE, double* __restrict__ bN,
+                                       double* __restrict__ bNE) {
   const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
   const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -358,13 +359,20 @@ dim3 grid_of(const Grid& g, int cx, int cy) {
 
 void nload_density2d(const Grid& g, const double* u, double* nl, const Density2D& b,
                      cudaStream_t s) {
+  if (!star2d_walks(g)) {
+    k_nload_density2d_node<double, const double*>
+        <<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
+            g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 180.0, g.h * g.h / 360.0, u,
+            nl, b.C, b.E, b.N, b.NE);
+    return;
+  }
   k_nload_density2d<<<star2d_grid(g.n, g.nb), star2d_block(), 0, s>>>(
       g.n, g.pitch, g.stride, g.h * g.h / 120.0, g.h * g.h / 360.0, u, nl, b.C, b.E, b.N, b.NE);
 }
 
 void nload_density2d_df(const Grid& g, SplitVec u, double* nl, const Density2D& b,
                         cudaStream_t s) {
-  k_nload_density2d_df<<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
+  k_nload_density2d_node<dfloat, SplitVec><<<grid_of(g, g.n - 1, g.n - 1), dim3(g.bx, g.by), 0, s>>>(
       g.n, g.pitch, g.stride, dfloat(g.h * g.h / 120.0), dfloat(g.h * g.h / 180.0),
       dfloat(g.h * g.h / 360.0), u, nl, b.C, b.E, b.N, b.NE);
 }

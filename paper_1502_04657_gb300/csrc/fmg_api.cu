@@ -214,7 +214,8 @@ int validate(const fmg_eig_problem* p) {
   if (!(p->box_len > 0.0) || !(p->zeta >= 0.0) || !(p->omega > 0.0 && p->omega <= 1.0))
     return FMG_EINVAL;
   if (!(p->scf_tol > 0.0) || p->scf_max_iter < 1) return FMG_EINVAL;
-  if (p->flags & ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS | FMG_FLAG_NO_TMA))
+  if (p->flags &
+      ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS | FMG_FLAG_NO_TMA | FMG_FLAG_STAR_WALKS))
     return FMG_EINVAL;
   if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision == FMG_FP64) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
@@ -287,6 +288,7 @@ void build_levels(fmg_eig_handle* h) {
     l.g.stride = (size_t)l.g.rows * l.g.pitch * (dim == 3 ? (size_t)l.g.rows : 1);
     l.g.h = p.box_len / l.g.n;
     l.g.nb = l.cap;
+    l.g.walk_all = (p.flags & FMG_FLAG_STAR_WALKS) != 0;
     const size_t s = l.g.stride * l.cap;
     if (dim == 2) {
       l.c.cC = h->alloc<double>(s);

@@ -25,6 +25,7 @@ struct Grid {
   double h = 0;
   int nb = 1;         // instances of a launch
   int bx = 32, by = 8;  // thread-block shape of the stencil kernels on this level
+  bool walk_all = false;  // FP64 cubic-load kernels as walks whatever the launch size
   size_t interior() const {
     size_t m = (size_t)(n - 1);
     return dim == 2 ? m * m : m * m * m;

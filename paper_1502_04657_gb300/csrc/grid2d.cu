@@ -195,9 +195,10 @@ __global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
 // 2 (2 S2 + P) = M2 + 2 S2 with M2 = sum m_k^2, 2 S3 + Q = M3 = sum m_k (q_k + q_{k+1})):
 //   |K|/60 [u^2 (24u + 3 M1) + u (M2 + 2 S2) + M3].
 // This per-node form serves the double-float and single-precision right-hand sides (T =
-// dfloat with u read as a SplitVec, or float); the FP64 kernels evaluate the same sums per
-// mesh edge (star2d.cuh), which saves FP64 instructions but, in double-float arithmetic,
-// loses more to the longer dependency chains and lane shuffles than it saves.
+// dfloat with u read as a SplitVec, or float) and the FP64 kernels of small launches; large
+// FP64 launches evaluate the same sums per mesh edge (star2d.cuh), which saves FP64
+// instructions but, in double-float arithmetic, loses more to the longer dependency chains
+// and lane shuffles than it saves.
 // M1 (twice the neighbour sum) is returned through m1_out when given: the mass stencil of
 // the right-hand side needs the same sum.
 template <typename T, typename U = const double*>
@@ -225,6 +226,24 @@ __device__ __forceinline__ T nload_at(const U& u, size_t k, int pitch, T* m1_out
   const T u2 = up * up;
   const T v = fma(up, fma(T(2), S2, M2), u2 * fma(T(24), up, T(3) * M1));
   return v + M3;
+}
+
+// FP64 node by node, for launches too small to fill the GPU as column walks
+__global__ void k_nload2d_node(int n, int pitch, size_t st, double scale,
+                               const double* __restrict__ u, double* __restrict__ out) {
+  INTERIOR_2D
+  out[k] = scale * nload_at<double>(u, k, pitch);
+}
+
+__global__ void k_rhs2d_node(int n, int pitch, size_t st, double h2_12, double h2_120,
+                             const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                             const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_2D
+  const double nscale = pp[ib].zeta * h2_120;
+  double m1;  // twice the sum of the six neighbours
+  const double nl = nload_at<double>(u, k, pitch, &m1);
+  const double mu = h2_12 * fma(6.0, u[k], 0.5 * m1);
+  f[k] = fma(lam[ib], mu, -nscale * nl);
 }
 
 // The FP64 cubic-load kernels below walk columns (star2d.cuh): launch with star2d_grid /
@@ -385,12 +404,22 @@ void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* x
 }
 
 void nload2d(const Grid& g, const double* u, double* out, cudaStream_t s) {
+  if (!star2d_walks(g)) {
+    k_nload2d_node<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
+        g.n, g.pitch, g.stride, g.h * g.h / 120.0, u, out);
+    return;
+  }
   k_nload2d<<<star2d_grid(g.n, g.nb), star2d_block(), 0, s>>>(g.n, g.pitch, g.stride,
                                                                g.h * g.h / 120.0, u, out);
 }
 
 void rhs2d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
            double* f, cudaStream_t s) {
+  if (!star2d_walks(g)) {
+    k_rhs2d_node<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
+        g.n, g.pitch, g.stride, g.h * g.h / 12.0, g.h * g.h / 120.0, lam, p, u, f);
+    return;
+  }
   k_rhs2d<<<star2d_grid(g.n, g.nb), star2d_block(), 0, s>>>(
       g.n, g.pitch, g.stride, g.h * g.h / 24.0, g.h * g.h / 120.0, lam, p, u, f);
 }

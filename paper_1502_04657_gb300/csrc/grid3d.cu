@@ -403,6 +403,26 @@ __device__ __forceinline__ void star3(const U& u, size_t k, int pitch, long plan
   }
 }
 
+// FP64 node by node through the link sums of star3, for launches too small to fill the GPU
+// as plane walks
+__global__ void k_nload3d_node(int n, int pitch, size_t st, double scale,
+                               const double* __restrict__ u, double* __restrict__ out) {
+  INTERIOR_3D
+  double nl;
+  star3<double, false>(u, k, pitch, plane, nl, nullptr);
+  out[k] = scale * nl;
+}
+
+__global__ void k_rhs3d_node(int n, int pitch, size_t st, double h3, double nscale,
+                             const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
+                             const double* __restrict__ u, double* __restrict__ f) {
+  INTERIOR_3D
+  double nl;
+  star3<double, false>(u, k, pitch, plane, nl, nullptr);
+  const double mu = h3 * mass_at(u, k, pitch, plane);
+  f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * nl);
+}
+
 // FP64 kernels from the plane walk (star3d.cuh): 6 x the star sum of
 // h3 + u_p h2 + u_p^2 h1 + u_p^3 is S3 + 3 u_p S2 + 6 u_p^2 S1 + 144 u_p^3 in its sums of
 // h1, 2 h2, 6 h3; launch with star3_grid / star3_block and kS3Smem bytes.
@@ -476,19 +496,20 @@ __global__ void k_rhs3d_df(int n, int pitch, size_t st, dfloat h3, dfloat nscale
   f[k] = fma(lam[ib], mu, -pp[ib].zeta * to_double(nscale * nl));
 }
 
-// The same in double-float arithmetic from the split u (mixed-precision modes), node by
-// node through the link sums of star3; the scales come in T, so the only FP64 work is the
-// output conversion.  MINB: resident blocks of 256 threads asked of the register allocator
-// (the double-float star needs 255 registers otherwise, which leaves 8 warps per SM).
+// The same node by node through the link sums of star3: T, U = FP64 (double, const double*)
+// for launches too small to fill the GPU as plane walks, or double-float from the split u
+// (dfloat, SplitVec) in the mixed modes, whose scales come in T so that the only FP64 work is
+// the output conversion.  MINB: resident blocks of 256 threads asked of the register
+// allocator (the double-float star needs 255 registers otherwise, which leaves 8 warps per SM).
 template <typename T, typename U, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-    k_nload_density3d_df(int n, int pitch, size_t st, T s140, T s210, T s420, U u,
-                         double* __restrict__ nl, Density3D b) {
+    k_nload_density3d_node(int n, int pitch, size_t st, T s140, T s210, T s420, U u,
+                           double* __restrict__ nl, Density3D b) {
   INTERIOR_3D
   T v, e[8];
   star3<T, true>(u, k, pitch, plane, v, e);
   nl[k] = out_of(s140 * v);
-  // the density stencil, kept split (double-float) for the coarsening
+  // the density stencil: FP64, or kept split (double-float) for the coarsening
   put_entry(b.a[0], k, s210 * e[0]);
 #pragma unroll
   for (int d = 0; d < 7; ++d) put_entry(b.a[1 + d], k, s420 * e[1 + d]);
@@ -694,18 +715,27 @@ static cudaError_t star3_prepare(K* kernel) {
 }
 
 void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s) {
+  const double vol = g.h * g.h * g.h / 6.0;
+  if (!star3_walks(g)) {
+    k_nload3d_node<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, vol / 140.0, u, out);
+    return;
+  }
   static const cudaError_t attr = star3_prepare(k_nload3d);
   (void)attr;
-  const double vol = g.h * g.h * g.h / 6.0;
   k_nload3d<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(g.n, g.pitch, g.stride,
                                                                   vol / 140.0 / 6.0, u, out);
 }
 
 void rhs3d(const Grid& g, const double* lam, const PotentialParams* p, const double* u,
            double* f, cudaStream_t s) {
+  const double h3 = g.h * g.h * g.h;
+  if (!star3_walks(g)) {
+    k_rhs3d_node<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, h3, h3 / 6.0 / 140.0, lam, p,
+                                         u, f);
+    return;
+  }
   static const cudaError_t attr = star3_prepare(k_rhs3d);
   (void)attr;
-  const double h3 = g.h * g.h * g.h;
   k_rhs3d<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(
       g.n, g.pitch, g.stride, h3 / 120.0, h3 / 6.0 / 140.0 / 6.0, lam, p, u, f);
 }
@@ -719,9 +749,14 @@ void rhs3d_f32(const Grid& g, const double* lam, const PotentialParams* p, const
 
 void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D& b,
                      cudaStream_t s) {
+  const double vol = g.h * g.h * g.h / 6.0;
+  if (!star3_walks(g)) {
+    k_nload_density3d_node<double, const double*, 1><<<INTERIOR_LAUNCH(g)>>>(
+        g.n, g.pitch, g.stride, vol / 140.0, vol / 210.0, vol / 420.0, u, nl, b);
+    return;
+  }
   static const cudaError_t attr = star3_prepare(k_nload_density3d);
   (void)attr;
-  const double vol = g.h * g.h * g.h / 6.0;
   k_nload_density3d<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(
       g.n, g.pitch, g.stride, vol / 140.0 / 6.0, vol / 210.0 / 2.0, vol / 420.0 / 2.0, u, nl, b);
 }
@@ -729,7 +764,7 @@ void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D
 void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& b,
                         cudaStream_t s) {
   const double vol = g.h * g.h * g.h / 6.0;
-  k_nload_density3d_df<dfloat, SplitVec, 2><<<INTERIOR_LAUNCH(g)>>>(
+  k_nload_density3d_node<dfloat, SplitVec, 2><<<INTERIOR_LAUNCH(g)>>>(
       g.n, g.pitch, g.stride, dfloat(vol / 140.0), dfloat(vol / 210.0), dfloat(vol / 420.0), u,
       nl, b);
 }

@@ -80,6 +80,17 @@ inline dim3 star2d_grid(int n, int nb) {
 }
 inline dim3 star2d_block() { return dim3(32, kStarWarps); }
 
+// A walk is a chain of dependent row steps, and a block's FP64 work lands on one SM, so a
+// level with few blocks is latency-bound (about 33 us for any n <= 512 on one GB300, against
+// 8 us node by node at n = 128).  The walk is taken when it gives at least two blocks per SM
+// (single 2D instances from n = 1024 on); smaller launches run node by node.
+// (FMG_FLAG_STAR_WALKS takes it everywhere.)
+constexpr unsigned kWalkMinBlocks = 2 * 152;
+inline bool star2d_walks(const Grid& lv) {
+  const dim3 g = star2d_grid(lv.n, lv.nb);
+  return lv.walk_all || (size_t)g.x * g.y * g.z >= kWalkMinBlocks;
+}
+
 // Walks the rows of this thread's strip of instance blockIdx.z and calls out(k, star) for
 // every interior node it produces (k = the node's index in the batched arrays).  u is read
 // through get<T>: FP64 or the split double-float copy.  blockDim = (32, kStarWarps).

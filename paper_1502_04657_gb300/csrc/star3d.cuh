@@ -55,6 +55,17 @@ inline dim3 star3_grid(int n, int nb) {
 }
 inline dim3 star3_block() { return dim3(kS3X, kS3Y); }
 
+// A block's 16 planes are dependent steps on one SM, so a level with few blocks is
+// latency-bound (about 0.23 ms for any n <= 64 on one GB300, against 0.025 ms node by node at
+// n = 32).  The walk is taken when it gives at least two blocks per SM (single 3D instances
+// from n = 128 on); smaller launches run node by node.
+// (FMG_FLAG_STAR_WALKS takes it everywhere.)
+constexpr unsigned kWalk3MinBlocks = 2 * 152;
+inline bool star3_walks(const Grid& lv) {
+  const dim3 g = star3_grid(lv.n, lv.nb);
+  return lv.walk_all || (size_t)g.x * g.y * g.z >= kWalk3MinBlocks;
+}
+
 // blockDim = (kS3X, kS3Y), kS3Smem bytes of dynamic shared memory; instance
 // blockIdx.z / star3_zchunks(n).  out(k, star) for every interior node the block produces.
 template <bool EDGES, typename Out>

@@ -18,6 +18,7 @@ FMG_SMOOTH_JACOBI, FMG_SMOOTH_CHEBYSHEV, FMG_SMOOTH_CG = 0, 1, 2
 FMG_FLAG_NO_AUTOTUNE = 1
 FMG_FLAG_FP32_RHS = 2
 FMG_FLAG_NO_TMA = 4
+FMG_FLAG_STAR_WALKS = 8
 FMG_MAX_LEVELS = 16
 
 
