@@ -81,6 +81,11 @@ extern "C" {
  * per SM, and smaller launches run node by node.  Both evaluate the same closed forms, so
  * results agree to rounding; the flag exists for comparison and testing.                   */
 #define FMG_FLAG_STAR_WALKS 8
+/* flags: run the small levels of every 2D V-cycle (at most 32 cells per side, damped Jacobi)
+ * as separate kernels, one per sweep and transfer, instead of one fused kernel per V-cycle
+ * with one CTA per instance.  Both evaluate the same expressions in the same order, so the
+ * results are bit-identical; the flag exists for comparison and testing.                   */
+#define FMG_FLAG_SEPARATE_VCYCLE 16
 
 /* Problem and method parameters.  Example 4.1 fixes the PDE; Algorithm 3.1 fixes m (vcycles)
  * and Algorithm 3.2 fixes p (corrections) and the level count n.                            */

@@ -215,7 +215,8 @@ int validate(const fmg_eig_problem* p) {
     return FMG_EINVAL;
   if (!(p->scf_tol > 0.0) || p->scf_max_iter < 1) return FMG_EINVAL;
   if (p->flags &
-      ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS | FMG_FLAG_NO_TMA | FMG_FLAG_STAR_WALKS))
+      ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS | FMG_FLAG_NO_TMA | FMG_FLAG_STAR_WALKS |
+        FMG_FLAG_SEPARATE_VCYCLE))
     return FMG_EINVAL;
   if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision == FMG_FP64) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
@@ -669,6 +670,29 @@ void enqueue_smooth(fmg_eig_handle* h, Level& l, int j, int nu, bool& zero, cuda
   }
 }
 
+// The whole V-cycle from level j in one kernel (vcycle_small.cu) when level j is small: 2D,
+// damped Jacobi, at most 32 cells per side.  The result lands in L(j).x; the levels below
+// keep their vectors in shared memory.
+bool enqueue_vcycle_fused(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
+  const fmg_eig_problem& p = h->prob;
+  if (p.dim != 2 || p.smoother != FMG_SMOOTH_JACOBI || (p.flags & FMG_FLAG_SEPARATE_VCYCLE))
+    return false;
+  if (j < 2 || j > kSmallMaxLevels || h->L(j).g.n > kSmallMaxCells) return false;
+  SmallVcycle v{};
+  v.levels = j;
+  v.nu_pre = p.nu_pre;
+  v.nu_post = p.nu_post;
+  v.x_zero = x_zero ? 1 : 0;
+  for (int k = 1; k <= j; ++k) {
+    const Level& l = h->L(k);
+    v.lv[k - 1] = SmallLevel2D{l.g.n, l.g.pitch, l.g.stride, l.c};
+  }
+  v.Linv = h->L1inv;
+  v.f = h->L(j).f;
+  v.x = h->L(j).x;
+  return vcycle_small(v, h->L(j).g.nb, s) == cudaSuccess;
+}
+
 // One V-cycle on level j for L_j x = f (x, f in L(j).x, L(j).f).
 void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
   Level& l = h->L(j);
@@ -676,6 +700,7 @@ void enqueue_vcycle(fmg_eig_handle* h, int j, bool x_zero, cudaStream_t s) {
     coarse_matvec(l.g, h->L1inv, l.f, l.x, s);
     return;
   }
+  if (enqueue_vcycle_fused(h, j, x_zero, s)) return;
   const fmg_eig_problem& p = h->prob;
   bool zero = x_zero;
   prof_begin(h, kProfVcycle, j, s);

@@ -324,4 +324,26 @@ void dense_spd_inverse(const double* L, double* Linv, int n, int nb, cudaStream_
 void coarse_matvec(const Grid& g, const double* Linv, const double* x, double* y,
                    cudaStream_t s);
 
+// ---- the small levels of a 2D V-cycle in one kernel (vcycle_small.cu) ---------------------
+constexpr int kSmallMaxLevels = 6;    // entry level and the levels below it
+constexpr int kSmallMaxCells = 32;    // cells per side of the entry level
+constexpr size_t kSmallSmemLimit = 96 * 1024;
+struct SmallLevel2D {
+  int n, pitch;
+  size_t stride;
+  Coef2D c;  // the V-cycle's operator on this level
+};
+struct SmallVcycle {
+  int levels;  // the entry level; levels 1 .. levels take part
+  int nu_pre, nu_post, x_zero;
+  SmallLevel2D lv[kSmallMaxLevels];  // level j at index j - 1
+  const double* Linv;                // level-1 inverse, nh x nh per instance
+  const double* f;                   // the entry level's right-hand side (batched arrays)
+  double* x;                         // the entry level's iterate, read unless x_zero
+};
+size_t vcycle_small_smem(const SmallVcycle& v);
+// One V-cycle from the entry level for instances 0 .. nb - 1; an error (before launching)
+// when the levels need more shared memory than kSmallSmemLimit.
+cudaError_t vcycle_small(const SmallVcycle& v, int nb, cudaStream_t s);
+
 }  // namespace fmg

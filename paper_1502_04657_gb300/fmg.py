@@ -19,6 +19,7 @@ FMG_FLAG_NO_AUTOTUNE = 1
 FMG_FLAG_FP32_RHS = 2
 FMG_FLAG_NO_TMA = 4
 FMG_FLAG_STAR_WALKS = 8
+FMG_FLAG_SEPARATE_VCYCLE = 16
 FMG_MAX_LEVELS = 16
 
 
