@@ -91,6 +91,22 @@ KERNELS = {
     2: {"nload_density": (69.0, 48.0, 55.0), "jacobi": (16.0, 64.0, 9.0)},
     3: {"nload_density": (256.0, 80.0, 218.0), "jacobi": (32.0, 96.0, 17.0)},
 }
+# Launches too small to fill the GPU as walks run node by node, each node forming the sums of
+# its own star: 2D 106 flop in 82 FP64 instructions (pair sums n_k + n_{k+1}), 3D 659 flop in
+# about 490 (sums over the link of the 24-tetrahedron star).
+NODE_KERNELS = {2: {"nload_density": (106.0, 48.0, 82.0)}, 3: {"nload_density": (659.0, 80.0, 490.0)}}
+
+
+def star_walks(dim: int, n: int, nb: int) -> bool:
+    """Whether the library runs a level of n cells per side (nb instances) as a column / plane
+    walk: when the walk's grid has at least two blocks per SM (30 x 64-node 2D blocks,
+    32 x 8 x 16-node 3D blocks)."""
+    m = n - 1
+    if dim == 2:
+        blocks = -(-m // 30) * -(-m // 64)
+    else:
+        blocks = -(-m // 32) * -(-m // 8) * -(-m // 16)
+    return blocks * nb >= 2 * N_SM
 # the kernel with the largest share of the solve in the ncu launch lists (2D FP64 solve:
 # k_jacobi2d 21 %; 3D FP64 solve: k_nload_density3d 35 %)
 DOMINANT = {2: "jacobi", 3: "nload_density"}
@@ -331,7 +347,8 @@ def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist
     out = {"value": world * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
            "step_ms": step_ms, "lambda": float(lam_d.item()), "dofs": n, "desc": desc,
            "profile": solver.profile(), "kernels": solver.kernel_count(), "clocks": clk,
-           "dim": gp.dim, "mixed": mixed}
+           "dim": gp.dim, "mixed": mixed, "n_finest": gp.coarse_cells << (gp.levels - 1),
+           "nb_finest": 1}
     if with_e2e:
         u_host = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
         e2e_steps = max(3, min(steps, 10))
@@ -428,7 +445,7 @@ def measure_batch(steps: int, warmup: int, world: int, local: int, dist=None) ->
     return {"value": world * nb * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
             "step_ms": step_ms, "dofs": dofs, "dofs_finest_launch": at_finest * ((8 << (finest - 1)) - 1) ** 2,
             "profile": prof, "kernels": kernels, "clocks": clk, "dim": 2, "mixed": True,
-            "nb": nb, "tiles": tiles, "create_s": create_s,
+            "n_finest": 8 << (finest - 1), "nb_finest": at_finest, "nb": nb, "tiles": tiles, "create_s": create_s,
             "e2e": {"value": world * nb * e2e_steps / e2e_s, "unit": "solves/s",
                     "h2d_bytes_per_step": nb * 112,
                     "d2h_bytes_per_step": 8 * dofs + nb * (8 + 4 + 16 * 12)},
@@ -628,7 +645,11 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
                                      "frac": ach / hpeak, "traffic": None, "launch_ms": ms,
                                      "bytes_per_node": bpn, "peak_source": hsrc}
     ops_peak = FP64_FLOP_PER_CLK_SM / 2 * N_SM * sm_max * 1e6 / 1e12
-    for name, (flops, nbytes, ops) in KERNELS[m["dim"]].items():
+    table = dict(KERNELS[m["dim"]])
+    node_run = "n_finest" in m and not star_walks(m["dim"], m["n_finest"], m.get("nb_finest", 1))
+    if node_run:
+        table.update(NODE_KERNELS[m["dim"]])
+    for name, (flops, nbytes, ops) in table.items():
         if mixed and name in MIXED_HBM_KERNELS:
             continue
         ms = m["profile"].get(name, -1.0)
@@ -643,7 +664,9 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
             continue
         if ms and ms > 0:
             ach = flops * nodes / (ms * 1e-3) / 1e12
-            tpn = TRAFFIC_PER_NODE.get((m["dim"], name))
+            # (the DRAM figures were captured on the walk kernels)
+            tpn = None if node_run and name in NODE_KERNELS[m["dim"]] else \
+                TRAFFIC_PER_NODE.get((m["dim"], name))
             ops_ach = ops * nodes / (ms * 1e-3) / 1e12
             roof[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                           "frac": ach / peak, "traffic": tpn * nodes if tpn else None,
