@@ -54,3 +54,26 @@ def test_create_rejects_bad_problem_before_touching_the_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.fmg_eig_create(ctypes.byref(p), ctypes.byref(h)) == fmg.FMG_EINVAL
     assert not h.value
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of the header that the binding names has the header's value."""
+    from paper_1502_04657_gb300 import fmg
+
+    text = open(os.path.join(ROOT, "include", "fmg_eig.h")).read()
+    defines = dict(re.findall(r"#define\s+(FMG_\w+)\s+(-?\d+)\b", text))
+    shared = [k for k in defines if hasattr(fmg, k)]
+    for must in ("FMG_FLAG_NO_AUTOTUNE", "FMG_FLAG_FP32_RHS", "FMG_FLAG_NO_TMA",
+                 "FMG_FLAG_STAR_WALKS", "FMG_FLAG_SEPARATE_VCYCLE", "FMG_SMOOTH_CG"):
+        assert must in shared, must
+    for k in shared:
+        assert getattr(fmg, k) == int(defines[k]), k
+
+
+def test_create_rejects_unknown_flag_bits_before_touching_the_gpu(lib):
+    from paper_1502_04657_gb300 import fmg
+
+    p = fmg.Problem(levels=2, flags=1 << 20).to_c()
+    h = ctypes.c_void_p()
+    assert lib.fmg_eig_create(ctypes.byref(p), ctypes.byref(h)) == fmg.FMG_EINVAL
+    assert not h.value
