@@ -396,9 +396,9 @@ __device__ __forceinline__ void star3(const U& u, size_t k, int pitch, long plan
           sh += fma(nv[r], nv[t], sq[r] + sq[t]);
         }
       }
-      const T U = up + uq;
+      const T upq = up + uq;
       const T h2pq = fma(up, uq, u2 + sq[2 * d]);
-      b[1 + d] = fma((T)kLink.npair[d], fma(U, U, T(2) * h2pq), fma(T(2) * U, sv, sh));
+      b[1 + d] = fma((T)kLink.npair[d], fma(upq, upq, T(2) * h2pq), fma(T(2) * upq, sv, sh));
     }
   }
 }
