@@ -1,19 +1,21 @@
 // Allocation-free variant of the coarsest-level nonlinear solve.
 //
-// Some callers may not allocate device memory at all: code that runs while a CUDA stream
-// is being captured in a mode that forbids allocation, frameworks that hand every byte of
-// the GPU to their own pool and do not let libraries call cudaMalloc, or services that must
-// not allocate once they are serving.  For them fmg_eig_coarse_solve_noalloc computes the
-// same result as fmg_eig_coarse_solve without a handle: the caller passes the problem and
-// the output buffers, and every intermediate lives in one fixed device array declared in
-// this file (kScratchDoubles doubles, 256 KiB, held by every GPU that loads the library
-// until the process exits).
+// Some callers may not allocate device memory at all: frameworks that hand every byte of
+// the GPU to their own pool and do not let libraries call cudaMalloc (an outside allocation
+// can fail or fragment their pool), and services that must not allocate once they serve
+// (cudaMalloc and cudaFree can synchronise the device and stall the requests in flight).
+// For them fmg_eig_coarse_solve_noalloc computes the same result as fmg_eig_coarse_solve
+// without a handle: the caller passes the problem and the output buffers, and every
+// intermediate lives in one fixed device array declared in this file (kScratchDoubles
+// doubles, 256 KiB, held by every GPU that loads the library until the process exits).
 //
 // The array's name is only a host-side stand-in in host code, so its device address is
 // looked up once per device with cudaGetSymbolAddress (with that device current) on the
-// first call that runs on the device.  That first call should therefore happen before any
-// stream capture begins.  All calls share the one array: concurrent or overlapping calls on
-// the GPU race with each other and must be serialised by the caller.
+// first call that runs on the device, and kept for the life of the process; the lookup is
+// not repeated after cudaDeviceReset, so a process that resets a device must not call this
+// function on that device again.  The call copies small tables from host memory and
+// synchronises its stream before it returns.  All calls share the one array: concurrent or
+// overlapping calls on the GPU race with each other and must be serialised by the caller.
 #include <mutex>
 
 #include "fmg_internal.h"
@@ -157,8 +159,10 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   d.status_out = status;
 
   // the array keeps the previous call's contents: clear everything this call will read
-  // before writing it, so no stale value can leak in
+  // before writing it, so no stale value can leak in; the status word starts non-zero
+  // (all bits set) so that a solve kernel that never ran cannot report success
   if (cudaMemsetAsync(base, 0, off * sizeof(double), s) != cudaSuccess ||
+      cudaMemsetAsync(status, 0xff, sizeof(int), s) != cudaSuccess ||
       cudaMemcpyAsync(tri, tri_h, sizeof(int) * ntri * 3, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(adj, adj_h, sizeof(int) * nh * 6, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(params, &pp, sizeof(pp), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -170,6 +174,7 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   dense_level1_2d(g, c, L1, M1, s);
   start_vector(g, cstart, nh + 1, s);
   dense_scf(d, 1, s);
+  if (cudaGetLastError() != cudaSuccess) return FMG_ECUDA;  // a launch above failed
   double lam_h = 0.0;
   int st[2] = {1, 0};
   if (cudaMemcpyAsync(&lam_h, lam, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -180,5 +185,6 @@ extern "C" int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double*
   }
   *lambda_out = lam_h;
   if (iters) *iters = st[1];
-  return st[0] == 0 ? FMG_OK : FMG_ENOCONV;
+  if (st[0] == 0) return FMG_OK;
+  return st[0] == 1 ? FMG_ENOCONV : FMG_ECUDA;  // 1: iteration cap hit; else it never ran
 }
