@@ -31,7 +31,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import batch_instances, seeded_problem_2d, serve_stream  # noqa: E402
+from workloads import batch_instances, seeded_problem, serve_stream  # noqa: E402
 
 METRIC = "GP ground-state solves/s and fine-grid MDOF/s at |Δλ|≤1e-8; p50/p99 latency"
 WORKLOADS = {
@@ -208,7 +208,7 @@ class Clocks:
 
 
 def problem_kwargs(config: str, levels=None) -> dict:
-    kw = seeded_problem_2d(config)
+    kw = seeded_problem(config)
     if levels is not None:
         kw["levels"] = levels
     return kw
@@ -218,8 +218,8 @@ ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 from oracle import fmg_oracle as O
-from workloads import seeded_problem_2d
-kw = seeded_problem_2d({cfg!r}, levels={levels})
+from workloads import seeded_problem
+kw = seeded_problem({cfg!r}, levels={levels})
 times = []
 for _ in range({reps}):
     t = time.perf_counter()

@@ -24,7 +24,10 @@
  *   - A handle is not thread-safe: use one handle per host thread.  All work of a handle is
  *     ordered on the stream passed to the call (NULL = the handle's own stream).
  *   - Every device-side loop (SCF/Newton iterations) is bounded; a bound that is hit is
- *     reported as FMG_ENOCONV with the partial result still written.
+ *     reported as FMG_ENOCONV with the partial result still written.  Every device-side wait
+ *     (the mbarrier waits of the TMA-fed sweeps) is bounded too; one that gives up is
+ *     reported as FMG_ETIMEOUT for its instance (it outranks FMG_ENOCONV), and that
+ *     instance's results are not meaningful.
  */
 #ifndef FMG_EIG_H
 #define FMG_EIG_H
@@ -81,6 +84,14 @@ extern "C" {
  * per SM, and smaller launches run node by node.  Both evaluate the same closed forms, so
  * results agree to rounding; the flag exists for comparison and testing.                   */
 #define FMG_FLAG_STAR_WALKS 8
+/* flags (test hook, no counterpart in the paper): every bounded device wait of the solve's
+ * TMA-fed sweeps (FMG_MIXED_FP32 / FMG_MIXED_BF16 levels with at least 512 (2D) or 128 (3D)
+ * cells per side) gives up at once instead of after its normal bound.  The sweep then takes
+ * the path of a wait that ran out: it records the instance in the solve's status word,
+ * writes NaN over its tile, waits (with the normal bound) for its own loads in flight and
+ * returns, and the solve reports FMG_ETIMEOUT for that instance.  This exercises the timeout
+ * path without a fault or a hang; results of such a solve are not meaningful.               */
+#define FMG_FLAG_EXPIRE_WAITS 32
 /* flags: run the small levels of every 2D V-cycle (at most 32 cells per side, damped Jacobi)
  * as separate kernels, one per sweep and transfer, instead of one fused kernel per V-cycle
  * with one CTA per instance.  Both evaluate the same expressions in the same order, so the
@@ -163,6 +174,14 @@ int fmg_eig_set_params(fmg_eig_handle* h, const fmg_eig_problem* prob);
  * Entries a solve does not contain read -1.  Synchronises the handle's stream.             */
 int fmg_eig_kernel_count(const fmg_eig_handle* h);
 int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count);
+
+/* Fault injection for tests (no counterpart in the paper): after `after` more device
+ * allocations by the library in this process succeed, the next one fails as if the device
+ * were out of memory, once; later allocations succeed again.  A negative value cancels a
+ * pending injection.  The failed call reports FMG_ENOMEM and releases what it had allocated
+ * (fmg_eig_create, fmg_eig_batch_create); fmg_eig_serve retries or rejects the cohort whose
+ * allocation failed and serves the others.  Returns FMG_OK.                                 */
+int fmg_eig_inject_alloc_failure(int64_t after);
 
 /* Static description of a return code.                                                    */
 const char* fmg_eig_strerror(int code);
@@ -330,9 +349,10 @@ int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev,
                          int32_t* iters);
 
 /* The same coarsest-level solve as fmg_eig_coarse_solve, for callers that must not allocate
- * device memory (the paper has no counterpart: this is a library service).  Examples are code
- * running under a stream capture that forbids allocation, frameworks that own every byte of
- * the GPU through their own pool, and services that may not allocate once they serve.  No
+ * device memory (the paper has no counterpart: this is a library service).  Examples are
+ * frameworks that own every byte of the GPU through their own pool (an allocation from
+ * outside can fail or fragment it) and services that may not allocate once they serve
+ * (cudaMalloc / cudaFree can synchronise the device and stall the work in flight).  No
  * handle is needed and nothing is allocated: the caller passes the problem (only dim,
  * coarse_cells, box_len, w_const, w_quad, zeta, omega, scf_tol and scf_max_iter are read)
  * and u_dev, a device buffer of (coarse_cells - 1)^2 doubles that receives u_{h_1} in the
@@ -341,10 +361,13 @@ int fmg_eig_coarse_solve(fmg_eig_handle* h, double* lambda_out, double* u_dev,
  * the library, which every GPU that loads the library keeps until the process exits.
  * Limits: dim = 2, FMG_FP64, FMG_W_LEFT (else FMG_ENOTSUP); 2 <= coarse_cells <= 9 (else
  * FMG_EINVAL, the array's capacity).  The first call on a device looks up the array's device
- * address and should come before any stream capture on that device.  Calls share the array
- * and run synchronously on `stream` (NULL = legacy default stream); calls that overlap on
- * the GPU, from several host threads or streams, race and must be serialised by the caller.
- * Returns FMG_OK, FMG_ENOCONV (cap hit, partial result written) or an error code.          */
+ * address and keeps it for the process (a device reset invalidates it: do not call again on
+ * a device after cudaDeviceReset).  The call copies small tables from host memory, runs on
+ * `stream` (NULL = legacy default stream) and synchronises it before returning.  Calls share
+ * the array; calls that overlap on the GPU, from several host threads or streams, race and
+ * must be serialised by the caller.  Returns FMG_OK, FMG_ENOCONV (cap hit, partial result
+ * written), FMG_ECUDA (a launch or copy failed, or the solve kernel never ran) or another
+ * error code.                                                                                */
 int fmg_eig_coarse_solve_noalloc(const fmg_eig_problem* prob, double* lambda_out, double* u_dev,
                                  int32_t* iters, void* stream);
 

@@ -62,6 +62,10 @@ struct CreateOptions {
   double* stage_lam = nullptr;
 };
 
+// Test hook behind fmg_eig_inject_alloc_failure: true when the device allocation about to
+// be made is the one chosen to fail (each call counts one allocation).
+bool injected_alloc_failure();
+
 }  // namespace fmg
 
 struct fmg_eig_handle {
@@ -98,6 +102,7 @@ struct fmg_eig_handle {
          *lam_levels = nullptr, *scal = nullptr, *kscratch = nullptr, *uout = nullptr;
   double* cg = nullptr;  // conjugate gradient smoother: r.r (2 slots) and p.L p per instance
   int *iters = nullptr, *status = nullptr;  // [level][instance]
+  int* wait_fail = nullptr;  // [instance]: 1 when a bounded device wait gave up in the solve
   int* inv_order = nullptr;                 // sorted index of the caller's instance i
   // device copy read by the kernels (nparams), and its pinned host staging uploaded at every
   // solve; the paper-literal form keeps nb more entries with the form set to W_LEFT, from
@@ -132,6 +137,7 @@ struct fmg_eig_handle {
       bytes += (nbytes + 511) / 512 * 512;
       return nullptr;
     }
+    if (fmg::injected_alloc_failure()) throw std::bad_alloc();
     const cudaError_t e = opt.async_alloc ? cudaMallocAsync(&p, nbytes, stream)
                                           : cudaMalloc(&p, nbytes);
     if (e != cudaSuccess) {
@@ -171,5 +177,8 @@ void fill_params(fmg_eig_handle* h);
 cudaError_t upload_params(fmg_eig_handle* h, cudaStream_t s);
 // every instance's u from its finest level into h->uout (interior layout)
 void enqueue_outputs(fmg_eig_handle* h, cudaStream_t s);
+// FMG_OK, FMG_ENOCONV or FMG_ETIMEOUT for sorted instance b with lb levels, from the copied
+// statuses st[level][instance] (nb per level) and wait words of a solve
+int instance_code(const int* st, const int* wait_fail, int nb, int b, int lb);
 
 }  // namespace fmg

@@ -6,6 +6,7 @@
 // largest first.  Level k's arrays hold the cnt[k] instances that have a level k back to
 // back, so on the FMG stage of level k the active instances are 0 .. cnt[k] - 1 of every
 // array and each step of the stage is one launch over all of them (Grid::nb).
+#include <atomic>
 #include <math.h>
 #include <string.h>
 
@@ -216,7 +217,7 @@ int validate(const fmg_eig_problem* p) {
   if (!(p->scf_tol > 0.0) || p->scf_max_iter < 1) return FMG_EINVAL;
   if (p->flags &
       ~(FMG_FLAG_NO_AUTOTUNE | FMG_FLAG_FP32_RHS | FMG_FLAG_NO_TMA | FMG_FLAG_STAR_WALKS |
-        FMG_FLAG_SEPARATE_VCYCLE))
+        FMG_FLAG_SEPARATE_VCYCLE | FMG_FLAG_EXPIRE_WAITS))
     return FMG_EINVAL;
   if ((p->flags & FMG_FLAG_FP32_RHS) && p->precision == FMG_FP64) return FMG_EINVAL;
   const double cells = (double)p->coarse_cells * pow(2.0, p->levels - 1);
@@ -475,6 +476,7 @@ void build_coarse(fmg_eig_handle* h) {
   h->lam_levels = h->alloc<double>((size_t)FMG_MAX_LEVELS * nb);
   h->iters = h->alloc<int>((size_t)FMG_MAX_LEVELS * nb);
   h->status = h->alloc<int>((size_t)FMG_MAX_LEVELS * nb);
+  h->wait_fail = h->alloc<int>(nb);
   size_t tot = 0;
   h->uoff.resize(nb);
   for (int b = 0; b < nb; ++b) {
@@ -728,7 +730,8 @@ void lv_sweep32(fmg_eig_handle* h, Level& l, int mode, cudaStream_t s) {
   const bool bf = h->bf16();
   if (l.tma) {
     const TMAMap& mx = l.x32 == l.tm_base[0] ? l.tm_x[0] : l.tm_x[1];
-    sweep32_tma(l.g, l.ct, mx, l.tm_f, mode == 0 ? l.r32 : l.xt32, mode, s, bf);
+    sweep32_tma(l.g, l.ct, mx, l.tm_f, mode == 0 ? l.r32 : l.xt32, mode, h->wait_fail,
+                (h->prob.flags & FMG_FLAG_EXPIRE_WAITS) != 0, s, bf);
   } else if (mode == 0) {
     residual32(l.g, l.ct, l.f32, l.x32, l.r32, s, bf);
   } else {
@@ -898,6 +901,7 @@ void enqueue_correction(fmg_eig_handle* h, int k, cudaStream_t s) {
 }
 
 void enqueue_fmg(fmg_eig_handle* h, cudaStream_t s, const StageHook* after_stage) {
+  cudaMemsetAsync(h->wait_fail, 0, sizeof(int) * h->nb, s);  // no bounded wait gave up yet
   enqueue_setup(h, s, true);
   h->activate(h->nb);
   enqueue_coarse(h, s);
@@ -1205,6 +1209,27 @@ int create_handle(const fmg_eig_problem* probs, int count, const CreateOptions& 
   return FMG_OK;
 }
 
+// fmg_eig_inject_alloc_failure: the number of device allocations that still succeed before
+// the chosen one fails (negative: none is chosen)
+std::atomic<long long> g_alloc_fail_after{-1};
+
+bool injected_alloc_failure() {
+  long long v = g_alloc_fail_after.load();
+  while (v >= 0)
+    if (g_alloc_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
+// Return code of sorted instance b (lb levels) from the per-level statuses of its small
+// solves (st[level][instance]) and its bounded-wait word: a wait that gave up outranks an
+// iteration cap that was hit.
+int instance_code(const int* st, const int* wait_fail, int nb, int b, int lb) {
+  if (wait_fail[b] != 0) return FMG_ETIMEOUT;
+  for (int k = 1; k <= lb; ++k)
+    if (st[(size_t)(k - 1) * nb + b] != 0) return FMG_ENOCONV;
+  return FMG_OK;
+}
+
 // Launch the solve graph of every handle (each on its own stream), then collect the outputs
 // of each in the callers' order.  out_index[h][b] is the caller's index of h's instance b.
 int run_handles(const std::vector<fmg_eig_handle*>& hs,
@@ -1265,9 +1290,10 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
     cudaStream_t s = h->stream;
     const int nb = h->nb, L = h->levels();
     std::vector<double> lam(nb), lv((size_t)L * nb), sc(3 * (size_t)nb);
-    std::vector<int> st((size_t)L * nb), it((size_t)L * nb);
+    std::vector<int> st((size_t)L * nb), it((size_t)L * nb), wf(nb);
     CK(cudaMemcpyAsync(lam.data(), h->lam, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(st.data(), h->status, sizeof(int) * L * nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(wf.data(), h->wait_fail, sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
     if (stats) {
       CK(cudaMemcpyAsync(lv.data(), h->lam_levels, sizeof(double) * L * nb,
                          cudaMemcpyDeviceToHost, s));
@@ -1286,10 +1312,8 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
     for (int b = 0; b < nb; ++b) {
       const int i = out_index[g][b];
       const int lb = h->probs[b].levels;
-      int code = FMG_OK;
-      for (int k = 1; k <= lb; ++k)
-        if (st[(size_t)(k - 1) * nb + b] != 0) code = FMG_ENOCONV;
-      if (code != FMG_OK) rc = FMG_ENOCONV;
+      const int code = instance_code(st.data(), wf.data(), nb, b, lb);
+      if (code == FMG_ETIMEOUT || (code == FMG_ENOCONV && rc == FMG_OK)) rc = code;
       lambdas[i] = lam[b];
       if (statuses) statuses[i] = code;
       if (stats) {
@@ -1381,6 +1405,11 @@ int fmg_eig_set_params(fmg_eig_handle* h, const fmg_eig_problem* prob) {
 }
 
 int fmg_eig_kernel_count(const fmg_eig_handle* h) { return h ? h->kernel_nodes : 0; }
+
+int fmg_eig_inject_alloc_failure(int64_t after) {
+  g_alloc_fail_after.store(after < 0 ? -1 : (long long)after);
+  return FMG_OK;
+}
 
 int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count) {
   if (!h || !ms || count < 1) return FMG_EINVAL;

@@ -207,9 +207,11 @@ constexpr int kTMAMinCells3 = 128;  // 3D levels likewise
 bool tma_sweep_applies(const Grid& g);
 bool encode_level_map(const Grid& g, int cap, const float* base, bool bf, bool halo,
                       TMAMap* out);
-// mode 0: residual y = f - L x; 1: Jacobi y = x + omega D^-1 (f - L x); 2: Jacobi from x = 0
+// mode 0: residual y = f - L x; 1: Jacobi y = x + omega D^-1 (f - L x); 2: Jacobi from x = 0.
+// A tile wait that runs out sets wait_fail[b] = 1 for its instance b (wait_fail: g.nb ints);
+// `expire` makes every tile wait give up at once (the FMG_FLAG_EXPIRE_WAITS test hook).
 void sweep32_tma(const Grid& g, const CoefT& ct, const TMAMap& mx, const TMAMap& mf, float* y,
-                 int mode, cudaStream_t s, bool bf = false);
+                 int mode, int* wait_fail, bool expire, cudaStream_t s, bool bf = false);
 // damped Jacobi sweep / residual with coefficients rebuilt from the FP32 tables
 void jacobi32(const Grid& g, const CoefT& ct, const float* f, const float* x, float* xo,
               bool zero, cudaStream_t s, bool bf = false);

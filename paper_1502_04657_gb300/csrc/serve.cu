@@ -218,13 +218,15 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
   auto finish = [&](Cohort& c) {
     fmg_eig_handle* h = c.h;
     const int nb = h->nb, L = h->levels();
-    std::vector<int> st((size_t)L * nb, 1);
+    std::vector<int> st((size_t)L * nb, 1), wf(nb, 0);
     bool ok = !c.failed;
     if (ok) {
       bool any_u = false;
       for (int b = 0; b < nb; ++b) any_u |= reqs[c.req[b]].u != nullptr;
       if (any_u) enqueue_outputs(h, h->stream);
       ok = cudaMemcpyAsync(st.data(), h->status, sizeof(int) * L * nb, cudaMemcpyDeviceToHost,
+                           h->stream) == cudaSuccess &&
+           cudaMemcpyAsync(wf.data(), h->wait_fail, sizeof(int) * nb, cudaMemcpyDeviceToHost,
                            h->stream) == cudaSuccess;
       for (int b = 0; ok && b < nb; ++b) {
         const fmg_eig_request& r = reqs[c.req[b]];
@@ -240,10 +242,7 @@ extern "C" int fmg_eig_serve(const fmg_eig_serve_config* cfg, const fmg_eig_requ
         o.status = FMG_ECUDA;
         continue;
       }
-      int code = FMG_OK;
-      for (int k = 1; k <= h->probs[b].levels; ++k)
-        if (st[(size_t)(k - 1) * nb + b] != 0) code = FMG_ENOCONV;
-      o.status = code;
+      o.status = instance_code(st.data(), wf.data(), nb, b, h->probs[b].levels);
     }
     if (!ok) {
       cudaGetLastError();

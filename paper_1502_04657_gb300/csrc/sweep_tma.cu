@@ -16,9 +16,12 @@
 // BF16 as the TMA requires, and are 136 columns wide (a multiple of 16 bytes for both);
 // columns and rows past n are zero-filled and never used.
 //
-// Every wait on an mbarrier is bounded.  If a wait runs out, the CTA writes NaN over its
-// current tile (which makes the solve fail visibly), waits a bounded time for its own loads
-// still in flight and returns.
+// Every wait on an mbarrier is bounded.  If a wait runs out, the CTA records it in the
+// launch's status word (wait_fail[instance] = 1, which the host reports as FMG_ETIMEOUT),
+// writes NaN over its current tile (so no stale value passes for a result), waits a bounded
+// time for its own loads still in flight and returns.  With `expire` set (a test hook) the
+// tile waits give up at once, which exercises that path without any fault; the final waits
+// for loads in flight always use the full bound.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -69,9 +72,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait for the phase with parity `parity` to complete; false if it never did
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long it = 0; it < kSpinLimit; ++it)
+// bounded wait for the phase with parity `parity` to complete; false if it did not within
+// `limit` try_wait rounds
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long limit = kSpinLimit) {
+  for (long it = 0; it < limit; ++it)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -110,9 +114,10 @@ __global__ void __launch_bounds__(kThreads)
     k_sweep32_tma_2d(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mf,
                      int n, int pitch, size_t st_, int tiles_x, int tiles_y, int ntiles,
                      const float* __restrict__ tab, const float* __restrict__ cst,
-                     S* __restrict__ y) {
+                     S* __restrict__ y, int* __restrict__ wait_fail, int expire) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes<S>());
+  const long limit = expire ? 0 : kSpinLimit;
   const int tid = threadIdx.x;
   const uint32_t tx_bytes = (MODE == kJacobiZero ? 0 : x_bytes<S>()) + f_bytes<S>();
   if (tid == 0) {
@@ -184,12 +189,13 @@ __global__ void __launch_bounds__(kThreads)
         yNE[q + 1] = Y[3 * s + jj];
       }
     }
-    const bool ok = mbar_wait(&bar[stage], (uint32_t)((it / kStages) & 1));
+    const bool ok = mbar_wait(&bar[stage], (uint32_t)((it / kStages) & 1), limit);
     const bool lost = __syncthreads_or(!ok);
     const S* xs = reinterpret_cast<const S*>(smem + (size_t)stage * stage_bytes<S>());
     const S* fs = reinterpret_cast<const S*>(smem + (size_t)stage * stage_bytes<S>() +
                                              round128(x_bytes<S>()));
     if (lost) {
+      if (tid == 0) atomicExch(&wait_fail[ib], 1);
       for (int q = 0; q < kRowsPerThread; ++q) {
         const int j = j0 + q;
         if (act && j < n) st(yb, (size_t)j * pitch + i, __int_as_float(0x7fc00000));
@@ -238,9 +244,10 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();  // every thread is done with this stage before it is refilled
     if (tid == 0) issue(it + kStages);
   }
-  // loads still in flight (only after a lost wait): wait for them a bounded time
+  // loads still in flight (only after a lost wait, whose own tile may still be arriving):
+  // wait for them a bounded time
   if (tid == 0) {
-    for (int k = it + 1; k < it + kStages; ++k) {
+    for (int k = it; k < it + kStages; ++k) {
       const int tile = blockIdx.x + k * gridDim.x;
       if (tile >= ntiles) break;
       mbar_wait(&bar[k % kStages], (uint32_t)((k / kStages) & 1));
@@ -293,9 +300,10 @@ __global__ void __launch_bounds__(kThreads)
     k_sweep32_tma_3d(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mf,
                      int n, int pitch, size_t st_, int tiles_x, int tiles_y, int tiles_z,
                      int ntiles, const float* __restrict__ tab, const float* __restrict__ cst,
-                     S* __restrict__ y) {
+                     S* __restrict__ y, int* __restrict__ wait_fail, int expire) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStages3 * stage_bytes3<S>());
+  const long limit = expire ? 0 : kSpinLimit;
   __shared__ float sTz[5][kTZ3 + 1];  // z tables at the tile's planes l0 - 1 + p
   const int tid = threadIdx.x;
   const uint32_t tx_bytes = (MODE == kJacobiZero ? 0 : x_bytes3<S>()) + f_bytes3<S>();
@@ -363,12 +371,13 @@ __global__ void __launch_bounds__(kThreads)
       w = MODE == kResidual ? 0.0f : C[kCstOmega];
     }
     const float K0 = C[0], K1 = C[1], K2 = C[2], K3 = C[3];
-    const bool ok = mbar_wait(&bar[stage], (uint32_t)((it / kStages3) & 1));
+    const bool ok = mbar_wait(&bar[stage], (uint32_t)((it / kStages3) & 1), limit);
     const bool lost = __syncthreads_or(!ok);  // also publishes sTz
     const S* xs = reinterpret_cast<const S*>(smem + (size_t)stage * stage_bytes3<S>());
     const S* fs = reinterpret_cast<const S*>(smem + (size_t)stage * stage_bytes3<S>() +
                                              round128(x_bytes3<S>()));
     if (lost) {
+      if (tid == 0) atomicExch(&wait_fail[ib], 1);
       for (int q = 0; q < kTZ3; ++q)
         if (act && l0 + q < n) st(yb, (size_t)(l0 + q) * plane, __int_as_float(0x7fc00000));
       break;
@@ -405,8 +414,8 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (tid == 0) issue(it + kStages3);
   }
-  if (tid == 0) {
-    for (int k = it + 1; k < it + kStages3; ++k) {
+  if (tid == 0) {  // loads still in flight after a lost wait (see the 2D kernel)
+    for (int k = it; k < it + kStages3; ++k) {
       const int tile = blockIdx.x + k * gridDim.x;
       if (tile >= ntiles) break;
       mbar_wait(&bar[k % kStages3], (uint32_t)((k / kStages3) & 1));
@@ -451,7 +460,7 @@ int sms() {
 
 template <typename S, int MODE>
 void launch(const Grid& g, const CoefT& ct, const TMAMap& mx, const TMAMap& mf, float* y,
-            cudaStream_t s) {
+            int* wait_fail, int expire, cudaStream_t s) {
   const CUtensorMap& tx = *reinterpret_cast<const CUtensorMap*>(mx.bytes);
   const CUtensorMap& tf = *reinterpret_cast<const CUtensorMap*>(mf.bytes);
   const int m = g.n - 1;
@@ -464,7 +473,7 @@ void launch(const Grid& g, const CoefT& ct, const TMAMap& mx, const TMAMap& mf, 
     const int cap = 3 * sms();  // 3 CTAs of 56 KB shared memory per SM
     k_sweep32_tma_2d<S, MODE><<<ntiles < cap ? ntiles : cap, kThreads, smem_bytes<S>(), s>>>(
         tx, tf, g.n, g.pitch, g.stride, tiles_x, tiles_y, ntiles, ct.tab, ct.cst,
-        reinterpret_cast<S*>(y));
+        reinterpret_cast<S*>(y), wait_fail, expire);
   } else {
     static const cudaError_t attr = cudaFuncSetAttribute(
         k_sweep32_tma_3d<S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes3<S>());
@@ -475,7 +484,7 @@ void launch(const Grid& g, const CoefT& ct, const TMAMap& mx, const TMAMap& mf, 
     const int cap = 2 * sms();  // 2 CTAs of 80 KB shared memory per SM
     k_sweep32_tma_3d<S, MODE><<<ntiles < cap ? ntiles : cap, kThreads, smem_bytes3<S>(), s>>>(
         tx, tf, g.n, g.pitch, g.stride, tiles_x, tiles_y, tiles_z, ntiles, ct.tab, ct.cst,
-        reinterpret_cast<S*>(y));
+        reinterpret_cast<S*>(y), wait_fail, expire);
   }
 }
 
@@ -519,15 +528,16 @@ bool encode_level_map(const Grid& g, int cap, const float* base, bool bf, bool h
 }
 
 void sweep32_tma(const Grid& g, const CoefT& ct, const TMAMap& mx, const TMAMap& mf, float* y,
-                 int mode, cudaStream_t s, bool bf) {
+                 int mode, int* wait_fail, bool expire, cudaStream_t s, bool bf) {
+  const int e = expire ? 1 : 0;
   if (bf) {
-    if (mode == 0) launch<bf16, kResidual>(g, ct, mx, mf, y, s);
-    else if (mode == 1) launch<bf16, kJacobi>(g, ct, mx, mf, y, s);
-    else launch<bf16, kJacobiZero>(g, ct, mx, mf, y, s);
+    if (mode == 0) launch<bf16, kResidual>(g, ct, mx, mf, y, wait_fail, e, s);
+    else if (mode == 1) launch<bf16, kJacobi>(g, ct, mx, mf, y, wait_fail, e, s);
+    else launch<bf16, kJacobiZero>(g, ct, mx, mf, y, wait_fail, e, s);
   } else {
-    if (mode == 0) launch<float, kResidual>(g, ct, mx, mf, y, s);
-    else if (mode == 1) launch<float, kJacobi>(g, ct, mx, mf, y, s);
-    else launch<float, kJacobiZero>(g, ct, mx, mf, y, s);
+    if (mode == 0) launch<float, kResidual>(g, ct, mx, mf, y, wait_fail, e, s);
+    else if (mode == 1) launch<float, kJacobi>(g, ct, mx, mf, y, wait_fail, e, s);
+    else launch<float, kJacobiZero>(g, ct, mx, mf, y, wait_fail, e, s);
   }
 }
 

@@ -20,6 +20,7 @@ FMG_FLAG_FP32_RHS = 2
 FMG_FLAG_NO_TMA = 4
 FMG_FLAG_STAR_WALKS = 8
 FMG_FLAG_SEPARATE_VCYCLE = 16
+FMG_FLAG_EXPIRE_WAITS = 32
 FMG_MAX_LEVELS = 16
 
 
@@ -97,6 +98,7 @@ _SIGS = {
     "fmg_eig_correction": (C.c_int, [_P, _I32, C.c_double, _P, _D, _P, _P, C.POINTER(_I32)]),
     "fmg_eig_coarse_solve": (C.c_int, [_P, _D, _P, C.POINTER(_I32)]),
     "fmg_eig_augmented_system": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _P]),
+    "fmg_eig_inject_alloc_failure": (C.c_int, [C.c_int64]),
     "fmg_eig_coarse_solve_noalloc": (C.c_int, [C.POINTER(fmg_eig_problem), _D, _P, C.POINTER(_I32), _P]),
     "fmg_eig_batch_create": (C.c_int, [C.POINTER(fmg_eig_problem), _I32, C.POINTER(_P)]),
     "fmg_eig_batch_count": (_I32, [_P]),
@@ -111,6 +113,12 @@ _SIGS = {
     "fmg_eig_serve": (C.c_int, [C.POINTER(fmg_eig_serve_config), C.POINTER(fmg_eig_request), _I32,
                                 C.POINTER(fmg_eig_result), C.POINTER(fmg_eig_serve_stats)]),
 }
+
+
+def inject_alloc_failure(after: int) -> None:
+    """fmg_eig_inject_alloc_failure: the device allocation after `after` more successful ones
+    fails once (test hook; negative cancels)."""
+    load_library().fmg_eig_inject_alloc_failure(int(after))
 
 
 def coarse_solve_noalloc(problem: "Problem", u_dev, stream=None):
@@ -359,21 +367,23 @@ class BatchSolver(Solver):
         return self._check(self.lib.fmg_eig_batch_solve_dev(self.h, _ptr(lams_dev), stream),
                            "fmg_eig_batch_solve_dev")
 
-    def solve_all(self, with_u: bool = True, stats: bool = False):
-        """lambdas (list), u per instance (numpy, or None), stats records (or None), codes."""
+    def solve_all(self, with_u: bool = True, stats: bool = False, allow=()):
+        """lambdas (list), u per instance (numpy, or None), stats records (or None), codes.
+        Return codes in `allow` (besides FMG_ENOCONV) are reported in codes, not raised."""
         lams, us, ptrs, lens, st, codes = _batch_outputs(self.problems, with_u, stats)
         rc = self.lib.fmg_eig_batch_solve(self.h, lams, ptrs, lens, st, codes)
-        self._check(rc, "fmg_eig_batch_solve", allow=(FMG_ENOCONV,))
+        self._check(rc, "fmg_eig_batch_solve", allow=(FMG_ENOCONV, *allow))
         return list(lams), us, (list(st) if stats else None), list(codes)
 
 
-def solve_batch(problems: list, with_u: bool = True, stats: bool = False):
-    """fmg_eig_solve_batch: one-shot batch over problems of any mix of settings."""
+def solve_batch(problems: list, with_u: bool = True, stats: bool = False, allow=()):
+    """fmg_eig_solve_batch: one-shot batch over problems of any mix of settings.  Return codes
+    in `allow` (besides FMG_ENOCONV) are reported per instance in codes, not raised."""
     lib = load_library()
     arr = (fmg_eig_problem * len(problems))(*[p.to_c() for p in problems])
     lams, us, ptrs, lens, st, codes = _batch_outputs(problems, with_u, stats)
     rc = lib.fmg_eig_solve_batch(arr, len(problems), lams, ptrs, lens, st, codes)
-    if rc not in (FMG_OK, FMG_ENOCONV):
+    if rc not in (FMG_OK, FMG_ENOCONV, *allow):
         raise FmgError(rc, "fmg_eig_solve_batch")
     return list(lams), us, (list(st) if stats else None), list(codes)
 
@@ -385,9 +395,10 @@ def estimate_bytes(problems: list) -> int:
 
 
 def serve(problems: list, arrivals: list, *, budget_bytes: float = 0.0, max_batch: int = 32,
-          max_inflight: int = 4, batch_window_s: float = 0.0, with_u: bool = False):
+          max_inflight: int = 4, batch_window_s: float = 0.0, with_u: bool = False, allow=()):
     """fmg_eig_serve over requests (problem, arrival time in s): per-request results as dicts
-    (lambda, latency_s, admit_s, done_s, status, cohort, u) and the serve statistics."""
+    (lambda, latency_s, admit_s, done_s, status, cohort, u) and the serve statistics.  Return
+    codes in `allow` (besides FMG_ENOCONV) are left to the per-request statuses."""
     import numpy as np
     lib = load_library()
     n = len(problems)
@@ -406,7 +417,7 @@ def serve(problems: list, arrivals: list, *, budget_bytes: float = 0.0, max_batc
     res = (fmg_eig_result * n)()
     st = fmg_eig_serve_stats()
     rc = lib.fmg_eig_serve(C.byref(cfg), reqs, n, res, C.byref(st))
-    if rc not in (FMG_OK, FMG_ENOCONV):
+    if rc not in (FMG_OK, FMG_ENOCONV, *allow):
         raise FmgError(rc, "fmg_eig_serve")
     out = [{"lambda": r.lambda_, "latency_s": r.latency_s, "admit_s": r.admit_s,
             "done_s": r.done_s, "status": r.status, "cohort": r.cohort,

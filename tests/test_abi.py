@@ -64,7 +64,8 @@ def test_binding_constants_match_the_header():
     defines = dict(re.findall(r"#define\s+(FMG_\w+)\s+(-?\d+)\b", text))
     shared = [k for k in defines if hasattr(fmg, k)]
     for must in ("FMG_FLAG_NO_AUTOTUNE", "FMG_FLAG_FP32_RHS", "FMG_FLAG_NO_TMA",
-                 "FMG_FLAG_STAR_WALKS", "FMG_FLAG_SEPARATE_VCYCLE", "FMG_SMOOTH_CG"):
+                 "FMG_FLAG_STAR_WALKS", "FMG_FLAG_SEPARATE_VCYCLE", "FMG_FLAG_EXPIRE_WAITS",
+                 "FMG_SMOOTH_CG"):
         assert must in shared, must
     for k in shared:
         assert getattr(fmg, k) == int(defines[k]), k

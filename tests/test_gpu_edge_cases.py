@@ -5,7 +5,7 @@ import pytest
 
 from oracle import fmg_oracle as O
 from tests.test_gpu_parity import LAM_TOL, U_TOL, _fmg, _pair
-from workloads import seeded_problem_2d
+from workloads import seeded_problem
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,7 +54,7 @@ def test_full_size_2d_configuration_properties():
     """The 16,769,025-dof configuration: lambda identity, normalisation, the x <-> y symmetry
     of W = x^2 + y^2, and O(h^2) consistency with the coarser solves of the same problem."""
     fmg = _fmg()
-    kw = seeded_problem_2d("config2")
+    kw = seeded_problem("config2")
     fields = fmg.Problem.__dataclass_fields__
     lams = {}
     for levels in (8, 9, 10):

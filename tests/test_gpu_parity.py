@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import fmg_oracle as O
-from workloads import seeded_problem_2d
+from workloads import seeded_problem
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -196,7 +196,7 @@ def test_fmg_solve_matches_oracle(kw):
 
 def test_fmg_config1_seeded_parity():
     """The 2D benchmark discretisation at full size of its first configuration (h = 1/256)."""
-    kw = seeded_problem_2d("config1")
+    kw = seeded_problem("config1")
     op, gp = _pair(**kw)
     ref = O.fmg_solve(op)
     with _fmg().Solver(gp) as s:

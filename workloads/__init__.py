@@ -31,7 +31,7 @@ CONFIGS = {
 }
 
 
-def seeded_problem_2d(name: str, **over) -> dict:
+def seeded_problem(name: str, **over) -> dict:
     """Keyword arguments of a problem (oracle Problem / library Problem field names)."""
     kw = {**CONFIGS[name], **METHOD, "box_len": 1.0}
     kw.update(over)
