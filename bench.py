@@ -215,7 +215,8 @@ def problem_kwargs(config: str, levels=None) -> dict:
 
 
 ORACLE_SNIPPET = r"""
-import json, sys, time
+import hashlib, json, sys, time
+import numpy as np
 sys.path.insert(0, {root!r})
 from oracle import fmg_oracle as O
 from workloads import seeded_problem
@@ -226,16 +227,40 @@ for _ in range({reps}):
     prob = O.Problem(**kw)
     r = O.fmg_solve(prob)
     times.append(time.perf_counter() - t)
-print(json.dumps({{"times": times, "lam": r.lam, "dofs": (prob.cells(prob.levels) - 1) ** prob.dim}}))
+if {u_path!r}:
+    np.save({u_path!r}, r.u)
+print(json.dumps({{"times": times, "lam": r.lam, "dofs": (prob.cells(prob.levels) - 1) ** prob.dim,
+                  "digest": hashlib.sha256(np.float64(r.lam).tobytes() + r.u.tobytes()).hexdigest()}}))
 """
+ONE_THREAD = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
 
 
-def run_oracle(config: str, levels: int, reps: int) -> dict:
-    """The oracle in a fresh single-threaded interpreter (exec'd, never forked from CUDA)."""
-    env = {**os.environ, "OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
-    code = ORACLE_SNIPPET.format(root=ROOT, cfg=config, levels=levels, reps=reps)
+def run_oracle(config: str, levels: int, reps: int, u_path: str = "") -> dict:
+    """The oracle in a fresh single-threaded interpreter (exec'd, never forked from CUDA);
+    u_path: where to save its final u (numpy .npy), if given."""
+    env = {**os.environ, **ONE_THREAD}
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=config, levels=levels, reps=reps, u_path=u_path)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_all_cores(config: str, levels: int, procs: int | None = None) -> dict:
+    """`procs` (default: every host core) single-threaded oracle interpreters, each solving the
+    same sample at once: the oracle's throughput on all cores, in solves of the sample per
+    second of wall time.  Independent solves need no communication, and each one's result is
+    the single-threaded result bit for bit (checked by digest)."""
+    procs = procs or os.cpu_count() or 1
+    env = {**os.environ, **ONE_THREAD}
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=config, levels=levels, reps=1, u_path="")
+    t = time.perf_counter()
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, text=True, env=env)
+          for _ in range(procs)]
+    outs = [json.loads(p.communicate()[0].strip().splitlines()[-1]) for p in ps]
+    wall = time.perf_counter() - t
+    if any(p.returncode != 0 for p in ps):
+        raise RuntimeError("an oracle process failed")
+    return {"procs": procs, "wall_s": wall, "per_sample_s": wall / procs,
+            "digests": sorted({o["digest"] for o in outs}), "dofs": outs[0]["dofs"]}
 
 
 def dofs_of(kw: dict) -> int:
@@ -277,28 +302,109 @@ def reference_arm(args):
         print(json.dumps(line), flush=True)
         return
     levels = ORACLE_SAMPLE[config][1]
-    steps = []
-    r = None
+    walls, r = [], None
     for i in range(args.warmup + args.steps):
-        r = run_oracle(config, levels, 1)
+        r = run_oracle_all_cores(config, levels)
         if i >= args.warmup:
-            steps.append(r["times"][0])
+            walls.append(r["wall_s"])
     full = dofs_of(problem_kwargs(config))
     scale = full / r["dofs"]
-    per_solve = statistics.mean(steps) * scale
+    wall = statistics.mean(walls)
+    per_solve = wall / r["procs"] * scale  # projected seconds per full-size solve
     value = 1.0 / per_solve
-    sample = (f"oracle solve of the same discretisation truncated to {levels} levels "
-              f"({r['dofs']} dofs) per step, scaled x{scale:.1f} to {full} dofs by the method's "
-              f"linear work (Theorem 3.3)")
+    sample = (f"each step: {r['procs']} single-threaded oracle solves (one per host core, at "
+              f"once) of the same discretisation truncated to {levels} levels ({r['dofs']} "
+              f"dofs); solves/s of the sample scaled x{scale:.1f} to {full} dofs by the "
+              f"method's linear work (Theorem 3.3)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3,
+        "ms_per_step_note": "measured wall time of one step (the sample on all cores)",
+        "projected_ms_per_full_solve": per_solve * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": r["procs"], "kind": "oracle",
+                         "sample": sample, "bitwise_equal_across_cores": len(r["digests"]) == 1},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+GOLDEN_3D = os.path.join(ROOT, "tests", "golden", "oracle_config3_6levels.txt")
+# precision modes whose eigenpair is compared with the oracle: (key, precision, flags)
+ACCURACY_MODES = (("fp64", 0, 0), ("mixed_fp32", 1, 0), ("mixed_fp32_rhs32", 1, 2),
+                  ("mixed_bf16_storage", 2, 0))
+
+
+def read_golden_3d(path: str = GOLDEN_3D) -> dict | None:
+    """The oracle's stored result for the 3D trap at h = 1/128 (config 3 truncated to 6 levels;
+    written by tests/golden/make_oracle_3d_golden.py, which calls only the oracle): lambda per
+    level, u at every `step`-th interior node per direction, and the sum and norm of u."""
+    import numpy as np
+
+    if not os.path.exists(path):
+        return None
+    d, samples = {}, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) == 1:
+                samples.append(float(parts[0]))
+            elif parts[0] == "lambda_levels":
+                d["lambda_levels"] = [float(v) for v in parts[1:]]
+            else:
+                d[parts[0]] = float(parts[1])
+    d["u"] = np.array(samples)
+    n, step = int(d["cells"]), int(d["step"])
+    g = np.arange(step, n, step) - 1
+    k, j, i = np.meshgrid(g, g, g, indexing="ij")
+    d["idx"] = (i + (n - 1) * (j + (n - 1) * k)).ravel()
+    return d
+
+
+def gpu_solve_u(kw: dict, precision: int, flags: int = 0):
+    """(lambda, u) of one solve through the C ABI with a host output buffer."""
+    import numpy as np
+
+    from paper_1502_04657_gb300 import fmg
+
+    p = fmg.Problem(**{k: v for k, v in kw.items() if k in fmg.Problem.__dataclass_fields__},
+                    precision=precision, flags=flags)
+    with fmg.Solver(p) as s:
+        u = np.empty(p.size(p.levels))
+        lam, _, rc = s.solve(u)
+    return lam, u, rc
+
+
+def accuracy_vs_oracle(lam2: float, u2, levels2: int, gold3: dict | None) -> dict:
+    """Eigenvalue and eigenvector error of every precision mode against the oracle, at sizes
+    whose finest FMG stage runs the single-precision V-cycles through the TMA-fed sweeps:
+    config 2 truncated to `levels2` levels (h = 1/512 at 7) against a live oracle run, and
+    config 3 truncated to 6 levels (h = 1/128) against the stored oracle result (u compared on
+    its sampled nodes)."""
+    import numpy as np
+
+    out = {}
+    kw2 = problem_kwargs("config2", levels2)
+    kw3 = problem_kwargs("config3", 6)
+    for key, prec, flags in ACCURACY_MODES:
+        lam, u, rc = gpu_solve_u(kw2, prec, flags)
+        row = {"config2_%dlevels" % levels2: {
+            "dlambda_rel": abs(lam - lam2) / lam2,
+            "du_rel_l2": float(np.linalg.norm(u - u2) / np.linalg.norm(u2)), "status": rc}}
+        if gold3 is not None:
+            lam, u, rc = gpu_solve_u(kw3, prec, flags)
+            ref = gold3["lambda_levels"][-1]
+            us = u[gold3["idx"]]
+            row["config3_6levels"] = {
+                "dlambda_rel": abs(lam - ref) / ref,
+                "du_rel_l2_sampled": float(np.linalg.norm(us - gold3["u"]) / np.linalg.norm(gold3["u"])),
+                "du_norm2_rel": abs(float(np.linalg.norm(u)) - gold3["u_norm2"]) / gold3["u_norm2"],
+                "status": rc}
+        out[key] = row
+    return out
 
 
 def measure(workload: str, steps: int, warmup: int, world: int, local: int, dist=None,
@@ -524,15 +630,18 @@ def paper_examples_arm(args, world, local, dist):
         dist.destroy_process_group()
 
 
-def serve_arm(args, world, local, dist):
-    """config5: fmg_eig_serve over the request stream (rank r serves every world-th request)."""
+def measure_serve(nreq: int, max_batch: int, max_inflight: int, window: float, world: int,
+                  local: int, dist=None, sample: int = 48) -> dict:
+    """fmg_eig_serve over the first nreq requests of the config-5 stream (rank r serves every
+    world-th one), after a short warm-up stream; accuracy on a seeded sample of requests
+    solved alone in FP64."""
     import numpy as np
     import torch
 
     from paper_1502_04657_gb300 import fmg
 
     rank = rank_info()[0]
-    reqs = shard(serve_stream(args.serve_requests), rank, world)
+    reqs = shard(serve_stream(nreq), rank, world)
     fields = fmg.Problem.__dataclass_fields__
     probs = [fmg.Problem(**{k: v for k, v in r.items() if k in fields},
                          precision=fmg.FMG_MIXED_FP32) for r in reqs]
@@ -545,12 +654,11 @@ def serve_arm(args, world, local, dist):
         dist.barrier()
     clk_s = Clocks(local)
     clk_s.start()
-    res, st = fmg.serve(probs, arrivals, max_batch=args.serve_batch, max_inflight=args.serve_inflight,
-                        batch_window_s=args.serve_window)
+    res, st = fmg.serve(probs, arrivals, max_batch=max_batch, max_inflight=max_inflight,
+                        batch_window_s=window)
     clk = clk_s.stop()
-    # accuracy: a seeded sample of requests solved alone in FP64
     rng = np.random.default_rng(4657)
-    idx = rng.choice(len(probs), size=min(48, len(probs)), replace=False)
+    idx = rng.choice(len(probs), size=min(sample, len(probs)), replace=False)
     worst = 0.0
     for i in idx:
         p = fmg.Problem(**{k: v for k, v in reqs[i].items() if k in fields})
@@ -559,8 +667,34 @@ def serve_arm(args, world, local, dist):
         worst = max(worst, abs(res[i]["lambda"] - lam) / lam)
     value = st["solves_per_s"]
     if dist:
-        value = args.serve_requests / max_over_ranks(dist, st["makespan_s"], "cuda")
-    dofs = sum(p.size(p.levels) for p in probs)
+        value = nreq / max_over_ranks(dist, st["makespan_s"], "cuda")
+    return {"value": value, "st": st, "res": res, "probs": probs, "arrivals": arrivals,
+            "clocks": clk, "worst": worst, "sample": int(len(idx))}
+
+
+def serve_summary(m: dict) -> dict:
+    st = m["st"]
+    dofs = sum(p.size(p.levels) for p in m["probs"])
+    return {
+        "latency_ms": {"p50": st["p50_s"] * 1e3, "p99": st["p99_s"] * 1e3,
+                       "mean": st["mean_s"] * 1e3, "max": st["max_s"] * 1e3},
+        "mdof_per_s": dofs / st["makespan_s"] / 1e6,
+        "peak_hbm_gb": st["peak_bytes"] / 1e9, "hbm_budget_gb": st["budget_bytes"] / 1e9,
+        "peak_hbm_note": "in-flight and pooled (reusable) hierarchies",
+        "cohorts": st["cohorts"], "max_cohort": st["max_cohort"],
+        "cohorts_replaying_pooled_graph": st["reused"], "pooled_evicted": st["evicted"],
+        "max_inflight_seen": st["max_inflight_seen"], "completed": st["completed"],
+        "max_dlambda_rel_vs_fp64_alone": m["worst"], "dlambda_sample": m["sample"],
+        "all_converged": all(r["status"] == 0 for r in m["res"]),
+    }
+
+
+def serve_arm(args, world, local, dist):
+    """config5: fmg_eig_serve over the request stream (rank r serves every world-th request)."""
+    rank = rank_info()[0]
+    m = measure_serve(args.serve_requests, args.serve_batch, args.serve_inflight,
+                      args.serve_window, world, local, dist)
+    probs, arrivals, value, st = m["probs"], m["arrivals"], m["value"], m["st"]
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": st["makespan_s"] * 1e3,
@@ -571,17 +705,8 @@ def serve_arm(args, world, local, dist):
                    "max_batch": args.serve_batch, "max_inflight": args.serve_inflight,
                    "batch_window_s": args.serve_window, "parallelism": "replicas",
                    "l2": "resident hierarchies of GBs >> 129 MB L2; no flush"},
-        "latency_ms": {"p50": st["p50_s"] * 1e3, "p99": st["p99_s"] * 1e3,
-                       "mean": st["mean_s"] * 1e3, "max": st["max_s"] * 1e3},
-        "mdof_per_s": dofs / st["makespan_s"] / 1e6,
-        "peak_hbm_gb": st["peak_bytes"] / 1e9, "hbm_budget_gb": st["budget_bytes"] / 1e9,
-        "peak_hbm_note": "in-flight and pooled (reusable) hierarchies",
-        "cohorts": st["cohorts"], "max_cohort": st["max_cohort"],
-        "cohorts_replaying_pooled_graph": st["reused"], "pooled_evicted": st["evicted"],
-        "max_inflight_seen": st["max_inflight_seen"], "completed": st["completed"],
-        "max_dlambda_rel_vs_fp64_alone": worst, "dlambda_sample": int(len(idx)),
-        "all_converged": all(r["status"] == 0 for r in res),
-        "clocks": clk,
+        **serve_summary(m),
+        "clocks": m["clocks"],
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 112 * len(probs),
                 "d2h_bytes_per_step": 8 * len(probs),
                 "note": "the serve call is the end-to-end path: requests in host memory, "
@@ -628,9 +753,13 @@ def serve_cpu_baseline(count: int = 6, cap2: int = 6, cap3: int = 4) -> dict:
                        f"core), scaled by total dofs to the 10,000 requests ({full} dofs)")}
 
 
-def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
+def roofline(m: dict, clk: dict, fp64_peak: dict | None = None) -> tuple[dict, dict]:
+    """Roofline of the dominant kernel (and the others): FP64 kernels against the measured
+    FP64 multiply-add rate of this run's probe when given (fp64_peak), else the nominal rate
+    from unit counts and clock; the nominal fraction is kept beside the measured one."""
     sm_max = (clk or {}).get("sm_max_mhz") or 2070
-    peak = FP64_FLOP_PER_CLK_SM * N_SM * sm_max * 1e6 / 1e12
+    nominal = FP64_FLOP_PER_CLK_SM * N_SM * sm_max * 1e6 / 1e12
+    peak = fp64_peak["tflops"] if fp64_peak else nominal
     roof = {}
     nodes = m.get("dofs_finest_launch", m["dofs"])  # nodes one finest-level launch processes
     mixed = m.get("mixed")
@@ -644,7 +773,7 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
                 roof[name + "32"] = {"bound": "hbm", "achieved": ach, "peak": hpeak, "unit": "GB/s",
                                      "frac": ach / hpeak, "traffic": None, "launch_ms": ms,
                                      "bytes_per_node": bpn, "peak_source": hsrc}
-    ops_peak = FP64_FLOP_PER_CLK_SM / 2 * N_SM * sm_max * 1e6 / 1e12
+    ops_peak = peak / 2  # one FP64 instruction per multiply-add lane of the probe
     table = dict(KERNELS[m["dim"]])
     node_run = "n_finest" in m and not star_walks(m["dim"], m["n_finest"], m.get("nb_finest", 1))
     if node_run:
@@ -670,6 +799,7 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
             ops_ach = ops * nodes / (ms * 1e-3) / 1e12
             roof[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                           "frac": ach / peak, "traffic": tpn * nodes if tpn else None,
+                          "peak_nominal": nominal, "frac_nominal": ach / nominal,
                           "launch_ms": ms,
                           "hbm_gbs_algorithmic": nbytes * nodes / (ms * 1e-3) / 1e9,
                           "fp64_inst": {"per_node": ops, "achieved": ops_ach, "peak": ops_peak,
@@ -680,10 +810,61 @@ def roofline(m: dict, clk: dict) -> tuple[dict, dict]:
         dom = "nload_density"
     main = dict(roof.get(dom, {}))
     main["kernel"] = dom
-    main.setdefault("peak_source", "FP64 (the kernel is FP64-ALU bound): 152 SMs x 2 DFMA/clk x "
-                    "sm_max_mhz, nominal 1.25 TFLOP/s; of fallback (no FP64 figure in the "
-                    "measured peaks)")
+    if fp64_peak:
+        main.setdefault("peak_source", "of measured: FP64 multiply-add probe of this run "
+                        f"(fmg_eig_probe_fma, best of {fp64_peak['launches']} launches, "
+                        f"{fp64_peak['tflops']:.4f} TFLOP/s); peak_nominal = 152 SMs x 2 FP64 "
+                        "FMA lanes/clk x sm_max_mhz")
+    else:
+        main.setdefault("peak_source", "FP64 (the kernel is FP64-ALU bound): 152 SMs x 2 FP64 "
+                        "FMA lanes/clk x sm_max_mhz, nominal 1.26 TFLOP/s (no probe run)")
     return main, {k: v for k, v in roof.items() if k != dom}
+
+
+def fma_probe(fp64: bool = True, shapes=(2, 4, 8), reps: int = 3) -> dict:
+    """Best multiply-add rate of the library's probe over a few launch shapes (TFLOP/s)."""
+    from paper_1502_04657_gb300 import fmg
+
+    iters = 8192 if fp64 else 262144
+    best, rows = 0.0, []
+    for cps in shapes:
+        for _ in range(reps):
+            ms, fl = fmg.probe_fma(fp64, cps, iters)
+            tf = fl / (ms * 1e-3) / 1e12
+            rows.append({"ctas_per_sm": cps, "ms": ms, "tflops": tf})
+            best = max(best, tf)
+    return {"tflops": best, "launches": len(rows), "iters": iters, "rows": rows,
+            "precision": "fp64" if fp64 else "fp32"}
+
+
+def probe_arm(args):
+    """--probe-fp64: the FP64 (and FP32) multiply-add rate, with the SM clock sampled while the
+    probe runs (about 2 s of launches), reported as measured, per sampled clock and scaled to
+    the maximum clock (time x median SM MHz)."""
+    import torch
+
+    torch.cuda.set_device(rank_info()[2])
+    fma_probe(True, (4,), 1)  # warm-up
+    clk_s = Clocks(rank_info()[2])
+    clk_s.start()
+    time.sleep(0.25)
+    t_end = time.perf_counter() + 2.0
+    runs = []
+    while time.perf_counter() < t_end:
+        runs.append(fma_probe(True, (2, 4, 8), 1))
+    fp32 = fma_probe(False, (2, 4, 8), 2)
+    clk = clk_s.stop()
+    best = max(r["tflops"] for r in runs)
+    mhz, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    out = {"probe": "fmg_eig_probe_fma", "fp64_tflops_best": best,
+           "fp64_tflops_median": statistics.median(x["tflops"] for r in runs for x in r["rows"]),
+           "fp64_launches": sum(r["launches"] for r in runs),
+           "fp64_rows_last": runs[-1]["rows"], "fp32_tflops_best": fp32["tflops"],
+           "fp32_rows": fp32["rows"], "clocks": clk,
+           "fp64_nominal_tflops_at_sm_max": FP64_FLOP_PER_CLK_SM * N_SM * (mx or 2070) * 1e6 / 1e12}
+    if mhz and mx:
+        out["fp64_tflops_scaled_to_sm_max"] = best * mx / mhz
+    print(json.dumps(out), flush=True)
 
 
 def ours_arm(args):
@@ -726,7 +907,8 @@ def ours_arm(args):
         "small_solve_iters_per_level": m.get("scf_iters"),
         "identity_defect": m.get("identity_defect"),
     }
-    if args.workload == "config2" and not args.no_extras:
+    extras = args.workload == "config2" and not args.no_extras
+    if extras:
         for key, wl, flags in (("mixed_fp32", "config2-mixed", 0),
                                ("mixed_fp32_rhs32", "config2-mixed", 2),
                                ("mixed_bf16_storage", "config2-bf16", 0)):
@@ -738,20 +920,73 @@ def ours_arm(args):
                          "dlambda_rel_vs_fp64": abs(mx["lambda"] - m["lambda"]) / m["lambda"],
                          "roofline_v_cycle": {k: v for k, v in mroof.items() if k.endswith("32")},
                          "kernel_ms_finest": mx["profile"]}
+    if not args.no_extras and m["dim"] in (2, 3):
+        # the FP64 roofline against this run's own multiply-add probe
+        probe = fma_probe(True)
+        main, other = roofline(m, m["clocks"], probe)
+        line["roofline"], line["roofline_other"] = main, other
+        line["fp64_probe"] = {"tflops": probe["tflops"], "launches": probe["launches"],
+                              "rows": probe["rows"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import numpy as np
+
         config = WORKLOADS[args.workload][0]
         levels = ORACLE_SAMPLE[config][0]
-        r = run_oracle(config, levels, 1)
+        fd, u_path = tempfile.mkstemp(suffix=".npy")
+        os.close(fd)
+        r = run_oracle(config, levels, 1, u_path=u_path)
+        u_or = np.load(u_path)
+        os.unlink(u_path)
+        allc = run_oracle_all_cores(config, levels)
         full = dofs_of(problem_kwargs(config))
         scale = full / r["dofs"]
         t = r["times"][0]
         line["cpu_baseline"] = {
-            "value": 1.0 / (t * scale), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one oracle solve of the same discretisation truncated to {levels} levels "
-                       f"({r['dofs']} dofs) took {t:.1f} s on 1 host core; scaled x{scale:.1f} to "
-                       f"{full} dofs by the method's linear work (Theorem 3.3)"),
+            "value": 1.0 / (allc["per_sample_s"] * scale), "unit": "solves/s",
+            "cores": allc["procs"], "kind": "oracle",
+            "sample": (f"{allc['procs']} single-threaded oracle solves of the same discretisation "
+                       f"truncated to {levels} levels ({r['dofs']} dofs), one per host core at "
+                       f"once, took {allc['wall_s']:.1f} s of wall time; solves/s of the sample "
+                       f"scaled x{scale:.1f} to {full} dofs by the method's linear work "
+                       f"(Theorem 3.3)"),
+            "nproc": os.cpu_count(),
+            "bitwise_equal_across_cores": allc["digests"] == [r["digest"]],
+            "single_core": {
+                "value": 1.0 / (t * scale), "cores": 1,
+                "sample": (f"one oracle solve of the same {r['dofs']} dofs took {t:.1f} s on 1 "
+                           f"host core, scaled x{scale:.1f}")},
             "lambda_sample": r["lam"],
         }
+        if config in ("config2", "config3") and not args.no_extras:
+            acc = accuracy_vs_oracle(r["lam"], u_or, levels, read_golden_3d()) \
+                if config == "config2" else None
+            if acc:
+                line["accuracy_vs_oracle"] = acc
+                for key, _, _ in ACCURACY_MODES:
+                    row = acc[key][f"config2_{levels}levels"]
+                    tgt = line if key == "fp64" else line.get(key)
+                    if tgt is not None:
+                        tgt["dlambda_rel_vs_oracle"] = row["dlambda_rel"]
+                        tgt["du_rel_vs_oracle"] = row["du_rel_l2"]
+                        tgt["vs_oracle_at"] = (f"config 2 truncated to {levels} levels "
+                                               f"({r['dofs']} dofs), the oracle's own size")
+    if extras:
+        b = measure_batch(5, 3, world, local, dist)
+        line["config4_batch"] = {
+            "workload": WORKLOADS["config4"][2], "steps": 5, "warmup": 3,
+            "value": b["value"], "unit": "solves/s", "ms_per_step": b["ms_per_step"],
+            "sequential_fp64": b["sequential_fp64"],
+            "speedup_vs_sequential_fp64": b["value"] / world / b["sequential_fp64"]["value"],
+            "max_dlambda_rel_vs_sequential_fp64": b["max_dlambda_rel_vs_sequential_fp64"],
+            "all_converged": b["all_converged"], "e2e": b["e2e"], "clocks": b["clocks"],
+            "kernels_per_step": b["kernels"]}
+        sv = measure_serve(2000, args.serve_batch, args.serve_inflight, args.serve_window,
+                           world, local, dist)
+        line["config5_serve"] = {
+            "workload": "the config-5 stream's first 2,000 requests (200/s offered, 70% 2D / "
+                        "30% 3D), FP32 V-cycles in FP64 defect correction",
+            "value": sv["value"], "unit": "solves/s", "makespan_s": sv["st"]["makespan_s"],
+            **serve_summary(sv), "clocks": sv["clocks"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -841,9 +1076,13 @@ def main():
     ap.add_argument("--serve-batch", type=int, default=32)
     ap.add_argument("--serve-inflight", type=int, default=6)
     ap.add_argument("--serve-window", type=float, default=0.002)
+    ap.add_argument("--probe-fp64", action="store_true",
+                    help="measure the FP64 / FP32 multiply-add rate with clocks and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
+    if args.probe_fp64:
+        probe_arm(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         ours_arm(args)

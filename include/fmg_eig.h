@@ -175,6 +175,16 @@ int fmg_eig_set_params(fmg_eig_handle* h, const fmg_eig_problem* prob);
 int fmg_eig_kernel_count(const fmg_eig_handle* h);
 int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count);
 
+/* Arithmetic-throughput probe (instrumentation, no counterpart in the paper): the rate of
+ * fused multiply-adds this GPU sustains, the denominator of the roofline of the FP64-bound
+ * kernels of this library.  Launches ctas_per_sm (1..8) blocks per SM of 256 threads, each
+ * thread running 8 independent chains of `iters` multiply-adds in registers (fp64 != 0:
+ * FP64, else FP32), once to warm up and once timed with CUDA events on `stream` (NULL =
+ * legacy default stream).  Writes the timed launch's duration in ms to *ms_out and its flop
+ * count (2 per multiply-add) to *flops_out.  Allocates nothing; synchronous.               */
+int fmg_eig_probe_fma(int32_t fp64, int32_t ctas_per_sm, int32_t iters, void* stream,
+                      double* ms_out, double* flops_out);
+
 /* Fault injection for tests (no counterpart in the paper): after `after` more device
  * allocations by the library in this process succeed, the next one fails as if the device
  * were out of memory, once; later allocations succeed again.  A negative value cancels a

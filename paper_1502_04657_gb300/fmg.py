@@ -99,6 +99,7 @@ _SIGS = {
     "fmg_eig_coarse_solve": (C.c_int, [_P, _D, _P, C.POINTER(_I32)]),
     "fmg_eig_augmented_system": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _P]),
     "fmg_eig_inject_alloc_failure": (C.c_int, [C.c_int64]),
+    "fmg_eig_probe_fma": (C.c_int, [_I32, _I32, _I32, _P, _D, _D]),
     "fmg_eig_coarse_solve_noalloc": (C.c_int, [C.POINTER(fmg_eig_problem), _D, _P, C.POINTER(_I32), _P]),
     "fmg_eig_batch_create": (C.c_int, [C.POINTER(fmg_eig_problem), _I32, C.POINTER(_P)]),
     "fmg_eig_batch_count": (_I32, [_P]),
@@ -119,6 +120,16 @@ def inject_alloc_failure(after: int) -> None:
     """fmg_eig_inject_alloc_failure: the device allocation after `after` more successful ones
     fails once (test hook; negative cancels)."""
     load_library().fmg_eig_inject_alloc_failure(int(after))
+
+
+def probe_fma(fp64: bool = True, ctas_per_sm: int = 4, iters: int = 4096, stream=None):
+    """fmg_eig_probe_fma: (ms, flops) of one timed launch of the multiply-add probe."""
+    ms, fl = C.c_double(), C.c_double()
+    rc = load_library().fmg_eig_probe_fma(1 if fp64 else 0, ctas_per_sm, iters, stream,
+                                          C.byref(ms), C.byref(fl))
+    if rc != FMG_OK:
+        raise FmgError(rc, "fmg_eig_probe_fma")
+    return ms.value, fl.value
 
 
 def coarse_solve_noalloc(problem: "Problem", u_dev, stream=None):
