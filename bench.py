@@ -825,7 +825,7 @@ def fma_probe(fp64: bool = True, shapes=(2, 4, 8), reps: int = 3) -> dict:
     """Best multiply-add rate of the library's probe over a few launch shapes (TFLOP/s)."""
     from paper_1502_04657_gb300 import fmg
 
-    iters = 8192 if fp64 else 262144
+    iters = 16384 if fp64 else 262144
     best, rows = 0.0, []
     for cps in shapes:
         for _ in range(reps):

@@ -178,9 +178,9 @@ int fmg_eig_profile(fmg_eig_handle* h, double* ms, int32_t count);
 /* Arithmetic-throughput probe (instrumentation, no counterpart in the paper): the rate of
  * fused multiply-adds this GPU sustains, the denominator of the roofline of the FP64-bound
  * kernels of this library.  Launches ctas_per_sm (1..8) blocks per SM of 256 threads, each
- * thread running 8 independent chains of `iters` multiply-adds in registers (fp64 != 0:
- * FP64, else FP32), once to warm up and once timed with CUDA events on `stream` (NULL =
- * legacy default stream).  Writes the timed launch's duration in ms to *ms_out and its flop
+ * thread running 4 (fp64 != 0: FP64) or 8 (FP32) independent chains of `iters`
+ * multiply-adds in registers, once to warm up and once timed with CUDA events on `stream`
+ * (NULL = legacy default stream).  Writes the timed launch's duration in ms to *ms_out and its flop
  * count (2 per multiply-add) to *flops_out.  Allocates nothing; synchronous.               */
 int fmg_eig_probe_fma(int32_t fp64, int32_t ctas_per_sm, int32_t iters, void* stream,
                       double* ms_out, double* flops_out);

@@ -33,6 +33,7 @@
 // warp-synchronous triangular solves.  The iteration count is bounded by max_iter; hitting it
 // sets status 1.
 #include <math.h>
+#include <stdint.h>
 
 #include "fmg_internal.h"
 
@@ -48,6 +49,10 @@ __host__ __device__ inline bool loc_in_A(int n, int ntri, int nvert) {
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxVert = 4;
 constexpr double kSwitch = 1e-2;  // relative residual below which Newton takes over
+// refinement steps of the linear solves (single-precision inverse, FP64 residuals): a Newton
+// step needs its correction to about FP64 rounding, an inverse-power step only a direction
+constexpr int kRefineNewton = 2;
+constexpr int kRefinePower = 1;
 
 struct Smem {
   double *K0, *MM, *G, *A, *loc;
@@ -124,11 +129,11 @@ __device__ void symv(const double* const* X, const double* x, double* const* y, 
   __syncthreads();
 }
 
-// rows of (K0 c, G c, M c)
+// rows of (K0 c, G c); M c is kept up to date by normalise_and_sign
 __device__ void apply_all(Smem& s) {
-  const double* X[3] = {s.K0, s.G, s.MM};
-  double* Y[3] = {s.Hc, s.Gc, s.Mc};
-  symv<3>(X, s.c, Y, s.n, s.sv);
+  const double* X[2] = {s.K0, s.G};
+  double* Y[2] = {s.Hc, s.Gc};
+  symv<2>(X, s.c, Y, s.n, s.sv);
 }
 
 // Local contributions of each simplex T (one thread per simplex): the pair entries
@@ -157,7 +162,9 @@ __device__ void local_G(const DenseProblem& p, Smem& s, double cu) {
     const double h2 = 0.5 * fma(h1, h1, s2);  // sum_{i <= j} w_i w_j
     const double* t3 = s.t3 + (size_t)t * p.nt3;
     double* lt = s.loc + (size_t)t * L * L;
-    double x3[NV][NV];
+    double ucp[NV];  // sum_b w_b x3_ab, accumulated pair by pair (x3 is symmetric)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) ucp[a] = 0.0;
 #pragma unroll
     for (int a = 0; a < NV; ++a)
 #pragma unroll
@@ -166,11 +173,11 @@ __device__ void local_G(const DenseProblem& p, Smem& s, double cu) {
         if (a == b) v = 2.0 * p.quart_off * fma(3.0, sq[a], fma(2.0 * wv[a], h1, h2));
         else v = p.quart_off * (fma(wv[a] + wv[b], h1, h2) + fma(wv[a], wv[b], sq[a] + sq[b]));
         if (p.aug) {
-          double x = 0.0;
+          double x = 0.0;  // x3_ab = sum_c w_c T3_abc
 #pragma unroll
           for (int c = 0; c < NV; ++c) x = fma(wv[c], t3[s.sym3[(a * NV + b) * NV + c]], x);
-          x3[a][b] = x;
-          x3[b][a] = x;
+          ucp[a] = fma(wv[b], x, ucp[a]);
+          if (b != a) ucp[b] = fma(wv[a], x, ucp[b]);
           v = fma(2.0 * cu, x, v);
         }
         lt[a * L + b] = v;
@@ -178,12 +185,7 @@ __device__ void local_G(const DenseProblem& p, Smem& s, double cu) {
       }
     if (p.aug) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        double x = 0.0;
-#pragma unroll
-        for (int c = 0; c < NV; ++c) x = fma(wv[c], x3[a][c], x);
-        lt[a * L + NV] = x;
-      }
+      for (int a = 0; a < NV; ++a) lt[a * L + NV] = ucp[a];
     }
   }
 }
@@ -286,6 +288,251 @@ __device__ void ldlt_solve_warp(const double* A, const double* dinv, int n, doub
   }
 }
 
+// Inverse of an SPD n x n matrix in single precision by the sweep operator (Gauss-Jordan
+// elimination without pivoting, stable for SPD matrices).  Sweeping a set P of indices maps
+// M to M' with H = (M_PP)^{-1}:
+//     M'_PP = -H,  M'_Pj = H M_Pj,  M'_iP = M_iP H,  M'_ij = M_ij - M_iP H M_Pj  (i, j not in P),
+// and after sweeping every index the matrix is -A^{-1}.  Sweeping P at once equals sweeping
+// its indices one after another, so the indices go in blocks of 4 (the matrix padded to a
+// multiple of 4 with an identity block, which sweeps to itself): one barrier per block.  The
+// sweep keeps M symmetric, so the pivot columns are read from the pivot rows.  Each row
+// belongs to 256 / R threads (R = 64 rows for n <= 64, 32 for n <= 32), each keeping
+// C = R / (256 / R) contiguous columns in registers for the whole elimination; the owners of
+// the next pivot rows publish them to shared memory (rowb: 2 x 4 rows of 64 floats,
+// double-buffered, 16-byte aligned).  Every thread inverts the 4 x 4 pivot block itself, by
+// four scalar sweeps in registers with fast approximate reciprocals (their error is one more
+// single-precision rounding, which the refinement removes).
+template <int R>
+__device__ __forceinline__ void sweep_rows(const double* __restrict__ A, float* __restrict__ M,
+                                           float* __restrict__ rowb, int n, bool& ok) {
+  constexpr int T = kThreads / R;  // threads per row
+  constexpr int C = R / T;         // columns per thread (T C = R >= n), a multiple of 4
+  const int i = threadIdx.x / T, jb = (threadIdx.x % T) * C;
+  const int np = (n + 3) & ~3;     // padded size, <= R
+  float v[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    const int j = jb + q;
+    v[q] = i < n && j < n ? (float)A[i * n + j] : (i == j ? 1.0f : 0.0f);
+  }
+  if (i < 4) {
+#pragma unroll
+    for (int q = 0; q < C; q += 4)
+      *reinterpret_cast<float4*>(rowb + i * 64 + jb + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+  }
+  __syncthreads();
+  for (int k = 0; k < np; k += 4) {
+    const float* rb = rowb + ((k >> 2) & 1) * 256;  // rows k .. k + 3
+    // H = (M_PP)^{-1}: four scalar sweeps of the pivot block give -H
+    float h[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) h[r][c] = rb[r * 64 + k + c];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float d = h[m][m];
+      if (!(d > 0.0f)) {
+        ok = false;
+        return;
+      }
+      const float inv = __fdividef(1.0f, d);
+      float g[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (r == m) g[r][c] = c == m ? -inv : h[m][c] * inv;
+          else g[r][c] = c == m ? h[r][m] * inv : fmaf(-h[r][m] * inv, h[m][c], h[r][c]);
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) h[r][c] = g[r][c];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) h[r][c] = -h[r][c];  // the sweeps left -H
+    float f[4];  // M_iP H, with M_iP = M_Pi from the pivot rows
+    {
+      float mi[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) mi[r] = rb[r * 64 + i];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        f[c] = fmaf(mi[0], h[0][c], fmaf(mi[1], h[1][c], fmaf(mi[2], h[2][c], mi[3] * h[3][c])));
+    }
+    const bool prow = i >= k && i < k + 4;
+#pragma unroll
+    for (int q = 0; q < C; q += 4) {
+      float4 a[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = *reinterpret_cast<const float4*>(rb + r * 64 + jb + q);
+      const float ak[4][4] = {{a[0].x, a[1].x, a[2].x, a[3].x}, {a[0].y, a[1].y, a[2].y, a[3].y},
+                              {a[0].z, a[1].z, a[2].z, a[3].z}, {a[0].w, a[1].w, a[2].w, a[3].w}};
+      if (jb + q == k) {  // the pivot columns: M_iP H, or -H on the pivot rows
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float hv = 0.0f;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (i == k + r) hv = -h[r][e];
+          v[q + e] = prow ? hv : f[e];
+        }
+      } else if (prow) {  // the pivot rows: H M_Pj
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float hv = 0.0f;
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (i == k + r)
+              hv = fmaf(h[r][0], ak[e][0], fmaf(h[r][1], ak[e][1], fmaf(h[r][2], ak[e][2], h[r][3] * ak[e][3])));
+          v[q + e] = hv;
+        }
+      } else {  // M_ij - M_iP H M_Pj
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          v[q + e] = fmaf(-f[0], ak[e][0], fmaf(-f[1], ak[e][1], fmaf(-f[2], ak[e][2], fmaf(-f[3], ak[e][3], v[q + e]))));
+      }
+    }
+    if (k + 4 < np && i >= k + 4 && i < k + 8) {  // publish rows k + 4 .. k + 7
+      float* rn = rowb + (((k >> 2) + 1) & 1) * 256 + (i - k - 4) * 64;
+#pragma unroll
+      for (int q = 0; q < C; q += 4)
+        *reinterpret_cast<float4*>(rn + jb + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    }
+    __syncthreads();
+  }
+  if (i < n) {
+#pragma unroll
+    for (int q = 0; q < C; ++q)
+      if (jb + q < n) M[i * n + jb + q] = v[q];
+  }
+  __syncthreads();
+}
+
+// -A^{-1} into M (n x n floats, row-major) for an SPD FP64 n x n matrix A, n <= 64; false at
+// a non-positive pivot or for n > 64 (every thread reads the same pivots, so all return
+// together).  rowb: 512 floats, 16-byte aligned.
+__device__ __forceinline__ bool sweep_inverse(const double* __restrict__ A, float* __restrict__ M,
+                                              float* __restrict__ rowb, int n) {
+  bool ok = true;
+  if (n <= 32) sweep_rows<32>(A, M, rowb, n, ok);
+  else if (n <= 64) sweep_rows<64>(A, M, rowb, n, ok);
+  else ok = false;
+  return ok;
+}
+
+// y_v = X x_v (v < NV) for one symmetric FP64 n x n matrix X and NV FP64 vectors, with the
+// row/part split of symv.  red: parts * n * NV doubles.
+template <int NV>
+__device__ void symv_vec(const double* X, const double* const* x, double* const* y, int n,
+                         double* red) {
+  const int parts = n <= kThreads ? kThreads / n : 1;
+  const int t = threadIdx.x;
+  const int a = t % n, part = t / n;
+  if (part < parts && t < parts * n) {
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int b = part; b < n; b += parts) {
+      const double xab = X[(size_t)b * n + a];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = fma(xab, x[v][b], acc[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[((size_t)v * parts + part) * n + a] = acc[v];
+  }
+  __syncthreads();
+  for (int r = t; r < n; r += kThreads) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double w = 0.0;
+      for (int pp = 0; pp < parts; ++pp) w += red[((size_t)v * parts + pp) * n + r];
+      y[v][r] = w;
+    }
+  }
+  __syncthreads();
+}
+
+// y_v (FP64) = -X x_v for the single-precision symmetric matrix X = -A^{-1} of the sweep
+// operator and NV vectors x_v (FP64), all in single precision: the vectors are rounded to
+// FP32 once into xf (NV n floats), the parts summed in FP32 in redf (parts n NV floats), and
+// only the n NV results converted back.  (Conversions between FP64 and FP32 issue at the
+// FP64 rate, so none sits inside the n^2 loop.)
+template <int NV>
+__device__ void symv_f32(const float* X, const double* const* x, double* const* y, int n,
+                         float* xf, float* redf) {
+  for (int r = threadIdx.x; r < n; r += kThreads) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) xf[v * n + r] = (float)x[v][r];
+  }
+  __syncthreads();
+  const int parts = n <= kThreads ? kThreads / n : 1;
+  const int t = threadIdx.x;
+  const int a = t % n, part = t / n;
+  if (part < parts && t < parts * n) {
+    float acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0f;
+    for (int b = part; b < n; b += parts) {
+      const float xab = X[(size_t)b * n + a];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = fmaf(xab, xf[v * n + b], acc[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) redf[((size_t)v * parts + part) * n + a] = acc[v];
+  }
+  __syncthreads();
+  for (int r = t; r < n; r += kThreads) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float w = 0.0f;
+      for (int pp = 0; pp < parts; ++pp) w += redf[((size_t)v * parts + pp) * n + r];
+      y[v][r] = -(double)w;
+    }
+  }
+  __syncthreads();
+}
+
+// Solve A y_v = b_v (v < NV) for the SPD FP64 matrix A (kept intact) to FP64 accuracy:
+// A^{-1} in single precision by the sweep operator (in the two float buffers P0, P1), then
+// `refine` steps of iterative refinement with FP64 residuals e = b - A y.  Each step cuts the
+// error by about cond(A) 2^-24 (cond(A) is of order 10^3 for these coarse spaces), so two
+// steps reach FP64 rounding.  b_v is read, y_v written, e_v is scratch; false (nothing
+// written) when the single-precision elimination meets a non-positive pivot.
+template <int NV>
+__device__ __forceinline__ bool solve_refined(const double* A, float* Ainv, int n,
+                                              const double* const* b, double* const* y,
+                                              double* const* e, int refine, double* red) {
+  // single-precision staging in the reduction scratch (3 kThreads doubles = 1536 floats):
+  // the sweep's pivot rows (512 floats + alignment), then NV n floats of vectors
+  // and parts n NV <= kThreads NV floats of partial sums (n <= 64 here); symv_vec's use of
+  // it never overlaps
+  float* xf = reinterpret_cast<float*>(red);
+  // the pivot row is read as float4: 16-byte alignment (red is only 8-byte aligned)
+  float* rowb = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(red) + 15) & ~uintptr_t(15));
+  if (!sweep_inverse(A, Ainv, rowb, n)) return false;
+  float* redf = xf + NV * n;
+  symv_f32<NV>(Ainv, b, y, n, xf, redf);  // y = A^{-1} b
+  for (int it = 0; it < refine; ++it) {
+    symv_vec<NV>(A, y, e, n, red);  // e = A y
+    for (int r = threadIdx.x; r < n; r += kThreads) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) e[v][r] = b[v][r] - e[v][r];
+    }
+    __syncthreads();
+    symv_f32<NV>(Ainv, e, e, n, xf, redf);  // correction A^{-1} e, in place of e
+    for (int r = threadIdx.x; r < n; r += kThreads) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) y[v][r] += e[v][r];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 __device__ void normalise_and_sign(const DenseProblem& p, Smem& s) {
   const int n = s.n;
   {
@@ -304,11 +551,14 @@ __device__ void normalise_and_sign(const DenseProblem& p, Smem& s) {
   }
   __syncthreads();  // every thread has read c before any thread rescales it
   const double f = (sg < 0.0 ? -1.0 : 1.0) / sqrt(cmc);
-  for (int i = threadIdx.x; i < n; i += kThreads) s.c[i] *= f;
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    s.c[i] *= f;
+    s.Mc[i] *= f;  // M c of the rescaled c
+  }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
+__global__ void __launch_bounds__(kThreads, 2) k_dense_scf(DenseProblem p) {
   extern __shared__ double sm[];
   if (blockIdx.x) {  // instance blockIdx.x of a batch: its slices of the per-instance arrays
     const size_t b = blockIdx.x, nh = p.nh, cs = nh + 1;
@@ -332,41 +582,47 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
     }
   }
   __shared__ int sym3_tab[kMaxVert * kMaxVert * kMaxVert];
-  Smem s;
-  s.nh = p.nh;
-  s.n = p.nh + p.aug;
-  s.L = p.nvert + 1;
-  const int n = s.n, nh = s.nh, nv = p.nvert;
+  // the layout is computed by every thread, then kept in shared memory (published by thread
+  // 0), so its ~25 pointers need not stay in registers through the iteration
+  __shared__ Smem s_layout;
+  Smem sl;
+  sl.nh = p.nh;
+  sl.n = p.nh + p.aug;
+  sl.L = p.nvert + 1;
+  const int n = sl.n, nh = sl.nh, nv = p.nvert;
   double* q = sm;
-  s.K0 = q; q += (size_t)n * n;
-  s.MM = q; q += (size_t)n * n;
-  s.G = q; q += (size_t)n * n;
-  s.A = q; q += (size_t)n * n;
+  sl.K0 = q; q += (size_t)n * n;
+  sl.MM = q; q += (size_t)n * n;
+  sl.G = q; q += (size_t)n * n;
+  sl.A = q; q += (size_t)n * n;
   // the simplex-local blocks are only live inside build_G, when A is free: they share its
   // space when they fit (2D), which with B1 read from global memory keeps a 2D CTA under
   // half the shared memory of an SM (two instances of a batch per SM)
   if (loc_in_A(n, p.ntri, p.nvert)) {
-    s.loc = s.A;
+    sl.loc = sl.A;
   } else {
-    s.loc = q;
-    q += (size_t)p.ntri * s.L * s.L;
+    sl.loc = q;
+    q += (size_t)p.ntri * sl.L * sl.L;
   }
-  s.c = q; q += n;
-  s.Mc = q; q += n;
-  s.Hc = q; q += n;
-  s.Gc = q; q += n;
-  s.r = q; q += n;
-  s.y1 = q; q += n;
-  s.y2 = q; q += n;
-  s.dinv = q; q += n;
-  s.red = q; q += kThreads;
-  s.sv = q; q += 3 * kThreads;
-  s.t1 = q; q += nh;
-  s.t3 = q; q += p.aug ? (size_t)p.ntri * p.nt3 : 0;
-  s.tri = reinterpret_cast<int*>(q); q += ((size_t)p.ntri * nv + 1) / 2;
-  s.adj = reinterpret_cast<int*>(q); q += ((size_t)nh * p.maxadj + 1) / 2;
-  s.B1 = p.aug ? p.B1 : nullptr;  // nh * nh in global memory (read twice per build_G)
-  s.sym3 = sym3_tab;
+  sl.c = q; q += n;
+  sl.Mc = q; q += n;
+  sl.Hc = q; q += n;
+  sl.Gc = q; q += n;
+  sl.r = q; q += n;
+  sl.y1 = q; q += n;
+  sl.y2 = q; q += n;
+  sl.dinv = q; q += n;
+  sl.red = q; q += kThreads;
+  sl.sv = q; q += 3 * kThreads;
+  sl.t1 = q; q += nh;
+  sl.t3 = q; q += p.aug ? (size_t)p.ntri * p.nt3 : 0;
+  sl.tri = reinterpret_cast<int*>(q); q += ((size_t)p.ntri * nv + 1) / 2;
+  sl.adj = reinterpret_cast<int*>(q); q += ((size_t)nh * p.maxadj + 1) / 2;
+  sl.B1 = p.aug ? p.B1 : nullptr;  // nh * nh in global memory (read twice per build_G)
+  sl.sym3 = sym3_tab;
+  if (threadIdx.x == 0) s_layout = sl;
+  __syncthreads();
+  Smem& s = s_layout;
 
   const double zeta = p.params->zeta;
   for (int e = threadIdx.x; e < n * n; e += kThreads) {
@@ -420,7 +676,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
   double lam = 0.0;
   for (;; ++it) {
     build_G(p, s);
-    apply_all(s);  // Hc = K0 c, Gc = G c, Mc = M c
+    apply_all(s);  // Hc = K0 c, Gc = G c (Mc = M c from normalise_and_sign)
     for (int a = threadIdx.x; a < n; a += kThreads) s.Hc[a] = fma(zeta, s.Gc[a], s.Hc[a]);
     __syncthreads();
     lam = dotv(s.c, s.Hc, n, s.red);
@@ -440,24 +696,46 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
     }
     if (it >= p.max_iter) break;
     bool newton = rn <= kSwitch;
+    // the single-precision inverse of the linear solves below lives in G's space (G is not
+    // read again before the next build_G)
+    float* Pinv = reinterpret_cast<float*>(s.G);
+    bool g_valid = true;
     if (newton) {
-      // A' = K0 + 3 zeta G - lambda M + |lambda| (Mc)(Mc)^T
-      const double tau = fabs(lam);
+      // A' = K0 + 3 zeta G - lambda M + |lambda| (Mc)(Mc)^T, symmetric: the lower triangle
+      // in FP64 (|lambda| Mc staged in dinv), then mirrored
+      const double tau = fabs(lam), z3 = 3.0 * zeta;
+      for (int a = threadIdx.x; a < n; a += kThreads) s.dinv[a] = tau * s.Mc[a];
+      __syncthreads();
       for (int e = threadIdx.x; e < n * n; e += kThreads) {
         const int a = e / n, b = e - (e / n) * n;
-        s.A[e] = fma(tau * s.Mc[a], s.Mc[b],
-                     fma(3.0 * zeta, s.G[e], fma(-lam, s.MM[e], s.K0[e])));
-      }
-      for (int a = threadIdx.x; a < n; a += kThreads) {
-        s.y1[a] = s.r[a];
-        s.y2[a] = s.Mc[a];
+        if (b <= a)
+          s.A[e] = fma(s.dinv[a], s.Mc[b], fma(z3, s.G[e], fma(-lam, s.MM[e], s.K0[e])));
       }
       __syncthreads();
-      newton = ldlt(s.A, n, s.dinv);
-      if (newton) {
-        if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
-        else if ((threadIdx.x >> 5) == 1) ldlt_solve_warp(s.A, s.dinv, n, s.y2);
+      for (int e = threadIdx.x; e < n * n; e += kThreads) {
+        const int a = e / n, b = e - (e / n) * n;
+        if (b > a) s.A[e] = s.A[(size_t)b * n + a];
+      }
+      __syncthreads();
+      const double* rhs[2] = {s.r, s.Mc};
+      double* sol[2] = {s.y1, s.y2};
+      double* scr[2] = {s.Hc, s.Gc};
+      g_valid = false;
+      if (!solve_refined<2>(s.A, Pinv, n, rhs, sol, scr, kRefineNewton, s.sv)) {
+        // single precision met a non-positive pivot: LDL^T in FP64
+        for (int a = threadIdx.x; a < n; a += kThreads) {
+          s.y1[a] = s.r[a];
+          s.y2[a] = s.Mc[a];
+        }
         __syncthreads();
+        newton = ldlt(s.A, n, s.dinv);
+        if (newton) {
+          if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
+          else if ((threadIdx.x >> 5) == 1) ldlt_solve_warp(s.A, s.dinv, n, s.y2);
+          __syncthreads();
+        }
+      }
+      if (newton) {
         const double m1 = dotv(s.Mc, s.y1, n, s.red);
         const double m2 = dotv(s.Mc, s.y2, n, s.red);
         const double dl = m1 / m2;
@@ -467,12 +745,19 @@ __global__ void __launch_bounds__(kThreads) k_dense_scf(DenseProblem p) {
     }
     if (!newton) {
       // inverse-power step: c <- (K0 + zeta G)^{-1} M c
+      if (!g_valid) build_G(p, s);  // the Newton attempt overwrote G
       for (int e = threadIdx.x; e < n * n; e += kThreads) s.A[e] = fma(zeta, s.G[e], s.K0[e]);
-      for (int a = threadIdx.x; a < n; a += kThreads) s.y1[a] = s.Mc[a];
       __syncthreads();
-      if (!ldlt(s.A, n, s.dinv)) break;
-      if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
-      __syncthreads();
+      const double* rhs[1] = {s.Mc};
+      double* sol[1] = {s.y1};
+      double* scr[1] = {s.Hc};
+      if (!solve_refined<1>(s.A, Pinv, n, rhs, sol, scr, kRefinePower, s.sv)) {
+        for (int a = threadIdx.x; a < n; a += kThreads) s.y1[a] = s.Mc[a];
+        __syncthreads();
+        if (!ldlt(s.A, n, s.dinv)) break;
+        if ((threadIdx.x >> 5) == 0) ldlt_solve_warp(s.A, s.dinv, n, s.y1);
+        __syncthreads();
+      }
       for (int a = threadIdx.x; a < n; a += kThreads) s.c[a] = s.y1[a];
       __syncthreads();
     }

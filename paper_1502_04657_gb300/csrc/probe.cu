@@ -1,34 +1,42 @@
 // Arithmetic-throughput probe: the FP64 (and FP32) fused multiply-add rate this GPU sustains,
 // the denominator of the roofline of the FP64-bound kernels.
 //
-// Every thread runs kChains independent multiply-add chains a <- a * b + c in registers (b
-// just below 1, so the values settle near c / (1 - b) and stay normal), `iters` rounds of all
-// chains, on ctas_per_sm x SMs blocks of kThreads threads.  The chains give enough
-// independent instructions per warp to keep the pipe busy whatever its latency; the result
-// reaches memory only through a store that a value test never takes, so the compiler keeps
-// every operation and the probe needs no buffer.  One multiply-add counts 2 flops.
+// Every thread runs C independent multiply-add chains a <- a * b + c in registers (b just
+// below 1, so the values settle near c / (1 - b) and stay normal), `iters` rounds of all
+// chains, on ctas_per_sm x SMs blocks of kThreads threads; the result reaches memory only
+// through a store that a value test never takes, so the compiler keeps every operation and
+// the probe needs no buffer.  One multiply-add counts 2 flops.  The form is the one that
+// measured fastest on GB300: FP64 multiply-adds (and adds and multiplies alike) peak with 4
+// chains per thread, each with its own multiplier and addend registers (1.91 of the nominal 2
+// lanes per clock per SM; 8 chains reached 1.67, 16 chains 1.58, whatever the occupancy);
+// FP32 with 8.
 #include "fmg_internal.h"
 
 namespace fmg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChains = 8;
+constexpr int kChains64 = 4;
+constexpr int kChains32 = 8;
 
 __device__ double g_probe_sink;
 
-template <typename T>
+template <typename T, int C>
 __global__ void __launch_bounds__(kThreads) k_fma_probe(int iters, T b, T c) {
-  T a[kChains];
+  T a[C], bk[C], ck[C];  // every chain has its own operands (the fastest form measured)
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) a[k] = (T)(threadIdx.x + k);
+  for (int k = 0; k < C; ++k) {
+    a[k] = (T)(threadIdx.x + k);
+    bk[k] = b - (T)k * (T)1e-9;
+    ck[k] = c + (T)k * (T)1e-9;
+  }
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], b, c);
+    for (int k = 0; k < C; ++k) a[k] = fma(a[k], bk[k], ck[k]);
   }
   T s = 0;
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) s += a[k];
+  for (int k = 0; k < C; ++k) s += a[k];
   if (s == (T)-1) g_probe_sink = (double)s;  // never true: keeps the chains alive
 }
 
@@ -56,8 +64,8 @@ extern "C" int fmg_eig_probe_fma(int32_t fp64, int32_t ctas_per_sm, int32_t iter
     return FMG_ECUDA;
   }
   auto launch = [&]() {
-    if (fp64) k_fma_probe<double><<<blocks, kThreads, 0, s>>>(iters, 0.999999, 1e-6);
-    else k_fma_probe<float><<<blocks, kThreads, 0, s>>>(iters, 0.999f, 1e-3f);
+    if (fp64) k_fma_probe<double, kChains64><<<blocks, kThreads, 0, s>>>(iters, 0.999999, 1e-6);
+    else k_fma_probe<float, kChains32><<<blocks, kThreads, 0, s>>>(iters, 0.999f, 1e-3f);
   };
   launch();  // warm-up (module load, clocks)
   cudaEventRecord(e0, s);
@@ -73,6 +81,6 @@ extern "C" int fmg_eig_probe_fma(int32_t fp64, int32_t ctas_per_sm, int32_t iter
     return FMG_ECUDA;
   }
   *ms_out = ms;
-  *flops_out = 2.0 * kChains * (double)iters * kThreads * (double)blocks;
+  *flops_out = 2.0 * (fp64 ? kChains64 : kChains32) * (double)iters * kThreads * (double)blocks;
   return FMG_OK;
 }

@@ -1,6 +1,12 @@
 """Mixed precision (FP32 V-cycles inside the FP64 defect correction) against the FP64 solve
 and the FP64 oracle.  The accuracy target is the benchmark's |delta lambda| <= 1e-8, read
-relative to lambda, against the FP64 result; the eigenvector is compared in relative L2 norm."""
+relative to lambda, against the FP64 result; the eigenvector is compared in relative L2 norm.
+
+Within a full solve the single-precision V-cycles run only on FMG stages with at least 512
+(2D) or 128 (3D) cells per side, so the whole-solve cases here (smaller) check that the mixed
+mode keeps the FP64 path on its small stages; the component multigrid call always takes the
+single-precision path, and test_gpu_mixed_oracle.py compares the single-precision stages
+with the oracle at the sizes where they run."""
 import numpy as np
 import pytest
 
