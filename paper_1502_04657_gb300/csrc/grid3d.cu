@@ -426,8 +426,9 @@ __global__ void k_rhs3d_node(int n, int pitch, size_t st, double h3, double nsca
 // FP64 kernels from the plane walk (star3d.cuh): 6 x the star sum of
 // h3 + u_p h2 + u_p^2 h1 + u_p^3 is S3 + 3 u_p S2 + 6 u_p^2 S1 + 144 u_p^3 in its sums of
 // h1, 2 h2, 6 h3; launch with star3_grid / star3_block and kS3Smem bytes.
-__device__ __forceinline__ double star3_cubic6(const Star3& p) {
-  return fma(p.u, fma(p.u, fma(144.0, p.u, 6.0 * p.S1), 3.0 * p.S2), p.S3);
+template <typename T>
+__device__ __forceinline__ T star3_cubic6(const Star3T<T>& p) {
+  return fma(p.u, fma(p.u, fma(T(144), p.u, T(6) * p.S1), T(3) * p.S2), p.S3);
 }
 
 __global__ void __launch_bounds__(kS3X * kS3Y, 2)
@@ -466,6 +467,38 @@ __global__ void __launch_bounds__(kS3X * kS3Y, 2)
       const double two_ne = (d >= 3 && d < 6) ? 8.0 : 12.0;
       b.a[1 + d][k] = s420_2 * fma(two_ne, t, fma(p.u + p.un[d], 2.0 * p.E1[d], p.E2[d]));
     }
+  });
+}
+
+// The same two walks in double-float arithmetic from the split u (mixed-precision modes): the
+// density stencil is stored split (put_entry) for the coarsening chain, N(u~) and the
+// right-hand side are combined in FP64.  Forming each tetrahedron's symmetric sums once
+// needs about half the double-float operations of the node-by-node form (k_*_node below).
+__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+    k_nload_density3d_df(int n, int pitch, size_t st, dfloat s140_6, dfloat s210_2,
+                         dfloat s420_2, SplitVec u, double* __restrict__ nl, Density3D b) {
+  star3_walk<true, dfloat>(n, pitch, st, u, [&](size_t k, const Star3T<dfloat>& p) {
+    nl[k] = out_of(s140_6 * star3_cubic6(p));
+    put_entry(b.a[0], k, s210_2 * fma(p.u, fma(dfloat(144), p.u, dfloat(4) * p.S1), p.S2));
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+      const dfloat t = fma(p.u, p.un[d], p.q + p.qn[d]);  // u_p^2 + u_q^2 + u_p u_q
+      const dfloat two_ne((d >= 3 && d < 6) ? 8 : 12);
+      put_entry(b.a[1 + d], k,
+                s420_2 * fma(two_ne, t, fma(p.u + p.un[d], dfloat(2) * p.E1[d], p.E2[d])));
+    }
+  });
+}
+
+__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+    k_rhs3d_dfw(int n, int pitch, size_t st, dfloat h3_120, dfloat nscale6,
+                const double* __restrict__ lam, const PotentialParams* __restrict__ pp, SplitVec u,
+                double* __restrict__ f) {
+  const int ib = blockIdx.z / star3_zchunks(n);
+  const double l = lam[ib], zeta = pp[ib].zeta;
+  star3_walk<false, dfloat>(n, pitch, st, u, [&](size_t k, const Star3T<dfloat>& p) {
+    const double mu = to_double(h3_120 * fma(dfloat(24), p.u, p.S1));
+    f[k] = fma(l, mu, -zeta * to_double(nscale6 * star3_cubic6(p)));
   });
 }
 
@@ -764,6 +797,14 @@ void nload_density3d(const Grid& g, const double* u, double* nl, const Density3D
 void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& b,
                         cudaStream_t s) {
   const double vol = g.h * g.h * g.h / 6.0;
+  if (star3_walks(g)) {
+    static const cudaError_t attr = star3_prepare(k_nload_density3d_df);
+    (void)attr;
+    k_nload_density3d_df<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(
+        g.n, g.pitch, g.stride, dfloat(vol / 140.0 / 6.0), dfloat(vol / 210.0 / 2.0),
+        dfloat(vol / 420.0 / 2.0), u, nl, b);
+    return;
+  }
   k_nload_density3d_node<dfloat, SplitVec, 2><<<INTERIOR_LAUNCH(g)>>>(
       g.n, g.pitch, g.stride, dfloat(vol / 140.0), dfloat(vol / 210.0), dfloat(vol / 420.0), u,
       nl, b);
@@ -772,6 +813,13 @@ void nload_density3d_df(const Grid& g, SplitVec u, double* nl, const Density3D& 
 void rhs3d_df(const Grid& g, const double* lam, const PotentialParams* p, SplitVec u, double* f,
               cudaStream_t s) {
   const double h3 = g.h * g.h * g.h;
+  if (star3_walks(g)) {
+    static const cudaError_t attr = star3_prepare(k_rhs3d_dfw);
+    (void)attr;
+    k_rhs3d_dfw<<<star3_grid(g.n, g.nb), star3_block(), kS3Smem, s>>>(
+        g.n, g.pitch, g.stride, dfloat(h3 / 120.0), dfloat(h3 / 6.0 / 140.0 / 6.0), lam, p, u, f);
+    return;
+  }
   k_rhs3d_df<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, dfloat(h3), dfloat(h3 / 6.0 / 140.0),
                                      lam, p, u, f);
 }

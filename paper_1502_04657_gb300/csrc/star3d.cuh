@@ -1,5 +1,6 @@
-// Plane-walked star sums of the 3D cubic load and density stencil, FP64 (device code of
-// grid3d.cu).
+// Plane-walked star sums of the 3D cubic load and density stencil (device code of
+// grid3d.cu), in FP64 or, for the mixed-precision modes, in double-float arithmetic (T =
+// dfloat, u read from its split copy).
 //
 // On a tetrahedron K with vertex values a, b, c, d let h1, h2, h3 be the complete homogeneous
 // symmetric sums of degree 1, 2, 3 of the four values.  Exact integration of P1 functions
@@ -26,6 +27,7 @@
 // the node above it.  Every sum is taken in a fixed order, so the result does not depend on
 // the launch shape.
 #pragma once
+#include "dfloat.cuh"
 #include "fmg_internal.h"
 
 namespace fmg {
@@ -36,18 +38,22 @@ constexpr int kS3Cubes = (kS3X + 1) * (kS3Y + 1);
 constexpr int kS3NX = kS3X + 2;                  // node plane row (nodes x0 - 1 .. x0 + 32)
 constexpr int kS3Nodes = (kS3X + 2) * (kS3Y + 2);
 constexpr int kS3Vals = 21;  // per cube: 6 tetrahedra x (h1, 2 h2, 6 h3), then their totals
-// three plane slots of (u, u^2, u^3) and one cube layer
+// three plane slots of (u, u^2, u^3) and one cube layer (a double-float value takes the 8
+// bytes of a double)
 constexpr size_t kS3Smem = sizeof(double) * (9 * (size_t)kS3Nodes + (size_t)kS3Vals * kS3Cubes);
+static_assert(sizeof(dfloat) == sizeof(double), "double-float values share the FP64 layout");
 
 // what a node hands to its epilogue: sums over its 24 tetrahedra of h1, 2 h2 and 6 h3, and for
 // each edge towards p + d (d = X, Y, Z, XY, XZ, YZ, XYZ) the sums of h1 and 2 h2 over the
 // tetrahedra of the edge with the values u, u^2 at p + d (EDGES only)
-struct Star3 {
-  double u, q;
-  double S1, S2, S3;
-  double E1[7], E2[7];
-  double un[7], qn[7];
+template <typename T>
+struct Star3T {
+  T u, q;
+  T S1, S2, S3;
+  T E1[7], E2[7];
+  T un[7], qn[7];
 };
+using Star3 = Star3T<double>;
 
 __host__ __device__ inline int star3_zchunks(int n) { return (n - 1 + kS3Z - 1) / kS3Z; }
 inline dim3 star3_grid(int n, int nb) {
@@ -68,14 +74,15 @@ inline bool star3_walks(const Grid& lv) {
 
 // blockDim = (kS3X, kS3Y), kS3Smem bytes of dynamic shared memory; instance
 // blockIdx.z / star3_zchunks(n).  out(k, star) for every interior node the block produces.
-template <bool EDGES, typename Out>
-__device__ __forceinline__ void star3_walk(int n, int pitch, size_t st,
-                                           const double* __restrict__ u, Out out) {
+// T: the arithmetic (double, or dfloat with u a SplitVec); the FP64 instantiation evaluates
+// exactly the expressions it did before it was templated.
+template <bool EDGES, typename T = double, typename U = const double*, typename Out>
+__device__ __forceinline__ void star3_walk(int n, int pitch, size_t st, const U u, Out out) {
   extern __shared__ double s3sm[];
-  double* const su = s3sm;                 // [3][kS3Nodes]
-  double* const sq = su + 3 * kS3Nodes;    // u^2
-  double* const sc = sq + 3 * kS3Nodes;    // u^3
-  double* const cube = sc + 3 * kS3Nodes;  // [kS3Vals][kS3Cubes]
+  T* const su = reinterpret_cast<T*>(s3sm);  // [3][kS3Nodes]
+  T* const sq = su + 3 * kS3Nodes;           // u^2
+  T* const sc = sq + 3 * kS3Nodes;           // u^3
+  T* const cube = sc + 3 * kS3Nodes;         // [kS3Vals][kS3Cubes]
   const int nzc = star3_zchunks(n);
   const int ib = blockIdx.z / nzc;
   const int z0 = 1 + (int)(blockIdx.z - ib * nzc) * kS3Z;
@@ -91,8 +98,8 @@ __device__ __forceinline__ void star3_walk(int n, int pitch, size_t st,
     for (int e = tid; e < kS3Nodes; e += kThreads) {
       const int xl = e % kS3NX, yl = e / kS3NX;
       const int x = x0 - 1 + xl, y = y0 - 1 + yl;
-      const double v = (x <= n && y <= n) ? u[base + zp * plane + (long)y * pitch + x] : 0.0;
-      const double v2 = v * v;
+      const T v = (x <= n && y <= n) ? get<T>(u, base + zp * plane + (long)y * pitch + x) : T(0);
+      const T v2 = v * v;
       su[sl + e] = v;
       sq[sl + e] = v2;
       sc[sl + e] = v2 * v;
@@ -105,18 +112,18 @@ __device__ __forceinline__ void star3_walk(int n, int pitch, size_t st,
       const int a = e % kS3CX, b = e / kS3CX;
       const int v0 = s0 + b * kS3NX + a, v1 = s1 + b * kS3NX + a;
       // corners: v, X, Y, XY in plane cz; Z, XZ, YZ, W in plane cz + 1
-      const double A = su[v0] + su[v1 + kS3NX + 1];
-      const double QA = sq[v0] + sq[v1 + kS3NX + 1];
-      const double CA = sc[v0] + sc[v1 + kS3NX + 1];
-      double h[6][3];
+      const T A = su[v0] + su[v1 + kS3NX + 1];
+      const T QA = sq[v0] + sq[v1 + kS3NX + 1];
+      const T CA = sc[v0] + sc[v1 + kS3NX + 1];
+      T h[6][3];
       auto tet = [&](int t, int iS, int iD) {
-        const double h1 = A + (su[iS] + su[iD]);
-        const double p2 = QA + (sq[iS] + sq[iD]);
-        const double p3 = CA + (sc[iS] + sc[iD]);
-        const double s2 = h1 * h1;
+        const T h1 = A + (su[iS] + su[iD]);
+        const T p2 = QA + (sq[iS] + sq[iD]);
+        const T p3 = CA + (sc[iS] + sc[iD]);
+        const T s2 = h1 * h1;
         h[t][0] = h1;
-        h[t][1] = s2 + p2;                            // 2 h2
-        h[t][2] = fma(h1, fma(3.0, p2, s2), 2.0 * p3);  // 6 h3
+        h[t][1] = s2 + p2;                              // 2 h2
+        h[t][2] = fma(h1, fma(T(3), p2, s2), T(2) * p3);  // 6 h3
       };
       const int X = v0 + 1, Y = v0 + kS3NX, XY = v0 + kS3NX + 1;
       const int Z = v1, XZ = v1 + 1, YZ = v1 + kS3NX;
@@ -148,13 +155,13 @@ __device__ __forceinline__ void star3_walk(int n, int pitch, size_t st,
 
   // contributions of layer z - 1 to the node of plane z: the node is corner Z of cube (x, y),
   // XZ of (x-1, y), YZ of (x, y-1) and W of (x-1, y-1)
-  double pS[3], pEX[2], pEY[2], pEXY[2];
-  double PZ[3];
+  T pS[3], pEX[2], pEY[2], pEXY[2];
+  T PZ[3];
   auto pending = [&]() {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const double pxz = G(1, j, c01) + G(4, j, c01);
-      const double pyz = G(3, j, c10) + G(5, j, c10);
+      const T pxz = G(1, j, c01) + G(4, j, c01);
+      const T pyz = G(3, j, c10) + G(5, j, c10);
       pS[j] = (PZ[j] + pxz) + (pyz + TOT(j, c00));
       if (EDGES && j < 2) {
         pEX[j] = G(4, j, c11) + pyz;   // edge +X: T4 of (x, y), pair YZ of (x, y-1)
@@ -180,19 +187,19 @@ __device__ __forceinline__ void star3_walk(int n, int pitch, size_t st,
     __syncthreads();
     // layer z: the node of plane z is corner v of cube (x, y), X of (x-1, y), Y of (x, y-1)
     // and XY of (x-1, y-1)
-    Star3 p;
+    Star3T<T> p;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const double px = G(0, j, c01) + G(1, j, c01);   // pair X of (x-1, y)
-      const double py = G(2, j, c10) + G(3, j, c10);   // pair Y of (x, y-1)
-      const double pxy = G(0, j, c00) + G(2, j, c00);  // pair XY of (x-1, y-1)
-      PZ[j] = G(4, j, c11) + G(5, j, c11);             // pair Z of (x, y)
-      const double S = pS[j] + ((TOT(j, c11) + px) + (py + pxy));
+      const T px = G(0, j, c01) + G(1, j, c01);   // pair X of (x-1, y)
+      const T py = G(2, j, c10) + G(3, j, c10);   // pair Y of (x, y-1)
+      const T pxy = G(0, j, c00) + G(2, j, c00);  // pair XY of (x-1, y-1)
+      PZ[j] = G(4, j, c11) + G(5, j, c11);        // pair Z of (x, y)
+      const T S = pS[j] + ((TOT(j, c11) + px) + (py + pxy));
       if (j == 0) p.S1 = S;
       else if (j == 1) p.S2 = S;
       else p.S3 = S;
       if (EDGES && j < 2) {
-        double* E = j == 0 ? p.E1 : p.E2;
+        T* E = j == 0 ? p.E1 : p.E2;
         E[0] = pEX[j] + ((G(0, j, c11) + G(1, j, c11)) + G(2, j, c10));
         E[1] = pEY[j] + ((G(2, j, c11) + G(3, j, c11)) + G(0, j, c01));
         E[2] = (PZ[j] + G(1, j, c01)) + (G(3, j, c10) + pxy);

@@ -75,3 +75,32 @@ def test_fp64_solve_spans_tiles(case):
     assert rc == 0
     assert abs(lam - ref.lam) / abs(ref.lam) <= 1e-11
     assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-9
+
+
+def test_mixed_double_float_walks_match_node_by_node_and_oracle():
+    """In the mixed modes the 3D cubic load, density stencil and right-hand side run in
+    double-float arithmetic, as plane walks where the FP64 ones walk (forced here on every
+    level) and node by node otherwise.  At this size every FMG stage keeps FP64 V-cycles, so
+    both must give the FP64 oracle's eigenpair to double-float rounding, and agree closely
+    with each other."""
+    fmg = _fmg()
+    kw, _ = CASES["3d_n48"]
+    op, gp = _pair(**kw)
+    key = (op.dim, op.coarse_cells, op.levels)
+    if key not in _SOLVED:
+        _SOLVED[key] = O.fmg_solve(op)
+    ref = _SOLVED[key]
+    out = {}
+    for mode, flags in (("walk", fmg.FMG_FLAG_STAR_WALKS), ("node", 0)):
+        gp.precision = fmg.FMG_MIXED_FP32
+        gp.flags = flags
+        with fmg.Solver(gp) as s:
+            u = np.empty(gp.size(gp.levels))
+            lam, _, rc = s.solve(u)
+        assert rc == 0
+        assert abs(lam - ref.lam) / ref.lam <= 1e-10
+        assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-8
+        out[mode] = (lam, u)
+    (lw, uw), (ln, un) = out["walk"], out["node"]
+    assert abs(lw - ln) / ln <= 1e-12
+    assert np.linalg.norm(uw - un) / np.linalg.norm(un) <= 1e-10
