@@ -117,11 +117,13 @@ MIXED_HBM_KERNELS = ("jacobi", "residual")
 # The mixed modes evaluate the cubic load + density stencil in double-float arithmetic on the
 # FP32 pipes: the kernel is bound by instruction issue (4 warp instructions per SM per clock).
 # Thread instructions per node (smsp__inst_executed.sum x 32 / nodes) and DRAM bytes per node
-# from one ncu capture of the finest launch of each mixed-precision solve.
+# from one ncu capture of each kernel: 2D the finest launch of the 10-level mixed solve
+# (node by node, 16,769,025 nodes); 3D the plane walk at h = 1/128 (2,048,383 nodes; the walk
+# runs every 3D level with n >= 128, so its per-node figures hold at h = 1/256).
 ISSUE_PER_CLK_SM = 4 * 32
-DF_INSTR_PER_NODE = {2: 618510721 * 32 / 16769025, 3: 2830436764 * 32 / 16581375}
+DF_INSTR_PER_NODE = {2: 618510721 * 32 / 16769025, 3: 200397029 * 32 / 2048383}
 DF_TRAFFIC_PER_NODE = {2: (136027392 + 609443328) / 16769025,
-                       3: (169865472 + 1133905920) / 16581375}
+                       3: (24750336 + 83417856) / 2048383}
 
 
 def hbm_peak() -> tuple[float, str]:

@@ -17,11 +17,15 @@ CASES = [
     dict(dim=2, coarse_cells=5, levels=1, w_quad=(1.0, 2.0, 0.0), zeta=3.0),     # coarse only
     dict(dim=3, coarse_cells=2, levels=2, w_quad=(0.0, 0.0, 0.0), zeta=0.0),     # 3D Laplacian
     dict(dim=2, coarse_cells=4, levels=3, w_const=5.0, w_quad=(0.0, 0.0, 0.0), zeta=200.0),
+    # 64 coarse unknowns: the augmented problems have 65, beyond the single-precision sweep
+    # inverse of the small solves (n <= 64), so they take its FP64 LDL^T fallback (3D coarse
+    # spaces of that size exceed the small solve's shared memory and are not supported)
+    dict(dim=2, coarse_cells=9, levels=3, w_quad=(1.0, 2.0, 0.0), zeta=30.0),
 ]
 
 
 @pytest.mark.parametrize("kw", CASES, ids=["linear", "laplace", "one-coarse-dof", "one-level",
-                                           "laplace-3d", "strong-zeta"])
+                                           "laplace-3d", "strong-zeta", "fallback-2d"])
 def test_degenerate_cases_match_oracle(kw):
     op, gp = _pair(**kw)
     ref = O.fmg_solve(op)
