@@ -37,12 +37,14 @@ __device__ __forceinline__ void monomials(double a, double b, double c, double* 
   m[15] = a * m[9]; m[16] = m[7] * b; m[17] = m[7] * c; m[18] = b * m[9]; m[19] = m[9] * c;
 }
 
-// Interior class: thread = one row (x1, x2) of the coarse cell, block (chunk of rows, tet,
-// instance).  On a row, the nodes strictly inside T_s are an interval of x0 (the chain
-// order a > b > c of T_s bounds x0 by the row's two other coordinates), and every monomial
-// is (powers of the row's fixed chain coordinates) x (a power of x0 / r): the thread sums
-// u (x0/r)^e, e = 0..3, along its interval (4 FMAs per node) and then adds the 20 monomial
-// sums of its row (40 FP64 operations per row).
+// Interior class: thread = one (x0, x2) line of the coarse cell along x1, x0 fastest across
+// the threads (coalesced loads), block (chunk of lines, tet, instance).  On a line, the nodes
+// strictly inside T_s are an interval of x1 (the chain order a > b > c of T_s bounds x1 by the
+// line's two other coordinates), and every monomial is (powers of the line's fixed chain
+// coordinates) x (a power of x1 / r): the thread sums u (x1/r)^e, e = 0..3, along its
+// interval with the powers from the level's table pw (4 FMAs per node, in two interleaved
+// sets of accumulators to halve the FP64 dependency chain) and then forms the 20 monomial
+// sums of its line.
 __constant__ int kMonoExpDev[20][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
                                        {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2},
                                        {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1},
@@ -58,7 +60,8 @@ __device__ __forceinline__ double pick4(double v0, double v1, double v2, double 
 
 __global__ void __launch_bounds__(kThreads)
     k_t3_interior3d(int pf, long planef, int n1, int r, size_t st, size_t pst,
-                    const double* __restrict__ u, double* __restrict__ partials) {
+                    const double* __restrict__ u, const double* __restrict__ pw,
+                    double* __restrict__ partials) {
   __shared__ double sh[kThreads];
   u += blockIdx.z * st;  // instance blockIdx.z
   partials += blockIdx.z * pst;
@@ -66,46 +69,58 @@ __global__ void __launch_bounds__(kThreads)
   const int cell = tet / 6, s = tet % 6;
   const int I = cell % n1, J = (cell / n1) % n1, L = cell / (n1 * n1);
   const int R = r + 1;
-  const double inv_r = 1.0 / r;
-  // chain position of axis 0 (the axis threads walk along)
-  const int pos0 = kPermDev[s][0] == 0 ? 0 : (kPermDev[s][1] == 0 ? 1 : 2);
+  // chain position of axis 1 (the axis threads walk along)
+  const int pos1 = kPermDev[s][0] == 1 ? 0 : (kPermDev[s][1] == 1 ? 1 : 2);
   double acc[kMono];
 #pragma unroll
   for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row < R * R) {
-    const int x1 = row % R, x2 = row / R;
-    // the two fixed chain coordinates (positions q1 < q2, the ones other than pos0)
-    const int q1 = pos0 == 0 ? 1 : 0, q2 = pos0 == 2 ? 1 : 2;
-    const int f1 = coord(kPermDev[s][q1], 0, x1, x2), f2 = coord(kPermDev[s][q2], 0, x1, x2);
-    // interval of x0 (exclusive bounds) from r > a > b > c > 0
+  const int line = blockIdx.x * blockDim.x + threadIdx.x;
+  if (line < R * R) {
+    const int x0 = line % R, x2 = line / R;
+    // the two fixed chain coordinates (positions q1 < q2, the ones other than pos1)
+    const int q1 = pos1 == 0 ? 1 : 0, q2 = pos1 == 2 ? 1 : 2;
+    const int f1 = coord(kPermDev[s][q1], x0, 0, x2), f2 = coord(kPermDev[s][q2], x0, 0, x2);
+    // interval of x1 (exclusive bounds) from r > a > b > c > 0
     int lo = 0, hi = -1;
-    if (pos0 == 0) {  // x0 = a, fixed b = f1, c = f2
+    if (pos1 == 0) {  // x1 = a, fixed b = f1, c = f2
       if (f1 > f2 && f2 > 0) { lo = f1; hi = r; }
-    } else if (pos0 == 1) {  // x0 = b, fixed a = f1, c = f2
+    } else if (pos1 == 1) {  // x1 = b, fixed a = f1, c = f2
       if (f1 < r && f2 > 0) { lo = f2; hi = f1; }
-    } else {  // x0 = c, fixed a = f1, b = f2
+    } else {  // x1 = c, fixed a = f1, b = f2
       if (f1 < r && f1 > f2) { lo = 0; hi = f2; }
     }
     if (lo + 1 < hi) {
-      const double* rowp =
-          u + (size_t)(L * r + x2) * planef + (size_t)(J * r + x1) * pf + (size_t)I * r;
-      double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
-      for (int x0 = lo + 1; x0 < hi; ++x0) {
-        const double val = rowp[x0];
-        const double t = x0 * inv_r, t2 = t * t;
-        m0 += val;
-        m1 = fma(val, t, m1);
-        m2 = fma(val, t2, m2);
-        m3 = fma(val, t2 * t, m3);
+      const double* colp =
+          u + (size_t)(L * r + x2) * planef + (size_t)(J * r) * pf + (size_t)(I * r + x0);
+      double m[2][4] = {{0.0, 0.0, 0.0, 0.0}, {0.0, 0.0, 0.0, 0.0}};
+      int x1 = lo + 1;
+      for (; x1 + 1 < hi; x1 += 2) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const double val = colp[(size_t)(x1 + h) * pf];
+          const double* p = pw + 4 * (x1 + h);  // (x1/r)^e
+          m[h][0] += val;
+          m[h][1] = fma(val, p[1], m[h][1]);
+          m[h][2] = fma(val, p[2], m[h][2]);
+          m[h][3] = fma(val, p[3], m[h][3]);
+        }
       }
-      const double g1 = f1 * inv_r, g2 = f2 * inv_r;
-      const double g1s = g1 * g1, g2s = g2 * g2;
+      if (x1 < hi) {
+        const double val = colp[(size_t)x1 * pf];
+        const double* p = pw + 4 * x1;
+        m[0][0] += val;
+        m[0][1] = fma(val, p[1], m[0][1]);
+        m[0][2] = fma(val, p[2], m[0][2]);
+        m[0][3] = fma(val, p[3], m[0][3]);
+      }
+      const double m0 = m[0][0] + m[1][0], m1 = m[0][1] + m[1][1], m2 = m[0][2] + m[1][2],
+                   m3 = m[0][3] + m[1][3];
+      const double* g1p = pw + 4 * f1;
+      const double* g2p = pw + 4 * f2;
 #pragma unroll
       for (int q = 0; q < kMono; ++q) {
-        const int e0 = kMonoExpDev[q][pos0], e1 = kMonoExpDev[q][q1], e2 = kMonoExpDev[q][q2];
-        acc[q] = pick4(1.0, g1, g1s, g1s * g1, e1) * pick4(1.0, g2, g2s, g2s * g2, e2) *
-                 pick4(m0, m1, m2, m3, e0);
+        const int e0 = kMonoExpDev[q][pos1], e1 = kMonoExpDev[q][q1], e2 = kMonoExpDev[q][q2];
+        acc[q] = g1p[e1] * g2p[e2] * pick4(m0, m1, m2, m3, e0);
       }
     }
   }
@@ -234,8 +249,8 @@ __global__ void k_t3_finalize3d(int chunks, double h3, size_t pst, size_t tst,
   t3[(size_t)tet * 20 + e] = h3 * acc;
 }
 
-// Interior: a block takes interior_threads(r) rows (whole warps, up to kThreads) of the
-// (r + 1)^2 rows of a tetrahedron.  Boundary: the face rows and edge nodes of a class number
+// Interior: a block takes interior_threads(r) lines (whole warps, up to kThreads) of the
+// (r + 1)^2 lines of a tetrahedron.  Boundary: the face rows and edge nodes of a class number
 // fewer than r, so a block of boundary_threads(r) covers them in one or a few passes.
 int interior_threads(int r) { return warps_for((long)(r + 1) * (r + 1), kThreads); }
 int interior_chunks(int r) {
@@ -357,8 +372,8 @@ size_t t3_partials3d(const Grid& fine, int n1) {
   return tets * kMono * ((size_t)interior_chunks(r) + (kClasses - 1));
 }
 
-void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
-                  double* partials, double* t3, cudaStream_t s) {
+void t3_moments3d(const Grid& fine, int n1, const double* u, const double* pw,
+                  const double* map, double* partials, double* t3, cudaStream_t s) {
   const int r = fine.n / n1;
   const int tets = 6 * n1 * n1 * n1;
   const int chunks = interior_chunks(r);
@@ -367,7 +382,7 @@ void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
   double* pin = partials;
   double* pbd = partials + (size_t)tets * chunks * kMono;
   k_t3_interior3d<<<dim3(chunks, tets, fine.nb), interior_threads(r), 0, s>>>(
-      fine.pitch, planef, n1, r, fine.stride, pst, u, pin);
+      fine.pitch, planef, n1, r, fine.stride, pst, u, pw, pin);
   k_t3_boundary3d<<<dim3(kClasses - 1, tets, fine.nb), boundary_threads(r), 0, s>>>(
       fine.pitch, planef, n1, r, fine.stride, pst, u, pbd);
   k_t3_finalize3d<<<dim3(tets, fine.nb), 32, 0, s>>>(chunks, fine.h * fine.h * fine.h, pst,

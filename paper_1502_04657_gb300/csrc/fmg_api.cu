@@ -140,7 +140,7 @@ void lv_coarsen_density(Level& fl, Level& cl, cudaStream_t s, bool split) {
 }
 void lv_t3(Level& l, int n1, const double* u, double* partials, double* t3, cudaStream_t s) {
   if (l.g.dim == 2) t3_moments2d(l.g, n1, u, l.pw, l.t3map, partials, t3, s);
-  else t3_moments3d(l.g, n1, u, l.t3map, partials, t3, s);
+  else t3_moments3d(l.g, n1, u, l.pw, l.t3map, partials, t3, s);
 }
 void lv_dense_level1(Level& l1, double* L, double* M, cudaStream_t s, bool full) {
   if (l1.g.dim == 2) dense_level1_2d(l1.g, full ? l1.cw : l1.c, L, M, s);
@@ -356,12 +356,12 @@ void build_levels(fmg_eig_handle* h) {
     l.z = h->alloc<double>(s);
     if (k >= 2) {
       const int r = 1 << (k - 1);
+      std::vector<double> pw(4 * (r + 1));  // (x/r)^m, m = 0..3, of the T3 sums
+      t3_power_table(r, pw.data());
+      l.pw = h->alloc<double>(pw.size());
+      if (!h->dry) cudaMemcpyAsync(l.pw, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice,
+                h->stream);
       if (dim == 2) {
-        std::vector<double> pw(4 * (r + 1));
-        t3_power_table(r, pw.data());
-        l.pw = h->alloc<double>(pw.size());
-        if (!h->dry) cudaMemcpyAsync(l.pw, pw.data(), pw.size() * sizeof(double), cudaMemcpyHostToDevice,
-                  h->stream);
         double map[2 * 10 * 25];
         t3_map2d(r, map);
         l.t3map = h->alloc<double>(2 * 10 * 25);

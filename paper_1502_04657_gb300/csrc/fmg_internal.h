@@ -153,8 +153,9 @@ void start_vector3d(const Grid& g, double* c, int cstride, cudaStream_t s);
 // tetrahedron index 6 * (I + n1 (J + n1 L)) + s, s the axis permutation in lexicographic
 // order, vertices (V, V + e_s0, V + e_s0 + e_s1, V + (1,1,1)).
 size_t t3_partials3d(const Grid& fine, int n1);
-void t3_moments3d(const Grid& fine, int n1, const double* u, const double* map,
-                  double* partials, double* t3, cudaStream_t s);
+// pw: the level's (x/r)^m table (t3_power_table)
+void t3_moments3d(const Grid& fine, int n1, const double* u, const double* pw,
+                  const double* map, double* partials, double* t3, cudaStream_t s);
 void t3_map3d(int r, double* out);  // 20 * 15 * 20 doubles
 
 // ---- Mixed precision (mixed.cu) ------------------------------------------------------------
