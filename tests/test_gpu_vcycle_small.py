@@ -1,8 +1,10 @@
 """The small levels of a 2D V-cycle (at most 32 cells per side) run as one fused kernel per
 V-cycle.  It evaluates the same expressions in the same order as the separate sweep and
 transfer kernels, so results must be bit-identical to FMG_FLAG_SEPARATE_VCYCLE: for the
-component V-cycles, for whole solves with even and odd sweep counts (which decide the
-ping-pong buffer of the result) and for a batch of uneven instances."""
+component V-cycles (entered at the fused levels and above them, on even and odd coarse
+sizes), for whole solves with even and odd sweep counts (which decide the ping-pong buffer of
+the result) up to 4 + 4 and beyond, on hierarchies up to 256 cells per side, and for a batch
+of uneven instances."""
 import numpy as np
 import pytest
 
@@ -25,9 +27,9 @@ def _separate(p):
     return q
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
-def test_component_vcycles_bit_identical(k):
-    p = _problem()
+@pytest.mark.parametrize("k,cells", [(2, 8), (3, 8), (4, 8), (5, 6), (6, 8)])
+def test_component_vcycles_bit_identical(k, cells):
+    p = _problem(coarse_cells=cells, levels=6)
     rng = np.random.default_rng(1500 + k)
     f, x0 = rng.normal(size=(2, p.size(k)))
     out = []
@@ -39,8 +41,9 @@ def test_component_vcycles_bit_identical(k):
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("nu", [(2, 2), (1, 3), (0, 1), (3, 0)], ids=lambda t: f"nu{t[0]}{t[1]}")
-@pytest.mark.parametrize("cells,levels", [(8, 5), (4, 4), (6, 3)])
+@pytest.mark.parametrize("nu", [(2, 2), (1, 3), (0, 1), (3, 0), (4, 4), (5, 1)],
+                         ids=lambda t: f"nu{t[0]}{t[1]}")
+@pytest.mark.parametrize("cells,levels", [(8, 5), (4, 4), (6, 3), (6, 6), (8, 6)])
 def test_solves_bit_identical(nu, cells, levels):
     p = _problem(coarse_cells=cells, levels=levels, nu_pre=nu[0], nu_post=nu[1])
     res = []
