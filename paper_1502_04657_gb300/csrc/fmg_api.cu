@@ -748,6 +748,16 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
     return;
   }
   const fmg_eig_problem& p = h->prob;
+  if (!l.tma && !(p.flags & FMG_FLAG_SEPARATE_VCYCLE) &&
+      vcycle32_mid_applies(l.g, p.nu_pre, p.nu_post)) {
+    // both legs of the level in one kernel each (vcycle32_mid.cu), same results
+    Level& lc = h->L(j - 1);
+    vcycle32_down2d(l.g, l.ct, lc.g, l.f32, l.x32, lc.f32, p.nu_pre, s, bf);
+    enqueue_vcycle32(h, j - 1, s);
+    vcycle32_up2d(l.g, l.ct, lc.g, l.f32, l.x32, l.xt32, lc.x32, p.nu_post, s, bf);
+    std::swap(l.x32, l.xt32);
+    return;
+  }
   bool zero = true;
   for (int it = 0; it < p.nu_pre; ++it) {
     // the profiled sweep is the first one that reads x (the zero-start sweep reads only f)
