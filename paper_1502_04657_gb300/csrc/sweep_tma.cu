@@ -12,9 +12,11 @@
 //
 // Tensor maps (cuTensorMapEncodeTiled, from the driver through the runtime's entry-point
 // query) describe a level vector as a 3D array: columns 0..n (x, innermost), rows 0..n,
-// instances.  A tile's boxes start at column 128 t_x, a multiple of 16 bytes for FP32 and
-// BF16 as the TMA requires, and are 136 columns wide (a multiple of 16 bytes for both);
-// columns and rows past n are zero-filled and never used.
+// instances.  2D tile t_x covers node columns 128 t_x .. 128 t_x + 127 (so that a thread's
+// four result columns are one aligned vector store).  Its f box starts at column 128 t_x; its
+// x box starts 4 (FP32) or 8 (BF16) columns further left, so that every box starts on a
+// 16-byte boundary as the TMA requires, and is 136 or 144 columns wide (a multiple of 16
+// bytes).  Columns before 0 and columns and rows past n are zero-filled and never used.
 //
 // Every wait on an mbarrier is bounded.  If a wait runs out, the CTA records it in the
 // launch's status word (wait_fail[instance] = 1, which the host reports as FMG_ETIMEOUT),
@@ -36,10 +38,8 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 constexpr int kTX = 128, kTY = 16;  // tile: columns x rows of nodes (wide rows: long TMA rows)
-constexpr int kBoxW = kTX + 8;      // box width in elements (halo + 16-byte multiple)
 constexpr int kStages = 3;
-constexpr int kThreads = 256;       // 128 columns x 2 row groups of 8 rows
-constexpr int kRowsPerThread = kTY / (kThreads / kTX);
+constexpr int kThreads = 256;       // 2D: 32 groups of 4 columns x 8 pairs of rows
 constexpr long kSpinLimit = 1L << 22;  // try_wait rounds before a wait counts as lost
 
 __device__ __forceinline__ float ld(const float* p, int k) { return p[k]; }
@@ -92,31 +92,81 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint
 enum SweepMode { kResidual = 0, kJacobi = 1, kJacobiZero = 2 };
 
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+// The x box of a 2D tile starts box_off columns left of the tile's first column, so that its
+// start is 16-byte aligned (4 FP32 or 8 BF16 elements), and is box_w columns wide: the tile,
+// the one-column halo on either side, rounded up to 16 bytes.  The f box is the tile itself.
+template <typename S>
+constexpr int box_off() {
+  return 16 / (int)sizeof(S);
+}
+template <typename S>
+constexpr int box_w() {
+  return kTX + 2 * box_off<S>();
+}
 template <typename S>
 constexpr int x_bytes() {  // the x box; the f box starts at the next 128-byte boundary
-  return (kTY + 2) * kBoxW * (int)sizeof(S);
+  return (kTY + 2) * box_w<S>() * (int)sizeof(S);
 }
 template <typename S>
 constexpr int f_bytes() {
-  return kTY * kBoxW * (int)sizeof(S);
+  return kTY * kTX * (int)sizeof(S);
 }
 template <typename S>
 constexpr int stage_bytes() {
   return round128(x_bytes<S>()) + round128(f_bytes<S>());
 }
 template <typename S>
-constexpr int smem_bytes() {  // the ring, then one mbarrier per stage
-  return kStages * stage_bytes<S>() + 8 * kStages;
+constexpr int smem_bytes() {  // the ring, the tile coordinates of each stage, one mbarrier each
+  return kStages * stage_bytes<S>() + 16 * kStages + 8 * kStages;
 }
 
+// four consecutive elements from shared memory (16-byte aligned for FP32, 8 for BF16)
+__device__ __forceinline__ void ld4(const float* p, int k, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p + k);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const bf16* p, int k, float v[4]) {
+  const uint2 t = *reinterpret_cast<const uint2*>(p + k);
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&t.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&t.y);
+  v[0] = __low2float(lo);
+  v[1] = __high2float(lo);
+  v[2] = __low2float(hi);
+  v[3] = __high2float(hi);
+}
+// four consecutive nodes to global memory (k a multiple of 4, the vector 16-byte aligned)
+__device__ __forceinline__ void st4(float* p, size_t k, const float v[4]) {
+  *reinterpret_cast<float4*>(p + k) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(bf16* p, size_t k, const float v[4]) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 t;
+  t.x = *reinterpret_cast<const uint32_t*>(&lo);
+  t.y = *reinterpret_cast<const uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(p + k) = t;
+}
+
+// One CTA per (up to) three on an SM, persistent over the tiles blockIdx.x + k gridDim.x.
+// Thread (cg, rg) = (tid % 32, tid / 32) takes tile columns 4 cg .. 4 cg + 3 (node columns
+// i0 .. i0 + 3, i0 = 128 tx + 4 cg) and tile rows 2 rg, 2 rg + 1 (node rows j0, j0 + 1,
+// j0 = 1 + 16 ty + 2 rg): each x row it needs is three vector loads of shared memory, its
+// results two vector stores.  Node columns 0 and >= n and rows >= n are computed from clamped
+// table entries and never stored.  Thread 0 issues the loads of a tile and writes its
+// coordinates beside the ring, where the other threads read them before the tile's wait.
 template <typename S, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_sweep32_tma_2d(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mf,
                      int n, int pitch, size_t st_, int tiles_x, int tiles_y, int ntiles,
                      const float* __restrict__ tab, const float* __restrict__ cst,
                      S* __restrict__ y, int* __restrict__ wait_fail, int expire) {
+  constexpr int W = box_w<S>(), OFF = box_off<S>();
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes<S>());
+  int4* tinfo = reinterpret_cast<int4*>(smem + kStages * stage_bytes<S>());
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tinfo + kStages);
   const long limit = expire ? 0 : kSpinLimit;
   const int tid = threadIdx.x;
   const uint32_t tx_bytes = (MODE == kJacobiZero ? 0 : x_bytes<S>()) + f_bytes<S>();
@@ -126,121 +176,145 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
 
-  // tile -> (column tile, row tile, instance)
-  auto decode = [&](int tile, int& tx, int& ty, int& ib) {
-    tx = tile % tiles_x;
-    const int r = tile / tiles_x;
-    ty = r % tiles_y;
-    ib = r / tiles_y;
-  };
   auto issue = [&](int it) {  // thread 0: loads of the block's it-th tile into stage it % kStages
     const int tile = blockIdx.x + it * gridDim.x;
     if (tile >= ntiles) return;
-    int tx, ty, ib;
-    decode(tile, tx, ty, ib);
-    unsigned char* base = smem + (size_t)(it % kStages) * stage_bytes<S>();
-    uint64_t* b = &bar[it % kStages];
+    const int tx = tile % tiles_x;
+    const int r = tile / tiles_x;
+    const int ty = r % tiles_y;
+    const int ib = r / tiles_y;
+    const int stage = it % kStages;
+    tinfo[stage] = make_int4(tx, ty, ib, 0);
+    unsigned char* base = smem + (size_t)stage * stage_bytes<S>();
+    uint64_t* b = &bar[stage];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect(b, tx_bytes);
-    if (MODE != kJacobiZero) tma_load(base, &mx, b, tx * kTX, ty * kTY, ib);
+    if (MODE != kJacobiZero) tma_load(base, &mx, b, tx * kTX - OFF, ty * kTY, ib);
     tma_load(base + round128(x_bytes<S>()), &mf, b, tx * kTX, 1 + ty * kTY, ib);
   };
   if (tid == 0)
     for (int it = 0; it < kStages; ++it) issue(it);
+  // Orders the first stages' coordinates before their readers; later ones are written after
+  // the barrier that ends an iteration and read at least one such barrier later.
+  __syncthreads();
 
-  const int c = tid % kTX;                   // tile column of this thread
-  const int r0 = (tid / kTX) * kRowsPerThread;  // first tile row of this thread
+  const int c0 = 4 * (tid & 31);  // first tile column of this thread
+  const int r0 = 2 * (tid >> 5);  // first tile row
   const int s = n + 1;
   int it = 0;
   for (;; ++it) {
     const int tile = blockIdx.x + it * gridDim.x;
     if (tile >= ntiles) break;
-    int tx, ty, ib;
-    decode(tile, tx, ty, ib);
     const int stage = it % kStages;
-    const int i = 1 + tx * kTX + c;
+    const int4 ti = tinfo[stage];
+    const int ib = ti.z;
+    const int i0 = ti.x * kTX + c0;
+    const int j0 = 1 + ti.y * kTY + r0;
     const float* X = tab + (size_t)ib * 8 * s;
     const float* Y = X + 4 * s;
     S* yb = y + (size_t)ib * st_;
-    const bool act = i < n;
-    // The table entries of the thread's nodes are loaded before the wait for the tile, so
-    // their latency overlaps it (rows past n - 1 clamped: loaded, never stored).  yN / yNE
-    // at index q + 1 belong to row j0 + q; index 0 is the row below the first (S, SW).
-    const int j0 = 1 + ty * kTY + r0;
-    float xc = 0, xe = 0, xw = 0, xn = 0, xne = 0, xsw = 0, w = 0;
-    float yC[kRowsPerThread], yE[kRowsPerThread], yN[kRowsPerThread + 1],
-        yNE[kRowsPerThread + 1];
-    if (act) {
-      xc = X[i];
-      xe = X[s + i];
-      xw = X[s + i - 1];
-      xn = X[2 * s + i];
-      xne = X[3 * s + i];
-      xsw = X[3 * s + i - 1];
-      w = MODE == kResidual ? 0.0f : cst[kCst * ib + kCstOmega];
-      yN[0] = Y[2 * s + j0 - 1];
-      yNE[0] = Y[3 * s + j0 - 1];
+    // Table entries, loaded before the wait for the tile so that their latency overlaps it:
+    // xE[e], xNE[e] (E and NE x tables) belong to column i0 - 1 + e, xC[e], xN[e] to column
+    // i0 + e; yN[q], yNE[q] to row j0 - 1 + q, yC[q], yE[q] to row j0 + q.
+    float xC[4], xN[4], xE[5], xNE[5], yC[2], yE[2], yN[3], yNE[3];
 #pragma unroll
-      for (int q = 0; q < kRowsPerThread; ++q) {
-        const int jj = min(j0 + q, n - 1);
-        yC[q] = Y[jj];
-        yE[q] = Y[s + jj];
-        yN[q + 1] = Y[2 * s + jj];
-        yNE[q + 1] = Y[3 * s + jj];
+    for (int e = 0; e < 5; ++e) {
+      const int ii = min(max(i0 - 1 + e, 0), n);
+      xE[e] = X[s + ii];
+      xNE[e] = X[3 * s + ii];
+      if (e > 0) {
+        xC[e - 1] = X[ii];
+        xN[e - 1] = X[2 * s + ii];
       }
     }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int jj = min(j0 - 1 + q, n);
+      yN[q] = Y[2 * s + jj];
+      yNE[q] = Y[3 * s + jj];
+      if (q > 0) {
+        yC[q - 1] = Y[jj];
+        yE[q - 1] = Y[s + jj];
+      }
+    }
+    const float w = MODE == kResidual ? 0.0f : cst[kCst * ib + kCstOmega];
     const bool ok = mbar_wait(&bar[stage], (uint32_t)((it / kStages) & 1), limit);
     const bool lost = __syncthreads_or(!ok);
     const S* xs = reinterpret_cast<const S*>(smem + (size_t)stage * stage_bytes<S>());
     const S* fs = reinterpret_cast<const S*>(smem + (size_t)stage * stage_bytes<S>() +
                                              round128(x_bytes<S>()));
+    float out[2][4];
     if (lost) {
       if (tid == 0) atomicExch(&wait_fail[ib], 1);
-      for (int q = 0; q < kRowsPerThread; ++q) {
-        const int j = j0 + q;
-        if (act && j < n) st(yb, (size_t)j * pitch + i, __int_as_float(0x7fc00000));
-      }
-      break;
-    }
-    if (act) {
-      // x rows r0 .. r0 + kRowsPerThread + 1 of the tile are node rows j - 1 .. j + 1
-      float rw[3], rc[3];  // rows j - 1 and j at columns c, c + 1, c + 2 (tile columns)
-      if (MODE != kJacobiZero) {
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          rw[e] = ld(xs, r0 * kBoxW + c + e);
-          rc[e] = ld(xs, (r0 + 1) * kBoxW + c + e);
-        }
-      }
+      for (int q = 0; q < 2; ++q)
 #pragma unroll
-      for (int q = 0; q < kRowsPerThread; ++q) {
-        const int j = j0 + q;
-        const float fv = ld(fs, (r0 + q) * kBoxW + c + 1);
-        const float cc = xc + yC[q];
-        float out;
-        if (MODE == kJacobiZero) {
-          out = __fdividef(w, cc) * fv;
-        } else {
-          float rn[3];  // row j + 1
+        for (int e = 0; e < 4; ++e) out[q][e] = __int_as_float(0x7fc00000);
+    } else {
+      float fv[2][4];
+      ld4(fs, r0 * kTX + c0, fv[0]);
+      ld4(fs, (r0 + 1) * kTX + c0, fv[1]);
+      if (MODE == kJacobiZero) {
 #pragma unroll
-          for (int e = 0; e < 3; ++e) rn[e] = ld(xs, (r0 + q + 2) * kBoxW + c + e);
-          float v = cc * rc[1];
-          v = fmaf(xe + yE[q], rc[2], v);
-          v = fmaf(xw + yE[q], rc[0], v);
-          v = fmaf(xn + yN[q + 1], rn[1], v);
-          v = fmaf(xn + yN[q], rw[1], v);
-          v = fmaf(xne + yNE[q + 1], rn[2], v);
-          v = fmaf(xsw + yNE[q], rw[0], v);
-          out = MODE == kResidual ? fv - v : fmaf(__fdividef(w, cc), fv - v, rc[1]);
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
-          for (int e = 0; e < 3; ++e) {
-            rw[e] = rc[e];
+          for (int e = 0; e < 4; ++e) out[q][e] = __fdividef(w, xC[e] + yC[q]) * fv[q][e];
+      } else {
+        // x row arrays: element k is node column i0 - 1 + k (shared-memory column
+        // c0 + OFF - 1 + k); tile row r0 + q + 1 is node row j0 + q
+        auto row = [&](int r, float v[6]) {
+          float a[4], b[4], c[4];
+          ld4(xs, r * W + c0 + OFF - 4, a);
+          ld4(xs, r * W + c0 + OFF, b);
+          ld4(xs, r * W + c0 + OFF + 4, c);
+          v[0] = a[3];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[e + 1] = b[e];
+          v[5] = c[0];
+        };
+        float rs[6], rc[6], rn[6];  // rows j - 1, j, j + 1
+        row(r0, rs);
+        row(r0 + 1, rc);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          row(r0 + q + 2, rn);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float cc = xC[e] + yC[q];
+            float v = cc * rc[e + 1];
+            v = fmaf(xE[e + 1] + yE[q], rc[e + 2], v);
+            v = fmaf(xE[e] + yE[q], rc[e], v);
+            v = fmaf(xN[e] + yN[q + 1], rn[e + 1], v);
+            v = fmaf(xN[e] + yN[q], rs[e + 1], v);
+            v = fmaf(xNE[e + 1] + yNE[q + 1], rn[e + 2], v);
+            v = fmaf(xNE[e] + yNE[q], rs[e], v);
+            out[q][e] = MODE == kResidual ? fv[q][e] - v
+                                          : fmaf(__fdividef(w, cc), fv[q][e] - v, rc[e + 1]);
+          }
+#pragma unroll
+          for (int e = 0; e < 6; ++e) {
+            rs[e] = rc[e];
             rc[e] = rn[e];
           }
         }
-        if (j < n) st(yb, (size_t)j * pitch + i, out);
       }
     }
+    // a lost wait writes NaN over the thread's nodes, so no stale value passes for a result
+    const bool full = i0 >= 1 && i0 + 3 < n;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int j = j0 + q;
+      if (j >= n) continue;
+      const size_t k = (size_t)j * pitch + i0;
+      if (full) {
+        st4(yb, k, out[q]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (i0 + e >= 1 && i0 + e < n) st(yb, k + e, out[q][e]);
+      }
+    }
+    if (lost) break;
     __syncthreads();  // every thread is done with this stage before it is refilled
     if (tid == 0) issue(it + kStages);
   }
@@ -468,9 +542,10 @@ void launch(const Grid& g, const CoefT& ct, const TMAMap& mx, const TMAMap& mf, 
     static const cudaError_t attr = cudaFuncSetAttribute(
         k_sweep32_tma_2d<S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<S>());
     (void)attr;
-    const int tiles_x = (m + kTX - 1) / kTX, tiles_y = (m + kTY - 1) / kTY;
+    // tile columns start at node column 0 (aligned vector stores); node columns 1 .. n - 1
+    const int tiles_x = (g.n - 1) / kTX + 1, tiles_y = (m + kTY - 1) / kTY;
     const int ntiles = tiles_x * tiles_y * g.nb;
-    const int cap = 3 * sms();  // 3 CTAs of 56 KB shared memory per SM
+    const int cap = 3 * sms();  // 3 CTAs of 54 KB shared memory per SM
     k_sweep32_tma_2d<S, MODE><<<ntiles < cap ? ntiles : cap, kThreads, smem_bytes<S>(), s>>>(
         tx, tf, g.n, g.pitch, g.stride, tiles_x, tiles_y, ntiles, ct.tab, ct.cst,
         reinterpret_cast<S*>(y), wait_fail, expire);
@@ -506,7 +581,8 @@ bool encode_level_map(const Grid& g, int cap, const float* base, bool bf, bool h
   if (g.dim == 2) {
     const cuuint64_t dims[3] = {n1, n1, (cuuint64_t)cap};
     const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.stride * es};
-    const cuuint32_t box[3] = {(cuuint32_t)kBoxW, (cuuint32_t)(halo ? kTY + 2 : kTY), 1};
+    const int bw = halo ? (bf ? box_w<bf16>() : box_w<float>()) : kTX;
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)(halo ? kTY + 2 : kTY), 1};
     r = enc(reinterpret_cast<CUtensorMap*>(out->bytes),
             bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
             const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
