@@ -201,32 +201,56 @@ __device__ void build_G(const DenseProblem& p, Smem& s) {
     double* Y[1] = {s.Hc};
     symv<1>(X, s.c, Y, nh, s.sv);
   }
-  // coarse rows: lanes fill the B1 part of a row, then each row's thread adds its simplices
   const double cu2 = cu * cu;
+  // coarse block: every entry starts as [c_u^2 B1_ab] (rounded on its own, no contraction)
   {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int a = warp; a < nh; a += kWarps) {
       double* row = s.G + (size_t)a * n;
       const double* brow = p.aug ? s.B1 + (size_t)a * nh : nullptr;
-      for (int b = lane; b < nh; b += 32) row[b] = p.aug ? cu2 * brow[b] : 0.0;
+      for (int b = lane; b < nh; b += 32) row[b] = p.aug ? __dmul_rn(cu2, brow[b]) : 0.0;
     }
   }
   __syncthreads();
-  for (int a = threadIdx.x; a < nh; a += kThreads) {
-    double* row = s.G + (size_t)a * n;
-    double au = 0.0;
-    for (int e = 0; e < p.maxadj; ++e) {
-      const int code = s.adj[a * p.maxadj + e];
-      if (code < 0) break;
-      const int t = code >> 3, la = code & 7;
-      const double* lt = s.loc + (size_t)t * L * L;
-      for (int lb = 0; lb < nv; ++lb) {
-        const int vb = s.tri[t * nv + lb];
-        if (vb >= 0) row[vb] += lt[la * L + lb];
-      }
-      if (p.aug) au += lt[la * L + nv];
+  if (p.gent) {
+    // then each structurally nonzero entry adds its simplex contributions, one thread per
+    // entry, in the order of the gather list (a's adjacency order, then vertex order)
+    for (int q = threadIdx.x; q < p.npat; q += kThreads) {
+      const int e = __ldg(p.gent + q), k1 = __ldg(p.gstart + q + 1);
+      const int a = e / nh, b = e - a * nh;
+      double* g = s.G + (size_t)a * n + b;
+      double v = *g;
+      for (int k = __ldg(p.gstart + q); k < k1; ++k) v += s.loc[__ldg(p.gidx + k)];
+      *g = v;
     }
-    if (p.aug) row[nh] = fma(cu2, s.t1[a], fma(2.0 * cu, s.Hc[a], au));
+  } else {
+    // no gather lists: each row's thread walks its simplices and adds into its row
+    for (int a = threadIdx.x; a < nh; a += kThreads) {
+      double* row = s.G + (size_t)a * n;
+      for (int k = 0; k < p.maxadj; ++k) {
+        const int code = s.adj[a * p.maxadj + k];
+        if (code < 0) break;
+        const int t = code >> 3, la = code & 7;
+        const double* lt = s.loc + (size_t)t * L * L;
+        for (int lb = 0; lb < nv; ++lb) {
+          const int vb = s.tri[t * nv + lb];
+          if (vb >= 0) row[vb] += lt[la * L + lb];
+        }
+      }
+    }
+  }
+  if (p.aug) {
+    // coupling of row a with u~, on the threads with the least work above (the last ones)
+    for (int a = kThreads - 1 - threadIdx.x; a < nh; a += kThreads) {
+      double au = 0.0;
+      for (int k = 0; k < p.maxadj; ++k) {
+        const int code = s.adj[a * p.maxadj + k];
+        if (code < 0) break;
+        const int t = code >> 3, la = code & 7;
+        au += s.loc[(size_t)t * L * L + la * L + nv];
+      }
+      s.G[(size_t)a * n + nh] = fma(cu2, s.t1[a], fma(2.0 * cu, s.Hc[a], au));
+    }
   }
   if (p.aug) {
     double part = 0.0;

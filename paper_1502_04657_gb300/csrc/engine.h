@@ -96,6 +96,8 @@ struct fmg_eig_handle {
   // coarsest V-cycle solve (the same array unless the form is paper-literal)
   double *L1 = nullptr, *L1A = nullptr, *M1 = nullptr, *L1inv = nullptr;
   int *tri = nullptr, *adj = nullptr;
+  int npat = 0;  // gather lists of the dense G(c) assembly (DenseProblem)
+  int *gent = nullptr, *gstart = nullptr, *gidx = nullptr;
   double *lam = nullptr, *c = nullptr, *cstart = nullptr, *auu = nullptr, *buu = nullptr,
          *partials = nullptr, *partials2 = nullptr, *t3 = nullptr, *t3_partials = nullptr, *gAd = nullptr,
          *gMd = nullptr, *t1d = nullptr, *B1d = nullptr, *t0 = nullptr,

@@ -439,12 +439,45 @@ void build_coarse(fmg_eig_handle* h) {
       const int a = tri[t * nv + v];
       if (a >= 0) adj[a * h->maxadj + fill[a]++] = (t << 3) | v;
     }
+  // gather lists of the dense solve's G(c) assembly: for each entry (a, b) with a simplex
+  // around a that has b as a vertex, the simplex-local indices in a's adjacency order
+  std::vector<int> gent, gstart{0}, gidx;
+  {
+    const int L = nv + 1;
+    for (int a = 0; a < h->nh; ++a)
+      for (int b = 0; b < h->nh; ++b) {
+        const size_t before = gidx.size();
+        for (int k = 0; k < h->maxadj; ++k) {
+          const int code = adj[a * h->maxadj + k];
+          if (code < 0) break;
+          const int t = code >> 3, la = code & 7;
+          for (int lb = 0; lb < nv; ++lb)
+            if (tri[t * nv + lb] == b) gidx.push_back(t * L * L + la * L + lb);
+        }
+        if (gidx.size() > before) {
+          gent.push_back(a * h->nh + b);
+          gstart.push_back((int)gidx.size());
+        }
+      }
+  }
+  h->npat = (int)gent.size();
   h->tri = h->alloc<int>(tri.size());
   h->adj = h->alloc<int>(adj.size());
-  if (!h->dry) cudaMemcpyAsync(h->tri, tri.data(), tri.size() * sizeof(int), cudaMemcpyHostToDevice,
-                  h->stream);
-  if (!h->dry) cudaMemcpyAsync(h->adj, adj.data(), adj.size() * sizeof(int), cudaMemcpyHostToDevice,
-                  h->stream);
+  h->gent = h->alloc<int>(gent.size());
+  h->gstart = h->alloc<int>(gstart.size());
+  h->gidx = h->alloc<int>(gidx.size());
+  if (!h->dry) {
+    cudaMemcpyAsync(h->tri, tri.data(), tri.size() * sizeof(int), cudaMemcpyHostToDevice,
+                    h->stream);
+    cudaMemcpyAsync(h->adj, adj.data(), adj.size() * sizeof(int), cudaMemcpyHostToDevice,
+                    h->stream);
+    cudaMemcpyAsync(h->gent, gent.data(), gent.size() * sizeof(int), cudaMemcpyHostToDevice,
+                    h->stream);
+    cudaMemcpyAsync(h->gstart, gstart.data(), gstart.size() * sizeof(int),
+                    cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->gidx, gidx.data(), gidx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                    h->stream);
+  }
   const size_t nn = (size_t)h->nh * h->nh;
   h->L1 = h->alloc<double>(nn * nb);
   h->L1A = h->literal() ? h->alloc<double>(nn * nb) : h->L1;
@@ -569,6 +602,10 @@ DenseProblem dense_base(fmg_eig_handle* h) {
   d.tri = h->tri;
   d.adj = h->adj;
   d.maxadj = h->maxadj;
+  d.npat = h->npat;
+  d.gent = h->gent;
+  d.gstart = h->gstart;
+  d.gidx = h->gidx;
   d.quart_off = h->tri_vol * 2.0 * factorial(h->prob.dim) / factorial(h->prob.dim + 4);
   d.tri_vol = h->tri_vol;
   d.L1 = h->L1;

@@ -302,6 +302,14 @@ struct DenseProblem {
   const int* tri;      // ntri * nvert coarse interior indices, -1 on the boundary
   const int* adj;      // nh * maxadj codes (simplex << 3 | local vertex), -1 terminated
   int maxadj;
+  // Gather lists of the coarse block of G(c) (optional; nullptr: walk the adjacency): the
+  // npat structurally nonzero entries gent[q] = a nh + b, and for each the simplex-local
+  // indices gidx[gstart[q] .. gstart[q + 1]) = t (nvert + 1)^2 + la (nvert + 1) + lb of the
+  // simplices t around a (adjacency order, then vertex order) with vertex lb = b.
+  int npat;
+  const int* gent;
+  const int* gstart;
+  const int* gidx;
   double tri_vol;      // |T|
   double quart_off;    // |T| 2 d! / (d + 4)!, d = nvert - 1 (int_T w^2 mu_a mu_b / h_2)
   const double* L1;    // nh*nh, operator of level 1
