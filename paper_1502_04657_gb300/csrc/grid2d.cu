@@ -167,23 +167,40 @@ __global__ void k_restrict2d(int nc, int pc, int pf, size_t stc, size_t stf,
 }
 
 // x_f (+)= P e_c (+ scale * extra): fine node (2I+a, 2J+b) is the midpoint of coarse nodes
-// (I,J) and (I+a, J+b), a, b in {0,1}.
+// (I,J) and (I+a, J+b), a, b in {0,1}.  One thread per coarse cell (I, J), I, J in
+// [0, nc): it reads the cell's four corners once and writes fine columns 2I, 2I + 1 of rows
+// 2J and 2J + 1 as 16-byte vectors (column 0 and row 0, on the boundary, are not written).
 // scale[ib * scale_stride] is instance ib's factor.
-__global__ void k_prolong2d(int nf, int pf, int pc, size_t st, size_t stc,
+__global__ void k_prolong2d(int nc, int pf, int pc, size_t st, size_t stc,
                             const double* __restrict__ ec, double* __restrict__ xf, int add,
                             const double* __restrict__ extra, const double* __restrict__ scale,
                             int scale_stride) {
-  const int n = nf, pitch = pf;
-  INTERIOR_2D
-  const int ai = i & 1, aj = j & 1;
-  const size_t kc = ib * stc + at(i >> 1, j >> 1, pc);
-  // the midpoint value 0.5 (a + b) is added with one FMA (0.5 s is exact, so this rounds
-  // exactly as the separate multiply and add would)
-  const double a = ec[kc];
-  const double x = add ? xf[k] : 0.0;
-  double e = (ai | aj) ? fma(0.5, a + ec[kc + ai + (size_t)aj * pc], x) : a + x;
-  if (extra) e = fma(scale[(size_t)ib * scale_stride], extra[k], e);
-  xf[k] = e;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= nc || J >= nc) return;
+  const int ib = blockIdx.z;
+  const size_t kc = ib * stc + at(I, J, pc);
+  const double e00 = ec[kc], e10 = ec[kc + 1], e01 = ec[kc + pc], e11 = ec[kc + pc + 1];
+  const double sc = extra ? scale[(size_t)ib * scale_stride] : 0.0;
+  const size_t k0 = ib * st + at(2 * I, 2 * J, pf);  // even: the pair is 16-byte aligned
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    if (b == 0 && J == 0) continue;
+    const size_t k = k0 + (size_t)b * pf;
+    double2 x = make_double2(0.0, 0.0);
+    if (add) x = *reinterpret_cast<const double2*>(xf + k);
+    // the midpoint value 0.5 (a + b) is added with one FMA (0.5 s is exact, so this rounds
+    // exactly as the separate multiply and add would)
+    double v0 = b == 0 ? e00 + x.x : fma(0.5, e00 + e01, x.x);
+    double v1 = fma(0.5, e00 + (b == 0 ? e10 : e11), x.y);
+    if (extra) {
+      const double2 t = *reinterpret_cast<const double2*>(extra + k);
+      v0 = fma(sc, t.x, v0);
+      v1 = fma(sc, t.y, v1);
+    }
+    if (I > 0) *reinterpret_cast<double2*>(xf + k) = make_double2(v0, v1);
+    else xf[k + 1] = v1;
+  }
 }
 
 // int u^3 phi_p over the six triangles of the star of p, exactly.  With the hexagon of
@@ -398,9 +415,11 @@ void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* 
 
 void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
                const double* extra, const double* scale, int scale_stride, cudaStream_t s) {
-  k_prolong2d<<<grid_of(fine, fine.n - 1, fine.n - 1), block_of(fine), 0, s>>>(
-      fine.n, fine.pitch, coarse.pitch, fine.stride, coarse.stride, ec, xf, add ? 1 : 0, extra,
-      scale, scale_stride);
+  const dim3 block(32, 8);
+  const dim3 grid((coarse.n + 31) / 32, (coarse.n + 7) / 8, fine.nb);
+  k_prolong2d<<<grid, block, 0, s>>>(coarse.n, fine.pitch, coarse.pitch, fine.stride,
+                                     coarse.stride, ec, xf, add ? 1 : 0, extra, scale,
+                                     scale_stride);
 }
 
 void nload2d(const Grid& g, const double* u, double* out, cudaStream_t s) {
