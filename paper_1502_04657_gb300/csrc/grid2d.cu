@@ -154,16 +154,42 @@ __global__ void k_residual2d(int n, int pitch, size_t st, Coef2D c, const double
 
 // r_c = P^T r_f: a coarse node takes its own fine value plus half of the six fine nodes on
 // the coarse edges through it (the (1,1)-diagonal edges included).
+// r_c = P^T r_f for coarse nodes (2P, J) and (2P + 1, J) on one thread: fine columns
+// 4P - 2 .. 4P + 3 of rows 2J - 1 .. 2J + 1 as three 16-byte loads per row (all inside the
+// array: row 2J - 1 >= 1 starts past column 1, and the pitch leaves room past column
+// nf + 1), the pair stored as one 16-byte vector when both are interior.
 __global__ void k_restrict2d(int nc, int pc, int pf, size_t stc, size_t stf,
                              const double* __restrict__ rf, double* __restrict__ rc) {
-  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-  if (I >= nc || J >= nc) return;
+  if (2 * P >= nc || J >= nc) return;
   const int ib = blockIdx.z;
-  const size_t kf = ib * stf + at(2 * I, 2 * J, pf);
-  const double s = ((rf[kf + 1] + rf[kf - 1]) + (rf[kf + pf] + rf[kf - pf])) +
-                   (rf[kf + pf + 1] + rf[kf - pf - 1]);
-  rc[ib * stc + at(I, J, pc)] = fma(0.5, s, rf[kf]);
+  const double* r0 = rf + ib * stf + at(4 * P - 2, 2 * J - 1, pf);  // column 4P - 2, row 2J - 1
+  double v[3][6];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 t = *reinterpret_cast<const double2*>(r0 + (size_t)q * pf + 2 * c);
+      v[q][2 * c] = t.x;
+      v[q][2 * c + 1] = t.y;
+    }
+  // coarse node 2P + d: fine centre column 4P + 2d is v[.][2 + 2d]
+  double out[2];
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const int c = 2 + 2 * d;
+    const double sum = ((v[1][c + 1] + v[1][c - 1]) + (v[2][c] + v[0][c])) +
+                       (v[2][c + 1] + v[0][c - 1]);
+    out[d] = fma(0.5, sum, v[1][c]);
+  }
+  double* o = rc + ib * stc + at(2 * P, J, pc);  // even: 16-byte aligned
+  if (P > 0 && 2 * P + 1 < nc) {
+    *reinterpret_cast<double2*>(o) = make_double2(out[0], out[1]);
+  } else {
+    if (P > 0) o[0] = out[0];
+    if (2 * P + 1 < nc) o[1] = out[1];
+  }
 }
 
 // x_f (+)= P e_c (+ scale * extra): fine node (2I+a, 2J+b) is the midpoint of coarse nodes
@@ -409,8 +435,10 @@ void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x
 
 void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s) {
-  k_restrict2d<<<grid_of(fine, coarse.n - 1, coarse.n - 1), block_of(fine), 0, s>>>(
-      coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, rf, rc);
+  const dim3 block(32, 8);
+  const dim3 grid((coarse.n / 2 + 32) / 32, (coarse.n - 1 + 7) / 8, fine.nb);
+  k_restrict2d<<<grid, block, 0, s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride,
+                                      fine.stride, rf, rc);
 }
 
 void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,

@@ -231,45 +231,102 @@ __global__ void k_mass3d(int n, int pitch, size_t st, double h3, const double* _
 }
 
 // r_c = P^T r_f: own fine value plus half of the 14 fine neighbours along the mesh edges.
+// r_c = P^T r_f for coarse nodes (2P, J, L) and (2P + 1, J, L) on one thread: each of the
+// seven fine rows the pair touches (rows 2J + dy of planes 2L + dz) is read as 16-byte pairs
+// of columns 4P - 2 .. 4P + 3 (inside the array: those rows start past column 1 and have
+// room past column nf + 1 or continue in the next row); the pair is stored as one vector
+// when both are interior.  Per node the sums run in direction order as a node-by-node
+// evaluation would: s = sum_d (r(c + o_d) + r(c - o_d)), r_c = 0.5 s + r(c).
 __global__ void k_restrict3d(int nc, int pc, int pf, size_t stc, size_t stf,
                              const double* __restrict__ rf, double* __restrict__ rc) {
-  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   const int ib = blockIdx.z / (nc - 1);
   const int L = 1 + (int)blockIdx.z - ib * (nc - 1);
-  if (I >= nc || J >= nc) return;
+  if (2 * P >= nc || J >= nc) return;
   const long planef = (long)(2 * nc + 1) * pf;
-  const size_t kf = ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
-  double s = 0.0;
+  const double* base = rf + ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 4 * P;
+  // v[r][c]: fine row (dy, dz) = kRow[r] at column 4P - 2 + c
+  constexpr int kRow[7][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}, {-1, 0}, {0, -1}, {-1, -1}};
+  double v[7][6];
 #pragma unroll
-  for (int d = 0; d < 7; ++d) {
-    const long o = dir_off(d, pf, planef);
-    s += rf[kf + o] + rf[kf - o];
+  for (int r = 0; r < 7; ++r) {
+    const double* row = base + (long)kRow[r][0] * pf + (long)kRow[r][1] * planef - 2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double2 t = *reinterpret_cast<const double2*>(row + 2 * c);
+      v[r][2 * c] = t.x;
+      v[r][2 * c + 1] = t.y;
+    }
   }
-  rc[ib * stc + ((size_t)L * (nc + 1) + J) * pc + I] = fma(0.5, s, rf[kf]);
+  // row index of (dy, dz) and -(dy, dz) for the seven directions
+  constexpr int kPlus[7] = {0, 1, 2, 1, 2, 3, 3};
+  constexpr int kMinus[7] = {0, 4, 5, 4, 5, 6, 6};
+  constexpr int kDx[7] = {1, 0, 0, 1, 1, 0, 1};
+  double out[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int c = 2 + 2 * q;  // fine centre column 4P + 2q
+    double sum = 0.0;
+#pragma unroll
+    for (int d = 0; d < 7; ++d) sum += v[kPlus[d]][c + kDx[d]] + v[kMinus[d]][c - kDx[d]];
+    out[q] = fma(0.5, sum, v[0][c]);
+  }
+  double* o = rc + ib * stc + ((size_t)L * (nc + 1) + J) * pc + 2 * P;  // even: aligned
+  if (P > 0 && 2 * P + 1 < nc) {
+    *reinterpret_cast<double2*>(o) = make_double2(out[0], out[1]);
+  } else {
+    if (P > 0) o[0] = out[0];
+    if (2 * P + 1 < nc) o[1] = out[1];
+  }
 }
 
 // x_f (+)= P e_c (+ scale * extra): fine node 2I + a (a in {0,1}^3) is the midpoint of coarse
-// nodes I and I + a, which are joined by a mesh edge.
+// nodes I and I + a, which are joined by a mesh edge.  One thread per coarse cell (I, J, L),
+// I, J, L in [0, nc): the cell's eight corners read once, fine columns 2I, 2I + 1 of its four
+// fine rows written as 16-byte vectors (column, row and plane 0 are not written).
 // scale[ib * scale_stride] is instance ib's factor.
-__global__ void k_prolong3d(int nf, int pf, int pc, size_t st, size_t stc,
+__global__ void k_prolong3d(int nc, int pf, int pc, size_t st, size_t stc,
                             const double* __restrict__ ec, double* __restrict__ xf, int add,
                             const double* __restrict__ extra, const double* __restrict__ scale,
                             int scale_stride) {
-  const int n = nf, pitch = pf;
-  INTERIOR_3D
-  const int ai = i & 1, aj = j & 1, al = l & 1;
-  const int nc = nf / 2;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ib = blockIdx.z / nc;
+  const int L = (int)blockIdx.z - ib * nc;
+  if (I >= nc || J >= nc) return;
   const long planec = (long)(nc + 1) * pc;
-  const size_t kc = ib * stc + (size_t)(l >> 1) * planec + (size_t)(j >> 1) * pc + (i >> 1);
-  // the midpoint value 0.5 (a + b) is added with one FMA (0.5 s is exact, so this rounds
-  // exactly as the separate multiply and add would)
-  const double a = ec[kc];
-  const double x = add ? xf[k] : 0.0;
-  double e = (ai | aj | al) ? fma(0.5, a + ec[kc + ai + (size_t)aj * pc + (size_t)al * planec], x)
-                            : a + x;
-  if (extra) e = fma(scale[(size_t)ib * scale_stride], extra[k], e);
-  xf[k] = e;
+  const long planef = (long)(2 * nc + 1) * pf;
+  const size_t kc = ib * stc + (size_t)L * planec + (size_t)J * pc + I;
+  double e[2][2][2];  // e[al][aj][ai] = e_c(I + ai, J + aj, L + al)
+#pragma unroll
+  for (int al = 0; al < 2; ++al)
+#pragma unroll
+    for (int aj = 0; aj < 2; ++aj)
+#pragma unroll
+      for (int ai = 0; ai < 2; ++ai) e[al][aj][ai] = ec[kc + ai + (size_t)aj * pc + al * planec];
+  const double sc = extra ? scale[(size_t)ib * scale_stride] : 0.0;
+#pragma unroll
+  for (int al = 0; al < 2; ++al)
+#pragma unroll
+    for (int aj = 0; aj < 2; ++aj) {
+      if ((al == 0 && L == 0) || (aj == 0 && J == 0)) continue;
+      const size_t k = ib * st + (size_t)(2 * L + al) * planef + (size_t)(2 * J + aj) * pf + 2 * I;
+      double2 x = make_double2(0.0, 0.0);
+      if (add) x = *reinterpret_cast<const double2*>(xf + k);
+      // the midpoint value 0.5 (a + b) is added with one FMA (0.5 s is exact, so this rounds
+      // exactly as the separate multiply and add would)
+      const double a = e[0][0][0];
+      double v0 = (aj | al) ? fma(0.5, a + e[al][aj][0], x.x) : a + x.x;
+      double v1 = fma(0.5, a + e[al][aj][1], x.y);
+      if (extra) {
+        const double2 t = *reinterpret_cast<const double2*>(extra + k);
+        v0 = fma(sc, t.x, v0);
+        v1 = fma(sc, t.y, v1);
+      }
+      if (I > 0) *reinterpret_cast<double2*>(xf + k) = make_double2(v0, v1);
+      else xf[k + 1] = v1;
+    }
 }
 
 // Star sums over the 24 tetrahedra of p (vertex values u_p, u_q, u_r, u_s; |K| = h^3/6):
@@ -729,15 +786,17 @@ void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x
 
 void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
                 cudaStream_t s) {
-  k_restrict3d<<<grid3(fine, coarse.n - 1, coarse.n - 1, coarse.n - 1), block3(fine), 0, s>>>(
-      coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, rf, rc);
+  const dim3 grid((coarse.n / 2 + 32) / 32, (coarse.n - 1 + 7) / 8, (coarse.n - 1) * fine.nb);
+  k_restrict3d<<<grid, dim3(32, 8), 0, s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride,
+                                            fine.stride, rf, rc);
 }
 
 void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
                const double* extra, const double* scale, int scale_stride, cudaStream_t s) {
-  k_prolong3d<<<INTERIOR_LAUNCH(fine)>>>(fine.n, fine.pitch, coarse.pitch, fine.stride,
-                                         coarse.stride, ec, xf, add ? 1 : 0, extra, scale,
-                                         scale_stride);
+  const dim3 grid((coarse.n + 31) / 32, (coarse.n + 7) / 8, coarse.n * fine.nb);
+  k_prolong3d<<<grid, dim3(32, 8), 0, s>>>(coarse.n, fine.pitch, coarse.pitch, fine.stride,
+                                           coarse.stride, ec, xf, add ? 1 : 0, extra, scale,
+                                           scale_stride);
 }
 
 // the plane-walk kernels take more than the default 48 KB of dynamic shared memory

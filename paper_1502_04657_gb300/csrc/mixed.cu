@@ -148,28 +148,108 @@ __global__ void k_sweep32_2d(int n, int pitch, size_t st_, const float* __restri
   }
 }
 
+// four consecutive elements (FP32: 16 bytes, BF16: 8 bytes; the index a multiple of 4)
+__device__ __forceinline__ void ld4v(const float* p, size_t k, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p + k);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld4v(const bf16* p, size_t k, float v[4]) {
+  const uint2 t = *reinterpret_cast<const uint2*>(p + k);
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&t.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&t.y);
+  v[0] = __low2float(lo);
+  v[1] = __high2float(lo);
+  v[2] = __low2float(hi);
+  v[3] = __high2float(hi);
+}
+__device__ __forceinline__ void st4v(float* p, size_t k, const float v[4]) {
+  *reinterpret_cast<float4*>(p + k) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4v(bf16* p, size_t k, const float v[4]) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 t;
+  t.x = *reinterpret_cast<const uint32_t*>(&lo);
+  t.y = *reinterpret_cast<const uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(p + k) = t;
+}
+
+// r_c = P^T r_f for coarse nodes 4Q .. 4Q + 3 of row J on one thread: fine columns
+// 8Q - 4 .. 8Q + 7 of rows 2J - 1 .. 2J + 1 as three vector loads per row (inside the array:
+// row 2J - 1 >= 1 starts past column 3, and rows have room past column nf + 3 or continue in
+// the next row), the four results stored as one vector when all are interior.
 template <typename S>
 __global__ void k_restrict32_2d(int nc, int pc, int pf, size_t stc, size_t stf,
                                 const S* __restrict__ rf, S* __restrict__ rc) {
-  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int Q = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-  if (I >= nc || J >= nc) return;
-  const size_t kf = blockIdx.z * stf + at(2 * I, 2 * J, pf);
-  const float s = ((ld(rf, kf + 1) + ld(rf, kf - 1)) + (ld(rf, kf + pf) + ld(rf, kf - pf))) +
-                  (ld(rf, kf + pf + 1) + ld(rf, kf - pf - 1));
-  st(rc, blockIdx.z * stc + at(I, J, pc), fmaf(0.5f, s, ld(rf, kf)));
+  if (4 * Q >= nc || J >= nc) return;
+  const size_t k0 = blockIdx.z * stf + at(8 * Q - 4, 2 * J - 1, pf);
+  float v[3][12];  // v[q][c]: fine row 2J - 1 + q, column 8Q - 4 + c
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ld4v(rf, k0 + (size_t)q * pf + 4 * c, &v[q][4 * c]);
+  float out[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {  // coarse node 4Q + d: fine centre column 8Q + 2d
+    const int c = 4 + 2 * d;
+    const float sum = ((v[1][c + 1] + v[1][c - 1]) + (v[2][c] + v[0][c])) +
+                      (v[2][c + 1] + v[0][c - 1]);
+    out[d] = fmaf(0.5f, sum, v[1][c]);
+  }
+  const size_t ko = blockIdx.z * stc + at(4 * Q, J, pc);
+  if (Q > 0 && 4 * Q + 3 < nc) {
+    st4v(rc, ko, out);
+  } else {
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (4 * Q + d >= 1 && 4 * Q + d < nc) st(rc, ko + d, out[d]);
+  }
 }
 
+// x_f += P e_c for fine columns 4P .. 4P + 3 of rows 2J and 2J + 1 (coarse cells 2P, 2P + 1
+// of row J) on one thread: six coarse values (columns past nc clamped: their fine nodes are
+// not written), two vector loads and stores of x; column 0 and row 0 are not written.
 template <typename S>
-__global__ void k_prolong32_2d(int nf, int pf, int pc, size_t st_, size_t stc,
+__global__ void k_prolong32_2d(int nc, int pf, int pc, size_t st_, size_t stc,
                                const S* __restrict__ ec, S* __restrict__ xf) {
-  const int n = nf, pitch = pf;
-  INTERIOR_2D
-  const int ai = i & 1, aj = j & 1;
-  const size_t kc = ib * stc + at(i >> 1, j >> 1, pc);
-  float e = ld(ec, kc);
-  if (ai | aj) e = 0.5f * (e + ld(ec, kc + ai + (size_t)aj * pc));
-  st(xf, k, ld(xf, k) + e);
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nf = 2 * nc;
+  if (4 * P >= nf || J >= nc) return;
+  const size_t kc = blockIdx.z * stc + at(0, J, pc);
+  float e0[3], e1[3];  // coarse rows J, J + 1 at columns 2P, 2P + 1, 2P + 2
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int I = min(2 * P + c, nc);
+    e0[c] = ld(ec, kc + I);
+    e1[c] = ld(ec, kc + pc + I);
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    if (b == 0 && J == 0) continue;
+    const size_t k = blockIdx.z * st_ + at(4 * P, 2 * J + b, pf);
+    float x[4];
+    ld4v(xf, k, x);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {  // fine column 4P + a: cell 2P + (a >> 1), offset a & 1
+      const int c = a >> 1, ai = a & 1;
+      float e = e0[c];
+      if (ai | b) e = 0.5f * (e + (b == 0 ? e0[c + 1] : (ai ? e1[c + 1] : e1[c])));
+      x[a] = x[a] + e;
+    }
+    if (P > 0 && 4 * P + 3 < nf) {
+      st4v(xf, k, x);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (4 * P + a >= 1 && 4 * P + a < nf) st(xf, k + a, x[a]);
+    }
+  }
 }
 
 // ---- single-precision 3D stencil kernels (Kuhn mesh, see grid3d.cu) --------------------------
@@ -403,8 +483,9 @@ void jacobi_t(const Grid& g, const CoefT& ct, const float* f, const float* x, fl
 template <typename S>
 void restrict_t(const Grid& fine, const Grid& coarse, const float* rf, float* rc, cudaStream_t s) {
   if (fine.dim == 2)
-    k_restrict32_2d<S><<<grid2(fine, coarse.n - 1, coarse.n - 1), blk(fine), 0, s>>>(
-        coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, sp<S>(rf), sp<S>(rc));
+    k_restrict32_2d<S><<<dim3((coarse.n / 4 + 32) / 32, (coarse.n - 1 + 7) / 8, fine.nb),
+                         dim3(32, 8), 0, s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride,
+                                              fine.stride, sp<S>(rf), sp<S>(rc));
   else
     k_restrict32_3d<S><<<grid3(fine, coarse.n - 1, coarse.n - 1, coarse.n - 1), blk(fine), 0, s>>>(
         coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, sp<S>(rf), sp<S>(rc));
@@ -413,8 +494,9 @@ void restrict_t(const Grid& fine, const Grid& coarse, const float* rf, float* rc
 template <typename S>
 void prolong_t(const Grid& fine, const Grid& coarse, const float* ec, float* xf, cudaStream_t s) {
   if (fine.dim == 2)
-    k_prolong32_2d<S><<<grid2(fine, fine.n - 1, fine.n - 1), blk(fine), 0, s>>>(
-        fine.n, fine.pitch, coarse.pitch, fine.stride, coarse.stride, sp<S>(ec), sp<S>(xf));
+    k_prolong32_2d<S><<<dim3(((fine.n + 3) / 4 + 31) / 32, (coarse.n + 7) / 8, fine.nb), dim3(32, 8),
+                        0, s>>>(coarse.n, fine.pitch, coarse.pitch, fine.stride, coarse.stride,
+                                sp<S>(ec), sp<S>(xf));
   else
     k_prolong32_3d<S><<<grid3(fine, fine.n - 1, fine.n - 1, fine.n - 1), blk(fine), 0, s>>>(
         fine.n, fine.pitch, coarse.pitch, fine.stride, coarse.stride, sp<S>(ec), sp<S>(xf));
