@@ -388,37 +388,96 @@ __global__ void k_consts(int dim, int nb, double h, const PotentialParams* __res
   }
 }
 
+// r_c = P^T r_f for coarse nodes 4Q .. 4Q + 3 of row (J, L) on one thread: each of the seven
+// fine rows they touch (rows 2J + dy of planes 2L + dz) read as vectors over columns
+// 8Q - 4 .. 8Q + 7 (inside the array, as in the 2D kernel); per node the sums run in
+// direction order as in a node-by-node evaluation.
 template <typename S>
 __global__ void k_restrict32_3d(int nc, int pc, int pf, size_t stc, size_t stf,
                                 const S* __restrict__ rf, S* __restrict__ rc) {
-  const int I = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int Q = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   const int ib = blockIdx.z / (nc - 1);
   const int L = 1 + (int)blockIdx.z - ib * (nc - 1);
-  if (I >= nc || J >= nc) return;
+  if (4 * Q >= nc || J >= nc) return;
   const long planef = (long)(2 * nc + 1) * pf;
-  const size_t kf = ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 2 * I;
-  float s = 0.0f;
+  const size_t base = ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 8 * Q - 4;
+  constexpr int kRow[7][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}, {-1, 0}, {0, -1}, {-1, -1}};
+  constexpr int kPlus[7] = {0, 1, 2, 1, 2, 3, 3};
+  constexpr int kMinus[7] = {0, 4, 5, 4, 5, 6, 6};
+  constexpr int kDx[7] = {1, 0, 0, 1, 1, 0, 1};
+  float v[7][12];  // v[r][c]: fine row kRow[r] at column 8Q - 4 + c
 #pragma unroll
-  for (int d = 0; d < 7; ++d) {
-    const long o = dir_off(d, pf, planef);
-    s += ld(rf, kf + o) + ld(rf, kf - o);
+  for (int r = 0; r < 7; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      ld4v(rf, base + (long)kRow[r][0] * pf + (long)kRow[r][1] * planef + 4 * c, &v[r][4 * c]);
+  float out[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {  // coarse node 4Q + d: fine centre column 8Q + 2d
+    const int c = 4 + 2 * d;
+    float sum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) sum += v[kPlus[q]][c + kDx[q]] + v[kMinus[q]][c - kDx[q]];
+    out[d] = fmaf(0.5f, sum, v[0][c]);
   }
-  st(rc, ib * stc + ((size_t)L * (nc + 1) + J) * pc + I, fmaf(0.5f, s, ld(rf, kf)));
+  const size_t ko = ib * stc + ((size_t)L * (nc + 1) + J) * pc + 4 * Q;
+  if (Q > 0 && 4 * Q + 3 < nc) {
+    st4v(rc, ko, out);
+  } else {
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (4 * Q + d >= 1 && 4 * Q + d < nc) st(rc, ko + d, out[d]);
+  }
 }
 
+// x_f += P e_c for fine columns 4P .. 4P + 3 of the four fine rows (2J + aj, 2L + al) of coarse
+// cells (2P, J, L), (2P + 1, J, L) on one thread: twelve coarse values (columns past nc
+// clamped: their fine nodes are not written), vector loads and stores of x; column, row and
+// plane 0 are not written.
 template <typename S>
-__global__ void k_prolong32_3d(int nf, int pf, int pc, size_t st_, size_t stc,
+__global__ void k_prolong32_3d(int nc, int pf, int pc, size_t st_, size_t stc,
                                const S* __restrict__ ec, S* __restrict__ xf) {
-  const int n = nf, pitch = pf;
-  INTERIOR_3D
-  const int ai = i & 1, aj = j & 1, al = l & 1;
-  const int nc = nf / 2;
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int ib = blockIdx.z / nc;
+  const int L = (int)blockIdx.z - ib * nc;
+  const int nf = 2 * nc;
+  if (4 * P >= nf || J >= nc) return;
   const long planec = (long)(nc + 1) * pc;
-  const size_t kc = ib * stc + (size_t)(l >> 1) * planec + (size_t)(j >> 1) * pc + (i >> 1);
-  float e = ld(ec, kc);
-  if (ai | aj | al) e = 0.5f * (e + ld(ec, kc + ai + (size_t)aj * pc + (size_t)al * planec));
-  st(xf, k, ld(xf, k) + e);
+  const long planef = (long)(nf + 1) * pf;
+  const size_t kc = ib * stc + (size_t)L * planec + (size_t)J * pc;
+  float e[2][2][3];  // e[al][aj][c] = e_c(2P + c, J + aj, L + al)
+#pragma unroll
+  for (int al = 0; al < 2; ++al)
+#pragma unroll
+    for (int aj = 0; aj < 2; ++aj)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        e[al][aj][c] = ld(ec, kc + (size_t)al * planec + (size_t)aj * pc + min(2 * P + c, nc));
+#pragma unroll
+  for (int al = 0; al < 2; ++al)
+#pragma unroll
+    for (int aj = 0; aj < 2; ++aj) {
+      if ((al == 0 && L == 0) || (aj == 0 && J == 0)) continue;
+      const size_t k = ib * st_ + (size_t)(2 * L + al) * planef + (size_t)(2 * J + aj) * pf + 4 * P;
+      float x[4];
+      ld4v(xf, k, x);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {  // fine column 4P + a: cell 2P + (a >> 1), offset a & 1
+        const int c = a >> 1, ai = a & 1;
+        float v = e[0][0][c];
+        if (ai | aj | al) v = 0.5f * (v + e[al][aj][c + ai]);
+        x[a] = x[a] + v;
+      }
+      if (P > 0 && 4 * P + 3 < nf) {
+        st4v(xf, k, x);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (4 * P + a >= 1 && 4 * P + a < nf) st(xf, k + a, x[a]);
+      }
+    }
 }
 
 // coarsest level: y = Linv x with x, y single-precision padded level-1 vectors (FP64
@@ -487,19 +546,23 @@ void restrict_t(const Grid& fine, const Grid& coarse, const float* rf, float* rc
                          dim3(32, 8), 0, s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride,
                                               fine.stride, sp<S>(rf), sp<S>(rc));
   else
-    k_restrict32_3d<S><<<grid3(fine, coarse.n - 1, coarse.n - 1, coarse.n - 1), blk(fine), 0, s>>>(
-        coarse.n, coarse.pitch, fine.pitch, coarse.stride, fine.stride, sp<S>(rf), sp<S>(rc));
+    k_restrict32_3d<S><<<dim3((coarse.n / 4 + 32) / 32, (coarse.n - 1 + 7) / 8,
+                              (coarse.n - 1) * fine.nb),
+                         dim3(32, 8), 0, s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride,
+                                              fine.stride, sp<S>(rf), sp<S>(rc));
 }
 
 template <typename S>
 void prolong_t(const Grid& fine, const Grid& coarse, const float* ec, float* xf, cudaStream_t s) {
   if (fine.dim == 2)
-    k_prolong32_2d<S><<<dim3(((fine.n + 3) / 4 + 31) / 32, (coarse.n + 7) / 8, fine.nb), dim3(32, 8),
-                        0, s>>>(coarse.n, fine.pitch, coarse.pitch, fine.stride, coarse.stride,
-                                sp<S>(ec), sp<S>(xf));
+    k_prolong32_2d<S><<<dim3(((fine.n + 3) / 4 + 31) / 32, (coarse.n + 7) / 8, fine.nb),
+                        dim3(32, 8), 0, s>>>(coarse.n, fine.pitch, coarse.pitch, fine.stride,
+                                             coarse.stride, sp<S>(ec), sp<S>(xf));
   else
-    k_prolong32_3d<S><<<grid3(fine, fine.n - 1, fine.n - 1, fine.n - 1), blk(fine), 0, s>>>(
-        fine.n, fine.pitch, coarse.pitch, fine.stride, coarse.stride, sp<S>(ec), sp<S>(xf));
+    k_prolong32_3d<S><<<dim3(((fine.n + 3) / 4 + 31) / 32, (coarse.n + 7) / 8,
+                             coarse.n * fine.nb),
+                        dim3(32, 8), 0, s>>>(coarse.n, fine.pitch, coarse.pitch, fine.stride,
+                                             coarse.stride, sp<S>(ec), sp<S>(xf));
 }
 
 }  // namespace
