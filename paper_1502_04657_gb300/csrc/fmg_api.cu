@@ -572,17 +572,10 @@ void enqueue_setup(fmg_eig_handle* h, cudaStream_t s, bool overlap = false) {
     const cudaStream_t s_saved = s;
     s = sk;
     prof_begin(h, kProfCoef, k, s);
-    if (h->mixed() && l.g.dim == 3) {
-      // mixed precision, 3D: the split tables first, then the coefficients in double-float
-      coef1d_3d(l.g, h->dparams, l.c3, s);
-      tables_f32(l.g, l.c, l.c3, h->dparams, l.ct, s);
-      coef3d_df(l.g, l.ct, l.c3, s);
-    } else {
-      lv_coef(l, h->dparams, s);
-    }
+    lv_coef(l, h->dparams, s);
     if (h->literal()) lv_coef(l, h->dparams_full, s, true);
     prof_end(h, kProfCoef, k, s);
-    if (h->mixed() && l.g.dim == 2) tables_f32(l.g, l.c, l.c3, h->dparams, l.ct, s);
+    if (h->mixed()) tables_f32(l.g, l.c, l.c3, h->dparams, l.ct, s);
     if (sk != s_saved) {
       cudaEventRecord(h->ev_level[k], sk);
       h->level_pending[k] = true;

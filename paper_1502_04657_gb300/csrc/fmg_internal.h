@@ -192,11 +192,6 @@ void residual_mixed(const Grid& g, const Coef2D& c2, const Coef3D& c3, const dou
 // the split tables and constants of level g from its FP64 tables (c2.tab / c3.tab written)
 void tables_f32(const Grid& g, const Coef2D& c2, const Coef3D& c3,
                 const PotentialParams* pp, const CoefT& ct, cudaStream_t s);
-// 3D coefficients (c.a, c.dinv) in double-float arithmetic from the split tables of
-// tables_f32, written in FP64 (mixed-precision modes)
-void coef3d_df(const Grid& g, const CoefT& ct, const Coef3D& c, cudaStream_t s);
-// 3D separable tables only (k_coef1d_3d of coef3d_setup)
-void coef1d_3d(const Grid& g, const PotentialParams* p_dev, const Coef3D& c, cudaStream_t s);
 // TMA-fed single-precision sweeps of the large levels (sweep_tma.cu).  A TMAMap holds a
 // tensor map (CUtensorMap) of one level vector: columns, rows and instances, with a box of
 // one tile (halo = true: the x box, 2 rows taller).

@@ -74,85 +74,46 @@ __device__ __forceinline__ double recip(double c) {
   return y;
 }
 
+// The stencil coefficients of a 3D level, one warp per grid row (j, l) of an instance with its
+// lanes over i.  Every coupling is a constant plus one table entry per axis; the constant and
+// the y and z entries are summed once per row, so a node adds its x entries (8 additions)
+// and forms omega / C: about 15 FP64 operations per node instead of 46 when every node
+// formed its constants and sums itself.  Couplings: C (tables 0, 0, 0), the axis
+// directions d (table 1 along d, 2 across), the face diagonals opposite axis e (table 3 on
+// the two axes of the face, 4 on e) and the body diagonal (table 1 on every axis).
 __global__ void k_coef3d(int n, int pitch, size_t st, double h, const double* __restrict__ tab,
                          const PotentialParams* __restrict__ pp, Coef3D c) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int ib = blockIdx.z / (n + 1);
-  const int l = (int)blockIdx.z - ib * (n + 1);
-  if (i > n || j > n) return;
+  const int lane = threadIdx.x & 31;
+  const int s = n + 1;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // j + (n + 1) l
+  if (row >= s * s) return;
+  const int j = row % s, l = row / s;
+  const int ib = blockIdx.y;
   const PotentialParams p = pp[ib];
-  tab += (size_t)ib * 15 * (n + 1);
+  const double* T = tab + (size_t)ib * 15 * s;
   const double wl = p.operator_form == FMG_W_LEFT ? 1.0 : 0.0;
-  const double h3 = h * h * h;
-  const int s = n + 1;
-  const int co[3] = {i, j, l};
-  auto T = [&](int ax, int q) { return tab[(ax * 5 + q) * s + co[ax]]; };
-  const size_t k = ib * st + ((size_t)l * (n + 1) + j) * pitch + i;
-  const double cc = 6.0 * h + wl * 0.4 * h3 * p.w0 + T(0, 0) + T(1, 0) + T(2, 0);
-  c.a[0][k] = cc;
-  // axis directions: along = table 1 on that axis, across = table 2 on the others
-  for (int d = 0; d < 3; ++d) {
-    double v = -h + wl * h3 * p.w0 * (1.0 / 20.0);
-    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == d ? 1 : 2);
-    c.a[1 + d][k] = v;
-  }
-  // face diagonals XY, XZ, YZ: along on the two axes, across on the third
-  const int other[3] = {2, 1, 0};
-  for (int f = 0; f < 3; ++f) {
-    double v = wl * h3 * p.w0 * (1.0 / 30.0);
-    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == other[f] ? 4 : 3);
-    c.a[4 + f][k] = v;
-  }
-  c.a[7][k] = wl * h3 * p.w0 * (1.0 / 20.0) + T(0, 1) + T(1, 1) + T(2, 1);
-  c.dinv[k] = p.omega * recip(cc);
-}
-
-// The same coefficients in double-float arithmetic (mixed-precision modes) from the split
-// tables (thi + tlo) and split constants of the single-precision V-cycle: every coefficient
-// is a constant plus three table entries, so the FP64 pipe only converts the 9 outputs.
-// omega / C: a Newton step in double-float from the FP32 reciprocal of C.
-__global__ void k_coef3d_df(int n, int pitch, size_t st, const float* __restrict__ thi,
-                            const float* __restrict__ tlo, const float* __restrict__ cst,
-                            Coef3D c) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int ib = blockIdx.z / (n + 1);
-  const int l = (int)blockIdx.z - ib * (n + 1);
-  if (i > n || j > n) return;
-  const int s = n + 1;
-  const size_t to = (size_t)ib * 15 * s;
-  const int co[3] = {i, j, l};
-  auto T = [&](int ax, int q) {
-    const size_t e = to + (size_t)(ax * 5 + q) * s + co[ax];
-    return dfloat(thi[e], tlo[e]);
-  };
-  const float* C = cst + (size_t)kCst * ib;
-  auto K = [&](int q) { return dfloat(C[q], C[kCstLo + q]); };
-  const size_t k = ib * st + ((size_t)l * (n + 1) + j) * pitch + i;
-  const dfloat cc = ((K(0) + T(0, 0)) + T(1, 0)) + T(2, 0);
-  c.a[0][k] = to_double(cc);
+  const double w3 = wl * (h * h * h) * p.w0;
+  // table index on the x, y and z axis of each coupling, and its constant
+  constexpr int kQ[8][3] = {{0, 0, 0}, {1, 2, 2}, {2, 1, 2}, {2, 2, 1},
+                            {3, 3, 4}, {3, 4, 3}, {4, 3, 3}, {1, 1, 1}};
+  const double axis = -h + w3 * (1.0 / 20.0), face = w3 * (1.0 / 30.0);
+  const double K[8] = {6.0 * h + w3 * 0.4, axis, axis, axis, face, face, face, w3 * (1.0 / 20.0)};
+  double R[8];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    dfloat v = K(1);
+  for (int q = 0; q < 8; ++q)
+    R[q] = (K[q] + T[(5 + kQ[q][1]) * s + j]) + T[(10 + kQ[q][2]) * s + l];
+  const size_t base = ib * st + ((size_t)l * s + j) * pitch;
+  for (int i = lane; i <= n; i += 32) {
+    const size_t k = base + i;
+    double cc = 0.0;
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == d ? 1 : 2);
-    c.a[1 + d][k] = to_double(v);
+    for (int q = 0; q < 8; ++q) {
+      const double v = R[q] + T[kQ[q][0] * s + i];
+      c.a[q][k] = v;
+      if (q == 0) cc = v;
+    }
+    c.dinv[k] = p.omega * recip(cc);
   }
-  const int other[3] = {2, 1, 0};
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    dfloat v = K(2);
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) v += T(ax, ax == other[f] ? 4 : 3);
-    c.a[4 + f][k] = to_double(v);
-  }
-  c.a[7][k] = to_double(((K(3) + T(0, 1)) + T(1, 1)) + T(2, 1));
-  // r = 1 / cc: FP32 seed, one Newton step r + r (1 - cc r) in double-float
-  const dfloat r0(__frcp_rn(cc.hi), 0.0f);
-  const dfloat e = dfloat(1) + -(cc * r0);
-  const dfloat r = fma(r0, e, r0);
-  c.dinv[k] = to_double(dfloat(C[kCstOmega], C[kCstOmegaLo]) * r);
 }
 
 __device__ __forceinline__ double lop3(const Coef3D& c, const double* __restrict__ x, size_t k,
@@ -737,19 +698,10 @@ dim3 block3(const Grid& g) { return dim3(g.bx, g.by); }
 
 }  // namespace
 
-void coef1d_3d(const Grid& g, const PotentialParams* p, const Coef3D& c, cudaStream_t s) {
-  k_coef1d_3d<<<dim3((g.n + 1 + 127) / 128, g.nb), 128, 0, s>>>(g.n, g.h, p, c.tab);
-}
-
-void coef3d_df(const Grid& g, const CoefT& ct, const Coef3D& c, cudaStream_t s) {
-  k_coef3d_df<<<grid3(g, g.n + 1, g.n + 1, g.n + 1), block3(g), 0, s>>>(
-      g.n, g.pitch, g.stride, ct.tab, ct.tablo, ct.cst, c);
-}
-
 void coef3d_setup(const Grid& g, const PotentialParams* p, const Coef3D& c, cudaStream_t s) {
   k_coef1d_3d<<<dim3((g.n + 1 + 127) / 128, g.nb), 128, 0, s>>>(g.n, g.h, p, c.tab);
-  k_coef3d<<<grid3(g, g.n + 1, g.n + 1, g.n + 1), block3(g), 0, s>>>(g.n, g.pitch, g.stride, g.h,
-                                                                      c.tab, p, c);
+  const int rows = (g.n + 1) * (g.n + 1);
+  k_coef3d<<<dim3((rows + 7) / 8, g.nb), 256, 0, s>>>(g.n, g.pitch, g.stride, g.h, c.tab, p, c);
 }
 
 #define INTERIOR_LAUNCH(g) grid3(g, g.n - 1, g.n - 1, g.n - 1), block3(g), 0, s
