@@ -179,7 +179,8 @@ constexpr int kCstOmega = 4;
 constexpr int kCstOmegaLo = 5;
 constexpr int kCstLo = 8;
 
-// hi[i] + lo[i] = u[i] to ~2^-48 relative, i < n
+// hi[i] + lo[i] = u[i] to 2^-47 relative (hi: u[i]'s significand cut to 24 bits), i < n;
+// n even, the arrays allocation-aligned
 void split_df(const double* u, float* hi, float* lo, size_t n, cudaStream_t s);
 // Storage of the single-precision V-cycle arrays (the float* below): FP32, or bfloat16 when
 // `bf` is set (FMG_MIXED_BF16; arithmetic stays FP32).  Bytes per element:
