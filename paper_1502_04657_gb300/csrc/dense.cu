@@ -81,9 +81,11 @@ __device__ double block_sum(double v, double* red) {
   return t;
 }
 
-// 1 / d by Newton's iteration from a single-precision seed (two steps reach FP64 rounding).
+// 1 / d by Newton's iteration from the hardware's approximate reciprocal (about 2^-20 relative
+// error; two steps reach FP64 rounding).
 __device__ __forceinline__ double recip(double d) {
-  double y = (double)__frcp_rn((float)d);
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
   y = fma(y, fma(-d, y, 1.0), y);
   y = fma(y, fma(-d, y, 1.0), y);
   return y;

@@ -50,10 +50,12 @@ __global__ void k_coef1d(int n, double h, const PotentialParams* __restrict__ pp
   tab[7 * s + x] = wl * h4 * p.wy * ad;
 }
 
-// 1 / c by Newton's iteration y <- y (2 - c y) from a single-precision seed: two steps take
-// the seed's 2^-23 relative error below FP64 rounding (4 DFMA instead of a full division).
+// 1 / c by Newton's iteration y <- y (2 - c y) from the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64, measured 2^-20 relative error on this part): two steps take it below FP64
+// rounding (4 DFMA, no conversions on the FP64 pipe, instead of a full division).
 __device__ __forceinline__ double recip(double c) {
-  double y = (double)__frcp_rn((float)c);
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(c));
   y = fma(y, fma(-c, y, 1.0), y);
   y = fma(y, fma(-c, y, 1.0), y);
   return y;

@@ -67,8 +67,12 @@ __global__ void k_coef1d_3d(int n, double h, const PotentialParams* __restrict__
     for (int q = 0; q < 5; ++q) tab[(ax * 5 + q) * s + x] = wl * h5 * w[ax] * poly[q];
 }
 
+// 1 / c by Newton's iteration y <- y (2 - c y) from the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64, measured 2^-20 relative error on this part): two steps take it below FP64
+// rounding (4 DFMA, no conversions on the FP64 pipe, instead of a full division).
 __device__ __forceinline__ double recip(double c) {
-  double y = (double)__frcp_rn((float)c);
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(c));
   y = fma(y, fma(-c, y, 1.0), y);
   y = fma(y, fma(-c, y, 1.0), y);
   return y;
