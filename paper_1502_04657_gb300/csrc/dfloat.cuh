@@ -87,6 +87,19 @@ __device__ __forceinline__ double f2d_exact(float f) {
 
 __device__ __forceinline__ double to_double(dfloat x) { return f2d_exact(x.hi) + f2d_exact(x.lo); }
 
+// FP64 -> FP32 rounded to nearest (ties to even) on the integer pipes: for results in the
+// normal FP32 range the same bits as the hardware conversion, which takes everything else
+// (zero, magnitudes below the smallest normal float, inf, NaN).
+__device__ __forceinline__ float d2f_rn(double v) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+  if (e < 897u || e > 1150u) return __double2float_rn(v);
+  uint64_t m = b & 0x7fffffffffffffffull;   // exponent and significand
+  m += 0x0fffffffull + ((m >> 29) & 1ull);  // round half to even at bit 29 (a carry may reach inf)
+  const uint32_t r = (uint32_t)((m >> 29) - (896ull << 23));
+  return __uint_as_float(r | ((uint32_t)(b >> 32) & 0x80000000u));
+}
+
 // The nonlinear kernels read u either as FP64 or as its split copy (SplitVec: hi and lo
 // arrays written by split_df) and compute in T.
 template <typename T>

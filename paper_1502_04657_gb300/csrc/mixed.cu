@@ -13,6 +13,7 @@
 // L x = f.
 #include <cuda_bf16.h>
 
+#include "dfloat.cuh"
 #include "fmg_internal.h"
 
 namespace fmg {
@@ -54,9 +55,9 @@ __global__ void k_split_df(size_t n, const double* __restrict__ u, float* __rest
 // hi = v with its significand cut to 24 bits, formed from the bit pattern by integer
 // operations (|v| below the smallest normal float gives hi = 0), and lo = RN(v - hi), whose
 // difference is exact: |v - hi - lo| <= 2^-24 |v - hi| <= 2^-47 |v| while lo is a normal
-// float (|v| above about 1e-30, as for the rounded split).  That is two FP64-pipe
-// operations per element (one subtraction, one conversion) where the rounded split above takes
-// four (three conversions and a subtraction), on a pipe that retires about 2 per SM and clock.
+// float (|v| above about 1e-30, as for the rounded split).  That is one FP64-pipe operation
+// per element (the subtraction; both conversions run on the integer pipes) where the split
+// with hardware conversions takes four, on a pipe that retires about 2 per SM and clock.
 __device__ __forceinline__ void split_trunc(double v, float& hi, float& lo) {
   const long long b = __double_as_longlong(v);
   const int e = (int)((b >> 52) & 0x7ff);
@@ -68,7 +69,7 @@ __device__ __forceinline__ void split_trunc(double v, float& hi, float& lo) {
     hi = __uint_as_float(hb);
     hd = __longlong_as_double(b & ~0x1fffffffLL);
   }
-  lo = __double2float_rn(v - hd);
+  lo = d2f_rn(v - hd);
 }
 
 __global__ void k_split_u(size_t n2, const double2* __restrict__ u, float2* __restrict__ hi,
@@ -88,7 +89,7 @@ template <typename S>
 __global__ void k_add_s(size_t n, const S* __restrict__ e, double* __restrict__ x) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
-    x[i] += (double)ld(e, i);
+    x[i] += f2d_exact(ld(e, i));
 }
 
 // thread (i, j) of instance ib = blockIdx.z; k is its element index in the batched arrays
@@ -111,7 +112,7 @@ __global__ void k_residual_mixed2d(int n, int pitch, size_t st_, Coef2D c,
   v = fma(c.cN[k - pitch], x[k - pitch], v);
   v = fma(c.cNE[k], x[k + pitch + 1], v);
   v = fma(c.cNE[k - pitch - 1], x[k - pitch - 1], v);
-  st(r, k, (float)(f[k] - v));
+  st(r, k, d2f_rn(f[k] - v));
 }
 
 // ---- single-precision 2D stencil kernels -----------------------------------------------------
@@ -316,7 +317,7 @@ __global__ void k_residual_mixed3d(int n, int pitch, size_t st_, Coef3D c,
     v = fma(c.a[1 + d][k], x[k + o], v);
     v = fma(c.a[1 + d][k - o], x[k - o], v);
   }
-  st(r, k, (float)(f[k] - v));
+  st(r, k, d2f_rn(f[k] - v));
 }
 
 // Coefficients of a 3D node p from the instance's tables T(ax, q)[c] = tab[(ax 5 + q) s + c]
