@@ -76,6 +76,10 @@ void lv_mass(Level& l, const double* x, double* y, cudaStream_t s) {
   if (l.g.dim == 2) mass2d(l.g, x, y, s);
   else mass3d(l.g, x, y, s);
 }
+void lv_mass_df(Level& l, SplitVec x, double* y, cudaStream_t s) {
+  if (l.g.dim == 2) mass2d_df(l.g, x, y, s);
+  else mass3d_df(l.g, x, y, s);
+}
 void lv_jacobi(Level& l, const double* f, const double* x, double* xo, bool zero, cudaStream_t s) {
   if (l.g.dim == 2) jacobi2d(l.g, l.c, f, x, xo, zero, s);
   else jacobi3d(l.g, l.c3, f, x, xo, zero, s);
@@ -128,8 +132,7 @@ void lv_rhs_df(Level& l, const double* lam, const PotentialParams* p, const doub
   if (l.g.dim == 2) rhs2d_df(l.g, lam, p, v, f, s);
   else rhs3d_df(l.g, lam, p, v, f, s);
 }
-void lv_nload_density_df(Level& l, const double* u, double* nl, cudaStream_t s) {
-  const SplitVec v = lv_split(l, u, s);
+void lv_nload_density_df(Level& l, SplitVec v, double* nl, cudaStream_t s) {
   if (l.g.dim == 2) nload_density2d_df(l.g, v, nl, l.b, s);
   else nload_density3d_df(l.g, v, nl, l.b3, s);
 }
@@ -856,6 +859,8 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
     lv_nload_density(l, ut, l.r, s);
     prof_end(h, kProfMoments, k, s);
   }
+  // mixed modes: the double-float split of u~, read by N(u~) / B(u~) and by the mass apply
+  const SplitVec us = h->mixed() ? lv_split(l, ut, s) : SplitVec{};
   fork_sides(h, s, 0, 2);
   // branch 1 (side 0): N(u~) and B(u~) (mixed modes), T0, and the restriction / coarsening
   // chains of both
@@ -863,7 +868,7 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
     const cudaStream_t b1 = h->side[0];
     if (h->mixed()) {
       prof_begin(h, kProfMoments, k, b1);
-      lv_nload_density_df(l, ut, l.r, b1);
+      lv_nload_density_df(l, us, l.r, b1);
       prof_end(h, kProfMoments, k, b1);
     }
     dot(ut, l.r, st, h->partials2, h->t0, b1, nb, st);
@@ -879,9 +884,12 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
     lv_t3(l, h->prob.coarse_cells, ut, h->t3_partials, h->t3, b2);
     prof_end(h, kProfT3, k, b2);
   }
-  // main branch: (A + W) u~, M u~, their dots and restriction chains
+  // main branch: (A + W) u~, M u~, their dots and restriction chains.  The mixed modes form
+  // M u~ in double-float on the FP32 pipes (positive weights: ~2^-47 of the result); the
+  // operator apply stays FP64 (its stencil cancels to O(h^2) of its terms).
   lv_apply_full(l, ut, l.y, s);
-  lv_mass(l, ut, l.z, s);
+  if (h->mixed()) lv_mass_df(l, us, l.z, s);
+  else lv_mass(l, ut, l.z, s);
   dot(ut, l.y, st, h->partials, h->auu, s, nb, st);
   dot(ut, l.z, st, h->partials, h->buu, s, nb, st);
   for (int j = k; j >= 2; --j) {
@@ -1012,7 +1020,7 @@ void time_mix(fmg_eig_handle* h, Level& l, int k, cudaStream_t s) {
       lv_jacobi(l, l.f, l.x, l.xt, false, s);
   }
   if (h->mixed()) {
-    lv_nload_density_df(l, l.u, l.r, s);
+    lv_nload_density_df(l, lv_split(l, l.u, s), l.r, s);
     lv_rhs_df(l, h->lam, h->dparams, l.u, l.f, s);
   } else {
     lv_nload_density(l, l.u, l.r, s);

@@ -63,6 +63,8 @@ struct PotentialParams {
 void coef2d_setup(const Grid& g, const PotentialParams* p_dev, const Coef2D& c, cudaStream_t s);
 void apply2d(const Grid& g, const Coef2D& c, const double* x, double* y, cudaStream_t s);
 void mass2d(const Grid& g, const double* x, double* y, cudaStream_t s);
+// the same from the double-float split of x (mixed-precision modes)
+void mass2d_df(const Grid& g, SplitVec x, double* y, cudaStream_t s);
 // f -= W u, W u = (A + W) u - A u from the coefficient sets cw (A + W) and ca (A)
 void sub_wmass2d(const Grid& g, const Coef2D& cw, const Coef2D& ca, const double* u, double* f,
                  cudaStream_t s);
@@ -113,6 +115,7 @@ struct Stencil15 {
 void coef3d_setup(const Grid& g, const PotentialParams* p_dev, const Coef3D& c, cudaStream_t s);
 void apply3d(const Grid& g, const Coef3D& c, const double* x, double* y, cudaStream_t s);
 void mass3d(const Grid& g, const double* x, double* y, cudaStream_t s);
+void mass3d_df(const Grid& g, SplitVec x, double* y, cudaStream_t s);
 void sub_wmass3d(const Grid& g, const Coef3D& cw, const Coef3D& ca, const double* u, double* f,
                  cudaStream_t s);
 void jacobi3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* xo,

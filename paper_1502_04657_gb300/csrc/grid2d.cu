@@ -122,6 +122,18 @@ __global__ void k_mass2d(int n, int pitch, size_t st, double h2_12, const double
   y[k] = h2_12 * fma(6.0, x[k], s);
 }
 
+// The same mass apply in double-float arithmetic from the split of x (mixed-precision modes'
+// augmented pass): every weight is positive, so the sloppy double-float sums keep ~2^-47 of
+// the result; FP64 output.
+__global__ void k_mass2d_df(int n, int pitch, size_t st, dfloat h2_12, SplitVec x,
+                            double* __restrict__ y) {
+  INTERIOR_2D
+  auto X = [&](size_t q) { return get<dfloat>(x, q); };
+  const dfloat s = ((X(k + 1) + X(k - 1)) + (X(k + pitch) + X(k - pitch))) +
+                   (X(k + pitch + 1) + X(k - pitch - 1));
+  y[k] = to_double(h2_12 * fma(dfloat(6), X(k), s));
+}
+
 __global__ void k_jacobi2d(int n, int pitch, size_t st, Coef2D c, const double* __restrict__ f,
                            const double* __restrict__ x, double* __restrict__ xo) {
   INTERIOR_2D
@@ -341,7 +353,7 @@ __global__ void k_rhs2d_f32(int n, int pitch, size_t st, float h2_12, float h2_1
   const float s = (((float)u[k + 1] + (float)u[k - 1]) + ((float)u[k + pitch] + (float)u[k - pitch])) +
                   ((float)u[k + pitch + 1] + (float)u[k - pitch - 1]);
   const float mu = h2_12 * fmaf(6.0f, (float)u[k], s);
-  f[k] = (double)fmaf((float)lam[ib], mu, -nscale * nload_at<float>(u, k, pitch));
+  f[k] = f2d_exact(fmaf((float)lam[ib], mu, -nscale * nload_at<float>(u, k, pitch)));
 }
 
 __global__ void k_dense_level1_2d(int n, int pitch, size_t st, double h2_12, Coef2D c,
@@ -411,6 +423,11 @@ void sub_wmass2d(const Grid& g, const Coef2D& cw, const Coef2D& ca, const double
 void mass2d(const Grid& g, const double* x, double* y, cudaStream_t s) {
   k_mass2d<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(g.n, g.pitch, g.stride,
                                                                  g.h * g.h / 12.0, x, y);
+}
+
+void mass2d_df(const Grid& g, SplitVec x, double* y, cudaStream_t s) {
+  k_mass2d_df<<<grid_of(g, g.n - 1, g.n - 1), block_of(g), 0, s>>>(
+      g.n, g.pitch, g.stride, dfloat(g.h * g.h / 12.0), x, y);
 }
 
 void jacobi2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* xo,

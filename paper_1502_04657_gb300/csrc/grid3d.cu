@@ -195,6 +195,14 @@ __global__ void k_mass3d(int n, int pitch, size_t st, double h3, const double* _
   y[k] = h3 * mass_at(x, k, pitch, plane);
 }
 
+// The same in double-float arithmetic from the split of x (mixed-precision modes' augmented
+// pass; positive weights, so ~2^-47 of the result); FP64 output.
+__global__ void k_mass3d_df(int n, int pitch, size_t st, dfloat h3, SplitVec x,
+                            double* __restrict__ y) {
+  INTERIOR_3D
+  y[k] = to_double(h3 * mass_at<dfloat>(x, k, pitch, plane));
+}
+
 // r_c = P^T r_f: own fine value plus half of the 14 fine neighbours along the mesh edges.
 // r_c = P^T r_f for coarse nodes (2P, J, L) and (2P + 1, J, L) on one thread: each of the
 // seven fine rows the pair touches (rows 2J + dy of planes 2L + dz) is read as 16-byte pairs
@@ -536,7 +544,7 @@ __global__ void k_rhs3d_f32(int n, int pitch, size_t st, float h3, float nscale,
   float nl;
   star3<float, false>(u, k, pitch, plane, nl, nullptr);
   const float mu = h3 * mass_at<float>(u, k, pitch, plane);
-  f[k] = (double)fmaf((float)lam[ib], mu, -((float)pp[ib].zeta * nscale) * nl);
+  f[k] = f2d_exact(fmaf((float)lam[ib], mu, -((float)pp[ib].zeta * nscale) * nl));
 }
 
 // The same right-hand side in double-float arithmetic from the split u (mixed-precision
@@ -721,6 +729,10 @@ void sub_wmass3d(const Grid& g, const Coef3D& cw, const Coef3D& ca, const double
 
 void mass3d(const Grid& g, const double* x, double* y, cudaStream_t s) {
   k_mass3d<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, g.h * g.h * g.h, x, y);
+}
+
+void mass3d_df(const Grid& g, SplitVec x, double* y, cudaStream_t s) {
+  k_mass3d_df<<<INTERIOR_LAUNCH(g)>>>(g.n, g.pitch, g.stride, dfloat(g.h * g.h * g.h), x, y);
 }
 
 void jacobi3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* xo,
