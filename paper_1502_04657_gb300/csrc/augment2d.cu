@@ -183,7 +183,7 @@ __global__ void k_coarsen_density2d(int nc, int pc, int pf, size_t stc, size_t s
 //   [22..24] vertex values (T0: V00, V10, V11;  T1: V00, V11, V01)
 constexpr int kSums = 25;
 constexpr int kSumThreads = 256;
-constexpr int kSumRows = 256;
+constexpr int kSumRows = 1024;
 
 template <int T>
 __device__ void t3_sums_body(int pf, int n1, int r, const double* __restrict__ u,
