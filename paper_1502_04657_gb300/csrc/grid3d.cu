@@ -453,6 +453,10 @@ __global__ void k_rhs3d_node(int n, int pitch, size_t st, double h3, double nsca
   f[k] = fma(lam[ib], mu, -(pp[ib].zeta * nscale) * nl);
 }
 
+// Three blocks per SM (74 KB of shared memory each, registers capped at 80) for the walks
+// that fit without spills; the FP64 density walk keeps two (at three it spills and measured
+// slower: 7.98 against 7.93 ms on the finest 3D level, where the right-hand side went from
+// 5.28 to 5.19 ms and the double-float walks from 2.28 / 1.46 to 2.22 / 1.26 ms).
 // FP64 kernels from the plane walk (star3d.cuh): 6 x the star sum of
 // h3 + u_p h2 + u_p^2 h1 + u_p^3 is S3 + 3 u_p S2 + 6 u_p^2 S1 + 144 u_p^3 in its sums of
 // h1, 2 h2, 6 h3; launch with star3_grid / star3_block and kS3Smem bytes.
@@ -461,7 +465,7 @@ __device__ __forceinline__ T star3_cubic6(const Star3T<T>& p) {
   return fma(p.u, fma(p.u, fma(T(144), p.u, T(6) * p.S1), T(3) * p.S2), p.S3);
 }
 
-__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+__global__ void __launch_bounds__(kS3X * kS3Y, 3)
     k_nload3d(int n, int pitch, size_t st, double scale6, const double* __restrict__ u,
               double* __restrict__ out) {
   star3_walk<false>(n, pitch, st, u, [&](size_t k, const Star3& p) {
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(kS3X * kS3Y, 2)
 }
 
 // f = lambda M u - zeta N(u); the mass stencil is h^3/120 (24 u_p + S1)
-__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+__global__ void __launch_bounds__(kS3X * kS3Y, 3)
     k_rhs3d(int n, int pitch, size_t st, double h3_120, double nscale6,
             const double* __restrict__ lam, const PotentialParams* __restrict__ pp,
             const double* __restrict__ u, double* __restrict__ f) {
@@ -504,7 +508,7 @@ __global__ void __launch_bounds__(kS3X * kS3Y, 2)
 // density stencil is stored split (put_entry) for the coarsening chain, N(u~) and the
 // right-hand side are combined in FP64.  Forming each tetrahedron's symmetric sums once
 // needs about half the double-float operations of the node-by-node form (k_*_node below).
-__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+__global__ void __launch_bounds__(kS3X * kS3Y, 3)
     k_nload_density3d_df(int n, int pitch, size_t st, dfloat s140_6, dfloat s210_2,
                          dfloat s420_2, SplitVec u, double* __restrict__ nl, Density3D b) {
   star3_walk<true, dfloat>(n, pitch, st, u, [&](size_t k, const Star3T<dfloat>& p) {
@@ -520,7 +524,7 @@ __global__ void __launch_bounds__(kS3X * kS3Y, 2)
   });
 }
 
-__global__ void __launch_bounds__(kS3X * kS3Y, 2)
+__global__ void __launch_bounds__(kS3X * kS3Y, 3)
     k_rhs3d_dfw(int n, int pitch, size_t st, dfloat h3_120, dfloat nscale6,
                 const double* __restrict__ lam, const PotentialParams* __restrict__ pp, SplitVec u,
                 double* __restrict__ f) {
