@@ -93,9 +93,10 @@ void lv_residual(Level& l, const double* f, const double* x, double* r, cudaStre
   if (l.g.dim == 2) residual2d(l.g, l.c, f, x, r, s);
   else residual3d(l.g, l.c3, f, x, r, s);
 }
-void lv_restrict(Level& fl, Level& cl, const double* rf, double* rc, cudaStream_t s) {
-  if (fl.g.dim == 2) restrict2d(fl.g, cl.g, rf, rc, s);
-  else restrict3d(fl.g, cl.g, rf, rc, s);
+void lv_restrict(Level& fl, Level& cl, const double* rf, double* rc, cudaStream_t s,
+                 const double* rf2 = nullptr, double* rc2 = nullptr) {
+  if (fl.g.dim == 2) restrict2d(fl.g, cl.g, rf, rc, s, rf2, rc2);
+  else restrict3d(fl.g, cl.g, rf, rc, s, rf2, rc2);
 }
 void lv_prolong(Level& fl, Level& cl, const double* ec, double* xf, bool add, const double* extra,
                 const double* scale, int scale_stride, cudaStream_t s) {
@@ -892,10 +893,8 @@ void enqueue_augment(fmg_eig_handle* h, int k, const double* ut, cudaStream_t s)
   else lv_mass(l, ut, l.z, s);
   dot(ut, l.y, st, h->partials, h->auu, s, nb, st);
   dot(ut, l.z, st, h->partials, h->buu, s, nb, st);
-  for (int j = k; j >= 2; --j) {
-    lv_restrict(h->L(j), h->L(j - 1), h->L(j).y, h->L(j - 1).y, s);
-    lv_restrict(h->L(j), h->L(j - 1), h->L(j).z, h->L(j - 1).z, s);
-  }
+  for (int j = k; j >= 2; --j)  // both chains in one launch per level
+    lv_restrict(h->L(j), h->L(j - 1), h->L(j).y, h->L(j - 1).y, s, h->L(j).z, h->L(j - 1).z);
   join_sides(h, s, 0, 2);
   Level& l1 = h->L(1);
   lv_gather_level1(l1, h->gAd, h->gMd, h->t1d, h->B1d, s, h->mixed());

@@ -34,6 +34,12 @@ struct Grid {
 
 // A vector split into double-float halves (hi + lo, FP32 each) for the nonlinear kernels of
 // the mixed-precision modes, which compute in double-float arithmetic on the FP32 pipes.
+// up to two vectors restricted by one launch
+struct RestrictVecs {
+  const double* rf[2];
+  double* rc[2];
+};
+
 struct SplitVec {
   const float* hi;
   const float* lo;
@@ -76,8 +82,9 @@ void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x
 // x_zero); needs the coefficients built with omega = 1 (dinv = 1/D)
 void cheb2d(const Grid& g, const Coef2D& c, const double* f, const double* x, double* d,
             double* xo, double alpha, double beta, bool first, bool x_zero, cudaStream_t s);
+// rc = P^T rf; with rf2 given, also rc2 = P^T rf2 in the same launch
 void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
-                cudaStream_t s);
+                cudaStream_t s, const double* rf2 = nullptr, double* rc2 = nullptr);
 // xf = (add ? xf : 0) + P ec (+ scale[b * scale_stride] * extra for instance b when extra is
 // given)
 void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
@@ -125,7 +132,7 @@ void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x
 void cheb3d(const Grid& g, const Coef3D& c, const double* f, const double* x, double* d,
             double* xo, double alpha, double beta, bool first, bool x_zero, cudaStream_t s);
 void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
-                cudaStream_t s);
+                cudaStream_t s, const double* rf2 = nullptr, double* rc2 = nullptr);
 void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
                const double* extra, const double* scale, int scale_stride, cudaStream_t s);
 void nload3d(const Grid& g, const double* u, double* out, cudaStream_t s);

@@ -172,12 +172,15 @@ __global__ void k_residual2d(int n, int pitch, size_t st, Coef2D c, const double
 // 4P - 2 .. 4P + 3 of rows 2J - 1 .. 2J + 1 as three 16-byte loads per row (all inside the
 // array: row 2J - 1 >= 1 starts past column 1, and the pitch leaves room past column
 // nf + 1), the pair stored as one 16-byte vector when both are interior.
-__global__ void k_restrict2d(int nc, int pc, int pf, size_t stc, size_t stf,
-                             const double* __restrict__ rf, double* __restrict__ rc) {
+// blockIdx.z = q nb + ib: vector q of vecs, instance ib.
+__global__ void k_restrict2d(int nc, int pc, int pf, size_t stc, size_t stf, RestrictVecs vecs,
+                             int nb) {
   const int P = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
   if (2 * P >= nc || J >= nc) return;
-  const int ib = blockIdx.z;
+  const int q = blockIdx.z / nb, ib = blockIdx.z - q * nb;
+  const double* __restrict__ rf = vecs.rf[q];
+  double* __restrict__ rc = vecs.rc[q];
   const double* r0 = rf + ib * stf + at(4 * P - 2, 2 * J - 1, pf);  // column 4P - 2, row 2J - 1
   double v[3][6];
 #pragma unroll
@@ -453,11 +456,13 @@ void residual2d(const Grid& g, const Coef2D& c, const double* f, const double* x
 }
 
 void restrict2d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
-                cudaStream_t s) {
+                cudaStream_t s, const double* rf2, double* rc2) {
+  const RestrictVecs v{{rf, rf2}, {rc, rc2}};
+  const int nv = rf2 ? 2 : 1;
   const dim3 block(32, 8);
-  const dim3 grid((coarse.n / 2 + 32) / 32, (coarse.n - 1 + 7) / 8, fine.nb);
+  const dim3 grid((coarse.n / 2 + 32) / 32, (coarse.n - 1 + 7) / 8, nv * fine.nb);
   k_restrict2d<<<grid, block, 0, s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride,
-                                      fine.stride, rf, rc);
+                                      fine.stride, v, fine.nb);
 }
 
 void prolong2d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,

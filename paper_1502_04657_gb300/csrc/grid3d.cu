@@ -210,12 +210,16 @@ __global__ void k_mass3d_df(int n, int pitch, size_t st, dfloat h3, SplitVec x,
 // room past column nf + 1 or continue in the next row); the pair is stored as one vector
 // when both are interior.  Per node the sums run in direction order as a node-by-node
 // evaluation would: s = sum_d (r(c + o_d) + r(c - o_d)), r_c = 0.5 s + r(c).
-__global__ void k_restrict3d(int nc, int pc, int pf, size_t stc, size_t stf,
-                             const double* __restrict__ rf, double* __restrict__ rc) {
+// blockIdx.z = (q nb + ib) (nc - 1) + L - 1: vector q of vecs, instance ib, coarse plane L.
+__global__ void k_restrict3d(int nc, int pc, int pf, size_t stc, size_t stf, RestrictVecs vecs,
+                             int nb) {
   const int P = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-  const int ib = blockIdx.z / (nc - 1);
-  const int L = 1 + (int)blockIdx.z - ib * (nc - 1);
+  const int qb = blockIdx.z / (nc - 1);
+  const int L = 1 + (int)blockIdx.z - qb * (nc - 1);
+  const int q = qb / nb, ib = qb - q * nb;
+  const double* __restrict__ rf = vecs.rf[q];
+  double* __restrict__ rc = vecs.rc[q];
   if (2 * P >= nc || J >= nc) return;
   const long planef = (long)(2 * nc + 1) * pf;
   const double* base = rf + ib * stf + (size_t)(2 * L) * planef + (size_t)(2 * J) * pf + 4 * P;
@@ -757,10 +761,18 @@ void residual3d(const Grid& g, const Coef3D& c, const double* f, const double* x
 }
 
 void restrict3d(const Grid& fine, const Grid& coarse, const double* rf, double* rc,
-                cudaStream_t s) {
-  const dim3 grid((coarse.n / 2 + 32) / 32, (coarse.n - 1 + 7) / 8, (coarse.n - 1) * fine.nb);
+                cudaStream_t s, const double* rf2, double* rc2) {
+  if (rf2 && (long)(coarse.n - 1) * 2 * fine.nb > 65535) {  // grid z limit: one at a time
+    restrict3d(fine, coarse, rf, rc, s);
+    restrict3d(fine, coarse, rf2, rc2, s);
+    return;
+  }
+  const RestrictVecs v{{rf, rf2}, {rc, rc2}};
+  const int nv = rf2 ? 2 : 1;
+  const dim3 grid((coarse.n / 2 + 32) / 32, (coarse.n - 1 + 7) / 8,
+                  (coarse.n - 1) * nv * fine.nb);
   k_restrict3d<<<grid, dim3(32, 8), 0, s>>>(coarse.n, coarse.pitch, fine.pitch, coarse.stride,
-                                            fine.stride, rf, rc);
+                                            fine.stride, v, fine.nb);
 }
 
 void prolong3d(const Grid& fine, const Grid& coarse, const double* ec, double* xf, bool add,
