@@ -37,13 +37,15 @@ __device__ __forceinline__ void monomials(double a, double b, double c, double* 
   m[15] = a * m[9]; m[16] = m[7] * b; m[17] = m[7] * c; m[18] = b * m[9]; m[19] = m[9] * c;
 }
 
-// Interior class: thread = one (x0, x2) line of the coarse cell along x1, x0 fastest across
-// the threads (coalesced loads), block (chunk of lines, tet, instance).  On a line, the nodes
+// Interior class: a thread takes (x0, x2) lines of the coarse cell along x1 (kLinesPerThread of
+// them, strided by the grid; x0 fastest across the threads: coalesced loads), block (chunk of
+// lines, tet, instance), and adds their monomial sums before one block reduction (most of
+// a line's FP64 work had been that reduction, many lines being empty).  On a line, the nodes
 // strictly inside T_s are an interval of x1 (the chain order a > b > c of T_s bounds x1 by the
 // line's two other coordinates), and every monomial is (powers of the line's fixed chain
 // coordinates) x (a power of x1 / r): the thread sums u (x1/r)^e, e = 0..3, along its
 // interval with the powers from the level's table pw (4 FMAs per node, in two interleaved
-// sets of accumulators to halve the FP64 dependency chain) and then forms the 20 monomial
+// sets of accumulators to halve the FP64 dependency chain) and then adds the 20 monomial
 // sums of its line.
 __constant__ int kMonoExpDev[20][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
                                        {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2},
@@ -74,8 +76,10 @@ __global__ void __launch_bounds__(kThreads)
   double acc[kMono];
 #pragma unroll
   for (int m = 0; m < kMono; ++m) acc[m] = 0.0;
-  const int line = blockIdx.x * blockDim.x + threadIdx.x;
-  if (line < R * R) {
+  // a thread takes several lines (strided over the block's chunk of the grid) and sums their
+  // monomial sums before the one block reduction
+  for (int line = blockIdx.x * blockDim.x + threadIdx.x; line < R * R;
+       line += gridDim.x * blockDim.x) {
     const int x0 = line % R, x2 = line / R;
     // the two fixed chain coordinates (positions q1 < q2, the ones other than pos1)
     const int q1 = pos1 == 0 ? 1 : 0, q2 = pos1 == 2 ? 1 : 2;
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int q = 0; q < kMono; ++q) {
         const int e0 = kMonoExpDev[q][pos1], e1 = kMonoExpDev[q][q1], e2 = kMonoExpDev[q][q2];
-        acc[q] = g1p[e1] * g2p[e2] * pick4(m0, m1, m2, m3, e0);
+        acc[q] = fma(g1p[e1] * g2p[e2], pick4(m0, m1, m2, m3, e0), acc[q]);
       }
     }
   }
@@ -253,9 +257,11 @@ __global__ void k_t3_finalize3d(int chunks, double h3, size_t pst, size_t tst,
 // (r + 1)^2 lines of a tetrahedron.  Boundary: the face rows and edge nodes of a class number
 // fewer than r, so a block of boundary_threads(r) covers them in one or a few passes.
 int interior_threads(int r) { return warps_for((long)(r + 1) * (r + 1), kThreads); }
+constexpr int kLinesPerThread = 4;  // lines summed per thread before the block reduction
 int interior_chunks(int r) {
   const long rows = (long)(r + 1) * (r + 1);
-  return (int)((rows + interior_threads(r) - 1) / interior_threads(r));
+  const long per_block = (long)interior_threads(r) * kLinesPerThread;
+  return (int)((rows + per_block - 1) / per_block);
 }
 int boundary_threads(int r) { return warps_for(r, kThreads); }
 
