@@ -257,7 +257,7 @@ __global__ void k_t3_finalize3d(int chunks, double h3, size_t pst, size_t tst,
 // (r + 1)^2 lines of a tetrahedron.  Boundary: the face rows and edge nodes of a class number
 // fewer than r, so a block of boundary_threads(r) covers them in one or a few passes.
 int interior_threads(int r) { return warps_for((long)(r + 1) * (r + 1), kThreads); }
-constexpr int kLinesPerThread = 4;  // lines summed per thread before the block reduction
+constexpr int kLinesPerThread = 8;  // lines summed per thread before the block reduction
 int interior_chunks(int r) {
   const long rows = (long)(r + 1) * (r + 1);
   const long per_block = (long)interior_threads(r) * kLinesPerThread;
