@@ -16,6 +16,8 @@
 // with m_ij the moments of phi_v over the fine triangles of v's star that lie in T.  Those
 // depend only on v's class (interior of T, one of T's three edges, one of its vertices), so
 // T3 follows from monomial sums of u~ per class: 4 FP64 FMAs per interior node.
+#include <type_traits>
+
 #include "fmg_internal.h"
 #include "reduce_dev.cuh"
 #include "dfloat.cuh"
@@ -130,10 +132,14 @@ __host__ __device__ constexpr bool in_stencil(int dx, int dy) {
          (dx == -1 && dy == -1);
 }
 
+// FP64: one FMA per pair.  Double-float: the entries (int u~^2 phi phi) are non-negative, so
+// they are summed per weight class (1, 1/2, 1/4) with double-float additions, three
+// independent chains, and scaled exactly once at the end.
 template <typename T, int TX, int TY>
 __device__ __forceinline__ T coarse_entry(const double* bC, const double* bE, const double* bN,
                                           const double* bNE, size_t kf, int pf) {
   T acc = 0;
+  T part[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int p = 0; p < 7; ++p) {
 #pragma unroll
@@ -141,11 +147,20 @@ __device__ __forceinline__ T coarse_entry(const double* bC, const double* bE, co
       const int dx = 2 * TX + kSX[q] - kSX[p];
       const int dy = 2 * TY + kSY[q] - kSY[p];
       if (in_stencil(dx, dy)) {
-        const T w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
         const size_t kv = kf + (long)kSY[p] * pf + kSX[p];
-        acc = fma(w, fine_entry<T>(bC, bE, bN, bNE, kv, dx, dy, pf), acc);
+        if constexpr (std::is_same<T, dfloat>::value) {
+          part[(p != 0) + (q != 0)] += fine_entry<T>(bC, bE, bN, bNE, kv, dx, dy, pf);
+        } else {
+          const T w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
+          acc = fma(w, fine_entry<T>(bC, bE, bN, bNE, kv, dx, dy, pf), acc);
+        }
       }
     }
+  }
+  if constexpr (std::is_same<T, dfloat>::value) {
+    const dfloat h1(part[1].hi * 0.5f, part[1].lo * 0.5f);
+    const dfloat h2(part[2].hi * 0.25f, part[2].lo * 0.25f);
+    acc = part[0] + (h1 + h2);
   }
   return acc;
 }

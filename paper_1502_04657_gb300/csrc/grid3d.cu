@@ -12,6 +12,8 @@
 // (Y, Z, XZ, YZ by permuting the axes; the coupling to p - d is the one of p - d to p).  The
 // mass stencil is h^3 (2/5 at C, 1/20 along axes and the body diagonal, 1/30 along face
 // diagonals).  As in 2D, the 8 coupling arrays and omega/D are materialised once per solve.
+#include <type_traits>
+
 #include "fmg_internal.h"
 #include "dfloat.cuh"
 #include "star3d.cuh"
@@ -612,7 +614,11 @@ __device__ __forceinline__ V coarse_entry3(const Density3D& f, size_t kf, int pf
   // target offset in coarse units: T = 0 self, 1 + d for +d
   const int tx = T == 0 ? 0 : kDir[T - 1][0], ty = T == 0 ? 0 : kDir[T - 1][1],
             tz = T == 0 ? 0 : kDir[T - 1][2];
+  // FP64: one FMA per pair.  Double-float: the entries (int u~^2 phi phi) are non-negative, so
+  // they are summed per weight class (1, 1/2, 1/4) with double-float additions, three
+  // independent chains, and scaled exactly once at the end.
   V acc = 0;
+  V part[3] = {V(0), V(0), V(0)};
 #pragma unroll
   for (int p = 0; p < 15; ++p) {
     const int px = p == 0 ? 0 : ((p - 1) & 1 ? -kDir[(p - 1) >> 1][0] : kDir[(p - 1) >> 1][0]);
@@ -625,11 +631,20 @@ __device__ __forceinline__ V coarse_entry3(const Density3D& f, size_t kf, int pf
       const int qz = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][2] : kDir[(q - 1) >> 1][2]);
       const int code = nb_of(2 * tx + qx - px, 2 * ty + qy - py, 2 * tz + qz - pz);
       if (code >= 0) {
-        const V w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
         const size_t kv = kf + px + (long)py * pf + (long)pz * planef;
-        acc = fma(w, fine_entry3<V>(f, kv, code, pf, planef), acc);
+        if constexpr (std::is_same<V, dfloat>::value) {
+          part[(p != 0) + (q != 0)] += fine_entry3<V>(f, kv, code, pf, planef);
+        } else {
+          const V w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
+          acc = fma(w, fine_entry3<V>(f, kv, code, pf, planef), acc);
+        }
       }
     }
+  }
+  if constexpr (std::is_same<V, dfloat>::value) {
+    const dfloat h1(part[1].hi * 0.5f, part[1].lo * 0.5f);
+    const dfloat h2(part[2].hi * 0.25f, part[2].lo * 0.25f);
+    acc = part[0] + (h1 + h2);
   }
   return acc;
 }
