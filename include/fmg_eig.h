@@ -92,12 +92,12 @@ extern "C" {
  * returns, and the solve reports FMG_ETIMEOUT for that instance.  This exercises the timeout
  * path without a fault or a hang; results of such a solve are not meaningful.               */
 #define FMG_FLAG_EXPIRE_WAITS 32
-/* flags: run the fused levels of 2D V-cycles as separate kernels, one per sweep and
- * transfer: the FP64 levels of at most 32 cells per side (damped Jacobi; otherwise one kernel
- * per V-cycle with one CTA per instance) and the single-precision levels of at most 256 cells
- * below the TMA-fed ones (mixed modes; otherwise two kernels per level on 32 x 32 tiles).
- * Both evaluate the same expressions in the same order, so the results are bit-identical;
- * the flag exists for comparison and testing.                                               */
+/* flags: run the fused levels of V-cycles as separate kernels, one per sweep and transfer:
+ * the 2D FP64 levels of at most 32 cells per side (damped Jacobi; otherwise one kernel per
+ * V-cycle with one CTA per instance) and the single-precision levels below the TMA-fed ones
+ * of at most 256 cells (2D) or 32 cells (3D) per side (mixed modes; otherwise two kernels per
+ * level on 32 x 32 or 8 x 8 x 8 tiles).  Both evaluate the same expressions in the same
+ * order, so the results are bit-identical; the flag exists for comparison and testing.      */
 #define FMG_FLAG_SEPARATE_VCYCLE 16
 
 /* Problem and method parameters.  Example 4.1 fixes the PDE; Algorithm 3.1 fixes m (vcycles)

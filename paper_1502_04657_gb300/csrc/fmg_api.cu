@@ -786,9 +786,9 @@ void enqueue_vcycle32(fmg_eig_handle* h, int j, cudaStream_t s) {
       vcycle32_mid_applies(l.g, p.nu_pre, p.nu_post)) {
     // both legs of the level in one kernel each (vcycle32_mid.cu), same results
     Level& lc = h->L(j - 1);
-    vcycle32_down2d(l.g, l.ct, lc.g, l.f32, l.x32, lc.f32, p.nu_pre, s, bf);
+    vcycle32_down(l.g, l.ct, lc.g, l.f32, l.x32, lc.f32, p.nu_pre, s, bf);
     enqueue_vcycle32(h, j - 1, s);
-    vcycle32_up2d(l.g, l.ct, lc.g, l.f32, l.x32, l.xt32, lc.x32, p.nu_post, s, bf);
+    vcycle32_up(l.g, l.ct, lc.g, l.f32, l.x32, l.xt32, lc.x32, p.nu_post, s, bf);
     std::swap(l.x32, l.xt32);
     return;
   }

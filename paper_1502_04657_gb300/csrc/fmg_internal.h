@@ -230,17 +230,20 @@ void prolong32_add(const Grid& fine, const Grid& coarse, const float* ec, float*
                    cudaStream_t s, bool bf = false);
 void coarse32(const Grid& g, const double* Linv, const float* x, float* y, cudaStream_t s,
               bool bf = false);
-// The 2D levels of a single-precision V-cycle below the TMA-fed ones (vcycle32_mid.cu), two
+// The levels of a single-precision V-cycle below the TMA-fed ones (vcycle32_mid.cu), two
 // kernels per level, bit-identical to the separate sweep, residual and transfer kernels:
 //   down: xo = nu_pre Jacobi sweeps from x = 0 on L(g) x = f, rc = P^T (f - L xo);
 //   up:   xo = nu_post Jacobi sweeps from x + P ec (xo and x distinct).
+// They take 2D levels of up to kMid32MaxCells cells per side with at most 4 + 4 sweeps, and
+// 3D levels of up to kMid32MaxCells3 with at most 2 + 2.
 constexpr int kMid32MaxCells = 256;
+constexpr int kMid32MaxCells3 = 32;  // measured: 64 no faster than the separate kernels
 bool vcycle32_mid_applies(const Grid& g, int nu_pre, int nu_post);
-void vcycle32_down2d(const Grid& g, const CoefT& ct, const Grid& gc, const float* f, float* xo,
-                     float* rc, int nu_pre, cudaStream_t s, bool bf = false);
-void vcycle32_up2d(const Grid& g, const CoefT& ct, const Grid& gc, const float* f,
-                   const float* x, float* xo, const float* ec, int nu_post, cudaStream_t s,
-                   bool bf = false);
+void vcycle32_down(const Grid& g, const CoefT& ct, const Grid& gc, const float* f, float* xo,
+                   float* rc, int nu_pre, cudaStream_t s, bool bf = false);
+void vcycle32_up(const Grid& g, const CoefT& ct, const Grid& gc, const float* f,
+                 const float* x, float* xo, const float* ec, int nu_post, cudaStream_t s,
+                 bool bf = false);
 
 // ---- Reductions (reduce.cu) -------------------------------------------------------------
 // out[b] = sum_i a[b vst + i] * b[b vst + i] over n entries for instances b < nb;
