@@ -86,10 +86,12 @@ N_SM = 152
 #     98 flop with u^2, u^3; star and edge sums 73; N, diagonal and 7 edge entries 85):
 #     256 flop; 8 B + 72 B
 # The third number counts FP64 instructions (DADD, DMUL and DFMA alike take one issue slot of
-# the FP64 pipe, 2 per SM per clock): the unit these kernels are bound by.
+# the FP64 pipe, 2 per SM per clock): the unit these kernels are bound by.  The Jacobi update
+# forms f - L x as one chain of fused multiply-adds from f, then x + (omega/D) r: 8 in 2D,
+# 16 in 3D.
 KERNELS = {
-    2: {"nload_density": (69.0, 48.0, 55.0), "jacobi": (16.0, 64.0, 9.0)},
-    3: {"nload_density": (256.0, 80.0, 218.0), "jacobi": (32.0, 96.0, 17.0)},
+    2: {"nload_density": (69.0, 48.0, 55.0), "jacobi": (16.0, 64.0, 8.0)},
+    3: {"nload_density": (256.0, 80.0, 218.0), "jacobi": (32.0, 96.0, 16.0)},
 }
 # Launches too small to fill the GPU as walks run node by node, each node forming the sums of
 # its own star: 2D 106 flop in 82 FP64 instructions (pair sums n_k + n_{k+1}), 3D 659 flop in

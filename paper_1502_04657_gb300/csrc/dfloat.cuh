@@ -55,6 +55,12 @@ __device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) { return x = 
 
 __device__ __forceinline__ dfloat operator-(dfloat x) { return dfloat(-x.hi, -x.lo); }
 
+// 2 x, exact (both parts scaled), and its FP64 counterpart: one FP64 addition
+__device__ __forceinline__ dfloat twice(dfloat x) {
+  return dfloat(__fmul_rn(2.0f, x.hi), __fmul_rn(2.0f, x.lo));
+}
+__device__ __forceinline__ double twice(double x) { return x + x; }
+
 __device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
   const float p = __fmul_rn(x.hi, y.hi);
   float e = fmaf(x.hi, y.hi, -p);  // exact: x.hi y.hi = p + e

@@ -105,14 +105,14 @@ __global__ void k_residual_mixed2d(int n, int pitch, size_t st_, Coef2D c,
                                    const double* __restrict__ f, const double* __restrict__ x,
                                    S* __restrict__ r) {
   INTERIOR_2D
-  double v = c.cC[k] * x[k];
-  v = fma(c.cE[k], x[k + 1], v);
-  v = fma(c.cE[k - 1], x[k - 1], v);
-  v = fma(c.cN[k], x[k + pitch], v);
-  v = fma(c.cN[k - pitch], x[k - pitch], v);
-  v = fma(c.cNE[k], x[k + pitch + 1], v);
-  v = fma(c.cNE[k - pitch - 1], x[k - pitch - 1], v);
-  st(r, k, d2f_rn(f[k] - v));
+  double v = fma(-c.cC[k], x[k], f[k]);  // f - L x as one chain from f
+  v = fma(-c.cE[k], x[k + 1], v);
+  v = fma(-c.cE[k - 1], x[k - 1], v);
+  v = fma(-c.cN[k], x[k + pitch], v);
+  v = fma(-c.cN[k - pitch], x[k - pitch], v);
+  v = fma(-c.cNE[k], x[k + pitch + 1], v);
+  v = fma(-c.cNE[k - pitch - 1], x[k - pitch - 1], v);
+  st(r, k, d2f_rn(v));
 }
 
 // ---- single-precision 2D stencil kernels -----------------------------------------------------
@@ -310,14 +310,14 @@ __global__ void k_residual_mixed3d(int n, int pitch, size_t st_, Coef3D c,
                                    const double* __restrict__ f, const double* __restrict__ x,
                                    S* __restrict__ r) {
   INTERIOR_3D
-  double v = c.a[0][k] * x[k];
+  double v = fma(-c.a[0][k], x[k], f[k]);  // f - L x as one chain from f
 #pragma unroll
   for (int d = 0; d < 7; ++d) {
     const long o = dir_off(d, pitch, plane);
-    v = fma(c.a[1 + d][k], x[k + o], v);
-    v = fma(c.a[1 + d][k - o], x[k - o], v);
+    v = fma(-c.a[1 + d][k], x[k + o], v);
+    v = fma(-c.a[1 + d][k - o], x[k - o], v);
   }
-  st(r, k, d2f_rn(f[k] - v));
+  st(r, k, d2f_rn(v));
 }
 
 // Coefficients of a 3D node p from the instance's tables T(ax, q)[c] = tab[(ax 5 + q) s + c]

@@ -81,7 +81,7 @@ __device__ __forceinline__ void star3_walk(int n, int pitch, size_t st, const U 
   extern __shared__ double s3sm[];
   T* const su = reinterpret_cast<T*>(s3sm);  // [3][kS3Nodes]
   T* const sq = su + 3 * kS3Nodes;           // u^2
-  T* const sc = sq + 3 * kS3Nodes;           // u^3
+  T* const sc = sq + 3 * kS3Nodes;           // 2 u^3
   T* const cube = sc + 3 * kS3Nodes;         // [kS3Vals][kS3Cubes]
   const int nzc = star3_zchunks(n);
   const int ib = blockIdx.z / nzc;
@@ -102,7 +102,7 @@ __device__ __forceinline__ void star3_walk(int n, int pitch, size_t st, const U 
       const T v2 = v * v;
       su[sl + e] = v;
       sq[sl + e] = v2;
-      sc[sl + e] = v2 * v;
+      sc[sl + e] = twice(v2 * v);  // 2 u^3: 6 h3 takes 2 p3, and doubling is exact
     }
   };
 
@@ -112,27 +112,31 @@ __device__ __forceinline__ void star3_walk(int n, int pitch, size_t st, const U 
       const int a = e % kS3CX, b = e / kS3CX;
       const int v0 = s0 + b * kS3NX + a, v1 = s1 + b * kS3NX + a;
       // corners: v, X, Y, XY in plane cz; Z, XZ, YZ, W in plane cz + 1
+      const int X = v0 + 1, Y = v0 + kS3NX, XY = v0 + kS3NX + 1;
+      const int Z = v1, XZ = v1 + 1, YZ = v1 + kS3NX;
       const T A = su[v0] + su[v1 + kS3NX + 1];
       const T QA = sq[v0] + sq[v1 + kS3NX + 1];
       const T CA = sc[v0] + sc[v1 + kS3NX + 1];
+      // the power sums of v, W and the first middle vertex, shared by its two tetrahedra
+      const T a1[3] = {A + su[X], A + su[Y], A + su[Z]};
+      const T a2[3] = {QA + sq[X], QA + sq[Y], QA + sq[Z]};
+      const T a3[3] = {CA + sc[X], CA + sc[Y], CA + sc[Z]};
       T h[6][3];
-      auto tet = [&](int t, int iS, int iD) {
-        const T h1 = A + (su[iS] + su[iD]);
-        const T p2 = QA + (sq[iS] + sq[iD]);
-        const T p3 = CA + (sc[iS] + sc[iD]);
+      auto tet = [&](int t, int m, int iD) {
+        const T h1 = a1[m] + su[iD];
+        const T p2 = a2[m] + sq[iD];
+        const T p3 = a3[m] + sc[iD];
         const T s2 = h1 * h1;
         h[t][0] = h1;
-        h[t][1] = s2 + p2;                              // 2 h2
-        h[t][2] = fma(h1, fma(T(3), p2, s2), T(2) * p3);  // 6 h3
+        h[t][1] = s2 + p2;                         // 2 h2
+        h[t][2] = fma(h1, fma(T(3), p2, s2), p3);  // 6 h3 (p3 from 2 u^3: 2 p3)
       };
-      const int X = v0 + 1, Y = v0 + kS3NX, XY = v0 + kS3NX + 1;
-      const int Z = v1, XZ = v1 + 1, YZ = v1 + kS3NX;
-      tet(0, X, XY);
-      tet(1, X, XZ);
-      tet(2, Y, XY);
-      tet(3, Y, YZ);
-      tet(4, Z, XZ);
-      tet(5, Z, YZ);
+      tet(0, 0, XY);
+      tet(1, 0, XZ);
+      tet(2, 1, XY);
+      tet(3, 1, YZ);
+      tet(4, 2, XZ);
+      tet(5, 2, YZ);
 #pragma unroll
       for (int t = 0; t < 6; ++t)
 #pragma unroll

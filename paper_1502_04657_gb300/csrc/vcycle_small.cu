@@ -21,18 +21,19 @@ __device__ __forceinline__ double warp_sum_xor(double v) {
   return v;
 }
 
-// (L x) at interior node (i, j): coefficients from the level's global arrays (index kg),
-// x from a shared-memory plane of row length w = n + 1 (zero boundary ring)
-__device__ __forceinline__ double lop_small(const Coef2D& c, size_t kg, int pitch,
-                                            const double* x, int e, int w) {
-  double v = c.cC[kg] * x[e];
-  v = fma(c.cE[kg], x[e + 1], v);
-  v = fma(c.cE[kg - 1], x[e - 1], v);
-  v = fma(c.cN[kg], x[e + w], v);
-  v = fma(c.cN[kg - pitch], x[e - w], v);
-  v = fma(c.cNE[kg], x[e + w + 1], v);
-  v = fma(c.cNE[kg - pitch - 1], x[e - w - 1], v);
-  return v;
+// f - L x at interior node (i, j) as grid2d.cu's defect(): coefficients from the level's
+// global arrays (index kg), x from a shared-memory plane of row length w = n + 1 (zero
+// boundary ring)
+__device__ __forceinline__ double defect_small(const Coef2D& c, size_t kg, int pitch, double f,
+                                               const double* x, int e, int w) {
+  double r = fma(-c.cC[kg], x[e], f);
+  r = fma(-c.cE[kg], x[e + 1], r);
+  r = fma(-c.cE[kg - 1], x[e - 1], r);
+  r = fma(-c.cN[kg], x[e + w], r);
+  r = fma(-c.cN[kg - pitch], x[e - w], r);
+  r = fma(-c.cNE[kg], x[e + w + 1], r);
+  r = fma(-c.cNE[kg - pitch - 1], x[e - w - 1], r);
+  return r;
 }
 
 __global__ void __launch_bounds__(kVThreads) k_vcycle_small2d(SmallVcycle v) {
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kVThreads) k_vcycle_small2d(SmallVcycle v) {
         const int e = jj * w + i;
         const size_t kg = ib * t.stride + (size_t)jj * t.pitch + i;
         XT[j][e] = zero ? t.c.dinv[kg] * F[j][e]
-                        : fma(t.c.dinv[kg], F[j][e] - lop_small(t.c, kg, t.pitch, X[j], e, w),
+                        : fma(t.c.dinv[kg], defect_small(t.c, kg, t.pitch, F[j][e], X[j], e, w),
                               X[j][e]);
       }
       double* tmp = X[j];
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kVThreads) k_vcycle_small2d(SmallVcycle v) {
       const int i = 1 + q % m, jj = 1 + q / m;
       const int e = jj * w + i;
       const size_t kg = ib * t.stride + (size_t)jj * t.pitch + i;
-      R[j][e] = F[j][e] - lop_small(t.c, kg, t.pitch, X[j], e, w);
+      R[j][e] = defect_small(t.c, kg, t.pitch, F[j][e], X[j], e, w);
     }
     __syncthreads();
     const int nc = v.lv[j - 1].n, wc = nc + 1, mc = nc - 1;
