@@ -76,22 +76,23 @@ WORKLOADS = {
 FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA per clock per SM (1.25 TFLOP/s nominal at 2070 MHz)
 N_SM = 152
 # Algorithmic FP64 flops and bytes per node of the finest-level launch:
-#   Jacobi 2D: 7-point L x (7 mul + 6 add) + residual + scale + update = 16 flop;
+#   Jacobi 2D: the defect f - L x as 7 multiply-adds + the update x + (omega/D) r = 16 flop;
 #     24 B (x, f, x') + 40 B (4 couplings + omega/D)
 #   cubic load + density stencil 2D (closed forms over the 6 star triangles from per-edge
 #     numbers: 3 own edges x 5 + square 1 + 3 six-term sums 15 + cubic bracket 8 + diagonal 6
 #     + 3 off-diagonal entries x 8): 69 flop; 8 B read + 40 B written
-#   Jacobi 3D: 15-point = 29 + 3 = 32 flop; 24 B + 72 B
-#   cubic load + density stencil 3D (symmetric sums of the 6 tetrahedra of a cube formed once:
-#     98 flop with u^2, u^3; star and edge sums 73; N, diagonal and 7 edge entries 85):
-#     256 flop; 8 B + 72 B
+#   Jacobi 3D: 15 multiply-adds + update = 32 flop; 24 B + 72 B
+#   cubic load + density stencil 3D (symmetric sums of the 6 tetrahedra of a cube formed once,
+#     the power sums of the base vertices and the first middle vertex shared by two tetrahedra:
+#     90 flop with u^2, 2 u^3; star and edge sums 73; N, diagonal and 7 edge entries 86):
+#     249 flop; 8 B + 72 B
 # The third number counts FP64 instructions (DADD, DMUL and DFMA alike take one issue slot of
 # the FP64 pipe, 2 per SM per clock): the unit these kernels are bound by.  The Jacobi update
 # forms f - L x as one chain of fused multiply-adds from f, then x + (omega/D) r: 8 in 2D,
 # 16 in 3D.
 KERNELS = {
     2: {"nload_density": (69.0, 48.0, 55.0), "jacobi": (16.0, 64.0, 8.0)},
-    3: {"nload_density": (256.0, 80.0, 218.0), "jacobi": (32.0, 96.0, 16.0)},
+    3: {"nload_density": (249.0, 80.0, 198.0), "jacobi": (32.0, 96.0, 16.0)},
 }
 # Launches too small to fill the GPU as walks run node by node, each node forming the sums of
 # its own star: 2D 106 flop in 82 FP64 instructions (pair sums n_k + n_{k+1}), 3D 659 flop in
@@ -139,9 +140,9 @@ def hbm_peak() -> tuple[float, str]:
 # solve, 4,190,209 nodes), scaled by the nodes a launch processes.
 TRAFFIC_PER_NODE = {(2, "nload_density"): (34.109952e6 + 106.015232e6) / 4190209,
                     # the first level-9 sweep of the 9-level 2D solve, 4,190,209 nodes
-                    (2, "jacobi"): (235150336 + 24169728) / 4190209,
+                    (2, "jacobi"): (235144960 + 24157184) / 4190209,
                     # 3D: the level-6 launch of the 6-level solve, 2,048,383 nodes
-                    (3, "nload_density"): (22.938624e6 + 83.353088e6) / 2048383}
+                    (3, "nload_density"): (22.779648e6 + 83.184128e6) / 2048383}
 
 
 def rank_info():
