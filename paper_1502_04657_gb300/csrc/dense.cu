@@ -49,9 +49,12 @@ __host__ __device__ inline bool loc_in_A(int n, int ntri, int nvert) {
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxVert = 4;
 constexpr double kSwitch = 1e-2;  // relative residual below which Newton takes over
-// refinement steps of the linear solves (single-precision inverse, FP64 residuals): a Newton
-// step needs its correction to about FP64 rounding, an inverse-power step only a direction
-constexpr int kRefineNewton = 2;
+// refinement steps of the linear solves (single-precision inverse, FP64 residuals).  The
+// single-precision inverse leaves a relative error of about 7e-7 in a solve and one step
+// squares it (~5e-13); a Newton correction is as large as the current error, so its own error
+// is then far below FP64 rounding of c (two steps gave the same iteration counts and the same
+// eigenvalues to 3e-16).  An inverse-power step needs only a direction.
+constexpr int kRefineNewton = 1;
 constexpr int kRefinePower = 1;
 
 struct Smem {
@@ -89,6 +92,24 @@ __device__ __forceinline__ double recip(double d) {
   y = fma(y, fma(-d, y, 1.0), y);
   y = fma(y, fma(-d, y, 1.0), y);
   return y;
+}
+
+// Two block-wide sums at once, each in block_sum's order (so each result is bit-identical to
+// its own block_sum), for the price of one: the second reduces in red[kWarps ..].
+__device__ double2 block_sum2(double a, double b, double* red) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = a;
+    red[kWarps + (threadIdx.x >> 5)] = b;
+  }
+  __syncthreads();
+  const int l = threadIdx.x & 31;
+  double ta = l < kWarps ? red[l] : 0.0, tb = l < kWarps ? red[kWarps + l] : 0.0;
+  ta = warp_sum(ta);
+  tb = warp_sum(tb);
+  __syncthreads();
+  return make_double2(ta, tb);
 }
 
 __device__ double dotv(const double* a, const double* b, int n, double* red) {
@@ -195,6 +216,28 @@ __device__ void local_G(const DenseProblem& p, Smem& s, double cu) {
 __device__ void build_G(const DenseProblem& p, Smem& s) {
   const int nv = p.nvert, L = s.L, nh = s.nh, n = s.n;
   const double cu = p.aug ? s.c[nh] : 0.0;
+  if (p.aug) {
+    // w = c_u u~ (the start of every augmented solve: c_H = 0 exactly): every simplex term
+    // vanishes and G is c_u^2 [B1 t1; t1^T T0], which the general path below also reaches
+    // (its sums then add only zeros), so the results are identical
+    bool any = false;
+    for (int a = threadIdx.x; a < nh; a += kThreads) any |= s.c[a] != 0.0;
+    if (!__syncthreads_or(any)) {
+      const double cu2 = cu * cu;
+      for (int e = threadIdx.x; e < nh * nh; e += kThreads) {
+        const int a = e / nh, b = e - a * nh;
+        s.G[(size_t)a * n + b] = __dmul_rn(cu2, s.B1[e]);
+      }
+      for (int a = threadIdx.x; a < nh; a += kThreads) {
+        const double g = __dmul_rn(cu2, s.t1[a]);
+        s.G[(size_t)a * n + nh] = g;
+        s.G[(size_t)nh * n + a] = g;
+      }
+      if (threadIdx.x == 0) s.G[(size_t)nh * n + nh] = __dmul_rn(cu * cu, p.t0[0]);
+      __syncthreads();
+      return;
+    }
+  }
   if (p.nvert == 3) local_G<3>(p, s, cu);
   else local_G<4>(p, s, cu);
   __syncthreads();
@@ -566,14 +609,19 @@ __device__ void normalise_and_sign(const DenseProblem& p, Smem& s) {
     double* Y[1] = {s.Mc};
     symv<1>(X, s.c, Y, n, s.sv);
   }
-  const double cmc = dotv(s.c, s.Mc, n, s.red);
-  double sg;
+  double cmc, sg;
   if (p.aug) {
+    cmc = dotv(s.c, s.Mc, n, s.red);
     sg = s.c[s.nh];
   } else {
-    double t = 0.0;
-    for (int i = threadIdx.x; i < n; i += kThreads) t += s.c[i];
-    sg = block_sum(t, s.red);
+    double d = 0.0, t = 0.0;
+    for (int i = threadIdx.x; i < n; i += kThreads) {
+      d = fma(s.c[i], s.Mc[i], d);
+      t += s.c[i];
+    }
+    const double2 dt = block_sum2(d, t, s.red);
+    cmc = dt.x;
+    sg = dt.y;
   }
   __syncthreads();  // every thread has read c before any thread rescales it
   const double f = (sg < 0.0 ? -1.0 : 1.0) / sqrt(cmc);
@@ -703,18 +751,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_dense_scf(DenseProblem p) {
   for (;; ++it) {
     build_G(p, s);
     apply_all(s);  // Hc = K0 c, Gc = G c (Mc = M c from normalise_and_sign)
-    for (int a = threadIdx.x; a < n; a += kThreads) s.Hc[a] = fma(zeta, s.Gc[a], s.Hc[a]);
-    __syncthreads();
-    lam = dotv(s.c, s.Hc, n, s.red);
-    double rr = 0.0, mm = 0.0;
+    // each thread forms, reads and later overwrites only its own rows of Hc and r here, so
+    // the loops need no barrier between them (the block sums order everything after them)
+    double lp = 0.0, mm = 0.0;
+    for (int a = threadIdx.x; a < n; a += kThreads) {
+      const double h = fma(zeta, s.Gc[a], s.Hc[a]);
+      s.Hc[a] = h;
+      lp = fma(s.c[a], h, lp);
+      mm = fma(s.Mc[a], s.Mc[a], mm);
+    }
+    const double2 lm = block_sum2(lp, mm, s.red);
+    lam = lm.x;
+    mm = lm.y;
+    double rr = 0.0;
     for (int a = threadIdx.x; a < n; a += kThreads) {
       const double r = fma(-lam, s.Mc[a], s.Hc[a]);
       s.r[a] = r;
       rr = fma(r, r, rr);
-      mm = fma(s.Mc[a], s.Mc[a], mm);
     }
     rr = block_sum(rr, s.red);
-    mm = block_sum(mm, s.red);
     const double rn = sqrt(rr) / (fabs(lam) * sqrt(mm));
     if (rn <= p.tol) {
       status = 0;
@@ -762,9 +817,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_dense_scf(DenseProblem p) {
         }
       }
       if (newton) {
-        const double m1 = dotv(s.Mc, s.y1, n, s.red);
-        const double m2 = dotv(s.Mc, s.y2, n, s.red);
-        const double dl = m1 / m2;
+        double p1 = 0.0, p2 = 0.0;
+        for (int a = threadIdx.x; a < n; a += kThreads) {
+          p1 = fma(s.Mc[a], s.y1[a], p1);
+          p2 = fma(s.Mc[a], s.y2[a], p2);
+        }
+        const double2 m12 = block_sum2(p1, p2, s.red);
+        const double dl = m12.x / m12.y;
         for (int a = threadIdx.x; a < n; a += kThreads) s.c[a] += fma(dl, s.y2[a], -s.y1[a]);
         __syncthreads();
       }
