@@ -53,8 +53,12 @@ constexpr double kSwitch = 1e-2;  // relative residual below which Newton takes 
 // single-precision inverse leaves a relative error of about 7e-7 in a solve and one step
 // squares it (~5e-13); a Newton correction is as large as the current error, so its own error
 // is then far below FP64 rounding of c (two steps gave the same iteration counts and the same
-// eigenvalues to 3e-16).  An inverse-power step needs only a direction.
+// eigenvalues to 3e-16).  While the residual is above kRefineBelow the step needs no
+// refinement at all: its error, about 7e-7 of the correction, is then below a tenth of the
+// quadratic term C e^2 (C ~ 10) that the step leaves anyway.  An inverse-power step needs
+// only a direction.
 constexpr int kRefineNewton = 1;
+constexpr double kRefineBelow = 1e-6;
 constexpr int kRefinePower = 1;
 
 struct Smem {
@@ -802,7 +806,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dense_scf(DenseProblem p) {
       double* sol[2] = {s.y1, s.y2};
       double* scr[2] = {s.Hc, s.Gc};
       g_valid = false;
-      if (!solve_refined<2>(s.A, Pinv, n, rhs, sol, scr, kRefineNewton, s.sv)) {
+      const int refine = rn < kRefineBelow ? kRefineNewton : 0;
+      if (!solve_refined<2>(s.A, Pinv, n, rhs, sol, scr, refine, s.sv)) {
         // single precision met a non-positive pivot: LDL^T in FP64
         for (int a = threadIdx.x; a < n; a += kThreads) {
           s.y1[a] = s.r[a];
