@@ -134,24 +134,29 @@ __host__ __device__ constexpr bool in_stencil(int dx, int dy) {
 
 // FP64: one FMA per pair.  Double-float: the entries (int u~^2 phi phi) are non-negative, so
 // they are summed per weight class (1, 1/2, 1/4) with double-float additions, three
-// independent chains, and scaled exactly once at the end.
+// independent chains, and scaled exactly once at the end.  The diagonal entry (TX = TY = 0)
+// pairs both supports with themselves, and (p, q), (q, p) read the same fine entry, so it
+// takes each unordered pair once with twice its weight (an exact doubling).
 template <typename T, int TX, int TY>
 __device__ __forceinline__ T coarse_entry(const double* bC, const double* bE, const double* bN,
                                           const double* bNE, size_t kf, int pf) {
+  constexpr bool kDiag = TX == 0 && TY == 0;
   T acc = 0;
   T part[3] = {T(0), T(0), T(0)};
 #pragma unroll
   for (int p = 0; p < 7; ++p) {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
+    for (int q = kDiag ? p : 0; q < 7; ++q) {
       const int dx = 2 * TX + kSX[q] - kSX[p];
       const int dy = 2 * TY + kSY[q] - kSY[p];
       if (in_stencil(dx, dy)) {
         const size_t kv = kf + (long)kSY[p] * pf + kSX[p];
+        const bool twice_w = kDiag && q != p;
         if constexpr (std::is_same<T, dfloat>::value) {
-          part[(p != 0) + (q != 0)] += fine_entry<T>(bC, bE, bN, bNE, kv, dx, dy, pf);
+          const dfloat e = fine_entry<T>(bC, bE, bN, bNE, kv, dx, dy, pf);
+          part[(p != 0) + (q != 0)] += twice_w ? twice(e) : e;
         } else {
-          const T w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
+          const T w((twice_w ? 2.0 : 1.0) * (p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
           acc = fma(w, fine_entry<T>(bC, bE, bN, bNE, kv, dx, dy, pf), acc);
         }
       }

@@ -632,7 +632,10 @@ __device__ __forceinline__ V coarse_entry3(const Density3D& f, size_t kf, int pf
             tz = T == 0 ? 0 : kDir[T - 1][2];
   // FP64: one FMA per pair.  Double-float: the entries (int u~^2 phi phi) are non-negative, so
   // they are summed per weight class (1, 1/2, 1/4) with double-float additions, three
-  // independent chains, and scaled exactly once at the end.
+  // independent chains, and scaled exactly once at the end.  The diagonal entry (T = 0) pairs
+  // the support with itself, and (p, q), (q, p) read the same fine entry, so it takes each
+  // unordered pair once with twice its weight (an exact doubling).
+  constexpr bool kDiag = T == 0;
   V acc = 0;
   V part[3] = {V(0), V(0), V(0)};
 #pragma unroll
@@ -641,17 +644,19 @@ __device__ __forceinline__ V coarse_entry3(const Density3D& f, size_t kf, int pf
     const int py = p == 0 ? 0 : ((p - 1) & 1 ? -kDir[(p - 1) >> 1][1] : kDir[(p - 1) >> 1][1]);
     const int pz = p == 0 ? 0 : ((p - 1) & 1 ? -kDir[(p - 1) >> 1][2] : kDir[(p - 1) >> 1][2]);
 #pragma unroll
-    for (int q = 0; q < 15; ++q) {
+    for (int q = kDiag ? p : 0; q < 15; ++q) {
       const int qx = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][0] : kDir[(q - 1) >> 1][0]);
       const int qy = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][1] : kDir[(q - 1) >> 1][1]);
       const int qz = q == 0 ? 0 : ((q - 1) & 1 ? -kDir[(q - 1) >> 1][2] : kDir[(q - 1) >> 1][2]);
       const int code = nb_of(2 * tx + qx - px, 2 * ty + qy - py, 2 * tz + qz - pz);
       if (code >= 0) {
         const size_t kv = kf + px + (long)py * pf + (long)pz * planef;
+        const bool twice_w = kDiag && q != p;
         if constexpr (std::is_same<V, dfloat>::value) {
-          part[(p != 0) + (q != 0)] += fine_entry3<V>(f, kv, code, pf, planef);
+          const dfloat e = fine_entry3<V>(f, kv, code, pf, planef);
+          part[(p != 0) + (q != 0)] += twice_w ? twice(e) : e;
         } else {
-          const V w((p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
+          const V w((twice_w ? 2.0 : 1.0) * (p == 0 ? 1.0 : 0.5) * (q == 0 ? 1.0 : 0.5));
           acc = fma(w, fine_entry3<V>(f, kv, code, pf, planef), acc);
         }
       }
