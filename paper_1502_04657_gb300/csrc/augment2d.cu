@@ -225,8 +225,10 @@ __device__ void t3_sums_body(int pf, int n1, int r, const double* __restrict__ u
   if (s <= r) {
     const double* col = u + (size_t)(J * r) * pf + (size_t)(I * r + s);
     // the rows of this column inside the triangle: T0 (lower) t <= s, T1 (upper) t >= s; the
-    // rows outside would add nothing
-    const int ta = T == 0 ? t0 : max(t0, s), tb = T == 0 ? min(t1, s + 1) : t1;
+    // rows outside would add nothing.  The lanes of a warp read one row per step (coalesced),
+    // so T1 starts at the warp's first column, and its lanes skip the rows above their own.
+    const int ta = T == 0 ? t0 : max(t0, s - (int)(threadIdx.x & 31));
+    const int tb = T == 0 ? min(t1, s + 1) : t1;
     for (int t = ta; t < tb; ++t) {
       const double val = col[(size_t)t * pf];
       const double* p = pw + 4 * t;  // tg^m, m = 0..3
