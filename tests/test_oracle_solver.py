@@ -37,6 +37,28 @@ def test_laplace_eigenvalue_converges_at_h_squared(dim, ns, limit):
     assert all(3.6 < x < 4.4 for x in r), r
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("omega", [2.0 / 3.0, 0.8])
+def test_jacobi_damps_each_sine_mode_by_its_closed_form_factor(dim, omega):
+    """W = 0: the P1 stiffness is the (2d+1)-point Laplacian (diagonal 4 in 2D, 6h on the 3D Kuhn
+    mesh), whose eigenvectors are the discrete sine modes, so one damped Jacobi sweep with
+    f = 0 multiplies the mode (k_1 .. k_d) by 1 - omega (2d - 2 sum cos(k_i pi h)) / (2d).
+    A wrong damping, diagonal, sign or operator changes that factor."""
+    n = 8 if dim == 2 else 6
+    prob = O.Problem(dim=dim, coarse_cells=n, levels=1, w_const=0.0, w_quad=(0.0, 0.0, 0.0),
+                     omega=omega)
+    lev = O.build_hierarchy(prob)[0]
+    ijk = lev.mesh.ijk[lev.mesh.interior]
+    h = 1.0 / n
+    for ks in [(1, 1, 1), (3, 5, 2), (n - 1, n - 1, n - 1), (1, n - 1, 4)]:
+        x = np.ones(len(ijk))
+        for ax in range(dim):
+            x *= np.sin(ks[ax] * np.pi * ijk[:, ax] * h)
+        factor = 1.0 - omega * (2 * dim - 2 * sum(np.cos(ks[ax] * np.pi * h) for ax in range(dim))) / (2 * dim)
+        y = O.jacobi(lev, np.zeros_like(x), x, omega)
+        assert np.max(np.abs(y - factor * x)) <= 1e-14, (ks, factor)
+
+
 def test_level_solve_minimises_gp_energy():
     """The SCF ground state equals the brute-force minimiser of
     E(u) = 1/2 u^T (A + W) u + zeta/4 int u^4 on u^T M u = 1 (int u^4 by independent quadrature)."""
