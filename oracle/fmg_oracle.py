@@ -30,7 +30,7 @@ Everything is written from definitions, with no blocking, fusion or reordering:
   lowest eigenpair is taken (the paper names SCF, Section 3.2), with a fixed density-mixing
   rule.
 
-Readings of the paper where it is silent (each is also listed in the design notes):
+Readings of the paper where it is silent:
 * meshes: 2D squares split along their (1,1) diagonal, 3D cubes split into the 6 Kuhn
   tetrahedra;
 * W sits on the left of the auxiliary problem, (A + W) u^ = lambda M u - N(u) (operator
