@@ -1292,19 +1292,19 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
       }
     }
   }
-  // A pinned (or registered) host buffer is written by the GPU directly through its device
-  // alias (over the CPU-GPU link, no staging copy); pageable buffers are staged in h->uout and
-  // copied.
-  std::vector<std::vector<double*>> alias(hs.size());
+  // A pinned (or registered) host buffer receives the interior of u straight from the padded
+  // finest level by one strided copy-engine transfer (no staging copy); pageable buffers are
+  // staged in h->uout and copied.
+  std::vector<std::vector<char>> pinned(hs.size());
   for (size_t g = 0; g < hs.size(); ++g) {
     fmg_eig_handle* h = hs[g];
-    alias[g].assign(h->nb, nullptr);
+    pinned[g].assign(h->nb, 0);
     for (int b = 0; u_hosts && b < h->nb; ++b) {
       const int i = out_index[g][b];
       cudaPointerAttributes attr;
       if (u_hosts[i] && cudaPointerGetAttributes(&attr, u_hosts[i]) == cudaSuccess &&
           attr.type == cudaMemoryTypeHost && attr.devicePointer)
-        alias[g][b] = static_cast<double*>(attr.devicePointer);
+        pinned[g][b] = 1;
       cudaGetLastError();
     }
   }
@@ -1319,9 +1319,9 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
       bool staged = false;
       for (int b = 0; b < h->nb; ++b) {
         if (!u_hosts[out_index[g][b]]) continue;
-        if (alias[g][b]) {
+        if (pinned[g][b]) {
           Level v = view(h->L(h->probs[b].levels), b, 1);
-          unpack_interior(v.g, v.u, alias[g][b], s);
+          CK(copy_interior_to_host(v.g, v.u, u_hosts[out_index[g][b]], s));
         } else {
           staged = true;
         }
@@ -1349,7 +1349,7 @@ int run_handles(const std::vector<fmg_eig_handle*>& hs,
     }
     for (int b = 0; u_hosts && b < nb; ++b) {
       const int i = out_index[g][b];
-      if (u_hosts[i] && !alias[g][b])
+      if (u_hosts[i] && !pinned[g][b])
         CK(cudaMemcpyAsync(u_hosts[i], h->uout + h->uoff[b], sizeof(double) * u_lens[i],
                            cudaMemcpyDeviceToHost, s));
     }

@@ -263,6 +263,10 @@ void cg_direction(size_t n, size_t stride, const double* rr_new, const double* r
 // (instance b: interior vector at b * g.interior(), padded one at b * g.stride)
 void pack_interior(const Grid& g, const double* interior, double* padded, cudaStream_t s);
 void unpack_interior(const Grid& g, const double* padded, double* interior, cudaStream_t s);
+// The interior of one instance's padded vector into a pinned host buffer by one strided
+// copy-engine transfer (2D: a pitched 2D copy, 3D: a pitched 3D copy), no staging buffer.
+cudaError_t copy_interior_to_host(const Grid& g, const double* padded, double* host,
+                                  cudaStream_t s);
 // dst[i] = src[idx[i]], i < n
 void gather_by_index(const double* src, const int* idx, double* dst, int n, cudaStream_t s);
 // padded level-1 vectors from dense coefficient vectors c (instance b at c + b * cstride)

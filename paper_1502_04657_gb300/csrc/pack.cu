@@ -50,6 +50,21 @@ void unpack_interior(const Grid& g, const double* padded, double* interior, cuda
       g.dim, g.n, g.pitch, count, count, g.stride, padded, interior);
 }
 
+cudaError_t copy_interior_to_host(const Grid& g, const double* padded, double* host,
+                                  cudaStream_t s) {
+  const size_t m = (size_t)(g.n - 1), row = m * sizeof(double), sp = (size_t)g.pitch * sizeof(double);
+  if (g.dim == 2)  // rows 1 .. n - 1, columns 1 .. n - 1
+    return cudaMemcpy2DAsync(host, row, padded + g.pitch + 1, sp, row, m,
+                             cudaMemcpyDeviceToHost, s);
+  cudaMemcpy3DParms q = {};
+  q.srcPtr = make_cudaPitchedPtr(const_cast<double*>(padded), sp, sp, (size_t)(g.n + 1));
+  q.srcPos = make_cudaPos(sizeof(double), 1, 1);  // element (1, 1, 1)
+  q.dstPtr = make_cudaPitchedPtr(host, row, row, m);
+  q.extent = make_cudaExtent(row, m, m);
+  q.kind = cudaMemcpyDeviceToHost;
+  return cudaMemcpy3DAsync(&q, s);
+}
+
 void scatter_level1(const Grid& g, const double* c, size_t cstride, double* padded,
                     cudaStream_t s) {
   const size_t count = g.interior();
